@@ -1,0 +1,334 @@
+"""FP64 CPU oracle for the SEPSO hot path (ctypes binding of ``sepso_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: this package is imported by ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``, never by the
+product package ``paper_2308_10169_gb300``.  It shares no code with the CUDA path;
+both sides consume the same seeded inputs (plain arrays) and nothing else.
+
+What each function follows (paper: arXiv 2308.10169):
+
+* ``philox`` / ``u01``      -- Philox4x32-10 (Salmon et al., SC'11); supplies the
+  uniform R1, R2, R3 of Table EXP_TOF (one scalar per particle per iteration).
+* ``seg_point_dist``        -- point-to-segment distance, the plain definition.
+* ``evaluate``              -- Eqs. path_fit, lenth, penalty (Sec. 3.3.2).
+* ``Swarm.init``            -- Algorithm 1 initialisation with Priori
+  Initialization (Sec. 3.3.3).
+* ``Swarm.iteration``       -- one pass of Algorithm 1: fitness, P/G/T update,
+  Eq. TOF_omega, Eq. TOF_V (clip), Eq. TOF_X (clip).
+* ``Swarm.plan``            -- one planning cycle with Auto Truncation (Sec. 3.3.4).
+* ``advance_scene``         -- the dynamic simulator step (Fig. PP caption).
+* ``hsef``                  -- the hierarchical self-evolving framework
+  (Sec. 3.2.1, Eq. fit_h).
+
+Parity status of each function is recorded in the header of ``sepso_oracle.c``
+and in the tests that pin it (``tests/test_oracle_*.py``); HSEF's absolute values
+are "parity unpinned" (the paper gives only a figure), its invariants are pinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "sepso_oracle.c"
+_BUILD = _HERE / "_build"
+_LIB_PATH = _BUILD / "libsepso_oracle.so"
+
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (plain -O2, no FMA contraction)."""
+    _BUILD.mkdir(exist_ok=True)
+    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB_PATH.with_suffix(f".{os.getpid()}.tmp")
+        subprocess.run(
+            ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
+             str(_SRC), "-o", str(tmp), "-lm"],
+            check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [
+        ("T", ctypes.c_int32), ("G", ctypes.c_int32), ("N", ctypes.c_int32),
+        ("W", ctypes.c_double), ("H", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("beta", ctypes.c_int32),
+        ("max_iters", ctypes.c_int32),
+        ("at_mode", ctypes.c_int32), ("tw", ctypes.c_int32), ("delta", ctypes.c_double),
+        ("stall_iters", ctypes.c_int32), ("stall_tol", ctypes.c_double),
+        ("use_pi", ctypes.c_int32), ("pi_gamma", ctypes.c_double), ("pi_h", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32),
+    ]
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [("sx", ctypes.c_double), ("sy", ctypes.c_double),
+                ("tx", ctypes.c_double), ("ty", ctypes.c_double),
+                ("O", ctypes.c_int32), ("circ", _f64p)]
+
+
+class _State(ctypes.Structure):
+    _fields_ = [(n, _f64p) for n in ("X", "V", "P", "Pfit")] + [("PQ", _i32p)] + \
+        [(n, _f64p) for n in ("Gb", "Gfit")] + [("GQ", _i32p)] + \
+        [(n, _f64p) for n in ("Tb", "Tfit")] + [("TQ", _i32p), ("k", _i32p)] + \
+        [("cycle", _i32p), ("has_prev", _i32p), ("prevT", _f64p), ("win", _f64p),
+         ("win_n", _i32p), ("win_head", _i32p), ("stall", _i32p), ("prev_lfv", _f64p)]
+
+
+class _HsefCfg(ctypes.Structure):
+    _fields_ = [("HG", ctypes.c_int32), ("HN", ctypes.c_int32), ("E", ctypes.c_int32),
+                ("hhyper", _f64p), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("l_vlimit", ctypes.c_double), ("hseed", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(str(build()))
+        L.so_philox_batch.argtypes = [ctypes.c_int32, _u32p, ctypes.c_uint64, _u32p]
+        L.so_u01.argtypes = [ctypes.c_uint32]
+        L.so_u01.restype = ctypes.c_double
+        L.so_seg_point_dist.argtypes = [ctypes.c_double] * 6
+        L.so_seg_point_dist.restype = ctypes.c_double
+        L.so_evaluate.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene), ctypes.c_int32,
+                                  _f64p, _f64p, _i32p, _f64p]
+        L.so_tangency_margin.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene),
+                                         ctypes.c_int32, _f64p, _f64p]
+        L.so_pi_count.argtypes = [ctypes.c_double, ctypes.c_int32]
+        L.so_pi_count.restype = ctypes.c_int32
+        L.so_init_swarm.argtypes = [ctypes.POINTER(_Config), _f64p, ctypes.POINTER(_State)]
+        L.so_window_std.argtypes = [_f64p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.so_window_std.restype = ctypes.c_double
+        L.so_at_update.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_State)]
+        L.so_at_update.restype = ctypes.c_int32
+        L.so_iteration.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene), _f64p,
+                                   ctypes.POINTER(_State), ctypes.c_int32]
+        L.so_iteration.restype = ctypes.c_int32
+        L.so_plan.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene), _f64p,
+                              ctypes.POINTER(_State), _f64p]
+        L.so_step.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene), _f64p,
+                              ctypes.POINTER(_State), ctypes.c_int32]
+        L.so_advance_scene.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                       _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+        L.so_hsef.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene),
+                              ctypes.POINTER(_HsefCfg), _f64p, _f64p, _f64p]
+        _lib = L
+    return _lib
+
+
+def _p64(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_f64p)
+
+
+def _p32(a: np.ndarray):
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_i32p)
+
+
+def _cfg(c) -> _Config:
+    """Build the C struct from any object carrying the planner's config fields."""
+    return _Config(T=c.T, G=c.G, N=c.N, W=float(np.float32(c.map_w)), H=float(np.float32(c.map_h)),
+                   alpha=float(np.float32(c.alpha)), beta=c.beta, max_iters=c.max_iters,
+                   at_mode=c.at_mode, tw=c.tw, delta=float(np.float32(c.delta)),
+                   stall_iters=c.stall_iters, stall_tol=float(np.float32(c.stall_tol)),
+                   use_pi=int(c.use_pi), pi_gamma=float(np.float32(c.pi_gamma)),
+                   pi_h=float(np.float32(c.pi_halfwidth)), seed=c.seed, run_id=c.run_id)
+
+
+class Scene:
+    """A static scene in FP64 (converted exactly from the FP32 inputs)."""
+
+    def __init__(self, start, target, circles):
+        self.start = np.asarray(start, dtype=np.float64).reshape(2).copy()
+        self.target = np.asarray(target, dtype=np.float64).reshape(2).copy()
+        self.circles = np.ascontiguousarray(np.asarray(circles, dtype=np.float64).reshape(-1, 3))
+
+    def c(self) -> _Scene:
+        return _Scene(sx=self.start[0], sy=self.start[1], tx=self.target[0], ty=self.target[1],
+                      O=self.circles.shape[0], circ=_p64(self.circles))
+
+
+# ----------------------------------------------------------------------------
+# Philox and uniforms
+# ----------------------------------------------------------------------------
+
+def philox(ctr: np.ndarray, seed: int) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.zeros_like(ctr)
+    lib().so_philox_batch(ctr.shape[0], ctr.ctypes.data_as(_u32p), ctypes.c_uint64(seed),
+                          out.ctypes.data_as(_u32p))
+    return out
+
+
+def u01(x: int) -> float:
+    return lib().so_u01(int(x))
+
+
+# ----------------------------------------------------------------------------
+# Fitness
+# ----------------------------------------------------------------------------
+
+def seg_point_dist(a, b, c) -> float:
+    return lib().so_seg_point_dist(float(a[0]), float(a[1]), float(b[0]), float(b[1]),
+                                   float(c[0]), float(c[1]))
+
+
+def evaluate(cfg, scene: Scene, X: np.ndarray):
+    """Fitness F, collision count Q and length of each row of X (n x 2T)."""
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, 2 * cfg.T))
+    n = X.shape[0]
+    F = np.zeros(n, np.float64)
+    Q = np.zeros(n, np.int32)
+    L = np.zeros(n, np.float64)
+    c = _cfg(cfg)
+    s = scene.c()
+    lib().so_evaluate(ctypes.byref(c), ctypes.byref(s), n, _p64(X), _p64(F), _p32(Q), _p64(L))
+    return F, Q, L
+
+
+def tangency_margin(cfg, scene: Scene, X: np.ndarray) -> np.ndarray:
+    """Per particle, min over its (segment, circle) pairs of |dist - r|."""
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, 2 * cfg.T))
+    m = np.zeros(X.shape[0])
+    c = _cfg(cfg)
+    s = scene.c()
+    lib().so_tangency_margin(ctypes.byref(c), ctypes.byref(s), X.shape[0], _p64(X), _p64(m))
+    return m
+
+
+def pi_count(gamma: float, N: int) -> int:
+    return lib().so_pi_count(float(np.float32(gamma)), N)
+
+
+def window_std(values) -> float:
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
+    return lib().so_window_std(_p64(v), v.size, v.size, 0)
+
+
+# ----------------------------------------------------------------------------
+# Swarm state
+# ----------------------------------------------------------------------------
+
+STATE_FIELDS = ("X", "V", "P", "Pfit", "PQ", "Gb", "Gfit", "GQ", "Tb", "Tfit", "TQ", "k",
+                "cycle", "has_prev", "prevT", "win", "win_n", "win_head", "stall", "prev_lfv")
+
+
+class Swarm:
+    """Owns the FP64 swarm state of one planner (Table EXP_TOF tensors)."""
+
+    def __init__(self, cfg, hyper):
+        self.cfg = cfg
+        T, G, N = cfg.T, cfg.G, cfg.N
+        D, M = 2 * T, G * N
+        self.hyper = np.ascontiguousarray(np.asarray(hyper, dtype=np.float64).reshape(G, 6))
+        tw = max(cfg.tw, 1)
+        f = np.zeros
+        self.s = {
+            "X": f(M * D), "V": f(M * D), "P": f(M * D), "Pfit": np.full(M, np.inf),
+            "PQ": f(M, np.int32), "Gb": f(G * D), "Gfit": np.full(G, np.inf), "GQ": f(G, np.int32),
+            "Tb": f(D), "Tfit": np.full(1, np.inf), "TQ": f(1, np.int32), "k": f(1, np.int32),
+            "cycle": f(1, np.int32), "has_prev": f(1, np.int32), "prevT": f(D), "win": f(tw),
+            "win_n": f(1, np.int32), "win_head": f(1, np.int32), "stall": f(1, np.int32),
+            "prev_lfv": np.full(1, np.inf),
+        }
+        self._c = _cfg(cfg)
+
+    def _st(self) -> _State:
+        kw = {}
+        for name in STATE_FIELDS:
+            a = self.s[name]
+            kw[name] = _p32(a) if a.dtype == np.int32 else _p64(a)
+        return _State(**kw)
+
+    def set_hyper(self, hyper):
+        self.hyper[...] = np.asarray(hyper, dtype=np.float64).reshape(self.hyper.shape)
+
+    def load(self, state: dict):
+        """Copy arrays (any float/int dtype) into the state, by field name."""
+        for k, v in state.items():
+            if k in self.s:
+                self.s[k][...] = np.asarray(v).reshape(self.s[k].shape).astype(self.s[k].dtype)
+
+    def state(self) -> dict:
+        return {k: v.copy() for k, v in self.s.items()}
+
+    def init(self):
+        st = self._st()
+        lib().so_init_swarm(ctypes.byref(self._c), _p64(self.hyper), ctypes.byref(st))
+
+    def iteration(self, scene: Scene, check_stop: bool = False) -> bool:
+        st = self._st()
+        s = scene.c()
+        return bool(lib().so_iteration(ctypes.byref(self._c), ctypes.byref(s), _p64(self.hyper),
+                                       ctypes.byref(st), int(check_stop)))
+
+    def step(self, scene: Scene, iters: int):
+        st = self._st()
+        s = scene.c()
+        lib().so_step(ctypes.byref(self._c), ctypes.byref(s), _p64(self.hyper), ctypes.byref(st),
+                      int(iters))
+
+    def at_update(self) -> bool:
+        st = self._st()
+        return bool(lib().so_at_update(ctypes.byref(self._c), ctypes.byref(st)))
+
+    def plan(self, scene: Scene) -> dict:
+        D = 2 * self.cfg.T
+        res = np.zeros(D + 4)
+        st = self._st()
+        s = scene.c()
+        lib().so_plan(ctypes.byref(self._c), ctypes.byref(s), _p64(self.hyper), ctypes.byref(st),
+                      _p64(res))
+        return {"waypoints": res[:D].copy(), "cost": float(res[D]), "length": float(res[D + 1]),
+                "Q": int(res[D + 2]), "iters": int(res[D + 3])}
+
+
+# ----------------------------------------------------------------------------
+# Dynamic scene and HSEF
+# ----------------------------------------------------------------------------
+
+def advance_scene(W, H, circles, cvel, start, svel, target, tvel):
+    """One dynamic step, in place, on FP64 copies; returns the new arrays."""
+    c = np.ascontiguousarray(np.asarray(circles, np.float64).reshape(-1, 3)).copy()
+    v = np.ascontiguousarray(np.asarray(cvel, np.float64).reshape(-1, 2)).copy()
+    s = np.asarray(start, np.float64).reshape(2).copy()
+    sv = np.asarray(svel, np.float64).reshape(2).copy()
+    t = np.asarray(target, np.float64).reshape(2).copy()
+    tv = np.asarray(tvel, np.float64).reshape(2).copy()
+    lib().so_advance_scene(float(np.float32(W)), float(np.float32(H)), c.shape[0], _p64(c), _p64(v),
+                           _p64(s), _p64(sv), _p64(t), _p64(tv))
+    return c, v, s, sv, t, tv
+
+
+def hsef(lcfg, scene: Scene, HG: int, HN: int, E: int, hhyper, lo, hi, l_vlimit: float,
+         hseed: int):
+    """Evolution phase of SEPSO; returns (best H-position, best LFV, per-evolution best)."""
+    G = lcfg.G
+    if G > 64:
+        raise ValueError("oracle HSEF supports G <= 64")
+    hh = np.ascontiguousarray(np.asarray(hhyper, np.float64).reshape(HG, 6))
+    hc = _HsefCfg(HG=HG, HN=HN, E=E, hhyper=_p64(hh),
+                  lo=(ctypes.c_double * 3)(*[float(np.float32(x)) for x in lo]),
+                  hi=(ctypes.c_double * 3)(*[float(np.float32(x)) for x in hi]),
+                  l_vlimit=float(np.float32(l_vlimit)), hseed=hseed)
+    best = np.zeros(3 * G)
+    bf = np.zeros(1)
+    hist = np.zeros(E)
+    c = _cfg(lcfg)
+    s = scene.c()
+    lib().so_hsef(ctypes.byref(c), ctypes.byref(s), ctypes.byref(hc), _p64(best), _p64(bf),
+                  _p64(hist))
+    return best, float(bf[0]), hist
+

@@ -1,0 +1,219 @@
+"""Seeded synthetic inputs for the SEPSO planner: configs, scenes, hyper-parameters.
+
+This module holds no arithmetic of the method.  It only draws inputs with numpy
+(`default_rng(seed)`) and writes down the paper's parameter tables, so that the CUDA
+library and the CPU oracle can be fed identical FP32 arrays.
+
+Workload shapes (all synthetic; the paper's own simulator scenes are not published):
+
+* ``static_workload``  -- one static scene: 400x400 map, start (20,20), target
+  (380,380), T=8 waypoints, G=8 groups x N=32, O=16 circles with centres
+  U[60,340]^2 and radii U[10,30], penalty 1000 per intersection (alpha=1000,
+  beta=1), 100 iterations, per-group w~U[0.4,0.9], C1,C2~U[1,2.5], Vmax=20.
+* ``dynamic_workload`` -- the dynamic planning run: T=20, G=8 x N=170, 64 circles
+  (32 static, 32 moving at speed U[0.5,2] per cycle in a random direction,
+  bouncing off the walls), start/target drifting 1 unit per cycle vertically,
+  Priori Initialization (gamma=0.25) and Auto Truncation by stall counter (10
+  stalled iterations, cap 300), alpha=30, beta=4 (Table params_path).
+
+Paper tables reproduced as data (they are inputs of the method):
+Table hyper8 (DTPSO / H-SEPSO / DPPSO hyper-parameters) and Table hyper8path
+(evolved L-SEPSO hyper-parameters for path planning), rows
+(C1, C2, C3, w_init, w_end, V_limit).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+AT_OFF, AT_STD_WINDOW, AT_STALL = 0, 1, 2
+
+
+@dataclass
+class SepsoConfig:
+    """Planner configuration (mirrors ``sepso_config`` in include/sepso.h)."""
+    T: int = 8                 # waypoints; a particle has D = 2T coordinates (Eq. coordinate)
+    G: int = 8                 # groups
+    N: int = 32                # particles per group
+    max_obstacles: int = 16
+    map_w: float = 400.0
+    map_h: float = 400.0
+    alpha: float = 1000.0      # Eq. penalty: alpha * Q^beta
+    beta: int = 1
+    max_iters: int = 100       # iteration cap = T of Eq. TOF_omega
+    at_mode: int = AT_OFF
+    tw: int = 20               # truncation window (Table params_path)
+    delta: float = 10.0
+    stall_iters: int = 10
+    stall_tol: float = 0.0
+    use_pi: bool = False
+    pi_gamma: float = 0.25
+    pi_halfwidth: float = 20.0
+    seed: int = 0              # Philox key
+    run_id: int = 0            # Philox counter word 3
+    runs: int = 1              # independent swarms on the same scene
+    ctas_per_group: int = 0    # 0 = automatic
+    threads: int = 0           # 0 = automatic
+    circle_split: int = 0      # 0 = automatic
+
+    @property
+    def D(self) -> int:
+        return 2 * self.T
+
+    def with_(self, **kw) -> "SepsoConfig":
+        return replace(self, **kw)
+
+
+@dataclass
+class Scene:
+    """Start, target and circles (cx, cy, r), plus their per-cycle velocities."""
+    start: np.ndarray                      # (2,) float32
+    target: np.ndarray                     # (2,) float32
+    circles: np.ndarray                    # (O, 3) float32
+    circle_vel: np.ndarray = field(default=None)   # (O, 2) float32
+    start_vel: np.ndarray = field(default=None)    # (2,) float32
+    target_vel: np.ndarray = field(default=None)   # (2,) float32
+
+    def __post_init__(self):
+        self.start = np.asarray(self.start, np.float32).reshape(2)
+        self.target = np.asarray(self.target, np.float32).reshape(2)
+        self.circles = np.ascontiguousarray(np.asarray(self.circles, np.float32).reshape(-1, 3))
+        O = self.circles.shape[0]
+        if self.circle_vel is None:
+            self.circle_vel = np.zeros((O, 2), np.float32)
+        if self.start_vel is None:
+            self.start_vel = np.zeros(2, np.float32)
+        if self.target_vel is None:
+            self.target_vel = np.zeros(2, np.float32)
+        self.circle_vel = np.ascontiguousarray(np.asarray(self.circle_vel, np.float32).reshape(O, 2))
+        self.start_vel = np.asarray(self.start_vel, np.float32).reshape(2)
+        self.target_vel = np.asarray(self.target_vel, np.float32).reshape(2)
+
+    @property
+    def O(self) -> int:
+        return self.circles.shape[0]
+
+
+# Table hyper8: hyper-parameters for DTPSO, H-SEPSO and DPPSO (C1, C2, C3, w_init, w_end, V_limit).
+TABLE_HYPER8 = np.array([
+    [2, 1, 1, 0.4, 0.2, 0.2],
+    [1, 1, 2, 0.7, 0.3, 0.1],
+    [2, 2, 1, 0.8, 0.1, 0.6],
+    [2, 2, 1, 0.8, 0.6, 0.4],
+    [2, 1, 2, 0.2, 0.1, 0.3],
+    [2, 1, 2, 0.9, 0.5, 0.5],
+    [1, 2, 2, 0.4, 0.1, 0.8],
+    [1, 2, 2, 0.9, 0.3, 0.3],
+], dtype=np.float32)
+
+# Table hyper8path: evolved L-SEPSO hyper-parameters for path planning.
+TABLE_HYPER8_PATH = np.array([
+    [1.53, 1.29, 1.34, 0.48, 0.19, 0.35],
+    [1.72, 1.53, 1.34, 0.73, 0.28, 0.32],
+    [1.34, 1.42, 1.33, 0.48, 0.21, 0.62],
+    [1.76, 1.60, 1.21, 0.47, 0.30, 0.63],
+    [1.68, 1.27, 1.25, 0.73, 0.36, 0.41],
+    [1.66, 1.54, 1.54, 0.39, 0.16, 0.45],
+    [1.57, 1.48, 1.75, 0.56, 0.34, 0.38],
+    [1.31, 1.71, 1.23, 0.36, 0.25, 0.50],
+], dtype=np.float32)
+
+# Table params_path: alpha, beta, gamma, delta, TW.
+PARAMS_PATH = dict(alpha=30.0, beta=4, pi_gamma=0.25, delta=10.0, tw=20)
+
+# Search box of the outer (H) swarm over per-group (w, C1, C2).
+HSEF_BOX_LO = (0.4, 1.0, 1.0)
+HSEF_BOX_HI = (0.9, 2.5, 2.5)
+
+
+def sample_hyper(seed: int, G: int, w_range=(0.4, 0.9), c_range=(1.0, 2.5),
+                 v_limit: float = 0.05) -> np.ndarray:
+    """Per-group constant w ~ U[w_range], C1, C2 ~ U[c_range], C3 = 0 -> (G, 6) float32."""
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(*w_range, G)
+    c1 = rng.uniform(*c_range, G)
+    c2 = rng.uniform(*c_range, G)
+    h = np.zeros((G, 6), np.float32)
+    h[:, 0], h[:, 1], h[:, 2] = c1, c2, 0.0
+    h[:, 3], h[:, 4], h[:, 5] = w, w, v_limit
+    return h
+
+
+def random_circles(rng, O: int, lo=60.0, hi=340.0, r_lo=10.0, r_hi=30.0) -> np.ndarray:
+    c = np.zeros((O, 3), np.float32)
+    c[:, 0] = rng.uniform(lo, hi, O)
+    c[:, 1] = rng.uniform(lo, hi, O)
+    c[:, 2] = rng.uniform(r_lo, r_hi, O)
+    return c
+
+
+def static_workload(seed: int = 0, O: int = 16):
+    """The static single-scene workload: (config, scene, hyper)."""
+    cfg = SepsoConfig(T=8, G=8, N=32, max_obstacles=max(O, 1), alpha=1000.0, beta=1,
+                      max_iters=100, at_mode=AT_OFF, use_pi=False, seed=0)
+    rng = np.random.default_rng(1000 + seed)
+    scene = Scene(start=(20, 20), target=(380, 380), circles=random_circles(rng, O))
+    hyper = sample_hyper(2000 + seed, cfg.G)
+    return cfg, scene, hyper
+
+
+def dynamic_workload(seed: int = 0, n_static: int = 32, n_moving: int = 32, T: int = 20,
+                     N: int = 170):
+    """The dynamic planning workload: (config, scene with velocities, hyper)."""
+    O = n_static + n_moving
+    cfg = SepsoConfig(T=T, G=8, N=N, max_obstacles=O, alpha=PARAMS_PATH["alpha"],
+                      beta=PARAMS_PATH["beta"], max_iters=300, at_mode=AT_STALL,
+                      stall_iters=10, stall_tol=0.0, tw=PARAMS_PATH["tw"],
+                      delta=PARAMS_PATH["delta"], use_pi=True, pi_gamma=PARAMS_PATH["pi_gamma"],
+                      pi_halfwidth=20.0, seed=seed)
+    rng = np.random.default_rng(3000 + seed)
+    circles = random_circles(rng, O)
+    vel = np.zeros((O, 2), np.float32)
+    speed = rng.uniform(0.5, 2.0, n_moving)
+    ang = rng.uniform(0.0, 2.0 * np.pi, n_moving)
+    vel[n_static:, 0] = speed * np.cos(ang)
+    vel[n_static:, 1] = speed * np.sin(ang)
+    scene = Scene(start=(20, 20), target=(380, 380), circles=circles, circle_vel=vel,
+                  start_vel=(0.0, 1.0), target_vel=(0.0, -1.0))
+    hyper = sample_hyper(4000 + seed, cfg.G)
+    return cfg, scene, hyper
+
+
+def random_paths(seed: int, n: int, T: int, W: float = 400.0, H: float = 400.0) -> np.ndarray:
+    """n random particles (n, 2T) uniform over the map, FP32."""
+    rng = np.random.default_rng(seed)
+    X = np.empty((n, 2 * T), np.float32)
+    X[:, :T] = rng.uniform(0.0, W, (n, T))
+    X[:, T:] = rng.uniform(0.0, H, (n, T))
+    return X
+
+
+def random_state(seed: int, cfg: SepsoConfig) -> dict:
+    """A random mid-run swarm state (FP32/int32 arrays named as in the state layout).
+
+    Pbest/Gbest/Tbest rows are drawn over the map; their fitness values are drawn
+    as plain numbers (the update reads them only through comparisons)."""
+    rng = np.random.default_rng(seed)
+    T, G, N = cfg.T, cfg.G, cfg.N
+    D, M = 2 * T, G * N
+
+    def pos(n):
+        a = np.empty((n, D), np.float32)
+        a[:, :T] = rng.uniform(0, cfg.map_w, (n, T))
+        a[:, T:] = rng.uniform(0, cfg.map_h, (n, T))
+        return a.reshape(-1)
+
+    st = {
+        "X": pos(M), "P": pos(M),
+        "V": rng.uniform(-20, 20, M * D).astype(np.float32),
+        "Pfit": rng.uniform(500, 5000, M).astype(np.float32),
+        "PQ": rng.integers(0, 5, M).astype(np.int32),
+        "Gb": pos(G), "Gfit": rng.uniform(450, 600, G).astype(np.float32),
+        "GQ": rng.integers(0, 2, G).astype(np.int32),
+        "Tb": pos(1), "TQ": np.zeros(1, np.int32),
+        "k": np.array([int(rng.integers(1, 50))], np.int32),
+        "cycle": np.array([int(rng.integers(0, 5))], np.int32),
+    }
+    st["Tfit"] = np.array([st["Gfit"].min() - 1.0], np.float32)
+    return st

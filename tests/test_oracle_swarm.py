@@ -1,0 +1,227 @@
+"""Pins of the oracle's swarm iteration (Algorithm 1; Eqs. TOF_omega, TOF_V, TOF_X).
+
+The random factors R1, R2, R3 are not controllable, so the update is pinned by
+what the equations fix whatever their values are: special cases with closed
+forms, per-particle constancy of R across coordinates (Table EXP_TOF: R is
+(4, G, N), one scalar per particle), additivity of the four terms of Eq. TOF_V,
+the direction of each attractor, the own-group Gbest, and clipping.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_10169_gb300.inputs import SepsoConfig
+
+T, G, N = 2, 2, 3
+D, M = 2 * T, G * N
+
+
+def _cfg(**kw):
+    base = dict(T=T, G=G, N=N, map_w=400.0, map_h=400.0, alpha=30.0, beta=4, max_iters=100)
+    base.update(kw)
+    return SepsoConfig(**base)
+
+
+def _frozen_swarm(hyper, k=0, seed=5, **kw):
+    """A swarm whose P/G/T rows cannot change (all best fitness values -inf)."""
+    rng = np.random.default_rng(seed)
+    sw = oracle.Swarm(_cfg(**kw), hyper)
+    X = rng.uniform(150, 250, (M, D))
+    sw.load({
+        "X": X, "V": rng.uniform(-5, 5, (M, D)), "P": X + rng.uniform(-8, 8, (M, D)),
+        "Pfit": np.full(M, -np.inf), "Gb": rng.uniform(150, 250, (G, D)), "Gfit": np.full(G, -np.inf),
+        "Tb": rng.uniform(150, 250, D), "Tfit": [-np.inf], "k": [k],
+    })
+    return sw
+
+
+EMPTY = oracle.Scene((20, 20), (380, 380), np.zeros((0, 3)))
+
+
+def _hyper(c1=0.0, c2=0.0, c3=0.0, w_init=0.0, w_end=0.0, vlim=0.5):
+    return np.tile(np.array([c1, c2, c3, w_init, w_end, vlim]), (G, 1))
+
+
+def test_pure_inertia_w1_moves_by_velocity():
+    sw = _frozen_swarm(_hyper(w_init=1.0, w_end=1.0))
+    s0 = sw.state()
+    sw.step(EMPTY, 1)
+    s1 = sw.state()
+    np.testing.assert_allclose(s1["V"], s0["V"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(s1["X"], s0["X"] + s0["V"], rtol=0, atol=1e-12)
+    assert s1["k"][0] == 1
+
+
+@pytest.mark.parametrize("k0,expect_w", [(0, 0.895), (49, 0.65), (99, 0.4)])
+def test_omega_schedule(k0, expect_w):
+    # Eq. TOF_omega: w^k = w_init - (w_init - w_end) / T * k with T = 100;
+    # hand values: k=1 -> 0.9 - 0.005 = 0.895, k=50 -> 0.65, k=100 -> 0.4.
+    sw = _frozen_swarm(_hyper(w_init=0.9, w_end=0.4), k=k0)
+    s0 = sw.state()
+    sw.step(EMPTY, 1)
+    s1 = sw.state()
+    np.testing.assert_allclose(s1["V"], expect_w * s0["V"], rtol=1e-12, atol=1e-12)
+
+
+def _ratio_after(term):
+    """Run one step with a single unit attractor coefficient; return r = dV / (A - X)."""
+    kw = {"c1": 0.0, "c2": 0.0, "c3": 0.0}
+    kw[term] = 1.0
+    sw = _frozen_swarm(_hyper(**kw))
+    s0 = sw.state()
+    sw.step(EMPTY, 1)
+    s1 = sw.state()
+    X = s0["X"].reshape(G, N, D)
+    A = {"c1": s0["P"].reshape(G, N, D),
+         "c2": np.broadcast_to(s0["Gb"].reshape(G, 1, D), (G, N, D)),
+         "c3": np.broadcast_to(s0["Tb"].reshape(1, 1, D), (G, N, D))}[term]
+    return s1["V"].reshape(G, N, D) / (A - X), s0, s1
+
+
+@pytest.mark.parametrize("term", ["c1", "c2", "c3"])
+def test_each_attractor_uses_one_scalar_per_particle(term):
+    r, s0, s1 = _ratio_after(term)
+    # the same R for every coordinate of a particle (Table EXP_TOF: N distinct scalars)
+    assert np.all(np.ptp(r, axis=2) < 1e-9)
+    rp = r[:, :, 0]
+    assert np.all(rp >= 0.0) and np.all(rp < 1.0)
+    # distinct across particles
+    assert len(np.unique(np.round(rp, 12))) == M
+
+
+def test_three_random_factors_are_distinct_draws():
+    r1 = _ratio_after("c1")[0][:, :, 0]
+    r2 = _ratio_after("c2")[0][:, :, 0]
+    r3 = _ratio_after("c3")[0][:, :, 0]
+    assert not np.allclose(r1, r2) and not np.allclose(r2, r3) and not np.allclose(r1, r3)
+
+
+def test_velocity_is_sum_of_the_four_terms():
+    # Eq. TOF_V: V' = I x [H . R . (K - L)] = wV + C1 R1 (P-X) + C2 R2 (G-X) + C3 R3 (T-X).
+    parts = []
+    for kw in ({"w_init": 0.7, "w_end": 0.7}, {"c1": 1.3}, {"c2": 0.9}, {"c3": 1.7}):
+        sw = _frozen_swarm(_hyper(**kw))
+        sw.step(EMPTY, 1)
+        parts.append(sw.state()["V"])
+    sw = _frozen_swarm(_hyper(c1=1.3, c2=0.9, c3=1.7, w_init=0.7, w_end=0.7))
+    sw.step(EMPTY, 1)
+    np.testing.assert_allclose(sw.state()["V"], sum(parts), rtol=1e-12, atol=1e-10)
+
+
+def test_attractors_pull_towards_their_rows():
+    for term in ("c1", "c2", "c3"):
+        r, s0, s1 = _ratio_after(term)
+        assert np.all(r >= 0)  # moves towards P, own-group Gbest, Tbest respectively
+
+
+def test_gbest_term_uses_own_group_row():
+    # If group g used another group's Gbest row, the ratio dV/(Gb_g - X) would not be
+    # constant across coordinates (checked above); check both groups explicitly.
+    r, s0, s1 = _ratio_after("c2")
+    for g in range(G):
+        assert np.ptp(r[g]) >= 0 and np.all(np.ptp(r[g], axis=1) < 1e-9)
+
+
+def test_velocity_and_position_clipping():
+    # V_range = V_limit * X_range = 0.05 * 400 = 20; X_range = [0, 400].
+    sw = oracle.Swarm(_cfg(), _hyper(c1=2.0, vlim=0.05))
+    X = np.full((M, D), 200.0)
+    X[0, :] = 399.0
+    P = X.copy()
+    P[:, :] = 0.0
+    P[0, :] = 400.0 + 1e4  # far beyond the border
+    sw.load({"X": X, "V": np.zeros((M, D)), "P": P, "Pfit": np.full(M, -np.inf),
+             "Gfit": np.full(G, -np.inf), "Tfit": [-np.inf]})
+    sw.step(EMPTY, 1)
+    s = sw.state()
+    V = s["V"].reshape(M, D)
+    Xn = s["X"].reshape(M, D)
+    assert np.all(np.abs(V) <= 20.0 + 1e-12)
+    np.testing.assert_allclose(Xn[0], 400.0)          # 399 + 20 clipped to the border
+    moved = V[1:] != 0
+    np.testing.assert_allclose(np.abs(V[1:][moved & (np.abs(V[1:]) > 19.999)]), 20.0)
+
+
+def test_uniform_factors_over_many_particles():
+    # One-step ratios over 2000 particles are U[0,1): mean 1/2, variance 1/12.
+    big = SepsoConfig(T=1, G=1, N=2000, max_iters=100)
+    h = np.array([[1.0, 0, 0, 0, 0, 0.5]])
+    rng = np.random.default_rng(3)
+    sw = oracle.Swarm(big, h)
+    X = rng.uniform(150, 250, (2000, 2))
+    P = X + 1.0
+    sw.load({"X": X, "V": np.zeros((2000, 2)), "P": P, "Pfit": np.full(2000, -np.inf),
+             "Gfit": [-np.inf], "Tfit": [-np.inf]})
+    sw.step(EMPTY, 1)
+    r = sw.state()["V"].reshape(2000, 2)[:, 0]
+    assert abs(r.mean() - 0.5) < 4 * np.sqrt(1 / 12 / 2000)
+    assert abs(r.var() - 1 / 12) < 0.01
+
+
+# ---------------------------------------------------------------------------
+# Best updates (Algorithm 1, "update P, G, T when better fitness is identified")
+# ---------------------------------------------------------------------------
+
+def test_first_iteration_bests_are_brute_force_argmins():
+    cfg = _cfg(T=3, G=3, N=5, max_iters=10)
+    rng = np.random.default_rng(1)
+    circ = np.column_stack([rng.uniform(60, 340, (8, 2)), rng.uniform(10, 30, 8)])
+    sc = oracle.Scene((20, 20), (380, 380), circ)
+    h = np.tile([1.5, 1.5, 0.0, 0.7, 0.7, 0.05], (3, 1))
+    sw = oracle.Swarm(cfg, h)
+    sw.init()
+    X0 = sw.state()["X"].reshape(15, 6)
+    F, Q, _ = oracle.evaluate(cfg, sc, X0)
+    sw.step(sc, 1)
+    s = sw.state()
+    np.testing.assert_array_equal(s["Pfit"], F)
+    np.testing.assert_array_equal(s["P"].reshape(15, 6), X0)
+    for g in range(3):
+        n = int(np.argmin(F[g * 5:(g + 1) * 5]))
+        assert s["Gfit"][g] == F[g * 5 + n]
+        assert s["GQ"][g] == Q[g * 5 + n]
+        np.testing.assert_array_equal(s["Gb"].reshape(3, 6)[g], X0[g * 5 + n])
+    g = int(np.argmin(s["Gfit"]))
+    assert s["Tfit"][0] == s["Gfit"][g]
+    np.testing.assert_array_equal(s["Tb"], s["Gb"].reshape(3, 6)[g])
+
+
+def test_bests_invariants_over_iterations():
+    cfg = _cfg(T=4, G=4, N=8, max_iters=40)
+    rng = np.random.default_rng(2)
+    circ = np.column_stack([rng.uniform(60, 340, (12, 2)), rng.uniform(10, 30, 12)])
+    sc = oracle.Scene((20, 20), (380, 380), circ)
+    h = np.tile([1.5, 1.5, 0.5, 0.9, 0.4, 0.05], (4, 1))
+    sw = oracle.Swarm(cfg, h)
+    sw.init()
+    prev_T, prev_P = np.inf, np.full(32, np.inf)
+    for it in range(30):
+        X = sw.state()["X"].reshape(32, 8)
+        F, _, _ = oracle.evaluate(cfg, sc, X)
+        sw.step(sc, 1)
+        s = sw.state()
+        assert np.all(s["Pfit"] <= prev_P) and np.all(s["Pfit"] <= F)
+        assert s["Tfit"][0] <= prev_T
+        for g in range(4):
+            assert s["Gfit"][g] == s["Pfit"][g * 8:(g + 1) * 8].min()
+        assert s["Tfit"][0] == s["Gfit"].min()
+        Fb, Qb, _ = oracle.evaluate(cfg, sc, s["Tb"])
+        assert Fb[0] == s["Tfit"][0] and Qb[0] == s["TQ"][0]
+        prev_T, prev_P = s["Tfit"][0], s["Pfit"].copy()
+
+
+def test_tie_goes_to_lowest_index():
+    # Two mirror-image one-waypoint paths of exactly equal length: particle 0 at
+    # (5, 8) and particle 1 at (5, 2), start (0, 5), target (10, 5).  The group best
+    # must be particle 0's path (strict '<' scanning from the lowest index).
+    cfg = SepsoConfig(T=1, G=1, N=2, map_w=10.0, map_h=10.0, max_iters=10)
+    sc = oracle.Scene((0, 5), (10, 5), np.zeros((0, 3)))
+    for order in ([(5, 8), (5, 2)], [(5, 2), (5, 8)]):
+        sw = oracle.Swarm(cfg, np.array([[0, 0, 0, 0, 0, 0.1]]))
+        X = np.array([[order[0][0], order[0][1]], [order[1][0], order[1][1]]], dtype=np.float64)
+        sw.load({"X": X, "P": X, "V": np.zeros(4)})
+        sw.step(sc, 1)
+        s = sw.state()
+        assert s["Pfit"][0] == s["Pfit"][1]
+        np.testing.assert_array_equal(s["Gb"], X[0])
+        np.testing.assert_array_equal(s["Tb"], X[0])
