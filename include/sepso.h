@@ -1,0 +1,236 @@
+/*
+ * sepso.h -- C ABI of the GB300 (sm_103a) SEPSO planner library (libsepso.so).
+ *
+ * SEPSO: Self-Evolving Particle Swarm Optimization for real-time path planning
+ * (Xin, Li, Zhang, Li; arXiv 2308.10169).  The library runs the grouped,
+ * tensor-form PSO (DTPSO, Sec. 3.1, Algorithm 1) over a swarm X[G][N][D=2T] of
+ * waypoint paths, scores paths with Eqs. path_fit / lenth / penalty
+ * (Sec. 3.3.2) against circular obstacles, and wraps the loop with Priori
+ * Initialization (Sec. 3.3.3), Auto Truncation (Sec. 3.3.4) and the
+ * hierarchical self-evolving framework HSEF (Sec. 3.2.1, Eq. fit_h).
+ *
+ * Conventions for every call:
+ *   - Return value: SEPSO_OK (0) or a negative SEPSO_E* code; nothing aborts.
+ *     sepso_strerror() names the code; sepso_last_error() gives a message.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global
+ *     memory of the device that was current at sepso_create().  All input arrays
+ *     are read during the call (host) or before the enqueued work completes
+ *     (device); the caller keeps ownership of everything it passes.
+ *   - The caller owns the workspace (device memory of sepso_workspace_size()
+ *     bytes, 256-byte aligned) and the CUDA stream; all device work of a handle
+ *     is enqueued on that stream.  Calls marked "async" return once the work is
+ *     enqueued; calls marked "sync" wait for the stream.
+ *   - Layouts: a particle / path is D = 2T floats [x_1..x_T, y_1..y_T]
+ *     (Eq. coordinate); hyper-parameters are G rows of
+ *     (C1, C2, C3, w_init, w_end, V_limit) (Table hyper8 layout);
+ *     circles are O rows of (cx, cy, r).
+ *   - A handle is not thread-safe; distinct handles may be used concurrently.
+ */
+#ifndef SEPSO_H
+#define SEPSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define SEPSO_OK 0
+#define SEPSO_EINVAL (-1)   /* bad argument: size, NaN/Inf, O > max, ...        */
+#define SEPSO_ESTATE (-2)   /* call out of order (e.g. plan before a scene)      */
+#define SEPSO_ENOSPC (-3)   /* workspace too small or misaligned                 */
+#define SEPSO_ECUDA (-4)    /* a CUDA runtime call failed                        */
+#define SEPSO_ETIMEOUT (-5) /* a device-side wait gave up (bounded spin)         */
+#define SEPSO_ENOMEM (-6)   /* host allocation failed                            */
+#define SEPSO_ERANGE (-7)   /* shape exceeds a kernel limit (shared memory etc.) */
+
+/* Auto Truncation modes (Sec. 3.3.4). */
+#define SEPSO_AT_OFF 0          /* run to max_iters                                  */
+#define SEPSO_AT_STD_WINDOW 1   /* std of the LFV over the last TW iterations < delta,
+                                   and the best path collision-free                  */
+#define SEPSO_AT_STALL 2        /* LFV not improved (by more than stall_tol) for
+                                   stall_iters iterations, and the best path
+                                   collision-free                                    */
+
+typedef struct sepso_ctx* sepso_handle;
+
+/* Fixed at sepso_create().  Fields follow Algorithm 1 and Tables params_path /
+ * hyper8; "runs" swarms share one scene (used by HSEF, whose H-particles each
+ * own one L-run). */
+typedef struct {
+  int32_t T;              /* waypoints per path; D = 2T, 1 <= T <= 64            */
+  int32_t G;              /* groups, 1 <= G <= 32                                */
+  int32_t N;              /* particles per group, >= 1                           */
+  int32_t max_obstacles;  /* capacity for circles, >= 0                          */
+  float map_w, map_h;     /* X_range: x in [0, map_w], y in [0, map_h]           */
+  float alpha;            /* Eq. penalty: alpha * Q^beta                         */
+  int32_t beta;           /* integer exponent, 1..8                              */
+  int32_t max_iters;      /* cap; also T of Eq. TOF_omega                        */
+  int32_t at_mode;        /* SEPSO_AT_*                                          */
+  int32_t tw;             /* truncation window TW (mode 1), 1..64                */
+  float delta;            /* std threshold (mode 1)                              */
+  int32_t stall_iters;    /* mode 2 limit                                        */
+  float stall_tol;        /* mode 2: improvement must exceed this                */
+  int32_t use_pi;         /* Priori Initialization on/off                        */
+  float pi_gamma;         /* fraction of each group placed by PI, [0, 1]         */
+  float pi_halfwidth;     /* half-width of the PI interval around the last best  */
+  uint64_t seed;          /* Philox4x32-10 key                                   */
+  uint32_t run_id;        /* Philox counter word 3 of run 0 (run r: run_id + r)  */
+  int32_t runs;           /* independent swarms on the same scene, >= 1          */
+  int32_t ctas_per_group; /* 0 = automatic; else CTAs cooperating on one group   */
+  int32_t threads;        /* 0 = automatic; else 64..1024, a multiple of 32      */
+  int32_t circle_split;   /* 0 = automatic; else circle chunks per segment test  */
+} sepso_config;
+
+/* Outcome of one planning cycle of one run. */
+typedef struct {
+  float cost;     /* F(Tbest) = length + alpha * Q^beta                          */
+  float length;   /* Eq. lenth of Tbest                                          */
+  int32_t Q;      /* collision count of Tbest                                    */
+  int32_t iters;  /* iterations run (k at exit)                                  */
+  int32_t status; /* SEPSO_OK or the device-side error of the run                */
+} sepso_result;
+
+/* ---- lifetime ----------------------------------------------------------- */
+
+/* Bytes of device workspace a config needs.  Errors: EINVAL on a bad config. */
+int sepso_workspace_size(const sepso_config* cfg, size_t* bytes);
+
+/* Validate cfg, lay out the caller's workspace (d_workspace, bytes; device,
+ * 256-byte aligned, not freed before sepso_destroy) and pick launch shapes for
+ * the current device.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Zeroes the workspace (async on the stream).  Errors: EINVAL, ENOSPC,
+ * ERANGE (shape does not fit the kernel), ECUDA, ENOMEM. */
+int sepso_create(const sepso_config* cfg, void* d_workspace, size_t bytes, void* stream,
+                 sepso_handle* out);
+
+/* Release the host context.  Does not free the workspace or the stream. */
+void sepso_destroy(sepso_handle h);
+
+/* ---- inputs ------------------------------------------------------------- */
+
+/* Hyper-parameters (host, G x 6 floats, Table hyper8 layout) for run `run`,
+ * or for every run when run < 0.  Copied to the device (async).
+ * Errors: EINVAL (non-finite value, V_limit < 0, run out of range). */
+int sepso_set_hyper(sepso_handle h, int32_t run, const float* hyper);
+
+/* Scene (host): start[2], target[2], circles O x 3 (cx, cy, r), 0 <= O <=
+ * max_obstacles, r >= 0.  Copied to the device (async); circle velocities are
+ * reset to zero.  Errors: EINVAL. */
+int sepso_set_scene(sepso_handle h, const float* start, const float* target,
+                    const float* circles, int32_t O);
+
+/* Per-cycle velocities for the dynamic scene (host): circle_vel O x 2,
+ * start_vel[2], target_vel[2].  Errors: EINVAL, ESTATE (no scene yet). */
+int sepso_set_motion(sepso_handle h, const float* circle_vel, const float* start_vel,
+                     const float* target_vel);
+
+/* Advance the dynamic scene `steps` times on the device (async): every circle and
+ * the start/target move by their velocity; a velocity component flips when the
+ * disk crosses the border it moves towards (Fig. PP caption).
+ * Errors: ESTATE, EINVAL (steps < 0). */
+int sepso_advance_scene(sepso_handle h, int32_t steps);
+
+/* Read the current scene back (host outputs, sync): start[2], target[2],
+ * circles O x 3, circle_vel O x 2 (any output may be NULL). */
+int sepso_get_scene(sepso_handle h, float* start, float* target, float* circles,
+                    float* circle_vel);
+
+/* ---- the hot path ------------------------------------------------------- */
+
+/* One planning cycle of every run (async): initialise the swarm (uniform over
+ * X_range, V uniform in +-V_range; with PI and a previous path, the first
+ * ceil(pi_gamma * N) particles of each group uniform in prevT +- pi_halfwidth,
+ * clipped), then iterate Algorithm 1 until Auto Truncation or max_iters, then
+ * store the result and the warm-start state (previous best path, AT window,
+ * cycle counter).  One cooperative persistent kernel launch.
+ * Errors: ESTATE (no scene), ECUDA (launch). Device-side errors are reported by
+ * sepso_read_result / sepso_sync. */
+int sepso_plan_async(sepso_handle h);
+
+/* sepso_plan_async, then read run 0's result (sync).  waypoints: host, D floats
+ * (may be NULL); res: host (may be NULL). */
+int sepso_plan(sepso_handle h, float* waypoints, sepso_result* res);
+
+/* Copy the last result of run `run` to the host (sync). */
+int sepso_read_result(sepso_handle h, int32_t run, float* waypoints, sepso_result* res);
+
+/* Device address of run `run`'s result waypoints (D floats) and of its
+ * sepso_result record, valid while the handle lives (for device-side consumers). */
+int sepso_result_device(sepso_handle h, int32_t run, float** d_waypoints,
+                        sepso_result** d_result);
+
+/* Continue the current swarm of every run for `iters` full iterations of
+ * Algorithm 1 (no re-initialisation, no truncation check, no cap) (async). */
+int sepso_step(sepso_handle h, int32_t iters);
+
+/* Fitness of n paths on the current scene (async): d_X device n x D floats;
+ * outputs device (any may be NULL): d_F fitness, d_Q collision counts,
+ * d_len lengths.  Errors: ESTATE, EINVAL. */
+int sepso_evaluate(sepso_handle h, const float* d_X, int32_t n, float* d_F, int32_t* d_Q,
+                   float* d_len);
+
+/* ---- state (checkpoint / parity) ---------------------------------------- */
+
+/* Bytes of one run's serialised state.  Layout, in order (floats unless noted):
+ *   X[M*D] V[M*D] P[M*D] Pfit[M] PQ[M](int32) Gb[G*D] Gfit[G] GQ[G](int32)
+ *   Tb[D] Tfit[1] TQ[1](int32) k[1](int32) cycle[1](int32) has_prev[1](int32)
+ *   prevT[D] win[TW](double) win_n[1](int32) win_head[1](int32) stall[1](int32)
+ *   prev_lfv[1]
+ * with M = G*N; the double block starts 8-byte aligned (zero padding before it
+ * when needed). */
+int sepso_state_size(sepso_handle h, size_t* bytes);
+
+/* Copy run `run`'s state to/from host memory (sync). */
+int sepso_get_state(sepso_handle h, int32_t run, void* host_buf, size_t bytes);
+int sepso_set_state(sepso_handle h, int32_t run, const void* host_buf, size_t bytes);
+
+/* ---- HSEF (Sec. 3.2.1) -------------------------------------------------- */
+
+/* The evolution phase.  The handle's runs are the H-particles (runs = HG * HN);
+ * each H-particle is a per-group (w, C1, C2) vector; its fitness is the LFV
+ * (Eq. fit_h) of an L-run of max_iters iterations with C3 = 0,
+ * w_init = w_end = w and V_limit = l_vlimit, AT and PI off, all L-runs of one
+ * evolution on the same random streams (run id cfg.run_id, cycle = evolution-1).
+ * The H-swarm is DTPSO with hhyper (HG x 6, Table hyper8) and omega schedule
+ * over E evolutions, inside the box [lo, hi] of (w, C1, C2). */
+typedef struct {
+  int32_t HG, HN;     /* H-swarm groups and particles per group                */
+  int32_t E;          /* evolutions                                            */
+  float hhyper[32 * 6]; /* HG rows, Table hyper8 layout                        */
+  float lo[3], hi[3]; /* box of (w, C1, C2)                                    */
+  float l_vlimit;     /* V_limit of the L-runs                                 */
+  uint64_t hseed;     /* Philox key of the H-swarm                             */
+} sepso_hsef_config;
+
+/* Run E evolutions (async; 2 launches per evolution).  d_history: device, E
+ * floats (may be NULL), receives the best LFV after each evolution.
+ * Errors: EINVAL (runs != HG*HN, HG > 32, 3G > 96), ESTATE. */
+int sepso_hsef(sepso_handle h, const sepso_hsef_config* hc, float* d_history);
+
+/* Best H-position found so far as G hyper rows (C1, C2, 0, w, w, l_vlimit)
+ * and its LFV (host outputs, sync). */
+int sepso_hsef_best(sepso_handle h, float* hyper_out, float* best_lfv);
+
+/* ---- misc --------------------------------------------------------------- */
+
+/* Wait for the handle's stream; returns the first device-side error of any run
+ * (e.g. SEPSO_ETIMEOUT), else SEPSO_OK, and clears it. */
+int sepso_sync(sepso_handle h);
+
+/* Launch shape chosen at create: CTAs per group, threads, circle split, grid. */
+int sepso_launch_shape(sepso_handle h, int32_t* ctas_per_group, int32_t* threads,
+                       int32_t* circle_split, int32_t* grid);
+
+/* Number of kernel launches this handle has issued so far. */
+int64_t sepso_launch_count(sepso_handle h);
+
+const char* sepso_strerror(int code);
+const char* sepso_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEPSO_H */

@@ -1,0 +1,128 @@
+"""ctypes binding of ``libsepso.so`` (declared in include/sepso.h).
+
+Argument marshalling only.  There is no fallback: if the library is missing or
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from pathlib import Path
+
+from . import build as _build
+
+_lib = None
+
+SEPSO_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ESTATE", -3: "ENOSPC", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOMEM",
+          -7: "ERANGE"}
+
+
+class SepsoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("T", ctypes.c_int32), ("G", ctypes.c_int32), ("N", ctypes.c_int32),
+        ("max_obstacles", ctypes.c_int32),
+        ("map_w", ctypes.c_float), ("map_h", ctypes.c_float),
+        ("alpha", ctypes.c_float), ("beta", ctypes.c_int32),
+        ("max_iters", ctypes.c_int32),
+        ("at_mode", ctypes.c_int32), ("tw", ctypes.c_int32), ("delta", ctypes.c_float),
+        ("stall_iters", ctypes.c_int32), ("stall_tol", ctypes.c_float),
+        ("use_pi", ctypes.c_int32), ("pi_gamma", ctypes.c_float), ("pi_halfwidth", ctypes.c_float),
+        ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32),
+        ("runs", ctypes.c_int32), ("ctas_per_group", ctypes.c_int32), ("threads", ctypes.c_int32),
+        ("circle_split", ctypes.c_int32),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("cost", ctypes.c_float), ("length", ctypes.c_float), ("Q", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class HsefConfig(ctypes.Structure):
+    _fields_ = [("HG", ctypes.c_int32), ("HN", ctypes.c_int32), ("E", ctypes.c_int32),
+                ("hhyper", ctypes.c_float * (32 * 6)), ("lo", ctypes.c_float * 3),
+                ("hi", ctypes.c_float * 3), ("l_vlimit", ctypes.c_float),
+                ("hseed", ctypes.c_uint64)]
+
+
+def make_config(cfg) -> Config:
+    return Config(T=cfg.T, G=cfg.G, N=cfg.N, max_obstacles=cfg.max_obstacles, map_w=cfg.map_w,
+                  map_h=cfg.map_h, alpha=cfg.alpha, beta=cfg.beta, max_iters=cfg.max_iters,
+                  at_mode=cfg.at_mode, tw=cfg.tw, delta=cfg.delta, stall_iters=cfg.stall_iters,
+                  stall_tol=cfg.stall_tol, use_pi=int(cfg.use_pi), pi_gamma=cfg.pi_gamma,
+                  pi_halfwidth=cfg.pi_halfwidth, seed=cfg.seed, run_id=cfg.run_id, runs=cfg.runs,
+                  ctas_per_group=cfg.ctas_per_group, threads=cfg.threads,
+                  circle_split=cfg.circle_split)
+
+
+# Every exported entry point with (restype, argtypes); the tests check the list
+# against include/sepso.h.
+_vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+_fp = ctypes.POINTER(ctypes.c_float)
+SIGNATURES = {
+    "sepso_workspace_size": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(_sz)]),
+    "sepso_create": (ctypes.c_int, [ctypes.POINTER(Config), _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "sepso_destroy": (None, [_vp]),
+    "sepso_set_hyper": (ctypes.c_int, [_vp, _i32, _fp]),
+    "sepso_set_scene": (ctypes.c_int, [_vp, _fp, _fp, _fp, _i32]),
+    "sepso_set_motion": (ctypes.c_int, [_vp, _fp, _fp, _fp]),
+    "sepso_advance_scene": (ctypes.c_int, [_vp, _i32]),
+    "sepso_get_scene": (ctypes.c_int, [_vp, _fp, _fp, _fp, _fp]),
+    "sepso_plan_async": (ctypes.c_int, [_vp]),
+    "sepso_plan": (ctypes.c_int, [_vp, _fp, ctypes.POINTER(Result)]),
+    "sepso_read_result": (ctypes.c_int, [_vp, _i32, _fp, ctypes.POINTER(Result)]),
+    "sepso_result_device": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "sepso_step": (ctypes.c_int, [_vp, _i32]),
+    "sepso_evaluate": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp, _vp]),
+    "sepso_state_size": (ctypes.c_int, [_vp, ctypes.POINTER(_sz)]),
+    "sepso_get_state": (ctypes.c_int, [_vp, _i32, _vp, _sz]),
+    "sepso_set_state": (ctypes.c_int, [_vp, _i32, _vp, _sz]),
+    "sepso_hsef": (ctypes.c_int, [_vp, ctypes.POINTER(HsefConfig), _vp]),
+    "sepso_hsef_best": (ctypes.c_int, [_vp, _fp, _fp]),
+    "sepso_sync": (ctypes.c_int, [_vp]),
+    "sepso_launch_shape": (ctypes.c_int, [_vp] + [ctypes.POINTER(_i32)] * 4),
+    "sepso_launch_count": (_i64, [_vp]),
+    "sepso_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sepso_last_error": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> Path:
+    return _build.LIB
+
+
+def lib(rebuild_if_stale: bool = True):
+    """Load libsepso.so (building it first if its sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if rebuild_if_stale else _build.LIB
+        if not Path(path).exists():
+            raise RuntimeError(f"libsepso.so not found at {path}; run __graft_entry__.build()")
+        L = ctypes.CDLL(os.fspath(path))
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code: int):
+    if code != SEPSO_OK:
+        msg = lib().sepso_last_error()
+        raise SepsoError(code, msg.decode() if msg else "")
+    return code
+
+
+def fptr(a):
+    """float* from a numpy float32 array (None -> NULL)."""
+    if a is None:
+        return None
+    return a.ctypes.data_as(_fp)

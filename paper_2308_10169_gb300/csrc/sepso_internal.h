@@ -1,0 +1,56 @@
+// sepso_internal.h -- declarations shared by the kernels and the C-ABI host code.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sepso.h"
+
+namespace sepso {
+
+struct SwarmParams;
+struct RunCtl;
+
+// Shared-memory carve of swarm_kernel (byte offsets); identical on host and device.
+struct SmemLayout {
+  int circ, win, X, V, P, R, Gall, Tb, Pfit, PQ, Q, Imp, Len, Gfit, GQ, Gsrc, total;
+  __host__ __device__ static SmemLayout make(int Omax, int ppc, int D, int T, int G, int tw);
+};
+
+struct EvalParams {
+  int T, D, n, per_cta, split, O, Omax;
+  float alpha;
+  int beta;
+  const float* X;      // n x D (device)
+  const float4* circ;  // Omax x (cx, cy, r, r^2)
+  const float* pts;    // start xy, target xy
+  float* F;
+  int32_t* Q;
+  float* len;
+  int* status;
+};
+
+struct HsefParams {
+  int G, HG, HN, HM, E;
+  uint32_t key0, key1, run_id;
+  float lo[3], hi[3];
+  float l_vlimit;
+  const float* hhyper;        // device copy, HG x 6
+  float *HX, *HV, *HP, *HPfit, *HGb, *HGfit, *HTb, *HTfit;
+  float* hyper;               // runs x G x 6 (the L-runs' hyper-parameters)
+  RunCtl* ctl;                // runs
+  const sepso_result* res;    // runs (the L-runs' LFV)
+  float* history;             // E (device) or null
+};
+
+cudaError_t configure_swarm_kernel(size_t smem_bytes);
+cudaError_t swarm_occupancy(int threads, size_t smem_bytes, int* blocks_per_sm);
+cudaError_t launch_swarm(const SwarmParams& p, int grid, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_evaluate(const EvalParams& p, cudaStream_t s);
+cudaError_t launch_advance(float4* circ, float2* cvel, float* pts, int O, float W, float H, int steps,
+                           cudaStream_t s);
+cudaError_t launch_hsef_init(const HsefParams& p, cudaStream_t s);
+cudaError_t launch_hsef_update(const HsefParams& p, int e, cudaStream_t s);
+
+}  // namespace sepso

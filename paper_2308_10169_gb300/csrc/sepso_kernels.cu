@@ -1,0 +1,731 @@
+// sepso_kernels.cu -- CUDA kernels of the SEPSO planner for GB300 (sm_103a).
+//
+//   swarm_kernel     one cooperative persistent launch runs whole planning cycles
+//                    (or plain continuation steps) of R independent swarms:
+//                    Algorithm 1 of the paper (fitness, P/G/T update,
+//                    Eq. TOF_omega, Eq. TOF_V with clip, Eq. TOF_X with clip),
+//                    Priori Initialization (Sec. 3.3.3) and Auto Truncation
+//                    (Sec. 3.3.4), all on the device.
+//   evaluate_kernel  fitness (Eqs. path_fit / lenth / penalty) of a batch of paths.
+//   advance_kernel   the dynamic scene step (Fig. PP caption).
+//   hsef_*_kernel    the outer H-swarm of HSEF (Sec. 3.2.1, Eq. fit_h).
+//
+// Work split of swarm_kernel: run r owns C = G * cpg CTAs; CTA (g, q) owns
+// particles [q * ppc, q * ppc + ppc) of group g and keeps their X, V, P rows in
+// shared memory for the whole launch.  Each iteration every CTA publishes its
+// best Pbest (value, index, Q, row) into a parity-double-buffered slot, meets
+// the other CTAs of its run at a bounded global-memory barrier, and then every
+// CTA reduces the same slots in the same order, so all CTAs hold identical
+// Gbest / Tbest copies and take identical truncation decisions.
+#include <cfloat>
+#include <climits>
+#include <cstdint>
+
+#include "sepso_device.cuh"
+#include "sepso_internal.h"
+
+namespace sepso {
+
+__host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a * a; }
+
+__host__ __device__ SmemLayout SmemLayout::make(int Omax, int ppc, int D, int T, int G, int tw) {
+  SmemLayout s;
+  int off = 0;
+  s.circ = off;
+  off = align_up(off + (Omax > 0 ? Omax : 1) * 16, 16);
+  s.win = off;
+  off = align_up(off + tw * 8, 16);
+  s.X = off;
+  off = align_up(off + ppc * D * 4, 16);
+  s.V = off;
+  off = align_up(off + ppc * D * 4, 16);
+  s.P = off;
+  off = align_up(off + ppc * D * 4, 16);
+  s.R = off;
+  off = align_up(off + ppc * 16, 16);
+  s.Gall = off;
+  off = align_up(off + G * D * 4, 16);
+  s.Tb = off;
+  off = align_up(off + D * 4, 16);
+  s.Pfit = off;
+  off += ppc * 4;
+  s.PQ = off;
+  off += ppc * 4;
+  s.Q = off;
+  off += ppc * 4;
+  s.Imp = off;
+  off += ppc * 4;
+  s.Len = off;
+  off += ppc * (T + 1) * 4;
+  s.Gfit = off;
+  off += G * 4;
+  s.GQ = off;
+  off += G * 4;
+  s.Gsrc = off;
+  off += G * 4;
+  s.total = align_up(off, 16);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// The fused persistent iteration.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t s_mbar;
+  __shared__ int s_ok, s_stop, s_bidx, s_bq;
+  __shared__ float s_best;
+
+  const SmemLayout L = SmemLayout::make(p.Omax, p.ppc, p.D, p.T, p.G, p.tw);
+  float4* sC = reinterpret_cast<float4*>(smem + L.circ);
+  double* sWin = reinterpret_cast<double*>(smem + L.win);
+  float* sX = reinterpret_cast<float*>(smem + L.X);
+  float* sV = reinterpret_cast<float*>(smem + L.V);
+  float* sP = reinterpret_cast<float*>(smem + L.P);
+  float* sR = reinterpret_cast<float*>(smem + L.R);
+  float* sGall = reinterpret_cast<float*>(smem + L.Gall);
+  float* sT = reinterpret_cast<float*>(smem + L.Tb);
+  float* sPfit = reinterpret_cast<float*>(smem + L.Pfit);
+  int* sPQ = reinterpret_cast<int*>(smem + L.PQ);
+  int* sQ = reinterpret_cast<int*>(smem + L.Q);
+  int* sImp = reinterpret_cast<int*>(smem + L.Imp);
+  float* sLen = reinterpret_cast<float*>(smem + L.Len);
+  float* sGfit = reinterpret_cast<float*>(smem + L.Gfit);
+  int* sGQ = reinterpret_cast<int*>(smem + L.GQ);
+  int* sGsrc = reinterpret_cast<int*>(smem + L.Gsrc);
+
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  const int T = p.T, D = p.D, G = p.G, N = p.N;
+  const int b = blockIdx.x;
+  const int r = b / p.C;
+  const int cr = b - r * p.C;
+  const int g = cr / p.cpg;
+  const int q = cr - g * p.cpg;
+  const int n0 = q * p.ppc;
+  const int nl = max(0, min(p.ppc, N - n0));
+  RunCtl* ctl = p.ctl + r;
+
+  const float* hy = p.hyper + ((size_t)r * G + g) * 6;
+  const float c1 = hy[0], c2 = hy[1], c3 = hy[2], w_init = hy[3], w_end = hy[4], vlim = hy[5];
+  const float sx = p.pts[0], sy = p.pts[1], tx = p.pts[2], ty = p.pts[3];
+  const uint32_t cycle = (uint32_t)ctl->cycle;
+  const uint32_t run = ctl->run_id;
+
+  // Obstacles -> shared memory through the bulk-copy engine.
+  if (tid == 0) mbar_init(&s_mbar, 1);
+  __syncthreads();
+  if (tid == 0 && p.O > 0) {
+    mbar_expect_tx(&s_mbar, (uint32_t)p.O * 16u);
+    bulk_g2s(sC, p.circ, (uint32_t)p.O * 16u, &s_mbar);
+  }
+
+  float* gX = p.X + ((size_t)r * p.M + (size_t)g * N + n0) * D;
+  float* gV = p.V + ((size_t)r * p.M + (size_t)g * N + n0) * D;
+  float* gP = p.P + ((size_t)r * p.M + (size_t)g * N + n0) * D;
+  float* gPfit = p.Pfit + (size_t)r * p.M + (size_t)g * N + n0;
+  int32_t* gPQ = p.PQ + (size_t)r * p.M + (size_t)g * N + n0;
+
+  float Tfit;
+  int TQ, k;
+  // AT state, tracked by thread 0 only
+  int win_n = 0, win_head = 0, stall = 0;
+  float prev_lfv = INFINITY;
+
+  if (p.mode == kModePlan) {
+    // Initialisation (Algorithm 1) with Priori Initialization (Sec. 3.3.3).
+    const int n_pi = (p.use_pi && ctl->has_prev) ? p.n_pi : 0;
+    const float* prevT = p.prevT + (size_t)r * D;
+    const int nch = (D + 3) >> 2;
+    for (int it = tid; it < nl * nch; it += nt) {
+      const int i = it / nch, ch = it - i * nch;
+      const int n = n0 + i;
+      const uint32_t pid = (uint32_t)(g * N + n);
+      const bool pi = n < n_pi;
+      const uint4 ux = draw(p.key0, p.key1, (uint32_t)ch, pid, pi ? kStreamPI : kStreamInitX, cycle, run);
+      const uint4 uv = draw(p.key0, p.key1, (uint32_t)ch, pid, kStreamInitV, cycle, run);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int j = ch * 4 + l;
+        if (j < D) {
+          const float ext = (j < T) ? p.W : p.H;
+          float x;
+          if (pi) x = fminf(fmaxf(prevT[j] + (2.0f * lane_of(ux, l) - 1.0f) * p.pi_h, 0.0f), ext);
+          else x = lane_of(ux, l) * ext;
+          sX[i * D + j] = x;
+          sP[i * D + j] = x;
+          sV[i * D + j] = (2.0f * lane_of(uv, l) - 1.0f) * (vlim * ext);
+        }
+      }
+    }
+    for (int i = tid; i < nl; i += nt) {
+      sPfit[i] = INFINITY;
+      sPQ[i] = 0;
+      sQ[i] = 0;
+    }
+    for (int j = tid; j < G * D; j += nt) sGall[j] = 0.0f;
+    for (int j = tid; j < D; j += nt) sT[j] = 0.0f;
+    for (int j = tid; j < G; j += nt) {
+      sGfit[j] = INFINITY;
+      sGQ[j] = 0;
+    }
+    Tfit = INFINITY;
+    TQ = 0;
+    k = 0;
+    if (tid == 0 && p.at_mode == SEPSO_AT_STD_WINDOW) {
+      if (cycle != 0) {
+        win_n = ctl->win_n;
+        win_head = ctl->win_head;
+        for (int i = 0; i < p.tw; ++i) sWin[i] = p.win[(size_t)r * p.tw + i];
+      }
+    }
+  } else {
+    for (int it = tid; it < nl * D; it += nt) {
+      sX[it] = gX[it];
+      sV[it] = gV[it];
+      sP[it] = gP[it];
+    }
+    for (int i = tid; i < nl; i += nt) {
+      sPfit[i] = gPfit[i];
+      sPQ[i] = gPQ[i];
+      sQ[i] = 0;
+    }
+    for (int j = tid; j < G * D; j += nt) sGall[j] = p.Gb[(size_t)r * G * D + j];
+    for (int j = tid; j < D; j += nt) sT[j] = p.Tb[(size_t)r * D + j];
+    for (int j = tid; j < G; j += nt) {
+      sGfit[j] = p.Gfit[(size_t)r * G + j];
+      sGQ[j] = p.GQ[(size_t)r * G + j];
+    }
+    Tfit = ctl->Tfit;
+    TQ = ctl->TQ;
+    k = ctl->k;
+  }
+
+  bool failed = false;
+  if (p.O > 0) {
+    const bool landed = mbar_wait_bounded(&s_mbar, 0, kWaitLimitNs);
+    if (__syncthreads_or(landed ? 0 : 1)) {
+      failed = true;
+      if (tid == 0) ctl->status = SEPSO_ETIMEOUT;
+    }
+  } else {
+    __syncthreads();
+  }
+
+  const int nseg = T + 1;
+  int done = 0;
+  while (!failed) {
+    if (p.mode == kModeStep && done >= p.step_iters) break;
+    ++k;
+    ++done;
+
+    // Fitness = F(X^k): Q by shared atomics, segment lengths per item.
+    fitness_items(sX, nl, T, D, sx, sy, tx, ty, sC, p.O, p.split, sQ, sLen);
+    __syncthreads();
+
+    // Per particle: Eq. path_fit, the Pbest test, and this iteration's R1..R3.
+    for (int i = tid; i < nl; i += nt) {
+      float len = 0.0f;
+      for (int s = 0; s < nseg; ++s) len += sLen[i * nseg + s];
+      const int qq = sQ[i];
+      sQ[i] = 0;
+      const float F = len + p.alpha * powi((float)qq, p.beta);
+      const int imp = F < sPfit[i];
+      if (imp) {
+        sPfit[i] = F;
+        sPQ[i] = qq;
+      }
+      sImp[i] = imp;
+      const uint4 o = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)(g * N + n0 + i), kStreamVel, cycle, run);
+      sR[i * 4 + 0] = c1 * u01(o.x);
+      sR[i * 4 + 1] = c2 * u01(o.y);
+      sR[i * 4 + 2] = c3 * u01(o.z);
+    }
+    __syncthreads();
+
+    // Pbest rows; warp 0 finds the CTA's best Pbest (lowest index on ties).
+    for (int it = tid; it < nl * D; it += nt) {
+      if (sImp[it / D]) sP[it] = sX[it];
+    }
+    if (warp == 0) {
+      float bv = INFINITY;
+      int bi = INT_MAX, bq = 0;
+      for (int i = lane; i < nl; i += 32) {
+        const float v = sPfit[i];
+        if (v < bv) {
+          bv = v;
+          bi = n0 + i;
+          bq = sPQ[i];
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float v2 = __shfl_xor_sync(0xffffffffu, bv, off);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, off);
+        const int q2 = __shfl_xor_sync(0xffffffffu, bq, off);
+        if (v2 < bv || (v2 == bv && i2 < bi)) {
+          bv = v2;
+          bi = i2;
+          bq = q2;
+        }
+      }
+      if (lane == 0) {
+        s_best = bv;
+        s_bidx = bi;
+        s_bq = bq;
+      }
+    }
+    __syncthreads();
+
+    // Publish the candidate (parity slot k & 1), then meet the run's other CTAs.
+    const int par = k & 1;
+    const size_t base = ((size_t)r * 2 + par) * p.C;
+    if (tid == 0) {
+      CandMeta m;
+      m.fit = s_best;
+      m.idx = s_bidx;
+      m.q = s_bq;
+      m.pad = 0;
+      p.cmeta[base + cr] = m;
+    }
+    if (s_bidx != INT_MAX) {
+      const int wi = s_bidx - n0;
+      for (int j = tid; j < D; j += nt) p.crows[(base + cr) * D + j] = sP[wi * D + j];
+    }
+    if (!run_barrier(p.bar + r, (unsigned int)p.C, &s_ok)) {
+      if (tid == 0) ctl->status = SEPSO_ETIMEOUT;
+      failed = true;
+      break;
+    }
+
+    // Gbest of every group: argmin over its CTAs' candidates, same order everywhere.
+    for (int gg = warp; gg < G; gg += nwarps) {
+      float bv = INFINITY;
+      int bi = INT_MAX, bq = 0, bs = -1;
+      for (int qq = lane; qq < p.cpg; qq += 32) {
+        const int4 raw = __ldcg(reinterpret_cast<const int4*>(p.cmeta + base + gg * p.cpg + qq));
+        const float v = __int_as_float(raw.x);
+        if (v < bv || (v == bv && raw.y < bi)) {
+          bv = v;
+          bi = raw.y;
+          bq = raw.z;
+          bs = gg * p.cpg + qq;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float v2 = __shfl_xor_sync(0xffffffffu, bv, off);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, off);
+        const int q2 = __shfl_xor_sync(0xffffffffu, bq, off);
+        const int s2 = __shfl_xor_sync(0xffffffffu, bs, off);
+        if (v2 < bv || (v2 == bv && i2 < bi)) {
+          bv = v2;
+          bi = i2;
+          bq = q2;
+          bs = s2;
+        }
+      }
+      if (lane == 0) {
+        if (bv < sGfit[gg]) {
+          sGfit[gg] = bv;
+          sGQ[gg] = bq;
+          sGsrc[gg] = bs;
+        } else {
+          sGsrc[gg] = -1;
+        }
+      }
+    }
+    __syncthreads();
+
+    // Tbest (every thread, identical registers), then the rows that changed.
+    float tb = INFINITY;
+    int tg = -1;
+    for (int gg = 0; gg < G; ++gg) {
+      const float v = sGfit[gg];
+      if (v < tb) {
+        tb = v;
+        tg = gg;
+      }
+    }
+    int t_src = -2;  // -2 unchanged, -1 copy from the (unchanged) group row, >= 0 slot
+    if (tg >= 0 && tb < Tfit) {
+      Tfit = tb;
+      TQ = sGQ[tg];
+      t_src = sGsrc[tg];
+    }
+    for (int it = tid; it < G * D; it += nt) {
+      const int src = sGsrc[it / D];
+      if (src >= 0) sGall[it] = __ldcg(p.crows + (base + src) * D + (it % D));
+    }
+    if (t_src >= 0) {
+      for (int j = tid; j < D; j += nt) sT[j] = __ldcg(p.crows + (base + t_src) * D + j);
+    } else if (t_src == -1) {
+      for (int j = tid; j < D; j += nt) sT[j] = sGall[tg * D + j];
+    }
+
+    // Auto Truncation (Sec. 3.3.4) and the iteration cap.
+    if (tid == 0) {
+      int stop = 0;
+      if (p.mode == kModePlan) {
+        if (p.at_mode == SEPSO_AT_STD_WINDOW) {
+          sWin[win_head] = (double)Tfit;
+          win_head = (win_head + 1) % p.tw;
+          if (win_n < p.tw) ++win_n;
+          if (win_n >= 2) {
+            double sum = 0.0;
+            for (int i = 0; i < win_n; ++i) sum += sWin[(win_head - win_n + i + 2 * p.tw) % p.tw];
+            const double mean = sum / (double)win_n;
+            double ss = 0.0;
+            for (int i = 0; i < win_n; ++i) {
+              const double d = sWin[(win_head - win_n + i + 2 * p.tw) % p.tw] - mean;
+              ss += d * d;
+            }
+            if (sqrt(ss / (double)win_n) < (double)p.delta && TQ == 0) stop = 1;
+          }
+        } else if (p.at_mode == SEPSO_AT_STALL) {
+          if (Tfit < prev_lfv - p.stall_tol) stall = 0;
+          else ++stall;
+          prev_lfv = Tfit;
+          if (stall >= p.stall_iters && TQ == 0) stop = 1;
+        }
+        if (k >= p.max_iters) stop = 1;
+      }
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+
+    // Eq. TOF_omega, Eq. TOF_V (+ clip to V_range), Eq. TOF_X (+ clip to X_range).
+    const float w = w_init - (w_init - w_end) / (float)p.max_iters * (float)k;
+    const float* sGown = sGall + g * D;
+    for (int it = tid; it < nl * D; it += nt) {
+      const int i = it / D;
+      const int j = it - i * D;
+      const float x = sX[it];
+      float v = w * sV[it];
+      v = fmaf(sR[i * 4 + 0], sP[it] - x, v);
+      v = fmaf(sR[i * 4 + 1], sGown[j] - x, v);
+      v = fmaf(sR[i * 4 + 2], sT[j] - x, v);
+      const float ext = (j < T) ? p.W : p.H;
+      const float vmax = vlim * ext;
+      v = fminf(fmaxf(v, -vmax), vmax);
+      sV[it] = v;
+      sX[it] = fminf(fmaxf(x + v, 0.0f), ext);
+    }
+    __syncthreads();
+  }
+
+  // Write back the swarm (state for sepso_step / sepso_get_state).
+  for (int it = tid; it < nl * D; it += nt) {
+    gX[it] = sX[it];
+    gV[it] = sV[it];
+    gP[it] = sP[it];
+  }
+  for (int i = tid; i < nl; i += nt) {
+    gPfit[i] = sPfit[i];
+    gPQ[i] = sPQ[i];
+  }
+  if (q == 0) {
+    for (int j = tid; j < D; j += nt) p.Gb[((size_t)r * G + g) * D + j] = sGall[g * D + j];
+    if (tid == 0) {
+      p.Gfit[(size_t)r * G + g] = sGfit[g];
+      p.GQ[(size_t)r * G + g] = sGQ[g];
+    }
+  }
+  if (cr == 0) {
+    for (int j = tid; j < D; j += nt) p.Tb[(size_t)r * D + j] = sT[j];
+    if (p.mode == kModePlan) {
+      for (int j = tid; j < D; j += nt) {
+        p.res_wp[(size_t)r * D + j] = sT[j];
+        p.prevT[(size_t)r * D + j] = sT[j];
+      }
+    }
+    if (tid == 0) {
+      ctl->Tfit = Tfit;
+      ctl->TQ = TQ;
+      ctl->k = k;
+      if (p.mode == kModePlan) {
+        float len = 0.0f;
+        for (int s = 0; s < nseg; ++s) {
+          const float ax = (s == 0) ? sx : sT[s - 1];
+          const float ay = (s == 0) ? sy : sT[T + s - 1];
+          const float bx = (s == T) ? tx : sT[s];
+          const float by = (s == T) ? ty : sT[T + s];
+          const float dx = bx - ax, dy = by - ay;
+          len += sqrtf(fmaf(dx, dx, dy * dy));
+        }
+        sepso_result* res = p.res + r;
+        res->cost = Tfit;
+        res->length = len;
+        res->Q = TQ;
+        res->iters = k;
+        res->status = failed ? SEPSO_ETIMEOUT : ctl->status;
+        ctl->has_prev = 1;
+        ctl->cycle = (int32_t)cycle + 1;
+        ctl->stall = stall;
+        ctl->prev_lfv = prev_lfv;
+        if (p.at_mode == SEPSO_AT_STD_WINDOW) {
+          ctl->win_n = win_n;
+          ctl->win_head = win_head;
+          for (int i = 0; i < p.tw; ++i) p.win[(size_t)r * p.tw + i] = sWin[i];
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fitness of a batch of paths.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) evaluate_kernel(const EvalParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t s_mbar;
+  const int D = p.D, T = p.T, nseg = T + 1;
+  float4* sC = reinterpret_cast<float4*>(smem);
+  float* sX = reinterpret_cast<float*>(smem + align_up((p.Omax > 0 ? p.Omax : 1) * 16, 16));
+  int* sQ = reinterpret_cast<int*>(sX + p.per_cta * D);
+  float* sLen = reinterpret_cast<float*>(sQ + p.per_cta);
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * p.per_cta;
+  const int nl = max(0, min(p.per_cta, p.n - i0));
+
+  if (tid == 0) mbar_init(&s_mbar, 1);
+  __syncthreads();
+  if (tid == 0 && p.O > 0) {
+    mbar_expect_tx(&s_mbar, (uint32_t)p.O * 16u);
+    bulk_g2s(sC, p.circ, (uint32_t)p.O * 16u, &s_mbar);
+  }
+  for (int it = tid; it < nl * D; it += blockDim.x) sX[it] = p.X[(size_t)i0 * D + it];
+  for (int i = tid; i < nl; i += blockDim.x) sQ[i] = 0;
+  if (p.O > 0) {
+    const bool landed = mbar_wait_bounded(&s_mbar, 0, kWaitLimitNs);
+    if (__syncthreads_or(landed ? 0 : 1)) {
+      if (tid == 0) atomicExch(p.status, SEPSO_ETIMEOUT);
+      return;
+    }
+  } else {
+    __syncthreads();
+  }
+  fitness_items(sX, nl, T, D, p.pts[0], p.pts[1], p.pts[2], p.pts[3], sC, p.O, p.split, sQ, sLen);
+  __syncthreads();
+  for (int i = tid; i < nl; i += blockDim.x) {
+    float len = 0.0f;
+    for (int s = 0; s < nseg; ++s) len += sLen[i * nseg + s];
+    const int qq = sQ[i];
+    if (p.F) p.F[i0 + i] = len + p.alpha * powi((float)qq, p.beta);
+    if (p.Q) p.Q[i0 + i] = qq;
+    if (p.len) p.len[i0 + i] = len;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dynamic scene: c += v; a velocity component flips when the disk crosses the
+// border it is moving towards (Fig. PP caption).  Start/target: radius 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void move1(float& c, float& v, float r, float hi) {
+  c += v;
+  if (c - r < 0.0f && v < 0.0f) v = -v;
+  if (c + r > hi && v > 0.0f) v = -v;
+}
+
+__global__ void advance_kernel(float4* circ, float2* cvel, float* pts, int O, float W, float H, int steps) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < O; o += gridDim.x * blockDim.x) {
+    float4 c = circ[o];
+    float2 v = cvel[o];
+    for (int s = 0; s < steps; ++s) {
+      move1(c.x, v.x, c.z, W);
+      move1(c.y, v.y, c.z, H);
+    }
+    circ[o] = c;
+    cvel[o] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    float sx = pts[0], sy = pts[1], tx = pts[2], ty = pts[3];
+    float svx = pts[4], svy = pts[5], tvx = pts[6], tvy = pts[7];
+    for (int s = 0; s < steps; ++s) {
+      move1(sx, svx, 0.0f, W);
+      move1(sy, svy, 0.0f, H);
+      move1(tx, tvx, 0.0f, W);
+      move1(ty, tvy, 0.0f, H);
+    }
+    pts[0] = sx; pts[1] = sy; pts[2] = tx; pts[3] = ty;
+    pts[4] = svx; pts[5] = svy; pts[6] = tvx; pts[7] = tvy;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// HSEF outer swarm (single CTA; the L-runs are the runs of swarm_kernel).
+// ---------------------------------------------------------------------------
+__device__ void hsef_write_hyper(const HsefParams& p) {
+  const int G = p.G, DH = 3 * G;
+  for (int it = threadIdx.x; it < p.HM * G; it += blockDim.x) {
+    const int h = it / G, g = it - h * G;
+    const float* x = p.HX + (size_t)h * DH;
+    float* dst = p.hyper + ((size_t)h * G + g) * 6;
+    dst[0] = x[G + g];
+    dst[1] = x[2 * G + g];
+    dst[2] = 0.0f;
+    dst[3] = x[g];
+    dst[4] = x[g];
+    dst[5] = p.l_vlimit;
+  }
+}
+
+__global__ void hsef_init_kernel(const HsefParams p) {
+  const int G = p.G, DH = 3 * G;
+  for (int it = threadIdx.x; it < p.HM * DH; it += blockDim.x) {
+    const int h = it / DH, j = it - h * DH;
+    const int hg = h / p.HN;
+    const int kind = j / G;
+    const float lo = p.lo[kind], hi = p.hi[kind];
+    const uint4 ux = draw(p.key0, p.key1, (uint32_t)(j / 4), (uint32_t)h, kStreamHInitX, 0u, 0u);
+    const uint4 uv = draw(p.key0, p.key1, (uint32_t)(j / 4), (uint32_t)h, kStreamHInitV, 0u, 0u);
+    const float x = lo + lane_of(ux, j & 3) * (hi - lo);
+    const float vmax = p.hhyper[hg * 6 + 5] * (hi - lo);
+    p.HX[it] = x;
+    p.HV[it] = (2.0f * lane_of(uv, j & 3) - 1.0f) * vmax;
+    p.HP[it] = x;
+  }
+  for (int h = threadIdx.x; h < p.HM; h += blockDim.x) {
+    p.HPfit[h] = INFINITY;
+    p.ctl[h].cycle = 0;
+    p.ctl[h].has_prev = 0;
+    p.ctl[h].run_id = p.run_id;
+  }
+  for (int g = threadIdx.x; g < p.HG; g += blockDim.x) p.HGfit[g] = INFINITY;
+  for (int j = threadIdx.x; j < p.HG * DH; j += blockDim.x) p.HGb[j] = 0.0f;
+  for (int j = threadIdx.x; j < DH; j += blockDim.x) p.HTb[j] = 0.0f;
+  if (threadIdx.x == 0) *p.HTfit = INFINITY;
+  __syncthreads();
+  hsef_write_hyper(p);
+}
+
+// Evolution e (1-based): H-fitness = LFV of each L-run (Eq. fit_h), H bests,
+// then Eqs. TOF_omega / TOF_V / TOF_X on the H-swarm inside the (w, C1, C2) box.
+__global__ void hsef_update_kernel(const HsefParams p, int e) {
+  const int G = p.G, DH = 3 * G, HN = p.HN;
+  for (int h = threadIdx.x; h < p.HM; h += blockDim.x) {
+    const float f = p.res[h].cost;
+    if (f < p.HPfit[h]) {
+      p.HPfit[h] = f;
+      for (int j = 0; j < DH; ++j) p.HP[(size_t)h * DH + j] = p.HX[(size_t)h * DH + j];
+    }
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < p.HG; g += blockDim.x) {
+    float best = INFINITY;
+    int bi = -1;
+    for (int n = 0; n < HN; ++n) {
+      const float v = p.HPfit[g * HN + n];
+      if (v < best) {
+        best = v;
+        bi = n;
+      }
+    }
+    if (bi >= 0 && best < p.HGfit[g]) {
+      p.HGfit[g] = best;
+      for (int j = 0; j < DH; ++j) p.HGb[(size_t)g * DH + j] = p.HP[(size_t)(g * HN + bi) * DH + j];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float best = INFINITY;
+    int bg = -1;
+    for (int g = 0; g < p.HG; ++g) {
+      if (p.HGfit[g] < best) {
+        best = p.HGfit[g];
+        bg = g;
+      }
+    }
+    if (bg >= 0 && best < *p.HTfit) {
+      *p.HTfit = best;
+      for (int j = 0; j < DH; ++j) p.HTb[j] = p.HGb[(size_t)bg * DH + j];
+    }
+    if (p.history) p.history[e - 1] = *p.HTfit;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < p.HM * DH; it += blockDim.x) {
+    const int h = it / DH, j = it - h * DH;
+    const int hg = h / HN;
+    const float* hh = p.hhyper + hg * 6;
+    const int kind = j / G;
+    const float lo = p.lo[kind], hi = p.hi[kind];
+    const float w = hh[3] - (hh[3] - hh[4]) / (float)p.E * (float)e;
+    const uint4 o = draw(p.key0, p.key1, (uint32_t)e, (uint32_t)h, kStreamHVel, 0u, 0u);
+    const float x = p.HX[it];
+    float v = w * p.HV[it];
+    v = fmaf(hh[0] * u01(o.x), p.HP[it] - x, v);
+    v = fmaf(hh[1] * u01(o.y), p.HGb[(size_t)hg * DH + j] - x, v);
+    v = fmaf(hh[2] * u01(o.z), p.HTb[j] - x, v);
+    const float vmax = hh[5] * (hi - lo);
+    v = fminf(fmaxf(v, -vmax), vmax);
+    p.HV[it] = v;
+    p.HX[it] = fminf(fmaxf(x + v, lo), hi);
+  }
+  for (int h = threadIdx.x; h < p.HM; h += blockDim.x) {
+    p.ctl[h].cycle = e;
+    p.ctl[h].has_prev = 0;
+  }
+  __syncthreads();
+  hsef_write_hyper(p);
+}
+
+// ---------------------------------------------------------------------------
+// Launch wrappers (host).
+// ---------------------------------------------------------------------------
+// Allow up to `smem_bytes` of dynamic shared memory, less the kernel's static part.
+cudaError_t configure_swarm_kernel(size_t smem_bytes) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, swarm_kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(swarm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(smem_bytes - a.sharedSizeBytes));
+}
+
+cudaError_t swarm_occupancy(int threads, size_t smem_bytes, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, swarm_kernel, threads, smem_bytes);
+}
+
+cudaError_t launch_swarm(const SwarmParams& p, int grid, int threads, size_t smem, cudaStream_t s) {
+  void* args[] = {const_cast<SwarmParams*>(&p)};
+  return cudaLaunchCooperativeKernel((const void*)swarm_kernel, dim3(grid), dim3(threads), args, smem, s);
+}
+
+cudaError_t launch_evaluate(const EvalParams& p, cudaStream_t s) {
+  const size_t smem = (size_t)align_up((p.Omax > 0 ? p.Omax : 1) * 16, 16) +
+                      (size_t)p.per_cta * p.D * 4 + (size_t)p.per_cta * 4 +
+                      (size_t)p.per_cta * (p.T + 1) * 4;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes a;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, evaluate_kernel);
+  if (e == cudaSuccess && smem + a.sharedSizeBytes > (size_t)optin) return cudaErrorInvalidValue;
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(evaluate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)a.sharedSizeBytes);
+  if (e != cudaSuccess) return e;
+  const int grid = (p.n + p.per_cta - 1) / p.per_cta;
+  evaluate_kernel<<<grid, 256, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(float4* circ, float2* cvel, float* pts, int O, float W, float H, int steps,
+                           cudaStream_t s) {
+  const int threads = 128;
+  const int grid = O > 0 ? (O + threads - 1) / threads : 1;
+  advance_kernel<<<grid, threads, 0, s>>>(circ, cvel, pts, O, W, H, steps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hsef_init(const HsefParams& p, cudaStream_t s) {
+  hsef_init_kernel<<<1, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hsef_update(const HsefParams& p, int e, cudaStream_t s) {
+  hsef_update_kernel<<<1, 256, 0, s>>>(p, e);
+  return cudaGetLastError();
+}
+
+}  // namespace sepso

@@ -1,0 +1,207 @@
+"""Python face of libsepso: a Planner owns one handle, its workspace and stream.
+
+PyTorch provides the device memory (the workspace is a torch uint8 tensor) and the
+stream; every step of the planner runs in the library's CUDA kernels, reached
+through the C ABI of include/sepso.h.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import HsefConfig, Result, check, fptr
+from .inputs import Scene, SepsoConfig
+
+
+def _f32(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    return a.reshape(shape) if shape is not None else a
+
+
+def state_layout(cfg: SepsoConfig) -> dict:
+    """(offset, dtype, count) of every field of one run's serialised state."""
+    G, N, D, tw = cfg.G, cfg.N, 2 * cfg.T, cfg.tw
+    M = G * N
+    spec = [("X", np.float32, M * D), ("V", np.float32, M * D), ("P", np.float32, M * D),
+            ("Pfit", np.float32, M), ("PQ", np.int32, M), ("Gb", np.float32, G * D),
+            ("Gfit", np.float32, G), ("GQ", np.int32, G), ("Tb", np.float32, D),
+            ("Tfit", np.float32, 1), ("TQ", np.int32, 1), ("k", np.int32, 1),
+            ("cycle", np.int32, 1), ("has_prev", np.int32, 1), ("prevT", np.float32, D),
+            ("win", np.float64, tw), ("win_n", np.int32, 1), ("win_head", np.int32, 1),
+            ("stall", np.int32, 1), ("prev_lfv", np.float32, 1)]
+    out, off = {}, 0
+    for name, dt, n in spec:
+        if dt == np.float64:
+            off = (off + 7) & ~7
+        out[name] = (off, dt, n)
+        off += np.dtype(dt).itemsize * n
+    out["_total"] = off
+    return out
+
+
+class Planner:
+    """One SEPSO planner (``cfg.runs`` swarms sharing one scene) on one GPU."""
+
+    def __init__(self, cfg: SepsoConfig, device=None, stream: torch.cuda.Stream | None = None):
+        self.lib = _native.lib()
+        self.cfg = cfg
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        c = _native.make_config(cfg)
+        size = ctypes.c_size_t()
+        check(self.lib.sepso_workspace_size(ctypes.byref(c), ctypes.byref(size)))
+        self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.sepso_create(ctypes.byref(c), ctypes.c_void_p(self.workspace.data_ptr()),
+                                        size.value, ctypes.c_void_p(self.stream.cuda_stream),
+                                        ctypes.byref(self._h)))
+        self.D = 2 * cfg.T
+        self.O = 0
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if self._h:
+            self.lib.sepso_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- inputs -----------------------------------------------------------
+    def set_hyper(self, hyper, run: int = -1):
+        h = _f32(hyper, (self.cfg.G, 6))
+        check(self.lib.sepso_set_hyper(self._h, run, fptr(h)))
+
+    def set_scene(self, scene: Scene, motion: bool = True):
+        circ = _f32(scene.circles, (-1, 3))
+        check(self.lib.sepso_set_scene(self._h, fptr(_f32(scene.start)), fptr(_f32(scene.target)),
+                                       fptr(circ) if circ.size else None, circ.shape[0]))
+        self.O = circ.shape[0]
+        if motion:
+            cv = _f32(scene.circle_vel, (-1, 2))
+            check(self.lib.sepso_set_motion(self._h, fptr(cv) if cv.size else None,
+                                            fptr(_f32(scene.start_vel)), fptr(_f32(scene.target_vel))))
+
+    def advance(self, steps: int = 1):
+        check(self.lib.sepso_advance_scene(self._h, steps))
+
+    def get_scene(self) -> Scene:
+        s, t = np.zeros(2, np.float32), np.zeros(2, np.float32)
+        c = np.zeros((max(self.O, 1), 3), np.float32)
+        v = np.zeros((max(self.O, 1), 2), np.float32)
+        check(self.lib.sepso_get_scene(self._h, fptr(s), fptr(t), fptr(c), fptr(v)))
+        return Scene(start=s, target=t, circles=c[:self.O], circle_vel=v[:self.O])
+
+    # -- hot path ---------------------------------------------------------
+    def plan_async(self):
+        check(self.lib.sepso_plan_async(self._h))
+
+    def read_result(self, run: int = 0) -> dict:
+        wp = np.zeros(self.D, np.float32)
+        res = Result()
+        check(self.lib.sepso_read_result(self._h, run, fptr(wp), ctypes.byref(res)))
+        return {"waypoints": wp, "cost": res.cost, "length": res.length, "Q": res.Q,
+                "iters": res.iters, "status": res.status}
+
+    def plan(self) -> dict:
+        self.plan_async()
+        return self.read_result(0)
+
+    def plan_into(self, waypoints: np.ndarray) -> Result:
+        """One synchronous planning cycle writing into a caller-owned host array."""
+        res = Result()
+        check(self.lib.sepso_plan(self._h, fptr(waypoints), ctypes.byref(res)))
+        return res
+
+    def result_device(self, run: int = 0):
+        wp, rr = ctypes.c_void_p(), ctypes.c_void_p()
+        check(self.lib.sepso_result_device(self._h, run, ctypes.byref(wp), ctypes.byref(rr)))
+        return wp.value, rr.value
+
+    def step(self, iters: int = 1):
+        check(self.lib.sepso_step(self._h, iters))
+
+    def evaluate(self, X: torch.Tensor):
+        """F, Q, length of the rows of a CUDA float32 tensor (n, 2T)."""
+        assert X.is_cuda and X.dtype == torch.float32 and X.is_contiguous() and X.shape[-1] == self.D
+        n = X.numel() // self.D
+        F = torch.empty(n, dtype=torch.float32, device=X.device)
+        Q = torch.empty(n, dtype=torch.int32, device=X.device)
+        L = torch.empty(n, dtype=torch.float32, device=X.device)
+        check(self.lib.sepso_evaluate(self._h, ctypes.c_void_p(X.data_ptr()), n,
+                                      ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(Q.data_ptr()),
+                                      ctypes.c_void_p(L.data_ptr())))
+        return F, Q, L
+
+    def sync(self):
+        check(self.lib.sepso_sync(self._h))
+
+    # -- state ------------------------------------------------------------
+    def get_state(self, run: int = 0) -> dict:
+        lay = state_layout(self.cfg)
+        buf = np.zeros(lay["_total"], np.uint8)
+        check(self.lib.sepso_get_state(self._h, run, buf.ctypes.data_as(ctypes.c_void_p), buf.size))
+        out = {}
+        for name, spec in lay.items():
+            if name.startswith("_"):
+                continue
+            off, dt, n = spec
+            out[name] = np.frombuffer(buf, dtype=dt, count=n, offset=off).copy()
+        return out
+
+    def set_state(self, state: dict, run: int = 0):
+        """Write the given fields (others keep their current values)."""
+        lay = state_layout(self.cfg)
+        cur = self.get_state(run)
+        cur.update({k: v for k, v in state.items() if k in cur})
+        buf = np.zeros(lay["_total"], np.uint8)
+        for name, spec in lay.items():
+            if name.startswith("_"):
+                continue
+            off, dt, n = spec
+            a = np.ascontiguousarray(np.asarray(cur[name]).reshape(-1).astype(dt))
+            if a.size != n:
+                raise ValueError(f"state field {name}: {a.size} values, expected {n}")
+            buf[off:off + a.nbytes] = a.view(np.uint8)
+        check(self.lib.sepso_set_state(self._h, run, buf.ctypes.data_as(ctypes.c_void_p), buf.size))
+
+    # -- HSEF -------------------------------------------------------------
+    def hsef(self, HG: int, HN: int, E: int, hhyper, lo, hi, l_vlimit: float, hseed: int,
+             history: bool = True):
+        hc = HsefConfig(HG=HG, HN=HN, E=E, l_vlimit=l_vlimit, hseed=hseed)
+        hh = _f32(hhyper, (HG, 6)).reshape(-1)
+        for i, v in enumerate(hh):
+            hc.hhyper[i] = float(v)
+        for i in range(3):
+            hc.lo[i] = float(lo[i])
+            hc.hi[i] = float(hi[i])
+        hist = torch.zeros(E, dtype=torch.float32, device=self.device) if history else None
+        check(self.lib.sepso_hsef(self._h, ctypes.byref(hc),
+                                  ctypes.c_void_p(hist.data_ptr()) if hist is not None else None))
+        return hist
+
+    def hsef_best(self):
+        hy = np.zeros((self.cfg.G, 6), np.float32)
+        lfv = np.zeros(1, np.float32)
+        check(self.lib.sepso_hsef_best(self._h, fptr(hy), fptr(lfv)))
+        return hy, float(lfv[0])
+
+    # -- introspection ----------------------------------------------------
+    def launch_shape(self) -> dict:
+        v = [ctypes.c_int32() for _ in range(4)]
+        check(self.lib.sepso_launch_shape(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("ctas_per_group", "threads", "circle_split", "grid"), [x.value for x in v]))
+
+    def launch_count(self) -> int:
+        return int(self.lib.sepso_launch_count(self._h))

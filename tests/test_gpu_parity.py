@@ -1,0 +1,347 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (libsepso.so).
+
+Tolerances (FP32 kernel vs FP64 oracle):
+  * collision counts Q: bit-exact for paths whose every (segment, circle) pair is
+    more than 1e-3 away from tangency (|dist - r| > 1e-3);
+  * fitness: 1e-4 relative;  lengths: 1e-5 relative;
+  * positions after one step from identical state: 1e-5 relative, with an absolute
+    floor of 1e-5 x the map extent (the operands of Eq. TOF_X are of that size);
+    velocities: 1e-5 relative with a floor of 1e-5 x V_range;
+  * end to end: median final cost over 64 seeds within 1% of the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2308_10169_gb300 import Planner, Scene, SepsoConfig, sample_hyper, static_workload
+from paper_2308_10169_gb300.inputs import (AT_STALL, AT_STD_WINDOW, HSEF_BOX_HI, HSEF_BOX_LO,
+                                           TABLE_HYPER8, dynamic_workload, random_circles,
+                                           random_paths, random_state)
+
+pytestmark = pytest.mark.gpu
+
+TANGENCY = 1e-3
+
+
+def make(cfg, scene, hyper):
+    pl = Planner(cfg)
+    pl.set_hyper(hyper)
+    pl.set_scene(scene)
+    return pl
+
+
+def osc(scene):
+    return oracle.Scene(scene.start, scene.target, scene.circles)
+
+
+def close_pos(a, b, scale, rtol=1e-5):
+    np.testing.assert_allclose(np.asarray(a, np.float64), np.asarray(b, np.float64), rtol=rtol,
+                               atol=rtol * scale)
+
+
+# ---------------------------------------------------------------------------
+# Fitness (Eqs. path_fit, lenth, penalty)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("T,O,n", [(8, 16, 1000), (20, 64, 1360), (1, 5, 301), (3, 0, 50),
+                                   (64, 1024, 200), (33, 100, 97)])
+def test_fitness_matches_oracle(native, T, O, n):
+    rng = np.random.default_rng(T * 1000 + O)
+    cfg = SepsoConfig(T=T, G=1, N=1, max_obstacles=max(O, 1), alpha=30.0, beta=4)
+    scene = Scene(start=(20, 20), target=(380, 380), circles=random_circles(rng, O, r_lo=5, r_hi=30))
+    X = random_paths(T * 7 + O, n, T)
+    pl = make(cfg, scene, sample_hyper(0, 1))
+    F, Q, L = pl.evaluate(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    F, Q, L = F.cpu().numpy(), Q.cpu().numpy(), L.cpu().numpy()
+    Fo, Qo, Lo = oracle.evaluate(cfg, osc(scene), X)
+    margin = oracle.tangency_margin(cfg, osc(scene), X)
+    ok = margin > TANGENCY
+    assert ok.mean() > 0.5
+    np.testing.assert_array_equal(Q[ok], Qo[ok])
+    np.testing.assert_allclose(F[ok], Fo[ok], rtol=1e-4)
+    np.testing.assert_allclose(L, Lo, rtol=1e-5)
+
+
+# ---------------------------------------------------------------------------
+# Initialisation and Priori Initialization
+# ---------------------------------------------------------------------------
+
+def test_initial_swarm_matches_oracle(native):
+    cfg, scene, hyper = static_workload(3)
+    cfg = cfg.with_(max_iters=1, N=37)  # ragged over the CTAs of a group
+    pl = make(cfg, scene, hyper)
+    pl.plan()
+    s = pl.get_state()
+    sw = oracle.Swarm(cfg, hyper)
+    sw.init()
+    o = sw.state()
+    close_pos(s["X"], o["X"], 400.0)
+    close_pos(s["V"], o["V"], 20.0)
+
+
+def test_priori_initialization_matches_oracle(native):
+    cfg, scene, hyper = static_workload(4)
+    cfg = cfg.with_(max_iters=1, use_pi=True, pi_gamma=0.25, pi_halfwidth=20.0, N=40)
+    prevT = np.linspace(5, 395, cfg.D).astype(np.float32)
+    pl = make(cfg, scene, hyper)
+    pl.set_state({"has_prev": [1], "prevT": prevT, "cycle": [5]})
+    pl.plan()
+    s = pl.get_state()
+    sw = oracle.Swarm(cfg, hyper)
+    sw.load({"has_prev": [1], "prevT": prevT, "cycle": [5]})
+    sw.init()
+    o = sw.state()
+    close_pos(s["X"], o["X"], 400.0)
+    close_pos(s["V"], o["V"], 20.0)
+    X = s["X"].reshape(cfg.G, cfg.N, cfg.D)
+    assert np.all(np.abs(X[:, :10] - prevT) <= 20.0 + 1e-3)   # ceil(0.25 * 40) = 10
+
+
+# ---------------------------------------------------------------------------
+# One iteration of Algorithm 1 from identical state
+# ---------------------------------------------------------------------------
+
+def _decisive_state(cfg, scene, hyper, seed):
+    """A random state whose best-update decisions are far from ties in the oracle."""
+    o_sc = osc(scene)
+    for s in range(seed, seed + 200):
+        st = random_state(s, cfg)
+        X = st["X"].reshape(-1, cfg.D)
+        F, Q, _ = oracle.evaluate(cfg, o_sc, X)
+        if np.min(oracle.tangency_margin(cfg, o_sc, X)) <= TANGENCY:
+            continue
+        pf = st["Pfit"].astype(np.float64)
+        if np.min(np.abs(F - pf) / F) < 1e-3:
+            continue
+        newp = np.minimum(pf, F).reshape(cfg.G, cfg.N)
+        gmin = newp.min(1)
+        gf = st["Gfit"].astype(np.float64)
+        if np.min(np.abs(gmin - gf) / gf) < 1e-3:
+            continue
+        srt = np.sort(newp, axis=1)
+        if cfg.N > 1 and np.min((srt[:, 1] - srt[:, 0]) / srt[:, 0]) < 1e-4:
+            continue
+        ng = np.minimum(gf, gmin)
+        if np.min(np.abs(ng.min() - st["Tfit"][0]) / st["Tfit"][0]) < 1e-3:
+            continue
+        return st
+    raise AssertionError("no decisive state found")
+
+
+@pytest.mark.parametrize("G,N,T,O,cpg", [(3, 10, 4, 12, 0), (2, 13, 6, 20, 4), (8, 32, 8, 16, 0),
+                                         (1, 1, 1, 3, 0), (4, 50, 20, 64, 7)])
+def test_single_step_matches_oracle(native, G, N, T, O, cpg):
+    cfg = SepsoConfig(T=T, G=G, N=N, max_obstacles=O, alpha=30.0, beta=4, max_iters=100,
+                      ctas_per_group=cpg, seed=11)
+    rng = np.random.default_rng(G * 100 + N)
+    scene = Scene(start=(20, 20), target=(380, 380), circles=random_circles(rng, O))
+    hyper = np.column_stack([rng.uniform(1, 2.5, G), rng.uniform(1, 2.5, G), rng.uniform(0, 2, G),
+                             rng.uniform(0.6, 0.9, G), rng.uniform(0.2, 0.5, G),
+                             rng.uniform(0.02, 0.3, G)]).astype(np.float32)
+    st = _decisive_state(cfg, scene, hyper, seed=G * 7 + N)
+    pl = make(cfg, scene, hyper)
+    pl.set_state(st)
+    pl.step(1)
+    pl.sync()
+    s = pl.get_state()
+    sw = oracle.Swarm(cfg, hyper)
+    sw.load(st)
+    sw.step(osc(scene), 1)
+    o = sw.state()
+    assert s["k"][0] == o["k"][0] == st["k"][0] + 1
+    np.testing.assert_array_equal(s["PQ"], o["PQ"])
+    np.testing.assert_allclose(s["Pfit"], o["Pfit"], rtol=1e-4)
+    close_pos(s["P"], o["P"], 400.0)
+    np.testing.assert_allclose(s["Gfit"], o["Gfit"], rtol=1e-4)
+    np.testing.assert_array_equal(s["GQ"], o["GQ"])
+    close_pos(s["Gb"], o["Gb"], 400.0)
+    np.testing.assert_allclose(s["Tfit"], o["Tfit"], rtol=1e-4)
+    assert s["TQ"][0] == o["TQ"][0]
+    close_pos(s["Tb"], o["Tb"], 400.0)
+    vscale = float(np.max(hyper[:, 5])) * 400.0
+    close_pos(s["V"], o["V"], vscale)
+    close_pos(s["X"], o["X"], 400.0)
+
+
+# ---------------------------------------------------------------------------
+# Planning cycles
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("iters", [1, 2, 3])
+def test_first_iterations_of_a_plan_match(native, iters):
+    cfg, scene, hyper = static_workload(5)
+    cfg = cfg.with_(max_iters=iters)
+    res = make(cfg, scene, hyper).plan()
+    ref = oracle.Swarm(cfg, hyper).plan(osc(scene))
+    assert res["iters"] == ref["iters"] == iters
+    assert res["Q"] == ref["Q"]
+    assert res["cost"] == pytest.approx(ref["cost"], rel=1e-4)
+    close_pos(res["waypoints"], ref["waypoints"], 400.0)
+
+
+def test_median_cost_over_64_seeds_within_1pct(native):
+    gpu, ora = [], []
+    for s in range(64):
+        cfg, scene, hyper = static_workload(s)
+        cfg = cfg.with_(seed=s)
+        gpu.append(make(cfg, scene, hyper).plan()["cost"])
+        ora.append(oracle.Swarm(cfg, hyper).plan(osc(scene))["cost"])
+    mg, mo = np.median(gpu), np.median(ora)
+    assert abs(mg - mo) <= 0.01 * mo, (mg, mo)
+
+
+def test_dynamic_cycles_with_pi_and_truncation(native):
+    # Stall-counter AT (cap 300) and PI over several cycles of a moving scene; the
+    # trajectories of FP32 and FP64 runs diverge, so compare medians over seeds.
+    gpu, ora, gi, oi = [], [], [], []
+    for s in range(16):
+        cfg, scene, hyper = dynamic_workload(s, n_static=8, n_moving=8, T=8, N=24)
+        gp = make(cfg, scene, hyper)
+        sw = oracle.Swarm(cfg, hyper)
+        c, v, st, sv, tg, tv = (scene.circles, scene.circle_vel, scene.start, scene.start_vel,
+                                scene.target, scene.target_vel)
+        for cyc in range(3):
+            if cyc > 0:
+                gp.advance(1)
+                c, v, st, sv, tg, tv = oracle.advance_scene(cfg.map_w, cfg.map_h, c, v, st, sv, tg, tv)
+            r = gp.plan()
+            o = sw.plan(oracle.Scene(st, tg, c))
+            assert r["iters"] <= 300 and o["iters"] <= 300
+            gpu.append(r["cost"]); ora.append(o["cost"])
+            gi.append(r["iters"]); oi.append(o["iters"])
+        s_g = gp.get_state()
+        assert s_g["cycle"][0] == 3 and s_g["has_prev"][0] == 1
+    assert abs(np.median(gpu) - np.median(ora)) <= 0.02 * np.median(ora)
+    assert abs(np.median(gi) - np.median(oi)) <= 0.5 * np.median(oi) + 5
+
+
+def test_std_window_truncation_runs(native):
+    cfg, scene, hyper = static_workload(6)
+    cfg = cfg.with_(at_mode=AT_STD_WINDOW, tw=20, delta=10.0, max_iters=300)
+    pl = make(cfg, scene, hyper)
+    r = pl.plan()
+    o = oracle.Swarm(cfg, hyper).plan(osc(scene))
+    assert r["iters"] < 300 and o["iters"] < 300
+    s = pl.get_state()
+    assert s["win_n"][0] == min(r["iters"], 20)
+
+
+def test_scene_advance_matches_oracle(native):
+    cfg, scene, hyper = dynamic_workload(2)
+    pl = make(cfg, scene, hyper)
+    pl.advance(50)
+    g = pl.get_scene()
+    c, v, st, sv, tg, tv = scene.circles, scene.circle_vel, scene.start, scene.start_vel, scene.target, scene.target_vel
+    for _ in range(50):
+        c, v, st, sv, tg, tv = oracle.advance_scene(cfg.map_w, cfg.map_h, c, v, st, sv, tg, tv)
+    np.testing.assert_allclose(g.circles, c, atol=1e-3)
+    np.testing.assert_allclose(g.circle_vel, v, atol=0)
+    np.testing.assert_allclose(g.start, st, atol=1e-4)
+    np.testing.assert_allclose(g.target, tg, atol=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# Full-size launch configuration of the dynamic planning workload
+# ---------------------------------------------------------------------------
+
+def test_full_size_dynamic_workload_first_iterations(native):
+    cfg, scene, hyper = dynamic_workload(0)
+    cfg2 = cfg.with_(max_iters=2, at_mode=0)
+    pl = make(cfg2, scene, hyper)
+    shape = pl.launch_shape()
+    assert shape["grid"] >= cfg.G
+    r = pl.plan()
+    o = oracle.Swarm(cfg2, hyper).plan(osc(scene))
+    assert r["Q"] == o["Q"] and r["iters"] == o["iters"] == 2
+    assert r["cost"] == pytest.approx(o["cost"], rel=1e-4)
+    close_pos(r["waypoints"], o["waypoints"], 400.0)
+
+
+def test_full_size_dynamic_plan_properties(native):
+    # At the full configuration the planner converges to a collision-free path whose
+    # cost is the fitness of the returned waypoints (checked by the oracle).
+    cfg, scene, hyper = dynamic_workload(0)
+    pl = make(cfg, scene, hyper)
+    for cyc in range(5):
+        if cyc:
+            pl.advance(1)
+        r = pl.plan()
+        sc = pl.get_scene()
+        F, Q, L = oracle.evaluate(cfg, osc(sc), r["waypoints"])
+        assert r["Q"] == Q[0]
+        assert r["cost"] == pytest.approx(F[0], rel=1e-4)
+        assert r["length"] == pytest.approx(L[0], rel=1e-5)
+        assert 11 <= r["iters"] <= 300
+
+
+# ---------------------------------------------------------------------------
+# HSEF
+# ---------------------------------------------------------------------------
+
+def _hsef_setup(E):
+    lcfg = SepsoConfig(T=3, G=2, N=6, max_obstacles=6, max_iters=8, alpha=30.0, beta=4, runs=8)
+    rng = np.random.default_rng(9)
+    circ = np.column_stack([rng.uniform(60, 340, (6, 2)), rng.uniform(10, 30, 6)]).astype(np.float32)
+    scene = Scene(start=(20, 20), target=(380, 380), circles=circ)
+    pl = Planner(lcfg)
+    pl.set_scene(scene)
+    hist = pl.hsef(HG=4, HN=2, E=E, hhyper=TABLE_HYPER8[:4], lo=HSEF_BOX_LO, hi=HSEF_BOX_HI,
+                   l_vlimit=0.05, hseed=77)
+    best, lfv = pl.hsef_best()
+    ob, olfv, ohist = oracle.hsef(lcfg, osc(scene), HG=4, HN=2, E=E, hhyper=TABLE_HYPER8[:4],
+                                  lo=HSEF_BOX_LO, hi=HSEF_BOX_HI, l_vlimit=0.05, hseed=77)
+    return lcfg, hist.cpu().numpy(), best, lfv, ohist, olfv
+
+
+def test_hsef_first_evolution_matches_oracle(native):
+    lcfg, hist, best, lfv, ohist, olfv = _hsef_setup(1)
+    assert lfv == pytest.approx(olfv, rel=1e-3)
+    assert hist[0] == lfv
+
+
+def test_hsef_invariants(native):
+    lcfg, hist, best, lfv, ohist, olfv = _hsef_setup(6)
+    assert np.all(np.diff(hist) <= 0)
+    assert lfv == hist[-1]
+    w, c1, c2 = best[:, 3], best[:, 0], best[:, 1]
+    assert np.all((w >= 0.4 - 1e-6) & (w <= 0.9 + 1e-6))
+    assert np.all((c1 >= 1 - 1e-6) & (c1 <= 2.5 + 1e-6)) and np.all((c2 >= 1 - 1e-6) & (c2 <= 2.5 + 1e-6))
+    assert lfv <= olfv * 1.05
+
+
+# ---------------------------------------------------------------------------
+# Edge cases and argument checks
+# ---------------------------------------------------------------------------
+
+def test_obstacle_free_and_degenerate_sizes(native):
+    for (T, G, N) in [(1, 1, 1), (2, 1, 3), (64, 2, 5)]:
+        cfg = SepsoConfig(T=T, G=G, N=N, max_obstacles=4, max_iters=2, seed=3)
+        scene = Scene(start=(20, 20), target=(380, 380), circles=np.zeros((0, 3)))
+        hyper = sample_hyper(1, G)
+        r = make(cfg, scene, hyper).plan()
+        o = oracle.Swarm(cfg, hyper).plan(osc(scene))
+        assert r["Q"] == 0 == o["Q"]
+        assert r["cost"] == pytest.approx(o["cost"], rel=1e-4)
+        assert r["cost"] == pytest.approx(r["length"], rel=1e-6)
+
+
+def test_argument_errors(native):
+    from paper_2308_10169_gb300._native import SepsoError
+    cfg, scene, hyper = static_workload(0)
+    pl = Planner(cfg)
+    with pytest.raises(SepsoError, match="ESTATE"):
+        pl.plan()
+    big = Scene(start=(0, 0), target=(1, 1), circles=np.ones((cfg.max_obstacles + 1, 3)))
+    with pytest.raises(SepsoError, match="EINVAL"):
+        pl.set_scene(big)
+    with pytest.raises(SepsoError, match="EINVAL"):
+        pl.set_hyper(np.full((cfg.G, 6), np.nan))
+    bad = Scene(start=(0, 0), target=(1, 1), circles=[[1, 1, -2]])
+    with pytest.raises(SepsoError, match="EINVAL"):
+        pl.set_scene(bad)
+    pl.set_hyper(hyper)
+    pl.set_scene(scene)
+    assert pl.plan()["status"] == 0
+    pl.sync()
