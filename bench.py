@@ -1,0 +1,387 @@
+"""Benchmark of the SEPSO planner on one GB300 (or N independent replicas).
+
+Workload: the dynamic planning run -- 400x400 map, T=20 waypoints, G=8 groups x
+N=170 particles, 64 circles (32 static, 32 moving at U[0.5,2] per cycle, bouncing
+off the walls), start/target drifting 1 unit per cycle, Priori Initialization
+(gamma = 0.25) and Auto Truncation by stall counter (10 stalled iterations, cap
+300), alpha = 30, beta = 4.  First the HSEF evolution phase tunes the per-group
+(w, C1, C2) (32 H-particles, each an L-run of 300 iterations); then one step =
+one planning cycle (scene advance + plan) with the evolved hyper-parameters.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  ``value`` is plans/s with the scene resident on the device;
+``e2e`` is the same metric through the C ABI with host buffers (pinned scene in,
+waypoints out, every cycle).  ``--impl reference`` times the FP64 CPU oracle on
+the host cores instead (bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import numpy as np  # noqa: E402
+
+METRIC = "plans/sec and particle-evals/sec at oracle-matched cost; p50/p99 plan latency"
+UNIT = "plans/s"
+WORKLOAD = ("dynamic SEPSO run: 400x400 map, T=20 (D=40), G=8 x N=170, 64 circles r~U[10,30] "
+            "(32 static, 32 moving |v|~U[0.5,2]/cycle, wall bounce), start/target drift 1/cycle, "
+            "PI gamma=0.25 + AT stall 10 / cap 300, alpha=30 beta=4, HSEF-evolved (w,C1,C2)")
+
+# FP32 peak from the unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic work of one particle evaluation: (T+1) segments x (18 flops per
+# segment-circle test x O circles + 8 flops of length), per the scope table.
+FLOPS_PER_PAIR, FLOPS_PER_SEGMENT = 18, 8
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--hsef-evolutions", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="0 = same as --steps")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# Oracle (CPU) arm
+# ----------------------------------------------------------------------------
+
+def oracle_cycles(seconds: float, max_cycles: int, seed: int = 0):
+    """Run the FP64 oracle on the same dynamic workload for a bounded time."""
+    import oracle
+    from paper_2308_10169_gb300.inputs import dynamic_workload
+    cfg, scene, hyper = dynamic_workload(seed)
+    sw = oracle.Swarm(cfg, hyper)
+    c, v, st, sv, tg, tv = (scene.circles, scene.circle_vel, scene.start, scene.start_vel,
+                            scene.target, scene.target_vel)
+    times, iters, costs = [], [], []
+    t_all = time.perf_counter()
+    for cyc in range(max_cycles):
+        t0 = time.perf_counter()
+        if cyc:
+            c, v, st, sv, tg, tv = oracle.advance_scene(cfg.map_w, cfg.map_h, c, v, st, sv, tg, tv)
+        r = sw.plan(oracle.Scene(st, tg, c))
+        times.append(time.perf_counter() - t0)
+        iters.append(r["iters"])
+        costs.append(r["cost"])
+        if time.perf_counter() - t_all > seconds:
+            break
+    return cfg, times, iters, costs
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    budget = max(10.0, min(150.0, 3.0 * (args.steps + args.warmup)))
+    warm = min(args.warmup, 1)
+    cfg, times, iters, costs = oracle_cycles(budget, warm + args.steps)
+    times, iters, costs = times[warm:], iters[warm:], costs[warm:]
+    n = len(times)
+    total = sum(times)
+    value = n / total
+    pe = sum(iters) * cfg.G * cfg.N / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": n, "warmup": warm, "ms_per_step": 1e3 * total / n, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (oracle: hyper-parameters as sampled, no HSEF)",
+                   "cycles_timed": n},
+        "particle_evals_per_s": pe, "iters_per_plan": float(np.mean(iters)),
+        "median_cost": float(np.median(costs)),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"cycles {warm}..{warm + n - 1} of the dynamic run, one thread, "
+                                   f"{total:.1f} s"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2308_10169_gb300 import Planner
+    from paper_2308_10169_gb300.inputs import (HSEF_BOX_HI, HSEF_BOX_LO, TABLE_HYPER8,
+                                               dynamic_workload)
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    K, W = args.steps, args.warmup
+    if W < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cfg, scene, hyper0 = dynamic_workload(seed=rank)
+
+    # -- evolution phase (HSEF): 8 H-groups x 4 H-particles, Table hyper8 --------
+    HG, HN = 8, 4
+    hcfg = cfg.with_(runs=HG * HN, at_mode=0, use_pi=False)
+    hp = Planner(hcfg, device=dev)
+    hp.set_scene(scene, motion=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hist = hp.hsef(HG=HG, HN=HN, E=args.hsef_evolutions, hhyper=TABLE_HYPER8, lo=HSEF_BOX_LO,
+                   hi=HSEF_BOX_HI, l_vlimit=0.05, hseed=1000 + rank)
+    e1.record(stream)
+    hp.sync()
+    hsef_ms = e0.elapsed_time(e1)
+    best_hyper, best_lfv = hp.hsef_best()
+    hsef_info = {"evolutions": args.hsef_evolutions, "h_particles": HG * HN,
+                 "l_run_iters": cfg.max_iters, "ms": hsef_ms,
+                 "evolutions_per_s": 1e3 * args.hsef_evolutions / hsef_ms,
+                 "lfv_first": float(hist[0].item()), "lfv_best": best_lfv,
+                 "launches": hp.launch_count()}
+    del hp
+
+    # -- application phase ----------------------------------------------------
+    pl = Planner(cfg, device=dev)
+    pl.set_hyper(best_hyper)
+    pl.set_scene(scene)
+    shape = pl.launch_shape()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for i in range(W):
+        if i:
+            pl.advance(1)
+        pl.plan_async()
+    pl.sync()
+    plans0, iters0 = pl.counters()
+    launches0 = pl.launch_count()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    costs = []
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for i in range(K):
+            flush.zero_()                      # L2 flush, outside the timed events
+            a, b, c = ev[i]
+            a.record(stream)
+            pl.advance(1)
+            b.record(stream)
+            pl.plan_async()
+            c.record(stream)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall0
+    barrier()
+    launches = pl.launch_count() - launches0
+    pl.sync()
+    plans1, iters1 = pl.counters()
+    step_ms = np.array([a.elapsed_time(c) for a, b, c in ev])
+    plan_ms = np.array([b.elapsed_time(c) for a, b, c in ev])
+    total_ms = float(step_ms.sum())
+    last = pl.read_result()
+    iters = iters1 - iters0
+    assert plans1 - plans0 == K
+
+    # max over ranks
+    t_local = torch.tensor([total_ms], dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    total_max = float(t_local.item())
+    value = world * K / (total_max / 1e3)
+    pe_local = iters * cfg.G * cfg.N
+    flops = iters * cfg.G * cfg.N * (cfg.T + 1) * (FLOPS_PER_PAIR * scene.O + FLOPS_PER_SEGMENT)
+    achieved = flops / (plan_ms.sum() / 1e3) / 1e12
+
+    # -- end to end through the C ABI with host buffers ----------------------------
+    Ke = args.e2e_steps or K
+    e2e = run_e2e(torch, pl, cfg, scene, best_hyper, dev, Ke, W)
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": total_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded scenes shaped like the paper's dynamic environment)",
+            "config": {"workload": WORKLOAD, "cycles": K, "replicas": world,
+                       "l2": "flushed before every step (256 MiB write outside the timed events)",
+                       "launch": shape},
+            "particle_evals_per_s": world * pe_local / (total_max / 1e3),
+            "iters_per_plan": iters / K,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99)),
+                           "max": float(step_ms.max())},
+            "median_cost_last": float(last["cost"]),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "swarm_kernel",
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "hsef": hsef_info,
+            "wall_s_timed_loop": t_wall,
+        }
+    return line
+
+
+def run_e2e(torch, pl_dev, cfg, scene, hyper, dev, K, W):
+    """plans/s through set_scene (pinned host scene) + sepso_plan (host waypoints)."""
+    from paper_2308_10169_gb300 import Planner
+    from paper_2308_10169_gb300.inputs import Scene
+    # the scene sequence the host simulator feeds in (produced before timing)
+    sim = Planner(cfg, device=dev)
+    sim.set_hyper(hyper)
+    sim.set_scene(scene)
+    O = scene.O
+    pin_c = torch.empty((W + K, O, 3), dtype=torch.float32).pin_memory()
+    pin_p = torch.empty((W + K, 4), dtype=torch.float32).pin_memory()
+    for i in range(W + K):
+        if i:
+            sim.advance(1)
+        sc = sim.get_scene()
+        pin_c[i] = torch.from_numpy(sc.circles)
+        pin_p[i, :2] = torch.from_numpy(sc.start)
+        pin_p[i, 2:] = torch.from_numpy(sc.target)
+    del sim
+    pl = Planner(cfg, device=dev)
+    pl.set_hyper(hyper)
+    cn, pn = pin_c.numpy(), pin_p.numpy()
+    wp = torch.empty(cfg.D, dtype=torch.float32).pin_memory().numpy()
+    lat = []
+
+    def one(i):
+        pl.set_scene(Scene(start=pn[i, :2], target=pn[i, 2:], circles=cn[i]), motion=False)
+        pl.plan_into(wp)
+
+    for i in range(W):
+        one(i)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(W, W + K):
+        t = time.perf_counter()
+        one(i)
+        lat.append(time.perf_counter() - t)
+    total = time.perf_counter() - t0
+    lat = np.array(lat) * 1e3
+    return {"value": K / total, "unit": UNIT, "h2d_bytes_per_step": O * 16 + 8 * 4,
+            "d2h_bytes_per_step": cfg.D * 4 + 20,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "path": "sepso_set_scene (pinned staging, async DMA) + sepso_plan (D2H waypoints, sync)"}
+
+
+def cpu_baseline(seconds: float):
+    cfg, times, iters, costs = oracle_cycles(seconds, 10_000)
+    n, total = len(times), sum(times)
+    return {"value": n / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} planning cycles of the same dynamic run (hyper-parameters as "
+                      f"sampled, no HSEF), FP64, one thread, {total:.1f} s",
+            "particle_evals_per_s": sum(iters) * cfg.G * cfg.N / total,
+            "iters_per_plan": float(np.mean(iters)), "median_cost": float(np.median(costs))}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    line = run_ours(args, rank, world, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

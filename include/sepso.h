@@ -117,8 +117,10 @@ void sepso_destroy(sepso_handle h);
 int sepso_set_hyper(sepso_handle h, int32_t run, const float* hyper);
 
 /* Scene (host): start[2], target[2], circles O x 3 (cx, cy, r), 0 <= O <=
- * max_obstacles, r >= 0.  Copied to the device (async); circle velocities are
- * reset to zero.  Errors: EINVAL. */
+ * max_obstacles, r >= 0.  Packed into the handle's pinned staging buffer and
+ * copied to the device (async DMA; the call first waits for the previous
+ * scene copy to leave the staging buffer); circle velocities are reset to
+ * zero.  Errors: EINVAL. */
 int sepso_set_scene(sepso_handle h, const float* start, const float* target,
                     const float* circles, int32_t O);
 
@@ -223,6 +225,10 @@ int sepso_sync(sepso_handle h);
 /* Launch shape chosen at create: CTAs per group, threads, circle split, grid. */
 int sepso_launch_shape(sepso_handle h, int32_t* ctas_per_group, int32_t* threads,
                        int32_t* circle_split, int32_t* grid);
+
+/* Cumulative counters of run `run` (host outputs, sync): planning cycles
+ * finished and iterations of Algorithm 1 executed (plans and steps). */
+int sepso_counters(sepso_handle h, int32_t run, int64_t* plans, int64_t* iterations);
 
 /* Number of kernel launches this handle has issued so far. */
 int64_t sepso_launch_count(sepso_handle h);

@@ -88,6 +88,7 @@ SIGNATURES = {
     "sepso_hsef_best": (ctypes.c_int, [_vp, _fp, _fp]),
     "sepso_sync": (ctypes.c_int, [_vp]),
     "sepso_launch_shape": (ctypes.c_int, [_vp] + [ctypes.POINTER(_i32)] * 4),
+    "sepso_counters": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "sepso_launch_count": (_i64, [_vp]),
     "sepso_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sepso_last_error": (ctypes.c_char_p, []),

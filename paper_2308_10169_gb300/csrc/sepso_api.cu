@@ -144,6 +144,13 @@ struct sepso_ctx {
   bool hsef_ready = false;
   int hsef_G = 0;
   float hsef_vlimit = 0.0f;
+  float4* staging = nullptr;          // pinned: packed circles then the 8 point floats
+  cudaEvent_t staging_free = nullptr; // recorded after each scene copy
+
+  ~sepso_ctx() {
+    if (staging_free) cudaEventDestroy(staging_free);
+    if (staging) cudaFreeHost(staging);
+  }
 
   template <class T>
   T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
@@ -363,6 +370,13 @@ int sepso_create(const sepso_config* cfg, void* d_workspace, size_t bytes, void*
     delete h;
     return rc;
   }
+  e = cudaMallocHost(reinterpret_cast<void**>(&h->staging),
+                     ((size_t)std::max(cfg->max_obstacles, 1) + 2) * sizeof(float4));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->staging_free, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "pinned staging buffer");
+  }
   // Zero the workspace, then seed each run's control block.
   std::vector<RunCtl> ctl((size_t)cfg->runs);
   for (int r = 0; r < cfg->runs; ++r) {
@@ -415,19 +429,27 @@ int sepso_set_scene(sepso_handle h, const float* start, const float* target, con
   if (O > 0 && !circles) return fail(SEPSO_EINVAL, "circles is NULL");
   if (!finite(start[0]) || !finite(start[1]) || !finite(target[0]) || !finite(target[1]))
     return fail(SEPSO_EINVAL, "start/target not finite");
-  std::vector<float4> c4((size_t)(O > 0 ? O : 0));
   for (int o = 0; o < O; ++o) {
     const float cx = circles[3 * o], cy = circles[3 * o + 1], r = circles[3 * o + 2];
     if (!finite(cx) || !finite(cy) || !finite(r) || r < 0)
       return fail(SEPSO_EINVAL, "circle %d invalid (non-finite or negative radius)", o);
+  }
+  // the previous scene copy must have left the staging buffer
+  CUDA_TRY(cudaEventSynchronize(h->staging_free));
+  float4* c4 = h->staging;
+  for (int o = 0; o < O; ++o) {
+    const float cx = circles[3 * o], cy = circles[3 * o + 1], r = circles[3 * o + 2];
     c4[o] = make_float4(cx, cy, r, r * r);
   }
-  const float pts[8] = {start[0], start[1], target[0], target[1], 0.f, 0.f, 0.f, 0.f};
+  float* pts = reinterpret_cast<float*>(h->staging + std::max(h->cfg.max_obstacles, 1));
+  const float pv[8] = {start[0], start[1], target[0], target[1], 0.f, 0.f, 0.f, 0.f};
+  std::memcpy(pts, pv, sizeof pv);
   if (O > 0) {
-    CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.circ, c4.data(), (size_t)O * 16, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.circ, c4, (size_t)O * 16, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(cudaMemsetAsync(h->ws + h->L.cvel, 0, (size_t)O * 8, h->stream));
   }
-  CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.pts, pts, sizeof pts, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.pts, pts, 8 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaEventRecord(h->staging_free, h->stream));
   h->O = O;
   h->has_scene = true;
   return SEPSO_OK;
@@ -760,6 +782,19 @@ int sepso_launch_shape(sepso_handle h, int32_t* ctas_per_group, int32_t* threads
   if (threads) *threads = h->threads;
   if (circle_split) *circle_split = h->split;
   if (grid) *grid = h->grid;
+  return SEPSO_OK;
+}
+
+int sepso_counters(sepso_handle h, int32_t run, int64_t* plans, int64_t* iterations) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if ((rc = run_ok(h, run))) return rc;
+  long long v[2] = {0, 0};
+  const size_t off = h->L.ctl + (size_t)run * sizeof(RunCtl) + offsetof(RunCtl, plans_total);
+  CUDA_TRY(cudaMemcpyAsync(v, h->ws + off, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (plans) *plans = v[0];
+  if (iterations) *iterations = v[1];
   return SEPSO_OK;
 }
 

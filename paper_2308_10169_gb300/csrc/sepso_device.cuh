@@ -29,6 +29,8 @@ struct RunCtl {
   float prev_lfv;     // LFV of the previous iteration (AT stall mode)
   uint32_t run_id;    // Philox counter word 3
   int32_t pad;
+  long long plans_total;  // planning cycles finished by this run
+  long long iters_total;  // iterations of Algorithm 1 run by this run
 };
 
 // Candidate published by one CTA each iteration: its best Pbest (lowest index on ties).

@@ -444,7 +444,9 @@ __global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
       ctl->Tfit = Tfit;
       ctl->TQ = TQ;
       ctl->k = k;
+      ctl->iters_total += done;
       if (p.mode == kModePlan) {
+        ctl->plans_total += 1;
         float len = 0.0f;
         for (int s = 0; s < nseg; ++s) {
           const float ax = (s == 0) ? sx : sT[s - 1];

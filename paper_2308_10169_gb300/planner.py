@@ -203,5 +203,11 @@ class Planner:
         check(self.lib.sepso_launch_shape(self._h, *[ctypes.byref(x) for x in v]))
         return dict(zip(("ctas_per_group", "threads", "circle_split", "grid"), [x.value for x in v]))
 
+    def counters(self, run: int = 0) -> tuple[int, int]:
+        """(planning cycles finished, iterations run) of one run, cumulative."""
+        p, i = ctypes.c_int64(), ctypes.c_int64()
+        check(self.lib.sepso_counters(self._h, run, ctypes.byref(p), ctypes.byref(i)))
+        return p.value, i.value
+
     def launch_count(self) -> int:
         return int(self.lib.sepso_launch_count(self._h))
