@@ -216,6 +216,35 @@ int sepso_hsef(sepso_handle h, const sepso_hsef_config* hc, float* d_history);
  * and its LFV (host outputs, sync). */
 int sepso_hsef_best(sepso_handle h, float* hyper_out, float* best_lfv);
 
+/* ---- planning without device allocation ---------------------------------- */
+
+/* One planning cycle, like a fresh handle's sepso_plan, for callers that cannot
+ * allocate device memory (code running inside another framework's memory pool,
+ * plugins whose host forbids allocations after start-up, real-time loops where
+ * an allocation may block).  The paper has no counterpart; this is a deployment
+ * convenience.
+ *
+ * The workspace is a static device array inside the library: 8 MiB per GPU that
+ * loads libsepso.so, held until the process exits.  The call allocates no device
+ * or pinned memory and creates no handle.  Inputs are host pointers (cfg;
+ * hyper G x 6; start[2]; target[2]; circles O x 3), copied during the call;
+ * outputs are host pointers (waypoints D floats, res; either may be NULL).
+ * stream: cudaStream_t (NULL = legacy default stream).  Sync.
+ *
+ * Limits: cfg->runs must be 1 and the configuration's workspace
+ * (sepso_workspace_size) must fit in the 8 MiB, else SEPSO_ENOSPC with a message.
+ * Every call starts from zeroed scratch, so no warm-start state (PI, AT window)
+ * carries over between calls.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any CUDA
+ * stream capture.  All calls on a device share the one array: calls that
+ * overlap on the GPU (other threads, other streams) race and corrupt each
+ * other; serialise them.
+ * Errors: EINVAL, ENOSPC, ERANGE, ECUDA, and device-side errors (ETIMEOUT). */
+int sepso_plan_static(const sepso_config* cfg, const float* hyper, const float* start,
+                      const float* target, const float* circles, int32_t O, float* waypoints,
+                      sepso_result* res, void* stream);
+
 /* ---- misc --------------------------------------------------------------- */
 
 /* Wait for the handle's stream; returns the first device-side error of any run

@@ -86,6 +86,8 @@ SIGNATURES = {
     "sepso_set_state": (ctypes.c_int, [_vp, _i32, _vp, _sz]),
     "sepso_hsef": (ctypes.c_int, [_vp, ctypes.POINTER(HsefConfig), _vp]),
     "sepso_hsef_best": (ctypes.c_int, [_vp, _fp, _fp]),
+    "sepso_plan_static": (ctypes.c_int, [ctypes.POINTER(Config), _fp, _fp, _fp, _fp, _i32, _fp,
+                                         ctypes.POINTER(Result), _vp]),
     "sepso_sync": (ctypes.c_int, [_vp]),
     "sepso_launch_shape": (ctypes.c_int, [_vp] + [ctypes.POINTER(_i32)] * 4),
     "sepso_counters": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),

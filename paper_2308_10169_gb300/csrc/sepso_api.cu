@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -801,3 +802,122 @@ int sepso_counters(sepso_handle h, int32_t run, int64_t* plans, int64_t* iterati
 int64_t sepso_launch_count(sepso_handle h) { return h ? h->launches : -1; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Planning without any device allocation.
+//
+// Some callers cannot call cudaMalloc at all: code that runs inside another
+// framework's memory pool, plugins whose host application forbids allocations
+// after start-up, or real-time loops where an allocation could block.  For
+// them, sepso_plan_static keeps its workspace in the file-scope device array
+// below instead of caller-provided memory.  The array is part of the library
+// image, so every GPU that loads libsepso holds these bytes until the process
+// exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;  // 8 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::once_flag g_scratch_once[kMaxDevices];
+void* g_scratch_addr[kMaxDevices];
+cudaError_t g_scratch_err[kMaxDevices];
+
+// The array's name is only a host-side stand-in in host code; its device
+// address must be looked up once per device with that device current.
+int static_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(SEPSO_EINVAL, "device %d out of range", device);
+  std::call_once(g_scratch_once[device], [device] {
+    g_scratch_err[device] = cudaGetSymbolAddress(&g_scratch_addr[device], g_static_scratch);
+  });
+  if (g_scratch_err[device] != cudaSuccess) return cuda_fail(g_scratch_err[device], "cudaGetSymbolAddress");
+  *out = g_scratch_addr[device];
+  return SEPSO_OK;
+}
+
+}  // namespace
+
+extern "C" int sepso_plan_static(const sepso_config* cfg, const float* hyper, const float* start,
+                                 const float* target, const float* circles, int32_t O, float* waypoints,
+                                 sepso_result* res, void* stream) {
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  if (cfg->runs != 1) return fail(SEPSO_EINVAL, "sepso_plan_static plans one run (runs=%d)", cfg->runs);
+  if (!hyper || !start || !target || (O > 0 && !circles))
+    return fail(SEPSO_EINVAL, "NULL input to sepso_plan_static");
+  if (O < 0 || O > cfg->max_obstacles)
+    return fail(SEPSO_EINVAL, "O=%d outside [0, max_obstacles=%d]", O, cfg->max_obstacles);
+  for (int i = 0; i < cfg->G * 6; ++i)
+    if (!finite(hyper[i])) return fail(SEPSO_EINVAL, "hyper[%d] is not finite", i);
+  if (!finite(start[0]) || !finite(start[1]) || !finite(target[0]) || !finite(target[1]))
+    return fail(SEPSO_EINVAL, "start/target not finite");
+  for (int o = 0; o < O; ++o) {
+    const float r = circles[3 * o + 2];
+    if (!finite(circles[3 * o]) || !finite(circles[3 * o + 1]) || !finite(r) || r < 0)
+      return fail(SEPSO_EINVAL, "circle %d invalid (non-finite or negative radius)", o);
+  }
+  const WsLayout L = make_ws(*cfg);
+  if (L.total > kStaticScratchBytes)
+    return fail(SEPSO_ENOSPC,
+                "sepso_plan_static: this configuration needs %zu bytes of workspace; the static "
+                "scratch holds %zu bytes (use sepso_create with caller memory instead)",
+                L.total, kStaticScratchBytes);
+
+  // A handle on the stack: no host or device allocation.
+  sepso_ctx h;
+  h.cfg = *cfg;
+  h.stream = static_cast<cudaStream_t>(stream);
+  h.L = L;
+  h.O = O;
+  h.has_scene = true;
+  {
+    const double v = std::ceil((double)cfg->pi_gamma * (double)cfg->N);
+    h.n_pi = (int)std::min<double>(std::max(v, 0.0), (double)cfg->N);
+  }
+  CUDA_TRY(cudaGetDevice(&h.device));
+  CUDA_TRY(cudaDeviceGetAttribute(&h.num_sms, cudaDevAttrMultiProcessorCount, h.device));
+  void* scratch = nullptr;
+  if ((rc = static_scratch(h.device, &scratch))) return rc;
+  h.ws = static_cast<char*>(scratch);
+  h.ws_bytes = kStaticScratchBytes;
+  if ((rc = choose_shape(&h))) return rc;
+
+  // Each call starts from zeroed scratch (barrier words, bests, counters), then
+  // writes its inputs.  Host inputs are copied from the caller's (pageable)
+  // memory, so they may be reused as soon as this call returns.
+  CUDA_TRY(cudaMemsetAsync(h.ws, 0, L.total, h.stream));
+  RunCtl ctl;
+  std::memset(&ctl, 0, sizeof ctl);
+  ctl.Tfit = INFINITY;
+  ctl.prev_lfv = INFINITY;
+  ctl.run_id = cfg->run_id;
+  CUDA_TRY(cudaMemcpyAsync(h.ws + L.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, h.stream));
+  CUDA_TRY(cudaMemcpyAsync(h.ws + L.hyper, hyper, (size_t)cfg->G * 6 * 4, cudaMemcpyHostToDevice, h.stream));
+  float4 chunk[128];
+  for (int o0 = 0; o0 < O; o0 += 128) {
+    const int n = std::min(128, O - o0);
+    for (int i = 0; i < n; ++i) {
+      const float* c = circles + 3 * (o0 + i);
+      chunk[i] = make_float4(c[0], c[1], c[2], c[2] * c[2]);
+    }
+    CUDA_TRY(cudaMemcpyAsync(h.ws + L.circ + (size_t)o0 * 16, chunk, (size_t)n * 16, cudaMemcpyHostToDevice,
+                             h.stream));
+  }
+  const float pts[8] = {start[0], start[1], target[0], target[1], 0.f, 0.f, 0.f, 0.f};
+  CUDA_TRY(cudaMemcpyAsync(h.ws + L.pts, pts, sizeof pts, cudaMemcpyHostToDevice, h.stream));
+
+  const SwarmParams p = swarm_params(&h, kModePlan, 0);
+  CUDA_TRY(launch_swarm(p, h.grid, h.threads, h.smem, h.stream));
+
+  sepso_result tmp;
+  if (waypoints)
+    CUDA_TRY(cudaMemcpyAsync(waypoints, h.ws + L.res_wp, (size_t)2 * cfg->T * 4, cudaMemcpyDeviceToHost,
+                             h.stream));
+  CUDA_TRY(cudaMemcpyAsync(&tmp, h.ws + L.res, sizeof tmp, cudaMemcpyDeviceToHost, h.stream));
+  CUDA_TRY(cudaStreamSynchronize(h.stream));
+  if (res) *res = tmp;
+  if (tmp.status != SEPSO_OK) return fail(tmp.status, "device-side error in sepso_plan_static");
+  return SEPSO_OK;
+}
