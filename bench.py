@@ -44,6 +44,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # segment-circle test x O circles + 8 flops of length), per the scope table.
 FLOPS_PER_PAIR, FLOPS_PER_SEGMENT = 18, 8
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one swarm_kernel launch of this
+# workload (ncu --set full capture summarised in profiles/swarm_kernel_dynamic_workload.md);
+# set to None whenever the kernel changes until it is captured again.
+SWARM_TRAFFIC_BYTES = 171520
 
 
 def parse():
@@ -296,7 +300,8 @@ def run_ours(args, rank, world, local):
                            "max": float(step_ms.max())},
             "median_cost_last": float(last["cost"]),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": SWARM_TRAFFIC_BYTES,
                          "kernel": "swarm_kernel",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "e2e": e2e,

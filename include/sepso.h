@@ -62,7 +62,7 @@ typedef struct sepso_ctx* sepso_handle;
 typedef struct {
   int32_t T;              /* waypoints per path; D = 2T, 1 <= T <= 64            */
   int32_t G;              /* groups, 1 <= G <= 32                                */
-  int32_t N;              /* particles per group, >= 1                           */
+  int32_t N;              /* particles per group, 1 <= N < 2^20                  */
   int32_t max_obstacles;  /* capacity for circles, >= 0                          */
   float map_w, map_h;     /* X_range: x in [0, map_w], y in [0, map_h]           */
   float alpha;            /* Eq. penalty: alpha * Q^beta                         */
@@ -80,8 +80,8 @@ typedef struct {
   uint32_t run_id;        /* Philox counter word 3 of run 0 (run r: run_id + r)  */
   int32_t runs;           /* independent swarms on the same scene, >= 1          */
   int32_t ctas_per_group; /* 0 = automatic; else CTAs cooperating on one group   */
-  int32_t threads;        /* 0 = automatic; else 64..1024, a multiple of 32      */
-  int32_t circle_split;   /* 0 = automatic; else circle chunks per segment test  */
+  int32_t threads;        /* 0 = automatic; else 64..512, a multiple of 32       */
+  int32_t circle_split;   /* 0 = automatic (1); else circle chunks per segment    */
 } sepso_config;
 
 /* Outcome of one planning cycle of one run. */

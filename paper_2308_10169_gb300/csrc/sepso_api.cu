@@ -47,7 +47,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 // Byte offsets of every array in the caller's workspace.
 struct WsLayout {
   size_t circ, cvel, pts, hyper, X, V, P, Pfit, PQ, Gb, Gfit, GQ, Tb, prevT, res_wp, ctl, res, win,
-      cmeta, crows, bar, hhyper, HX, HV, HP, HPfit, HGb, HGfit, HTb, HTfit, estatus, total;
+      gword, counter, crows, hhyper, HX, HV, HP, HPfit, HGb, HGfit, HTb, HTfit, estatus, total;
 };
 
 WsLayout make_ws(const sepso_config& c) {
@@ -81,9 +81,9 @@ WsLayout make_ws(const sepso_config& c) {
   L.ctl = take(R * sizeof(RunCtl));
   L.res = take(R * sizeof(sepso_result));
   L.win = take(R * (size_t)c.tw * 8);
-  L.cmeta = take(R * 2 * Cmax * sizeof(CandMeta));
-  L.crows = take(R * 2 * Cmax * D * 4);
-  L.bar = take(R * sizeof(RunBarrier));
+  L.gword = take(R * 3 * G * 8);
+  L.counter = take(R * sizeof(RunCounter));
+  L.crows = take(R * 2 * M * (D + 4) * 4);
   L.hhyper = take(32 * 6 * 4);
   L.HX = take(R * DH * 4);
   L.HV = take(R * DH * 4);
@@ -104,7 +104,7 @@ int check_config(const sepso_config* c) {
   if (!c) return fail(SEPSO_EINVAL, "config is NULL");
   if (c->T < 1 || c->T > 64) return fail(SEPSO_EINVAL, "T=%d outside [1, 64]", c->T);
   if (c->G < 1 || c->G > 32) return fail(SEPSO_EINVAL, "G=%d outside [1, 32]", c->G);
-  if (c->N < 1 || c->N > (1 << 20)) return fail(SEPSO_EINVAL, "N=%d outside [1, 2^20]", c->N);
+  if (c->N < 1 || c->N >= (1 << 20)) return fail(SEPSO_EINVAL, "N=%d outside [1, 2^20)", c->N);
   if (c->max_obstacles < 0 || c->max_obstacles > 8192)
     return fail(SEPSO_EINVAL, "max_obstacles=%d outside [0, 8192]", c->max_obstacles);
   if (!finite(c->map_w) || !finite(c->map_h) || c->map_w <= 0 || c->map_h <= 0)
@@ -121,8 +121,8 @@ int check_config(const sepso_config* c) {
   if (!finite(c->pi_halfwidth) || c->pi_halfwidth < 0) return fail(SEPSO_EINVAL, "pi_halfwidth < 0");
   if (c->runs < 1 || c->runs > 65536) return fail(SEPSO_EINVAL, "runs=%d outside [1, 65536]", c->runs);
   if (c->ctas_per_group < 0) return fail(SEPSO_EINVAL, "ctas_per_group < 0");
-  if (c->threads != 0 && (c->threads < 64 || c->threads > 1024 || c->threads % 32 != 0))
-    return fail(SEPSO_EINVAL, "threads=%d must be 0 or a multiple of 32 in [64, 1024]", c->threads);
+  if (c->threads != 0 && (c->threads < 64 || c->threads > 512 || c->threads % 32 != 0))
+    return fail(SEPSO_EINVAL, "threads=%d must be 0 or a multiple of 32 in [64, 512]", c->threads);
   if (c->circle_split < 0) return fail(SEPSO_EINVAL, "circle_split < 0");
   return SEPSO_OK;
 }
@@ -138,7 +138,7 @@ struct sepso_ctx {
   WsLayout L{};
   int O = 0;
   bool has_scene = false;
-  int cpg = 1, ppc = 1, C = 1, threads = 256, split = 1, grid = 1;
+  int cpg = 1, ppc = 1, C = 1, threads = 256, split = 1, lp = 32, grid = 1;
   size_t smem = 0;
   int n_pi = 0;
   int64_t launches = 0;
@@ -172,6 +172,7 @@ SwarmParams swarm_params(const sepso_ctx* h, int mode, int step_iters) {
   p.C = h->C;
   p.ppc = h->ppc;
   p.split = h->split;
+  p.lp = h->lp;
   p.O = h->O;
   p.Omax = c.max_obstacles;
   p.W = c.map_w;
@@ -208,63 +209,64 @@ SwarmParams swarm_params(const sepso_ctx* h, int mode, int step_iters) {
   p.ctl = h->at<RunCtl>(h->L.ctl);
   p.res = h->at<sepso_result>(h->L.res);
   p.win = h->at<double>(h->L.win);
-  p.cmeta = h->at<CandMeta>(h->L.cmeta);
+  p.gword = h->at<unsigned long long>(h->L.gword);
+  p.counter = h->at<RunCounter>(h->L.counter);
   p.crows = h->at<float>(h->L.crows);
-  p.bar = h->at<RunBarrier>(h->L.bar);
   return p;
 }
 
-// Pick CTAs per group, threads and circle split, then check co-residency.
+// Pick CTAs per group, threads and circle split, then check co-residency: the
+// cooperative launch needs every CTA resident at once.  Automatic choices start
+// from one CTA per SM and back off (fewer threads, then fewer CTAs per group).
 int choose_shape(sepso_ctx* h) {
   const sepso_config& c = h->cfg;
   const int R = c.runs, G = c.G, N = c.N, T = c.T, D = 2 * T;
   const int Omax = c.max_obstacles;
   int smem_optin = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+  // One lane group of lp lanes (a power of two, <= 32) per particle; lanes take
+  // (segment, circle chunk) items.
+  const int split = c.circle_split > 0 ? c.circle_split : 1;
+  int lp = 1;
+  while (lp < 32 && lp < (T + 1) * split) lp <<= 1;
+  CUDA_TRY(configure_swarm_kernel((size_t)smem_optin));
   int cpg = c.ctas_per_group > 0 ? c.ctas_per_group : std::max(1, h->num_sms / std::max(1, R * G));
   cpg = std::min(cpg, N);
-  for (;;) {
-    int ppc = (N + cpg - 1) / cpg;
+  size_t smem = 0;
+  int bps = 0, threads = 0;
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    const int ppc = (N + cpg - 1) / cpg;
     cpg = (N + ppc - 1) / ppc;  // no empty CTAs
-    const int items = ppc * (T + 1);
-    int threads = c.threads;
-    if (threads == 0) threads = std::min(256, std::max(64, (items + 31) / 32 * 32));
-    int split = c.circle_split;
-    if (split == 0) split = std::max(1, std::min(threads / std::max(1, items), std::max(1, Omax / 8)));
     const SmemLayout S = SmemLayout::make(Omax, ppc, D, T, G, c.tw);
-    const size_t smem = (size_t)S.total;
-    bool fits = smem + 256 <= (size_t)smem_optin;  // static shared memory is < 256 B
-    int bps = 0;
-    if (fits) {
-      // The attribute is per function: set it to the device maximum so that handles with
-      // different shared-memory needs can coexist; occupancy uses the actual size.
-      CUDA_TRY(configure_swarm_kernel((size_t)smem_optin));
-      CUDA_TRY(swarm_occupancy(threads, smem, &bps));
-      fits = (long long)R * G * cpg <= (long long)bps * h->num_sms;
-    }
-    if (fits) {
-      h->cpg = cpg;
-      h->ppc = ppc;
-      h->C = G * cpg;
-      h->threads = threads;
-      h->split = split;
-      h->smem = smem;
-      h->grid = R * G * cpg;
-      return SEPSO_OK;
-    }
-    if (c.ctas_per_group > 0 || cpg == 1) {
-      // more CTAs per group only lowers shared memory per CTA; fewer is the only other knob
-      if (c.ctas_per_group == 0 && smem > (size_t)smem_optin && cpg < N) {
-        ++cpg;
-        continue;
+    smem = (size_t)S.total;
+    const int ppw = 32 / lp;
+    const int want = std::min(512, std::max(64, (ppc + ppw - 1) / ppw * 32));
+    for (threads = (c.threads ? c.threads : want); threads >= 64; threads -= 64) {
+      bps = 0;
+      if (smem + 256 <= (size_t)smem_optin) CUDA_TRY(swarm_occupancy(threads, smem, &bps));
+      if ((long long)R * G * cpg <= (long long)bps * h->num_sms) {
+        h->cpg = cpg;
+        h->ppc = ppc;
+        h->C = G * cpg;
+        h->threads = threads;
+        h->split = split;
+        h->lp = lp;
+        h->smem = smem;
+        h->grid = R * G * cpg;
+        return SEPSO_OK;
       }
-      return fail(SEPSO_ERANGE,
-                  "launch does not fit: %d runs x %d groups x %d CTAs, %zu B shared memory per CTA, "
-                  "%d CTAs per SM on %d SMs",
-                  R, G, cpg, smem, bps, h->num_sms);
+      if (c.threads) break;
     }
-    cpg = std::max(1, cpg / 2);
+    if (c.ctas_per_group > 0) break;
+    // Fewer CTAs when the grid is too large; more when one CTA's rows do not fit.
+    if (smem + 256 > (size_t)smem_optin && cpg < N) ++cpg;
+    else if ((long long)R * G * cpg > (long long)h->num_sms && cpg > 1) cpg = std::max(1, cpg / 2);
+    else break;
   }
+  return fail(SEPSO_ERANGE,
+              "launch does not fit: %d runs x %d groups x %d CTAs, %zu B shared memory per CTA, "
+              "%d CTAs per SM on %d SMs",
+              R, G, cpg, smem, bps, h->num_sms);
 }
 
 int check_handle(sepso_handle h) {
@@ -387,6 +389,8 @@ int sepso_create(const sepso_config* cfg, void* d_workspace, size_t bytes, void*
     ctl[r].run_id = cfg->run_id + (uint32_t)r;
   }
   e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);
+  if (e == cudaSuccess)  // empty group-best keys
+    e = cudaMemsetAsync(h->ws + L.gword, 0xff, (size_t)cfg->runs * 3 * cfg->G * 8, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->ws + L.ctl, ctl.data(), ctl.size() * sizeof(RunCtl), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -440,7 +444,7 @@ int sepso_set_scene(sepso_handle h, const float* start, const float* target, con
   float4* c4 = h->staging;
   for (int o = 0; o < O; ++o) {
     const float cx = circles[3 * o], cy = circles[3 * o + 1], r = circles[3 * o + 2];
-    c4[o] = make_float4(cx, cy, r, r * r);
+    c4[o] = make_float4(cx, cy, r, 4.0f * (r * r));
   }
   float* pts = reinterpret_cast<float*>(h->staging + std::max(h->cfg.max_obstacles, 1));
   const float pv[8] = {start[0], start[1], target[0], target[1], 0.f, 0.f, 0.f, 0.f};
@@ -766,10 +770,17 @@ int sepso_sync(sepso_handle h) {
       dirty = true;
     }
   if (dirty) {
-    // clear the error words and re-zero the barriers, which a timed-out wait leaves inconsistent
+    // Clear the error words.  A wait that gave up leaves the barrier counters and
+    // group words of its run inconsistent: rebuild them from the iteration counts.
+    std::vector<RunCounter> cnt(ctl.size());
+    for (size_t r = 0; r < ctl.size(); ++r) {
+      std::memset(&cnt[r], 0, sizeof(RunCounter));
+      cnt[r].count = (unsigned int)h->C * (unsigned int)ctl[r].iters_total;
+    }
     CUDA_TRY(cudaMemcpy(h->ws + h->L.ctl, ctl.data(), ctl.size() * sizeof(RunCtl), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(h->ws + h->L.counter, cnt.data(), cnt.size() * sizeof(RunCounter), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemset(h->ws + h->L.gword, 0xff, ctl.size() * 3 * h->cfg.G * 8));
     CUDA_TRY(cudaMemset(h->ws + h->L.estatus, 0, 4));
-    CUDA_TRY(cudaMemset(h->ws + h->L.bar, 0, (size_t)h->cfg.runs * sizeof(RunBarrier)));
     return fail(first, "device-side error: %s", sepso_strerror(first));
   }
   return SEPSO_OK;
@@ -884,10 +895,11 @@ extern "C" int sepso_plan_static(const sepso_config* cfg, const float* hyper, co
   h.ws_bytes = kStaticScratchBytes;
   if ((rc = choose_shape(&h))) return rc;
 
-  // Each call starts from zeroed scratch (barrier words, bests, counters), then
-  // writes its inputs.  Host inputs are copied from the caller's (pageable)
+  // Each call starts from zeroed scratch (barrier counter, bests, counters) with
+  // empty group-best keys, then writes its inputs.  Host inputs are copied from the caller's (pageable)
   // memory, so they may be reused as soon as this call returns.
   CUDA_TRY(cudaMemsetAsync(h.ws, 0, L.total, h.stream));
+  CUDA_TRY(cudaMemsetAsync(h.ws + L.gword, 0xff, (size_t)3 * cfg->G * 8, h.stream));  // empty keys
   RunCtl ctl;
   std::memset(&ctl, 0, sizeof ctl);
   ctl.Tfit = INFINITY;
@@ -900,7 +912,7 @@ extern "C" int sepso_plan_static(const sepso_config* cfg, const float* hyper, co
     const int n = std::min(128, O - o0);
     for (int i = 0; i < n; ++i) {
       const float* c = circles + 3 * (o0 + i);
-      chunk[i] = make_float4(c[0], c[1], c[2], c[2] * c[2]);
+      chunk[i] = make_float4(c[0], c[1], c[2], 4.0f * (c[2] * c[2]));
     }
     CUDA_TRY(cudaMemcpyAsync(h.ws + L.circ + (size_t)o0 * 16, chunk, (size_t)n * 16, cudaMemcpyHostToDevice,
                              h.stream));

@@ -1,7 +1,8 @@
 // sepso_device.cuh -- device-side building blocks of the SEPSO planner (sm_103a).
 //
 // Internal to libsepso: the workspace records, Philox4x32-10, the bulk-copy /
-// mbarrier helpers, the bounded inter-CTA barrier and the segment-circle test.
+// mbarrier helpers, the group-best exchange (atomic-min keys and a monotone
+// barrier counter) and the segment-circle test.
 #pragma once
 
 #include <cstdint>
@@ -33,19 +34,33 @@ struct RunCtl {
   long long iters_total;  // iterations of Algorithm 1 run by this run
 };
 
-// Candidate published by one CTA each iteration: its best Pbest (lowest index on ties).
-struct __align__(16) CandMeta {
-  float fit;
-  int32_t idx;  // particle index n within the group (INT32_MAX when the CTA is empty)
-  int32_t q;    // collision count of that Pbest
-  int32_t pad;
-};
+// Group bests without moving rows through a reduction: every particle whose
+// Pbest is below its group's best folds its key into the group's word with a
+// 64-bit atomic min.  Fitness values are non-negative, so their IEEE bit
+// patterns order like the values; the key is (fitness bits << 32) | (particle
+// index n << 12) | min(Q, kQSat), and the minimum key is the lowest-index
+// particle of minimum fitness (indices are unique, so Q never decides).  Words
+// are triple-buffered by iteration (read during iteration k, reset by CTA 0
+// during k + 1, reused at k + 3).  Such a particle also writes its row and Q to
+// its slot, where readers fetch the winner's.
+constexpr unsigned long long kKeyEmpty = ~0ull;
 
-// Inter-CTA barrier of one run (own 128-byte line).
-struct __align__(128) RunBarrier {
+constexpr uint32_t kQSat = 0xfffu;  // Q field saturates here (exact Q then read from the slot)
+
+__device__ __forceinline__ unsigned long long best_key(float fit, uint32_t idx, uint32_t q) {
+  return ((unsigned long long)__float_as_uint(fit) << 32) | ((unsigned long long)(idx & 0xfffffu) << 12) |
+         (unsigned long long)(q < kQSat ? q : kQSat);
+}
+__device__ __forceinline__ float key_fit(unsigned long long key) { return __uint_as_float((uint32_t)(key >> 32)); }
+__device__ __forceinline__ int key_idx(unsigned long long key) { return (int)((uint32_t)key >> 12); }
+__device__ __forceinline__ int key_q(unsigned long long key) { return (int)((uint32_t)key & kQSat); }
+
+// Per-run barrier counter on its own 128-byte line.  It only grows: the CTAs of
+// a run add 1 each per iteration, so the barrier of the run's gk-th iteration
+// (counted across launches) is complete when the counter reaches C * gk.
+struct __align__(128) RunCounter {
   unsigned int count;
-  unsigned int gen;
-  unsigned int pad[30];
+  unsigned int pad[31];
 };
 
 enum : int { kModePlan = 0, kModeStep = 1 };
@@ -61,6 +76,7 @@ struct SwarmParams {
   int R;                      // runs in this launch
   int cpg, C, ppc;            // CTAs per group, CTAs per run, particles per CTA
   int split;                  // circle chunks per (particle, segment) item
+  int lp;                     // lanes per particle (power of two, <= 32)
   int O, Omax;                // obstacles now / capacity (shared-memory carve)
   float W, H, alpha;
   int beta, max_iters, at_mode, tw;
@@ -72,7 +88,7 @@ struct SwarmParams {
   uint32_t key0, key1;
   int mode, step_iters;
   // device pointers
-  const float4* circ;         // Omax x (cx, cy, r, r^2)
+  const float4* circ;         // Omax x (cx, cy, r, 4 r^2)
   const float* pts;           // start xy, target xy, start vel, target vel
   const float* hyper;         // R x G x 6
   float *X, *V, *P, *Pfit;    // R x M x D (X, V, P), R x M
@@ -83,9 +99,9 @@ struct SwarmParams {
   RunCtl* ctl;                // R
   sepso_result* res;          // R
   double* win;                // R x tw
-  CandMeta* cmeta;            // R x 2 x C
-  float* crows;               // R x 2 x C x D
-  RunBarrier* bar;            // R
+  unsigned long long* gword;  // R x 3 x G group best keys
+  RunCounter* counter;        // R
+  float* crows;               // R x 2 x M x (D + 4): candidate row, its Q, padding
 };
 
 // ---------------------------------------------------------------------------
@@ -174,63 +190,46 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ---------------------------------------------------------------------------
-// Bounded barrier across the CTAs of one run (co-resident: cooperative launch).
+// Acquire/release accesses for the candidate exchange between the CTAs of a run
+// (co-resident: cooperative launch).  Waits on them are bounded by kWaitLimitNs.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* p) {
   unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+
+__device__ __forceinline__ void red_min_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.relaxed.gpu.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// After relaxed loads that observed a writer's stores: an acquire.  Before a
+// writer's relaxed stores: a release of everything it wrote earlier.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
-
-// Every CTA of the run calls this with the same n.  Returns false (in every
-// thread of the CTA) when the wait gave up; the barrier is then unusable until
-// the host re-zeroes it.
-__device__ __forceinline__ bool run_barrier(RunBarrier* b, unsigned int n, int* s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned int g0 = ld_acquire(&b->gen);
-    __threadfence();
-    const unsigned int prev = atomicAdd(&b->count, 1u);
-    if (prev == n - 1) {
-      atomicExch(&b->count, 0u);
-      __threadfence();
-      st_release(&b->gen, g0 + 1u);
-    } else {
-      unsigned int spins = 0;
-      unsigned long long t0 = 0;
-      while (ld_acquire(&b->gen) == g0) {
-        if ((++spins & 255u) == 0u) {
-          const unsigned long long t = global_ns();
-          if (t0 == 0) t0 = t;
-          else if (t - t0 > kWaitLimitNs) {
-            ok = 0;
-            break;
-          }
-        }
-      }
-    }
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
-}
 
 // ---------------------------------------------------------------------------
 // Segment-circle test (Eq. penalty's Q for circular obstacles).
 // The segment [a, b] is described by its midpoint m, unit direction u, normal
 // n = (-u_y, u_x) and half-length h.  For a circle centre c, along = (c - m).u
 // and perp = (c - m).n; the squared distance to the segment is
-// max(|along| - h, 0)^2 + perp^2, compared with r^2 (strict: open disk).
+// max(|along| - h, 0)^2 + perp^2; the pair collides when it is below r^2 (open
+// disk).  Everything is kept on the FP32 FMA pipe: with a = |along| - h,
+// t = a + |a| = 2 max(a, 0) exactly, the normal is pre-scaled by 2 (exact) so
+// that p2 = 2 perp, and s = 4r^2 - p2^2 - t^2 = 4 (r^2 - dist^2) is formed by two
+// FMAs; hit = saturate(s * 2^100) is exactly 1 for s > 0 and 0 otherwise (a
+// positive s is never below 2^-100 here), and hits accumulate in FP32 (exact
+// below 2^24).  Circles are stored as (cx, cy, r, 4 r^2).
 // ---------------------------------------------------------------------------
 struct SegFrame {
-  float ux, uy, mu, mn, h;
+  float ux, uy, mu, nx2, ny2, mn2, h;
 };
 
 __device__ __forceinline__ SegFrame seg_frame(float ax, float ay, float bx, float by, float* len_out) {
@@ -247,22 +246,25 @@ __device__ __forceinline__ SegFrame seg_frame(float ax, float ay, float bx, floa
   f.ux = ux;
   f.uy = uy;
   f.mu = fmaf(mx, ux, my * uy);
-  f.mn = fmaf(my, ux, -(mx * uy));
+  f.nx2 = -2.0f * uy;
+  f.ny2 = 2.0f * ux;
+  f.mn2 = fmaf(mx, f.nx2, my * f.ny2);
   f.h = 0.5f * len;
   *len_out = len;
   return f;
 }
 
-__device__ __forceinline__ int seg_hits(const SegFrame& f, const float4* __restrict__ circ, int o0, int o1) {
-  int hits = 0;
-#pragma unroll 4
+__device__ __forceinline__ float seg_hits(const SegFrame& f, const float4* __restrict__ circ, int o0, int o1) {
+  float hits = 0.0f;
+#pragma unroll 8
   for (int o = o0; o < o1; ++o) {
     const float4 c = circ[o];
     const float al = fmaf(c.x, f.ux, fmaf(c.y, f.uy, -f.mu));
-    const float pe = fmaf(c.y, f.ux, fmaf(-c.x, f.uy, -f.mn));
-    const float e = fmaxf(fabsf(al) - f.h, 0.0f);
-    const float d2 = fmaf(e, e, pe * pe);
-    hits += (d2 < c.w) ? 1 : 0;
+    const float p2 = fmaf(c.x, f.nx2, fmaf(c.y, f.ny2, -f.mn2));
+    const float a = fabsf(al) - f.h;
+    const float t = a + fabsf(a);
+    const float s = fmaf(-t, t, fmaf(-p2, p2, c.w));
+    hits += __saturatef(s * 0x1p100f);
   }
   return hits;
 }
@@ -296,7 +298,7 @@ __device__ __forceinline__ void fitness_items(const float* sX, int nl, int T, in
     const SegFrame f = seg_frame(ax, ay, bx, by, &len);
     const int o0 = c * chunk;
     const int o1 = min(O, o0 + chunk);
-    const int hits = seg_hits(f, circ, o0, o1);
+    const int hits = (int)seg_hits(f, circ, o0, o1);
     if (hits) atomicAdd(&sQ[i], hits);
     if (c == 0) seg_len[i * nseg + s] = len;
   }

@@ -14,7 +14,7 @@ struct RunCtl;
 
 // Shared-memory carve of swarm_kernel (byte offsets); identical on host and device.
 struct SmemLayout {
-  int circ, win, X, V, P, R, Gall, Tb, Pfit, PQ, Q, Imp, Len, Gfit, GQ, Gsrc, total;
+  int circ, win, X, V, P, R, Gown, Tb, Pfit, PQ, Q, Imp, Len, Gfit, GQ, Gsrc, total;
   __host__ __device__ static SmemLayout make(int Omax, int ppc, int D, int T, int G, int tw);
 };
 
@@ -23,7 +23,7 @@ struct EvalParams {
   float alpha;
   int beta;
   const float* X;      // n x D (device)
-  const float4* circ;  // Omax x (cx, cy, r, r^2)
+  const float4* circ;  // Omax x (cx, cy, r, 4 r^2)
   const float* pts;    // start xy, target xy
   float* F;
   int32_t* Q;

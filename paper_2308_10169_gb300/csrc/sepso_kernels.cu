@@ -12,11 +12,15 @@
 //
 // Work split of swarm_kernel: run r owns C = G * cpg CTAs; CTA (g, q) owns
 // particles [q * ppc, q * ppc + ppc) of group g and keeps their X, V, P rows in
-// shared memory for the whole launch.  Each iteration every CTA publishes its
-// best Pbest (value, index, Q, row) into a parity-double-buffered slot, meets
-// the other CTAs of its run at a bounded global-memory barrier, and then every
-// CTA reduces the same slots in the same order, so all CTAs hold identical
-// Gbest / Tbest copies and take identical truncation decisions.
+// shared memory for the whole launch.  Each iteration every particle whose Pbest
+// is below its group's best leaves its row in a parity-double-buffered slot and
+// folds its key (fitness bits, index, Q) into the group's word with a 64-bit
+// atomic min; each CTA then arrives at the run's monotone barrier counter; after
+// the barrier every CTA reads the same G words, so all CTAs hold identical Gbest
+// / Tbest values and take identical truncation decisions, and each fetches the
+// winning rows it needs.  A slot of parity k & 1 is rewritten only at k + 2,
+// after the barrier of k + 1, i.e. after every CTA has finished reading the
+// slots of k.
 #include <cfloat>
 #include <climits>
 #include <cstdint>
@@ -43,8 +47,8 @@ __host__ __device__ SmemLayout SmemLayout::make(int Omax, int ppc, int D, int T,
   off = align_up(off + ppc * D * 4, 16);
   s.R = off;
   off = align_up(off + ppc * 16, 16);
-  s.Gall = off;
-  off = align_up(off + G * D * 4, 16);
+  s.Gown = off;
+  off = align_up(off + D * 4, 16);
   s.Tb = off;
   off = align_up(off + D * 4, 16);
   s.Pfit = off;
@@ -70,11 +74,10 @@ __host__ __device__ SmemLayout SmemLayout::make(int Omax, int ppc, int D, int T,
 // ---------------------------------------------------------------------------
 // The fused persistent iteration.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
+__global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t s_mbar;
-  __shared__ int s_ok, s_stop, s_bidx, s_bq;
-  __shared__ float s_best;
+  __shared__ int s_stop;
 
   const SmemLayout L = SmemLayout::make(p.Omax, p.ppc, p.D, p.T, p.G, p.tw);
   float4* sC = reinterpret_cast<float4*>(smem + L.circ);
@@ -83,13 +86,10 @@ __global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
   float* sV = reinterpret_cast<float*>(smem + L.V);
   float* sP = reinterpret_cast<float*>(smem + L.P);
   float* sR = reinterpret_cast<float*>(smem + L.R);
-  float* sGall = reinterpret_cast<float*>(smem + L.Gall);
+  float* sG = reinterpret_cast<float*>(smem + L.Gown);
   float* sT = reinterpret_cast<float*>(smem + L.Tb);
   float* sPfit = reinterpret_cast<float*>(smem + L.Pfit);
   int* sPQ = reinterpret_cast<int*>(smem + L.PQ);
-  int* sQ = reinterpret_cast<int*>(smem + L.Q);
-  int* sImp = reinterpret_cast<int*>(smem + L.Imp);
-  float* sLen = reinterpret_cast<float*>(smem + L.Len);
   float* sGfit = reinterpret_cast<float*>(smem + L.Gfit);
   int* sGQ = reinterpret_cast<int*>(smem + L.GQ);
   int* sGsrc = reinterpret_cast<int*>(smem + L.Gsrc);
@@ -125,6 +125,8 @@ __global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
   float* gP = p.P + ((size_t)r * p.M + (size_t)g * N + n0) * D;
   float* gPfit = p.Pfit + (size_t)r * p.M + (size_t)g * N + n0;
   int32_t* gPQ = p.PQ + (size_t)r * p.M + (size_t)g * N + n0;
+  float* gGb = p.Gb + (size_t)r * G * D;  // G rows, kept current by the CTAs that win them
+  float* gTb = p.Tb + (size_t)r * D;      // kept current likewise
 
   float Tfit;
   int TQ, k;
@@ -161,10 +163,13 @@ __global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
     for (int i = tid; i < nl; i += nt) {
       sPfit[i] = INFINITY;
       sPQ[i] = 0;
-      sQ[i] = 0;
     }
-    for (int j = tid; j < G * D; j += nt) sGall[j] = 0.0f;
-    for (int j = tid; j < D; j += nt) sT[j] = 0.0f;
+    for (int j = tid; j < D; j += nt) {
+      sG[j] = 0.0f;
+      sT[j] = 0.0f;
+      if (q == 0) gGb[g * D + j] = 0.0f;  // before this CTA's first publication
+      if (cr == 0) gTb[j] = 0.0f;
+    }
     for (int j = tid; j < G; j += nt) {
       sGfit[j] = INFINITY;
       sGQ[j] = 0;
@@ -188,10 +193,11 @@ __global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
     for (int i = tid; i < nl; i += nt) {
       sPfit[i] = gPfit[i];
       sPQ[i] = gPQ[i];
-      sQ[i] = 0;
     }
-    for (int j = tid; j < G * D; j += nt) sGall[j] = p.Gb[(size_t)r * G * D + j];
-    for (int j = tid; j < D; j += nt) sT[j] = p.Tb[(size_t)r * D + j];
+    for (int j = tid; j < D; j += nt) {
+      sG[j] = gGb[g * D + j];
+      sT[j] = gTb[j];
+    }
     for (int j = tid; j < G; j += nt) {
       sGfit[j] = p.Gfit[(size_t)r * G + j];
       sGQ[j] = p.GQ[(size_t)r * G + j];
@@ -213,131 +219,146 @@ __global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
   }
 
   const int nseg = T + 1;
+  // Iterations already run by this run (across launches): they index the
+  // barrier count and the rotation of the group words.
+  const unsigned long long kbase = (unsigned long long)ctl->iters_total;
+  const int rstride = D + 4;
+  const bool need_T = c3 != 0.0f;  // the Tbest row enters this group's update
+  int last_t_src = -2, last_tg = -1;
+  size_t last_rbase = 0;
   int done = 0;
   while (!failed) {
     if (p.mode == kModeStep && done >= p.step_iters) break;
     ++k;
     ++done;
+    const unsigned long long gk = kbase + (unsigned long long)done;  // the run's iteration count
+    const size_t rbase = ((size_t)r * 2 + (size_t)(gk & 1ull)) * p.M;    // candidate rows
+    const size_t wbase = ((size_t)r * 3 + (size_t)(gk % 3ull)) * G;      // group words of gk
+    const size_t wprev = ((size_t)r * 3 + (size_t)((gk + 2ull) % 3ull)) * G;  // of gk - 1
 
-    // Fitness = F(X^k): Q by shared atomics, segment lengths per item.
-    fitness_items(sX, nl, T, D, sx, sy, tx, ty, sC, p.O, p.split, sQ, sLen);
-    __syncthreads();
-
-    // Per particle: Eq. path_fit, the Pbest test, and this iteration's R1..R3.
-    for (int i = tid; i < nl; i += nt) {
-      float len = 0.0f;
-      for (int s = 0; s < nseg; ++s) len += sLen[i * nseg + s];
-      const int qq = sQ[i];
-      sQ[i] = 0;
-      const float F = len + p.alpha * powi((float)qq, p.beta);
-      const int imp = F < sPfit[i];
-      if (imp) {
-        sPfit[i] = F;
-        sPQ[i] = qq;
+    // Fitness = F(X^k), Pbest test and publication, one lane group (lp lanes) per
+    // particle: lanes take (segment, circle chunk) items, the group sums length
+    // and Q with a fixed shuffle tree.  A particle whose Pbest is below its
+    // group's current best writes its row and Q to its slot and folds its key
+    // into the group word.
+    {
+      const int lp = p.lp;
+      const int ppw = 32 / lp;
+      const int lsub = lane & (lp - 1);
+      const int items = nseg * p.split;
+      const int chunk = (p.O + p.split - 1) / p.split;
+      for (int i0 = warp * ppw; i0 < nl; i0 += nwarps * ppw) {
+        const int i = i0 + lane / lp;
+        const bool live = i < nl;
+        float len = 0.0f, hits = 0.0f;
+        if (live) {
+          const float* x = sX + i * D;
+          for (int it = lsub; it < items; it += lp) {
+            const int c = it % p.split;
+            const int sg = it / p.split;
+            const float ax = (sg == 0) ? sx : x[sg - 1];
+            const float ay = (sg == 0) ? sy : x[T + sg - 1];
+            const float bx = (sg == T) ? tx : x[sg];
+            const float by = (sg == T) ? ty : x[T + sg];
+            float l;
+            const SegFrame f = seg_frame(ax, ay, bx, by, &l);
+            if (c == 0) len += l;
+            hits += seg_hits(f, sC, c * chunk, min(p.O, c * chunk + chunk));
+          }
+        }
+        for (int off = lp >> 1; off > 0; off >>= 1) {
+          len += __shfl_xor_sync(0xffffffffu, len, off);
+          hits += __shfl_xor_sync(0xffffffffu, hits, off);
+        }
+        int imp = 0, pub = 0;
+        float pf = INFINITY;
+        int pq = 0;
+        if (live && lsub == 0) {
+          const int qq = (int)hits;
+          const float F = len + p.alpha * powi((float)qq, p.beta);
+          pf = sPfit[i];
+          pq = sPQ[i];
+          if (F < pf) {
+            imp = 1;
+            pf = F;
+            pq = qq;
+            sPfit[i] = F;
+            sPQ[i] = qq;
+          }
+          pub = pf < sGfit[g];
+        }
+        const int leader = lane & ~(lp - 1);
+        imp = __shfl_sync(0xffffffffu, imp, leader);
+        pub = __shfl_sync(0xffffffffu, pub, leader);
+        if (live && (imp || pub)) {
+          const size_t m = (size_t)g * N + n0 + i;
+          float* slot = p.crows + (rbase + m) * rstride;
+          for (int j = lsub; j < D; j += lp) {
+            const float v = imp ? sX[i * D + j] : sP[i * D + j];
+            if (imp) sP[i * D + j] = v;
+            if (pub) slot[j] = v;
+          }
+          if (pub && lsub == 0) {
+            slot[D] = __int_as_float(pq);
+            red_min_u64(p.gword + wbase + g, best_key(pf, (uint32_t)(n0 + i), (uint32_t)pq));
+          }
+        }
       }
-      sImp[i] = imp;
+    }
+    // This iteration's R1..R3 (independent of the exchange).
+    for (int i = tid; i < nl; i += nt) {
       const uint4 o = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)(g * N + n0 + i), kStreamVel, cycle, run);
       sR[i * 4 + 0] = c1 * u01(o.x);
       sR[i * 4 + 1] = c2 * u01(o.y);
       sR[i * 4 + 2] = c3 * u01(o.z);
     }
     __syncthreads();
+    // Arrive: the release orders this CTA's rows and keys before the arrival.
+    if (tid == 0) red_release_add(&p.counter[r].count, 1u);
 
-    // Pbest rows; warp 0 finds the CTA's best Pbest (lowest index on ties).
-    for (int it = tid; it < nl * D; it += nt) {
-      if (sImp[it / D]) sP[it] = sX[it];
-    }
-    if (warp == 0) {
-      float bv = INFINITY;
-      int bi = INT_MAX, bq = 0;
-      for (int i = lane; i < nl; i += 32) {
-        const float v = sPfit[i];
-        if (v < bv) {
-          bv = v;
-          bi = n0 + i;
-          bq = sPQ[i];
-        }
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float v2 = __shfl_xor_sync(0xffffffffu, bv, off);
-        const int i2 = __shfl_xor_sync(0xffffffffu, bi, off);
-        const int q2 = __shfl_xor_sync(0xffffffffu, bq, off);
-        if (v2 < bv || (v2 == bv && i2 < bi)) {
-          bv = v2;
-          bi = i2;
-          bq = q2;
-        }
-      }
-      if (lane == 0) {
-        s_best = bv;
-        s_bidx = bi;
-        s_bq = bq;
-      }
-    }
-    __syncthreads();
-
-    // Publish the candidate (parity slot k & 1), then meet the run's other CTAs.
-    const int par = k & 1;
-    const size_t base = ((size_t)r * 2 + par) * p.C;
+    // Barrier: every CTA of the run has arrived once per iteration, gk times in all.
+    int timed_out = 0;
     if (tid == 0) {
-      CandMeta m;
-      m.fit = s_best;
-      m.idx = s_bidx;
-      m.q = s_bq;
-      m.pad = 0;
-      p.cmeta[base + cr] = m;
+      const unsigned int target = (unsigned int)p.C * (unsigned int)gk;
+      unsigned int v = ld_relaxed_u32(&p.counter[r].count);
+      if ((int)(v - target) < 0) {
+        const unsigned long long t0 = global_ns();
+        do {
+          if (global_ns() - t0 > kWaitLimitNs) {
+            timed_out = 1;
+            break;
+          }
+          v = ld_relaxed_u32(&p.counter[r].count);
+        } while ((int)(v - target) < 0);
+      }
+      fence_acq_rel_gpu();  // with the relaxed load that saw the count: an acquire
     }
-    if (s_bidx != INT_MAX) {
-      const int wi = s_bidx - n0;
-      for (int j = tid; j < D; j += nt) p.crows[(base + cr) * D + j] = sP[wi * D + j];
-    }
-    if (!run_barrier(p.bar + r, (unsigned int)p.C, &s_ok)) {
+    if (__syncthreads_or(timed_out)) {
       if (tid == 0) ctl->status = SEPSO_ETIMEOUT;
       failed = true;
       break;
     }
 
-    // Gbest of every group: argmin over its CTAs' candidates, same order everywhere.
-    for (int gg = warp; gg < G; gg += nwarps) {
-      float bv = INFINITY;
-      int bi = INT_MAX, bq = 0, bs = -1;
-      for (int qq = lane; qq < p.cpg; qq += 32) {
-        const int4 raw = __ldcg(reinterpret_cast<const int4*>(p.cmeta + base + gg * p.cpg + qq));
-        const float v = __int_as_float(raw.x);
-        if (v < bv || (v == bv && raw.y < bi)) {
-          bv = v;
-          bi = raw.y;
-          bq = raw.z;
-          bs = gg * p.cpg + qq;
-        }
+    // Group bests: a group improved when its word holds a key below its Gfit; the
+    // winner is particle key_idx of that group (slot g * N + n).  The key carries
+    // Q saturated at kQSat; the exact value is then read from the slot.
+    for (int gg = tid; gg < G; gg += nt) {
+      const unsigned long long key = __ldcg(p.gword + wbase + gg);
+      int src = -1;
+      if (key != kKeyEmpty && key_fit(key) < sGfit[gg]) {
+        sGfit[gg] = key_fit(key);
+        src = gg * N + key_idx(key);
+        const int qs = key_q(key);
+        sGQ[gg] = (qs < (int)kQSat) ? qs : __float_as_int(__ldcg(p.crows + (rbase + src) * rstride + D));
       }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float v2 = __shfl_xor_sync(0xffffffffu, bv, off);
-        const int i2 = __shfl_xor_sync(0xffffffffu, bi, off);
-        const int q2 = __shfl_xor_sync(0xffffffffu, bq, off);
-        const int s2 = __shfl_xor_sync(0xffffffffu, bs, off);
-        if (v2 < bv || (v2 == bv && i2 < bi)) {
-          bv = v2;
-          bi = i2;
-          bq = q2;
-          bs = s2;
-        }
-      }
-      if (lane == 0) {
-        if (bv < sGfit[gg]) {
-          sGfit[gg] = bv;
-          sGQ[gg] = bq;
-          sGsrc[gg] = bs;
-        } else {
-          sGsrc[gg] = -1;
-        }
-      }
+      sGsrc[gg] = src;
+    }
+    if (cr == 0) {
+      for (int gg = tid; gg < G; gg += nt) p.gword[wprev + gg] = kKeyEmpty;  // read by all during gk - 1
     }
     __syncthreads();
 
-    // Tbest (every thread, identical registers), then the rows that changed.
+    // Tbest (every thread, identical registers).
     float tb = INFINITY;
     int tg = -1;
     for (int gg = 0; gg < G; ++gg) {
@@ -347,21 +368,37 @@ __global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
         tg = gg;
       }
     }
-    int t_src = -2;  // -2 unchanged, -1 copy from the (unchanged) group row, >= 0 slot
+    int t_src = -2;  // -2 unchanged; -1 the (unchanged) row of group tg; >= 0 a candidate slot
     if (tg >= 0 && tb < Tfit) {
       Tfit = tb;
       TQ = sGQ[tg];
       t_src = sGsrc[tg];
     }
-    for (int it = tid; it < G * D; it += nt) {
-      const int src = sGsrc[it / D];
-      if (src >= 0) sGall[it] = __ldcg(p.crows + (base + src) * D + (it % D));
+    // This group's new Gbest row, and the persistent copies kept by the winners.
+    const int gsrc = sGsrc[g];
+    if (gsrc >= 0) {
+      for (int j = tid; j < D; j += nt) sG[j] = __ldcg(p.crows + (rbase + gsrc) * rstride + j);
     }
-    if (t_src >= 0) {
-      for (int j = tid; j < D; j += nt) sT[j] = __ldcg(p.crows + (base + t_src) * D + j);
-    } else if (t_src == -1) {
-      for (int j = tid; j < D; j += nt) sT[j] = sGall[tg * D + j];
+    // (a winning particle's P row is final for this iteration: the update below
+    // does not touch P)
+    const int own_lo = g * N + n0, own_hi = g * N + n0 + nl;
+    if (gsrc >= own_lo && gsrc < own_hi)
+      for (int j = tid; j < D; j += nt) gGb[g * D + j] = sP[(gsrc - own_lo) * D + j];
+    if (t_src >= own_lo && t_src < own_hi)
+      for (int j = tid; j < D; j += nt) gTb[j] = sP[(t_src - own_lo) * D + j];
+    if (t_src == -1 && tg == g && q == 0) {
+      for (int j = tid; j < D; j += nt) gTb[j] = sG[j];  // group g did not improve: sG is stable
     }
+    if (need_T) {
+      if (t_src >= 0) {
+        for (int j = tid; j < D; j += nt) sT[j] = __ldcg(p.crows + (rbase + t_src) * rstride + j);
+      } else if (t_src == -1) {
+        for (int j = tid; j < D; j += nt) sT[j] = __ldcg(gGb + tg * D + j);
+      }
+    }
+    last_t_src = t_src;
+    last_tg = tg;
+    last_rbase = rbase;
 
     // Auto Truncation (Sec. 3.3.4) and the iteration cap.
     if (tid == 0) {
@@ -397,15 +434,14 @@ __global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
 
     // Eq. TOF_omega, Eq. TOF_V (+ clip to V_range), Eq. TOF_X (+ clip to X_range).
     const float w = w_init - (w_init - w_end) / (float)p.max_iters * (float)k;
-    const float* sGown = sGall + g * D;
     for (int it = tid; it < nl * D; it += nt) {
       const int i = it / D;
       const int j = it - i * D;
       const float x = sX[it];
       float v = w * sV[it];
       v = fmaf(sR[i * 4 + 0], sP[it] - x, v);
-      v = fmaf(sR[i * 4 + 1], sGown[j] - x, v);
-      v = fmaf(sR[i * 4 + 2], sT[j] - x, v);
+      v = fmaf(sR[i * 4 + 1], sG[j] - x, v);
+      if (need_T) v = fmaf(sR[i * 4 + 2], sT[j] - x, v);
       const float ext = (j < T) ? p.W : p.H;
       const float vmax = vlim * ext;
       v = fminf(fmaxf(v, -vmax), vmax);
@@ -425,17 +461,21 @@ __global__ void __launch_bounds__(1024) swarm_kernel(const SwarmParams p) {
     gPfit[i] = sPfit[i];
     gPQ[i] = sPQ[i];
   }
-  if (q == 0) {
-    for (int j = tid; j < D; j += nt) p.Gb[((size_t)r * G + g) * D + j] = sGall[g * D + j];
-    if (tid == 0) {
-      p.Gfit[(size_t)r * G + g] = sGfit[g];
-      p.GQ[(size_t)r * G + g] = sGQ[g];
-    }
+  if (q == 0 && tid == 0) {
+    p.Gfit[(size_t)r * G + g] = sGfit[g];
+    p.GQ[(size_t)r * G + g] = sGQ[g];
   }
   if (cr == 0) {
-    for (int j = tid; j < D; j += nt) p.Tb[(size_t)r * D + j] = sT[j];
-    if (p.mode == kModePlan) {
-      for (int j = tid; j < D; j += nt) {
+    // The Tbest row: from this iteration's candidate slot if it changed in the
+    // last iteration, else from the persistent copies written in earlier ones.
+    const float* src = gTb;
+    if (last_t_src >= 0) src = p.crows + (last_rbase + last_t_src) * (D + 4);
+    else if (last_t_src == -1) src = gGb + last_tg * D;
+    for (int j = tid; j < D; j += nt) sT[j] = __ldcg(src + j);
+    __syncthreads();
+    for (int j = tid; j < D; j += nt) {
+      gTb[j] = sT[j];
+      if (p.mode == kModePlan) {
         p.res_wp[(size_t)r * D + j] = sT[j];
         p.prevT[(size_t)r * D + j] = sT[j];
       }
@@ -524,6 +564,7 @@ __global__ void __launch_bounds__(256) evaluate_kernel(const EvalParams p) {
 // Dynamic scene: c += v; a velocity component flips when the disk crosses the
 // border it is moving towards (Fig. PP caption).  Start/target: radius 0.
 // ---------------------------------------------------------------------------
+// (circle records keep 4 r^2 in .w; the radius itself does not change)
 __device__ __forceinline__ void move1(float& c, float& v, float r, float hi) {
   c += v;
   if (c - r < 0.0f && v < 0.0f) v = -v;
