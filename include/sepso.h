@@ -216,6 +216,71 @@ int sepso_hsef(sepso_handle h, const sepso_hsef_config* hc, float* d_history);
  * and its LFV (host outputs, sync). */
 int sepso_hsef_best(sepso_handle h, float* hyper_out, float* best_lfv);
 
+/* ---- many scenes of uneven size in one batch ------------------------------ */
+
+/* One independent DTPSO run per scene (Algorithm 1 with the path fitness of
+ * Sec. 3.3.2; no PI, no AT: each scene runs max_iters iterations).  Each launch
+ * advances every unfinished scene by one iteration; the whole run is one CUDA
+ * graph.  Scenes may differ in T, G, N, O, max_iters, alpha, beta and seed; the
+ * map extent is shared.  A scene's result does not depend on the rest of the
+ * batch (its random streams are keyed by its seed and run id). */
+typedef struct sepso_batch_ctx* sepso_batch_handle;
+
+typedef struct {
+  int32_t T, G, N, O;   /* waypoints (1..64), groups (1..32), particles per group, circles */
+  int32_t max_iters;    /* iterations of this scene (>= 1)                              */
+  float alpha;          /* Eq. penalty                                                  */
+  int32_t beta;         /* 1..8                                                         */
+  uint64_t seed;        /* Philox key                                                   */
+  uint32_t run_id;      /* Philox counter word 3                                        */
+} sepso_batch_scene;
+
+/* Launch shape: particles per work item (8..256), threads per CTA (64..512, a
+ * multiple of 32); lanes is 32 (a warp per particle; 0 is accepted); reserved
+ * must be 0.  The shape changes speed only, never results. */
+typedef struct {
+  int32_t tile, threads, lanes, reserved;
+} sepso_batch_shape;
+
+/* Bytes of device workspace for n scenes.  Errors: EINVAL. */
+int sepso_batch_workspace_size(const sepso_batch_scene* scenes, int32_t n, size_t* bytes);
+
+/* Lay out the batch in the caller's workspace (device, 256-byte aligned, owned by
+ * the caller), on the caller's stream; the map is [0, map_w] x [0, map_h].
+ * Errors: EINVAL, ENOSPC, ECUDA, ENOMEM, ERANGE. */
+int sepso_batch_create(const sepso_batch_scene* scenes, int32_t n, float map_w, float map_h,
+                       void* d_workspace, size_t bytes, void* stream, sepso_batch_handle* out);
+void sepso_batch_destroy(sepso_batch_handle h);
+
+/* Inputs (host, copied; sync): hyper = the scenes' G x 6 rows back to back (Table
+ * hyper8 layout), points = n x 4 (start x, y, target x, y), circles = the scenes'
+ * O x 3 rows back to back.  Errors: EINVAL. */
+int sepso_batch_set_inputs(sepso_batch_handle h, const float* hyper, const float* points,
+                           const float* circles);
+
+/* Set or read the launch shape (work_items: number of CTAs per launch). */
+int sepso_batch_set_shape(sepso_batch_handle h, const sepso_batch_shape* shape);
+int sepso_batch_get_shape(sepso_batch_handle h, sepso_batch_shape* shape, int32_t* work_items);
+
+/* Time the candidate shapes (tile 8..64, threads 128..512) over
+ * trial_launches iteration launches on the loaded batch and keep the fastest
+ * (sync).  best_ms: time of one iteration launch with it.  The batch state is
+ * overwritten (a later run starts from scratch). */
+int sepso_batch_autotune(sepso_batch_handle h, int32_t trial_launches, sepso_batch_shape* best,
+                         float* best_ms);
+
+/* Run every scene from initialisation to its max_iters (async).  use_graph != 0
+ * replays a CUDA graph of the run (captured at the first call after a shape
+ * change); 0 launches the kernels directly.  Errors: ESTATE, ECUDA. */
+int sepso_batch_run_async(sepso_batch_handle h, int32_t use_graph);
+
+/* Results (host, sync): waypoints = the scenes' 2T floats back to back, res = n
+ * records.  Either may be NULL. */
+int sepso_batch_read(sepso_batch_handle h, float* waypoints, sepso_result* res);
+
+int64_t sepso_batch_launch_count(sepso_batch_handle h);
+const char* sepso_batch_last_error(void);
+
 /* ---- planning without device allocation ---------------------------------- */
 
 /* One planning cycle, like a fresh handle's sepso_plan, for callers that cannot

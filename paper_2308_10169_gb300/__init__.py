@@ -8,7 +8,7 @@ The CUDA library is required: nothing here falls back to a CPU implementation.
 from .inputs import (AT_OFF, AT_STALL, AT_STD_WINDOW, TABLE_HYPER8, TABLE_HYPER8_PATH, Scene,
                      SepsoConfig, dynamic_workload, sample_hyper, static_workload)
 
-__all__ = ["Planner", "SepsoConfig", "Scene", "static_workload", "dynamic_workload",
+__all__ = ["Planner", "BatchPlanner", "SepsoConfig", "Scene", "static_workload", "dynamic_workload",
            "sample_hyper", "TABLE_HYPER8", "TABLE_HYPER8_PATH", "AT_OFF", "AT_STALL",
            "AT_STD_WINDOW"]
 
@@ -17,4 +17,7 @@ def __getattr__(name):
     if name == "Planner":
         from .planner import Planner
         return Planner
+    if name == "BatchPlanner":
+        from .planner import BatchPlanner
+        return BatchPlanner
     raise AttributeError(name)

@@ -52,6 +52,17 @@ class HsefConfig(ctypes.Structure):
                 ("hseed", ctypes.c_uint64)]
 
 
+class BatchScene(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("G", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("O", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("alpha", ctypes.c_float),
+                ("beta", ctypes.c_int32), ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32)]
+
+
+class BatchShape(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("threads", ctypes.c_int32), ("lanes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 def make_config(cfg) -> Config:
     return Config(T=cfg.T, G=cfg.G, N=cfg.N, max_obstacles=cfg.max_obstacles, map_w=cfg.map_w,
                   map_h=cfg.map_h, alpha=cfg.alpha, beta=cfg.beta, max_iters=cfg.max_iters,
@@ -92,6 +103,21 @@ SIGNATURES = {
     "sepso_launch_shape": (ctypes.c_int, [_vp] + [ctypes.POINTER(_i32)] * 4),
     "sepso_counters": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "sepso_launch_count": (_i64, [_vp]),
+    "sepso_batch_workspace_size": (ctypes.c_int, [ctypes.POINTER(BatchScene), _i32,
+                                                   ctypes.POINTER(_sz)]),
+    "sepso_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchScene), _i32, ctypes.c_float,
+                                          ctypes.c_float, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "sepso_batch_destroy": (None, [_vp]),
+    "sepso_batch_set_inputs": (ctypes.c_int, [_vp, _fp, _fp, _fp]),
+    "sepso_batch_set_shape": (ctypes.c_int, [_vp, ctypes.POINTER(BatchShape)]),
+    "sepso_batch_get_shape": (ctypes.c_int, [_vp, ctypes.POINTER(BatchShape),
+                                             ctypes.POINTER(_i32)]),
+    "sepso_batch_autotune": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(BatchShape),
+                                            ctypes.POINTER(ctypes.c_float)]),
+    "sepso_batch_run_async": (ctypes.c_int, [_vp, _i32]),
+    "sepso_batch_read": (ctypes.c_int, [_vp, _fp, ctypes.POINTER(Result)]),
+    "sepso_batch_launch_count": (_i64, [_vp]),
+    "sepso_batch_last_error": (ctypes.c_char_p, []),
     "sepso_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sepso_last_error": (ctypes.c_char_p, []),
 }
@@ -120,6 +146,13 @@ def lib(rebuild_if_stale: bool = True):
 def check(code: int):
     if code != SEPSO_OK:
         msg = lib().sepso_last_error()
+        raise SepsoError(code, msg.decode() if msg else "")
+    return code
+
+
+def check_batch(code: int):
+    if code != SEPSO_OK:
+        msg = lib().sepso_batch_last_error()
         raise SepsoError(code, msg.decode() if msg else "")
     return code
 

@@ -269,6 +269,60 @@ __device__ __forceinline__ float seg_hits(const SegFrame& f, const float4* __res
   return hits;
 }
 
+// Length and Q of one particle by a lane group of lp lanes (a power of two <= 32,
+// aligned within the warp): lanes take (segment, circle chunk) items of the row x
+// (D = 2T floats in shared memory), then the group sums both with a fixed
+// shuffle tree, so every lane of the group ends with the same deterministic
+// values.  All 32 lanes of the warp must call this (live = false for lanes
+// without a particle).
+__device__ __forceinline__ void group_fitness(const float* x, bool live, int lp, int T, int split, int O,
+                                              float sx, float sy, float tx, float ty, const float4* circ,
+                                              float* len_out, int* q_out) {
+  const int lsub = (threadIdx.x & 31) & (lp - 1);
+  const int items = (T + 1) * split;
+  const int chunk = (O + split - 1) / split;
+  float len = 0.0f, hits = 0.0f;
+  if (live) {
+    // segment fastest: neighbouring lanes read the same circle (broadcast)
+    for (int it = lsub; it < items; it += lp) {
+      const int sg = it % (T + 1);
+      const int c = it / (T + 1);
+      const float ax = (sg == 0) ? sx : x[sg - 1];
+      const float ay = (sg == 0) ? sy : x[T + sg - 1];
+      const float bx = (sg == T) ? tx : x[sg];
+      const float by = (sg == T) ? ty : x[T + sg];
+      float l;
+      const SegFrame f = seg_frame(ax, ay, bx, by, &l);
+      if (c == 0) len += l;
+      hits += seg_hits(f, circ, c * chunk, min(O, c * chunk + chunk));
+    }
+  }
+  for (int off = lp >> 1; off > 0; off >>= 1) {
+    len += __shfl_xor_sync(0xffffffffu, len, off);
+    hits += __shfl_xor_sync(0xffffffffu, hits, off);
+  }
+  *len_out = len;
+  *q_out = (int)hits;
+}
+
+// Circle chunks per segment for a warp (32 lanes) evaluating one particle of T
+// waypoints against O circles: the split (1..8) that minimises the per-lane work
+// rounds * (chunk + setup), so that the warp's rounds are nearly full.
+__host__ __device__ inline int warp_split(int T, int O) {
+  int best = 1;
+  long long best_cost = -1;
+  for (int sp = 1; sp <= 8; ++sp) {
+    const long long rounds = ((long long)(T + 1) * sp + 31) / 32;
+    const long long chunk = (O + sp - 1) / sp;
+    const long long cost = rounds * (chunk + 4);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = sp;
+    }
+  }
+  return best;
+}
+
 __device__ __forceinline__ float powi(float q, int beta) {
   float r = 1.0f;
   for (int i = 0; i < beta; ++i) r *= q;

@@ -245,36 +245,16 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
       const int lp = p.lp;
       const int ppw = 32 / lp;
       const int lsub = lane & (lp - 1);
-      const int items = nseg * p.split;
-      const int chunk = (p.O + p.split - 1) / p.split;
       for (int i0 = warp * ppw; i0 < nl; i0 += nwarps * ppw) {
         const int i = i0 + lane / lp;
         const bool live = i < nl;
-        float len = 0.0f, hits = 0.0f;
-        if (live) {
-          const float* x = sX + i * D;
-          for (int it = lsub; it < items; it += lp) {
-            const int c = it % p.split;
-            const int sg = it / p.split;
-            const float ax = (sg == 0) ? sx : x[sg - 1];
-            const float ay = (sg == 0) ? sy : x[T + sg - 1];
-            const float bx = (sg == T) ? tx : x[sg];
-            const float by = (sg == T) ? ty : x[T + sg];
-            float l;
-            const SegFrame f = seg_frame(ax, ay, bx, by, &l);
-            if (c == 0) len += l;
-            hits += seg_hits(f, sC, c * chunk, min(p.O, c * chunk + chunk));
-          }
-        }
-        for (int off = lp >> 1; off > 0; off >>= 1) {
-          len += __shfl_xor_sync(0xffffffffu, len, off);
-          hits += __shfl_xor_sync(0xffffffffu, hits, off);
-        }
+        float len;
+        int qq;
+        group_fitness(sX + (live ? i : 0) * D, live, lp, T, p.split, p.O, sx, sy, tx, ty, sC, &len, &qq);
         int imp = 0, pub = 0;
         float pf = INFINITY;
         int pq = 0;
         if (live && lsub == 0) {
-          const int qq = (int)hits;
           const float F = len + p.alpha * powi((float)qq, p.beta);
           pf = sPfit[i];
           pq = sPQ[i];

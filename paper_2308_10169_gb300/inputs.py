@@ -217,3 +217,49 @@ def random_state(seed: int, cfg: SepsoConfig) -> dict:
     }
     st["Tfit"] = np.array([st["Gfit"].min() - 1.0], np.float32)
     return st
+
+
+@dataclass
+class BatchSceneSpec:
+    """One scene of a batch (mirrors ``sepso_batch_scene`` in include/sepso.h)."""
+    T: int
+    G: int
+    N: int
+    O: int
+    max_iters: int = 200
+    alpha: float = 30.0
+    beta: int = 4
+    seed: int = 0
+    run_id: int = 0
+
+    @property
+    def D(self) -> int:
+        return 2 * self.T
+
+    def config(self, map_w: float = 400.0, map_h: float = 400.0) -> SepsoConfig:
+        """The equivalent single-scene configuration (no PI, no AT)."""
+        return SepsoConfig(T=self.T, G=self.G, N=self.N, max_obstacles=max(self.O, 1),
+                           map_w=map_w, map_h=map_h, alpha=self.alpha, beta=self.beta,
+                           max_iters=self.max_iters, at_mode=AT_OFF, use_pi=False,
+                           seed=self.seed, run_id=self.run_id)
+
+
+def batch_workload(seed: int = 0, n: int = 4096, T_range=(8, 64), O_range=(16, 1024),
+                   N_range=(32, 512), G: int = 8, r_range=(5.0, 30.0), max_iters: int = 200):
+    """The batched workload: n independent scenes with T ~ U{T_range}, O ~ U{O_range},
+    N per group ~ U{N_range}, G groups, radii U[r_range], centres uniform over the
+    400x400 map, start (20,20), target (380,380), per-group w ~ U[0.4,0.9],
+    C1, C2 ~ U[1,2.5], C3 = 0, V_limit 0.05, alpha 30, beta 4.  Philox key = seed,
+    run id = scene index.  Returns (specs, hyper list, points (n,4), circle list)."""
+    rng = np.random.default_rng(5000 + seed)
+    specs, hyper, circles = [], [], []
+    points = np.zeros((n, 4), np.float32)
+    for s in range(n):
+        T = int(rng.integers(T_range[0], T_range[1] + 1))
+        O = int(rng.integers(O_range[0], O_range[1] + 1))
+        N = int(rng.integers(N_range[0], N_range[1] + 1))
+        specs.append(BatchSceneSpec(T=T, G=G, N=N, O=O, max_iters=max_iters, seed=seed, run_id=s))
+        hyper.append(sample_hyper(int(rng.integers(1 << 30)), G))
+        circles.append(random_circles(rng, O, lo=0.0, hi=400.0, r_lo=r_range[0], r_hi=r_range[1]))
+        points[s] = (20.0, 20.0, 380.0, 380.0)
+    return specs, hyper, points, circles

@@ -211,3 +211,92 @@ class Planner:
 
     def launch_count(self) -> int:
         return int(self.lib.sepso_launch_count(self._h))
+
+
+class BatchPlanner:
+    """Many independent scenes of uneven size planned together (sepso_batch_*)."""
+
+    def __init__(self, specs, map_w: float = 400.0, map_h: float = 400.0, device=None,
+                 stream: torch.cuda.Stream | None = None):
+        from ._native import BatchScene, check_batch
+        self.lib = _native.lib()
+        self._check = check_batch
+        self.specs = list(specs)
+        self.n = len(self.specs)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        arr = (BatchScene * self.n)()
+        for i, sp in enumerate(self.specs):
+            arr[i] = BatchScene(T=sp.T, G=sp.G, N=sp.N, O=sp.O, max_iters=sp.max_iters,
+                                alpha=sp.alpha, beta=sp.beta, seed=sp.seed, run_id=sp.run_id)
+        self._arr = arr
+        size = ctypes.c_size_t()
+        check_batch(self.lib.sepso_batch_workspace_size(arr, self.n, ctypes.byref(size)))
+        self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check_batch(self.lib.sepso_batch_create(arr, self.n, map_w, map_h,
+                                                    ctypes.c_void_p(self.workspace.data_ptr()),
+                                                    size.value, ctypes.c_void_p(self.stream.cuda_stream),
+                                                    ctypes.byref(self._h)))
+        self.D = [sp.D for sp in self.specs]
+
+    def close(self):
+        if self._h:
+            self.lib.sepso_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_inputs(self, hyper, points, circles):
+        h = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).reshape(-1) for x in hyper]))
+        pts = np.ascontiguousarray(np.asarray(points, np.float32).reshape(self.n, 4))
+        cl = [np.asarray(c, np.float32).reshape(-1) for c in circles]
+        c = np.ascontiguousarray(np.concatenate(cl)) if sum(x.size for x in cl) else np.zeros(3, np.float32)
+        self._check(self.lib.sepso_batch_set_inputs(self._h, fptr(h), fptr(pts), fptr(c)))
+
+    def set_shape(self, tile: int, threads: int):
+        from ._native import BatchShape
+        sh = BatchShape(tile=tile, threads=threads, lanes=32, reserved=0)
+        self._check(self.lib.sepso_batch_set_shape(self._h, ctypes.byref(sh)))
+
+    def shape(self) -> dict:
+        from ._native import BatchShape
+        sh, n = BatchShape(), ctypes.c_int32()
+        self._check(self.lib.sepso_batch_get_shape(self._h, ctypes.byref(sh), ctypes.byref(n)))
+        return {"tile": sh.tile, "threads": sh.threads, "lanes": sh.lanes, "work_items": n.value}
+
+    def autotune(self, trial_launches: int = 3):
+        from ._native import BatchShape
+        sh, ms = BatchShape(), ctypes.c_float()
+        self._check(self.lib.sepso_batch_autotune(self._h, trial_launches, ctypes.byref(sh),
+                                                  ctypes.byref(ms)))
+        return {"tile": sh.tile, "threads": sh.threads, "lanes": sh.lanes}, float(ms.value)
+
+    def run_async(self, use_graph: bool = True):
+        self._check(self.lib.sepso_batch_run_async(self._h, int(use_graph)))
+
+    def read(self):
+        total = sum(self.D)
+        wp = np.zeros(max(total, 1), np.float32)
+        res = (Result * self.n)()
+        self._check(self.lib.sepso_batch_read(self._h, fptr(wp), res))
+        out, off = [], 0
+        for i in range(self.n):
+            d = self.D[i]
+            out.append({"waypoints": wp[off:off + d].copy(), "cost": res[i].cost,
+                        "length": res[i].length, "Q": res[i].Q, "iters": res[i].iters,
+                        "status": res[i].status})
+            off += d
+        return out
+
+    def run(self, use_graph: bool = True):
+        self.run_async(use_graph)
+        return self.read()
+
+    def launch_count(self) -> int:
+        return int(self.lib.sepso_batch_launch_count(self._h))
