@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=0, help="0 = same as --steps")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-scenes", type=int, default=4096,
+                    help="scenes of the batched section (0 = skip it)")
+    ap.add_argument("--batch-iters", type=int, default=200)
     return ap.parse_args()
 
 
@@ -358,6 +361,45 @@ def run_e2e(torch, pl_dev, cfg, scene, hyper, dev, K, W):
             "path": "sepso_set_scene (pinned staging, async DMA) + sepso_plan (D2H waypoints, sync)"}
 
 
+def run_batch(n: int, iters: int):
+    """The batched workload: n uneven scenes x iters iterations in one CUDA graph."""
+    import torch
+
+    from paper_2308_10169_gb300 import BatchPlanner
+    from paper_2308_10169_gb300.inputs import batch_workload
+    specs, hyper, points, circles = batch_workload(seed=0, n=n, max_iters=iters)
+    bp = BatchPlanner(specs)
+    bp.set_inputs(hyper, points, circles)
+    shape, tune_ms = bp.autotune(trial_launches=3)
+    bp.run_async(True)              # warm-up run (captures the graph)
+    torch.cuda.synchronize()
+    l0 = bp.launch_count()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    bp.run_async(True)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e)
+    res = bp.read()
+    pairs = sum(sp.G * sp.N * (sp.T + 1) * sp.O for sp in specs) * iters
+    segs = sum(sp.G * sp.N * (sp.T + 1) for sp in specs) * iters
+    flops = pairs * FLOPS_PER_PAIR + segs * FLOPS_PER_SEGMENT
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"workload": f"{n} scenes, T~U{{8..64}}, O~U{{16..1024}} r~U[5,30], N/group~U{{32..512}}, "
+                        f"G=8, 400x400, {iters} iterations each, one CUDA graph",
+            "plans_per_s": n / (ms / 1e3), "ms": ms,
+            "particle_evals_per_s": sum(sp.G * sp.N for sp in specs) * iters / (ms / 1e3),
+            "pair_tests_per_s": pairs / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                         "kernel": "batch_kernel"},
+            "shape": bp.shape(), "autotune_ms_per_launch": tune_ms,
+            "gpu_launches": bp.launch_count() - l0,
+            "median_cost": float(np.median([r["cost"] for r in res])),
+            "l2": "inputs larger than L2 (13 GB of swarm state)"}
+
+
 def cpu_baseline(seconds: float):
     cfg, times, iters, costs = oracle_cycles(seconds, 10_000)
     n, total = len(times), sum(times)
@@ -381,6 +423,8 @@ def main():
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if world == 1 and args.batch_scenes > 0:
+            line["batch"] = run_batch(args.batch_scenes, args.batch_iters)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

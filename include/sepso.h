@@ -281,6 +281,84 @@ int sepso_batch_read(sepso_batch_handle h, float* waypoints, sepso_result* res);
 int64_t sepso_batch_launch_count(sepso_batch_handle h);
 const char* sepso_batch_last_error(void);
 
+/* ---- serving: continuous batching of planning requests -------------------- */
+
+/* Agents submit planning requests (their current scene).  Up to S requests are
+ * on the device at once, each in a slot; every tick advances every occupied slot
+ * by one iteration of Algorithm 1 (one launch).  A request starts with Priori
+ * Initialization (Sec. 3.3.3) around its agent's previous best path, kept on the
+ * device, and ends by Auto Truncation with the stall counter (Sec. 3.3.4) or at
+ * max_iters; its slot then takes the next queued request at the following tick.
+ * S is max_slots, lowered to fit mem_budget (admission by device memory).  An
+ * agent has at most one request on the device; its later requests wait in the
+ * queue.  Random streams are keyed by (seed, agent, the agent's request count),
+ * so a result does not depend on the other requests in flight. */
+typedef struct sepso_server_ctx* sepso_server_handle;
+
+typedef struct {
+  int32_t n_agents;      /* rows of the warm-start table                          */
+  int32_t max_slots;     /* requests on the device at most                        */
+  size_t mem_budget;     /* workspace bytes the slots may use (0: no bound)       */
+  int32_t G, N;          /* swarm of every request                                */
+  int32_t Tmax, Omax;    /* largest request: waypoints, circles                   */
+  int32_t max_iters;     /* cap per request                                       */
+  int32_t stall_iters;   /* AT stall limit (0: run to the cap)                    */
+  float stall_tol;
+  float alpha;           /* Eq. penalty                                           */
+  int32_t beta;
+  float pi_gamma, pi_halfwidth;
+  float map_w, map_h;
+  uint64_t seed;         /* Philox key                                            */
+  int32_t tile, threads; /* launch shape (0: 32 particles, 128 threads)           */
+} sepso_server_config;
+
+/* A finished request. */
+typedef struct {
+  int64_t tag;           /* the caller's tag from sepso_server_submit             */
+  int32_t agent, T;
+  sepso_result res;
+  double arrival_s;      /* server clock at arrival                               */
+  double finish_s;       /* server clock when its completion was collected        */
+} sepso_server_done;
+
+/* Bytes of workspace and the number of slots S a config gets.  Errors: EINVAL. */
+int sepso_server_workspace_size(const sepso_server_config* cfg, size_t* bytes, int32_t* slots);
+/* Create on the caller's workspace and stream (as sepso_create).  Allocates pinned
+ * host staging buffers.  Errors: EINVAL, ENOSPC, ERANGE, ECUDA, ENOMEM. */
+int sepso_server_create(const sepso_server_config* cfg, void* d_workspace, size_t bytes, void* stream,
+                        sepso_server_handle* out);
+void sepso_server_destroy(sepso_server_handle h);
+/* Hyper-parameters (host G x 6) of one agent, or of all when agent < 0 (sync). */
+int sepso_server_set_hyper(sepso_server_handle h, int32_t agent, const float* hyper);
+/* Queue a request (host inputs, copied): T waypoints (<= Tmax), start[2],
+ * target[2], circles O x 3 (O <= Omax).  Errors: EINVAL. */
+int sepso_server_submit(sepso_server_handle h, int32_t agent, int32_t T, const float* start,
+                        const float* target, const float* circles, int32_t O, int64_t tag);
+/* As sepso_server_submit for a request that arrives at arrival_s on the server
+ * clock (seconds); it is admitted only once the clock has passed it.  Requests
+ * must be submitted in arrival order.  Errors: EINVAL. */
+int sepso_server_submit_at(sepso_server_handle h, int32_t agent, int32_t T, const float* start,
+                           const float* target, const float* circles, int32_t O, int64_t tag,
+                           double arrival_s);
+/* The server clock (s since creation or the last restart); restart != 0 resets it. */
+double sepso_server_clock(sepso_server_handle h, int32_t restart);
+/* Tick natively until every submitted request (including future arrivals) has
+ * finished, waiting for arrivals when the device is idle (at most max_ticks). */
+int sepso_server_run(sepso_server_handle h, int64_t max_ticks);
+/* One tick: launch one iteration of every occupied slot, collect the requests
+ * that finished in the previous tick, admit queued requests into free slots.
+ * active / queued (may be NULL): slots occupied and requests waiting after it. */
+int sepso_server_tick(sepso_server_handle h, int32_t* active, int32_t* queued);
+/* Move up to max_n finished requests to out (and their 2 * Tmax waypoint floats,
+ * padded, to waypoints; either may be NULL); n = how many. */
+int sepso_server_poll(sepso_server_handle h, sepso_server_done* out, float* waypoints, int32_t max_n,
+                      int32_t* n);
+/* Tick until nothing is queued or on the device (at most max_ticks; ETIMEOUT). */
+int sepso_server_drain(sepso_server_handle h, int64_t max_ticks);
+int sepso_server_stats(sepso_server_handle h, int32_t* slots, int64_t* admitted, int64_t* completed,
+                       int64_t* ticks, int64_t* launches);
+const char* sepso_server_last_error(void);
+
 /* ---- planning without device allocation ---------------------------------- */
 
 /* One planning cycle, like a fresh handle's sepso_plan, for callers that cannot

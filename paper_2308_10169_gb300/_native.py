@@ -63,6 +63,21 @@ class BatchShape(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("n_agents", ctypes.c_int32), ("max_slots", ctypes.c_int32),
+                ("mem_budget", ctypes.c_size_t), ("G", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("Tmax", ctypes.c_int32), ("Omax", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("stall_iters", ctypes.c_int32), ("stall_tol", ctypes.c_float),
+                ("alpha", ctypes.c_float), ("beta", ctypes.c_int32), ("pi_gamma", ctypes.c_float),
+                ("pi_halfwidth", ctypes.c_float), ("map_w", ctypes.c_float), ("map_h", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("tile", ctypes.c_int32), ("threads", ctypes.c_int32)]
+
+
+class ServerDone(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_int64), ("agent", ctypes.c_int32), ("T", ctypes.c_int32),
+                ("res", Result), ("arrival_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
+
+
 def make_config(cfg) -> Config:
     return Config(T=cfg.T, G=cfg.G, N=cfg.N, max_obstacles=cfg.max_obstacles, map_w=cfg.map_w,
                   map_h=cfg.map_h, alpha=cfg.alpha, beta=cfg.beta, max_iters=cfg.max_iters,
@@ -118,6 +133,23 @@ SIGNATURES = {
     "sepso_batch_read": (ctypes.c_int, [_vp, _fp, ctypes.POINTER(Result)]),
     "sepso_batch_launch_count": (_i64, [_vp]),
     "sepso_batch_last_error": (ctypes.c_char_p, []),
+    "sepso_server_workspace_size": (ctypes.c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_sz),
+                                                    ctypes.POINTER(_i32)]),
+    "sepso_server_create": (ctypes.c_int, [ctypes.POINTER(ServerConfig), _vp, _sz, _vp,
+                                           ctypes.POINTER(_vp)]),
+    "sepso_server_destroy": (None, [_vp]),
+    "sepso_server_set_hyper": (ctypes.c_int, [_vp, _i32, _fp]),
+    "sepso_server_submit": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp, _fp, _i32, _i64]),
+    "sepso_server_submit_at": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp, _fp, _i32, _i64,
+                                              ctypes.c_double]),
+    "sepso_server_clock": (ctypes.c_double, [_vp, _i32]),
+    "sepso_server_run": (ctypes.c_int, [_vp, _i64]),
+    "sepso_server_tick": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "sepso_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(ServerDone), _fp, _i32,
+                                         ctypes.POINTER(_i32)]),
+    "sepso_server_drain": (ctypes.c_int, [_vp, _i64]),
+    "sepso_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)] + [ctypes.POINTER(_i64)] * 4),
+    "sepso_server_last_error": (ctypes.c_char_p, []),
     "sepso_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sepso_last_error": (ctypes.c_char_p, []),
 }
@@ -146,6 +178,13 @@ def lib(rebuild_if_stale: bool = True):
 def check(code: int):
     if code != SEPSO_OK:
         msg = lib().sepso_last_error()
+        raise SepsoError(code, msg.decode() if msg else "")
+    return code
+
+
+def check_server(code: int):
+    if code != SEPSO_OK:
+        msg = lib().sepso_server_last_error()
         raise SepsoError(code, msg.decode() if msg else "")
     return code
 

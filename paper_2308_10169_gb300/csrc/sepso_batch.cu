@@ -29,71 +29,11 @@
 #include <string>
 #include <vector>
 
+#include "sepso_batch.cuh"
 #include "sepso_device.cuh"
 #include "sepso_internal.h"
 
 namespace sepso {
-
-struct BatchScene {
-  int T, D, G, N, M, O, max_iters, beta;
-  float alpha;
-  uint32_t key0, key1, run_id;
-  long long xo;   // float offset of the scene's rows in X, V, P (M x D)
-  long long mo;   // offset in Pfit, PQ (M)
-  long long so;   // float offset of the candidate slots (2 x M x (D + 4))
-  long long go;   // float offset of the Gbest rows (G x D)
-  long long to;   // float offset of the Tbest row and the result row (D)
-  long long co;   // float4 offset of the circles (O)
-  long long ho;   // float offset of the hyper-parameters (G x 6)
-  long long wo;   // offset of the group words (3 x G)
-  long long gso;  // offset of the group scalars Gfit / GQ (2 x G, by parity)
-};
-
-struct BatchParams {
-  const BatchScene* sc;
-  const int4* tiles;   // (scene, group, first particle, particles)
-  int ntiles, nscenes;
-  float W, H;
-  int Omax, Dmax, Gmax, tile;
-  float *X, *V, *P, *Pfit;
-  int32_t* PQ;
-  float* slots;
-  float *Gb, *Tb;
-  const float4* circ;
-  const float* hyper;
-  const float* pts;    // 4 per scene: start, target
-  unsigned long long* words;
-  float* Gfit2;
-  int32_t* GQ2;
-  float* Tfit2;        // 2 per scene
-  int32_t* TQ2;
-  float* res_wp;
-  sepso_result* res;
-  int* status;
-};
-
-struct BatchSmem {
-  int circ, X, V, P, R, G, T, Pfit, PQ, Gfit, GQ, Gsrc, total;
-  __host__ __device__ static BatchSmem make(int Omax, int tile, int Dmax, int Gmax) {
-    BatchSmem s;
-    int off = 0;
-    auto al = [](int v) { return (v + 15) / 16 * 16; };
-    s.circ = off; off = al(off + (Omax > 0 ? Omax : 1) * 16);
-    s.X = off; off = al(off + tile * Dmax * 4);
-    s.V = off; off = al(off + tile * Dmax * 4);
-    s.P = off; off = al(off + tile * Dmax * 4);
-    s.R = off; off = al(off + tile * 16);
-    s.G = off; off = al(off + Dmax * 4);
-    s.T = off; off = al(off + Dmax * 4);
-    s.Pfit = off; off = al(off + tile * 4);
-    s.PQ = off; off = al(off + tile * 4);
-    s.Gfit = off; off = al(off + Gmax * 4);
-    s.GQ = off; off = al(off + Gmax * 4);
-    s.Gsrc = off; off = al(off + Gmax * 4);
-    s.total = off;
-    return s;
-  }
-};
 
 // Bests of every scene empty, group words empty.
 __global__ void batch_reset_kernel(const BatchParams p) {
@@ -109,6 +49,11 @@ __global__ void batch_reset_kernel(const BatchParams p) {
     p.Tfit2[2 * s + 1] = INFINITY;
     p.TQ2[2 * s] = 0;
     p.TQ2[2 * s + 1] = 0;
+    if (p.stall2 != nullptr) {
+      p.stall2[2 * s] = p.stall2[2 * s + 1] = 0;
+      p.plv2[2 * s] = p.plv2[2 * s + 1] = INFINITY;
+      p.done[s] = 0;
+    }
   }
 }
 
@@ -118,7 +63,9 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
   const int4 tl = p.tiles[blockIdx.x];
   const int s = tl.x, g = tl.y, n0 = tl.z, nl = tl.w;
   const BatchScene S = p.sc[s];
-  if (j > S.max_iters + 1) return;  // this scene has finished
+  const int jl = j - S.j0;  // this launch is the scene's jl-th
+  if (jl < 1 || jl > S.max_iters + 1) return;  // not started, or finished
+  if (p.done != nullptr && p.done[s]) return;   // truncated earlier
 
   const BatchSmem L = BatchSmem::make(p.Omax, p.tile, p.Dmax, p.Gmax);
   float4* sC = reinterpret_cast<float4*>(smem + L.circ);
@@ -137,7 +84,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   const int T = S.T, D = S.D, G = S.G, N = S.N, M = S.M;
-  const bool fit_phase = j <= S.max_iters;
+  const bool fit_phase = jl <= S.max_iters;
   const bool first = (g == 0 && n0 == 0);
 
   if (tid == 0) mbar_init(&s_mbar, 1);
@@ -159,20 +106,26 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
   float* gTb = p.Tb + S.to;
   const uint32_t run = S.run_id;
 
-  if (j == 1) {
-    // Initialisation (Algorithm 1; no previous path, so no Priori Initialization).
+  const uint32_t cyc = S.cycle;
+  if (jl == 1) {
+    // Initialisation (Algorithm 1), with Priori Initialization (Sec. 3.3.3) around
+    // the agent's previous best path when it has one.
+    const int n_pi = (S.has_prev && p.agent_prevT != nullptr && S.agent >= 0) ? S.n_pi : 0;
+    const float* prevT = (n_pi > 0) ? p.agent_prevT + (long long)S.agent * p.Dmax : nullptr;
     const int nch = (D + 3) >> 2;
     for (int it = tid; it < nl * nch; it += nt) {
       const int i = it / nch, ch = it - i * nch;
       const uint32_t pid = (uint32_t)(g * N + n0 + i);
-      const uint4 ux = draw(S.key0, S.key1, (uint32_t)ch, pid, kStreamInitX, 0u, run);
-      const uint4 uv = draw(S.key0, S.key1, (uint32_t)ch, pid, kStreamInitV, 0u, run);
+      const bool pi = n0 + i < n_pi;
+      const uint4 ux = draw(S.key0, S.key1, (uint32_t)ch, pid, pi ? kStreamPI : kStreamInitX, cyc, run);
+      const uint4 uv = draw(S.key0, S.key1, (uint32_t)ch, pid, kStreamInitV, cyc, run);
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int jj = ch * 4 + l;
         if (jj < D) {
           const float ext = (jj < T) ? p.W : p.H;
-          const float x = lane_of(ux, l) * ext;
+          const float x = pi ? fminf(fmaxf(prevT[jj] + (2.0f * lane_of(ux, l) - 1.0f) * S.pi_h, 0.0f), ext)
+                             : lane_of(ux, l) * ext;
           sX[i * D + jj] = x;
           sP[i * D + jj] = x;
           sV[i * D + jj] = (2.0f * lane_of(uv, l) - 1.0f) * (vlim * ext);
@@ -187,7 +140,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
     __syncthreads();
   } else {
     // Bests of iteration k = j - 1 (every item of the scene computes the same).
-    const int k = j - 1;
+    const int k = jl - 1;
     const float* oGfit = p.Gfit2 + S.gso + ((k - 1) & 1) * G;
     const int32_t* oGQ = p.GQ2 + S.gso + ((k - 1) & 1) * G;
     const unsigned long long* wk = p.words + S.wo + (k % 3) * G;
@@ -226,7 +179,19 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
     }
     const float* trow = (t_src >= 0) ? p.slots + sk + (long long)t_src * (D + 4)
                                      : (t_src == -1 ? gGb + tg * D : gTb);
+    // Truncation: the cap, or Auto Truncation by stall counter (Sec. 3.3.4).
+    bool stop = (k == S.max_iters);
+    int stall = 0;
+    if (S.at_stall > 0) {
+      const float plv = p.plv2[2 * s + ((k - 1) & 1)];
+      stall = (Tfit < plv - S.stall_tol) ? 0 : p.stall2[2 * s + ((k - 1) & 1)] + 1;
+      if (stall >= S.at_stall && TQ == 0) stop = true;
+    }
     if (first) {
+      if (S.at_stall > 0 && tid == 0) {
+        p.stall2[2 * s + (k & 1)] = stall;
+        p.plv2[2 * s + (k & 1)] = Tfit;
+      }
       // Store the new scalars (other parity) and rows for the next launch; clear
       // the words the launch after next will fill.
       for (int gg = tid; gg < G; gg += nt) {
@@ -245,13 +210,17 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
       if (t_src != -2)
         for (int jj = tid; jj < D; jj += nt) gTb[jj] = trow[jj];
     }
-    if (k == S.max_iters) {
-      // Algorithm 1 returns F(Tbest): write the scene's result.
+    if (stop) {
+      // Algorithm 1 returns F(Tbest): write the scene's result (and, for a
+      // request, the agent's warm-start path).
       if (first) {
+        float* warm = (S.agent >= 0 && p.agent_prevT != nullptr) ? p.agent_prevT + (long long)S.agent * p.Dmax
+                                                                 : nullptr;
         for (int jj = tid; jj < D; jj += nt) {
           const float v = trow[jj];
           p.res_wp[S.to + jj] = v;
           sT[jj] = v;
+          if (warm) warm[jj] = v;
         }
         __syncthreads();
         if (tid == 0) {
@@ -270,6 +239,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
           r->Q = TQ;
           r->iters = k;
           r->status = SEPSO_OK;
+          if (p.done != nullptr) p.done[s] = 1;
         }
       }
       return;
@@ -290,7 +260,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
     for (int i = tid; i < nl; i += nt) {
       sPfit[i] = gPfit[i];
       sPQ[i] = gPQ[i];
-      const uint4 o = draw(S.key0, S.key1, (uint32_t)k, (uint32_t)(g * N + n0 + i), kStreamVel, 0u, run);
+      const uint4 o = draw(S.key0, S.key1, (uint32_t)k, (uint32_t)(g * N + n0 + i), kStreamVel, cyc, run);
       sR[i * 4 + 0] = c1 * u01(o.x);
       sR[i * 4 + 1] = c2 * u01(o.y);
       sR[i * 4 + 2] = c3 * u01(o.z);
@@ -328,7 +298,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
     const int ppw = 1;
     const int lsub = lane;
     const int split = warp_split(T, S.O);
-    const long long sj = S.so + (long long)(j & 1) * M * (D + 4);
+    const long long sj = S.so + (long long)(jl & 1) * M * (D + 4);
     for (int i0 = warp * ppw; i0 < nl; i0 += nwarps * ppw) {
       const int i = i0 + lane / lp;
       const bool live = i < nl;
@@ -363,7 +333,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
         }
         if (pub && lsub == 0) {
           slot[D] = __int_as_float(pq);
-          red_min_u64(p.words + S.wo + (j % 3) * G + g, best_key(pf, (uint32_t)(n0 + i), (uint32_t)pq));
+          red_min_u64(p.words + S.wo + (jl % 3) * G + g, best_key(pf, (uint32_t)(n0 + i), (uint32_t)pq));
         }
       }
     }
@@ -378,6 +348,29 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
     gPfit[i] = sPfit[i];
     gPQ[i] = sPQ[i];
   }
+}
+
+cudaError_t batch_configure(int* smem_optin_out) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, batch_kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess && smem_optin_out) *smem_optin_out = optin - (int)fa.sharedSizeBytes;
+  return e;
+}
+
+cudaError_t launch_batch_reset(const BatchParams& p, cudaStream_t s) {
+  batch_reset_kernel<<<std::max(1, std::min(1024, (p.nscenes + 255) / 256)), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_iter(const BatchParams& p, int j, int ntiles, int threads, size_t smem, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  batch_kernel<<<ntiles, threads, smem, s>>>(p, j);
+  return cudaGetLastError();
 }
 
 }  // namespace sepso
@@ -537,6 +530,10 @@ BatchParams batch_params(const sepso_batch_ctx* h) {
   p.res_wp = h->at<float>(h->L.res_wp);
   p.res = h->at<sepso_result>(h->L.res);
   p.status = h->at<int>(h->L.status);
+  p.stall2 = nullptr;
+  p.plv2 = nullptr;
+  p.done = nullptr;
+  p.agent_prevT = nullptr;
   return p;
 }
 
@@ -676,6 +673,14 @@ int sepso_batch_create(const sepso_batch_scene* scenes, int32_t n, float map_w, 
     d.ho = ho; ho += 6LL * d.G;
     d.wo = wo; wo += 3LL * d.G;
     d.gso = gso; gso += 2LL * d.G;
+    d.j0 = 0;
+    d.at_stall = 0;
+    d.stall_tol = 0.0f;
+    d.n_pi = 0;
+    d.pi_h = 0.0f;
+    d.cycle = 0;
+    d.agent = -1;
+    d.has_prev = 0;
     h->Omax = std::max(h->Omax, c.O);
     h->Dmax = std::max(h->Dmax, 2 * c.T);
     h->Gmax = std::max(h->Gmax, c.G);

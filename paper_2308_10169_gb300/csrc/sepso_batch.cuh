@@ -1,0 +1,92 @@
+// sepso_batch.cuh -- records shared by the batched kernels (sepso_batch.cu) and
+// the request server (sepso_server.cu).  Internal to libsepso.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sepso.h"
+
+namespace sepso {
+
+struct BatchScene {
+  int T, D, G, N, M, O, max_iters, beta;
+  float alpha;
+  uint32_t key0, key1, run_id;
+  long long xo;   // float offset of the scene's rows in X, V, P (M x D)
+  long long mo;   // offset in Pfit, PQ (M)
+  long long so;   // float offset of the candidate slots (2 x M x (D + 4))
+  long long go;   // float offset of the Gbest rows (G x D)
+  long long to;   // float offset of the Tbest row and the result row (D)
+  long long co;   // float4 offset of the circles (O)
+  long long ho;   // float offset of the hyper-parameters (G x 6)
+  long long wo;   // offset of the group words (3 x G)
+  long long gso;  // offset of the group scalars Gfit / GQ (2 x G, by parity)
+  // Request-slot fields (all zero / -1 for a plain batch run):
+  int j0;          // launch index before the scene's first iteration (iteration k runs at j0 + k)
+  int at_stall;    // 0: run max_iters; else Auto Truncation by stall counter with this limit
+  float stall_tol;
+  int n_pi;        // particles per group placed by Priori Initialization (when agent has_prev)
+  float pi_h;      // half-width of the PI interval
+  uint32_t cycle;  // Philox counter word 2 (low 24 bits): the agent's planning cycle
+  int agent;       // row of the warm-start table (-1: none)
+  int has_prev;    // the agent has a previous best path
+};
+
+struct BatchParams {
+  const BatchScene* sc;
+  const int4* tiles;   // (scene, group, first particle, particles)
+  int ntiles, nscenes;
+  float W, H;
+  int Omax, Dmax, Gmax, tile;
+  float *X, *V, *P, *Pfit;
+  int32_t* PQ;
+  float* slots;
+  float *Gb, *Tb;
+  const float4* circ;
+  const float* hyper;
+  const float* pts;    // 4 per scene: start, target
+  unsigned long long* words;
+  float* Gfit2;
+  int32_t* GQ2;
+  float* Tfit2;        // 2 per scene
+  int32_t* TQ2;
+  float* res_wp;
+  sepso_result* res;
+  int* status;
+  // Request slots (null for a plain batch run):
+  int32_t* stall2;     // 2 per scene, by parity
+  float* plv2;         // 2 per scene: previous LFV, by parity
+  int32_t* done;       // 1 per scene: set when the scene's plan has finished
+  float* agent_prevT;  // warm-start table: Dmax floats per agent
+};
+
+struct BatchSmem {
+  int circ, X, V, P, R, G, T, Pfit, PQ, Gfit, GQ, Gsrc, total;
+  __host__ __device__ static BatchSmem make(int Omax, int tile, int Dmax, int Gmax) {
+    BatchSmem s;
+    int off = 0;
+    auto al = [](int v) { return (v + 15) / 16 * 16; };
+    s.circ = off; off = al(off + (Omax > 0 ? Omax : 1) * 16);
+    s.X = off; off = al(off + tile * Dmax * 4);
+    s.V = off; off = al(off + tile * Dmax * 4);
+    s.P = off; off = al(off + tile * Dmax * 4);
+    s.R = off; off = al(off + tile * 16);
+    s.G = off; off = al(off + Dmax * 4);
+    s.T = off; off = al(off + Dmax * 4);
+    s.Pfit = off; off = al(off + tile * 4);
+    s.PQ = off; off = al(off + tile * 4);
+    s.Gfit = off; off = al(off + Gmax * 4);
+    s.GQ = off; off = al(off + Gmax * 4);
+    s.Gsrc = off; off = al(off + Gmax * 4);
+    s.total = off;
+    return s;
+  }
+};
+
+
+cudaError_t batch_configure(int* smem_optin_out);
+cudaError_t launch_batch_reset(const BatchParams& p, cudaStream_t s);
+cudaError_t launch_batch_iter(const BatchParams& p, int j, int ntiles, int threads, size_t smem, cudaStream_t s);
+
+}  // namespace sepso

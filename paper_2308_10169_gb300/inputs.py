@@ -263,3 +263,35 @@ def batch_workload(seed: int = 0, n: int = 4096, T_range=(8, 64), O_range=(16, 1
         circles.append(random_circles(rng, O, lo=0.0, hi=400.0, r_lo=r_range[0], r_hi=r_range[1]))
         points[s] = (20.0, 20.0, 380.0, 380.0)
     return specs, hyper, points, circles
+
+
+def serving_workload(seed: int = 0, n_agents: int = 2048, T_choices=(8, 20, 40), O_choices=(32, 256),
+                     r_range=(5.0, 25.0)):
+    """Agents of the serving workload: each has a T in T_choices, a scene of O in
+    O_choices circles (centres U[0,400]^2, radii U[r_range], velocities
+    U[0.5,2] per request in a uniform direction), start (20,20) and target
+    (380,380) drifting 1 unit per request vertically, and its own hyper-parameters
+    (w ~ U[0.4,0.9], C1, C2 ~ U[1,2.5]).  Returns a list of dicts."""
+    rng = np.random.default_rng(7000 + seed)
+    agents = []
+    for a in range(n_agents):
+        T = int(rng.choice(T_choices))
+        O = int(rng.choice(O_choices))
+        c = random_circles(rng, O, lo=0.0, hi=400.0, r_lo=r_range[0], r_hi=r_range[1])
+        sp = rng.uniform(0.5, 2.0, O)
+        ang = rng.uniform(0, 2 * np.pi, O)
+        v = np.stack([sp * np.cos(ang), sp * np.sin(ang)], 1).astype(np.float32)
+        agents.append(dict(T=T, O=O, circles=c, circle_vel=v, start=np.array([20.0, 20.0], np.float32),
+                           target=np.array([380.0, 380.0], np.float32),
+                           start_vel=np.array([0.0, 1.0], np.float32),
+                           target_vel=np.array([0.0, -1.0], np.float32),
+                           hyper=sample_hyper(int(rng.integers(1 << 30)), 8)))
+    return agents
+
+
+def poisson_arrivals(seed: int, rate: float, duration: float) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate over [0, duration)."""
+    rng = np.random.default_rng(9000 + seed)
+    n = int(rate * duration * 1.2) + 16
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    return t[t < duration]

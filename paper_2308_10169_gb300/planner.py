@@ -300,3 +300,99 @@ class BatchPlanner:
 
     def launch_count(self) -> int:
         return int(self.lib.sepso_batch_launch_count(self._h))
+
+
+class Server:
+    """Continuous-batching request server (sepso_server_*): submit, tick, poll."""
+
+    def __init__(self, n_agents: int, max_slots: int, G: int = 8, N: int = 32, Tmax: int = 40,
+                 Omax: int = 256, max_iters: int = 100, stall_iters: int = 10, stall_tol: float = 0.0,
+                 alpha: float = 30.0, beta: int = 4, pi_gamma: float = 0.25,
+                 pi_halfwidth: float = 20.0, map_w: float = 400.0, map_h: float = 400.0,
+                 seed: int = 0, mem_budget: int = 0, tile: int = 0, threads: int = 0, device=None,
+                 stream: torch.cuda.Stream | None = None):
+        from ._native import ServerConfig, check_server
+        self.lib = _native.lib()
+        self._check = check_server
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.cfg = ServerConfig(n_agents=n_agents, max_slots=max_slots, mem_budget=mem_budget, G=G, N=N,
+                                Tmax=Tmax, Omax=Omax, max_iters=max_iters, stall_iters=stall_iters,
+                                stall_tol=stall_tol, alpha=alpha, beta=beta, pi_gamma=pi_gamma,
+                                pi_halfwidth=pi_halfwidth, map_w=map_w, map_h=map_h, seed=seed,
+                                tile=tile, threads=threads)
+        size, slots = ctypes.c_size_t(), ctypes.c_int32()
+        check_server(self.lib.sepso_server_workspace_size(ctypes.byref(self.cfg), ctypes.byref(size),
+                                                         ctypes.byref(slots)))
+        self.slots = slots.value
+        self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check_server(self.lib.sepso_server_create(ctypes.byref(self.cfg),
+                                                      ctypes.c_void_p(self.workspace.data_ptr()), size.value,
+                                                      ctypes.c_void_p(self.stream.cuda_stream),
+                                                      ctypes.byref(self._h)))
+        self.Dm = 2 * Tmax
+        self.G = G
+
+    def close(self):
+        if self._h:
+            self.lib.sepso_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_hyper(self, hyper, agent: int = -1):
+        h = _f32(hyper, (self.G, 6))
+        self._check(self.lib.sepso_server_set_hyper(self._h, agent, fptr(h)))
+
+    def submit(self, agent: int, T: int, start, target, circles, tag: int):
+        c = _f32(circles, (-1, 3))
+        self._check(self.lib.sepso_server_submit(self._h, agent, T, fptr(_f32(start)), fptr(_f32(target)),
+                                                 fptr(c) if c.size else None, c.shape[0], tag))
+
+    def submit_at(self, agent: int, T: int, start, target, circles, tag: int, arrival_s: float):
+        c = _f32(circles, (-1, 3))
+        self._check(self.lib.sepso_server_submit_at(self._h, agent, T, fptr(_f32(start)),
+                                                    fptr(_f32(target)), fptr(c) if c.size else None,
+                                                    c.shape[0], tag, float(arrival_s)))
+
+    def clock(self, restart: bool = False) -> float:
+        return float(self.lib.sepso_server_clock(self._h, int(restart)))
+
+    def run(self, max_ticks: int = 100_000_000):
+        self._check(self.lib.sepso_server_run(self._h, max_ticks))
+
+    def tick(self):
+        a, q = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.sepso_server_tick(self._h, ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, max_n: int = 4096):
+        from ._native import ServerDone
+        out = (ServerDone * max_n)()
+        wp = np.zeros(max_n * self.Dm, np.float32)
+        n = ctypes.c_int32()
+        self._check(self.lib.sepso_server_poll(self._h, out, fptr(wp), max_n, ctypes.byref(n)))
+        res = []
+        for i in range(n.value):
+            d = out[i]
+            res.append({"tag": d.tag, "agent": d.agent, "T": d.T, "cost": d.res.cost,
+                        "length": d.res.length, "Q": d.res.Q, "iters": d.res.iters,
+                        "status": d.res.status, "arrival_s": d.arrival_s, "finish_s": d.finish_s,
+                        "waypoints": wp[i * self.Dm:i * self.Dm + 2 * d.T].copy()})
+        return res
+
+    def drain(self, max_ticks: int = 1_000_000):
+        self._check(self.lib.sepso_server_drain(self._h, max_ticks))
+
+    def stats(self) -> dict:
+        s = ctypes.c_int32()
+        v = [ctypes.c_int64() for _ in range(4)]
+        self._check(self.lib.sepso_server_stats(self._h, ctypes.byref(s), *[ctypes.byref(x) for x in v]))
+        return dict(slots=s.value, admitted=v[0].value, completed=v[1].value, ticks=v[2].value,
+                    launches=v[3].value)
