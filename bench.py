@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--batch-scenes", type=int, default=4096,
                     help="scenes of the batched section (0 = skip it)")
     ap.add_argument("--batch-iters", type=int, default=200)
+    ap.add_argument("--serve-rates", type=str, default="20000,5000",
+                    help="offered request rates (1/s) of the serving section ('' = skip it)")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -400,6 +403,48 @@ def run_batch(n: int, iters: int):
             "l2": "inputs larger than L2 (13 GB of swarm state)"}
 
 
+def _world_step(ag):
+    """The client's simulated world between two requests of an agent: circles and
+    start/target move by their velocity and bounce off the map border."""
+    c, v = ag["circles"], ag["circle_vel"]
+    for d in (0, 1):
+        c[:, d] += v[:, d]
+        flip = ((c[:, d] - c[:, 2] < 0) & (v[:, d] < 0)) | ((c[:, d] + c[:, 2] > 400.0) & (v[:, d] > 0))
+        v[flip, d] *= -1
+    for p, pv in (("start", "start_vel"), ("target", "target_vel")):
+        ag[p] += ag[pv]
+        for d in (0, 1):
+            if (ag[p][d] < 0 and ag[pv][d] < 0) or (ag[p][d] > 400 and ag[pv][d] > 0):
+                ag[pv][d] *= -1
+
+
+def run_serve(rate: float, seconds: float, n_agents: int = 2048):
+    """Open-loop serving: Poisson arrivals at `rate`, 2048 agents with mixed T and O."""
+    from paper_2308_10169_gb300 import Server
+    from paper_2308_10169_gb300.inputs import poisson_arrivals, serving_workload
+    agents = serving_workload(0, n_agents)
+    arr = poisson_arrivals(0, rate, seconds)
+    who = np.random.default_rng(11).integers(0, n_agents, len(arr))
+    sv = Server(n_agents=n_agents, max_slots=1024, G=8, N=32, Tmax=40, Omax=256, max_iters=100,
+                stall_iters=10)
+    for a, ag in enumerate(agents):
+        sv.set_hyper(ag["hyper"], agent=a)
+    for i, (t, a) in enumerate(zip(arr, who)):
+        ag = agents[a]
+        _world_step(ag)
+        sv.submit_at(int(a), ag["T"], ag["start"], ag["target"], ag["circles"], tag=i, arrival_s=float(t))
+    sv.clock(restart=True)
+    sv.run()
+    done = sv.poll(max_n=len(arr) + 1)
+    lat = np.array([d["finish_s"] - d["arrival_s"] for d in done]) * 1e3
+    span = max(d["finish_s"] for d in done) - min(d["arrival_s"] for d in done)
+    st = sv.stats()
+    return {"offered_per_s": rate, "requests": len(arr), "plans_per_s": len(done) / span,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "iters_per_plan": float(np.mean([d["iters"] for d in done])), "slots": st["slots"],
+            "ticks": st["ticks"], "gpu_launches": st["launches"]}
+
+
 def cpu_baseline(seconds: float):
     cfg, times, iters, costs = oracle_cycles(seconds, 10_000)
     n, total = len(times), sum(times)
@@ -425,6 +470,12 @@ def main():
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         if world == 1 and args.batch_scenes > 0:
             line["batch"] = run_batch(args.batch_scenes, args.batch_iters)
+        if world == 1 and args.serve_rates:
+            line["serve"] = {
+                "workload": "2048 agents, Poisson arrivals, T in {8,20,40}, O in {32,256} r~U[5,25], "
+                            "obstacles advanced per request, G=8 x N=32, PI warm start on the device, "
+                            "AT stall 10 / cap 100, continuous batching (1024 slots)",
+                "runs": [run_serve(float(r), args.serve_seconds) for r in args.serve_rates.split(",")]}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
