@@ -19,6 +19,9 @@ What each function follows (paper: arXiv 2308.10169):
 * ``advance_scene``         -- the dynamic simulator step (Fig. PP caption).
 * ``hsef``                  -- the hierarchical self-evolving framework
   (Sec. 3.2.1, Eq. fit_h).
+* ``raster`` / ``prior_encode`` / ``prior_decode`` / ``Mlp`` / ``adam`` -- the
+  learned prior (``prior_oracle.c``): occupancy raster features, label encoding,
+  MLP forward, loss gradient and the Adam step (Kingma and Ba, 2015).
 
 Parity status of each function is recorded in the header of ``sepso_oracle.c``
 and in the tests that pin it (``tests/test_oracle_*.py``); HSEF's absolute values
@@ -34,7 +37,7 @@ from pathlib import Path
 import numpy as np
 
 _HERE = Path(__file__).resolve().parent
-_SRC = _HERE / "sepso_oracle.c"
+_SRCS = [_HERE / "sepso_oracle.c", _HERE / "prior_oracle.c"]
 _BUILD = _HERE / "_build"
 _LIB_PATH = _BUILD / "libsepso_oracle.so"
 
@@ -46,11 +49,12 @@ _u32p = ctypes.POINTER(ctypes.c_uint32)
 def build(force: bool = False) -> Path:
     """Compile the oracle with gcc (plain -O2, no FMA contraction)."""
     _BUILD.mkdir(exist_ok=True)
-    if force or not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
+    stale = not _LIB_PATH.exists() or any(_LIB_PATH.stat().st_mtime < f.stat().st_mtime for f in _SRCS)
+    if force or stale:
         tmp = _LIB_PATH.with_suffix(f".{os.getpid()}.tmp")
         subprocess.run(
             ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-             str(_SRC), "-o", str(tmp), "-lm"],
+             *[str(f) for f in _SRCS], "-o", str(tmp), "-lm"],
             check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -89,6 +93,11 @@ class _HsefCfg(ctypes.Structure):
                 ("l_vlimit", ctypes.c_double), ("hseed", ctypes.c_uint64)]
 
 
+class _MlpDims(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("H1", ctypes.c_int32), ("H2", ctypes.c_int32),
+                ("O", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -123,6 +132,20 @@ def lib():
                                        _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
         L.so_hsef.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene),
                               ctypes.POINTER(_HsefCfg), _f64p, _f64p, _f64p]
+        L.so_mlp_num_params.argtypes = [ctypes.POINTER(_MlpDims)]
+        L.so_mlp_num_params.restype = ctypes.c_long
+        L.so_raster.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _f64p,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_int32, _f64p]
+        L.so_prior_encode.argtypes = [ctypes.c_int32] + [ctypes.c_double] * 6 + [_f64p, _f64p]
+        L.so_prior_decode.argtypes = [ctypes.c_int32] + [ctypes.c_double] * 6 + [_f64p, _f64p]
+        L.so_mlp_forward.argtypes = [ctypes.POINTER(_MlpDims), _f64p, ctypes.c_int32, _f64p, _f64p,
+                                     _f64p, _f64p]
+        L.so_mlp_loss_grad.argtypes = [ctypes.POINTER(_MlpDims), _f64p, ctypes.c_int32, _f64p, _f64p,
+                                       _f64p]
+        L.so_mlp_loss_grad.restype = ctypes.c_double
+        L.so_adam.argtypes = [ctypes.c_long, _f64p, _f64p, _f64p, _f64p, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32]
         _lib = L
     return _lib
 
@@ -332,3 +355,92 @@ def hsef(lcfg, scene: Scene, HG: int, HN: int, E: int, hhyper, lo, hi, l_vlimit:
                   _p64(hist))
     return best, float(bf[0]), hist
 
+
+
+# ----------------------------------------------------------------------------
+# Learned prior (prior_oracle.c)
+# ----------------------------------------------------------------------------
+
+def _f64(a, shape=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, np.float64))
+    return a.reshape(shape) if shape is not None else a
+
+
+def raster(grid: int, W: float, H: float, circles, start, target, K: int) -> np.ndarray:
+    """Features of one scene: g*g occupancy cells (decided in FP32), then start and
+    target over the map extent, then zeros up to K."""
+    c = _f64(circles).reshape(-1, 3).copy()
+    out = np.zeros(K)
+    lib().so_raster(grid, float(W), float(H), c.shape[0], _p64(c), float(start[0]), float(start[1]),
+                    float(target[0]), float(target[1]), K, _p64(out))
+    return out
+
+
+def prior_encode(T: int, W: float, H: float, start, target, waypoints) -> np.ndarray:
+    """A path's label: offset from the straight start-target line over the extent."""
+    wp = _f64(waypoints, (2 * T,))
+    y = np.zeros(2 * T)
+    lib().so_prior_encode(T, float(W), float(H), float(start[0]), float(start[1]), float(target[0]),
+                          float(target[1]), _p64(wp), _p64(y))
+    return y
+
+
+def prior_decode(T: int, W: float, H: float, start, target, y) -> np.ndarray:
+    """Waypoints of a network output (inverse of prior_encode, clipped to the map)."""
+    yy = _f64(y, (2 * T,))
+    wp = np.zeros(2 * T)
+    lib().so_prior_decode(T, float(W), float(H), float(start[0]), float(start[1]), float(target[0]),
+                          float(target[1]), _p64(yy), _p64(wp))
+    return wp
+
+
+class Mlp:
+    """h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3 in FP64, with the
+    parameters as one flat vector W1, b1, W2, b2, W3, b3 (row-major)."""
+
+    def __init__(self, K: int, H1: int, H2: int, O: int):
+        self.dims = _MlpDims(K=K, H1=H1, H2=H2, O=O)
+        self.K, self.H1, self.H2, self.O = K, H1, H2, O
+
+    @property
+    def num_params(self) -> int:
+        return int(lib().so_mlp_num_params(ctypes.byref(self.dims)))
+
+    def split(self, flat) -> dict:
+        """Views of the six tensors of a flat parameter vector."""
+        f = np.asarray(flat)
+        K, H1, H2, O = self.K, self.H1, self.H2, self.O
+        out, o = {}, 0
+        for name, shape in (("W1", (H1, K)), ("b1", (H1,)), ("W2", (H2, H1)), ("b2", (H2,)),
+                            ("W3", (O, H2)), ("b3", (O,))):
+            n = int(np.prod(shape))
+            out[name] = f[o:o + n].reshape(shape)
+            o += n
+        return out
+
+    def forward(self, params, X):
+        p = _f64(params, (self.num_params,))
+        x = _f64(X).reshape(-1, self.K)
+        B = x.shape[0]
+        h1, h2, y = np.zeros((B, self.H1)), np.zeros((B, self.H2)), np.zeros((B, self.O))
+        lib().so_mlp_forward(ctypes.byref(self.dims), _p64(p), B, _p64(x), _p64(h1), _p64(h2), _p64(y))
+        return h1, h2, y
+
+    def loss_grad(self, params, X, targets):
+        """(loss, flat gradient) of (1/2B) sum (y - t)^2."""
+        p = _f64(params, (self.num_params,))
+        x = _f64(X).reshape(-1, self.K)
+        t = _f64(targets).reshape(x.shape[0], self.O)
+        g = np.zeros(self.num_params)
+        loss = lib().so_mlp_loss_grad(ctypes.byref(self.dims), _p64(p), x.shape[0], _p64(x), _p64(t),
+                                      _p64(g))
+        return float(loss), g
+
+
+def adam(w, m, v, g, lr: float, b1: float, b2: float, eps: float, t: int):
+    """One Adam step t (1-based), in place on FP64 copies; returns (w, m, v)."""
+    w, m, v = _f64(w).copy(), _f64(m).copy(), _f64(v).copy()
+    gg = _f64(g)
+    lib().so_adam(w.size, _p64(w), _p64(m), _p64(v), _p64(gg), float(lr), float(b1), float(b2), float(eps),
+                  int(t))
+    return w, m, v
