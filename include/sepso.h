@@ -388,6 +388,118 @@ int sepso_plan_static(const sepso_config* cfg, const float* hyper, const float* 
                       const float* target, const float* circles, int32_t O, float* waypoints,
                       sepso_result* res, void* stream);
 
+/* ---- learned prior: an MLP proposing a cycle's initial waypoints ---------- */
+
+/* The paper seeds each cycle with Priori Initialization (Sec. 3.3.3): part of each
+ * group starts around the previous cycle's best path.  The learned prior is a
+ * second seed of that kind: a network maps the scene to a proposed path of T
+ * waypoints, and a batch scene with n_prior > 0 starts that many particles per
+ * group around it (sepso_batch_set_starts).  The paper has no learned component.
+ *
+ * Features of a scene (K = g*g + 4 rounded up to a multiple of 8): the g x g
+ * occupancy raster of [0, W] x [0, H] (cell (i, j), row i along y, is 1 when its
+ * centre ((j + 1/2) W / g, (i + 1/2) H / g) lies in a closed disk; decided in
+ * FP32), then start x / W, start y / H, target x / W, target y / H, then zeros.
+ * Label of a path (2T values, layout x_0..x_{T-1}, y_0..y_{T-1}): each waypoint's
+ * offset from the straight start-target line point at fraction (k + 1) / (T + 1),
+ * over the extent.  Network: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2),
+ * y = W3 h2 + b3 with BF16 weights and activations on the tensor cores (tcgen05,
+ * FP32 accumulation) and FP32 master weights; loss (1/2B) sum (y - t)^2; Adam
+ * (Kingma and Ba, 2015).  Parameters as one flat FP32 vector: W1 (H1 x K,
+ * row-major), b1, W2 (H2 x H1), b2, W3 (2T x H2), b3.
+ *
+ * The dataset (features, labels, start/target) lives in the workspace: rows
+ * [0, capacity).  Calls are ordered on the handle's stream; those marked sync
+ * wait for it. */
+typedef struct sepso_prior_ctx* sepso_prior_handle;
+
+typedef struct {
+  int32_t T;            /* waypoints of a proposal (1..64); 2T outputs            */
+  int32_t grid;         /* raster side g (8..256)                                 */
+  int32_t hidden1;      /* H1 (multiple of 8)                                     */
+  int32_t hidden2;      /* H2 (multiple of 8)                                     */
+  int32_t max_batch;    /* rows per step / per inference chunk (multiple of 8)    */
+  int32_t capacity;     /* dataset rows                                           */
+  int32_t max_circles;  /* circles per scene at most (add_scenes)                 */
+  float map_w, map_h;
+  float lr, beta1, beta2, eps; /* Adam                                            */
+} sepso_prior_config;
+
+/* Bytes of device workspace.  Errors: EINVAL. */
+int sepso_prior_workspace_size(const sepso_prior_config* cfg, size_t* bytes);
+
+/* Lay out the prior in the caller's workspace (device, 256-byte aligned, owned by
+ * the caller, at least sepso_prior_workspace_size bytes) on the caller's stream
+ * (cudaStream_t).  Parameters start at zero.  Errors: EINVAL, ENOSPC, ECUDA, ENOMEM. */
+int sepso_prior_create(const sepso_prior_config* cfg, void* d_workspace, size_t bytes, void* stream,
+                       sepso_prior_handle* out);
+void sepso_prior_destroy(sepso_prior_handle h);
+
+/* Length of the flat parameter vector. */
+int64_t sepso_prior_num_params(sepso_prior_handle h);
+
+/* Set (host, copied; resets Adam's moments and step count) or read (host, sync)
+ * the FP32 parameters.  Errors: EINVAL, ECUDA. */
+int sepso_prior_set_params(sepso_prior_handle h, const float* params);
+int sepso_prior_get_params(sepso_prior_handle h, float* params);
+
+/* Rasterise n scenes into dataset rows [first, first + n) (host inputs, copied;
+ * sync): points n x 4 (start x, y, target x, y), counts n circle counts (each <=
+ * max_circles), circles = the scenes' (cx, cy, r) rows back to back, waypoints
+ * n x 2T labels' paths or NULL (rows keep their old labels).
+ * Errors: EINVAL (range, counts), ECUDA. */
+int sepso_prior_add_scenes(sepso_prior_handle h, int32_t first, int32_t n, const float* points,
+                           const int32_t* counts, const float* circles, const float* waypoints);
+
+/* Read dataset rows back (host outputs, sync; either may be NULL): features as
+ * FP32 (n x K), labels (n x 2T).  Errors: EINVAL, ECUDA. */
+int sepso_prior_get_rows(sepso_prior_handle h, int32_t first, int32_t n, float* features, float* labels);
+
+/* Network outputs y (normalised, n x 2T, host, sync) of rows [first, first + n).
+ * Errors: EINVAL, ECUDA, ETIMEOUT. */
+int sepso_prior_forward(sepso_prior_handle h, int32_t first, int32_t n, float* y);
+
+/* Loss and its gradient (flat, host, sync) on rows [first, first + n), n a
+ * multiple of 8 and <= max_batch; no update.  Errors: EINVAL, ECUDA, ETIMEOUT. */
+int sepso_prior_grad(sepso_prior_handle h, int32_t first, int32_t n, float* grad, float* loss);
+
+/* Training: `steps` Adam steps (async unless losses is given).  rows < 0: minibatches of `batch` rows
+ * drawn with replacement from dataset rows [0, n_rows) by Philox keyed by seed
+ * (counter: the handle's step count); first >= 0: every step uses rows
+ * [first, first + batch).  batch: a multiple of 8, <= max_batch.  losses: host
+ * array of `steps` (<= 65536) floats, the minibatch loss of each step, filled
+ * before the call returns (it then waits for the stream), or NULL.
+ * Errors: EINVAL, ECUDA. */
+int sepso_prior_train(sepso_prior_handle h, int32_t n_rows, int32_t first, int32_t steps, int32_t batch,
+                      uint64_t seed, float* losses);
+
+/* Proposals of rows [first, first + n): waypoints (2T floats per row, the row
+ * stride ld >= 2T) written to the device array out on the handle's stream
+ * (async).  Errors: EINVAL, ECUDA. */
+int sepso_prior_infer(sepso_prior_handle h, int32_t first, int32_t n, float* d_out, int32_t ld);
+
+/* Wait for the handle's stream and return the first device-side error (ETIMEOUT
+ * of a tensor-core wait), else OK; clears it. */
+int sepso_prior_sync(sepso_prior_handle h);
+
+/* Kernel launches issued so far. */
+int64_t sepso_prior_launch_count(sepso_prior_handle h);
+const char* sepso_prior_last_error(void);
+
+/* The tensor-core GEMM used by the prior, exposed for testing and benchmarking:
+ * C[m][n] = epilogue(alpha * sum_k A[m][k] * B[n][k]) for m < M, n < N, with A
+ * (M x K, row stride lda) and B (N x K, row stride ldb) BF16 device arrays, K,
+ * lda and ldb multiples of 8, A and B 16-byte aligned.  Epilogue: + bias[n]
+ * (device FP32, or NULL), then max(., 0) if relu, then 0 where mask[m][n] (BF16,
+ * row stride ldm, or NULL) is not > 0.  Outputs: Cf (FP32, row stride ldcf)
+ * and/or Cb (BF16, ldcb), device, either may be NULL.  Async on stream; a
+ * device-side timeout is reported by the next sepso_gemm_bf16_sync.
+ * Errors: EINVAL, ECUDA. */
+int sepso_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, int32_t lda, int32_t ldb,
+                    float alpha, const float* bias, int32_t relu, const void* mask, int32_t ldm, float* Cf,
+                    int32_t ldcf, void* Cb, int32_t ldcb, void* stream);
+int sepso_gemm_bf16_sync(void* stream);
+
 /* ---- misc --------------------------------------------------------------- */
 
 /* Wait for the handle's stream; returns the first device-side error of any run

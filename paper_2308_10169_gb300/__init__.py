@@ -8,7 +8,7 @@ The CUDA library is required: nothing here falls back to a CPU implementation.
 from .inputs import (AT_OFF, AT_STALL, AT_STD_WINDOW, TABLE_HYPER8, TABLE_HYPER8_PATH, Scene,
                      SepsoConfig, dynamic_workload, sample_hyper, static_workload)
 
-__all__ = ["Planner", "BatchPlanner", "Server", "SepsoConfig", "Scene", "static_workload", "dynamic_workload",
+__all__ = ["Planner", "BatchPlanner", "Server", "Prior", "SepsoConfig", "Scene", "static_workload", "dynamic_workload",
            "sample_hyper", "TABLE_HYPER8", "TABLE_HYPER8_PATH", "AT_OFF", "AT_STALL",
            "AT_STD_WINDOW"]
 
@@ -20,6 +20,9 @@ def __getattr__(name):
     if name == "Server":
         from .planner import Server
         return Server
+    if name == "Prior":
+        from .prior import Prior
+        return Prior
     if name == "BatchPlanner":
         from .planner import BatchPlanner
         return BatchPlanner

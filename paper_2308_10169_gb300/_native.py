@@ -78,6 +78,14 @@ class ServerDone(ctypes.Structure):
                 ("res", Result), ("arrival_s", ctypes.c_double), ("finish_s", ctypes.c_double)]
 
 
+class PriorConfig(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("grid", ctypes.c_int32), ("hidden1", ctypes.c_int32),
+                ("hidden2", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("capacity", ctypes.c_int32),
+                ("max_circles", ctypes.c_int32), ("map_w", ctypes.c_float), ("map_h", ctypes.c_float),
+                ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
 def make_config(cfg) -> Config:
     return Config(T=cfg.T, G=cfg.G, N=cfg.N, max_obstacles=cfg.max_obstacles, map_w=cfg.map_w,
                   map_h=cfg.map_h, alpha=cfg.alpha, beta=cfg.beta, max_iters=cfg.max_iters,
@@ -150,6 +158,24 @@ SIGNATURES = {
     "sepso_server_drain": (ctypes.c_int, [_vp, _i64]),
     "sepso_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)] + [ctypes.POINTER(_i64)] * 4),
     "sepso_server_last_error": (ctypes.c_char_p, []),
+    "sepso_prior_workspace_size": (ctypes.c_int, [ctypes.POINTER(PriorConfig), ctypes.POINTER(_sz)]),
+    "sepso_prior_create": (ctypes.c_int, [ctypes.POINTER(PriorConfig), _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "sepso_prior_destroy": (None, [_vp]),
+    "sepso_prior_num_params": (_i64, [_vp]),
+    "sepso_prior_set_params": (ctypes.c_int, [_vp, _fp]),
+    "sepso_prior_get_params": (ctypes.c_int, [_vp, _fp]),
+    "sepso_prior_add_scenes": (ctypes.c_int, [_vp, _i32, _i32, _fp, ctypes.POINTER(_i32), _fp, _fp]),
+    "sepso_prior_get_rows": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp]),
+    "sepso_prior_forward": (ctypes.c_int, [_vp, _i32, _i32, _fp]),
+    "sepso_prior_grad": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp]),
+    "sepso_prior_train": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, ctypes.c_uint64, _fp]),
+    "sepso_prior_infer": (ctypes.c_int, [_vp, _i32, _i32, _vp, _i32]),
+    "sepso_prior_sync": (ctypes.c_int, [_vp]),
+    "sepso_prior_launch_count": (_i64, [_vp]),
+    "sepso_prior_last_error": (ctypes.c_char_p, []),
+    "sepso_gemm_bf16": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _i32, _i32, ctypes.c_float, _vp, _i32,
+                                       _vp, _i32, _vp, _i32, _vp, _i32, _vp]),
+    "sepso_gemm_bf16_sync": (ctypes.c_int, [_vp]),
     "sepso_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sepso_last_error": (ctypes.c_char_p, []),
 }
@@ -185,6 +211,13 @@ def check(code: int):
 def check_server(code: int):
     if code != SEPSO_OK:
         msg = lib().sepso_server_last_error()
+        raise SepsoError(code, msg.decode() if msg else "")
+    return code
+
+
+def check_prior(code: int):
+    if code != SEPSO_OK:
+        msg = lib().sepso_prior_last_error()
         raise SepsoError(code, msg.decode() if msg else "")
     return code
 

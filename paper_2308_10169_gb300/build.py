@@ -1,6 +1,6 @@
 """Build ``libsepso.so`` in-tree with nvcc for sm_103a (GB300).
 
-Two translation units are compiled in parallel and linked into one shared library
+The translation units are compiled in parallel and linked into one shared library
 with the CUDA runtime linked statically.  Nothing is installed anywhere.
 """
 from __future__ import annotations
@@ -16,7 +16,7 @@ INCLUDE = ROOT / "include"
 BUILD = PKG / "_build"
 LIB = BUILD / "libsepso.so"
 
-SOURCES = ["sepso_kernels.cu", "sepso_api.cu", "sepso_batch.cu", "sepso_server.cu"]
+SOURCES = ["sepso_kernels.cu", "sepso_api.cu", "sepso_batch.cu", "sepso_server.cu", "sepso_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          f"-I{INCLUDE}", f"-I{CSRC}"]

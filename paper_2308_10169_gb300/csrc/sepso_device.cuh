@@ -67,7 +67,7 @@ enum : int { kModePlan = 0, kModeStep = 1 };
 
 enum : uint32_t {
   kStreamVel = 0, kStreamInitX = 1, kStreamInitV = 2, kStreamPI = 3,
-  kStreamHInitX = 5, kStreamHInitV = 6, kStreamHVel = 7
+  kStreamPrior = 4, kStreamHInitX = 5, kStreamHInitV = 6, kStreamHVel = 7, kStreamSample = 8
 };
 
 // Everything one launch of the swarm kernel needs (passed by value).

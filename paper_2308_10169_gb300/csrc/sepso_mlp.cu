@@ -1,0 +1,1017 @@
+// sepso_mlp.cu -- the learned prior of the planner on GB300 (sm_103a): an MLP
+// (64x64 occupancy raster + start/target -> 1024 -> 512 -> 2T) with BF16 weights
+// and FP32 accumulation, trained and run with the project's own kernels.
+//
+//   gemm_tc_kernel     C = A . B^T on the 5th-generation tensor cores: operands
+//                      staged in shared memory by cp.async (3 stages), one elected
+//                      thread issues tcgen05.mma (kind::f16, BF16 inputs, FP32
+//                      accumulator in tensor memory), tcgen05.commit signals an
+//                      mbarrier per stage, and the four warps read the accumulator
+//                      back with tcgen05.ld for a fused epilogue (scale, bias, ReLU,
+//                      ReLU mask of the backward pass, FP32 and/or BF16 output).
+//   raster_kernel      occupancy raster of the circles (cell centre inside a disk).
+//   small kernels      transpose, column sums (bias gradients), MSE loss gradient,
+//                      Adam, FP32 -> BF16 weight copies.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cuda_bf16.h>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sepso_device.cuh"
+#include "sepso_internal.h"
+
+namespace sepso {
+
+// ---------------------------------------------------------------------------
+// tcgen05 / cp.async helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(smem_dst)), "l"(gsrc),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* smem_dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(smem_dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor (no swizzle, K-major canonical layout of 8-row x
+// 16-byte core matrices): start address, leading-dimension byte offset (between
+// core matrices adjacent in K), stride-dimension byte offset (between 8-row
+// groups), the fixed version bits 46..48 = 0b001, swizzle mode 0.
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+  const uint64_t a = (uint64_t)((smem_addr(p) >> 4) & 0x3FFFu);
+  return a | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t mma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------------------
+// GEMM: C[M x N] = alpha * A[M x K] . B[N x K]^T (+ bias[n]) (then ReLU, or the
+// ReLU mask mask[m][n] > 0), A and B row-major BF16 with K contiguous.
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  int M, N, K, lda, ldb;
+  float alpha;
+  const float* bias;           // N, or null
+  int relu;
+  const __nv_bfloat16* mask;   // M x N (ldm), or null
+  int ldm;
+  float* Cf;                   // FP32 output, or null
+  int ldcf;
+  __nv_bfloat16* Cb;           // BF16 output, or null
+  int ldcb;
+  int* status;
+};
+
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3, kGemmThreads = 128;
+constexpr int kTileBytes = kBM * kBK * 2;            // 16 KB per operand per stage
+constexpr int kStageBytes = 2 * kTileBytes;          // A + B
+// Slack after the stages: a descriptor stride read the other way round would still
+// stay inside the CTA's shared memory.
+constexpr int kGemmSmem = kStages * kStageBytes + 32768;
+
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_tc_kernel(const GemmArgs g) {
+  extern __shared__ __align__(1024) uint8_t gsm[];
+  __shared__ uint64_t mbar[kStages];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  const int nkb = (g.K + kBK - 1) / kBK;
+  constexpr uint32_t kIdesc = mma_idesc_bf16(kBM, kBN);
+
+  if (warp == 0) tmem_alloc(&tmem_base, kBN);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&mbar[s], 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  // Tile layout in shared memory (rows R = 128, 8 chunks of 8 K-elements): chunk
+  // (row, kc) at kc * R * 16 + row * 16 bytes, i.e. core matrices of 8 rows x 16 B
+  // with an 8-row stride of 128 B and a K stride of R * 16 = 2048 B.
+  auto load_stage = [&](int kb, int s) {
+    uint8_t* sa = gsm + s * kStageBytes;
+    uint8_t* sb = sa + kTileBytes;
+    for (int c = tid; c < kBM * 8; c += kGemmThreads) {
+      const int row = c % kBM, kc = c / kBM;
+      const int gk = kb * kBK + kc * 8;
+      const int gm = m0 + row;
+      const bool ok = gm < g.M && gk < g.K;
+      cp_async16(sa + kc * (kBM * 16) + row * 16, ok ? (const void*)(g.A + (size_t)gm * g.lda + gk) : (const void*)g.A,
+                 ok ? 16 : 0);
+      const int gn = n0 + row;
+      const bool okb = gn < g.N && gk < g.K;
+      cp_async16(sb + kc * (kBN * 16) + row * 16, okb ? (const void*)(g.B + (size_t)gn * g.ldb + gk) : (const void*)g.B,
+                 okb ? 16 : 0);
+    }
+  };
+
+  for (int kb = 0; kb < kStages - 1; ++kb) {
+    if (kb < nkb) load_stage(kb, kb);
+    cp_async_commit();
+  }
+  bool fail = false;
+  int committed = -1;  // last K-block whose MMAs were committed
+  for (int kb = 0; kb < nkb && !fail; ++kb) {
+    const int s = kb % kStages;
+    cp_async_wait<kStages - 2>();
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint8_t* sa = gsm + s * kStageBytes;
+      const uint8_t* sb = sa + kTileBytes;
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk) {
+        const uint64_t ad = smem_desc(sa + kk * 2 * (kBM * 16), kBM * 16, 128);
+        const uint64_t bd = smem_desc(sb + kk * 2 * (kBN * 16), kBN * 16, 128);
+        mma_bf16(tmem, ad, bd, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(&mbar[s]);
+    }
+    committed = kb;
+    const int nk = kb + kStages - 1;
+    if (nk < nkb) {
+      const int ps = nk % kStages;
+      if (kb >= 1) {
+        // the MMAs of block kb - 1 read stage ps: wait for them before refilling it
+        const uint32_t parity = (uint32_t)(((kb - 1) / kStages) & 1);
+        if (!mbar_wait_bounded(&mbar[ps], parity, kWaitLimitNs)) fail = true;
+      }
+      if (!fail) load_stage(nk, ps);
+    }
+    cp_async_commit();
+    if (__syncthreads_or(fail ? 1 : 0)) fail = true;
+  }
+  // MMAs complete in issue order: the last commit covers all of them.  On a timeout
+  // the wait is repeated once (bounded) so that no MMA is in flight at dealloc.
+  if (committed >= 0) {
+    const bool ok = mbar_wait_bounded(&mbar[committed % kStages], (uint32_t)((committed / kStages) & 1), kWaitLimitNs);
+    if (!ok) fail = true;
+  }
+  cp_async_wait<0>();
+  if (__syncthreads_or(fail ? 1 : 0)) {
+    if (tid == 0 && g.status) atomicExch(g.status, SEPSO_ETIMEOUT);
+  } else if (committed >= 0) {
+    tc_fence_after();
+    // Epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31.  The accumulator tile
+    // goes through shared memory (row stride 129 floats: conflict-free both ways) so
+    // that the global stores are row-contiguous.
+    float* tile = reinterpret_cast<float*>(gsm);
+    constexpr int kLd = kBN + 1;
+    const int r = warp * 32 + lane;
+    float v[32];
+#pragma unroll 1
+    for (int c0 = 0; c0 < kBN; c0 += 32) {
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) tile[r * kLd + c0 + i] = v[i];
+    }
+    __syncthreads();
+    const int ncol = min(kBN, g.N - n0);
+    for (int rr = warp; rr < kBM; rr += kGemmThreads / 32) {
+      const int row = m0 + rr;
+      if (row >= g.M) break;
+      for (int c = lane; c < ncol; c += 32) {
+        const int col = n0 + c;
+        float x = g.alpha * tile[rr * kLd + c];
+        if (g.bias) x += g.bias[col];
+        if (g.relu) x = fmaxf(x, 0.0f);
+        if (g.mask && !(__bfloat162float(g.mask[(size_t)row * g.ldm + col]) > 0.0f)) x = 0.0f;
+        if (g.Cf) g.Cf[(size_t)row * g.ldcf + col] = x;
+        if (g.Cb) g.Cb[(size_t)row * g.ldcb + col] = __float2bfloat16_rn(x);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kBN);
+}
+
+}  // namespace sepso
+
+namespace sepso {
+
+// ---------------------------------------------------------------------------
+// Features and labels of a chunk of scenes (one CTA per scene).
+//   feature row: g*g occupancy cells (cell (i, j) occupied when its centre lies in
+//   a closed disk; FP32 decision with explicit round-to-nearest operations), then
+//   start / target over the map extent, then zeros up to K.
+//   label row (when waypoints are given): offset of each waypoint from the point
+//   of the straight start-target line at fraction (k + 1) / (T + 1), over the extent.
+// ---------------------------------------------------------------------------
+struct RasterArgs {
+  int n, grid, K, T, O_max;
+  float W, H;
+  const float4* circ;      // staged circles (cx, cy, r, 0) of the chunk
+  const int* coff;         // n + 1 prefix offsets into circ
+  const float* pts;        // n x 4
+  const float* wp;         // n x 2T, or null
+  __nv_bfloat16* X;        // n rows of K (destination rows)
+  float* Y;                // n rows of 2T, or null
+};
+
+__global__ void __launch_bounds__(256) raster_kernel(const RasterArgs a) {
+  extern __shared__ float4 rc[];
+  const int s = blockIdx.x;
+  const int c0 = a.coff[s], O = a.coff[s + 1] - c0;
+  for (int i = threadIdx.x; i < O; i += blockDim.x) rc[i] = a.circ[c0 + i];
+  __syncthreads();
+  const float cw = a.W / (float)a.grid, ch = a.H / (float)a.grid;
+  __nv_bfloat16* row = a.X + (size_t)s * a.K;
+  const int g2 = a.grid * a.grid;
+  for (int c = threadIdx.x; c < g2; c += blockDim.x) {
+    const int i = c / a.grid, j = c - i * a.grid;
+    const float x = __fmul_rn((float)j + 0.5f, cw), y = __fmul_rn((float)i + 0.5f, ch);
+    bool occ = false;
+    for (int o = 0; o < O; ++o) {
+      const float4 q = rc[o];
+      const float dx = __fsub_rn(x, q.x), dy = __fsub_rn(y, q.y);
+      const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+      occ |= d2 <= __fmul_rn(q.z, q.z);
+    }
+    row[c] = __float2bfloat16_rn(occ ? 1.0f : 0.0f);
+  }
+  const float* p = a.pts + 4 * s;
+  for (int k = g2 + threadIdx.x; k < a.K; k += blockDim.x) {
+    const int e = k - g2;
+    const float v = (e < 4) ? p[e] / ((e & 1) ? a.H : a.W) : 0.0f;
+    row[k] = __float2bfloat16_rn(v);
+  }
+  if (a.wp != nullptr && a.Y != nullptr) {
+    const int T = a.T;
+    for (int d = threadIdx.x; d < 2 * T; d += blockDim.x) {
+      const int k = d < T ? d : d - T;
+      const float f = (float)(k + 1) / (float)(T + 1);
+      const float s0 = d < T ? p[0] : p[1], t0 = d < T ? p[2] : p[3];
+      const float ext = d < T ? a.W : a.H;
+      a.Y[(size_t)s * 2 * T + d] = (a.wp[(size_t)s * 2 * T + d] - (s0 + f * (t0 - s0))) / ext;
+    }
+  }
+}
+
+// Minibatch rows: idx[b] = Philox(seed; step, b) mod n_rows (with replacement).
+__global__ void sample_kernel(int* idx, int B, int n_rows, uint32_t k0, uint32_t k1, uint32_t step) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) {
+    const uint4 r = draw(k0, k1, step, (uint32_t)b, kStreamSample, 0u, 0u);
+    idx[b] = (int)(r.x % (uint32_t)n_rows);
+  }
+}
+
+// x[b] = X[r] (K bf16, 16-byte vectors), t[b] = Y[r], with r = idx[b] (or first + b
+// without an index list).
+__global__ void gather_kernel(const int* __restrict__ idx, int first, int B, int K, const __nv_bfloat16* __restrict__ X,
+                              const float* __restrict__ Y, int O, __nv_bfloat16* __restrict__ x, float* __restrict__ t) {
+  const int b = blockIdx.x;
+  if (b >= B) return;
+  const int r = idx ? idx[b] : first + b;
+  const uint4* src = reinterpret_cast<const uint4*>(X + (size_t)r * K);
+  uint4* dst = reinterpret_cast<uint4*>(x + (size_t)b * K);
+  for (int v = threadIdx.x; v < K / 8; v += blockDim.x) dst[v] = src[v];
+  for (int d = threadIdx.x; d < O; d += blockDim.x) t[(size_t)b * O + d] = Y[(size_t)r * O + d];
+}
+
+// out[c][r] = in[r][c] for r < R, c < C (bf16); 32 x 32 tiles through shared memory.
+__global__ void transpose_kernel(const __nv_bfloat16* __restrict__ in, int R, int C, int ldi,
+                                 __nv_bfloat16* __restrict__ out, int ldo) {
+  __shared__ __nv_bfloat16 t[32][34];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int r = r0 + dy, c = c0 + threadIdx.x;
+    if (r < R && c < C) t[dy][threadIdx.x] = in[(size_t)r * ldi + c];
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int c = c0 + dy, r = r0 + threadIdx.x;
+    if (r < R && c < C) out[(size_t)c * ldo + r] = t[threadIdx.x][dy];
+  }
+}
+
+// dY = (y - t) / B (FP32, and BF16 with columns O .. ldb-1 zero); loss += sum (y - t)^2 / 2B.
+__global__ void loss_grad_kernel(const float* __restrict__ y, const float* __restrict__ t, int B, int O,
+                                 float* __restrict__ dyf, __nv_bfloat16* __restrict__ dyb, int ldb, float* loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float sq = 0.0f;
+  if (i < B * ldb) {
+    const int b = i / ldb, d = i - b * ldb;
+    float g = 0.0f;
+    if (d < O) {
+      const float e = y[(size_t)b * O + d] - t[(size_t)b * O + d];
+      sq = e * e;
+      g = e / (float)B;
+      dyf[(size_t)b * O + d] = g;
+    }
+    dyb[i] = __float2bfloat16_rn(g);
+  }
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0 && sq != 0.0f) atomicAdd(loss, 0.5f * sq / (float)B);
+}
+
+// db[j] = sum_b D[b][j]: 32 columns per CTA, 8 row lanes, fixed summation order.
+__global__ void colsum_kernel(const float* __restrict__ D, int B, int N, int ld, float* __restrict__ db) {
+  __shared__ float part[8][33];
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  float s = 0.0f;
+  if (j < N)
+    for (int b = threadIdx.y; b < B; b += 8) s += D[(size_t)b * ld + j];
+  part[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < N) {
+    float v = 0.0f;
+    for (int r = 0; r < 8; ++r) v += part[r][threadIdx.x];
+    db[j] = v;
+  }
+}
+
+// Adam (Kingma and Ba, 2015), FP32 masters; also refreshes the BF16 mirror.
+__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, __nv_bfloat16* __restrict__ wb, long long n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    wb[i] = __float2bfloat16_rn(wi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    wb[i] = __float2bfloat16_rn(w[i]);
+}
+
+// Waypoints of the network outputs: straight-line point + y * extent, clipped to the map.
+__global__ void decode_kernel(const float* __restrict__ y, int n, int T, const float* __restrict__ pts, float W,
+                              float H, float* __restrict__ out, int ldo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * 2 * T) return;
+  const int s = i / (2 * T), d = i - s * 2 * T;
+  const int k = d < T ? d : d - T;
+  const float f = (float)(k + 1) / (float)(T + 1);
+  const float* p = pts + 4 * s;
+  const float s0 = d < T ? p[0] : p[1], t0 = d < T ? p[2] : p[3];
+  const float ext = d < T ? W : H;
+  out[(size_t)s * ldo + d] = fminf(fmaxf(s0 + f * (t0 - s0) + y[i] * ext, 0.0f), ext);
+}
+
+}  // namespace sepso
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+using sepso::GemmArgs;
+using bf16 = __nv_bfloat16;
+
+namespace {
+
+thread_local std::string g_prior_error;
+
+int pfail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int pfail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_prior_error = buf;
+  return code;
+}
+
+#define PCUDA(expr)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) return pfail(SEPSO_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+#define PTRY(expr)              \
+  do {                          \
+    const int r_ = (expr);      \
+    if (r_ != SEPSO_OK) return r_; \
+  } while (0)
+
+size_t al256(size_t v) { return (v + 255) & ~size_t(255); }
+int round8(int v) { return (v + 7) / 8 * 8; }
+constexpr int kLossRing = 65536;
+
+__device__ int g_gemm_status;
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int gemm_launch(const GemmArgs& g, cudaStream_t s) {
+  if (g.M < 1 || g.N < 1 || g.K < 8 || (g.K & 7) || (g.lda & 7) || (g.ldb & 7) || g.lda < g.K || g.ldb < g.K)
+    return pfail(SEPSO_EINVAL, "gemm: bad sizes M %d N %d K %d lda %d ldb %d", g.M, g.N, g.K, g.lda, g.ldb);
+  if (!g.A || !g.B || !aligned16(g.A) || !aligned16(g.B))
+    return pfail(SEPSO_EINVAL, "gemm: A and B must be 16-byte aligned device arrays");
+  if ((g.Cf && g.ldcf < g.N) || (g.Cb && g.ldcb < g.N) || (g.mask && g.ldm < g.N))
+    return pfail(SEPSO_EINVAL, "gemm: output or mask row stride below N");
+  PCUDA(cudaFuncSetAttribute(sepso::gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sepso::kGemmSmem));
+  const dim3 grid((g.M + sepso::kBM - 1) / sepso::kBM, (g.N + sepso::kBN - 1) / sepso::kBN);
+  if (grid.y > 65535u) return pfail(SEPSO_EINVAL, "gemm: N too large");
+  sepso::gemm_tc_kernel<<<grid, sepso::kGemmThreads, sepso::kGemmSmem, s>>>(g);
+  PCUDA(cudaGetLastError());
+  return SEPSO_OK;
+}
+
+struct PriorLayout {
+  size_t prm, m, v, grad, wb, w2t, w3t, X, Y, P, scirc, scoff, spts, swp, idx, x, xT, h1, h1T, h2, h2T, y, t, dyf,
+      dyb, dyT, dh2f, dh2b, dh2T, dh1f, dh1b, dh1T, loss, status, total;
+};
+
+struct Dims {
+  int K, O, O8, H1, H2, B, g;
+  long long P;
+  long long off[6];
+};
+
+bool make_dims(const sepso_prior_config* c, Dims* d) {
+  if (!c || c->T < 1 || c->T > 64 || c->grid < 8 || c->grid > 256 || c->hidden1 < 8 || (c->hidden1 & 7) ||
+      c->hidden2 < 8 || (c->hidden2 & 7) || c->max_batch < 8 || (c->max_batch & 7) || c->max_batch > 65536 ||
+      c->capacity < 1 || c->max_circles < 0 || c->max_circles > 8192 || !(c->map_w > 0) || !(c->map_h > 0) ||
+      !(c->lr > 0) || !(c->beta1 >= 0 && c->beta1 < 1) || !(c->beta2 >= 0 && c->beta2 < 1) || !(c->eps > 0))
+    return false;
+  d->g = c->grid;
+  d->K = round8(c->grid * c->grid + 4);
+  d->O = 2 * c->T;
+  d->O8 = round8(d->O);
+  d->H1 = c->hidden1;
+  d->H2 = c->hidden2;
+  d->B = c->max_batch;
+  d->off[0] = 0;
+  d->off[1] = d->off[0] + (long long)d->H1 * d->K;
+  d->off[2] = d->off[1] + d->H1;
+  d->off[3] = d->off[2] + (long long)d->H2 * d->H1;
+  d->off[4] = d->off[3] + d->H2;
+  d->off[5] = d->off[4] + (long long)d->O * d->H2;
+  d->P = d->off[5] + d->O;
+  return (long long)c->capacity * d->K < (1ll << 40);
+}
+
+PriorLayout layout(const sepso_prior_config* c, const Dims& d) {
+  PriorLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = al256(off);
+    const size_t o = off;
+    off += std::max<size_t>(bytes, 16);
+    return o;
+  };
+  const size_t P = (size_t)d.P, B = (size_t)d.B, K = (size_t)d.K, O = (size_t)d.O;
+  const size_t H1 = (size_t)d.H1, H2 = (size_t)d.H2, cap = (size_t)c->capacity;
+  L.prm = take(P * 4);
+  L.m = take(P * 4);
+  L.v = take(P * 4);
+  L.grad = take(P * 4);
+  L.wb = take(P * 2);
+  L.w2t = take(H1 * H2 * 2);
+  L.w3t = take(H2 * d.O8 * 2);
+  L.X = take(cap * K * 2);
+  L.Y = take(cap * O * 4);
+  L.P = take(cap * 16);
+  L.scirc = take(B * (size_t)std::max(c->max_circles, 1) * 16);
+  L.scoff = take((B + 1) * 4);
+  L.spts = take(B * 16);
+  L.swp = take(B * O * 4);
+  L.idx = take(B * 4);
+  L.x = take(B * K * 2);
+  L.xT = take(K * B * 2);
+  L.h1 = take(B * H1 * 2);
+  L.h1T = take(H1 * B * 2);
+  L.h2 = take(B * H2 * 2);
+  L.h2T = take(H2 * B * 2);
+  L.y = take(B * O * 4);
+  L.t = take(B * O * 4);
+  L.dyf = take(B * O * 4);
+  L.dyb = take(B * d.O8 * 2);
+  L.dyT = take(O * B * 2);
+  L.dh2f = take(B * H2 * 4);
+  L.dh2b = take(B * H2 * 2);
+  L.dh2T = take(H2 * B * 2);
+  L.dh1f = take(B * H1 * 4);
+  L.dh1b = take(B * H1 * 2);
+  L.dh1T = take(H1 * B * 2);
+  L.loss = take((size_t)kLossRing * 4);
+  L.status = take(4);
+  L.total = al256(off);
+  return L;
+}
+
+}  // namespace
+
+struct sepso_prior_ctx {
+  sepso_prior_config c{};
+  Dims d{};
+  PriorLayout L{};
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  int64_t step = 0;      // Adam steps taken
+  int64_t launches = 0;
+  int loss_head = 0;     // next slot of the loss ring
+  struct Pending {
+    float* host;
+    int n, slot;
+  };
+  std::vector<Pending> pending;
+  template <class T>
+  T* at(size_t o) const { return reinterpret_cast<T*>(ws + o); }
+};
+
+namespace {
+
+int gemm(sepso_prior_ctx* h, const bf16* A, const bf16* B, int M, int N, int K, int lda, int ldb, const float* bias,
+         int relu, const bf16* mask, int ldm, float* Cf, int ldcf, bf16* Cb, int ldcb) {
+  GemmArgs g{};
+  g.A = A;
+  g.B = B;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.lda = lda;
+  g.ldb = ldb;
+  g.alpha = 1.0f;
+  g.bias = bias;
+  g.relu = relu;
+  g.mask = mask;
+  g.ldm = ldm;
+  g.Cf = Cf;
+  g.ldcf = ldcf;
+  g.Cb = Cb;
+  g.ldcb = ldcb;
+  g.status = h->at<int>(h->L.status);
+  ++h->launches;
+  return gemm_launch(g, h->stream);
+}
+
+int transpose(sepso_prior_ctx* h, const bf16* in, int R, int C, int ldi, bf16* out, int ldo) {
+  const dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+  sepso::transpose_kernel<<<grid, block, 0, h->stream>>>(in, R, C, ldi, out, ldo);
+  ++h->launches;
+  PCUDA(cudaGetLastError());
+  return SEPSO_OK;
+}
+
+int colsum(sepso_prior_ctx* h, const float* D, int B, int N, int ld, float* db) {
+  sepso::colsum_kernel<<<(N + 31) / 32, dim3(32, 8), 0, h->stream>>>(D, B, N, ld, db);
+  ++h->launches;
+  PCUDA(cudaGetLastError());
+  return SEPSO_OK;
+}
+
+// Forward pass of n <= B rows x (row stride K): h1, h2 (BF16), y (FP32).
+int forward(sepso_prior_ctx* h, const bf16* x, int n) {
+  const Dims& d = h->d;
+  const float* prm = h->at<float>(h->L.prm);
+  const bf16* wb = h->at<bf16>(h->L.wb);
+  bf16* h1 = h->at<bf16>(h->L.h1);
+  bf16* h2 = h->at<bf16>(h->L.h2);
+  PTRY(gemm(h, x, wb + d.off[0], n, d.H1, d.K, d.K, d.K, prm + d.off[1], 1, nullptr, 0, nullptr, 0, h1, d.H1));
+  PTRY(gemm(h, h1, wb + d.off[2], n, d.H2, d.H1, d.H1, d.H1, prm + d.off[3], 1, nullptr, 0, nullptr, 0, h2, d.H2));
+  PTRY(gemm(h, h2, wb + d.off[4], n, d.O, d.H2, d.H2, d.H2, prm + d.off[5], 0, nullptr, 0, h->at<float>(h->L.y), d.O,
+            nullptr, 0));
+  return SEPSO_OK;
+}
+
+// Backward pass after forward(x, n) with targets in t: gradient into grad, the
+// loss added to loss[slot].  n is a multiple of 8 (the K of the weight GEMMs).
+int backward(sepso_prior_ctx* h, const bf16* x, int n, int slot) {
+  const Dims& d = h->d;
+  float* grad = h->at<float>(h->L.grad);
+  bf16 *h1 = h->at<bf16>(h->L.h1), *h2 = h->at<bf16>(h->L.h2);
+  bf16 *dyb = h->at<bf16>(h->L.dyb), *dyT = h->at<bf16>(h->L.dyT);
+  bf16 *h2T = h->at<bf16>(h->L.h2T), *h1T = h->at<bf16>(h->L.h1T), *xT = h->at<bf16>(h->L.xT);
+  bf16 *dh2b = h->at<bf16>(h->L.dh2b), *dh2T = h->at<bf16>(h->L.dh2T);
+  bf16 *dh1b = h->at<bf16>(h->L.dh1b), *dh1T = h->at<bf16>(h->L.dh1T);
+  float *dyf = h->at<float>(h->L.dyf), *dh2f = h->at<float>(h->L.dh2f), *dh1f = h->at<float>(h->L.dh1f);
+  const int tot = n * d.O8;
+  sepso::loss_grad_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(h->at<float>(h->L.y), h->at<float>(h->L.t), n, d.O,
+                                                                    dyf, dyb, d.O8, h->at<float>(h->L.loss) + slot);
+  ++h->launches;
+  PCUDA(cudaGetLastError());
+  PTRY(transpose(h, dyb, n, d.O, d.O8, dyT, n));
+  PTRY(transpose(h, h2, n, d.H2, d.H2, h2T, n));
+  PTRY(transpose(h, h1, n, d.H1, d.H1, h1T, n));
+  PTRY(transpose(h, x, n, d.K, d.K, xT, n));
+  // layer 3: gW3 = dY^T h2, gb3 = colsum dY, dh2 = (dY W3) * [h2 > 0]
+  PTRY(gemm(h, dyT, h2T, d.O, d.H2, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[4], d.H2, nullptr, 0));
+  PTRY(colsum(h, dyf, n, d.O, d.O, grad + d.off[5]));
+  PTRY(gemm(h, dyb, h->at<bf16>(h->L.w3t), n, d.H2, d.O8, d.O8, d.O8, nullptr, 0, h2, d.H2, dh2f, d.H2, dh2b, d.H2));
+  // layer 2
+  PTRY(colsum(h, dh2f, n, d.H2, d.H2, grad + d.off[3]));
+  PTRY(transpose(h, dh2b, n, d.H2, d.H2, dh2T, n));
+  PTRY(gemm(h, dh2T, h1T, d.H2, d.H1, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[2], d.H1, nullptr, 0));
+  PTRY(gemm(h, dh2b, h->at<bf16>(h->L.w2t), n, d.H1, d.H2, d.H2, d.H2, nullptr, 0, h1, d.H1, dh1f, d.H1, dh1b, d.H1));
+  // layer 1
+  PTRY(colsum(h, dh1f, n, d.H1, d.H1, grad + d.off[1]));
+  PTRY(transpose(h, dh1b, n, d.H1, d.H1, dh1T, n));
+  PTRY(gemm(h, dh1T, xT, d.H1, d.K, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[0], d.K, nullptr, 0));
+  return SEPSO_OK;
+}
+
+// BF16 transposed copies of W2 (H1 x H2) and W3 (H2 x O8, columns O.. zero).
+int refresh_transposes(sepso_prior_ctx* h) {
+  const Dims& d = h->d;
+  const bf16* wb = h->at<bf16>(h->L.wb);
+  PTRY(transpose(h, wb + d.off[2], d.H2, d.H1, d.H1, h->at<bf16>(h->L.w2t), d.H2));
+  PTRY(transpose(h, wb + d.off[4], d.O, d.H2, d.H2, h->at<bf16>(h->L.w3t), d.O8));
+  return SEPSO_OK;
+}
+
+int gather(sepso_prior_ctx* h, const int* idx, int first, int n) {
+  const Dims& d = h->d;
+  sepso::gather_kernel<<<n, 256, 0, h->stream>>>(idx, first, n, d.K, h->at<bf16>(h->L.X), h->at<float>(h->L.Y), d.O,
+                                                 h->at<bf16>(h->L.x), h->at<float>(h->L.t));
+  ++h->launches;
+  PCUDA(cudaGetLastError());
+  return SEPSO_OK;
+}
+
+int adam_step(sepso_prior_ctx* h) {
+  const Dims& d = h->d;
+  ++h->step;
+  const double c1 = 1.0 - std::pow((double)h->c.beta1, (double)h->step);
+  const double c2 = 1.0 - std::pow((double)h->c.beta2, (double)h->step);
+  const long long blocks = std::min<long long>((d.P + 255) / 256, 152LL * 16);
+  sepso::adam_kernel<<<(unsigned)blocks, 256, 0, h->stream>>>(
+      h->at<float>(h->L.prm), h->at<float>(h->L.m), h->at<float>(h->L.v), h->at<float>(h->L.grad), h->at<bf16>(h->L.wb),
+      d.P, h->c.lr, h->c.beta1, h->c.beta2, h->c.eps, (float)c1, (float)c2);
+  ++h->launches;
+  PCUDA(cudaGetLastError());
+  return refresh_transposes(h);
+}
+
+int check_rows(const sepso_prior_ctx* h, int first, int n) {
+  if (first < 0 || n < 0 || (long long)first + n > h->c.capacity)
+    return pfail(SEPSO_EINVAL, "rows [%d, %d) outside the dataset's %d rows", first, first + n, h->c.capacity);
+  return SEPSO_OK;
+}
+
+int read_status(sepso_prior_ctx* h) {
+  int st = 0;
+  PCUDA(cudaMemcpyAsync(&st, h->at<int>(h->L.status), 4, cudaMemcpyDeviceToHost, h->stream));
+  PCUDA(cudaStreamSynchronize(h->stream));
+  if (st != 0) {
+    PCUDA(cudaMemsetAsync(h->at<int>(h->L.status), 0, 4, h->stream));
+    PCUDA(cudaStreamSynchronize(h->stream));
+    return pfail(st, "device-side error %d (tensor-core wait timed out)", st);
+  }
+  return SEPSO_OK;
+}
+
+int flush_pending(sepso_prior_ctx* h) {
+  for (const auto& p : h->pending) {
+    const int a = std::min(p.n, kLossRing - p.slot);
+    PCUDA(cudaMemcpyAsync(p.host, h->at<float>(h->L.loss) + p.slot, (size_t)a * 4, cudaMemcpyDeviceToHost, h->stream));
+    if (a < p.n)
+      PCUDA(cudaMemcpyAsync(p.host + a, h->at<float>(h->L.loss), (size_t)(p.n - a) * 4, cudaMemcpyDeviceToHost,
+                            h->stream));
+  }
+  h->pending.clear();
+  PCUDA(cudaStreamSynchronize(h->stream));
+  return SEPSO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sepso_prior_workspace_size(const sepso_prior_config* cfg, size_t* bytes) {
+  Dims d;
+  if (!bytes || !make_dims(cfg, &d)) return pfail(SEPSO_EINVAL, "bad prior configuration");
+  *bytes = layout(cfg, d).total;
+  return SEPSO_OK;
+}
+
+int sepso_prior_create(const sepso_prior_config* cfg, void* d_workspace, size_t bytes, void* stream,
+                       sepso_prior_handle* out) {
+  if (!out) return pfail(SEPSO_EINVAL, "out is NULL");
+  *out = nullptr;
+  Dims d;
+  if (!make_dims(cfg, &d)) return pfail(SEPSO_EINVAL, "bad prior configuration");
+  const PriorLayout L = layout(cfg, d);
+  if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
+    return pfail(SEPSO_ENOSPC, "workspace must be non-NULL and 256-byte aligned");
+  if (bytes < L.total) return pfail(SEPSO_ENOSPC, "workspace of %zu bytes, need %zu", bytes, L.total);
+  sepso_prior_ctx* h = new (std::nothrow) sepso_prior_ctx;
+  if (!h) return pfail(SEPSO_ENOMEM, "host allocation failed");
+  h->c = *cfg;
+  h->d = d;
+  h->L = L;
+  h->ws = static_cast<char*>(d_workspace);
+  h->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return pfail(SEPSO_ECUDA, "workspace clear: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return SEPSO_OK;
+}
+
+void sepso_prior_destroy(sepso_prior_handle h) { delete h; }
+
+int64_t sepso_prior_num_params(sepso_prior_handle h) { return h ? h->d.P : -1; }
+
+int sepso_prior_set_params(sepso_prior_handle h, const float* params) {
+  if (!h || !params) return pfail(SEPSO_EINVAL, "NULL argument");
+  const size_t n = (size_t)h->d.P * 4;
+  PCUDA(cudaMemcpyAsync(h->at<float>(h->L.prm), params, n, cudaMemcpyHostToDevice, h->stream));
+  PCUDA(cudaMemsetAsync(h->at<float>(h->L.m), 0, n, h->stream));
+  PCUDA(cudaMemsetAsync(h->at<float>(h->L.v), 0, n, h->stream));
+  const long long blocks = std::min<long long>((h->d.P + 255) / 256, 152LL * 16);
+  sepso::to_bf16_kernel<<<(unsigned)blocks, 256, 0, h->stream>>>(h->at<float>(h->L.prm), h->at<bf16>(h->L.wb), h->d.P);
+  ++h->launches;
+  PCUDA(cudaGetLastError());
+  PTRY(refresh_transposes(h));
+  h->step = 0;
+  PCUDA(cudaStreamSynchronize(h->stream));
+  return SEPSO_OK;
+}
+
+int sepso_prior_get_params(sepso_prior_handle h, float* params) {
+  if (!h || !params) return pfail(SEPSO_EINVAL, "NULL argument");
+  PCUDA(cudaMemcpyAsync(params, h->at<float>(h->L.prm), (size_t)h->d.P * 4, cudaMemcpyDeviceToHost, h->stream));
+  PCUDA(cudaStreamSynchronize(h->stream));
+  return SEPSO_OK;
+}
+
+int sepso_prior_add_scenes(sepso_prior_handle h, int32_t first, int32_t n, const float* points, const int32_t* counts,
+                           const float* circles, const float* waypoints) {
+  if (!h || (n > 0 && (!points || !counts))) return pfail(SEPSO_EINVAL, "NULL argument");
+  PTRY(check_rows(h, first, n));
+  const Dims& d = h->d;
+  long long total = 0;
+  for (int i = 0; i < n; ++i) {
+    if (counts[i] < 0 || counts[i] > h->c.max_circles)
+      return pfail(SEPSO_EINVAL, "scene %d: %d circles (max %d)", i, counts[i], h->c.max_circles);
+    total += counts[i];
+  }
+  if (total > 0 && !circles) return pfail(SEPSO_EINVAL, "circles is NULL");
+  std::vector<float4> hc;
+  std::vector<int> off;
+  long long c0 = 0;
+  for (int s0 = 0; s0 < n; s0 += d.B) {
+    const int m = std::min(d.B, n - s0);
+    hc.clear();
+    off.assign(1, 0);
+    for (int i = 0; i < m; ++i) {
+      for (int o = 0; o < counts[s0 + i]; ++o) {
+        const float* q = circles + 3 * (c0 + o);
+        hc.push_back(make_float4(q[0], q[1], q[2], 0.0f));
+      }
+      c0 += counts[s0 + i];
+      off.push_back((int)hc.size());
+    }
+    if (!hc.empty())
+      PCUDA(cudaMemcpyAsync(h->at<float4>(h->L.scirc), hc.data(), hc.size() * 16, cudaMemcpyHostToDevice, h->stream));
+    PCUDA(cudaMemcpyAsync(h->at<int>(h->L.scoff), off.data(), off.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    PCUDA(cudaMemcpyAsync(h->at<float>(h->L.P) + 4LL * (first + s0), points + 4LL * s0, (size_t)m * 16,
+                          cudaMemcpyHostToDevice, h->stream));
+    if (waypoints)
+      PCUDA(cudaMemcpyAsync(h->at<float>(h->L.swp), waypoints + (long long)s0 * d.O, (size_t)m * d.O * 4,
+                            cudaMemcpyHostToDevice, h->stream));
+    sepso::RasterArgs a;
+    a.n = m;
+    a.grid = d.g;
+    a.K = d.K;
+    a.T = h->c.T;
+    a.O_max = h->c.max_circles;
+    a.W = h->c.map_w;
+    a.H = h->c.map_h;
+    a.circ = h->at<float4>(h->L.scirc);
+    a.coff = h->at<int>(h->L.scoff);
+    a.pts = h->at<float>(h->L.P) + 4LL * (first + s0);
+    a.wp = waypoints ? h->at<float>(h->L.swp) : nullptr;
+    a.X = h->at<bf16>(h->L.X) + (long long)(first + s0) * d.K;
+    a.Y = h->at<float>(h->L.Y) + (long long)(first + s0) * d.O;
+    const size_t smem = (size_t)std::max(h->c.max_circles, 1) * 16;
+    if (smem > 48 * 1024)
+      PCUDA(cudaFuncSetAttribute(sepso::raster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    sepso::raster_kernel<<<m, 256, smem, h->stream>>>(a);
+    ++h->launches;
+    PCUDA(cudaGetLastError());
+    // the staging buffers are reused by the next chunk
+    PCUDA(cudaStreamSynchronize(h->stream));
+  }
+  return SEPSO_OK;
+}
+
+int sepso_prior_get_rows(sepso_prior_handle h, int32_t first, int32_t n, float* features, float* labels) {
+  if (!h) return pfail(SEPSO_EINVAL, "NULL handle");
+  PTRY(check_rows(h, first, n));
+  const Dims& d = h->d;
+  if (features && n > 0) {
+    std::vector<uint16_t> raw((size_t)n * d.K);
+    PCUDA(cudaMemcpyAsync(raw.data(), h->at<bf16>(h->L.X) + (long long)first * d.K, raw.size() * 2,
+                          cudaMemcpyDeviceToHost, h->stream));
+    PCUDA(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < raw.size(); ++i) {
+      const uint32_t bits = (uint32_t)raw[i] << 16;
+      std::memcpy(&features[i], &bits, 4);
+    }
+  }
+  if (labels && n > 0) {
+    PCUDA(cudaMemcpyAsync(labels, h->at<float>(h->L.Y) + (long long)first * d.O, (size_t)n * d.O * 4,
+                          cudaMemcpyDeviceToHost, h->stream));
+    PCUDA(cudaStreamSynchronize(h->stream));
+  }
+  return SEPSO_OK;
+}
+
+int sepso_prior_forward(sepso_prior_handle h, int32_t first, int32_t n, float* y) {
+  if (!h || !y) return pfail(SEPSO_EINVAL, "NULL argument");
+  PTRY(check_rows(h, first, n));
+  const Dims& d = h->d;
+  for (int s0 = 0; s0 < n; s0 += d.B) {
+    const int m = std::min(d.B, n - s0);
+    PTRY(forward(h, h->at<bf16>(h->L.X) + (long long)(first + s0) * d.K, m));
+    PCUDA(cudaMemcpyAsync(y + (long long)s0 * d.O, h->at<float>(h->L.y), (size_t)m * d.O * 4, cudaMemcpyDeviceToHost,
+                          h->stream));
+    PTRY(read_status(h));
+  }
+  return SEPSO_OK;
+}
+
+int sepso_prior_grad(sepso_prior_handle h, int32_t first, int32_t n, float* grad, float* loss) {
+  if (!h || !grad) return pfail(SEPSO_EINVAL, "NULL argument");
+  PTRY(check_rows(h, first, n));
+  if (n < 8 || (n & 7) || n > h->d.B) return pfail(SEPSO_EINVAL, "rows %d: need a multiple of 8 up to %d", n, h->d.B);
+  const int slot = h->loss_head;
+  h->loss_head = (h->loss_head + 1) % kLossRing;
+  PCUDA(cudaMemsetAsync(h->at<float>(h->L.loss) + slot, 0, 4, h->stream));
+  PTRY(gather(h, nullptr, first, n));
+  PTRY(forward(h, h->at<bf16>(h->L.x), n));
+  PTRY(backward(h, h->at<bf16>(h->L.x), n, slot));
+  PCUDA(cudaMemcpyAsync(grad, h->at<float>(h->L.grad), (size_t)h->d.P * 4, cudaMemcpyDeviceToHost, h->stream));
+  if (loss) PCUDA(cudaMemcpyAsync(loss, h->at<float>(h->L.loss) + slot, 4, cudaMemcpyDeviceToHost, h->stream));
+  return read_status(h);
+}
+
+int sepso_prior_train(sepso_prior_handle h, int32_t n_rows, int32_t first, int32_t steps, int32_t batch,
+                      uint64_t seed, float* losses) {
+  if (!h) return pfail(SEPSO_EINVAL, "NULL handle");
+  if (batch < 8 || (batch & 7) || batch > h->d.B)
+    return pfail(SEPSO_EINVAL, "batch %d: need a multiple of 8 up to %d", batch, h->d.B);
+  if (steps < 0 || (losses && steps > kLossRing)) return pfail(SEPSO_EINVAL, "bad step count %d", steps);
+  if (first >= 0) {
+    PTRY(check_rows(h, first, batch));
+  } else if (n_rows < 1 || n_rows > h->c.capacity) {
+    return pfail(SEPSO_EINVAL, "n_rows %d outside [1, %d]", n_rows, h->c.capacity);
+  }
+  const int slot0 = h->loss_head;
+  for (int s = 0; s < steps; ++s) {
+    const int slot = h->loss_head;
+    h->loss_head = (h->loss_head + 1) % kLossRing;
+    PCUDA(cudaMemsetAsync(h->at<float>(h->L.loss) + slot, 0, 4, h->stream));
+    if (first >= 0) {
+      PTRY(gather(h, nullptr, first, batch));
+    } else {
+      sepso::sample_kernel<<<(batch + 255) / 256, 256, 0, h->stream>>>(h->at<int>(h->L.idx), batch, n_rows,
+                                                                        (uint32_t)seed, (uint32_t)(seed >> 32),
+                                                                        (uint32_t)h->step);
+      ++h->launches;
+      PCUDA(cudaGetLastError());
+      PTRY(gather(h, h->at<int>(h->L.idx), 0, batch));
+    }
+    PTRY(forward(h, h->at<bf16>(h->L.x), batch));
+    PTRY(backward(h, h->at<bf16>(h->L.x), batch, slot));
+    PTRY(adam_step(h));
+  }
+  if (losses && steps > 0) {
+    h->pending.push_back({losses, steps, slot0});
+    PTRY(flush_pending(h));
+  }
+  return SEPSO_OK;
+}
+
+int sepso_prior_infer(sepso_prior_handle h, int32_t first, int32_t n, float* d_out, int32_t ld) {
+  if (!h || (n > 0 && !d_out)) return pfail(SEPSO_EINVAL, "NULL argument");
+  PTRY(check_rows(h, first, n));
+  const Dims& d = h->d;
+  if (ld < d.O) return pfail(SEPSO_EINVAL, "ld %d below 2T = %d", ld, d.O);
+  for (int s0 = 0; s0 < n; s0 += d.B) {
+    const int m = std::min(d.B, n - s0);
+    PTRY(forward(h, h->at<bf16>(h->L.X) + (long long)(first + s0) * d.K, m));
+    const int tot = m * d.O;
+    sepso::decode_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(h->at<float>(h->L.y), m, h->c.T,
+                                                                    h->at<float>(h->L.P) + 4LL * (first + s0),
+                                                                    h->c.map_w, h->c.map_h,
+                                                                    d_out + (long long)s0 * ld, ld);
+    ++h->launches;
+    PCUDA(cudaGetLastError());
+  }
+  return SEPSO_OK;
+}
+
+int sepso_prior_sync(sepso_prior_handle h) {
+  if (!h) return pfail(SEPSO_EINVAL, "NULL handle");
+  PTRY(flush_pending(h));
+  return read_status(h);
+}
+
+int64_t sepso_prior_launch_count(sepso_prior_handle h) { return h ? h->launches : -1; }
+
+const char* sepso_prior_last_error(void) { return g_prior_error.c_str(); }
+
+int sepso_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, int32_t lda, int32_t ldb,
+                    float alpha, const float* bias, int32_t relu, const void* mask, int32_t ldm, float* Cf,
+                    int32_t ldcf, void* Cb, int32_t ldcb, void* stream) {
+  GemmArgs g{};
+  g.A = static_cast<const bf16*>(A);
+  g.B = static_cast<const bf16*>(B);
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.lda = lda;
+  g.ldb = ldb;
+  g.alpha = alpha;
+  g.bias = bias;
+  g.relu = relu;
+  g.mask = static_cast<const bf16*>(mask);
+  g.ldm = ldm;
+  g.Cf = Cf;
+  g.ldcf = ldcf;
+  g.Cb = static_cast<bf16*>(Cb);
+  g.ldcb = ldcb;
+  void* st = nullptr;
+  PCUDA(cudaGetSymbolAddress(&st, g_gemm_status));
+  g.status = static_cast<int*>(st);
+  return gemm_launch(g, static_cast<cudaStream_t>(stream));
+}
+
+int sepso_gemm_bf16_sync(void* stream) {
+  PCUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  int st = 0;
+  PCUDA(cudaMemcpyFromSymbol(&st, g_gemm_status, 4));
+  if (st != 0) {
+    const int zero = 0;
+    PCUDA(cudaMemcpyToSymbol(g_gemm_status, &zero, 4));
+    return pfail(st, "device-side error %d (tensor-core wait timed out)", st);
+  }
+  return SEPSO_OK;
+}
+
+}  // extern "C"

@@ -295,3 +295,51 @@ def poisson_arrivals(seed: int, rate: float, duration: float) -> np.ndarray:
     n = int(rate * duration * 1.2) + 16
     t = np.cumsum(rng.exponential(1.0 / rate, n))
     return t[t < duration]
+
+
+# ----------------------------------------------------------------------------
+# Learned prior: scenes shaped like the dynamic workload, initial weights
+# ----------------------------------------------------------------------------
+
+def prior_scenes(seed: int, n: int, O: int = 64, n_moving: int = 32, W: float = 400.0,
+                 H: float = 400.0) -> dict:
+    """n independent snapshots of the dynamic workload: O circles (centres
+    U[60,340]^2, radii U[10,30]; the last n_moving with velocities U[0.5,2] per
+    cycle in a uniform direction), start (20, 20 + c) and target (380, 380 - c)
+    for a cycle c ~ U{0..359} of the 1-unit vertical drift.  Returns float32
+    arrays points (n, 4), circles (n, O, 3), vel (n, O, 2)."""
+    rng = np.random.default_rng(11000 + seed)
+    circles = np.empty((n, O, 3), np.float32)
+    vel = np.zeros((n, O, 2), np.float32)
+    points = np.empty((n, 4), np.float32)
+    for i in range(n):
+        circles[i] = random_circles(rng, O)
+        sp = rng.uniform(0.5, 2.0, n_moving)
+        ang = rng.uniform(0.0, 2.0 * np.pi, n_moving)
+        vel[i, O - n_moving:, 0] = sp * np.cos(ang)
+        vel[i, O - n_moving:, 1] = sp * np.sin(ang)
+        c = float(rng.integers(0, 360))
+        points[i] = (20.0, 20.0 + c, W - 20.0, H - 20.0 - c)
+    return dict(points=points, circles=circles, vel=vel)
+
+
+def previous_cycle(scenes: dict, cycles: int = 1) -> dict:
+    """The same scenes `cycles` planning cycles earlier (circles moved back along
+    their velocities, start/target drifted back), float32."""
+    c = scenes["circles"].copy()
+    c[..., :2] -= cycles * scenes["vel"]
+    p = scenes["points"].copy()
+    p[:, 1] -= cycles
+    p[:, 3] += cycles
+    return dict(points=p, circles=c, vel=scenes["vel"])
+
+
+def prior_init_params(seed: int, K: int, H1: int, H2: int, O: int, out_scale: float = 0.1) -> np.ndarray:
+    """He-normal W1, W2 (std sqrt(2 / fan_in)), W3 scaled by out_scale (the first
+    proposals stay near the straight line), zero biases; flat float32 in the order
+    W1, b1, W2, b2, W3, b3."""
+    rng = np.random.default_rng(13000 + seed)
+    parts = [rng.normal(0.0, np.sqrt(2.0 / K), H1 * K), np.zeros(H1),
+             rng.normal(0.0, np.sqrt(2.0 / H1), H2 * H1), np.zeros(H2),
+             rng.normal(0.0, out_scale * np.sqrt(2.0 / H2), O * H2), np.zeros(O)]
+    return np.concatenate(parts).astype(np.float32)

@@ -16,7 +16,7 @@ HEADER = Path(__file__).resolve().parents[1] / "include" / "sepso.h"
 def declared_functions():
     text = HEADER.read_text()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sepso_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(sepso_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_library_exports_every_declared_symbol():
