@@ -84,7 +84,8 @@ class _State(ctypes.Structure):
         [(n, _f64p) for n in ("Gb", "Gfit")] + [("GQ", _i32p)] + \
         [(n, _f64p) for n in ("Tb", "Tfit")] + [("TQ", _i32p), ("k", _i32p)] + \
         [("cycle", _i32p), ("has_prev", _i32p), ("prevT", _f64p), ("win", _f64p),
-         ("win_n", _i32p), ("win_head", _i32p), ("stall", _i32p), ("prev_lfv", _f64p)]
+         ("win_n", _i32p), ("win_head", _i32p), ("stall", _i32p), ("prev_lfv", _f64p),
+         ("n_prior", _i32p), ("priorT", _f64p)]
 
 
 class _HsefCfg(ctypes.Structure):
@@ -245,7 +246,8 @@ def window_std(values) -> float:
 # ----------------------------------------------------------------------------
 
 STATE_FIELDS = ("X", "V", "P", "Pfit", "PQ", "Gb", "Gfit", "GQ", "Tb", "Tfit", "TQ", "k",
-                "cycle", "has_prev", "prevT", "win", "win_n", "win_head", "stall", "prev_lfv")
+                "cycle", "has_prev", "prevT", "win", "win_n", "win_head", "stall", "prev_lfv",
+                "n_prior", "priorT")
 
 
 class Swarm:
@@ -265,6 +267,9 @@ class Swarm:
             "cycle": f(1, np.int32), "has_prev": f(1, np.int32), "prevT": f(D), "win": f(tw),
             "win_n": f(1, np.int32), "win_head": f(1, np.int32), "stall": f(1, np.int32),
             "prev_lfv": np.full(1, np.inf),
+            # optional second seed (a learned prior's proposal): n_prior particles per
+            # group start around priorT, before PI's
+            "n_prior": f(1, np.int32), "priorT": f(D),
         }
         self._c = _cfg(cfg)
 

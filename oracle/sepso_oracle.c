@@ -45,7 +45,7 @@
 
 /* Random stream identifiers, carried in the top byte of counter word 2. */
 enum { SO_STREAM_VEL = 0, SO_STREAM_INIT_X = 1, SO_STREAM_INIT_V = 2, SO_STREAM_PI = 3,
-       SO_STREAM_H_INIT_X = 5, SO_STREAM_H_INIT_V = 6, SO_STREAM_H_VEL = 7 };
+       SO_STREAM_PRIOR = 4, SO_STREAM_H_INIT_X = 5, SO_STREAM_H_INIT_V = 6, SO_STREAM_H_VEL = 7 };
 
 void so_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
   uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
@@ -128,6 +128,9 @@ typedef struct {
   int32_t *win_n, *win_head;  /* (1), (1)                                     */
   int32_t *stall;             /* (1) stall counter for AT mode 2              */
   double *prev_lfv;           /* (1)                                          */
+  /* optional second seed of the initialisation (a learned prior's proposal) */
+  int32_t *n_prior;           /* (1) particles per group around priorT, or NULL */
+  double *priorT;             /* (D) or NULL                                  */
 } so_state;
 
 /* ------------------------------------------------------------------------- */
@@ -242,6 +245,9 @@ void so_init_swarm(const so_config* cfg, const double* hyper, so_state* st) {
   const int32_t T = cfg->T, G = cfg->G, N = cfg->N, D = 2 * T;
   const uint32_t cyc = (uint32_t)*st->cycle;
   const int32_t n_pi = (cfg->use_pi && *st->has_prev) ? so_pi_count(cfg->pi_gamma, N) : 0;
+  /* A second seed of the same kind as PI (the learned prior's proposal) takes the
+   * first n_pr particles of each group; PI's particles follow it. */
+  const int32_t n_pr = (st->n_prior != NULL && st->priorT != NULL) ? *st->n_prior : 0;
   for (int32_t g = 0; g < G; ++g) {
     const double vlim = hyper[6 * g + 5];
     for (int32_t n = 0; n < N; ++n) {
@@ -250,7 +256,10 @@ void so_init_swarm(const so_config* cfg, const double* hyper, so_state* st) {
         const double ext = so_extent(cfg, j);
         double u[4];
         double x;
-        if (n < n_pi) {
+        if (n < n_pr) {
+          so_draw4(cfg->seed, (uint32_t)(j / 4), (uint32_t)p, SO_STREAM_PRIOR, cyc, cfg->run_id, u);
+          x = so_clip(st->priorT[j] + (2.0 * u[j % 4] - 1.0) * cfg->pi_h, 0.0, ext);
+        } else if (n < n_pr + n_pi) {
           so_draw4(cfg->seed, (uint32_t)(j / 4), (uint32_t)p, SO_STREAM_PI, cyc, cfg->run_id, u);
           x = so_clip(st->prevT[j] + (2.0 * u[j % 4] - 1.0) * cfg->pi_h, 0.0, ext);
         } else {

@@ -95,6 +95,35 @@ def test_no_pi_without_previous_path_or_when_disabled():
         assert near.sum() == 0
 
 
+def test_learned_seed_takes_the_first_particles_then_pi():
+    # A second seed of PI's kind (Sec. 3.3.3): n_prior particles per group around
+    # priorT (Philox stream 4), then PI's ceil(gamma N) around prevT (stream 3).
+    prevT = np.full(8, 100.0)
+    priorT = np.full(8, 300.0)
+    cfg = SepsoConfig(T=4, G=2, N=16, use_pi=True, pi_gamma=0.25, pi_halfwidth=20.0, seed=9, run_id=2)
+    h = np.tile([1.5, 1.5, 0.0, 0.7, 0.7, 0.05], (2, 1))
+    sw = oracle.Swarm(cfg, h)
+    sw.load({"has_prev": [1], "prevT": prevT, "cycle": [3], "n_prior": [3], "priorT": priorT})
+    sw.init()
+    X = sw.state()["X"].reshape(2, 16, 8)
+    assert np.all(np.abs(X[:, :3] - 300.0) <= 20.0)
+    assert np.all(np.abs(X[:, 3:7] - 100.0) <= 20.0)
+    far = np.all(np.abs(X[:, 7:] - 100.0) > 20.0, axis=2) | np.any(np.abs(X[:, 7:] - 300.0) > 20.0, axis=2)
+    assert far.all()
+    # coordinate j of particle p comes from lane j % 4 of Philox block (j // 4, p, 4 << 24 | cycle, run)
+    g, n, j = 1, 2, 5
+    ctr = np.array([[j // 4, g * 16 + n, (4 << 24) | 3, 2]], np.uint32)
+    u = oracle.u01(int(oracle.philox(ctr, 9)[0, j % 4]))
+    assert X[g, n, j] == pytest.approx(300.0 + (2 * u - 1) * 20.0, abs=1e-12)
+    # without the seed the initialisation is PI's alone
+    sw2 = oracle.Swarm(cfg, h)
+    sw2.load({"has_prev": [1], "prevT": prevT, "cycle": [3]})
+    sw2.init()
+    X2 = sw2.state()["X"].reshape(2, 16, 8)
+    assert np.all(np.abs(X2[:, :4] - 100.0) <= 20.0)
+    np.testing.assert_array_equal(X2[:, 7:], X[:, 7:])
+
+
 # ---------------------------------------------------------------------------
 # Auto Truncation
 # ---------------------------------------------------------------------------
