@@ -219,11 +219,14 @@ int sepso_hsef_best(sepso_handle h, float* hyper_out, float* best_lfv);
 /* ---- many scenes of uneven size in one batch ------------------------------ */
 
 /* One independent DTPSO run per scene (Algorithm 1 with the path fitness of
- * Sec. 3.3.2; no PI, no AT: each scene runs max_iters iterations).  Each launch
- * advances every unfinished scene by one iteration; the whole run is one CUDA
- * graph.  Scenes may differ in T, G, N, O, max_iters, alpha, beta and seed; the
- * map extent is shared.  A scene's result does not depend on the rest of the
- * batch (its random streams are keyed by its seed and run id). */
+ * Sec. 3.3.2).  Each launch advances every unfinished scene by one iteration;
+ * the whole run is one CUDA graph.  Scenes may differ in T, G, N, O, max_iters,
+ * alpha, beta, seed and truncation; the map extent is shared.  Optional per
+ * scene: Auto Truncation by stall counter (Sec. 3.3.4) and warm starts
+ * (sepso_batch_set_starts): Priori Initialization around the scene's previous
+ * path (Sec. 3.3.3) and a second seed of the same kind around a learned prior's
+ * proposal.  A scene's result does not depend on the rest of the batch (its
+ * random streams are keyed by its seed, run id and cycle). */
 typedef struct sepso_batch_ctx* sepso_batch_handle;
 
 typedef struct {
@@ -233,6 +236,14 @@ typedef struct {
   int32_t beta;         /* 1..8                                                         */
   uint64_t seed;        /* Philox key                                                   */
   uint32_t run_id;      /* Philox counter word 3                                        */
+  int32_t stall_iters;  /* 0: run max_iters; else Auto Truncation (Sec. 3.3.4): stop
+                           once Tbest is collision-free and its fitness has not dropped
+                           by more than stall_tol for stall_iters iterations            */
+  float stall_tol;
+  int32_t n_pi;         /* particles per group started around the previous path (PI) */
+  int32_t n_prior;      /* particles per group started around the prior's proposal   */
+  float pi_halfwidth;   /* half-width of both start intervals                         */
+  uint32_t cycle;       /* Philox counter word 2 (low 24 bits): the planning cycle    */
 } sepso_batch_scene;
 
 /* Launch shape: particles per work item (8..256), threads per CTA (64..512, a
@@ -265,9 +276,27 @@ int sepso_batch_get_shape(sepso_batch_handle h, sepso_batch_shape* shape, int32_
 /* Time the candidate shapes (tile 8..64, threads 128..512) over
  * trial_launches iteration launches on the loaded batch and keep the fastest
  * (sync).  best_ms: time of one iteration launch with it.  The batch state is
- * overwritten (a later run starts from scratch). */
+ * overwritten (a later run starts from scratch), the stored previous paths
+ * included: call it before sepso_batch_set_starts. */
 int sepso_batch_autotune(sepso_batch_handle h, int32_t trial_launches, sepso_batch_shape* best,
                          float* best_ms);
+
+/* Warm starts of the next run (sync).  prev, prior: device arrays of row stride
+ * ld floats (ld >= the batch's largest 2T), row s for scene s, waypoint layout
+ * x_0..x_{T-1}, y_0..y_{T-1}; either may be NULL.  prev: the scenes' previous
+ * best paths, the centres of PI (NULL keeps the stored paths: every run stores
+ * each scene's result there, the next cycle's PI centre); n rows of ld floats.  has_prev: n host flags
+ * (a scene without a previous path starts without PI), or NULL (all 1 when prev
+ * is given, else unchanged).  prior: proposals of the learned prior (NULL: none).
+ * A scene's n_prior particles start around its proposal only when the proposal's
+ * fitness (Sec. 3.3.2, FP32) on the scene is below that of its previous path, or
+ * it has none; otherwise the scene starts from PI alone.  The decision is taken
+ * on the device at this call.  Errors: EINVAL, ECUDA. */
+int sepso_batch_set_starts(sepso_batch_handle h, const float* prev, const float* prior, int32_t ld,
+                           const int32_t* has_prev);
+
+/* Number of scenes that will use their prior proposal (host output, sync). */
+int sepso_batch_prior_used(sepso_batch_handle h, int32_t* n_used);
 
 /* Run every scene from initialisation to its max_iters (async).  use_graph != 0
  * replays a CUDA graph of the run (captured at the first call after a shape

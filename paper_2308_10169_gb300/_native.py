@@ -55,7 +55,9 @@ class HsefConfig(ctypes.Structure):
 class BatchScene(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("G", ctypes.c_int32), ("N", ctypes.c_int32),
                 ("O", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("alpha", ctypes.c_float),
-                ("beta", ctypes.c_int32), ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32)]
+                ("beta", ctypes.c_int32), ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32),
+                ("stall_iters", ctypes.c_int32), ("stall_tol", ctypes.c_float), ("n_pi", ctypes.c_int32),
+                ("n_prior", ctypes.c_int32), ("pi_halfwidth", ctypes.c_float), ("cycle", ctypes.c_uint32)]
 
 
 class BatchShape(ctypes.Structure):
@@ -137,6 +139,8 @@ SIGNATURES = {
                                              ctypes.POINTER(_i32)]),
     "sepso_batch_autotune": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(BatchShape),
                                             ctypes.POINTER(ctypes.c_float)]),
+    "sepso_batch_set_starts": (ctypes.c_int, [_vp, _vp, _vp, _i32, ctypes.POINTER(_i32)]),
+    "sepso_batch_prior_used": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "sepso_batch_run_async": (ctypes.c_int, [_vp, _i32]),
     "sepso_batch_read": (ctypes.c_int, [_vp, _fp, ctypes.POINTER(Result)]),
     "sepso_batch_launch_count": (_i64, [_vp]),

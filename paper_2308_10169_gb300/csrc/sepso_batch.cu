@@ -109,23 +109,29 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
   const uint32_t cyc = S.cycle;
   if (jl == 1) {
     // Initialisation (Algorithm 1), with Priori Initialization (Sec. 3.3.3) around
-    // the agent's previous best path when it has one.
+    // the agent's previous best path when it has one, after the first n_pr
+    // particles placed the same way around the learned prior's proposal when the
+    // scene uses it.
     const int n_pi = (S.has_prev && p.agent_prevT != nullptr && S.agent >= 0) ? S.n_pi : 0;
     const float* prevT = (n_pi > 0) ? p.agent_prevT + (long long)S.agent * p.Dmax : nullptr;
+    const int n_pr = (p.prior_path != nullptr && p.prior_use[s] != 0) ? S.n_pr : 0;
+    const float* priT = (n_pr > 0) ? p.prior_path + (long long)s * p.Dmax : nullptr;
     const int nch = (D + 3) >> 2;
     for (int it = tid; it < nl * nch; it += nt) {
       const int i = it / nch, ch = it - i * nch;
       const uint32_t pid = (uint32_t)(g * N + n0 + i);
-      const bool pi = n0 + i < n_pi;
-      const uint4 ux = draw(S.key0, S.key1, (uint32_t)ch, pid, pi ? kStreamPI : kStreamInitX, cyc, run);
+      const int n = n0 + i;
+      const float* ctr = (n < n_pr) ? priT : (n < n_pr + n_pi) ? prevT : nullptr;
+      const uint32_t stream = (n < n_pr) ? kStreamPrior : (n < n_pr + n_pi) ? kStreamPI : kStreamInitX;
+      const uint4 ux = draw(S.key0, S.key1, (uint32_t)ch, pid, stream, cyc, run);
       const uint4 uv = draw(S.key0, S.key1, (uint32_t)ch, pid, kStreamInitV, cyc, run);
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         const int jj = ch * 4 + l;
         if (jj < D) {
           const float ext = (jj < T) ? p.W : p.H;
-          const float x = pi ? fminf(fmaxf(prevT[jj] + (2.0f * lane_of(ux, l) - 1.0f) * S.pi_h, 0.0f), ext)
-                             : lane_of(ux, l) * ext;
+          const float x = ctr ? fminf(fmaxf(ctr[jj] + (2.0f * lane_of(ux, l) - 1.0f) * S.pi_h, 0.0f), ext)
+                              : lane_of(ux, l) * ext;
           sX[i * D + jj] = x;
           sP[i * D + jj] = x;
           sV[i * D + jj] = (2.0f * lane_of(uv, l) - 1.0f) * (vlim * ext);
@@ -373,6 +379,43 @@ cudaError_t launch_batch_iter(const BatchParams& p, int j, int ntiles, int threa
   return cudaGetLastError();
 }
 
+// Learned-prior gate, one warp per scene: the proposal seeds the scene only when
+// its fitness (Sec. 3.3.2, FP32, the swarm's own evaluation) is below that of the
+// scene's previous path, or the scene has none.
+__global__ void batch_gate_kernel(const BatchParams p) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= p.nscenes) return;  // warp-uniform
+  const int s = warp;
+  const BatchScene S = p.sc[s];
+  int32_t* use = const_cast<int32_t*>(p.prior_use);
+  if (S.n_pr == 0) {
+    if (lane == 0) use[s] = 0;
+    return;
+  }
+  const float sx = p.pts[4 * s], sy = p.pts[4 * s + 1], tx = p.pts[4 * s + 2], ty = p.pts[4 * s + 3];
+  const int split = warp_split(S.T, S.O);
+  const float4* circ = p.circ + S.co;
+  float len;
+  int q;
+  group_fitness(p.prior_path + (long long)s * p.Dmax, true, 32, S.T, split, S.O, sx, sy, tx, ty, circ, &len, &q);
+  const float f_prior = len + S.alpha * powi((float)q, S.beta);
+  int ok = 1;
+  if (S.has_prev && S.n_pi > 0) {
+    group_fitness(p.agent_prevT + (long long)s * p.Dmax, true, 32, S.T, split, S.O, sx, sy, tx, ty, circ, &len, &q);
+    const float f_prev = len + S.alpha * powi((float)q, S.beta);
+    ok = f_prior < f_prev;
+  }
+  if (lane == 0) use[s] = ok;
+}
+
+cudaError_t launch_batch_gate(const BatchParams& p, cudaStream_t s) {
+  const int threads = 128;
+  const int blocks = (p.nscenes * 32 + threads - 1) / threads;
+  batch_gate_kernel<<<blocks, threads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace sepso
 
 using namespace sepso;
@@ -407,8 +450,8 @@ constexpr int kMinTile = 8;
 
 struct BatchLayout {
   size_t sc, tiles, X, V, P, Pfit, PQ, slots, Gb, Tb, circ, hyper, pts, words, Gfit2, GQ2, Tfit2, TQ2, res_wp, res,
-      status, total;
-  long long nX, nM, nS, nG, nT, nC, nH, nW, nGS, ntiles_max;
+      stall2, plv2, done, prevT, priorT, prior_use, status, total;
+  long long nX, nM, nS, nG, nT, nC, nH, nW, nGS, ntiles_max, Dmax;
 };
 
 int check_scenes(const sepso_batch_scene* sc, int32_t n) {
@@ -418,6 +461,9 @@ int check_scenes(const sepso_batch_scene* sc, int32_t n) {
     if (c.T < 1 || c.T > 64 || c.G < 1 || c.G > 32 || c.N < 1 || c.N >= (1 << 20) || c.O < 0 || c.O > 8192 ||
         c.max_iters < 1 || c.beta < 1 || c.beta > 8 || !std::isfinite(c.alpha) || c.alpha < 0)
       return bfail(SEPSO_EINVAL, "scene %d: bad shape or parameters", s);
+    if (c.stall_iters < 0 || !std::isfinite(c.stall_tol) || c.stall_tol < 0 || c.n_pi < 0 || c.n_prior < 0 ||
+        c.n_pi > c.N || c.n_prior > c.N || !std::isfinite(c.pi_halfwidth) || c.pi_halfwidth < 0)
+      return bfail(SEPSO_EINVAL, "scene %d: bad truncation or warm-start parameters", s);
   }
   return SEPSO_OK;
 }
@@ -436,6 +482,7 @@ BatchLayout batch_layout(const sepso_batch_scene* sc, int32_t n) {
     L.nW += 3LL * sc[s].G;
     L.nGS += 2LL * sc[s].G;
     L.ntiles_max += (long long)sc[s].G * ((sc[s].N + kMinTile - 1) / kMinTile);
+    L.Dmax = std::max(L.Dmax, D);
   }
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -464,6 +511,12 @@ BatchLayout batch_layout(const sepso_batch_scene* sc, int32_t n) {
   L.TQ2 = take((size_t)n * 8);
   L.res_wp = take((size_t)L.nT * 4);
   L.res = take((size_t)n * sizeof(sepso_result));
+  L.stall2 = take((size_t)n * 8);
+  L.plv2 = take((size_t)n * 8);
+  L.done = take((size_t)n * 4);
+  L.prevT = take((size_t)n * L.Dmax * 4);
+  L.priorT = take((size_t)n * L.Dmax * 4);
+  L.prior_use = take((size_t)n * 4);
   L.status = take(4);
   L.total = al256(off);
   return L;
@@ -530,10 +583,12 @@ BatchParams batch_params(const sepso_batch_ctx* h) {
   p.res_wp = h->at<float>(h->L.res_wp);
   p.res = h->at<sepso_result>(h->L.res);
   p.status = h->at<int>(h->L.status);
-  p.stall2 = nullptr;
-  p.plv2 = nullptr;
-  p.done = nullptr;
-  p.agent_prevT = nullptr;
+  p.stall2 = h->at<int32_t>(h->L.stall2);
+  p.plv2 = h->at<float>(h->L.plv2);
+  p.done = h->at<int32_t>(h->L.done);
+  p.agent_prevT = h->at<float>(h->L.prevT);
+  p.prior_path = h->at<float>(h->L.priorT);
+  p.prior_use = h->at<int32_t>(h->L.prior_use);
   return p;
 }
 
@@ -674,12 +729,13 @@ int sepso_batch_create(const sepso_batch_scene* scenes, int32_t n, float map_w, 
     d.wo = wo; wo += 3LL * d.G;
     d.gso = gso; gso += 2LL * d.G;
     d.j0 = 0;
-    d.at_stall = 0;
-    d.stall_tol = 0.0f;
-    d.n_pi = 0;
-    d.pi_h = 0.0f;
-    d.cycle = 0;
-    d.agent = -1;
+    d.at_stall = c.stall_iters;
+    d.stall_tol = c.stall_tol;
+    d.n_pi = c.n_pi;
+    d.n_pr = c.n_prior;
+    d.pi_h = c.pi_halfwidth;
+    d.cycle = c.cycle;
+    d.agent = s;  // row of the scene's previous path (PI centre, written by every run)
     d.has_prev = 0;
     h->Omax = std::max(h->Omax, c.O);
     h->Dmax = std::max(h->Dmax, 2 * c.T);
@@ -786,6 +842,43 @@ int sepso_batch_autotune(sepso_batch_handle h, int32_t trial_launches, sepso_bat
   if (best) *best = win;
   if (best_ms) *best_ms = win_ms / (float)(trials - 1);
   (void)keep;
+  return SEPSO_OK;
+}
+
+int sepso_batch_set_starts(sepso_batch_handle h, const float* prev, const float* prior, int32_t ld,
+                           const int32_t* has_prev) {
+  if (!h) return bfail(SEPSO_EINVAL, "NULL handle");
+  const long long Dm = h->L.Dmax;
+  if ((prev || prior) && ld < Dm) return bfail(SEPSO_EINVAL, "ld %d below the largest 2T (%lld)", ld, Dm);
+  if (prev)
+    BCUDA(cudaMemcpy2DAsync(h->ws + h->L.prevT, (size_t)Dm * 4, prev, (size_t)ld * 4, (size_t)Dm * 4, (size_t)h->n,
+                            cudaMemcpyDeviceToDevice, h->stream));
+  if (has_prev || prev) {
+    for (int s = 0; s < h->n; ++s) h->desc[s].has_prev = has_prev ? (has_prev[s] != 0) : 1;
+    BCUDA(cudaMemcpyAsync(h->ws + h->L.sc, h->desc.data(), h->desc.size() * sizeof(BatchScene),
+                          cudaMemcpyHostToDevice, h->stream));
+  }
+  if (prior) {
+    BCUDA(cudaMemcpy2DAsync(h->ws + h->L.priorT, (size_t)Dm * 4, prior, (size_t)ld * 4, (size_t)Dm * 4,
+                            (size_t)h->n, cudaMemcpyDeviceToDevice, h->stream));
+    if (!h->inputs) return bfail(SEPSO_ESTATE, "the prior gate needs the scenes' inputs (set_inputs first)");
+    BCUDA(launch_batch_gate(batch_params(h), h->stream));
+    ++h->launches;
+  } else {
+    BCUDA(cudaMemsetAsync(h->ws + h->L.prior_use, 0, (size_t)h->n * 4, h->stream));
+  }
+  BCUDA(cudaStreamSynchronize(h->stream));
+  return SEPSO_OK;
+}
+
+int sepso_batch_prior_used(sepso_batch_handle h, int32_t* n_used) {
+  if (!h || !n_used) return bfail(SEPSO_EINVAL, "NULL argument");
+  std::vector<int32_t> u((size_t)h->n);
+  BCUDA(cudaMemcpyAsync(u.data(), h->ws + h->L.prior_use, u.size() * 4, cudaMemcpyDeviceToHost, h->stream));
+  BCUDA(cudaStreamSynchronize(h->stream));
+  int32_t c = 0;
+  for (int32_t v : u) c += v != 0;
+  *n_used = c;
   return SEPSO_OK;
 }
 

@@ -27,6 +27,7 @@ struct BatchScene {
   int at_stall;    // 0: run max_iters; else Auto Truncation by stall counter with this limit
   float stall_tol;
   int n_pi;        // particles per group placed by Priori Initialization (when agent has_prev)
+  int n_pr;        // particles per group placed around the learned prior's proposal (when used)
   float pi_h;      // half-width of the PI interval
   uint32_t cycle;  // Philox counter word 2 (low 24 bits): the agent's planning cycle
   int agent;       // row of the warm-start table (-1: none)
@@ -59,6 +60,9 @@ struct BatchParams {
   float* plv2;         // 2 per scene: previous LFV, by parity
   int32_t* done;       // 1 per scene: set when the scene's plan has finished
   float* agent_prevT;  // warm-start table: Dmax floats per agent
+  // Learned prior (null for the server):
+  const float* prior_path;   // Dmax floats per scene: the prior's proposal
+  const int32_t* prior_use;  // 1 per scene: the proposal seeds the scene's first n_pr particles
 };
 
 struct BatchSmem {
@@ -88,5 +92,6 @@ struct BatchSmem {
 cudaError_t batch_configure(int* smem_optin_out);
 cudaError_t launch_batch_reset(const BatchParams& p, cudaStream_t s);
 cudaError_t launch_batch_iter(const BatchParams& p, int j, int ntiles, int threads, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_gate(const BatchParams& p, cudaStream_t s);
 
 }  // namespace sepso

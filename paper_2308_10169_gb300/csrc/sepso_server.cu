@@ -265,6 +265,8 @@ struct sepso_server_ctx {
     p.plv2 = at<float>(L.plv2);
     p.done = at<int32_t>(L.done);
     p.agent_prevT = at<float>(L.prevT);
+    p.prior_path = nullptr;
+    p.prior_use = nullptr;
     return p;
   }
 };
@@ -338,6 +340,7 @@ int admit(sepso_server_ctx* h, int b) {
     d.at_stall = c.stall_iters;
     d.stall_tol = c.stall_tol;
     d.n_pi = (int)std::min<double>(std::max(std::ceil((double)c.pi_gamma * c.N), 0.0), (double)c.N);
+    d.n_pr = 0;
     d.pi_h = c.pi_halfwidth;
     d.cycle = (uint32_t)h->agent_cycle[r.agent];
     d.agent = r.agent;

@@ -231,16 +231,28 @@ class BatchSceneSpec:
     beta: int = 4
     seed: int = 0
     run_id: int = 0
+    stall_iters: int = 0      # 0: no Auto Truncation; else stall-counter AT (Sec. 3.3.4)
+    stall_tol: float = 0.0
+    n_pi: int = 0             # particles per group around the previous path (PI)
+    n_prior: int = 0          # particles per group around the learned prior's proposal
+    pi_halfwidth: float = 20.0
+    cycle: int = 0
 
     @property
     def D(self) -> int:
         return 2 * self.T
 
-    def config(self, map_w: float = 400.0, map_h: float = 400.0) -> SepsoConfig:
-        """The equivalent single-scene configuration (no PI, no AT)."""
+    def config(self, map_w: float = 400.0, map_h: float = 400.0, pi_gamma: float | None = None) -> SepsoConfig:
+        """The equivalent single-scene configuration.  PI is on when n_pi > 0, with the
+        gamma whose ceil(gamma N) is n_pi; AT is the stall counter when stall_iters > 0."""
+        use_pi = self.n_pi > 0
+        g = pi_gamma if pi_gamma is not None else ((self.n_pi - 0.5) / self.N if use_pi else 0.0)
         return SepsoConfig(T=self.T, G=self.G, N=self.N, max_obstacles=max(self.O, 1),
                            map_w=map_w, map_h=map_h, alpha=self.alpha, beta=self.beta,
-                           max_iters=self.max_iters, at_mode=AT_OFF, use_pi=False,
+                           max_iters=self.max_iters,
+                           at_mode=AT_STALL if self.stall_iters > 0 else AT_OFF,
+                           stall_iters=max(self.stall_iters, 1), stall_tol=self.stall_tol,
+                           use_pi=use_pi, pi_gamma=g, pi_halfwidth=self.pi_halfwidth,
                            seed=self.seed, run_id=self.run_id)
 
 

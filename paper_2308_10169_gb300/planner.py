@@ -228,7 +228,9 @@ class BatchPlanner:
         arr = (BatchScene * self.n)()
         for i, sp in enumerate(self.specs):
             arr[i] = BatchScene(T=sp.T, G=sp.G, N=sp.N, O=sp.O, max_iters=sp.max_iters,
-                                alpha=sp.alpha, beta=sp.beta, seed=sp.seed, run_id=sp.run_id)
+                                alpha=sp.alpha, beta=sp.beta, seed=sp.seed, run_id=sp.run_id,
+                                stall_iters=sp.stall_iters, stall_tol=sp.stall_tol, n_pi=sp.n_pi,
+                                n_prior=sp.n_prior, pi_halfwidth=sp.pi_halfwidth, cycle=sp.cycle)
         self._arr = arr
         size = ctypes.c_size_t()
         check_batch(self.lib.sepso_batch_workspace_size(arr, self.n, ctypes.byref(size)))
@@ -276,6 +278,34 @@ class BatchPlanner:
         self._check(self.lib.sepso_batch_autotune(self._h, trial_launches, ctypes.byref(sh),
                                                   ctypes.byref(ms)))
         return {"tile": sh.tile, "threads": sh.threads, "lanes": sh.lanes}, float(ms.value)
+
+    @property
+    def Dmax(self) -> int:
+        return max(self.D)
+
+    def set_starts(self, prev: torch.Tensor | None = None, prior: torch.Tensor | None = None,
+                   has_prev=None):
+        """Warm starts of the next run: device tensors (n, >= Dmax) of previous paths
+        (PI centres) and/or learned-prior proposals; has_prev: n flags."""
+        ld = None
+        for t in (prev, prior):
+            if t is not None:
+                assert t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.stride(1) == 1
+                assert t.shape[0] >= self.n and t.shape[1] >= self.Dmax
+                assert ld is None or ld == t.stride(0), "prev and prior need the same row stride"
+                ld = t.stride(0)
+        hp = None
+        if has_prev is not None:
+            hp = np.ascontiguousarray(np.asarray(has_prev, np.int32).reshape(self.n))
+        self._check(self.lib.sepso_batch_set_starts(
+            self._h, ctypes.c_void_p(prev.data_ptr()) if prev is not None else None,
+            ctypes.c_void_p(prior.data_ptr()) if prior is not None else None, ld or self.Dmax,
+            hp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if hp is not None else None))
+
+    def prior_used(self) -> int:
+        n = ctypes.c_int32()
+        self._check(self.lib.sepso_batch_prior_used(self._h, ctypes.byref(n)))
+        return n.value
 
     def run_async(self, use_graph: bool = True):
         self._check(self.lib.sepso_batch_run_async(self._h, int(use_graph)))

@@ -111,3 +111,133 @@ def test_full_size_batch_shapes_sampled_against_oracle(native):
                                   res[s]["waypoints"])
         assert res[s]["Q"] == Q[0]
         assert res[s]["cost"] == pytest.approx(F[0], rel=1e-4)
+
+
+def _warm_batch(iters, seed=3, stall=0, tol=0.0):
+    """The small batch with warm starts: PI for scenes with a previous path, and a
+    learned-prior seed, half of the proposals close to the previous path."""
+    specs, hyper, points, circles = _small_batch(iters, seed=seed)
+    rng = np.random.default_rng(900 + seed)
+    n = len(specs)
+    for i, sp in enumerate(specs):
+        sp.n_pi = (sp.N + 3) // 4
+        sp.n_prior = [0, 1, (sp.N + 2) // 3][i % 3]
+        sp.cycle = 3 + i
+        sp.pi_halfwidth = 15.0
+        sp.stall_iters = stall
+        sp.stall_tol = tol
+    Dmax = max(sp.D for sp in specs)
+    prev = np.zeros((n, Dmax), np.float32)
+    prior = np.zeros((n, Dmax), np.float32)
+    for i, sp in enumerate(specs):
+        T = sp.T
+        line = np.concatenate([np.linspace(20, 380, T + 2)[1:-1], np.linspace(20, 380, T + 2)[1:-1]])
+        prev[i, :sp.D] = np.clip(line + rng.normal(0, 40, sp.D), 0, 400)
+        prior[i, :sp.D] = np.clip((prev[i, :sp.D] if i % 2 else line) + rng.normal(0, 10, sp.D), 0, 400)
+    has_prev = np.array([0 if i % 4 == 1 else 1 for i in range(n)], np.int32)
+    return specs, hyper, points, circles, prev, prior, has_prev
+
+
+def _oracle_gate(sp, pts, circ, prev_row, prior_row, hp):
+    """(use the proposal, ambiguous): fitness of the proposal below the previous path's."""
+    if sp.n_prior == 0:
+        return False, False
+    if not (hp and sp.n_pi > 0):
+        return True, False
+    sc = oracle.Scene(pts[:2], pts[2:], circ)
+    f, _, _ = oracle.evaluate(sp.config(), sc, np.stack([prior_row[:sp.D], prev_row[:sp.D]]))
+    return bool(f[0] < f[1]), abs(f[0] - f[1]) <= 1e-3 * max(abs(f[1]), 1.0)
+
+
+def _oracle_warm(sp, hyper, pts, circ, prev_row, prior_row, hp, use):
+    sw = oracle.Swarm(sp.config(), hyper)
+    st = {"has_prev": [hp], "prevT": prev_row[:sp.D], "cycle": [sp.cycle]}
+    if use:
+        st.update({"n_prior": [sp.n_prior], "priorT": prior_row[:sp.D]})
+    sw.load(st)
+    return sw.plan(oracle.Scene(pts[:2], pts[2:], circ))
+
+
+@pytest.mark.parametrize("iters", [1, 2])
+def test_batch_warm_starts_match_oracle(native, iters):
+    import torch
+    specs, hyper, points, circles, prev, prior, has_prev = _warm_batch(iters)
+    bp = BatchPlanner(specs)
+    bp.set_inputs(hyper, points, circles)
+    bp.set_starts(prev=torch.from_numpy(prev).cuda(), prior=torch.from_numpy(prior).cuda(), has_prev=has_prev)
+    res = bp.run(use_graph=False)
+    n_use = 0
+    for s, r in enumerate(res):
+        use, ambiguous = _oracle_gate(specs[s], points[s], circles[s], prev[s], prior[s], has_prev[s])
+        n_use += use
+        if ambiguous:
+            continue
+        o = _oracle_warm(specs[s], hyper[s], points[s], circles[s], prev[s], prior[s], has_prev[s], use)
+        assert r["iters"] == o["iters"] == iters
+        assert r["Q"] == o["Q"], s
+        assert r["cost"] == pytest.approx(o["cost"], rel=1e-4), s
+        np.testing.assert_allclose(r["waypoints"], o["waypoints"], rtol=1e-5, atol=4e-3)
+    assert bp.prior_used() == n_use
+    assert 0 < n_use < len(specs)
+
+
+def test_batch_stores_results_as_next_pi_centres(native):
+    # set_starts without prev keeps the stored paths: each scene's last result
+    import torch
+    specs, hyper, points, circles, prev, prior, has_prev = _warm_batch(4, seed=4)
+    bp = BatchPlanner(specs)
+    bp.set_inputs(hyper, points, circles)
+    bp.set_starts(prev=torch.from_numpy(prev).cuda(), has_prev=has_prev)
+    first = bp.run(use_graph=True)
+    bp.set_starts(has_prev=np.ones(len(specs), np.int32))
+    second = bp.run(use_graph=True)
+    for s, sp in enumerate(specs):
+        o = _oracle_warm(sp, hyper[s], points[s], circles[s], first[s]["waypoints"], prior[s], 1, False)
+        assert second[s]["Q"] == o["Q"], s
+        assert second[s]["cost"] == pytest.approx(o["cost"], rel=1e-3), s
+
+
+def test_batch_stall_truncation(native):
+    # Auto Truncation by stall counter in the batch (Sec. 3.3.4): scenes stop early
+    # once their best path is collision-free and stalls, and truncation does not
+    # change the trajectory (the same scene run for exactly that many iterations
+    # without AT gives the same result); median cost over 48 scenes within 2% of the
+    # oracle's (FP32 and FP64 trajectories separate over many iterations).
+    import torch
+    rng = np.random.default_rng(77)
+    n = 48
+    specs, hyper, circles = [], [], []
+    for i in range(n):
+        specs.append(BatchSceneSpec(T=8, G=3, N=12, O=6, max_iters=150, alpha=30.0, beta=4, seed=5, run_id=i,
+                                    stall_iters=10, stall_tol=1.0, n_pi=3, pi_halfwidth=20.0, cycle=1))
+        hyper.append(sample_hyper(300 + i, 3))
+        circles.append(random_circles(rng, 6, lo=20, hi=380, r_lo=5, r_hi=25))
+    points = np.tile(np.array([[20, 20, 380, 380]], np.float32), (n, 1))
+    prev = np.clip(np.linspace(40, 360, 16)[None, :] + rng.normal(0, 30, (n, 16)), 0, 400).astype(np.float32)
+    prev[:, 8:] = prev[:, :8]
+    bp = BatchPlanner(specs)
+    bp.set_inputs(hyper, points, circles)
+    bp.set_starts(prev=torch.from_numpy(prev).cuda())
+    res = bp.run()
+    its = np.array([r["iters"] for r in res])
+    assert np.median(its) < 150
+    for r in res:
+        if r["iters"] < 150:
+            assert r["Q"] == 0
+    # truncation keeps the trajectory
+    for s in (0, 5, 11):
+        k = int(its[s])
+        sp = BatchSceneSpec(**{**specs[s].__dict__, "stall_iters": 0, "max_iters": k})
+        one = BatchPlanner([sp])
+        one.set_inputs([hyper[s]], points[s:s + 1], [circles[s]])
+        one.set_starts(prev=torch.from_numpy(prev[s:s + 1]).cuda())
+        r1 = one.run()[0]
+        assert r1["cost"] == res[s]["cost"] and r1["iters"] == k
+        np.testing.assert_array_equal(r1["waypoints"], res[s]["waypoints"])
+    ora = []
+    for s, sp in enumerate(specs):
+        sw = oracle.Swarm(sp.config(), hyper[s])
+        sw.load({"has_prev": [1], "prevT": prev[s], "cycle": [1]})
+        ora.append(sw.plan(oracle.Scene(points[s, :2], points[s, 2:], circles[s]))["cost"])
+    gpu = [r["cost"] for r in res]
+    assert abs(np.median(gpu) - np.median(ora)) <= 0.02 * np.median(ora)
