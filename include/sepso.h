@@ -480,6 +480,11 @@ int sepso_prior_get_params(sepso_prior_handle h, float* params);
 int sepso_prior_add_scenes(sepso_prior_handle h, int32_t first, int32_t n, const float* points,
                            const int32_t* counts, const float* circles, const float* waypoints);
 
+/* Replace the labels of rows [first, first + n) (already added) by the paths in
+ * the device array d_waypoints (n rows of stride ld >= 2T), encoded on the
+ * device (async).  Errors: EINVAL, ECUDA. */
+int sepso_prior_set_labels(sepso_prior_handle h, int32_t first, int32_t n, const float* d_waypoints, int32_t ld);
+
 /* Read dataset rows back (host outputs, sync; either may be NULL): features as
  * FP32 (n x K), labels (n x 2T).  Errors: EINVAL, ECUDA. */
 int sepso_prior_get_rows(sepso_prior_handle h, int32_t first, int32_t n, float* features, float* labels);

@@ -169,6 +169,7 @@ SIGNATURES = {
     "sepso_prior_set_params": (ctypes.c_int, [_vp, _fp]),
     "sepso_prior_get_params": (ctypes.c_int, [_vp, _fp]),
     "sepso_prior_add_scenes": (ctypes.c_int, [_vp, _i32, _i32, _fp, ctypes.POINTER(_i32), _fp, _fp]),
+    "sepso_prior_set_labels": (ctypes.c_int, [_vp, _i32, _i32, _vp, _i32]),
     "sepso_prior_get_rows": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp]),
     "sepso_prior_forward": (ctypes.c_int, [_vp, _i32, _i32, _fp]),
     "sepso_prior_grad": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp]),

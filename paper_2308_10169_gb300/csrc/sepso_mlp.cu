@@ -310,6 +310,20 @@ __global__ void __launch_bounds__(256) raster_kernel(const RasterArgs a) {
   }
 }
 
+// Labels of rows from device waypoints (row stride ld): the same encoding as above.
+__global__ void label_kernel(const float* __restrict__ wp, int ld, int n, int T, const float* __restrict__ pts,
+                             float W, float H, float* __restrict__ Y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * 2 * T) return;
+  const int s = i / (2 * T), d = i - s * 2 * T;
+  const int k = d < T ? d : d - T;
+  const float f = (float)(k + 1) / (float)(T + 1);
+  const float* p = pts + 4 * s;
+  const float s0 = d < T ? p[0] : p[1], t0 = d < T ? p[2] : p[3];
+  const float ext = d < T ? W : H;
+  Y[i] = (wp[(size_t)s * ld + d] - (s0 + f * (t0 - s0))) / ext;
+}
+
 // Minibatch rows: idx[b] = Philox(seed; step, b) mod n_rows (with replacement).
 __global__ void sample_kernel(int* idx, int B, int n_rows, uint32_t k0, uint32_t k1, uint32_t step) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -856,6 +870,20 @@ int sepso_prior_add_scenes(sepso_prior_handle h, int32_t first, int32_t n, const
     // the staging buffers are reused by the next chunk
     PCUDA(cudaStreamSynchronize(h->stream));
   }
+  return SEPSO_OK;
+}
+
+int sepso_prior_set_labels(sepso_prior_handle h, int32_t first, int32_t n, const float* d_waypoints, int32_t ld) {
+  if (!h || (n > 0 && !d_waypoints)) return pfail(SEPSO_EINVAL, "NULL argument");
+  PTRY(check_rows(h, first, n));
+  if (ld < h->d.O) return pfail(SEPSO_EINVAL, "ld %d below 2T = %d", ld, h->d.O);
+  if (n == 0) return SEPSO_OK;
+  const int tot = n * h->d.O;
+  sepso::label_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(d_waypoints, ld, n, h->c.T,
+                                                                 h->at<float>(h->L.P) + 4LL * first, h->c.map_w,
+                                                                 h->c.map_h, h->at<float>(h->L.Y) + (long long)first * h->d.O);
+  ++h->launches;
+  PCUDA(cudaGetLastError());
   return SEPSO_OK;
 }
 

@@ -87,6 +87,13 @@ class Prior:
             self._h, first, n, _native.fptr(pts), counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
             _native.fptr(flat) if flat.size else None, _native.fptr(wp)))
 
+    def set_labels(self, first: int, waypoints: torch.Tensor) -> None:
+        """Relabel rows [first, first + n) with the paths of a device tensor (n, >= 2T)."""
+        assert waypoints.is_cuda and waypoints.dtype == torch.float32 and waypoints.stride(1) == 1
+        check_prior(_native.lib().sepso_prior_set_labels(self._h, first, waypoints.shape[0],
+                                                         ctypes.c_void_p(waypoints.data_ptr()),
+                                                         waypoints.stride(0)))
+
     def get_rows(self, first: int, n: int):
         f = np.empty((n, self.K), np.float32)
         y = np.empty((n, self.O), np.float32)
@@ -152,3 +159,168 @@ def gemm_bf16(A: torch.Tensor, B: torch.Tensor, alpha: float = 1.0, bias: torch.
     if sync:
         check_prior(_native.lib().sepso_gemm_bf16_sync(vp(stream)))
     return Cf, Cb
+
+
+# ----------------------------------------------------------------------------
+# Pipeline: SEPSO solutions as labels, training, held-out comparison
+# ----------------------------------------------------------------------------
+
+def plan_scenes(scenes: dict, T: int = 20, G: int = 8, N: int = 170, hyper=None, max_iters: int = 300,
+                stall_iters: int = 10, stall_tol: float = 0.0, seed: int = 0, run0: int = 0, cycle: int = 0,
+                prev: torch.Tensor | None = None, prior: torch.Tensor | None = None, n_pi: int = 0,
+                n_prior: int = 0, pi_halfwidth: float = 20.0, chunk: int = 8192, shape=None, device=None) -> dict:
+    """Plan every scene (points (n,4), circles (n,O,3)) with the batch planner in
+    chunks: Algorithm 1 with stall-counter Auto Truncation, PI around prev (rows of
+    a device tensor, n_pi particles per group) and the learned seed around prior
+    (n_prior particles).  Returns waypoints (device tensor (n, 2T)), cost, iters, Q
+    (numpy), the launch shape used and the device seconds of the runs."""
+    from .inputs import TABLE_HYPER8_PATH, BatchSceneSpec
+    from .planner import BatchPlanner
+
+    hy = np.asarray(TABLE_HYPER8_PATH if hyper is None else hyper, np.float32)[:G]
+    pts, circ = scenes["points"], scenes["circles"]
+    n, O = pts.shape[0], circ.shape[1]
+    dev = _dev(device)
+    wp = torch.empty((n, 2 * T), dtype=torch.float32, device=dev)
+    cost, iters, Q = np.empty(n, np.float32), np.empty(n, np.int32), np.empty(n, np.int32)
+    secs = 0.0
+    used = 0
+    for c0 in range(0, n, chunk):
+        m = min(chunk, n - c0)
+        specs = [BatchSceneSpec(T=T, G=G, N=N, O=O, max_iters=max_iters, alpha=30.0, beta=4, seed=seed,
+                                run_id=run0 + c0 + i, stall_iters=stall_iters, stall_tol=stall_tol,
+                                n_pi=n_pi if prev is not None else 0,
+                                n_prior=n_prior if prior is not None else 0, pi_halfwidth=pi_halfwidth,
+                                cycle=cycle) for i in range(m)]
+        bp = BatchPlanner(specs, device=dev)
+        bp.set_inputs([hy] * m, pts[c0:c0 + m], [circ[c0 + i] for i in range(m)])
+        if shape is None:
+            shape, _ = bp.autotune(trial_launches=3)
+        else:
+            bp.set_shape(shape["tile"], shape["threads"])
+        if prev is not None or prior is not None:
+            bp.set_starts(prev=prev[c0:c0 + m] if prev is not None else None,
+                          prior=prior[c0:c0 + m] if prior is not None else None)
+            if prior is not None:
+                used += bp.prior_used()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(bp.stream)
+        bp.run_async(use_graph=True)
+        ev1.record(bp.stream)
+        res = bp.read()
+        secs += ev0.elapsed_time(ev1) / 1e3
+        wp[c0:c0 + m] = torch.from_numpy(np.stack([r["waypoints"] for r in res])).to(dev)
+        cost[c0:c0 + m] = [r["cost"] for r in res]
+        iters[c0:c0 + m] = [r["iters"] for r in res]
+        Q[c0:c0 + m] = [r["Q"] for r in res]
+        bp.close()
+    return dict(waypoints=wp, cost=cost, iters=iters, Q=Q, shape=shape, seconds=secs,
+                prior_used=used if prior is not None else None)
+
+
+def fit_prior(prior: Prior, scenes: dict, rounds: int = 3, epochs: int = 30, batch: int = 1024, seed: int = 0,
+              n_prior: int = 43, shape=None, **plan_kw) -> dict:
+    """Train the prior on SEPSO solutions the planner itself generates, in rounds:
+    the first labels are plain SEPSO plans of the scenes; after each training phase
+    the scenes are planned again with the prior's proposals as a second seed, and a
+    scene's label becomes the new plan when its cost is lower.  Scenes occupy rows
+    [0, n).  Returns the label costs per round, the losses and timings."""
+    n = scenes["points"].shape[0]
+    prior.add_scenes(0, scenes["points"], [scenes["circles"][i] for i in range(n)])
+    lab = plan_scenes(scenes, seed=seed, run0=0, shape=shape, **plan_kw)
+    shape = lab["shape"]
+    labels, cost = lab["waypoints"], lab["cost"]
+    hist = dict(label_cost=[float(np.median(cost))], label_iters=[float(np.mean(lab["iters"]))],
+                losses=[], plan_s=lab["seconds"], train_s=0.0, steps=0)
+    steps = max(1, epochs * n // batch)
+    for r in range(rounds):
+        prior.set_labels(0, labels)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(prior.stream)
+        loss = np.concatenate([prior.train(steps=min(65536, steps - s0), batch=batch, n_rows=n,
+                                           seed=seed * 1000 + r) for s0 in range(0, steps, 65536)])
+        ev1.record(prior.stream)
+        ev1.synchronize()
+        hist["train_s"] += ev0.elapsed_time(ev1) / 1e3
+        hist["steps"] += steps
+        hist["losses"].append([float(loss[:10].mean()), float(loss[-10:].mean())])
+        if r + 1 < rounds:
+            prop = prior.infer(0, n)
+            nl = plan_scenes(scenes, seed=seed, run0=0, cycle=r + 1, prior=prop, n_prior=n_prior, shape=shape,
+                             **plan_kw)
+            hist["plan_s"] += nl["seconds"]
+            better = nl["cost"] < cost
+            labels = torch.where(torch.from_numpy(better).to(labels.device)[:, None], nl["waypoints"], labels)
+            cost = np.where(better, nl["cost"], cost)
+            hist["label_cost"].append(float(np.median(cost)))
+            hist["label_iters"].append(float(np.mean(nl["iters"])))
+    hist["shape"] = shape
+    return hist
+
+
+def propose(prior: Prior, scenes: dict, first: int) -> torch.Tensor:
+    """The prior's proposals (device (n, 2T)) for scenes loaded into rows [first, first + n)."""
+    n = scenes["points"].shape[0]
+    prior.add_scenes(first, scenes["points"], [scenes["circles"][i] for i in range(n)])
+    return prior.infer(first, n)
+
+
+def _summary(r: dict, n: int) -> dict:
+    return dict(cost_median=float(np.median(r["cost"])), iters_mean=float(np.mean(r["iters"])),
+                iters_median=float(np.median(r["iters"])), collision_free=float(np.mean(r["Q"] == 0)),
+                seconds=float(r["seconds"]), plans_per_s=float(n / r["seconds"]) if r["seconds"] > 0 else None,
+                prior_used=None if r.get("prior_used") is None else float(r["prior_used"] / n))
+
+
+def evaluate_prior(prior: Prior, scenes: dict, first: int, budgets=(10, 25, 50, 100, 200, 300), cycles: int = 5,
+                   n_pi: int = 43, n_prior: int = 43, seed: int = 2, run0: int = 10 ** 6, shape=None,
+                   **plan_kw) -> dict:
+    """Held-out comparison of the PI-only start with prior + PI.
+
+    cold: a new scene (no previous path, so PI-only is the uniform start), planned
+      with Auto Truncation; budgets: median cost after exactly k iterations (no AT)
+      for each k, and iterations-to-converge = the smallest budget at which a start
+      reaches the PI-only start's median cost at the largest budget.
+    dynamic: `cycles` planning cycles of each scene moving as in the dynamic workload
+      (the last cycle is the given scene), every cycle warm-started by PI from the
+      same method's previous plan; per cycle the AT-run summary of each method.
+    Scenes are rasterised into prior rows [first, first + n)."""
+    n = scenes["points"].shape[0]
+    from .inputs import previous_cycle
+    out: dict = {"n": n}
+    prop = propose(prior, scenes, first)
+    base = plan_scenes(scenes, seed=seed, run0=run0, shape=shape, **plan_kw)
+    shape = base["shape"]
+    withp = plan_scenes(scenes, seed=seed, run0=run0, prior=prop, n_prior=n_prior, shape=shape, **plan_kw)
+    out["cold"] = {"pi_only": _summary(base, n), "prior_pi": _summary(withp, n)}
+    kw = {k: v for k, v in plan_kw.items() if k not in ("max_iters", "stall_iters")}
+    curve = {"pi_only": [], "prior_pi": []}
+    for k in budgets:
+        a = plan_scenes(scenes, seed=seed, run0=run0, max_iters=k, stall_iters=0, shape=shape, **kw)
+        b = plan_scenes(scenes, seed=seed, run0=run0, max_iters=k, stall_iters=0, prior=prop, n_prior=n_prior,
+                        shape=shape, **kw)
+        curve["pi_only"].append(dict(_summary(a, n), iters=k))
+        curve["prior_pi"].append(dict(_summary(b, n), iters=k))
+    target = curve["pi_only"][-1]["cost_median"]
+    conv = {}
+    for m, pts in curve.items():
+        hit = [p["iters"] for p in pts if p["cost_median"] <= target * (1.0 + 1e-6)]
+        conv[m] = hit[0] if hit else None
+    out["budgets"] = curve
+    out["iters_to_converge"] = conv
+    out["converged_cost"] = target
+    dyn = {"pi_only": [], "prior_pi": []}
+    prev = {"pi_only": None, "prior_pi": None}
+    for c in range(cycles):
+        sc = previous_cycle(scenes, cycles - 1 - c) if c < cycles - 1 else scenes
+        pc = propose(prior, sc, first)
+        for m in ("pi_only", "prior_pi"):
+            use_prior = m == "prior_pi"
+            r = plan_scenes(sc, seed=seed, run0=run0, cycle=c, prev=prev[m], n_pi=n_pi,
+                            prior=pc if use_prior else None, n_prior=n_prior if use_prior else 0, shape=shape,
+                            **plan_kw)
+            dyn[m].append(_summary(r, n))
+            prev[m] = r["waypoints"]
+    out["dynamic"] = dyn
+    out["shape"] = shape
+    return out

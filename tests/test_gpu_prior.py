@@ -5,7 +5,9 @@
 * features, labels, forward pass and loss gradient of the MLP vs the FP64 oracle
   (prior_oracle.c), which computes its own features from the same scenes;
 * one Adam step vs the closed form of Adam's first step on the oracle gradient;
-* training lowers the loss.
+* training lowers the loss;
+* the network trained on the planner's own solutions gains over the PI-only start
+  on held-out scenes, its proposals judged by the oracle's fitness.
 
 Tolerances.  The GEMM accumulates in FP32: |error| <= K * 2^-24 * sum |a||b|, far
 below the 1e-4 relative bound used.  The MLP rounds its weights and activations
@@ -170,3 +172,44 @@ def test_training_lowers_the_loss(native):
     assert np.all(np.isfinite(losses))
     assert losses[-20:].mean() < 0.5 * losses[:5].mean()
     pr.sync()
+
+
+def test_trained_prior_gains_over_pi_only(native):
+    # The prior trained on the planner's own solutions (self-training rounds) vs the
+    # method without it, on held-out scenes of the dynamic workload's kind:
+    # cold start (no previous path), iteration budgets, and a short dynamic run.
+    # The oracle's fitness judges the proposals themselves.
+    from paper_2308_10169_gb300.prior import evaluate_prior, fit_prior
+    ntr, nev = 4096, 256
+    tr, ev = prior_scenes(20, ntr), prior_scenes(21, nev)
+    pr = Prior(T=T, capacity=ntr + nev, max_batch=512)
+    init = prior_init_params(0, pr.K, H1, H2, 2 * T)
+    pr.set_params(init)
+    # proposals of the untrained network, judged by the oracle
+    untrained = _oracle_judge(pr, ev, ntr)
+    hist = fit_prior(pr, tr, rounds=3, epochs=30, batch=512, seed=1)
+    assert hist["label_cost"][-1] < 0.6 * hist["label_cost"][0]
+    trained = _oracle_judge(pr, ev, ntr)
+    assert np.median(trained) < np.median(untrained)
+    res = evaluate_prior(pr, ev, ntr, budgets=(10, 50, 300), cycles=3)
+    cold = res["cold"]
+    assert cold["prior_pi"]["cost_median"] < 0.6 * cold["pi_only"]["cost_median"]
+    assert cold["prior_pi"]["collision_free"] >= cold["pi_only"]["collision_free"]
+    conv = res["iters_to_converge"]
+    assert conv["prior_pi"] == 10 and (conv["pi_only"] is None or conv["pi_only"] > 10)
+    last = {m: res["dynamic"][m][-1]["cost_median"] for m in ("pi_only", "prior_pi")}
+    assert last["prior_pi"] < last["pi_only"]
+
+
+def _oracle_judge(pr, ev, first):
+    """Oracle fitness (Sec. 3.3.2, FP64) of the prior's proposed paths."""
+    from paper_2308_10169_gb300.inputs import SepsoConfig
+    from paper_2308_10169_gb300.prior import propose
+    wp = propose(pr, ev, first).cpu().numpy()
+    cfg = SepsoConfig(T=T, G=1, N=1, max_obstacles=64, alpha=30.0, beta=4)
+    out = []
+    for i in range(wp.shape[0]):
+        p = ev["points"][i]
+        f, _, _ = oracle.evaluate(cfg, oracle.Scene(p[:2], p[2:], ev["circles"][i]), wp[i])
+        out.append(f[0])
+    return np.array(out)
