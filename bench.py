@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--hsef-evolutions", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=0, help="0 = same as --steps")
+    ap.add_argument("--cost-cycles", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-scenes", type=int, default=4096,
@@ -66,6 +67,11 @@ def parse():
     ap.add_argument("--serve-rates", type=str, default="20000,5000",
                     help="offered request rates (1/s) of the serving section ('' = skip it)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--prior-train", type=int, default=16384,
+                    help="training scenes of the learned-prior section (0 = skip it; 200000 = full size)")
+    ap.add_argument("--prior-eval", type=int, default=2048, help="held-out scenes (10000 = full size)")
+    ap.add_argument("--prior-rounds", type=int, default=3)
+    ap.add_argument("--prior-epochs", type=int, default=30)
     return ap.parse_args()
 
 
@@ -274,6 +280,11 @@ def run_ours(args, rank, world, local):
     last = pl.read_result()
     iters = iters1 - iters0
     assert plans1 - plans0 == K
+    # median path cost of the same run over the next cycles (untimed: each is read back)
+    for _ in range(args.cost_cycles):
+        pl.advance(1)
+        pl.plan_async()
+        costs.append(pl.read_result()["cost"])
 
     # max over ranks
     t_local = torch.tensor([total_ms], dtype=torch.float64)
@@ -304,7 +315,9 @@ def run_ours(args, rank, world, local):
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                            "p99": float(np.percentile(step_ms, 99)),
                            "max": float(step_ms.max())},
-            "median_cost_last": float(last["cost"]),
+            "cost_last": float(last["cost"]),
+            "median_cost": float(np.median(costs)) if costs else None,
+            "median_cost_sample": f"the {len(costs)} cycles after the timed ones, read back one by one",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                          "traffic": SWARM_TRAFFIC_BYTES,
@@ -445,6 +458,75 @@ def run_serve(rate: float, seconds: float, n_agents: int = 2048):
             "ticks": st["ticks"], "gpu_launches": st["launches"]}
 
 
+def run_prior(n_train: int, n_eval: int, rounds: int, epochs: int, single: dict):
+    """Learned prior: self-training on the planner's own solutions, held-out
+    comparison with the PI-only start, tensor-core GEMM and training throughput."""
+    import torch
+
+    from paper_2308_10169_gb300.inputs import prior_init_params, prior_scenes
+    from paper_2308_10169_gb300.prior import Prior, evaluate_prior, fit_prior, gemm_bf16
+    H1, H2, T, B = 1024, 512, 20, 1024
+    tr, ev = prior_scenes(0, n_train), prior_scenes(1, n_eval)
+    pr = Prior(T=T, hidden1=H1, hidden2=H2, capacity=n_train + n_eval, max_batch=B)
+    pr.set_params(prior_init_params(0, pr.K, H1, H2, 2 * T))
+    l0 = pr.launch_count()
+    hist = fit_prior(pr, tr, rounds=rounds, epochs=epochs, batch=B, seed=1)
+    res = evaluate_prior(pr, ev, n_train)
+    K, O = pr.K, 2 * T
+    flops_fwd = 2.0 * B * (K * H1 + H1 * H2 + H2 * O)
+    flops_step = 3.0 * flops_fwd          # forward + the two backward products per layer
+    train = {"steps": hist["steps"], "batch": B, "seconds": hist["train_s"],
+             "steps_per_s": hist["steps"] / hist["train_s"],
+             "tflops": hist["steps"] * flops_step / hist["train_s"] / 1e12,
+             "loss_first_last_per_round": hist["losses"]}
+    # the tensor-core GEMM alone on the two largest products of a training step
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    gem = {}
+    for name, (M, N, Kd) in {"forward_layer1": (B, H1, K), "grad_W1": (H1, K, B)}.items():
+        A = torch.randn(M, Kd, device="cuda").to(torch.bfloat16)
+        Bm = torch.randn(N, Kd, device="cuda").to(torch.bfloat16)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            gemm_bf16(A, Bm, sync=False)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(20):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gemm_bf16(A, Bm, sync=False)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        ach = 2.0 * M * N * Kd / (ms / 1e3) / 1e12
+        gem[name] = {"M": M, "N": N, "K": Kd, "ms": ms, "tflops": ach}
+    dom = gem["grad_W1"]
+    roof = {"bound": "tensor", "achieved": dom["tflops"], "peak": peak, "unit": "TFLOP/s",
+            "frac": dom["tflops"] / peak, "traffic": None, "kernel": "gemm_tc_kernel (grad_W1 shape)",
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
+    # batched + prior throughput at the single-scene kernel's median path cost
+    eq = None
+    c_single = single.get("median_cost")
+    if c_single is not None:
+        hit = [p for p in res["budgets"]["prior_pi"] if p["cost_median"] <= c_single]
+        if hit:
+            eq = {"single_scene_median_cost": c_single, "single_scene_plans_per_s": single.get("value"),
+                  "batched_prior_iters": hit[0]["iters"], "batched_prior_median_cost": hit[0]["cost_median"],
+                  "batched_prior_plans_per_s": hit[0]["plans_per_s"]}
+        else:
+            eq = {"single_scene_median_cost": c_single, "reached": False}
+    return {"workload": f"MLP 64x64 raster + start/target ({K} features) -> {H1} -> {H2} -> {O}, BF16 "
+                        f"weights/activations, FP32 accumulate and masters, Adam; {n_train} training scenes "
+                        f"(64 circles r~U[10,30], 32 moving, start/target drift) labelled by the planner "
+                        f"(T=20, G=8 x N=170, Table hyper8 path rows, AT stall 10 / cap 300), {rounds} "
+                        f"self-training rounds x {epochs} epochs; {n_eval} held-out scenes",
+            "labels": {"median_cost_per_round": hist["label_cost"], "plan_seconds": hist["plan_s"]},
+            "train": train, "gemm": gem, "roofline": roof, "eval": res, "at_single_scene_cost": eq,
+            "gpu_launches": pr.launch_count() - l0}
+
+
 def cpu_baseline(seconds: float):
     cfg, times, iters, costs = oracle_cycles(seconds, 10_000)
     n, total = len(times), sum(times)
@@ -470,6 +552,9 @@ def main():
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         if world == 1 and args.batch_scenes > 0:
             line["batch"] = run_batch(args.batch_scenes, args.batch_iters)
+        if world == 1 and args.prior_train > 0:
+            line["prior"] = run_prior(args.prior_train, args.prior_eval, args.prior_rounds, args.prior_epochs,
+                                      line)
         if world == 1 and args.serve_rates:
             line["serve"] = {
                 "workload": "2048 agents, Poisson arrivals, T in {8,20,40}, O in {32,256} r~U[5,25], "
