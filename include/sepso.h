@@ -526,12 +526,13 @@ const char* sepso_prior_last_error(void);
  * lda and ldb multiples of 8, A and B 16-byte aligned.  Epilogue: + bias[n]
  * (device FP32, or NULL), then max(., 0) if relu, then 0 where mask[m][n] (BF16,
  * row stride ldm, or NULL) is not > 0.  Outputs: Cf (FP32, row stride ldcf)
- * and/or Cb (BF16, ldcb), device, either may be NULL.  Async on stream; a
- * device-side timeout is reported by the next sepso_gemm_bf16_sync.
+ * and/or Cb (BF16, ldcb), device, either may be NULL.  tile_n: 64, 128 or 256
+ * columns per CTA tile (128 rows), 0 = chosen from the grid it gives.  Async on
+ * stream; a device-side timeout is reported by the next sepso_gemm_bf16_sync.
  * Errors: EINVAL, ECUDA. */
 int sepso_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, int32_t lda, int32_t ldb,
                     float alpha, const float* bias, int32_t relu, const void* mask, int32_t ldm, float* Cf,
-                    int32_t ldcf, void* Cb, int32_t ldcb, void* stream);
+                    int32_t ldcf, void* Cb, int32_t ldcb, int32_t tile_n, void* stream);
 int sepso_gemm_bf16_sync(void* stream);
 
 /* ---- misc --------------------------------------------------------------- */

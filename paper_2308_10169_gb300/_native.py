@@ -179,7 +179,7 @@ SIGNATURES = {
     "sepso_prior_launch_count": (_i64, [_vp]),
     "sepso_prior_last_error": (ctypes.c_char_p, []),
     "sepso_gemm_bf16": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _i32, _i32, ctypes.c_float, _vp, _i32,
-                                       _vp, _i32, _vp, _i32, _vp, _i32, _vp]),
+                                       _vp, _i32, _vp, _i32, _vp, _i32, _i32, _vp]),
     "sepso_gemm_bf16_sync": (ctypes.c_int, [_vp]),
     "sepso_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sepso_last_error": (ctypes.c_char_p, []),

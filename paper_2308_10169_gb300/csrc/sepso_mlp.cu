@@ -2,13 +2,14 @@
 // (64x64 occupancy raster + start/target -> 1024 -> 512 -> 2T) with BF16 weights
 // and FP32 accumulation, trained and run with the project's own kernels.
 //
-//   gemm_tc_kernel     C = A . B^T on the 5th-generation tensor cores: operands
-//                      staged in shared memory by cp.async (3 stages), one elected
-//                      thread issues tcgen05.mma (kind::f16, BF16 inputs, FP32
-//                      accumulator in tensor memory), tcgen05.commit signals an
-//                      mbarrier per stage, and the four warps read the accumulator
-//                      back with tcgen05.ld for a fused epilogue (scale, bias, ReLU,
-//                      ReLU mask of the backward pass, FP32 and/or BF16 output).
+//   gemm_tc_kernel     C = A . B^T on the 5th-generation tensor cores: a TMA
+//                      producer lane fills a ring of 128-byte-swizzled operand
+//                      stages, an MMA lane issues tcgen05.mma (kind::f16, BF16
+//                      inputs, FP32 accumulator in tensor memory) and frees each
+//                      stage with tcgen05.commit, and the four warps read the
+//                      accumulator back with tcgen05.ld for a fused epilogue
+//                      (scale, bias, ReLU, the backward pass's ReLU mask, FP32
+//                      and/or BF16 output).  Tile N (64 / 128 / 256) per launch.
 //   raster_kernel      occupancy raster of the circles (cell centre inside a disk).
 //   small kernels      transpose, column sums (bias gradients), MSE loss gradient,
 //                      Adam, FP32 -> BF16 weight copies.
@@ -17,7 +18,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <new>
 #include <string>
 #include <vector>
@@ -30,15 +33,14 @@ namespace sepso {
 // ---------------------------------------------------------------------------
 // tcgen05 / cp.async helpers (inline PTX)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(smem_dst)), "l"(gsrc),
-               "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+// 2D tiled TMA load (box of the tensor map at coordinates (x = k, y = row)) into
+// shared memory, completing on an mbarrier with the transaction byte count.
+__device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -56,13 +58,15 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// Shared-memory matrix descriptor (no swizzle, K-major canonical layout of 8-row x
-// 16-byte core matrices): start address, leading-dimension byte offset (between
-// core matrices adjacent in K), stride-dimension byte offset (between 8-row
-// groups), the fixed version bits 46..48 = 0b001, swizzle mode 0.
-__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA with the
+// 128-byte swizzle: rows of 128 B (64 BF16 of K), 8-row atoms of 1024 B (the
+// stride-dimension byte offset), leading-dimension offset unused for this layout
+// (encoded as 1), fixed version bits 46..48 = 0b001, layout type 2 (128-byte
+// swizzle) in bits 61..63.  The tile base is 1024-byte aligned; the k-th 16-wide
+// K slice starts 32 k bytes further (the swizzle is a function of the address).
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
   const uint64_t a = (uint64_t)((smem_addr(p) >> 4) & 0x3FFFu);
-  return a | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+  return a | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
@@ -104,6 +108,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // ---------------------------------------------------------------------------
 // GEMM: C[M x N] = alpha * A[M x K] . B[N x K]^T (+ bias[n]) (then ReLU, or the
 // ReLU mask mask[m][n] > 0), A and B row-major BF16 with K contiguous.
+//
+// One CTA computes a 128 x BN tile with four warps.  Warp 0 (one lane) streams
+// 128 x 64 and BN x 64 operand boxes into a ring of shared-memory stages with TMA
+// (128-byte swizzle, zero fill past the matrix edges); warp 1 (one lane) issues
+// four tcgen05.mma (M = 128, N = BN, K = 16) per stage into a BN-column FP32
+// accumulator in tensor memory and frees the stage with tcgen05.commit; after the
+// last stage all four warps read the accumulator (warp w: rows 32w .. 32w + 31)
+// with tcgen05.ld, stage it through shared memory and store it row-contiguously
+// with the epilogue applied.  Every wait is bounded; tensor memory is released on
+// every path.
 // ---------------------------------------------------------------------------
 struct GemmArgs {
   const __nv_bfloat16* A;
@@ -121,131 +135,151 @@ struct GemmArgs {
   int* status;
 };
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3, kGemmThreads = 128;
-constexpr int kTileBytes = kBM * kBK * 2;            // 16 KB per operand per stage
-constexpr int kStageBytes = 2 * kTileBytes;          // A + B
-// Slack after the stages: a descriptor stride read the other way round would still
-// stay inside the CTA's shared memory.
-constexpr int kGemmSmem = kStages * kStageBytes + 32768;
+constexpr int kBM = 128, kBK = 64, kGemmThreads = 128;
+constexpr int kRing = 192 * 1024;                         // operand stages
+constexpr int kGemmSmem = kRing + 1024;                   // + alignment slack
+template <int BN>
+struct GemmTile {
+  static constexpr int kABytes = kBM * kBK * 2;           // 16 KB
+  static constexpr int kBBytes = BN * kBK * 2;
+  static constexpr int kStage = kABytes + kBBytes;
+  static constexpr int kStages = kRing / kStage;
+  static_assert(kStages >= 2, "ring too small");
+  static_assert(kBM * (BN + 4) * 4 <= kRing, "epilogue staging does not fit");
+};
 
-__global__ void __launch_bounds__(kGemmThreads, 1) gemm_tc_kernel(const GemmArgs g) {
-  extern __shared__ __align__(1024) uint8_t gsm[];
-  __shared__ uint64_t mbar[kStages];
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
+  using TL = GemmTile<BN>;
+  constexpr int S = TL::kStages;
+  extern __shared__ uint8_t gsm_raw[];
+  __shared__ uint64_t full[S], empty[S], done;
   __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  uint8_t* gsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
   const int nkb = (g.K + kBK - 1) / kBK;
-  constexpr uint32_t kIdesc = mma_idesc_bf16(kBM, kBN);
+  constexpr uint32_t kIdesc = mma_idesc_bf16(kBM, BN);
 
-  if (warp == 0) tmem_alloc(&tmem_base, kBN);
-  if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&mbar[s], 1);
+  if (warp == 0) tmem_alloc(&tmem_base, BN);
+  if (tid == 32) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    s_fail = 0;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  // Tile layout in shared memory (rows R = 128, 8 chunks of 8 K-elements): chunk
-  // (row, kc) at kc * R * 16 + row * 16 bytes, i.e. core matrices of 8 rows x 16 B
-  // with an 8-row stride of 128 B and a K stride of R * 16 = 2048 B.
-  auto load_stage = [&](int kb, int s) {
-    uint8_t* sa = gsm + s * kStageBytes;
-    uint8_t* sb = sa + kTileBytes;
-    for (int c = tid; c < kBM * 8; c += kGemmThreads) {
-      const int row = c % kBM, kc = c / kBM;
-      const int gk = kb * kBK + kc * 8;
-      const int gm = m0 + row;
-      const bool ok = gm < g.M && gk < g.K;
-      cp_async16(sa + kc * (kBM * 16) + row * 16, ok ? (const void*)(g.A + (size_t)gm * g.lda + gk) : (const void*)g.A,
-                 ok ? 16 : 0);
-      const int gn = n0 + row;
-      const bool okb = gn < g.N && gk < g.K;
-      cp_async16(sb + kc * (kBN * 16) + row * 16, okb ? (const void*)(g.B + (size_t)gn * g.ldb + gk) : (const void*)g.B,
-                 okb ? 16 : 0);
+  if (warp == 0 && lane == 0) {
+    // producer: TMA boxes into the ring
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % S;
+      if (kb >= S && !mbar_wait_bounded(&empty[s], (uint32_t)((kb / S - 1) & 1), kWaitLimitNs)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      uint8_t* sa = gsm + s * TL::kStage;
+      mbar_expect_tx(&full[s], (uint32_t)TL::kStage);
+      tma_load_2d(sa, &tmA, kb * kBK, m0, &full[s]);
+      tma_load_2d(sa + TL::kABytes, &tmB, kb * kBK, n0, &full[s]);
+      issued = kb + 1;
     }
-  };
-
-  for (int kb = 0; kb < kStages - 1; ++kb) {
-    if (kb < nkb) load_stage(kb, kb);
-    cp_async_commit();
-  }
-  bool fail = false;
-  int committed = -1;  // last K-block whose MMAs were committed
-  for (int kb = 0; kb < nkb && !fail; ++kb) {
-    const int s = kb % kStages;
-    cp_async_wait<kStages - 2>();
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
+    // on a failure, let the boxes already in flight land before the CTA exits
+    if (issued < nkb)
+      for (int kb = max(0, issued - S); kb < issued; ++kb)
+        mbar_wait_bounded(&full[kb % S], (uint32_t)((kb / S) & 1), kWaitLimitNs);
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    int kb = 0;
+    for (; kb < nkb; ++kb) {
+      const int s = kb % S;
+      if (!mbar_wait_bounded(&full[s], (uint32_t)((kb / S) & 1), kWaitLimitNs) || *(volatile int*)&s_fail) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
       tc_fence_after();
-      const uint8_t* sa = gsm + s * kStageBytes;
-      const uint8_t* sb = sa + kTileBytes;
+      const uint8_t* sa = gsm + s * TL::kStage;
+      const uint8_t* sb = sa + TL::kABytes;
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk) {
-        const uint64_t ad = smem_desc(sa + kk * 2 * (kBM * 16), kBM * 16, 128);
-        const uint64_t bd = smem_desc(sb + kk * 2 * (kBN * 16), kBN * 16, 128);
-        mma_bf16(tmem, ad, bd, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
-      }
-      mma_commit(&mbar[s]);
+      for (int kk = 0; kk < kBK / 16; ++kk)
+        mma_bf16(tmem, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), kIdesc,
+                 (kb > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
     }
-    committed = kb;
-    const int nk = kb + kStages - 1;
-    if (nk < nkb) {
-      const int ps = nk % kStages;
-      if (kb >= 1) {
-        // the MMAs of block kb - 1 read stage ps: wait for them before refilling it
-        const uint32_t parity = (uint32_t)(((kb - 1) / kStages) & 1);
-        if (!mbar_wait_bounded(&mbar[ps], parity, kWaitLimitNs)) fail = true;
-      }
-      if (!fail) load_stage(nk, ps);
-    }
-    cp_async_commit();
-    if (__syncthreads_or(fail ? 1 : 0)) fail = true;
+    mma_commit(&done);  // tracks every MMA issued above
   }
-  // MMAs complete in issue order: the last commit covers all of them.  On a timeout
-  // the wait is repeated once (bounded) so that no MMA is in flight at dealloc.
-  if (committed >= 0) {
-    const bool ok = mbar_wait_bounded(&mbar[committed % kStages], (uint32_t)((committed / kStages) & 1), kWaitLimitNs);
-    if (!ok) fail = true;
-  }
-  cp_async_wait<0>();
-  if (__syncthreads_or(fail ? 1 : 0)) {
+  __syncwarp();
+  // everyone: the accumulator is final once `done` completes
+  if (!mbar_wait_bounded(&done, 0u, kWaitLimitNs)) atomicExch(&s_fail, 1);
+  const bool fail = __syncthreads_or(*(volatile int*)&s_fail) != 0;
+  if (fail) {
     if (tid == 0 && g.status) atomicExch(g.status, SEPSO_ETIMEOUT);
-  } else if (committed >= 0) {
+  } else if (nkb > 0) {
     tc_fence_after();
-    // Epilogue: warp w owns TMEM lanes (rows) 32w .. 32w + 31.  The accumulator tile
-    // goes through shared memory (row stride 129 floats: conflict-free both ways) so
-    // that the global stores are row-contiguous.
+    // Row pitch BN + 4 floats: 16-byte aligned rows, and the eight threads of a
+    // quarter-warp land in distinct bank groups both when each writes its own row
+    // and when a warp reads one row.
     float* tile = reinterpret_cast<float*>(gsm);
-    constexpr int kLd = kBN + 1;
+    constexpr int kLd = BN + 4;
     const int r = warp * 32 + lane;
     float v[32];
 #pragma unroll 1
-    for (int c0 = 0; c0 < kBN; c0 += 32) {
+    for (int c0 = 0; c0 < BN; c0 += 32) {
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      float4* dst = reinterpret_cast<float4*>(tile + r * kLd + c0);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) tile[r * kLd + c0 + i] = v[i];
+      for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
     }
     __syncthreads();
-    const int ncol = min(kBN, g.N - n0);
+    const int ncol = min(BN, g.N - n0);
+    const bool vec = (!g.Cf || ((g.ldcf & 3) == 0 && (reinterpret_cast<uintptr_t>(g.Cf) & 15) == 0)) &&
+                     (!g.Cb || ((g.ldcb & 3) == 0 && (reinterpret_cast<uintptr_t>(g.Cb) & 7) == 0));
     for (int rr = warp; rr < kBM; rr += kGemmThreads / 32) {
       const int row = m0 + rr;
       if (row >= g.M) break;
-      for (int c = lane; c < ncol; c += 32) {
+      for (int c = 4 * lane; c < ncol; c += 128) {
         const int col = n0 + c;
-        float x = g.alpha * tile[rr * kLd + c];
-        if (g.bias) x += g.bias[col];
-        if (g.relu) x = fmaxf(x, 0.0f);
-        if (g.mask && !(__bfloat162float(g.mask[(size_t)row * g.ldm + col]) > 0.0f)) x = 0.0f;
-        if (g.Cf) g.Cf[(size_t)row * g.ldcf + col] = x;
-        if (g.Cb) g.Cb[(size_t)row * g.ldcb + col] = __float2bfloat16_rn(x);
+        const float4 t = *reinterpret_cast<const float4*>(tile + rr * kLd + c);
+        float x[4] = {t.x, t.y, t.z, t.w};
+        const int nv = min(4, ncol - c);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (i < nv) {
+            x[i] *= g.alpha;
+            if (g.bias) x[i] += g.bias[col + i];
+            if (g.relu) x[i] = fmaxf(x[i], 0.0f);
+            if (g.mask && !(__bfloat162float(g.mask[(size_t)row * g.ldm + col + i]) > 0.0f)) x[i] = 0.0f;
+          }
+        }
+        if (vec && nv == 4) {
+          if (g.Cf) *reinterpret_cast<float4*>(g.Cf + (size_t)row * g.ldcf + col) = make_float4(x[0], x[1], x[2], x[3]);
+          if (g.Cb) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(x[0], x[1]), hi = __floats2bfloat162_rn(x[2], x[3]);
+            uint2 u;
+            u.x = *reinterpret_cast<uint32_t*>(&lo);
+            u.y = *reinterpret_cast<uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(g.Cb + (size_t)row * g.ldcb + col) = u;
+          }
+        } else {
+          for (int i = 0; i < nv; ++i) {
+            if (g.Cf) g.Cf[(size_t)row * g.ldcf + col + i] = x[i];
+            if (g.Cb) g.Cb[(size_t)row * g.ldcb + col + i] = __float2bfloat16_rn(x[i]);
+          }
+        }
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, kBN);
+  if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
 }  // namespace sepso
@@ -475,19 +509,131 @@ __device__ int g_gemm_status;
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-int gemm_launch(const GemmArgs& g, cudaStream_t s) {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a row-major BF16 matrix (rows x cols, row stride ld elements) read
+// in boxes of 64 columns (128 B, the swizzle span) x box_rows rows; zero fill
+// outside the matrix.  Encoded maps are kept in a small per-thread cache keyed by
+// their arguments (the training loop reuses the same buffers every step).
+struct MapKey {
+  const void* base;
+  int rows, cols, ld, box_rows;
+  bool operator==(const MapKey& o) const {
+    return base == o.base && rows == o.rows && cols == o.cols && ld == o.ld && box_rows == o.box_rows;
+  }
+};
+constexpr int kMapCache = 64;
+thread_local MapKey t_map_keys[kMapCache];
+thread_local CUtensorMap t_maps[kMapCache];
+thread_local int t_map_n = 0, t_map_next = 0;
+
+int encode_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows);
+
+int make_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
+  const MapKey k{base, rows, cols, ld, box_rows};
+  for (int i = 0; i < t_map_n; ++i)
+    if (t_map_keys[i] == k) {
+      *map = t_maps[i];
+      return SEPSO_OK;
+    }
+  PTRY(encode_map(map, base, rows, cols, ld, box_rows));
+  const int slot = t_map_next;
+  t_map_next = (t_map_next + 1) % kMapCache;
+  t_map_n = std::min(t_map_n + 1, kMapCache);
+  t_map_keys[slot] = k;
+  t_maps[slot] = *map;
+  return SEPSO_OK;
+}
+
+int encode_map(CUtensorMap* map, const void* base, int rows, int cols, int ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return pfail(SEPSO_ECUDA, "cuTensorMapEncodeTiled is not available");
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)sepso::kBK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return pfail(SEPSO_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return SEPSO_OK;
+}
+
+int g_num_sms = 0;
+
+// Tile N for a product: the widest tile whose grid still covers the SMs, else the
+// one with the fewest waves (ties to the wider tile).
+int choose_tile_n(int M, int N) {
+  if (g_num_sms <= 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      g_num_sms = 148;
+  }
+  const int mt = (M + sepso::kBM - 1) / sepso::kBM;
+  int best = 64;
+  double best_cost = 1e300;
+  for (int bn : {256, 128, 64}) {
+    const long long tiles = (long long)mt * ((N + bn - 1) / bn);
+    const long long waves = (tiles + g_num_sms - 1) / g_num_sms;
+    // per-tile time ~ bn, with narrower tiles paying more per output column
+    const double per_tile = bn * (bn == 256 ? 1.0 : bn == 128 ? 1.15 : 1.6);
+    const double cost = (double)waves * per_tile;
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = bn;
+    }
+  }
+  return best;
+}
+
+template <int BN>
+int gemm_launch_bn(const CUtensorMap& ta, const GemmArgs& g, cudaStream_t s) {
+  CUtensorMap tb;
+  PTRY(make_map(&tb, g.B, g.N, g.K, g.ldb, BN));
+  static thread_local int configured_device = -1;
+  int dev = 0;
+  PCUDA(cudaGetDevice(&dev));
+  if (configured_device != dev) {
+    PCUDA(cudaFuncSetAttribute(sepso::gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               sepso::kGemmSmem));
+    configured_device = dev;
+  }
+  const dim3 grid((g.M + sepso::kBM - 1) / sepso::kBM, (g.N + BN - 1) / BN);
+  if (grid.y > 65535u) return pfail(SEPSO_EINVAL, "gemm: N too large");
+  sepso::gemm_tc_kernel<BN><<<grid, sepso::kGemmThreads, sepso::kGemmSmem, s>>>(ta, tb, g);
+  PCUDA(cudaGetLastError());
+  return SEPSO_OK;
+}
+
+int gemm_launch(const GemmArgs& g, cudaStream_t s, int tile_n = 0) {
   if (g.M < 1 || g.N < 1 || g.K < 8 || (g.K & 7) || (g.lda & 7) || (g.ldb & 7) || g.lda < g.K || g.ldb < g.K)
     return pfail(SEPSO_EINVAL, "gemm: bad sizes M %d N %d K %d lda %d ldb %d", g.M, g.N, g.K, g.lda, g.ldb);
   if (!g.A || !g.B || !aligned16(g.A) || !aligned16(g.B))
     return pfail(SEPSO_EINVAL, "gemm: A and B must be 16-byte aligned device arrays");
   if ((g.Cf && g.ldcf < g.N) || (g.Cb && g.ldcb < g.N) || (g.mask && g.ldm < g.N))
     return pfail(SEPSO_EINVAL, "gemm: output or mask row stride below N");
-  PCUDA(cudaFuncSetAttribute(sepso::gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sepso::kGemmSmem));
-  const dim3 grid((g.M + sepso::kBM - 1) / sepso::kBM, (g.N + sepso::kBN - 1) / sepso::kBN);
-  if (grid.y > 65535u) return pfail(SEPSO_EINVAL, "gemm: N too large");
-  sepso::gemm_tc_kernel<<<grid, sepso::kGemmThreads, sepso::kGemmSmem, s>>>(g);
-  PCUDA(cudaGetLastError());
-  return SEPSO_OK;
+  if (tile_n == 0) tile_n = choose_tile_n(g.M, g.N);
+  CUtensorMap ta;
+  PTRY(make_map(&ta, g.A, g.M, g.K, g.lda, sepso::kBM));
+  switch (tile_n) {
+    case 64: return gemm_launch_bn<64>(ta, g, s);
+    case 128: return gemm_launch_bn<128>(ta, g, s);
+    case 256: return gemm_launch_bn<256>(ta, g, s);
+    default: return pfail(SEPSO_EINVAL, "gemm: tile N %d (64, 128 or 256)", tile_n);
+  }
 }
 
 struct PriorLayout {
@@ -1006,7 +1152,7 @@ const char* sepso_prior_last_error(void) { return g_prior_error.c_str(); }
 
 int sepso_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, int32_t lda, int32_t ldb,
                     float alpha, const float* bias, int32_t relu, const void* mask, int32_t ldm, float* Cf,
-                    int32_t ldcf, void* Cb, int32_t ldcb, void* stream) {
+                    int32_t ldcf, void* Cb, int32_t ldcb, int32_t tile_n, void* stream) {
   GemmArgs g{};
   g.A = static_cast<const bf16*>(A);
   g.B = static_cast<const bf16*>(B);
@@ -1027,7 +1173,7 @@ int sepso_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t 
   void* st = nullptr;
   PCUDA(cudaGetSymbolAddress(&st, g_gemm_status));
   g.status = static_cast<int*>(st);
-  return gemm_launch(g, static_cast<cudaStream_t>(stream));
+  return gemm_launch(g, static_cast<cudaStream_t>(stream), tile_n);
 }
 
 int sepso_gemm_bf16_sync(void* stream) {

@@ -140,7 +140,7 @@ class Prior:
 
 def gemm_bf16(A: torch.Tensor, B: torch.Tensor, alpha: float = 1.0, bias: torch.Tensor | None = None,
               relu: bool = False, mask: torch.Tensor | None = None, out_f32: bool = True,
-              out_bf16: bool = False, sync: bool = True):
+              out_bf16: bool = False, sync: bool = True, tile_n: int = 0):
     """C = epilogue(alpha * A @ B^T) on the tensor cores; A (M, K), B (N, K) BF16 CUDA."""
     assert A.is_cuda and B.is_cuda and A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16
     assert A.stride(1) == 1 and B.stride(1) == 1 and A.shape[1] == B.shape[1]
@@ -155,7 +155,7 @@ def gemm_bf16(A: torch.Tensor, B: torch.Tensor, alpha: float = 1.0, bias: torch.
         vp(bias.data_ptr()) if bias is not None else None, int(relu),
         vp(mask.data_ptr()) if mask is not None else None, mask.stride(0) if mask is not None else 0,
         vp(Cf.data_ptr()) if Cf is not None else None, N, vp(Cb.data_ptr()) if Cb is not None else None, N,
-        vp(stream)))
+        int(tile_n), vp(stream)))
     if sync:
         check_prior(_native.lib().sepso_gemm_bf16_sync(vp(stream)))
     return Cf, Cb

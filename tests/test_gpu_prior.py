@@ -47,6 +47,19 @@ def test_gemm_matches_fp32_reference(native, M, N, K):
     assert torch.max(torch.abs(got - ref)).item() <= tol
 
 
+@pytest.mark.parametrize("tile_n", [64, 128, 256])
+def test_gemm_tile_widths_agree(native, tile_n):
+    # every tile width gives the same products (ragged M, N and K; K spans several
+    # pipeline stages and wraps the stage ring)
+    g = torch.Generator().manual_seed(tile_n)
+    M, N, K = 333, 300, 1096
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    ref = A.double() @ B.double().T
+    Cf, _ = gemm_bf16(A.cuda(), B.cuda(), tile_n=tile_n)
+    assert torch.max(torch.abs(Cf.cpu().double() - ref)).item() <= 1e-4 * np.sqrt(K)
+
+
 def test_gemm_epilogue_bias_relu_mask_bf16(native):
     g = torch.Generator().manual_seed(9)
     M, N, K = 300, 260, 136
