@@ -555,6 +555,15 @@ int64_t sepso_launch_count(sepso_handle h);
 const char* sepso_strerror(int code);
 const char* sepso_last_error(void);
 
+/* Watchdog self-test (failure detection without a fault): one kernel runs the two
+ * kinds of bounded wait the library's kernels use -- an mbarrier that no copy
+ * completes, and the inter-CTA counter that no CTA increments -- with a limit of
+ * limit_us microseconds (1..1e6) instead of 2 s.  Both give up, the kernel
+ * returns normally and *fired gets bit 0 (mbarrier) and bit 1 (counter) set, so a
+ * healthy build reports 3 and leaves the context usable.  The paper has no
+ * counterpart.  Sync on stream.  Errors: EINVAL, ECUDA. */
+int sepso_watchdog_selftest(int32_t limit_us, int32_t* fired, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

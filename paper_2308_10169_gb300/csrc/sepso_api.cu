@@ -815,6 +815,32 @@ int64_t sepso_launch_count(sepso_handle h) { return h ? h->launches : -1; }
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Watchdog self-test: the kernels' bounded waits, left to run out on purpose.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ unsigned int g_wd_never;  // nothing ever increments it
+__device__ int g_wd_fired;
+}  // namespace
+
+extern "C" int sepso_watchdog_selftest(int32_t limit_us, int32_t* fired, void* stream) {
+  if (!fired || limit_us < 1 || limit_us > 1000000) return fail(SEPSO_EINVAL, "limit_us must be in [1, 1e6]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* never = nullptr;
+  void* out = nullptr;
+  CUDA_TRY(cudaGetSymbolAddress(&never, g_wd_never));
+  CUDA_TRY(cudaGetSymbolAddress(&out, g_wd_fired));
+  CUDA_TRY(cudaMemsetAsync(never, 0, sizeof(unsigned int), s));
+  CUDA_TRY(cudaMemsetAsync(out, 0xff, sizeof(int), s));
+  CUDA_TRY(launch_watchdog_selftest(static_cast<const unsigned int*>(never), (unsigned long long)limit_us * 1000ull,
+                                    static_cast<int*>(out), s));
+  int f = -1;
+  CUDA_TRY(cudaMemcpyAsync(&f, out, sizeof f, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *fired = f;
+  return SEPSO_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Planning without any device allocation.
 //
 // Some callers cannot call cudaMalloc at all: code that runs inside another

@@ -211,6 +211,20 @@ __device__ __forceinline__ void red_min_u64(unsigned long long* p, unsigned long
 // writer's relaxed stores: a release of everything it wrote earlier.
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
+// Polls a monotone counter until it reaches target (wrap-around safe) or the
+// limit passes; false on a timeout.  The caller adds the acquire fence.
+__device__ __forceinline__ bool counter_wait_bounded(const unsigned int* ctr, unsigned int target,
+                                                     unsigned long long limit_ns) {
+  unsigned int v = ld_relaxed_u32(ctr);
+  if ((int)(v - target) >= 0) return true;
+  const unsigned long long t0 = global_ns();
+  do {
+    if (global_ns() - t0 > limit_ns) return false;
+    v = ld_relaxed_u32(ctr);
+  } while ((int)(v - target) < 0);
+  return true;
+}
+
 
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s

@@ -52,5 +52,7 @@ cudaError_t launch_advance(float4* circ, float2* cvel, float* pts, int O, float 
                            cudaStream_t s);
 cudaError_t launch_hsef_init(const HsefParams& p, cudaStream_t s);
 cudaError_t launch_hsef_update(const HsefParams& p, int e, cudaStream_t s);
+cudaError_t launch_watchdog_selftest(const unsigned int* never, unsigned long long limit_ns, int* fired,
+                                     cudaStream_t s);
 
 }  // namespace sepso

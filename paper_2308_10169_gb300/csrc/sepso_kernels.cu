@@ -300,17 +300,7 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
     int timed_out = 0;
     if (tid == 0) {
       const unsigned int target = (unsigned int)p.C * (unsigned int)gk;
-      unsigned int v = ld_relaxed_u32(&p.counter[r].count);
-      if ((int)(v - target) < 0) {
-        const unsigned long long t0 = global_ns();
-        do {
-          if (global_ns() - t0 > kWaitLimitNs) {
-            timed_out = 1;
-            break;
-          }
-          v = ld_relaxed_u32(&p.counter[r].count);
-        } while ((int)(v - target) < 0);
-      }
+      timed_out = counter_wait_bounded(&p.counter[r].count, target, kWaitLimitNs) ? 0 : 1;
       fence_acq_rel_gpu();  // with the relaxed load that saw the count: an acquire
     }
     if (__syncthreads_or(timed_out)) {
@@ -748,6 +738,27 @@ cudaError_t launch_hsef_init(const HsefParams& p, cudaStream_t s) {
 
 cudaError_t launch_hsef_update(const HsefParams& p, int e, cudaStream_t s) {
   hsef_update_kernel<<<1, 256, 0, s>>>(p, e);
+  return cudaGetLastError();
+}
+
+// Watchdog self-test: the two kinds of bounded wait the kernels use (an mbarrier
+// that no copy completes, a counter that no CTA increments) are left to run out;
+// bit 0 / bit 1 of *fired report that each gave up.
+__global__ void watchdog_selftest_kernel(const unsigned int* never, unsigned long long limit_ns, int* fired) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int f = 0;
+    if (!mbar_wait_bounded(&bar, 0u, limit_ns)) f |= 1;
+    if (!counter_wait_bounded(never, 1u, limit_ns)) f |= 2;
+    *fired = f;
+  }
+}
+
+cudaError_t launch_watchdog_selftest(const unsigned int* never, unsigned long long limit_ns, int* fired,
+                                     cudaStream_t s) {
+  watchdog_selftest_kernel<<<1, 32, 0, s>>>(never, limit_ns, fired);
   return cudaGetLastError();
 }
 

@@ -345,3 +345,26 @@ def test_argument_errors(native):
     pl.set_scene(scene)
     assert pl.plan()["status"] == 0
     pl.sync()
+
+
+def test_watchdog_waits_give_up_and_leave_the_context_usable(native):
+    # Failure detection without a fault: the kernels' bounded waits (mbarrier and
+    # inter-CTA counter) are left to run out with a 20 ms limit; the kernel returns,
+    # the host reads which waits fired, and the next plan on the device still works.
+    import ctypes
+    import time
+
+    import torch
+
+    from paper_2308_10169_gb300 import _native
+    fired = ctypes.c_int32(-1)
+    stream = torch.cuda.current_stream().cuda_stream
+    t0 = time.perf_counter()
+    _native.check(_native.lib().sepso_watchdog_selftest(20000, ctypes.byref(fired), ctypes.c_void_p(stream)))
+    elapsed = time.perf_counter() - t0
+    assert fired.value == 3
+    assert elapsed >= 0.04 - 1e-3
+    cfg, scene, hyper = static_workload(0)
+    pl = make(cfg.with_(max_iters=3), scene, hyper)
+    res = pl.plan()
+    assert res["iters"] == 3 and np.isfinite(res["cost"])
