@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--prior-eval", type=int, default=2048, help="held-out scenes (10000 = full size)")
     ap.add_argument("--prior-rounds", type=int, default=3)
     ap.add_argument("--prior-epochs", type=int, default=30)
+    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve",
+                    help="comma list of main, cpu, batch, prior, serve, gemm (gemm: the tensor-core GEMM alone)")
     return ap.parse_args()
 
 
@@ -413,7 +415,7 @@ def run_batch(n: int, iters: int):
             "shape": bp.shape(), "autotune_ms_per_launch": tune_ms,
             "gpu_launches": bp.launch_count() - l0,
             "median_cost": float(np.median([r["cost"] for r in res])),
-            "l2": "inputs larger than L2 (13 GB of swarm state)"}
+            "l2": f"inputs larger than L2 ({bp.workspace.numel() / 1e9:.1f} GB of batch state)"}
 
 
 def _world_step(ag):
@@ -479,30 +481,9 @@ def run_prior(n_train: int, n_eval: int, rounds: int, epochs: int, single: dict)
              "steps_per_s": hist["steps"] / hist["train_s"],
              "tflops": hist["steps"] * flops_step / hist["train_s"] / 1e12,
              "loss_first_last_per_round": hist["losses"]}
-    # the tensor-core GEMM alone on the two largest products of a training step
-    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
-    peak = peaks.get("bf16_tflops", 1900.0)
-    gem = {}
-    for name, (M, N, Kd) in {"forward_layer1": (B, H1, K), "grad_W1": (H1, K, B)}.items():
-        A = torch.randn(M, Kd, device="cuda").to(torch.bfloat16)
-        Bm = torch.randn(N, Kd, device="cuda").to(torch.bfloat16)
-        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-        for _ in range(3):
-            gemm_bf16(A, Bm, sync=False)
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(20):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            gemm_bf16(A, Bm, sync=False)
-            e1.record()
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        ms = float(np.median(ts))
-        ach = 2.0 * M * N * Kd / (ms / 1e3) / 1e12
-        gem[name] = {"M": M, "N": N, "K": Kd, "ms": ms, "tflops": ach}
+    gem = run_gemm(B, H1, K)
     dom = gem["grad_W1"]
+    peak = _bf16_peak()
     roof = {"bound": "tensor", "achieved": dom["tflops"], "peak": peak, "unit": "TFLOP/s",
             "frac": dom["tflops"] / peak, "traffic": None, "kernel": "gemm_tc_kernel (grad_W1 shape)",
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
@@ -527,6 +508,41 @@ def run_prior(n_train: int, n_eval: int, rounds: int, epochs: int, single: dict)
             "gpu_launches": pr.launch_count() - l0}
 
 
+def _bf16_peak() -> float:
+    path = ROOT / "MEASURED_PEAKS.json"
+    return float(json.loads(path.read_text()).get("bf16_tflops", 1900.0)) if path.exists() else 1900.0
+
+
+def run_gemm(B: int = 1024, H1: int = 1024, K: int = 4104, reps: int = 20):
+    """The tensor-core GEMM alone on the two largest products of a training step
+    (grad W1 first, then forward layer 1), each launch timed with CUDA events after
+    an L2 flush."""
+    import torch
+
+    from paper_2308_10169_gb300.prior import gemm_bf16
+    gem = {}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for name, (M, N, Kd) in {"grad_W1": (H1, K, B), "forward_layer1": (B, H1, K)}.items():
+        A = torch.randn(M, Kd, device="cuda").to(torch.bfloat16)
+        Bm = torch.randn(N, Kd, device="cuda").to(torch.bfloat16)
+        for _ in range(3):
+            gemm_bf16(A, Bm, sync=False)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gemm_bf16(A, Bm, sync=False)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.median(ts))
+        gem[name] = {"M": M, "N": N, "K": Kd, "ms": ms, "tflops": 2.0 * M * N * Kd / (ms / 1e3) / 1e12,
+                     "frac_of_measured_bf16_peak": 2.0 * M * N * Kd / (ms / 1e3) / 1e12 / _bf16_peak()}
+    return gem
+
+
 def cpu_baseline(seconds: float):
     cfg, times, iters, costs = oracle_cycles(seconds, 10_000)
     n, total = len(times), sum(times)
@@ -546,16 +562,22 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    line = run_ours(args, rank, world, local)
+    sections = set(x.strip() for x in args.sections.split(",") if x.strip())
+    if "main" in sections:
+        line = run_ours(args, rank, world, local)
+    else:
+        line = {"metric": METRIC, "unit": UNIT, "sections": sorted(sections)} if rank == 0 else None
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and "cpu" in sections and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
-        if world == 1 and args.batch_scenes > 0:
+        if world == 1 and "batch" in sections and args.batch_scenes > 0:
             line["batch"] = run_batch(args.batch_scenes, args.batch_iters)
-        if world == 1 and args.prior_train > 0:
+        if world == 1 and "prior" in sections and args.prior_train > 0:
             line["prior"] = run_prior(args.prior_train, args.prior_eval, args.prior_rounds, args.prior_epochs,
                                       line)
-        if world == 1 and args.serve_rates:
+        if world == 1 and "gemm" in sections:
+            line["gemm"] = run_gemm()
+        if world == 1 and "serve" in sections and args.serve_rates:
             line["serve"] = {
                 "workload": "2048 agents, Poisson arrivals, T in {8,20,40}, O in {32,256} r~U[5,25], "
                             "obstacles advanced per request, G=8 x N=32, PI warm start on the device, "
