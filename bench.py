@@ -47,7 +47,10 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one swarm_kernel launch of this
 # workload (ncu --set full capture summarised in profiles/swarm_kernel_dynamic_workload.md);
 # set to None whenever the kernel changes until it is captured again.
-SWARM_TRAFFIC_BYTES = 171520
+SWARM_TRAFFIC_BYTES = 155136
+# The same for gemm_tc_kernel on the MLP's grad-W1 product (1024 x 4104 x 1024),
+# profiles/gemm_tc_kernel_mlp_gradW1.md.
+GEMM_GRADW1_TRAFFIC_BYTES = 10520832
 
 
 def parse():
@@ -485,7 +488,8 @@ def run_prior(n_train: int, n_eval: int, rounds: int, epochs: int, single: dict)
     dom = gem["grad_W1"]
     peak = _bf16_peak()
     roof = {"bound": "tensor", "achieved": dom["tflops"], "peak": peak, "unit": "TFLOP/s",
-            "frac": dom["tflops"] / peak, "traffic": None, "kernel": "gemm_tc_kernel (grad_W1 shape)",
+            "frac": dom["tflops"] / peak, "traffic": GEMM_GRADW1_TRAFFIC_BYTES,
+            "kernel": "gemm_tc_kernel (grad_W1 shape)",
             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured"}
     # batched + prior throughput at the single-scene kernel's median path cost
     eq = None
