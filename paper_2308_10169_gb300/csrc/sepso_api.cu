@@ -53,7 +53,6 @@ struct WsLayout {
 WsLayout make_ws(const sepso_config& c) {
   const size_t R = (size_t)c.runs, G = (size_t)c.G, N = (size_t)c.N, D = 2 * (size_t)c.T;
   const size_t M = G * N, Omax = (size_t)(c.max_obstacles > 0 ? c.max_obstacles : 1);
-  const size_t Cmax = G * N;  // at most one CTA per particle
   const size_t DH = 3 * G;
   WsLayout L;
   size_t off = 0;

@@ -57,7 +57,7 @@ __global__ void batch_reset_kernel(const BatchParams p) {
   }
 }
 
-__global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) {
+__global__ void __launch_bounds__(512, 2) batch_kernel(const BatchParams p, int j) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t s_mbar;
   const int4 tl = p.tiles[blockIdx.x];
@@ -90,8 +90,9 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
   if (tid == 0) mbar_init(&s_mbar, 1);
   __syncthreads();
   if (tid == 0 && fit_phase && S.O > 0) {
-    mbar_expect_tx(&s_mbar, (uint32_t)S.O * 16u);
-    bulk_g2s(sC, p.circ + S.co, (uint32_t)S.O * 16u, &s_mbar);
+    const uint32_t bytes = (uint32_t)pair_block_f4(S.O) * 16u;
+    mbar_expect_tx(&s_mbar, bytes);
+    bulk_g2s(sC, p.circ + S.co, bytes, &s_mbar);
   }
 
   const float* hy = p.hyper + S.ho + g * 6;
@@ -303,14 +304,16 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchParams p, int j) 
     const int lp = 32;
     const int ppw = 1;
     const int lsub = lane;
-    const int split = warp_split(T, S.O);
+    const int K = circle_pairs(S.O);
+    const int split = warp_split(T, K);
+    const float2* sNr2 = reinterpret_cast<const float2*>(sC + K);
     const long long sj = S.so + (long long)(jl & 1) * M * (D + 4);
     for (int i0 = warp * ppw; i0 < nl; i0 += nwarps * ppw) {
       const int i = i0 + lane / lp;
       const bool live = i < nl;
       float len;
       int qq;
-      group_fitness(sX + (live ? i : 0) * D, live, lp, T, split, S.O, sx, sy, tx, ty, sC, &len, &qq);
+      group_fitness_pairs(sX + (live ? i : 0) * D, live, lp, T, split, K, sx, sy, tx, ty, sC, sNr2, &len, &qq);
       int imp = 0, pub = 0;
       float pf = INFINITY;
       int pq = 0;
@@ -394,15 +397,19 @@ __global__ void batch_gate_kernel(const BatchParams p) {
     return;
   }
   const float sx = p.pts[4 * s], sy = p.pts[4 * s + 1], tx = p.pts[4 * s + 2], ty = p.pts[4 * s + 3];
-  const int split = warp_split(S.T, S.O);
-  const float4* circ = p.circ + S.co;
+  const int K = circle_pairs(S.O);
+  const int split = warp_split(S.T, K);
+  const float4* cxy = p.circ + S.co;
+  const float2* nr2 = reinterpret_cast<const float2*>(cxy + K);
   float len;
   int q;
-  group_fitness(p.prior_path + (long long)s * p.Dmax, true, 32, S.T, split, S.O, sx, sy, tx, ty, circ, &len, &q);
+  group_fitness_pairs(p.prior_path + (long long)s * p.Dmax, true, 32, S.T, split, K, sx, sy, tx, ty, cxy, nr2, &len,
+                      &q);
   const float f_prior = len + S.alpha * powi((float)q, S.beta);
   int ok = 1;
   if (S.has_prev && S.n_pi > 0) {
-    group_fitness(p.agent_prevT + (long long)s * p.Dmax, true, 32, S.T, split, S.O, sx, sy, tx, ty, circ, &len, &q);
+    group_fitness_pairs(p.agent_prevT + (long long)s * p.Dmax, true, 32, S.T, split, K, sx, sy, tx, ty, cxy, nr2,
+                        &len, &q);
     const float f_prev = len + S.alpha * powi((float)q, S.beta);
     ok = f_prior < f_prev;
   }
@@ -477,7 +484,7 @@ BatchLayout batch_layout(const sepso_batch_scene* sc, int32_t n) {
     L.nS += 2 * M * (D + 4);
     L.nG += (long long)sc[s].G * D;
     L.nT += D;
-    L.nC += sc[s].O;
+    L.nC += sc[s].O > 0 ? pair_block_f4(sc[s].O) : 0;
     L.nH += 6LL * sc[s].G;
     L.nW += 3LL * sc[s].G;
     L.nGS += 2LL * sc[s].G;
@@ -724,7 +731,7 @@ int sepso_batch_create(const sepso_batch_scene* scenes, int32_t n, float map_w, 
     d.so = so; so += 2LL * d.M * (d.D + 4);
     d.go = go; go += (long long)d.G * d.D;
     d.to = to; to += d.D;
-    d.co = co; co += d.O;
+    d.co = co; co += d.O > 0 ? pair_block_f4(d.O) : 0;
     d.ho = ho; ho += 6LL * d.G;
     d.wo = wo; wo += 3LL * d.G;
     d.gso = gso; gso += 2LL * d.G;
@@ -775,12 +782,24 @@ int sepso_batch_set_inputs(sepso_batch_handle h, const float* hyper, const float
   for (int i = 0; i < 4 * h->n; ++i)
     if (!std::isfinite(points[i])) return bfail(SEPSO_EINVAL, "points[%d] not finite", i);
   if (L.nC > 0 && !circles) return bfail(SEPSO_EINVAL, "circles is NULL");
-  std::vector<float4> c4((size_t)std::max(L.nC, 1LL));
-  for (long long o = 0; o < L.nC; ++o) {
-    const float cx = circles[3 * o], cy = circles[3 * o + 1], r = circles[3 * o + 2];
-    if (!std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(r) || r < 0)
-      return bfail(SEPSO_EINVAL, "circle %lld invalid", o);
-    c4[o] = make_float4(cx, cy, r, 4.0f * (r * r));
+  // circle-pair blocks (layout in sepso_device.cuh)
+  std::vector<float4> c4((size_t)std::max(L.nC, 1LL), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+  long long src = 0;
+  for (int s = 0; s < h->n; ++s) {
+    const int O = h->scenes[s].O;
+    if (O == 0) continue;
+    const int K = circle_pairs(O);
+    float4* blk = c4.data() + h->desc[s].co;
+    float* nr2 = reinterpret_cast<float*>(blk + K);
+    for (int o = 0; o < O; ++o, ++src) {
+      const float cx = circles[3 * src], cy = circles[3 * src + 1], r = circles[3 * src + 2];
+      if (!std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(r) || r < 0)
+        return bfail(SEPSO_EINVAL, "circle %lld invalid", src);
+      float* pr = reinterpret_cast<float*>(blk + o / 2);
+      pr[o & 1] = cx;
+      pr[2 + (o & 1)] = cy;
+      nr2[o] = -(r * r);
+    }
   }
   BCUDA(cudaMemcpyAsync(h->ws + L.hyper, hyper, (size_t)L.nH * 4, cudaMemcpyHostToDevice, h->stream));
   BCUDA(cudaMemcpyAsync(h->ws + L.pts, points, (size_t)h->n * 16, cudaMemcpyHostToDevice, h->stream));

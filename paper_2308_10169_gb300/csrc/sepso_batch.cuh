@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "sepso.h"
+#include "sepso_device.cuh"
 
 namespace sepso {
 
@@ -18,7 +19,7 @@ struct BatchScene {
   long long so;   // float offset of the candidate slots (2 x M x (D + 4))
   long long go;   // float offset of the Gbest rows (G x D)
   long long to;   // float offset of the Tbest row and the result row (D)
-  long long co;   // float4 offset of the circles (O)
+  long long co;   // float4 offset of the scene's circle-pair block (pair_block_f4(O) float4s)
   long long ho;   // float offset of the hyper-parameters (G x 6)
   long long wo;   // offset of the group words (3 x G)
   long long gso;  // offset of the group scalars Gfit / GQ (2 x G, by parity)
@@ -44,7 +45,7 @@ struct BatchParams {
   int32_t* PQ;
   float* slots;
   float *Gb, *Tb;
-  const float4* circ;
+  const float4* circ;  // circle-pair blocks of the scenes
   const float* hyper;
   const float* pts;    // 4 per scene: start, target
   unsigned long long* words;
@@ -71,7 +72,7 @@ struct BatchSmem {
     BatchSmem s;
     int off = 0;
     auto al = [](int v) { return (v + 15) / 16 * 16; };
-    s.circ = off; off = al(off + (Omax > 0 ? Omax : 1) * 16);
+    s.circ = off; off = al(off + pair_block_f4(Omax > 0 ? Omax : 1) * 16);
     s.X = off; off = al(off + tile * Dmax * 4);
     s.V = off; off = al(off + tile * Dmax * 4);
     s.P = off; off = al(off + tile * Dmax * 4);

@@ -319,6 +319,134 @@ __device__ __forceinline__ void group_fitness(const float* x, bool live, int lp,
   *q_out = (int)hits;
 }
 
+// ---------------------------------------------------------------------------
+// Packed form of the same test: two circles per FP32x2 instruction.
+// Circles are stored in pairs: pair k holds circles 2k and 2k + 1 as
+// cxy[k] = (cx_2k, cx_2k+1, cy_2k, cy_2k+1) and nr2[k] = (-r_2k^2, -r_2k+1^2), the
+// K = ceil(O / 2) cxy records first, then the K nr2 records, the block padded to
+// whole float4s (pair_block_f4 float4s); an odd O is completed by a circle of
+// radius 0 at the origin (it never counts).  With m = max(|along| - h, 0) and the
+// unscaled perpendicular p, a pair collides when m^2 + p^2 - r^2 < 0, formed as
+// fma(m, m, fma(p, p, -r^2)): this is exactly -1/4 of the scaled form's s above
+// (scaling by powers of two commutes with rounding), never -0, so the sign bit
+// gives the same decision; hits accumulate as integers.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int circle_pairs(int O) { return (O + 1) >> 1; }
+__host__ __device__ inline int pair_block_f4(int O) {
+  const int K = circle_pairs(O);
+  return K + ((K + 1) >> 1);
+}
+
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+struct PairFrame {
+  unsigned long long ux, uy, nmu, nx, ny, nmn;  // each value in both halves
+  float h;
+};
+
+__device__ __forceinline__ PairFrame pair_frame(float ax, float ay, float bx, float by, float* len_out) {
+  const float dx = bx - ax, dy = by - ay;
+  const float len = sqrtf(fmaf(dx, dx, dy * dy));
+  float ux = 1.0f, uy = 0.0f;
+  if (len > 0.0f) {
+    const float inv = 1.0f / len;
+    ux = dx * inv;
+    uy = dy * inv;
+  }
+  const float mx = 0.5f * (ax + bx), my = 0.5f * (ay + by);
+  const float mu = fmaf(mx, ux, my * uy);
+  const float nx = -uy, ny = ux;
+  const float mn = fmaf(mx, nx, my * ny);
+  PairFrame f;
+  f.ux = pack2(ux, ux);
+  f.uy = pack2(uy, uy);
+  f.nmu = pack2(-mu, -mu);
+  f.nx = pack2(nx, nx);
+  f.ny = pack2(ny, ny);
+  f.nmn = pack2(-mn, -mn);
+  f.h = 0.5f * len;
+  *len_out = len;
+  return f;
+}
+
+__device__ __forceinline__ int pair_hits(const PairFrame& f, const float4* __restrict__ cxy,
+                                         const float2* __restrict__ nr2, int k0, int k1) {
+  int hits = 0;
+#pragma unroll 4
+  for (int k = k0; k < k1; ++k) {
+    const float4 c = cxy[k];
+    const float2 w = nr2[k];
+    const unsigned long long CX = pack2(c.x, c.y), CY = pack2(c.z, c.w), W = pack2(w.x, w.y);
+    const unsigned long long AL = ffma2(CX, f.ux, ffma2(CY, f.uy, f.nmu));
+    const unsigned long long P = ffma2(CX, f.nx, ffma2(CY, f.ny, f.nmn));
+    float al0, al1;
+    unpack2(AL, al0, al1);
+    const float m0 = fmaxf(fabsf(al0) - f.h, 0.0f), m1 = fmaxf(fabsf(al1) - f.h, 0.0f);
+    const unsigned long long S = ffma2(pack2(m0, m1), pack2(m0, m1), ffma2(P, P, W));
+    float s0, s1;
+    unpack2(S, s0, s1);
+    hits += (int)(__float_as_uint(s0) >> 31) + (int)(__float_as_uint(s1) >> 31);
+  }
+  return hits;
+}
+
+// group_fitness on circle pairs (K of them; split chunks of pairs per segment).
+__device__ __forceinline__ void group_fitness_pairs(const float* x, bool live, int lp, int T, int split, int K,
+                                                    float sx, float sy, float tx, float ty,
+                                                    const float4* cxy, const float2* nr2, float* len_out,
+                                                    int* q_out) {
+  const int lsub = (threadIdx.x & 31) & (lp - 1);
+  const int items = (T + 1) * split;
+  const int chunk = (K + split - 1) / split;
+  float len = 0.0f;
+  int hits = 0;
+  if (live) {
+    for (int it = lsub; it < items; it += lp) {
+      const int sg = it % (T + 1);
+      const int c = it / (T + 1);
+      const float ax = (sg == 0) ? sx : x[sg - 1];
+      const float ay = (sg == 0) ? sy : x[T + sg - 1];
+      const float bx = (sg == T) ? tx : x[sg];
+      const float by = (sg == T) ? ty : x[T + sg];
+      float l;
+      const PairFrame f = pair_frame(ax, ay, bx, by, &l);
+      if (c == 0) len += l;
+      hits += pair_hits(f, cxy, nr2, c * chunk, min(K, c * chunk + chunk));
+    }
+  }
+  for (int off = lp >> 1; off > 0; off >>= 1) {
+    len += __shfl_xor_sync(0xffffffffu, len, off);
+    hits += __shfl_xor_sync(0xffffffffu, hits, off);
+  }
+  *len_out = len;
+  *q_out = hits;
+}
+
+// Pairs of a float4 circle list (cx, cy, r, .) into a pair block (cooperative,
+// all threads of the block; the caller synchronises before use).
+__device__ __forceinline__ void circles_to_pairs(const float4* circ, int O, float4* block) {
+  const int K = circle_pairs(O);
+  float2* nr2 = reinterpret_cast<float2*>(block + K);
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const float4 a = circ[2 * k];
+    const float4 b = (2 * k + 1 < O) ? circ[2 * k + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    block[k] = make_float4(a.x, b.x, a.y, b.y);
+    nr2[k] = make_float2(-(a.z * a.z), (2 * k + 1 < O) ? -(b.z * b.z) : 0.0f);
+  }
+}
+
 // Circle chunks per segment for a warp (32 lanes) evaluating one particle of T
 // waypoints against O circles: the split (1..8) that minimises the per-lane work
 // rounds * (chunk + setup), so that the warp's rounds are nearly full.

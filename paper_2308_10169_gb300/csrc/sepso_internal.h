@@ -14,7 +14,7 @@ struct RunCtl;
 
 // Shared-memory carve of swarm_kernel (byte offsets); identical on host and device.
 struct SmemLayout {
-  int circ, win, X, V, P, R, Gown, Tb, Pfit, PQ, Q, Imp, Len, Gfit, GQ, Gsrc, total;
+  int circ, pairs, win, X, V, P, R, Gown, Tb, Pfit, PQ, Q, Imp, Len, Gfit, GQ, Gsrc, total;
   __host__ __device__ static SmemLayout make(int Omax, int ppc, int D, int T, int G, int tw);
 };
 

@@ -37,6 +37,8 @@ __host__ __device__ SmemLayout SmemLayout::make(int Omax, int ppc, int D, int T,
   int off = 0;
   s.circ = off;
   off = align_up(off + (Omax > 0 ? Omax : 1) * 16, 16);
+  s.pairs = off;
+  off = align_up(off + pair_block_f4(Omax > 0 ? Omax : 1) * 16, 16);
   s.win = off;
   off = align_up(off + tw * 8, 16);
   s.X = off;
@@ -208,15 +210,21 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
   }
 
   bool failed = false;
+  float4* sPairs = reinterpret_cast<float4*>(smem + L.pairs);
+  const int K = circle_pairs(p.O);
   if (p.O > 0) {
     const bool landed = mbar_wait_bounded(&s_mbar, 0, kWaitLimitNs);
     if (__syncthreads_or(landed ? 0 : 1)) {
       failed = true;
       if (tid == 0) ctl->status = SEPSO_ETIMEOUT;
+    } else {
+      circles_to_pairs(sC, p.O, sPairs);
+      __syncthreads();
     }
   } else {
     __syncthreads();
   }
+  const float2* sNr2 = reinterpret_cast<const float2*>(sPairs + K);
 
   const int nseg = T + 1;
   // Iterations already run by this run (across launches): they index the
@@ -250,7 +258,8 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
         const bool live = i < nl;
         float len;
         int qq;
-        group_fitness(sX + (live ? i : 0) * D, live, lp, T, p.split, p.O, sx, sy, tx, ty, sC, &len, &qq);
+        group_fitness_pairs(sX + (live ? i : 0) * D, live, lp, T, p.split, K, sx, sy, tx, ty, sPairs, sNr2, &len,
+                            &qq);
         int imp = 0, pub = 0;
         float pf = INFINITY;
         int pq = 0;

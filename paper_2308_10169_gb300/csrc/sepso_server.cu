@@ -93,7 +93,7 @@ ServerLayout server_layout(const sepso_server_config& c, int S) {
   L.slots = take(S * 2 * M * (Dm + 4) * 4);
   L.Gb = take(S * G * Dm * 4);
   L.Tb = take(S * Dm * 4);
-  L.circ = take(S * Om * 16);
+  L.circ = take(S * (size_t)pair_block_f4((int)Om) * 16);
   L.hyper = take((size_t)c.n_agents * G * 6 * 4);
   L.pts = take(S * 16);
   L.words = take(S * 3 * G * 8);
@@ -108,7 +108,7 @@ ServerLayout server_layout(const sepso_server_config& c, int S) {
   L.res = take(S * sizeof(sepso_result));
   L.prevT = take((size_t)c.n_agents * Dm * 4);
   L.admits = take(S * sizeof(Admit));
-  L.admit_circ = take(S * Om * 16);
+  L.admit_circ = take(S * (size_t)pair_block_f4((int)Om) * 16);
   L.status = take(4);
   L.total = a256(off);
   return L;
@@ -154,8 +154,10 @@ __global__ void server_admit_kernel(BatchParams p, const Admit* admits, const fl
     p.plv2[2 * s] = p.plv2[2 * s + 1] = INFINITY;
     p.done[s] = 0;
   }
-  float4* circ = const_cast<float4*>(p.circ) + (long long)s * Omax;
-  for (int o = threadIdx.x; o < S.O; o += blockDim.x) circ[o] = admit_circ[A.c0 + o];
+  // the request's circle-pair block, staged by the host in the same layout
+  float4* circ = const_cast<float4*>(p.circ) + S.co;
+  const int nf4 = S.O > 0 ? pair_block_f4(S.O) : 0;
+  for (int o = threadIdx.x; o < nf4; o += blockDim.x) circ[o] = admit_circ[A.c0 + o];
   for (int g = threadIdx.x; g < 2 * S.G; g += blockDim.x) {
     p.Gfit2[S.gso + g] = INFINITY;
     p.GQ2[S.gso + g] = 0;
@@ -173,7 +175,7 @@ struct Request {
 
 struct Slot {
   bool busy = false;
-  int agent = -1, T = 0;
+  int agent = -1, T = 0, O = 0;
   long long tag = 0;
   long long start_tick = 0;  // tick of the first iteration
   double arrival = 0.0;
@@ -194,6 +196,7 @@ struct sepso_server_ctx {
   int smem_optin = 0, tile = 32, threads = 128;
   size_t smem = 0;
   std::vector<Slot> slots;
+  std::vector<int> order;  // occupied slots by cost (scratch of upload_tiles)
   std::deque<Request> queue;
   std::vector<int> agent_cycle;
   std::vector<char> agent_busy;
@@ -332,7 +335,7 @@ int admit(sepso_server_ctx* h, int b) {
     d.so = (long long)i * 2 * M * (h->Dm + 4);
     d.go = (long long)i * c.G * h->Dm;
     d.to = (long long)i * h->Dm;
-    d.co = (long long)i * h->Om;
+    d.co = (long long)i * pair_block_f4(h->Om);
     d.ho = (long long)r.agent * c.G * 6;
     d.wo = (long long)i * 3 * c.G;
     d.gso = (long long)i * 2 * c.G;
@@ -348,15 +351,26 @@ int admit(sepso_server_ctx* h, int b) {
     std::memcpy(A.pts, r.pts, sizeof A.pts);
     A.slot = i;
     A.c0 = c0;
-    for (int o = 0; o < r.O; ++o) {
-      const float rr = r.circ[3 * o + 2];
-      h->h_acirc[b][c0 + o] = make_float4(r.circ[3 * o], r.circ[3 * o + 1], rr, 4.0f * (rr * rr));
+    if (r.O > 0) {
+      // circle-pair block (layout in sepso_device.cuh)
+      const int K = circle_pairs(r.O), nf4 = pair_block_f4(r.O);
+      float4* blk = h->h_acirc[b] + c0;
+      for (int q = 0; q < nf4; ++q) blk[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      float* nr2 = reinterpret_cast<float*>(blk + K);
+      for (int o = 0; o < r.O; ++o) {
+        const float rr = r.circ[3 * o + 2];
+        float* pr = reinterpret_cast<float*>(blk + o / 2);
+        pr[o & 1] = r.circ[3 * o];
+        pr[2 + (o & 1)] = r.circ[3 * o + 1];
+        nr2[o] = -(rr * rr);
+      }
+      c0 += nf4;
     }
-    c0 += r.O;
     Slot& sl = h->slots[i];
     sl.busy = true;
     sl.agent = r.agent;
     sl.T = r.T;
+    sl.O = r.O;
     sl.tag = r.tag;
     sl.start_tick = h->tick + 1;
     sl.arrival = r.arrival;
@@ -379,15 +393,22 @@ int admit(sepso_server_ctx* h, int b) {
   return SEPSO_OK;
 }
 
+// Work items of the occupied slots, costliest first (segments x circles), so that
+// each launch ends with its cheapest items.
 int upload_tiles(sepso_server_ctx* h, int b) {
   if (!h->tiles_dirty) return SEPSO_OK;
+  h->order.clear();
+  for (size_t i = 0; i < h->slots.size(); ++i)
+    if (h->slots[i].busy) h->order.push_back((int)i);
+  std::stable_sort(h->order.begin(), h->order.end(), [h](int a, int c) {
+    const Slot &x = h->slots[a], &y = h->slots[c];
+    return (long long)(x.T + 1) * (std::max(x.O, 1) + 8) > (long long)(y.T + 1) * (std::max(y.O, 1) + 8);
+  });
   int n = 0;
-  for (size_t i = 0; i < h->slots.size(); ++i) {
-    if (!h->slots[i].busy) continue;
+  for (int i : h->order)
     for (int g = 0; g < h->cfg.G; ++g)
       for (int n0 = 0; n0 < h->cfg.N; n0 += h->tile)
-        h->h_tiles[b][n++] = make_int4((int)i, g, n0, std::min(h->tile, h->cfg.N - n0));
-  }
+        h->h_tiles[b][n++] = make_int4(i, g, n0, std::min(h->tile, h->cfg.N - n0));
   if (n > 0)
     SCUDA(cudaMemcpyAsync(h->ws + h->L.tiles, h->h_tiles[b], (size_t)n * sizeof(int4), cudaMemcpyHostToDevice,
                           h->stream));
@@ -440,15 +461,17 @@ int sepso_server_create(const sepso_server_config* cfg, void* d_workspace, size_
   cudaError_t e = batch_configure(&h->smem_optin);
   h->smem = (size_t)BatchSmem::make(h->Om, h->tile, h->Dm, cfg->G).total;
   if (e == cudaSuccess && h->smem > (size_t)h->smem_optin) {
+    const size_t need = h->smem;
     delete h;
-    return sfail(SEPSO_ERANGE, "a work item needs %zu B of shared memory", h->smem);
+    return sfail(SEPSO_ERANGE, "a work item needs %zu B of shared memory", need);
   }
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaMallocHost(reinterpret_cast<void**>(&h->rb_done[i]), (size_t)S * 4);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->rb_res[i]), (size_t)S * sizeof(sepso_result));
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->rb_wp[i]), (size_t)S * h->Dm * 4);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->h_admit[i]), (size_t)S * sizeof(Admit));
-    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->h_acirc[i]), (size_t)S * h->Om * 16);
+    if (e == cudaSuccess)
+      e = cudaMallocHost(reinterpret_cast<void**>(&h->h_acirc[i]), (size_t)S * pair_block_f4(h->Om) * 16);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&h->h_tiles[i]), (size_t)S * tps * sizeof(int4));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_ev[i], cudaEventDisableTiming);
   }
