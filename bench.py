@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-seconds", type=float, default=0.0,
+                    help="CPU budget of the reference arm (0 = from --steps/--warmup, 10..150 s)")
     ap.add_argument("--hsef-evolutions", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=0, help="0 = same as --steps")
     ap.add_argument("--cost-cycles", type=int, default=200)
@@ -172,10 +174,22 @@ def oracle_cycles(seconds: float, max_cycles: int, seed: int = 0):
     return cfg, times, iters, costs
 
 
+def aggregate_timing(total_ms: float, steps: int, world: int):
+    """Whole-job timing over the ranks (one replica per GPU, no data exchange): the
+    slowest rank's time, and the units all ranks processed over it."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_max = float(t.item())
+    return total_max, world * steps / (total_max / 1e3)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    budget = max(10.0, min(150.0, 3.0 * (args.steps + args.warmup)))
+    budget = args.ref_seconds if args.ref_seconds > 0 else max(10.0, min(150.0, 3.0 * (args.steps + args.warmup)))
     warm = min(args.warmup, 1)
     cfg, times, iters, costs = oracle_cycles(budget, warm + args.steps)
     times, iters, costs = times[warm:], iters[warm:], costs[warm:]
@@ -291,12 +305,7 @@ def run_ours(args, rank, world, local):
         pl.plan_async()
         costs.append(pl.read_result()["cost"])
 
-    # max over ranks
-    t_local = torch.tensor([total_ms], dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    total_max = float(t_local.item())
-    value = world * K / (total_max / 1e3)
+    total_max, value = aggregate_timing(total_ms, K, world)
     pe_local = iters * cfg.G * cfg.N
     flops = iters * cfg.G * cfg.N * (cfg.T + 1) * (FLOPS_PER_PAIR * scene.O + FLOPS_PER_SEGMENT)
     achieved = flops / (plan_ms.sum() / 1e3) / 1e12
