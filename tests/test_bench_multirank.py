@@ -33,13 +33,14 @@ def test_timing_is_the_slowest_rank_and_value_counts_all_ranks(tmp_path):
         rank, world, _ = bench.dist_env()
         dist.init_process_group("gloo")
         total, value = bench.aggregate_timing(100.0 * (rank + 1), 50, world)
-        print(json.dumps({{"rank": rank, "total": total, "value": value}}), flush=True)
+        with open(os.path.join({str(tmp_path)!r}, f"rank{{rank}}.json"), "w") as f:
+            json.dump({{"rank": rank, "total": total, "value": value}}, f)
         dist.barrier()
         dist.destroy_process_group()
     """))
     out = _torchrun([str(script)], cwd=tmp_path)
     assert out.returncode == 0, out.stderr[-2000:]
-    rows = [json.loads(l) for l in out.stdout.splitlines() if l.startswith("{")]
+    rows = [json.loads((tmp_path / f"rank{r}.json").read_text()) for r in range(2)]
     assert sorted(r["rank"] for r in rows) == [0, 1]
     for r in rows:
         assert r["total"] == 200.0                  # the slower rank's 200 ms
