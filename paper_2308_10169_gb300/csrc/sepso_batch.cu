@@ -249,6 +249,9 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchParams p, int 
           if (p.done != nullptr) p.done[s] = 1;
         }
       }
+      // The obstacle bulk copy issued at the start must land before the CTA exits
+      // (its shared memory is handed to the next CTA).
+      if (tid == 0 && fit_phase && S.O > 0) mbar_wait_bounded(&s_mbar, 0, kWaitLimitNs);
       return;
     }
     // Rows for this group's update.

@@ -216,7 +216,10 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
     const bool landed = mbar_wait_bounded(&s_mbar, 0, kWaitLimitNs);
     if (__syncthreads_or(landed ? 0 : 1)) {
       failed = true;
-      if (tid == 0) ctl->status = SEPSO_ETIMEOUT;
+      if (tid == 0) {
+        ctl->status = SEPSO_ETIMEOUT;
+        mbar_wait_bounded(&s_mbar, 0, kWaitLimitNs);  // once more: no copy in flight at exit
+      }
     } else {
       circles_to_pairs(sC, p.O, sPairs);
       __syncthreads();
@@ -521,7 +524,10 @@ __global__ void __launch_bounds__(256) evaluate_kernel(const EvalParams p) {
   if (p.O > 0) {
     const bool landed = mbar_wait_bounded(&s_mbar, 0, kWaitLimitNs);
     if (__syncthreads_or(landed ? 0 : 1)) {
-      if (tid == 0) atomicExch(p.status, SEPSO_ETIMEOUT);
+      if (tid == 0) {
+        atomicExch(p.status, SEPSO_ETIMEOUT);
+        mbar_wait_bounded(&s_mbar, 0, kWaitLimitNs);  // once more: no copy in flight at exit
+      }
       return;
     }
   } else {
