@@ -527,7 +527,9 @@ const char* sepso_prior_last_error(void);
  * (device FP32, or NULL), then max(., 0) if relu, then 0 where mask[m][n] (BF16,
  * row stride ldm, or NULL) is not > 0.  Outputs: Cf (FP32, row stride ldcf)
  * and/or Cb (BF16, ldcb), device, either may be NULL.  tile_n: 64, 128 or 256
- * columns per CTA tile (128 rows), 0 = chosen from the grid it gives.  Async on
+ * columns per 128-row tile on persistent CTAs (each loops over tiles, the
+ * epilogue of one overlapping the main loop of the next), -64 / -128 / -256 the
+ * same widths with one tile per CTA, 0 = chosen from the grid it gives.  Async on
  * stream; a device-side timeout is reported by the next sepso_gemm_bf16_sync.
  * Errors: EINVAL, ECUDA. */
 int sepso_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, int32_t lda, int32_t ldb,

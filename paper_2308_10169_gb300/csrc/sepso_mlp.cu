@@ -282,6 +282,188 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent form: each CTA loops over tiles (t = blockIdx.x, + gridDim.x ...),
+// with two BN-column accumulators in tensor memory so that the epilogue of one
+// tile overlaps the main loop of the next.  Six warps: warp 0 lane 0 is the TMA
+// producer (a ring of stages shared by all the CTA's tiles), warp 1 lane 0 issues
+// the MMAs, warps 2..5 drain the accumulators (warp w reads TMEM lanes
+// 32 (w % 4) .. + 31, as the hardware requires) through a per-warp 32 x 33 staging
+// tile, storing rows of 32 consecutive columns (coalesced).
+// ---------------------------------------------------------------------------
+constexpr int kPThreads = 192;
+constexpr int kStageWarpFloats = 32 * 33;
+constexpr int kPRing = 192 * 1024 - 4 * kStageWarpFloats * 4 - 1024;  // ring + staging + alignment in 192 KB
+constexpr int kPSmem = 192 * 1024;
+
+template <int BN>
+struct PTile {
+  static constexpr int kABytes = kBM * kBK * 2;
+  static constexpr int kStage = kABytes + BN * kBK * 2;
+  static constexpr int kStages = (kPRing / kStage) < 8 ? (kPRing / kStage) : 8;
+  static constexpr int kRingBytes = kStages * kStage;
+  static_assert(kStages >= 2, "ring too small");
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kPThreads, 1)
+    gemm_tc_persistent(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                       const GemmArgs g) {
+  using TL = PTile<BN>;
+  constexpr int S = TL::kStages;
+  extern __shared__ uint8_t psm_raw[];
+  __shared__ uint64_t full[S], empty[S], acc_full[2], acc_empty[2], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  uint8_t* ring = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(psm_raw) + 1023) & ~uintptr_t(1023));
+  float* stage_all = reinterpret_cast<float*>(ring + TL::kRingBytes);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = (g.M + kBM - 1) / kBM, ntl = (g.N + BN - 1) / BN;
+  const int tiles = mt * ntl;
+  const int nkb = (g.K + kBK - 1) / kBK;
+  constexpr uint32_t kIdesc = mma_idesc_bf16(kBM, BN);
+
+  if (warp == 0) tmem_alloc(&tmem_base, 2 * BN);
+  if (tid == 32) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    mbar_init(&done, 1);
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: one running k-block counter across the CTA's tiles
+      long long it = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x) {
+        const int m0 = (t % mt) * kBM, n0 = (t / mt) * BN;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % S);
+          const long long u = it / S;
+          if (u >= 1 && !mbar_wait_bounded(&empty[s], (uint32_t)((u - 1) & 1), kWaitLimitNs)) {
+            atomicExch(&s_fail, 1);
+            stop = true;
+            break;
+          }
+          if (*(volatile int*)&s_fail) {
+            stop = true;
+            break;
+          }
+          uint8_t* sa = ring + s * TL::kStage;
+          mbar_expect_tx(&full[s], (uint32_t)TL::kStage);
+          tma_load_2d(sa, &tmA, kb * kBK, m0, &full[s]);
+          tma_load_2d(sa + TL::kABytes, &tmB, kb * kBK, n0, &full[s]);
+        }
+      }
+      // boxes still in flight land before the CTA exits
+      for (long long q = (it > S ? it - S : 0); q < it; ++q)
+        mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      long long it = 0;
+      int lt = 0;
+      bool stop = false;
+      for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x, ++lt) {
+        const int a = lt & 1;
+        const int v = lt >> 1;
+        if (v >= 1 && !mbar_wait_bounded(&acc_empty[a], (uint32_t)((v - 1) & 1), kWaitLimitNs)) {
+          atomicExch(&s_fail, 1);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(a * BN);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = (int)(it % S);
+          if (!mbar_wait_bounded(&full[s], (uint32_t)((it / S) & 1), kWaitLimitNs) || *(volatile int*)&s_fail) {
+            atomicExch(&s_fail, 1);
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint8_t* sa = ring + s * TL::kStage;
+          const uint8_t* sb = sa + TL::kABytes;
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk)
+            mma_bf16(acc, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), kIdesc,
+                     (kb > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (!stop) mma_commit(&acc_full[a]);
+      }
+      mma_commit(&done);  // tracks every MMA issued above
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter (warp % 4)
+    const int q = warp & 3;
+    float* st = stage_all + (warp - 2) * kStageWarpFloats;
+    const bool vec_ok = true;
+    (void)vec_ok;
+    int lt = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
+      const int a = lt & 1;
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait_bounded(&acc_full[a], (uint32_t)((lt >> 1) & 1), kWaitLimitNs) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok || *(volatile int*)&s_fail) {
+        if (lane == 0) atomicExch(&s_fail, 1);
+        break;
+      }
+      tc_fence_after();
+      const int m0 = (t % mt) * kBM, n0 = (t / mt) * BN;
+      const int rbase = m0 + q * 32;
+      float v[32];
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        // this lane holds row rbase + lane, columns c0 .. c0 + 31
+#pragma unroll
+        for (int c = 0; c < 32; ++c) st[lane * 33 + c] = v[c];
+        __syncwarp();
+        const int col = n0 + c0 + lane;
+        if (col < g.N) {
+          const float bcol = g.bias ? g.bias[col] : 0.0f;
+          for (int r = 0; r < 32; ++r) {
+            const int row = rbase + r;
+            if (row >= g.M) break;
+            float x = g.alpha * st[r * 33 + lane] + bcol;
+            if (g.relu) x = fmaxf(x, 0.0f);
+            if (g.mask && !(__bfloat162float(g.mask[(size_t)row * g.ldm + col]) > 0.0f)) x = 0.0f;
+            if (g.Cf) g.Cf[(size_t)row * g.ldcf + col] = x;
+            if (g.Cb) g.Cb[(size_t)row * g.ldcb + col] = __float2bfloat16_rn(x);
+          }
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[a]);
+    }
+  }
+  __syncwarp();
+  // teardown: every MMA has completed before tensor memory is released
+  if (!mbar_wait_bounded(&done, 0u, kWaitLimitNs)) atomicExch(&s_fail, 1);
+  if (__syncthreads_or(*(volatile int*)&s_fail) && tid == 0 && g.status) atomicExch(g.status, SEPSO_ETIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 2 * BN);
+}
+
 }  // namespace sepso
 
 namespace sepso {
@@ -618,6 +800,43 @@ int gemm_launch_bn(const CUtensorMap& ta, const GemmArgs& g, cudaStream_t s) {
   return SEPSO_OK;
 }
 
+template <int BN>
+int gemm_launch_persistent(const CUtensorMap& ta, const GemmArgs& g, cudaStream_t s) {
+  CUtensorMap tb;
+  PTRY(make_map(&tb, g.B, g.N, g.K, g.ldb, BN));
+  static thread_local int configured_device = -1;
+  int dev = 0;
+  PCUDA(cudaGetDevice(&dev));
+  if (configured_device != dev) {
+    PCUDA(cudaFuncSetAttribute(sepso::gemm_tc_persistent<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               sepso::kPSmem));
+    configured_device = dev;
+  }
+  const long long tiles = (long long)((g.M + sepso::kBM - 1) / sepso::kBM) * ((g.N + BN - 1) / BN);
+  if (g_num_sms <= 0) choose_tile_n(g.M, g.N);  // fills the SM count
+  const int grid = (int)std::min<long long>(tiles, (long long)g_num_sms);
+  sepso::gemm_tc_persistent<BN><<<grid, sepso::kPThreads, sepso::kPSmem, s>>>(ta, tb, g);
+  PCUDA(cudaGetLastError());
+  return SEPSO_OK;
+}
+
+// Kernel and tile width for a product (positive: persistent; negative: one tile
+// per CTA), from a sweep of both kernels on GB300 (TFLOP/s, persistent / one per CTA):
+//   many tiles (>= 2 per SM at width 256; 4096^3: 975 / 941)  -> persistent, 256
+//   about one wave of 256-wide tiles (1024 x 4104 x 1024: 316 / 364)   -> one per CTA, 256
+//   few tiles and a long K (1024 x 1024 x 4104, width 64: 237 / 262)  -> one per CTA, 64
+//   few tiles and a short K (1024 x 512 x 1024: 66 / 60)              -> persistent, 64
+int choose_tile_n_auto(int M, int N, int K) {
+  choose_tile_n(M, N);  // fills the SM count
+  const long long mt = (M + sepso::kBM - 1) / sepso::kBM;
+  const long long t256 = mt * ((N + 255) / 256);
+  if (t256 >= 2LL * g_num_sms) return 256;
+  if (4 * t256 >= 3LL * g_num_sms) return -256;
+  return K >= 2048 ? -64 : 64;
+}
+
+// tile_n: 0 automatic (persistent kernel); 64 / 128 / 256 the persistent kernel
+// with that tile; -64 / -128 / -256 the one-tile-per-CTA kernel.
 int gemm_launch(const GemmArgs& g, cudaStream_t s, int tile_n = 0) {
   if (g.M < 1 || g.N < 1 || g.K < 8 || (g.K & 7) || (g.lda & 7) || (g.ldb & 7) || g.lda < g.K || g.ldb < g.K)
     return pfail(SEPSO_EINVAL, "gemm: bad sizes M %d N %d K %d lda %d ldb %d", g.M, g.N, g.K, g.lda, g.ldb);
@@ -625,14 +844,17 @@ int gemm_launch(const GemmArgs& g, cudaStream_t s, int tile_n = 0) {
     return pfail(SEPSO_EINVAL, "gemm: A and B must be 16-byte aligned device arrays");
   if ((g.Cf && g.ldcf < g.N) || (g.Cb && g.ldcb < g.N) || (g.mask && g.ldm < g.N))
     return pfail(SEPSO_EINVAL, "gemm: output or mask row stride below N");
-  if (tile_n == 0) tile_n = choose_tile_n(g.M, g.N);
+  if (tile_n == 0) tile_n = choose_tile_n_auto(g.M, g.N, g.K);
   CUtensorMap ta;
   PTRY(make_map(&ta, g.A, g.M, g.K, g.lda, sepso::kBM));
   switch (tile_n) {
-    case 64: return gemm_launch_bn<64>(ta, g, s);
-    case 128: return gemm_launch_bn<128>(ta, g, s);
-    case 256: return gemm_launch_bn<256>(ta, g, s);
-    default: return pfail(SEPSO_EINVAL, "gemm: tile N %d (64, 128 or 256)", tile_n);
+    case 64: return gemm_launch_persistent<64>(ta, g, s);
+    case 128: return gemm_launch_persistent<128>(ta, g, s);
+    case 256: return gemm_launch_persistent<256>(ta, g, s);
+    case -64: return gemm_launch_bn<64>(ta, g, s);
+    case -128: return gemm_launch_bn<128>(ta, g, s);
+    case -256: return gemm_launch_bn<256>(ta, g, s);
+    default: return pfail(SEPSO_EINVAL, "gemm: tile N %d (64, 128 or 256; negative for one tile per CTA)", tile_n);
   }
 }
 

@@ -141,7 +141,9 @@ class Prior:
 def gemm_bf16(A: torch.Tensor, B: torch.Tensor, alpha: float = 1.0, bias: torch.Tensor | None = None,
               relu: bool = False, mask: torch.Tensor | None = None, out_f32: bool = True,
               out_bf16: bool = False, sync: bool = True, tile_n: int = 0):
-    """C = epilogue(alpha * A @ B^T) on the tensor cores; A (M, K), B (N, K) BF16 CUDA."""
+    """C = epilogue(alpha * A @ B^T) on the tensor cores; A (M, K), B (N, K) BF16 CUDA.
+    tile_n: 0 automatic; 64 / 128 / 256 the persistent kernel; negative, the
+    one-tile-per-CTA kernel with that width."""
     assert A.is_cuda and B.is_cuda and A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16
     assert A.stride(1) == 1 and B.stride(1) == 1 and A.shape[1] == B.shape[1]
     M, K = A.shape

@@ -47,12 +47,13 @@ def test_gemm_matches_fp32_reference(native, M, N, K):
     assert torch.max(torch.abs(got - ref)).item() <= tol
 
 
-@pytest.mark.parametrize("tile_n", [64, 128, 256])
+@pytest.mark.parametrize("tile_n", [64, 128, 256, -64, -128, -256])
 def test_gemm_tile_widths_agree(native, tile_n):
-    # every tile width gives the same products (ragged M, N and K; K spans several
-    # pipeline stages and wraps the stage ring)
+    # every tile width of both kernels (positive: persistent with two accumulators;
+    # negative: one tile per CTA) gives the same products (ragged M, N and K; K spans
+    # several pipeline stages and wraps the stage ring; several tiles per CTA)
     g = torch.Generator().manual_seed(tile_n)
-    M, N, K = 333, 300, 1096
+    M, N, K = 2333, 1300, 1096
     A = torch.randn(M, K, generator=g).to(torch.bfloat16)
     B = torch.randn(N, K, generator=g).to(torch.bfloat16)
     ref = A.double() @ B.double().T
