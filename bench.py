@@ -563,7 +563,33 @@ def cpu_baseline(seconds: float):
             "sample": f"first {n} planning cycles of the same dynamic run (hyper-parameters as "
                       f"sampled, no HSEF), FP64, one thread, {total:.1f} s",
             "particle_evals_per_s": sum(iters) * cfg.G * cfg.N / total,
-            "iters_per_plan": float(np.mean(iters)), "median_cost": float(np.median(costs))}
+            "iters_per_plan": float(np.mean(iters)), "median_cost": float(np.median(costs)),
+            "_costs": [float(c) for c in costs], "_iters": [int(i) for i in iters]}
+
+
+def oracle_match(seeds: int = 64):
+    """Path cost of the GPU planner beside the FP64 oracle's on the static workload
+    (400 x 400 map, T = 8, G = 8 x N = 32, 16 circles, 100 iterations), one plan per
+    seed: FP32 and FP64 trajectories separate, so the medians over the seeds are the
+    comparison (the parity tests hold them within 1%)."""
+    import oracle
+    from paper_2308_10169_gb300 import Planner
+    from paper_2308_10169_gb300.inputs import static_workload
+    gpu, ora = [], []
+    t0 = time.perf_counter()
+    for s in range(seeds):
+        cfg, scene, hyper = static_workload(s)
+        cfg = cfg.with_(seed=s)
+        pl = Planner(cfg)
+        pl.set_hyper(hyper)
+        pl.set_scene(scene)
+        gpu.append(float(pl.plan()["cost"]))
+        ora.append(float(oracle.Swarm(cfg, hyper).plan(oracle.Scene(scene.start, scene.target,
+                                                                       scene.circles))["cost"]))
+    g, o = float(np.median(gpu)), float(np.median(ora))
+    return {"workload": "static: 400x400, T=8, G=8 x N=32, 16 circles, 100 iterations, alpha 1000, beta 1",
+            "seeds": seeds, "gpu_median_cost": g, "oracle_median_cost": o, "rel_diff": (g - o) / o,
+            "seconds": time.perf_counter() - t0}
 
 
 def main():
@@ -582,7 +608,11 @@ def main():
         line = {"metric": METRIC, "unit": UNIT, "sections": sorted(sections)} if rank == 0 else None
     if rank == 0:
         if world == 1 and "cpu" in sections and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+            cb = cpu_baseline(args.cpu_seconds)
+            cb.pop("_costs")
+            cb.pop("_iters")
+            line["cpu_baseline"] = cb
+            line["oracle_match"] = oracle_match()
         if world == 1 and "batch" in sections and args.batch_scenes > 0:
             line["batch"] = run_batch(args.batch_scenes, args.batch_iters)
         if world == 1 and "prior" in sections and args.prior_train > 0:
