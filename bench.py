@@ -468,8 +468,63 @@ def run_serve(rate: float, seconds: float, n_agents: int = 2048):
     st = sv.stats()
     return {"offered_per_s": rate, "requests": len(arr), "plans_per_s": len(done) / span,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "iters_per_plan": float(np.mean([d["iters"] for d in done])), "slots": st["slots"],
+            "iters_per_plan": float(np.mean([d["iters"] for d in done])),
+            "median_cost": float(np.median([d["cost"] for d in done])), "slots": st["slots"],
             "ticks": st["ticks"], "gpu_launches": st["launches"]}
+
+
+def serve_single_scene(n: int = 256, n_agents: int = 2048):
+    """The plain single-scene kernel on the serving mix: the first request of n agents
+    (no previous path), one plan at a time through sepso_plan (host scene in,
+    waypoints out), with the server's planner settings; and the same n requests as
+    one burst through the server.  Same algorithm and random streams, so the median
+    costs agree; throughput and latency are the comparison."""
+    import torch
+
+    from paper_2308_10169_gb300 import Planner, Server
+    from paper_2308_10169_gb300.inputs import AT_STALL, Scene, SepsoConfig, serving_workload
+    agents = serving_workload(0, n_agents)[:n]
+    lat, costs, its = [], [], []
+    for a, ag in enumerate(agents):
+        cfg = SepsoConfig(T=ag["T"], G=8, N=32, max_obstacles=256, alpha=30.0, beta=4, max_iters=100,
+                          at_mode=AT_STALL, stall_iters=10, stall_tol=0.0, use_pi=True, pi_gamma=0.25,
+                          pi_halfwidth=20.0, seed=0, run_id=a)
+        pl = Planner(cfg)
+        pl.set_hyper(ag["hyper"])
+        wp = np.zeros(2 * ag["T"], np.float32)
+        if a == 0:  # warm-up
+            pl.set_scene(Scene(start=ag["start"], target=ag["target"], circles=ag["circles"]), motion=False)
+            pl.plan_into(wp)
+            pl = Planner(cfg)
+            pl.set_hyper(ag["hyper"])
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        pl.set_scene(Scene(start=ag["start"], target=ag["target"], circles=ag["circles"]), motion=False)
+        r = pl.plan_into(wp)
+        lat.append(time.perf_counter() - t)
+        costs.append(float(r.cost))
+        its.append(int(r.iters))
+    lat = np.array(lat) * 1e3
+    sv = Server(n_agents=n_agents, max_slots=1024, G=8, N=32, Tmax=40, Omax=256, max_iters=100, stall_iters=10)
+    for a, ag in enumerate(agents):
+        sv.set_hyper(ag["hyper"], agent=a)
+    for a, ag in enumerate(agents):
+        sv.submit_at(a, ag["T"], ag["start"], ag["target"], ag["circles"], tag=a, arrival_s=0.0)
+    sv.clock(restart=True)
+    sv.run()
+    done = sv.poll(max_n=n + 1)
+    slat = np.array([d["finish_s"] - d["arrival_s"] for d in done]) * 1e3
+    span = max(d["finish_s"] for d in done)
+    return {"requests": n,
+            "single_scene": {"plans_per_s": n / (lat.sum() / 1e3),
+                             "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                            "p99": float(np.percentile(lat, 99))},
+                             "median_cost": float(np.median(costs)), "iters_per_plan": float(np.mean(its))},
+            "server_burst": {"plans_per_s": len(done) / span,
+                             "latency_ms": {"p50": float(np.percentile(slat, 50)),
+                                            "p99": float(np.percentile(slat, 99))},
+                             "median_cost": float(np.median([d["cost"] for d in done])),
+                             "iters_per_plan": float(np.mean([d["iters"] for d in done]))}}
 
 
 def run_prior(n_train: int, n_eval: int, rounds: int, epochs: int, single: dict):
@@ -625,7 +680,8 @@ def main():
                 "workload": "2048 agents, Poisson arrivals, T in {8,20,40}, O in {32,256} r~U[5,25], "
                             "obstacles advanced per request, G=8 x N=32, PI warm start on the device, "
                             "AT stall 10 / cap 100, continuous batching (1024 slots)",
-                "runs": [run_serve(float(r), args.serve_seconds) for r in args.serve_rates.split(",")]}
+                "runs": [run_serve(float(r), args.serve_seconds) for r in args.serve_rates.split(",")],
+                "vs_single_scene": serve_single_scene()}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
