@@ -837,13 +837,21 @@ int choose_tile_n_auto(int M, int N, int K) {
 
 // tile_n: 0 automatic (persistent kernel); 64 / 128 / 256 the persistent kernel
 // with that tile; -64 / -128 / -256 the one-tile-per-CTA kernel.
-int gemm_launch(const GemmArgs& g, cudaStream_t s, int tile_n = 0) {
+int gemm_check(const GemmArgs& g, int tile_n) {
   if (g.M < 1 || g.N < 1 || g.K < 8 || (g.K & 7) || (g.lda & 7) || (g.ldb & 7) || g.lda < g.K || g.ldb < g.K)
     return pfail(SEPSO_EINVAL, "gemm: bad sizes M %d N %d K %d lda %d ldb %d", g.M, g.N, g.K, g.lda, g.ldb);
   if (!g.A || !g.B || !aligned16(g.A) || !aligned16(g.B))
     return pfail(SEPSO_EINVAL, "gemm: A and B must be 16-byte aligned device arrays");
   if ((g.Cf && g.ldcf < g.N) || (g.Cb && g.ldcb < g.N) || (g.mask && g.ldm < g.N))
     return pfail(SEPSO_EINVAL, "gemm: output or mask row stride below N");
+  if (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256 && tile_n != -64 && tile_n != -128 &&
+      tile_n != -256)
+    return pfail(SEPSO_EINVAL, "gemm: tile N %d (64, 128 or 256; negative for one tile per CTA)", tile_n);
+  return SEPSO_OK;
+}
+
+int gemm_launch(const GemmArgs& g, cudaStream_t s, int tile_n = 0) {
+  PTRY(gemm_check(g, tile_n));
   if (tile_n == 0) tile_n = choose_tile_n_auto(g.M, g.N, g.K);
   CUtensorMap ta;
   PTRY(make_map(&ta, g.A, g.M, g.K, g.lda, sepso::kBM));
@@ -1392,6 +1400,7 @@ int sepso_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t 
   g.ldcf = ldcf;
   g.Cb = static_cast<bf16*>(Cb);
   g.ldcb = ldcb;
+  PTRY(gemm_check(g, tile_n));  // before any CUDA call
   void* st = nullptr;
   PCUDA(cudaGetSymbolAddress(&st, g_gemm_status));
   g.status = static_cast<int*>(st);

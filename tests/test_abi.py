@@ -65,3 +65,79 @@ def test_strerror_names_codes():
     lib = _native.lib()
     assert lib.sepso_strerror(0) == b"ok"
     assert lib.sepso_strerror(-5) == b"device-side wait timed out"
+
+
+# ---------------------------------------------------------------------------
+# Host-side argument checks of the batch, server and prior entry points (no GPU:
+# the checks run before any CUDA call).
+# ---------------------------------------------------------------------------
+
+def _batch_size(**kw):
+    base = dict(T=8, G=4, N=32, O=16, max_iters=10, alpha=30.0, beta=4, seed=1, run_id=0)
+    base.update(kw)
+    arr = (_native.BatchScene * 2)(_native.BatchScene(**base), _native.BatchScene(**base))
+    size = ctypes.c_size_t()
+    return _native.lib().sepso_batch_workspace_size(arr, 2, ctypes.byref(size)), size.value
+
+
+def test_batch_workspace_size_and_bad_scenes():
+    rc, size = _batch_size()
+    assert rc == 0 and size > 0 and size % 256 == 0
+    assert _batch_size(O=1000)[1] > size and _batch_size(N=64)[1] > size
+    for bad in (dict(T=0), dict(T=65), dict(G=33), dict(N=0), dict(O=-1), dict(max_iters=0), dict(beta=9),
+                dict(alpha=-1.0), dict(stall_iters=-1), dict(stall_tol=-0.5), dict(n_pi=33), dict(n_prior=-1),
+                dict(pi_halfwidth=-1.0)):
+        assert _batch_size(**bad)[0] == -1, bad
+    assert _native.lib().sepso_batch_last_error()
+    size = ctypes.c_size_t()
+    assert _native.lib().sepso_batch_workspace_size(None, 0, ctypes.byref(size)) == -1
+
+
+def _server_size(**kw):
+    base = dict(n_agents=16, max_slots=8, mem_budget=0, G=4, N=32, Tmax=20, Omax=64, max_iters=50, stall_iters=10,
+                stall_tol=0.0, alpha=30.0, beta=4, pi_gamma=0.25, pi_halfwidth=20.0, map_w=400.0, map_h=400.0,
+                seed=0, tile=0, threads=0)
+    base.update(kw)
+    c = _native.ServerConfig(**base)
+    size, slots = ctypes.c_size_t(), ctypes.c_int32()
+    rc = _native.lib().sepso_server_workspace_size(ctypes.byref(c), ctypes.byref(size), ctypes.byref(slots))
+    return rc, size.value, slots.value
+
+
+def test_server_slots_follow_the_memory_budget():
+    rc, size, slots = _server_size()
+    assert rc == 0 and slots == 8 and size > 0
+    rc2, size2, slots2 = _server_size(max_slots=64, mem_budget=size)
+    assert rc2 == 0 and 1 <= slots2 <= 8 and size2 <= size
+    for bad in (dict(n_agents=0), dict(max_slots=0), dict(G=0), dict(N=0), dict(Tmax=0), dict(Tmax=65),
+                dict(Omax=-1), dict(max_iters=0), dict(beta=0), dict(pi_gamma=1.5), dict(map_w=0.0)):
+        assert _server_size(**bad)[0] == -1, bad
+    assert _native.lib().sepso_server_last_error()
+
+
+def _prior_size(**kw):
+    base = dict(T=20, grid=64, hidden1=1024, hidden2=512, max_batch=256, capacity=1000, max_circles=64,
+                map_w=400.0, map_h=400.0, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8)
+    base.update(kw)
+    c = _native.PriorConfig(**base)
+    size = ctypes.c_size_t()
+    return _native.lib().sepso_prior_workspace_size(ctypes.byref(c), ctypes.byref(size)), size.value
+
+
+def test_prior_workspace_size_and_bad_configs():
+    rc, size = _prior_size()
+    # the dataset alone: 1000 rows x 4104 BF16 features
+    assert rc == 0 and size > 1000 * 4104 * 2 and size % 256 == 0
+    assert _prior_size(capacity=2000)[1] - size >= 1000 * 4104 * 2
+    for bad in (dict(T=0), dict(T=65), dict(grid=4), dict(hidden1=100), dict(hidden2=0), dict(max_batch=12),
+                dict(capacity=0), dict(max_circles=-1), dict(lr=0.0), dict(beta1=1.0), dict(eps=0.0)):
+        assert _prior_size(**bad)[0] == -1, bad
+    assert _native.lib().sepso_prior_last_error()
+
+
+def test_gemm_rejects_bad_shapes_before_any_launch():
+    L = _native.lib()
+    # K not a multiple of 8, or NULL operands: rejected on the host
+    assert L.sepso_gemm_bf16(None, None, 8, 8, 12, 16, 16, 1.0, None, 0, None, 0, None, 8, None, 8, 0, None) == -1
+    assert L.sepso_gemm_bf16(None, None, 8, 8, 16, 16, 16, 1.0, None, 0, None, 0, None, 8, None, 8, 0, None) == -1
+    assert L.sepso_prior_last_error()
