@@ -81,7 +81,10 @@ typedef struct {
   int32_t runs;           /* independent swarms on the same scene, >= 1          */
   int32_t ctas_per_group; /* 0 = automatic; else CTAs cooperating on one group   */
   int32_t threads;        /* 0 = automatic; else 64..512, a multiple of 32       */
-  int32_t circle_split;   /* 0 = automatic (1); else circle chunks per segment    */
+  int32_t circle_split;   /* 0 = automatic; else circle chunks per segment        */
+  int32_t fitness_mode;   /* 0 = automatic; 1 = a lane group per particle; 2 =
+                             (particle, segment, circle chunk) items spread over
+                             all threads of a CTA                                  */
 } sepso_config;
 
 /* Outcome of one planning cycle of one run. */

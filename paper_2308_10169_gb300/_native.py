@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
         ("use_pi", ctypes.c_int32), ("pi_gamma", ctypes.c_float), ("pi_halfwidth", ctypes.c_float),
         ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32),
         ("runs", ctypes.c_int32), ("ctas_per_group", ctypes.c_int32), ("threads", ctypes.c_int32),
-        ("circle_split", ctypes.c_int32),
+        ("circle_split", ctypes.c_int32), ("fitness_mode", ctypes.c_int32),
     ]
 
 
@@ -95,7 +95,7 @@ def make_config(cfg) -> Config:
                   stall_tol=cfg.stall_tol, use_pi=int(cfg.use_pi), pi_gamma=cfg.pi_gamma,
                   pi_halfwidth=cfg.pi_halfwidth, seed=cfg.seed, run_id=cfg.run_id, runs=cfg.runs,
                   ctas_per_group=cfg.ctas_per_group, threads=cfg.threads,
-                  circle_split=cfg.circle_split)
+                  circle_split=cfg.circle_split, fitness_mode=cfg.fitness_mode)
 
 
 # Every exported entry point with (restype, argtypes); the tests check the list

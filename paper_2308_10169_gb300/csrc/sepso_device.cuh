@@ -77,6 +77,7 @@ struct SwarmParams {
   int cpg, C, ppc;            // CTAs per group, CTAs per run, particles per CTA
   int split;                  // circle chunks per (particle, segment) item
   int lp;                     // lanes per particle (power of two, <= 32)
+  int items;                  // 1: fitness as (particle, segment, chunk) items over the CTA
   int O, Omax;                // obstacles now / capacity (shared-memory carve)
   float W, H, alpha;
   int beta, max_iters, at_mode, tw;
@@ -495,6 +496,36 @@ __device__ __forceinline__ void fitness_items(const float* sX, int nl, int T, in
     const int o0 = c * chunk;
     const int o1 = min(O, o0 + chunk);
     const int hits = (int)seg_hits(f, circ, o0, o1);
+    if (hits) atomicAdd(&sQ[i], hits);
+    if (c == 0) seg_len[i * nseg + s] = len;
+  }
+}
+
+// Q and per-segment lengths of nl particles (rows in shared memory) against circle
+// pairs, as (particle, segment, circle chunk) items spread over all threads of the
+// block, chunk-major so that the lanes of a warp read the same circle pair (a
+// broadcast).  Q accumulates with shared-memory integer atomics (exact); lengths
+// land in seg_len[i * (T+1) + s].  sQ must be zero on entry.
+__device__ __forceinline__ void fitness_items_pairs(const float* sX, int nl, int T, int D, float sx, float sy,
+                                                    float tx, float ty, const float4* cxy, const float2* nr2,
+                                                    int K, int split, int* sQ, float* seg_len) {
+  const int nseg = T + 1;
+  const int chunk = (K + split - 1) / split;
+  const int per_c = nl * nseg;
+  const int items = per_c * split;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int c = it / per_c;
+    const int r = it - c * per_c;
+    const int i = r / nseg;
+    const int s = r - i * nseg;
+    const float* x = sX + i * D;
+    const float ax = (s == 0) ? sx : x[s - 1];
+    const float ay = (s == 0) ? sy : x[T + s - 1];
+    const float bx = (s == T) ? tx : x[s];
+    const float by = (s == T) ? ty : x[T + s];
+    float len;
+    const PairFrame f = pair_frame(ax, ay, bx, by, &len);
+    const int hits = pair_hits(f, cxy, nr2, c * chunk, min(K, c * chunk + chunk));
     if (hits) atomicAdd(&sQ[i], hits);
     if (c == 0) seg_len[i * nseg + s] = len;
   }

@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
   float* sV = reinterpret_cast<float*>(smem + L.V);
   float* sP = reinterpret_cast<float*>(smem + L.P);
   float* sR = reinterpret_cast<float*>(smem + L.R);
+  int* sQi = reinterpret_cast<int*>(smem + L.Q);        // item mode: Q per particle
+  float* sLen = reinterpret_cast<float*>(smem + L.Len);  // item mode: length per (particle, segment)
   float* sG = reinterpret_cast<float*>(smem + L.Gown);
   float* sT = reinterpret_cast<float*>(smem + L.Tb);
   float* sPfit = reinterpret_cast<float*>(smem + L.Pfit);
@@ -229,6 +231,8 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
   }
   const float2* sNr2 = reinterpret_cast<const float2*>(sPairs + K);
 
+  for (int i = tid; i < nl; i += nt) sQi[i] = 0;
+  __syncthreads();
   const int nseg = T + 1;
   // Iterations already run by this run (across launches): they index the
   // barrier count and the rotation of the group words.
@@ -252,17 +256,31 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
     // and Q with a fixed shuffle tree.  A particle whose Pbest is below its
     // group's current best writes its row and Q to its slot and folds its key
     // into the group word.
+    if (p.items) {
+      // (particle, segment, chunk) items over the whole CTA, then one warp per
+      // particle sums its segment lengths in segment order and takes Q.
+      fitness_items_pairs(sX, nl, T, D, sx, sy, tx, ty, sPairs, sNr2, K, p.split, sQi, sLen);
+      __syncthreads();
+    }
     {
-      const int lp = p.lp;
+      const int lp = p.items ? 32 : p.lp;
       const int ppw = 32 / lp;
       const int lsub = lane & (lp - 1);
       for (int i0 = warp * ppw; i0 < nl; i0 += nwarps * ppw) {
         const int i = i0 + lane / lp;
         const bool live = i < nl;
-        float len;
-        int qq;
-        group_fitness_pairs(sX + (live ? i : 0) * D, live, lp, T, p.split, K, sx, sy, tx, ty, sPairs, sNr2, &len,
-                            &qq);
+        float len = 0.0f;
+        int qq = 0;
+        if (p.items) {
+          if (live && lsub == 0) {
+            for (int sg = 0; sg < nseg; ++sg) len += sLen[i * nseg + sg];
+            qq = sQi[i];
+            sQi[i] = 0;  // ready for the next iteration (read again only after two barriers)
+          }
+        } else {
+          group_fitness_pairs(sX + (live ? i : 0) * D, live, lp, T, p.split, K, sx, sy, tx, ty, sPairs, sNr2,
+                              &len, &qq);
+        }
         int imp = 0, pub = 0;
         float pf = INFINITY;
         int pq = 0;

@@ -56,6 +56,7 @@ class SepsoConfig:
     ctas_per_group: int = 0    # 0 = automatic
     threads: int = 0           # 0 = automatic
     circle_split: int = 0      # 0 = automatic
+    fitness_mode: int = 0      # 0 = automatic; 1 lane group per particle; 2 items over the CTA
 
     @property
     def D(self) -> int:
