@@ -313,9 +313,12 @@ def evaluate_prior(prior: Prior, scenes: dict, first: int, budgets=(10, 25, 50, 
     out["converged_cost"] = target
     dyn = {"pi_only": [], "prior_pi": []}
     prev = {"pi_only": None, "prior_pi": None}
+    prev_before_last = {"pi_only": None, "prior_pi": None}
     for c in range(cycles):
         sc = previous_cycle(scenes, cycles - 1 - c) if c < cycles - 1 else scenes
         pc = propose(prior, sc, first)
+        if c == cycles - 1:
+            prev_before_last = dict(prev)
         for m in ("pi_only", "prior_pi"):
             use_prior = m == "prior_pi"
             r = plan_scenes(sc, seed=seed, run0=run0, cycle=c, prev=prev[m], n_pi=n_pi,
@@ -324,5 +327,51 @@ def evaluate_prior(prior: Prior, scenes: dict, first: int, budgets=(10, 25, 50, 
             dyn[m].append(_summary(r, n))
             prev[m] = r["waypoints"]
     out["dynamic"] = dyn
+    # the last cycle again with fixed iteration budgets (no AT), each method warm-
+    # started by PI from its own plans of the cycle before
+    last_prev = {m: prev_before_last[m] for m in prev_before_last}
+    sc_last = scenes
+    dyn_budgets = {"pi_only": [], "prior_pi": []}
+    pc = propose(prior, sc_last, first)
+    for k in budgets:
+        for m in ("pi_only", "prior_pi"):
+            use_prior = m == "prior_pi"
+            r = plan_scenes(sc_last, seed=seed, run0=run0, cycle=cycles - 1, prev=last_prev[m], n_pi=n_pi,
+                            prior=pc if use_prior else None, n_prior=n_prior if use_prior else 0, shape=shape,
+                            max_iters=k, stall_iters=0, **kw)
+            dyn_budgets[m].append(dict(_summary(r, n), iters=k))
+    out["dynamic_budgets"] = dyn_budgets
     out["shape"] = shape
     return out
+
+
+def single_scene_dynamic(scenes: dict, n: int = 64, cycles: int = 5, T: int = 20, G: int = 8, N: int = 170,
+                         hyper=None, seed: int = 2, run0: int = 10 ** 6, device=None) -> dict:
+    """The plain single-scene kernel on the first n held-out scenes, each through the
+    same `cycles`-cycle dynamic sequence as evaluate_prior (PI from its own previous
+    plan, AT stall 10 / cap 300): median path cost of the last cycle and plans/s
+    (device time of the planning calls)."""
+    from .inputs import TABLE_HYPER8_PATH, AT_STALL, Scene, SepsoConfig, previous_cycle
+    from .planner import Planner
+    hy = np.asarray(TABLE_HYPER8_PATH if hyper is None else hyper, np.float32)[:G]
+    seqs = [previous_cycle(scenes, cycles - 1 - c) if c < cycles - 1 else scenes for c in range(cycles)]
+    costs, ms = [], 0.0
+    for i in range(n):
+        cfg = SepsoConfig(T=T, G=G, N=N, max_obstacles=scenes["circles"].shape[1], alpha=30.0, beta=4,
+                          max_iters=300, at_mode=AT_STALL, stall_iters=10, stall_tol=0.0, use_pi=True,
+                          pi_gamma=(43 - 0.5) / N, pi_halfwidth=20.0, seed=seed, run_id=run0 + i)
+        pl = Planner(cfg, device=device)
+        pl.set_hyper(hy)
+        for c in range(cycles):
+            sc = seqs[c]
+            pt = sc["points"][i]
+            pl.set_scene(Scene(start=pt[:2], target=pt[2:], circles=sc["circles"][i]), motion=False)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(pl.stream)
+            pl.plan_async()
+            e1.record(pl.stream)
+            res = pl.read_result()
+            if c == cycles - 1:
+                ms += e0.elapsed_time(e1)
+                costs.append(float(res["cost"]))
+    return dict(n=n, cost_median=float(np.median(costs)), plans_per_s=n / (ms / 1e3), ms_per_plan=ms / n)
