@@ -48,9 +48,9 @@ L2_FLUSH_BYTES = 256 << 20
 # workload (ncu --set full capture summarised in profiles/swarm_kernel_dynamic_workload.md);
 # set to None whenever the kernel changes until it is captured again.
 SWARM_TRAFFIC_BYTES = 154880
-# The same for gemm_tc_kernel on the MLP's grad-W1 product (1024 x 4104 x 1024),
+# The same for gemm_tc_kernel on the MLP's grad-W1 product (1024 x 4104 x 4096),
 # profiles/gemm_tc_kernel_mlp_gradW1.md.
-GEMM_GRADW1_TRAFFIC_BYTES = 10520832
+GEMM_GRADW1_TRAFFIC_BYTES = 42225920
 
 
 def parse():
@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--prior-eval", type=int, default=2048, help="held-out scenes (10000 = full size)")
     ap.add_argument("--prior-rounds", type=int, default=3)
     ap.add_argument("--prior-epochs", type=int, default=30)
+    ap.add_argument("--prior-batch", type=int, default=4096, help="rows per Adam step")
     ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve",
                     help="comma list of main, cpu, batch, prior, serve, gemm (gemm: the tensor-core GEMM alone)")
     return ap.parse_args()
@@ -527,14 +528,14 @@ def serve_single_scene(n: int = 256, n_agents: int = 2048):
                              "iters_per_plan": float(np.mean([d["iters"] for d in done]))}}
 
 
-def run_prior(n_train: int, n_eval: int, rounds: int, epochs: int, single: dict):
+def run_prior(n_train: int, n_eval: int, rounds: int, epochs: int, single: dict, B: int = 4096):
     """Learned prior: self-training on the planner's own solutions, held-out
     comparison with the PI-only start, tensor-core GEMM and training throughput."""
     import torch
 
     from paper_2308_10169_gb300.inputs import prior_init_params, prior_scenes
     from paper_2308_10169_gb300.prior import Prior, evaluate_prior, fit_prior, gemm_bf16
-    H1, H2, T, B = 1024, 512, 20, 1024
+    H1, H2, T = 1024, 512, 20
     tr, ev = prior_scenes(0, n_train), prior_scenes(1, n_eval)
     pr = Prior(T=T, hidden1=H1, hidden2=H2, capacity=n_train + n_eval, max_batch=B)
     pr.set_params(prior_init_params(0, pr.K, H1, H2, 2 * T))
@@ -585,7 +586,7 @@ def _bf16_peak() -> float:
     return float(json.loads(path.read_text()).get("bf16_tflops", 1900.0)) if path.exists() else 1900.0
 
 
-def run_gemm(B: int = 1024, H1: int = 1024, K: int = 4104, reps: int = 20):
+def run_gemm(B: int = 4096, H1: int = 1024, K: int = 4104, reps: int = 20):
     """The tensor-core GEMM alone on the two largest products of a training step
     (grad W1 first, then forward layer 1), each launch timed with CUDA events after
     an L2 flush."""
@@ -676,7 +677,7 @@ def main():
             line["batch"] = run_batch(args.batch_scenes, args.batch_iters)
         if world == 1 and "prior" in sections and args.prior_train > 0:
             line["prior"] = run_prior(args.prior_train, args.prior_eval, args.prior_rounds, args.prior_epochs,
-                                      line)
+                                      line, args.prior_batch)
         if world == 1 and "gemm" in sections:
             line["gemm"] = run_gemm()
         if world == 1 and "serve" in sections and args.serve_rates:

@@ -33,7 +33,7 @@ class Prior:
     tensor-core kernels, FP32 masters and Adam; dataset rows held on the device."""
 
     def __init__(self, T: int = 20, grid: int = 64, hidden1: int = 1024, hidden2: int = 512,
-                 max_batch: int = 1024, capacity: int = 4096, max_circles: int = 1024,
+                 max_batch: int = 4096, capacity: int = 4096, max_circles: int = 1024,
                  map_w: float = 400.0, map_h: float = 400.0, lr: float = 1e-3, beta1: float = 0.9,
                  beta2: float = 0.999, eps: float = 1e-8, device=None):
         self.device = _dev(device)
@@ -220,7 +220,7 @@ def plan_scenes(scenes: dict, T: int = 20, G: int = 8, N: int = 170, hyper=None,
                 prior_used=used if prior is not None else None)
 
 
-def fit_prior(prior: Prior, scenes: dict, rounds: int = 3, epochs: int = 30, batch: int = 1024, seed: int = 0,
+def fit_prior(prior: Prior, scenes: dict, rounds: int = 3, epochs: int = 30, batch: int = 4096, seed: int = 0,
               n_prior: int = 43, shape=None, **plan_kw) -> dict:
     """Train the prior on SEPSO solutions the planner itself generates, in rounds:
     the first labels are plain SEPSO plans of the scenes; after each training phase
