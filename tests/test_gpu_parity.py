@@ -130,11 +130,14 @@ def _decisive_state(cfg, scene, hyper, seed):
     raise AssertionError("no decisive state found")
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("G,N,T,O,cpg", [(3, 10, 4, 12, 0), (2, 13, 6, 20, 4), (8, 32, 8, 16, 0),
-                                         (1, 1, 1, 3, 0), (4, 50, 20, 64, 7)])
-def test_single_step_matches_oracle(native, G, N, T, O, cpg):
+                                         (1, 1, 1, 3, 0), (4, 50, 20, 64, 7), (2, 40, 33, 65, 1)])
+def test_single_step_matches_oracle(native, G, N, T, O, cpg, mode):
+    # both fitness forms: a lane group per particle (1) and items over the CTA (2);
+    # the last shape has T + 1 > 32 segments and an odd circle count
     cfg = SepsoConfig(T=T, G=G, N=N, max_obstacles=O, alpha=30.0, beta=4, max_iters=100,
-                      ctas_per_group=cpg, seed=11)
+                      ctas_per_group=cpg, seed=11, fitness_mode=mode)
     rng = np.random.default_rng(G * 100 + N)
     scene = Scene(start=(20, 20), target=(380, 380), circles=random_circles(rng, O))
     hyper = np.column_stack([rng.uniform(1, 2.5, G), rng.uniform(1, 2.5, G), rng.uniform(0, 2, G),
