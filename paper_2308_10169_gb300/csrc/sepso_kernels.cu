@@ -246,6 +246,13 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
     if (p.mode == kModeStep && done >= p.step_iters) break;
     ++k;
     ++done;
+    // This iteration's R1..R3 (independent of the exchange), drawn by the last threads.
+    for (int i = nt - 1 - tid; i < nl; i += nt) {
+      const uint4 o = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)(g * N + n0 + i), kStreamVel, cycle, run);
+      sR[i * 4 + 0] = c1 * u01(o.x);
+      sR[i * 4 + 1] = c2 * u01(o.y);
+      sR[i * 4 + 2] = c3 * u01(o.z);
+    }
     const unsigned long long gk = kbase + (unsigned long long)done;  // the run's iteration count
     const size_t rbase = ((size_t)r * 2 + (size_t)(gk & 1ull)) * p.M;    // candidate rows
     const size_t wbase = ((size_t)r * 3 + (size_t)(gk % 3ull)) * G;      // group words of gk
@@ -314,13 +321,6 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
           }
         }
       }
-    }
-    // This iteration's R1..R3 (independent of the exchange).
-    for (int i = tid; i < nl; i += nt) {
-      const uint4 o = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)(g * N + n0 + i), kStreamVel, cycle, run);
-      sR[i * 4 + 0] = c1 * u01(o.x);
-      sR[i * 4 + 1] = c2 * u01(o.y);
-      sR[i * 4 + 2] = c3 * u01(o.z);
     }
     __syncthreads();
     // Arrive: the release orders this CTA's rows and keys before the arrival.
