@@ -540,6 +540,34 @@ int sepso_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t 
                     int32_t ldcf, void* Cb, int32_t ldcb, int32_t tile_n, void* stream);
 int sepso_gemm_bf16_sync(void* stream);
 
+/* Outputs of sepso_gemm_bf16_ex beyond those of sepso_gemm_bf16 (the backward
+ * pass of the learned prior uses all three). */
+typedef struct {
+  void* Ct;               /* BF16 copy of the output transposed, Ct[n * ldct + m] (device), or NULL */
+  int32_t ldct;           /* >= M */
+  float* colsum;          /* colsum[n] = sum over m of the output (device FP32, N floats), or NULL;
+                             summed per 32-row slab in row order, then over the slabs in order */
+  int32_t ksplit;         /* 0 or 1: one pass over K.  S > 1: K in S slices of whole 64-deep blocks
+                             (fewer when K has fewer blocks), one CTA per tile and slice, the slices'
+                             FP32 products summed in slice order before the epilogue; Cf/Cb only */
+  void* workspace;        /* device scratch, 16-byte aligned, caller-owned: */
+  size_t workspace_bytes; /* >= sepso_gemm_bf16_ex_workspace(M, N, ksplit, colsum != NULL) */
+} sepso_gemm_extra;
+
+/* Scratch bytes sepso_gemm_bf16_ex needs: S M N 4 for a K split in S slices,
+ * else ceil(M / 32) N 4 with column sums, else 0.  Errors: EINVAL. */
+int sepso_gemm_bf16_ex_workspace(int32_t M, int32_t N, int32_t ksplit, int32_t colsum, size_t* bytes);
+
+/* sepso_gemm_bf16 with the outputs of `extra` (NULL: none).  The epilogue's
+ * values (after bias, ReLU and mask) are what Ct and colsum receive.  A K split
+ * uses the one-tile-per-CTA kernel with width |tile_n| (0: 128) and a second
+ * launch for the sum and the epilogue.  Errors: EINVAL (also a K split with Ct
+ * or colsum), ENOSPC (workspace), ECUDA. */
+int sepso_gemm_bf16_ex(const void* A, const void* B, int32_t M, int32_t N, int32_t K, int32_t lda, int32_t ldb,
+                       float alpha, const float* bias, int32_t relu, const void* mask, int32_t ldm, float* Cf,
+                       int32_t ldcf, void* Cb, int32_t ldcb, const sepso_gemm_extra* extra, int32_t tile_n,
+                       void* stream);
+
 /* ---- misc --------------------------------------------------------------- */
 
 /* Wait for the handle's stream; returns the first device-side error of any run

@@ -88,6 +88,11 @@ class PriorConfig(ctypes.Structure):
                 ("eps", ctypes.c_float)]
 
 
+class GemmExtra(ctypes.Structure):
+    _fields_ = [("Ct", ctypes.c_void_p), ("ldct", ctypes.c_int32), ("colsum", ctypes.c_void_p),
+                ("ksplit", ctypes.c_int32), ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
 def make_config(cfg) -> Config:
     return Config(T=cfg.T, G=cfg.G, N=cfg.N, max_obstacles=cfg.max_obstacles, map_w=cfg.map_w,
                   map_h=cfg.map_h, alpha=cfg.alpha, beta=cfg.beta, max_iters=cfg.max_iters,
@@ -181,6 +186,10 @@ SIGNATURES = {
     "sepso_gemm_bf16": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _i32, _i32, ctypes.c_float, _vp, _i32,
                                        _vp, _i32, _vp, _i32, _vp, _i32, _i32, _vp]),
     "sepso_gemm_bf16_sync": (ctypes.c_int, [_vp]),
+    "sepso_gemm_bf16_ex_workspace": (ctypes.c_int, [_i32, _i32, _i32, _i32, ctypes.POINTER(_sz)]),
+    "sepso_gemm_bf16_ex": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _i32, _i32, ctypes.c_float, _vp, _i32,
+                                          _vp, _i32, _vp, _i32, _vp, _i32, ctypes.POINTER(GemmExtra), _i32,
+                                          _vp]),
     "sepso_watchdog_selftest": (ctypes.c_int, [_i32, ctypes.POINTER(_i32), _vp]),
     "sepso_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sepso_last_error": (ctypes.c_char_p, []),

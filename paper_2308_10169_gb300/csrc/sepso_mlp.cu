@@ -9,10 +9,13 @@
 //                      stage with tcgen05.commit, and the four warps read the
 //                      accumulator back with tcgen05.ld for a fused epilogue
 //                      (scale, bias, ReLU, the backward pass's ReLU mask, FP32
-//                      and/or BF16 output).  Tile N (64 / 128 / 256) per launch.
+//                      and/or BF16 output, a transposed BF16 copy, column
+//                      sums; K split into slices summed in order).  Tile N
+//                      (64 / 128 / 256) per launch.
 //   raster_kernel      occupancy raster of the circles (cell centre inside a disk).
-//   small kernels      transpose, column sums (bias gradients), MSE loss gradient,
-//                      Adam, FP32 -> BF16 weight copies.
+//   small kernels      row gather with a transposed copy, column sums (bias
+//                      gradients), MSE loss gradient, split-K sums, Adam with the
+//                      BF16 weight copies the products read.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -109,15 +112,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // GEMM: C[M x N] = alpha * A[M x K] . B[N x K]^T (+ bias[n]) (then ReLU, or the
 // ReLU mask mask[m][n] > 0), A and B row-major BF16 with K contiguous.
 //
-// One CTA computes a 128 x BN tile with four warps.  Warp 0 (one lane) streams
+// One CTA computes a 128 x BN tile with eight warps.  Warp 0 (one lane) streams
 // 128 x 64 and BN x 64 operand boxes into a ring of shared-memory stages with TMA
 // (128-byte swizzle, zero fill past the matrix edges); warp 1 (one lane) issues
 // four tcgen05.mma (M = 128, N = BN, K = 16) per stage into a BN-column FP32
 // accumulator in tensor memory and frees the stage with tcgen05.commit; after the
-// last stage all four warps read the accumulator (warp w: rows 32w .. 32w + 31)
-// with tcgen05.ld, stage it through shared memory and store it row-contiguously
-// with the epilogue applied.  Every wait is bounded; tensor memory is released on
-// every path.
+// last stage all eight warps read the accumulator (warp w: rows 32 (w % 4) ..
+// + 31, column half w / 4) with tcgen05.ld, stage it through shared memory and
+// store it row-contiguously with the epilogue applied, then, when asked, a
+// transposed BF16 copy and per-slab column sums.  A split product gives each CTA
+// one K-slice (blockIdx.z) and stores its raw FP32 products.  Every wait is
+// bounded; tensor memory is released on every path.
 // ---------------------------------------------------------------------------
 struct GemmArgs {
   const __nv_bfloat16* A;
@@ -132,10 +137,15 @@ struct GemmArgs {
   int ldcf;
   __nv_bfloat16* Cb;           // BF16 output, or null
   int ldcb;
+  __nv_bfloat16* CbT;          // BF16 output transposed, CbT[n * ldct + m], or null
+  int ldct;
+  float* colpart;              // column sums of the output per 32-row slab: [ceil(M / 32)][N], or null
+  float* part;                 // split K: raw FP32 products of K-slice z at part + z * M * N (row stride N)
+  int kcb;                     // split K: K-blocks (of 64) per slice; 0 = the whole K in one slice
   int* status;
 };
 
-constexpr int kBM = 128, kBK = 64, kGemmThreads = 128;
+constexpr int kBM = 128, kBK = 64, kGemmThreads = 256;
 constexpr int kRing = 192 * 1024;                         // operand stages
 constexpr int kGemmSmem = kRing + 1024;                   // + alignment slack
 template <int BN>
@@ -147,6 +157,175 @@ struct GemmTile {
   static_assert(kStages >= 2, "ring too small");
   static_assert(kBM * (BN + 4) * 4 <= kRing, "epilogue staging does not fit");
 };
+
+// BF16 element j (0..7) of eight packed in a uint4, as FP32 (exact).
+__device__ __forceinline__ float bf16_of(const uint4& u, int j) {
+  const uint32_t w = (j >> 1) == 0 ? u.x : (j >> 1) == 1 ? u.y : (j >> 1) == 2 ? u.z : u.w;
+  return __uint_as_float((j & 1) ? (w & 0xffff0000u) : (w << 16));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // a in the low half
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Epilogue of a staged 128 x BN FP32 tile into the row-major outputs.  Work items
+// are 8 columns of one row (consecutive threads: consecutive columns); the mask
+// loads of a batch of items are all issued before the first of them is used, so
+// that their latencies overlap.  A split-K slice stores its raw products to its
+// slice of `part`.  With a transposed output or column sums the final values also
+// go back into the tile.
+template <int BN>
+__device__ __forceinline__ void tile_epilogue_rows(const GemmArgs& g, float* tile, int m0, int n0, int tid) {
+  constexpr int kLd = BN + 4, kUnits = BN / 8, kItems = kBM * kUnits, kBatch = 8;
+  const bool raw = g.part != nullptr;
+  float* Cf = raw ? g.part + (size_t)blockIdx.z * g.M * g.N : g.Cf;
+  const int ldcf = raw ? g.N : g.ldcf;
+  const __nv_bfloat16* mask = raw ? nullptr : g.mask;
+  __nv_bfloat16* Cb = raw ? nullptr : g.Cb;
+  const bool keep = !raw && (g.CbT || g.colpart);
+  const int ncol = min(BN, g.N - n0), nrow = min(kBM, g.M - m0);
+  const bool mvec = mask && (g.ldm & 7) == 0 && (reinterpret_cast<uintptr_t>(mask) & 15) == 0;
+  const bool fvec = Cf && (ldcf & 3) == 0 && (reinterpret_cast<uintptr_t>(Cf) & 15) == 0;
+  const bool bvec = Cb && (g.ldcb & 7) == 0 && (reinterpret_cast<uintptr_t>(Cb) & 15) == 0;
+  const bool svec = g.bias && (reinterpret_cast<uintptr_t>(g.bias) & 15) == 0;
+  for (int i0 = tid; i0 < kItems; i0 += kGemmThreads * kBatch) {
+    uint4 mk[kBatch];
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      mk[b] = make_uint4(0u, 0u, 0u, 0u);
+      const int it = i0 + b * kGemmThreads;
+      const int rl = it / kUnits, c = (it % kUnits) * 8;
+      if (mask && it < kItems && rl < nrow && c < ncol) {
+        const __nv_bfloat16* mp = mask + (size_t)(m0 + rl) * g.ldm + (n0 + c);
+        if (mvec && c + 8 <= ncol) {
+          mk[b] = __ldg(reinterpret_cast<const uint4*>(mp));
+        } else {
+          uint32_t w0 = 0u, w1 = 0u, w2 = 0u, w3 = 0u;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (c + j < ncol) {
+              const uint32_t h = (uint32_t)__bfloat16_as_ushort(mp[j]) << (16 * (j & 1));
+              if ((j >> 1) == 0) w0 |= h;
+              else if ((j >> 1) == 1) w1 |= h;
+              else if ((j >> 1) == 2) w2 |= h;
+              else w3 |= h;
+            }
+          }
+          mk[b] = make_uint4(w0, w1, w2, w3);
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      const int it = i0 + b * kGemmThreads;
+      const int rl = it / kUnits, c = (it % kUnits) * 8;
+      if (it >= kItems || rl >= nrow || c >= ncol) continue;
+      float* tp = tile + rl * kLd + c;
+      const float4 t0 = *reinterpret_cast<const float4*>(tp), t1 = *reinterpret_cast<const float4*>(tp + 4);
+      float x[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+      const int nv = min(8, ncol - c);
+      const int row = m0 + rl, col = n0 + c;
+      if (!raw) {
+        float bb[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (g.bias) {
+          if (svec && nv == 8) {
+            const float4 p = __ldg(reinterpret_cast<const float4*>(g.bias + col));
+            const float4 q = __ldg(reinterpret_cast<const float4*>(g.bias + col + 4));
+            bb[0] = p.x, bb[1] = p.y, bb[2] = p.z, bb[3] = p.w, bb[4] = q.x, bb[5] = q.y, bb[6] = q.z, bb[7] = q.w;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (j < nv) bb[j] = g.bias[col + j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j < nv) {
+            float y = x[j] * g.alpha;
+            if (g.bias) y += bb[j];
+            if (g.relu) y = fmaxf(y, 0.0f);
+            if (mask && !(bf16_of(mk[b], j) > 0.0f)) y = 0.0f;
+            x[j] = y;
+          }
+        }
+        if (keep) {
+          *reinterpret_cast<float4*>(tp) = make_float4(x[0], x[1], x[2], x[3]);
+          *reinterpret_cast<float4*>(tp + 4) = make_float4(x[4], x[5], x[6], x[7]);
+        }
+      }
+      if (Cf) {
+        float* o = Cf + (size_t)row * ldcf + col;
+        if (fvec && nv == 8) {
+          *reinterpret_cast<float4*>(o) = make_float4(x[0], x[1], x[2], x[3]);
+          *reinterpret_cast<float4*>(o + 4) = make_float4(x[4], x[5], x[6], x[7]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (j < nv) o[j] = x[j];
+        }
+      }
+      if (Cb) {
+        __nv_bfloat16* o = Cb + (size_t)row * g.ldcb + col;
+        if (bvec && nv == 8) {
+          *reinterpret_cast<uint4*>(o) = make_uint4(pack_bf16x2(x[0], x[1]), pack_bf16x2(x[2], x[3]),
+                                                    pack_bf16x2(x[4], x[5]), pack_bf16x2(x[6], x[7]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (j < nv) o[j] = __float2bfloat16_rn(x[j]);
+        }
+      }
+    }
+  }
+}
+
+// Transposed BF16 output of the final tile values: lane = a pair of rows of a
+// 64-row group, so that each store instruction writes 64 consecutive elements (128
+// bytes) of one output row as BF16 pairs.
+template <int BN>
+__device__ __forceinline__ void tile_store_transposed(const GemmArgs& g, const float* tile, int m0, int n0, int warp,
+                                                      int lane) {
+  constexpr int kLd = BN + 4, kQuads = BN / 4;
+  const int ncol = min(BN, g.N - n0), nrow = min(kBM, g.M - m0);
+  const bool pair = (g.ldct & 1) == 0 && (reinterpret_cast<uintptr_t>(g.CbT) & 3) == 0;
+  for (int it = warp; it < (kBM / 64) * kQuads; it += kGemmThreads / 32) {
+    const int r0 = (it / kQuads) * 64 + 2 * lane, c = (it % kQuads) * 4;
+    if (c >= ncol) continue;
+    const float4 a = *reinterpret_cast<const float4*>(tile + r0 * kLd + c);
+    const float4 b = *reinterpret_cast<const float4*>(tile + (r0 + 1) * kLd + c);
+    if (r0 >= nrow) continue;
+    const float xa[4] = {a.x, a.y, a.z, a.w}, xb[4] = {b.x, b.y, b.z, b.w};
+    const bool two = r0 + 1 < nrow;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (c + j >= ncol) continue;
+      __nv_bfloat16* o = g.CbT + (size_t)(n0 + c + j) * g.ldct + (m0 + r0);
+      if (pair && two) {
+        *reinterpret_cast<uint32_t*>(o) = pack_bf16x2(xa[j], xb[j]);
+      } else {
+        o[0] = __float2bfloat16_rn(xa[j]);
+        if (two) o[1] = __float2bfloat16_rn(xb[j]);
+      }
+    }
+  }
+}
+
+// Column sums of the final tile values over each 32-row slab (rows in order).
+template <int BN>
+__device__ __forceinline__ void tile_column_sums(const GemmArgs& g, const float* tile, int m0, int n0, int tid) {
+  constexpr int kLd = BN + 4;
+  const int ncol = min(BN, g.N - n0), nrow = min(kBM, g.M - m0);
+  for (int it = tid; it < (kBM / 32) * BN; it += kGemmThreads) {
+    const int slab = it / BN, c = it % BN;
+    const int r0 = slab * 32;
+    if (c >= ncol || r0 >= nrow) continue;
+    const int r1 = min(r0 + 32, nrow);
+    float s = 0.0f;
+    for (int r = r0; r < r1; ++r) s += tile[r * kLd + c];
+    g.colpart[(size_t)(m0 / 32 + slab) * g.N + (n0 + c)] = s;
+  }
+}
 
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
@@ -160,7 +339,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   uint8_t* gsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-  const int nkb = (g.K + kBK - 1) / kBK;
+  // this CTA's K-blocks: all of them, or K-slice blockIdx.z of a split product
+  const int nkb_all = (g.K + kBK - 1) / kBK;
+  const int kb0 = g.kcb > 0 ? (int)blockIdx.z * g.kcb : 0;
+  const int nkb = g.kcb > 0 ? max(0, min(g.kcb, nkb_all - kb0)) : nkb_all;
   constexpr uint32_t kIdesc = mma_idesc_bf16(kBM, BN);
 
   if (warp == 0) tmem_alloc(&tmem_base, BN);
@@ -188,8 +370,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       }
       uint8_t* sa = gsm + s * TL::kStage;
       mbar_expect_tx(&full[s], (uint32_t)TL::kStage);
-      tma_load_2d(sa, &tmA, kb * kBK, m0, &full[s]);
-      tma_load_2d(sa + TL::kABytes, &tmB, kb * kBK, n0, &full[s]);
+      tma_load_2d(sa, &tmA, (kb0 + kb) * kBK, m0, &full[s]);
+      tma_load_2d(sa + TL::kABytes, &tmB, (kb0 + kb) * kBK, n0, &full[s]);
       issued = kb + 1;
     }
     // on a failure, let the boxes already in flight land before the CTA exits
@@ -212,7 +394,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       for (int kk = 0; kk < kBK / 16; ++kk)
         mma_bf16(tmem, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), kIdesc,
                  (kb > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
+      // Free the stage only for a load that will reuse it: every commit is then
+      // waited for by the producer or by `done`, and none can arrive on this CTA's
+      // shared memory after it exits.
+      if (kb + S < nkb) mma_commit(&empty[s]);
     }
     mma_commit(&done);  // tracks every MMA issued above
   }
@@ -229,52 +414,23 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     // and when a warp reads one row.
     float* tile = reinterpret_cast<float*>(gsm);
     constexpr int kLd = BN + 4;
-    const int r = warp * 32 + lane;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows), column half w / 4
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;
     float v[32];
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 32) {
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
       float4* dst = reinterpret_cast<float4*>(tile + r * kLd + c0);
 #pragma unroll
       for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
     }
     __syncthreads();
-    const int ncol = min(BN, g.N - n0);
-    const bool vec = (!g.Cf || ((g.ldcf & 3) == 0 && (reinterpret_cast<uintptr_t>(g.Cf) & 15) == 0)) &&
-                     (!g.Cb || ((g.ldcb & 3) == 0 && (reinterpret_cast<uintptr_t>(g.Cb) & 7) == 0));
-    for (int rr = warp; rr < kBM; rr += kGemmThreads / 32) {
-      const int row = m0 + rr;
-      if (row >= g.M) break;
-      for (int c = 4 * lane; c < ncol; c += 128) {
-        const int col = n0 + c;
-        const float4 t = *reinterpret_cast<const float4*>(tile + rr * kLd + c);
-        float x[4] = {t.x, t.y, t.z, t.w};
-        const int nv = min(4, ncol - c);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          if (i < nv) {
-            x[i] *= g.alpha;
-            if (g.bias) x[i] += g.bias[col + i];
-            if (g.relu) x[i] = fmaxf(x[i], 0.0f);
-            if (g.mask && !(__bfloat162float(g.mask[(size_t)row * g.ldm + col + i]) > 0.0f)) x[i] = 0.0f;
-          }
-        }
-        if (vec && nv == 4) {
-          if (g.Cf) *reinterpret_cast<float4*>(g.Cf + (size_t)row * g.ldcf + col) = make_float4(x[0], x[1], x[2], x[3]);
-          if (g.Cb) {
-            __nv_bfloat162 lo = __floats2bfloat162_rn(x[0], x[1]), hi = __floats2bfloat162_rn(x[2], x[3]);
-            uint2 u;
-            u.x = *reinterpret_cast<uint32_t*>(&lo);
-            u.y = *reinterpret_cast<uint32_t*>(&hi);
-            *reinterpret_cast<uint2*>(g.Cb + (size_t)row * g.ldcb + col) = u;
-          }
-        } else {
-          for (int i = 0; i < nv; ++i) {
-            if (g.Cf) g.Cf[(size_t)row * g.ldcf + col + i] = x[i];
-            if (g.Cb) g.Cb[(size_t)row * g.ldcb + col + i] = __float2bfloat16_rn(x[i]);
-          }
-        }
-      }
+    tile_epilogue_rows<BN>(g, tile, m0, n0, tid);
+    if (!g.part && (g.CbT || g.colpart)) {
+      __syncthreads();  // the final values are back in the tile
+      if (g.CbT) tile_store_transposed<BN>(g, tile, m0, n0, warp, lane);
+      if (g.colpart) tile_column_sums<BN>(g, tile, m0, n0, tid);
     }
   }
   tc_fence_before();
@@ -379,6 +535,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
       long long it = 0;
       int lt = 0;
       bool stop = false;
+      // k-blocks this CTA streams in all: a stage is freed only for a later load
+      const long long total_it =
+          (long long)((tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x) * nkb;
       for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x, ++lt) {
         const int a = lt & 1;
         const int v = lt >> 1;
@@ -402,7 +561,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
           for (int kk = 0; kk < kBK / 16; ++kk)
             mma_bf16(acc, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), kIdesc,
                      (kb > 0 || kk > 0) ? 1u : 0u);
-          mma_commit(&empty[s]);
+          if (it + S < total_it) mma_commit(&empty[s]);
         }
         if (!stop) mma_commit(&acc_full[a]);
       }
@@ -435,17 +594,44 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
         for (int c = 0; c < 32; ++c) st[lane * 33 + c] = v[c];
         __syncwarp();
+        // lane = column: rows rbase .. rbase + 31, the 32 mask loads issued first
         const int col = n0 + c0 + lane;
-        if (col < g.N) {
+        if (col < g.N && rbase < g.M) {
+          float mk[32];
+          if (g.mask) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+              const int row = rbase + r;
+              mk[r] = row < g.M ? __bfloat162float(g.mask[(size_t)row * g.ldm + col]) : 0.0f;
+            }
+          }
           const float bcol = g.bias ? g.bias[col] : 0.0f;
+          float csum = 0.0f;
+#pragma unroll
           for (int r = 0; r < 32; ++r) {
             const int row = rbase + r;
-            if (row >= g.M) break;
-            float x = g.alpha * st[r * 33 + lane] + bcol;
-            if (g.relu) x = fmaxf(x, 0.0f);
-            if (g.mask && !(__bfloat162float(g.mask[(size_t)row * g.ldm + col]) > 0.0f)) x = 0.0f;
-            if (g.Cf) g.Cf[(size_t)row * g.ldcf + col] = x;
-            if (g.Cb) g.Cb[(size_t)row * g.ldcb + col] = __float2bfloat16_rn(x);
+            if (row < g.M) {
+              float x = g.alpha * st[r * 33 + lane] + bcol;
+              if (g.relu) x = fmaxf(x, 0.0f);
+              if (g.mask && !(mk[r] > 0.0f)) x = 0.0f;
+              if (g.Cf) g.Cf[(size_t)row * g.ldcf + col] = x;
+              if (g.Cb) g.Cb[(size_t)row * g.ldcb + col] = __float2bfloat16_rn(x);
+              st[r * 33 + lane] = x;
+              csum += x;
+            }
+          }
+          if (g.colpart) g.colpart[(size_t)(rbase / 32) * g.N + col] = csum;
+        }
+        if (g.CbT) {
+          // lane = row: 32 consecutive rows of each transposed output row
+          __syncwarp();
+          const int row = rbase + lane;
+          if (row < g.M) {
+#pragma unroll 8
+            for (int c = 0; c < 32; ++c) {
+              const int cc = n0 + c0 + c;
+              if (cc < g.N) g.CbT[(size_t)cc * g.ldct + row] = __float2bfloat16_rn(st[lane * 33 + c]);
+            }
           }
         }
         __syncwarp();
@@ -477,13 +663,13 @@ namespace sepso {
 //   of the straight start-target line at fraction (k + 1) / (T + 1), over the extent.
 // ---------------------------------------------------------------------------
 struct RasterArgs {
-  int n, grid, K, T, O_max;
+  int n, grid, K, ldx, T, O_max;
   float W, H;
   const float4* circ;      // staged circles (cx, cy, r, 0) of the chunk
   const int* coff;         // n + 1 prefix offsets into circ
   const float* pts;        // n x 4
   const float* wp;         // n x 2T, or null
-  __nv_bfloat16* X;        // n rows of K (destination rows)
+  __nv_bfloat16* X;        // n rows of K features, row pitch ldx >= K (pad zero)
   float* Y;                // n rows of 2T, or null
 };
 
@@ -494,7 +680,7 @@ __global__ void __launch_bounds__(256) raster_kernel(const RasterArgs a) {
   for (int i = threadIdx.x; i < O; i += blockDim.x) rc[i] = a.circ[c0 + i];
   __syncthreads();
   const float cw = a.W / (float)a.grid, ch = a.H / (float)a.grid;
-  __nv_bfloat16* row = a.X + (size_t)s * a.K;
+  __nv_bfloat16* row = a.X + (size_t)s * a.ldx;
   const int g2 = a.grid * a.grid;
   for (int c = threadIdx.x; c < g2; c += blockDim.x) {
     const int i = c / a.grid, j = c - i * a.grid;
@@ -509,9 +695,9 @@ __global__ void __launch_bounds__(256) raster_kernel(const RasterArgs a) {
     row[c] = __float2bfloat16_rn(occ ? 1.0f : 0.0f);
   }
   const float* p = a.pts + 4 * s;
-  for (int k = g2 + threadIdx.x; k < a.K; k += blockDim.x) {
+  for (int k = g2 + threadIdx.x; k < a.ldx; k += blockDim.x) {
     const int e = k - g2;
-    const float v = (e < 4) ? p[e] / ((e & 1) ? a.H : a.W) : 0.0f;
+    const float v = (e < 4 && k < a.K) ? p[e] / ((e & 1) ? a.H : a.W) : 0.0f;
     row[k] = __float2bfloat16_rn(v);
   }
   if (a.wp != nullptr && a.Y != nullptr) {
@@ -551,36 +737,12 @@ __global__ void sample_kernel(int* idx, int B, int n_rows, uint32_t k0, uint32_t
 
 // x[b] = X[r] (K bf16, 16-byte vectors), t[b] = Y[r], with r = idx[b] (or first + b
 // without an index list).
-__global__ void gather_kernel(const int* __restrict__ idx, int first, int B, int K, const __nv_bfloat16* __restrict__ X,
-                              const float* __restrict__ Y, int O, __nv_bfloat16* __restrict__ x, float* __restrict__ t) {
-  const int b = blockIdx.x;
-  if (b >= B) return;
-  const int r = idx ? idx[b] : first + b;
-  const uint4* src = reinterpret_cast<const uint4*>(X + (size_t)r * K);
-  uint4* dst = reinterpret_cast<uint4*>(x + (size_t)b * K);
-  for (int v = threadIdx.x; v < K / 8; v += blockDim.x) dst[v] = src[v];
-  for (int d = threadIdx.x; d < O; d += blockDim.x) t[(size_t)b * O + d] = Y[(size_t)r * O + d];
-}
-
-// out[c][r] = in[r][c] for r < R, c < C (bf16); 32 x 32 tiles through shared memory.
-__global__ void transpose_kernel(const __nv_bfloat16* __restrict__ in, int R, int C, int ldi,
-                                 __nv_bfloat16* __restrict__ out, int ldo) {
-  __shared__ __nv_bfloat16 t[32][34];
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
-    const int r = r0 + dy, c = c0 + threadIdx.x;
-    if (r < R && c < C) t[dy][threadIdx.x] = in[(size_t)r * ldi + c];
-  }
-  __syncthreads();
-  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
-    const int c = c0 + dy, r = r0 + threadIdx.x;
-    if (r < R && c < C) out[(size_t)c * ldo + r] = t[threadIdx.x][dy];
-  }
-}
-
-// dY = (y - t) / B (FP32, and BF16 with columns O .. ldb-1 zero); loss += sum (y - t)^2 / 2B.
+// dY = (y - t) / B: FP32 (B x O), BF16 (B x ldb, columns O .. ldb-1 zero) and BF16
+// transposed (O x B); loss += sum (y - t)^2 / 2B, one atomic per CTA.
 __global__ void loss_grad_kernel(const float* __restrict__ y, const float* __restrict__ t, int B, int O,
-                                 float* __restrict__ dyf, __nv_bfloat16* __restrict__ dyb, int ldb, float* loss) {
+                                 float* __restrict__ dyf, __nv_bfloat16* __restrict__ dyb, int ldb,
+                                 __nv_bfloat16* __restrict__ dyT, float* loss) {
+  __shared__ float wsum[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float sq = 0.0f;
   if (i < B * ldb) {
@@ -591,11 +753,98 @@ __global__ void loss_grad_kernel(const float* __restrict__ y, const float* __res
       sq = e * e;
       g = e / (float)B;
       dyf[(size_t)b * O + d] = g;
+      dyT[(size_t)d * B + b] = __float2bfloat16_rn(g);
     }
     dyb[i] = __float2bfloat16_rn(g);
   }
   for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  if ((threadIdx.x & 31) == 0 && sq != 0.0f) atomicAdd(loss, 0.5f * sq / (float)B);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wsum[w];
+    if (s != 0.0f) atomicAdd(loss, 0.5f * s / (float)B);
+  }
+}
+
+// Column sums, first stage: part[p][j] = sum of D[b][j] over rows b of 32-row block p
+// (8 row lanes, then the lanes in order).
+__global__ void colsum_part_kernel(const float* __restrict__ D, int B, int N, int ld, float* __restrict__ part) {
+  __shared__ float s[8][33];
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int b0 = blockIdx.y * 32;
+  float acc = 0.0f;
+  if (j < N)
+    for (int b = b0 + threadIdx.y; b < min(B, b0 + 32); b += 8) acc += D[(size_t)b * ld + j];
+  s[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < N) {
+    float v = 0.0f;
+    for (int r = 0; r < 8; ++r) v += s[r][threadIdx.x];
+    part[(size_t)blockIdx.y * N + j] = v;
+  }
+}
+
+// Split K: C = epilogue(alpha * (sum of the K-slices' FP32 products, in slice order)).
+__global__ void splitk_reduce_kernel(const GemmArgs g, int slices) {
+  const long long MN = (long long)g.M * g.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < MN; i += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int z = 0; z < slices; ++z) acc += __ldcs(g.part + z * MN + i);
+    const int m = (int)(i / g.N), n = (int)(i - (long long)m * g.N);
+    float x = acc * g.alpha;
+    if (g.bias) x += g.bias[n];
+    if (g.relu) x = fmaxf(x, 0.0f);
+    if (g.mask && !(__bfloat162float(g.mask[(size_t)m * g.ldm + n]) > 0.0f)) x = 0.0f;
+    if (g.Cf) g.Cf[(size_t)m * g.ldcf + n] = x;
+    if (g.Cb) g.Cb[(size_t)m * g.ldcb + n] = __float2bfloat16_rn(x);
+  }
+}
+
+// x[b] = X[row b] and xT[k][b] = X[row b][k] (row b = idx[b], or first + b; rows of
+// K features at pitch ldx), t[b] = Y[row b]: 64 rows x 128 features per CTA, read
+// and copied with 16-byte accesses, transposed through shared memory into 128-byte
+// row segments of xT (K a multiple of 8, n even).
+__global__ void __launch_bounds__(256) gather_t_kernel(const int* __restrict__ idx, int first, int n, int K, int ldx,
+                                                       const __nv_bfloat16* __restrict__ X, const float* __restrict__ Y,
+                                                       int O, __nv_bfloat16* __restrict__ x,
+                                                       __nv_bfloat16* __restrict__ xT, float* __restrict__ t) {
+  __shared__ uint32_t sm[64][65];  // 64 rows b x 64 feature pairs
+  const int k0 = blockIdx.x * 128, b0 = blockIdx.y * 64;
+  const int tid = threadIdx.x, lane = tid & 31;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int e = tid + i * 256;
+    const int rb = e >> 4, qd = e & 15;  // row of the tile, 8-feature group
+    const int b = b0 + rb, k = k0 + qd * 8;
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    if (b < n && k < K) {
+      const int r = idx ? idx[b] : first + b;
+      w = *reinterpret_cast<const uint4*>(X + (size_t)r * ldx + k);
+      *reinterpret_cast<uint4*>(x + (size_t)b * ldx + k) = w;
+    }
+    sm[rb][qd * 4 + 0] = w.x;
+    sm[rb][qd * 4 + 1] = w.y;
+    sm[rb][qd * 4 + 2] = w.z;
+    sm[rb][qd * 4 + 3] = w.w;
+  }
+  if (blockIdx.x == 0) {
+    for (int e = tid; e < 64 * O; e += 256) {
+      const int rb = e / O, d = e - rb * O, b = b0 + rb;
+      if (b < n) t[(size_t)b * O + d] = Y[(size_t)(idx ? idx[b] : first + b) * O + d];
+    }
+  }
+  __syncthreads();
+#pragma unroll 4
+  for (int kk = tid >> 5; kk < 128; kk += 8) {
+    const int k = k0 + kk, b = b0 + 2 * lane;
+    if (k < K && b < n) {
+      const int sh = (kk & 1) ? 16 : 0;
+      const uint32_t lo = (sm[2 * lane][kk >> 1] >> sh) & 0xffffu, hi = (sm[2 * lane + 1][kk >> 1] >> sh) & 0xffffu;
+      *reinterpret_cast<uint32_t*>(xT + (size_t)k * n + b) = lo | (hi << 16);
+    }
+  }
 }
 
 // db[j] = sum_b D[b][j]: 32 columns per CTA, 8 row lanes, fixed summation order.
@@ -614,25 +863,90 @@ __global__ void colsum_kernel(const float* __restrict__ D, int B, int N, int ld,
   }
 }
 
-// Adam (Kingma and Ba, 2015), FP32 masters; also refreshes the BF16 mirror.
-__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
-                            const float* __restrict__ g, __nv_bfloat16* __restrict__ wb, long long n, float lr,
-                            float b1, float b2, float eps, float c1, float c2) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    w[i] = wi;
-    wb[i] = __float2bfloat16_rn(wi);
+// BF16 copies of the weights that the products read: W1 (h1 x k, at offset 0) in
+// rows of pitch ldp (128-byte rows for the TMA boxes), W2 (h2 x h1, at off2) and
+// W3 (o x h2, at off4) transposed (the backward pass's B operands).
+struct BfMirrors {
+  __nv_bfloat16* w1p;
+  int h1, k, ldp;
+  __nv_bfloat16* w2t;
+  long long off2;
+  int h2;
+  __nv_bfloat16* w3t;
+  long long off4;
+  int o, o8;
+};
+
+__device__ __forceinline__ void mirror_store(const BfMirrors& mr, long long i, __nv_bfloat16 b) {
+  if (i < (long long)mr.h1 * mr.k) {  // h1 * ldp < 2^31
+    const int ii = (int)i, r = ii / mr.k;
+    mr.w1p[r * mr.ldp + (ii - r * mr.k)] = b;
+    return;
+  }
+  long long j = i - mr.off2;
+  if (j >= 0 && j < (long long)mr.h2 * mr.h1) {
+    const int jj = (int)j, r = jj / mr.h1;
+    mr.w2t[(size_t)(jj - r * mr.h1) * mr.h2 + r] = b;
+    return;
+  }
+  j = i - mr.off4;
+  if (j >= 0 && j < (long long)mr.o * mr.h2) {
+    const int jj = (int)j, r = jj / mr.h2;
+    mr.w3t[(size_t)(jj - r * mr.h2) * mr.o8 + r] = b;
   }
 }
 
-__global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    wb[i] = __float2bfloat16_rn(w[i]);
+__device__ __forceinline__ float adam_update(float& w, float& m, float& v, float g, float lr, float b1, float b2,
+                                             float eps, float c1, float c2) {
+  m = b1 * m + (1.0f - b1) * g;
+  v = b2 * v + (1.0f - b2) * g * g;
+  w = w - lr * (m / c1) / (sqrtf(v / c2) + eps);
+  return w;
+}
+
+// Adam (Kingma and Ba, 2015) on FP32 masters, four parameters per thread step
+// (16-byte accesses), then the BF16 copies: wb (all parameters) and the mirrors.
+__global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, __nv_bfloat16* __restrict__ wb, long long n, float lr,
+                            float b1, float b2, float eps, float c1, float c2, const BfMirrors mr) {
+  const long long n4 = n / 4;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n4; q += stride) {
+    float4 W = reinterpret_cast<float4*>(w)[q], M = reinterpret_cast<float4*>(m)[q];
+    float4 V = reinterpret_cast<float4*>(v)[q];
+    const float4 Gq = reinterpret_cast<const float4*>(g)[q];
+    const float a = adam_update(W.x, M.x, V.x, Gq.x, lr, b1, b2, eps, c1, c2);
+    const float b = adam_update(W.y, M.y, V.y, Gq.y, lr, b1, b2, eps, c1, c2);
+    const float c = adam_update(W.z, M.z, V.z, Gq.z, lr, b1, b2, eps, c1, c2);
+    const float d = adam_update(W.w, M.w, V.w, Gq.w, lr, b1, b2, eps, c1, c2);
+    reinterpret_cast<float4*>(w)[q] = W;
+    reinterpret_cast<float4*>(m)[q] = M;
+    reinterpret_cast<float4*>(v)[q] = V;
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    uint2 u;
+    u.x = *reinterpret_cast<const uint32_t*>(&lo);
+    u.y = *reinterpret_cast<const uint32_t*>(&hi);
+    reinterpret_cast<uint2*>(wb)[q] = u;
+    mirror_store(mr, 4 * q, lo.x);
+    mirror_store(mr, 4 * q + 1, lo.y);
+    mirror_store(mr, 4 * q + 2, hi.x);
+    mirror_store(mr, 4 * q + 3, hi.y);
+  }
+  for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float wi = adam_update(w[i], m[i], v[i], g[i], lr, b1, b2, eps, c1, c2);
+    const __nv_bfloat16 bi = __float2bfloat16_rn(wi);
+    wb[i] = bi;
+    mirror_store(mr, i, bi);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, long long n,
+                               const BfMirrors mr) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(w[i]);
+    wb[i] = b;
+    mirror_store(mr, i, b);
+  }
 }
 
 // Waypoints of the network outputs: straight-line point + y * extent, clipped to the map.
@@ -782,7 +1096,7 @@ int choose_tile_n(int M, int N) {
 }
 
 template <int BN>
-int gemm_launch_bn(const CUtensorMap& ta, const GemmArgs& g, cudaStream_t s) {
+int gemm_launch_bn(const CUtensorMap& ta, const GemmArgs& g, cudaStream_t s, int slices = 1) {
   CUtensorMap tb;
   PTRY(make_map(&tb, g.B, g.N, g.K, g.ldb, BN));
   static thread_local int configured_device = -1;
@@ -793,8 +1107,8 @@ int gemm_launch_bn(const CUtensorMap& ta, const GemmArgs& g, cudaStream_t s) {
                                sepso::kGemmSmem));
     configured_device = dev;
   }
-  const dim3 grid((g.M + sepso::kBM - 1) / sepso::kBM, (g.N + BN - 1) / BN);
-  if (grid.y > 65535u) return pfail(SEPSO_EINVAL, "gemm: N too large");
+  const dim3 grid((g.M + sepso::kBM - 1) / sepso::kBM, (g.N + BN - 1) / BN, slices);
+  if (grid.y > 65535u || grid.z > 65535u) return pfail(SEPSO_EINVAL, "gemm: N or the K split too large");
   sepso::gemm_tc_kernel<BN><<<grid, sepso::kGemmThreads, sepso::kGemmSmem, s>>>(ta, tb, g);
   PCUDA(cudaGetLastError());
   return SEPSO_OK;
@@ -821,18 +1135,21 @@ int gemm_launch_persistent(const CUtensorMap& ta, const GemmArgs& g, cudaStream_
 }
 
 // Kernel and tile width for a product (positive: persistent; negative: one tile
-// per CTA), from a sweep of both kernels on GB300 (TFLOP/s, persistent / one per CTA):
-//   many tiles (>= 2 per SM at width 256; 4096^3: 975 / 941)  -> persistent, 256
-//   about one wave of 256-wide tiles (1024 x 4104 x 1024: 316 / 364)   -> one per CTA, 256
-//   few tiles and a long K (1024 x 1024 x 4104, width 64: 237 / 262)  -> one per CTA, 64
-//   few tiles and a short K (1024 x 512 x 1024: 66 / 60)              -> persistent, 64
+// per CTA), from sweeps of both kernels on GB300:
+//   many tiles (>= 2 per SM at width 256; 4096^3: 975 / 941 TFLOP/s) -> persistent, 256
+//   about one wave of 256-wide tiles (1024 x 4104 x 1024: 316 / 364)  -> one per CTA, 256
+//   few tiles and a long K (1024 x 1024 x 4104, width 64: 237 / 262) -> one per CTA, 64
+//   few tiles and a short K, with the eight-warp epilogue (4096 x 512 x 1024:
+//   persistent 64 22.8 us, one per CTA 128 16.6 us; 4096 x 512 x 40 with mask,
+//   transposed copy and column sums: 31.1 / 18.7 us)                  -> one per CTA, 128
+//   (64 when N <= 64: 4096 x 40 x 512, 11.0 / 8.7 us)
 int choose_tile_n_auto(int M, int N, int K) {
   choose_tile_n(M, N);  // fills the SM count
   const long long mt = (M + sepso::kBM - 1) / sepso::kBM;
   const long long t256 = mt * ((N + 255) / 256);
   if (t256 >= 2LL * g_num_sms) return 256;
   if (4 * t256 >= 3LL * g_num_sms) return -256;
-  return K >= 2048 ? -64 : 64;
+  return (K >= 2048 || N <= 64) ? -64 : -128;
 }
 
 // tile_n: 0 automatic (persistent kernel); 64 / 128 / 256 the persistent kernel
@@ -866,13 +1183,104 @@ int gemm_launch(const GemmArgs& g, cudaStream_t s, int tile_n = 0) {
   }
 }
 
+// What a product needs beyond the plain epilogue: a transposed BF16 copy of the
+// output, its column sums, or a split of K into slices whose FP32 products are
+// summed in slice order (row-major outputs only).
+struct GemmExtra {
+  bf16* CbT = nullptr;
+  int ldct = 0;
+  float* colsum = nullptr;
+  int ksplit = 1;
+  float* ws = nullptr;  // device scratch of gemm_ws_bytes
+  size_t ws_bytes = 0;
+};
+
+size_t gemm_ws_bytes(long long M, long long N, int ksplit, bool colsum) {
+  if (ksplit > 1) return (size_t)ksplit * M * N * 4;
+  return colsum ? (size_t)((M + 31) / 32) * N * 4 : 0;
+}
+
+// K slices for a product whose tiles fill few SMs: about one wave of CTAs, at
+// least 4 K-blocks per slice, at most kMaxSlices.
+constexpr int kMaxSlices = 16;
+int auto_ksplit(int M, int N, int K, int bn) {
+  choose_tile_n(M, N);  // fills the SM count
+  const long long tiles = (long long)((M + sepso::kBM - 1) / sepso::kBM) * ((N + bn - 1) / bn);
+  const long long nkb = (K + sepso::kBK - 1) / sepso::kBK;
+  if (2 * tiles > g_num_sms) return 1;
+  long long sl = std::min<long long>(g_num_sms / tiles, nkb / 4);
+  sl = std::min<long long>(sl, kMaxSlices);
+  return (int)std::max<long long>(sl, 1);
+}
+
+int gemm_run_check(const GemmArgs& g, const GemmExtra& e, int tile_n) {
+  PTRY(gemm_check(g, tile_n));
+  if (e.CbT && e.ldct < g.M) return pfail(SEPSO_EINVAL, "gemm: transposed output row stride %d below M", e.ldct);
+  if (e.ksplit < 1 || e.ksplit > 4096) return pfail(SEPSO_EINVAL, "gemm: K split %d", e.ksplit);
+  if (e.ksplit > 1 && (e.CbT || e.colsum))
+    return pfail(SEPSO_EINVAL, "gemm: a K split supports the row-major outputs only");
+  const size_t need = gemm_ws_bytes(g.M, g.N, e.ksplit, e.colsum != nullptr);
+  if (need && (!e.ws || e.ws_bytes < need || !aligned16(e.ws)))
+    return pfail(SEPSO_ENOSPC, "gemm: workspace of %zu bytes, need %zu (16-byte aligned)", e.ws_bytes, need);
+  return SEPSO_OK;
+}
+
+// One product with its extras; *launches gets the kernels launched.
+int gemm_run(GemmArgs g, const GemmExtra& e, cudaStream_t s, int tile_n, int* launches) {
+  *launches = 0;
+  PTRY(gemm_run_check(g, e, tile_n));
+  g.CbT = nullptr;
+  g.colpart = nullptr;
+  g.part = nullptr;
+  g.kcb = 0;
+  if (e.ksplit > 1) {
+    const int nkb = (g.K + sepso::kBK - 1) / sepso::kBK;
+    const int kcb = (nkb + e.ksplit - 1) / e.ksplit;
+    const int slices = (nkb + kcb - 1) / kcb;  // every slice non-empty
+    GemmArgs r = g;
+    r.alpha = 1.0f;
+    r.bias = nullptr;
+    r.relu = 0;
+    r.mask = nullptr;
+    r.Cf = nullptr;
+    r.Cb = nullptr;
+    r.part = e.ws;
+    r.kcb = kcb;
+    CUtensorMap ta;
+    PTRY(make_map(&ta, g.A, g.M, g.K, g.lda, sepso::kBM));
+    const int bn = tile_n ? std::abs(tile_n) : 128;
+    if (bn == 64) PTRY(gemm_launch_bn<64>(ta, r, s, slices));
+    else if (bn == 128) PTRY(gemm_launch_bn<128>(ta, r, s, slices));
+    else PTRY(gemm_launch_bn<256>(ta, r, s, slices));
+    GemmArgs f = g;
+    f.part = e.ws;
+    const long long MN = (long long)g.M * g.N;
+    const int blocks = (int)std::min<long long>((MN + 255) / 256, 16LL * std::max(g_num_sms, 1));
+    sepso::splitk_reduce_kernel<<<blocks, 256, 0, s>>>(f, slices);
+    PCUDA(cudaGetLastError());
+    *launches = 2;
+    return SEPSO_OK;
+  }
+  g.CbT = e.CbT;
+  g.ldct = e.ldct;
+  g.colpart = e.colsum ? e.ws : nullptr;
+  PTRY(gemm_launch(g, s, tile_n));
+  *launches = 1;
+  if (e.colsum) {
+    sepso::colsum_kernel<<<(g.N + 31) / 32, dim3(32, 8), 0, s>>>(e.ws, (g.M + 31) / 32, g.N, g.N, e.colsum);
+    PCUDA(cudaGetLastError());
+    *launches = 2;
+  }
+  return SEPSO_OK;
+}
+
 struct PriorLayout {
-  size_t prm, m, v, grad, wb, w2t, w3t, X, Y, P, scirc, scoff, spts, swp, idx, x, xT, h1, h1T, h2, h2T, y, t, dyf,
-      dyb, dyT, dh2f, dh2b, dh2T, dh1f, dh1b, dh1T, loss, status, total;
+  size_t prm, m, v, grad, wb, w1p, w2t, w3t, X, Y, P, scirc, scoff, spts, swp, idx, x, xT, h1, h1T, h2, h2T, y, t, dyf,
+      dyb, dyT, dh2b, dh2T, dh1T, kpart, cpart, loss, status, total;
 };
 
 struct Dims {
-  int K, O, O8, H1, H2, B, g;
+  int K, Kp, O, O8, H1, H2, B, g;  // Kp: feature row pitch, a multiple of 64 (128-byte rows)
   long long P;
   long long off[6];
 };
@@ -885,6 +1293,7 @@ bool make_dims(const sepso_prior_config* c, Dims* d) {
     return false;
   d->g = c->grid;
   d->K = round8(c->grid * c->grid + 4);
+  d->Kp = (d->K + 63) / 64 * 64;
   d->O = 2 * c->T;
   d->O8 = round8(d->O);
   d->H1 = c->hidden1;
@@ -897,7 +1306,7 @@ bool make_dims(const sepso_prior_config* c, Dims* d) {
   d->off[4] = d->off[3] + d->H2;
   d->off[5] = d->off[4] + (long long)d->O * d->H2;
   d->P = d->off[5] + d->O;
-  return (long long)c->capacity * d->K < (1ll << 40);
+  return (long long)c->capacity * d->Kp < (1ll << 40) && (long long)d->H1 * d->Kp < (1ll << 31);
 }
 
 PriorLayout layout(const sepso_prior_config* c, const Dims& d) {
@@ -916,9 +1325,10 @@ PriorLayout layout(const sepso_prior_config* c, const Dims& d) {
   L.v = take(P * 4);
   L.grad = take(P * 4);
   L.wb = take(P * 2);
+  L.w1p = take(H1 * (size_t)d.Kp * 2);
   L.w2t = take(H1 * H2 * 2);
   L.w3t = take(H2 * d.O8 * 2);
-  L.X = take(cap * K * 2);
+  L.X = take(cap * (size_t)d.Kp * 2);
   L.Y = take(cap * O * 4);
   L.P = take(cap * 16);
   L.scirc = take(B * (size_t)std::max(c->max_circles, 1) * 16);
@@ -926,7 +1336,7 @@ PriorLayout layout(const sepso_prior_config* c, const Dims& d) {
   L.spts = take(B * 16);
   L.swp = take(B * O * 4);
   L.idx = take(B * 4);
-  L.x = take(B * K * 2);
+  L.x = take(B * (size_t)d.Kp * 2);
   L.xT = take(K * B * 2);
   L.h1 = take(B * H1 * 2);
   L.h1T = take(H1 * B * 2);
@@ -937,12 +1347,11 @@ PriorLayout layout(const sepso_prior_config* c, const Dims& d) {
   L.dyf = take(B * O * 4);
   L.dyb = take(B * d.O8 * 2);
   L.dyT = take(O * B * 2);
-  L.dh2f = take(B * H2 * 4);
   L.dh2b = take(B * H2 * 2);
   L.dh2T = take(H2 * B * 2);
-  L.dh1f = take(B * H1 * 4);
-  L.dh1b = take(B * H1 * 2);
   L.dh1T = take(H1 * B * 2);
+  L.kpart = take((size_t)kMaxSlices * std::max(O * H2, H2 * H1) * 4);  // K-split partial products
+  L.cpart = take((B + 31) / 32 * std::max(std::max(H1, H2), O) * 4);    // column sums per 32-row slab
   L.loss = take((size_t)kLossRing * 4);
   L.status = take(4);
   L.total = al256(off);
@@ -972,7 +1381,8 @@ struct sepso_prior_ctx {
 namespace {
 
 int gemm(sepso_prior_ctx* h, const bf16* A, const bf16* B, int M, int N, int K, int lda, int ldb, const float* bias,
-         int relu, const bf16* mask, int ldm, float* Cf, int ldcf, bf16* Cb, int ldcb) {
+         int relu, const bf16* mask, int ldm, float* Cf, int ldcf, bf16* Cb, int ldcb,
+         const GemmExtra& e = GemmExtra(), int tile_n = 0) {
   GemmArgs g{};
   g.A = A;
   g.B = B;
@@ -991,88 +1401,118 @@ int gemm(sepso_prior_ctx* h, const bf16* A, const bf16* B, int M, int N, int K, 
   g.Cb = Cb;
   g.ldcb = ldcb;
   g.status = h->at<int>(h->L.status);
-  ++h->launches;
-  return gemm_launch(g, h->stream);
+  int n = 0;
+  const int r = gemm_run(g, e, h->stream, tile_n, &n);
+  h->launches += n;
+  return r;
 }
 
-int transpose(sepso_prior_ctx* h, const bf16* in, int R, int C, int ldi, bf16* out, int ldo) {
-  const dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
-  sepso::transpose_kernel<<<grid, block, 0, h->stream>>>(in, R, C, ldi, out, ldo);
-  ++h->launches;
-  PCUDA(cudaGetLastError());
-  return SEPSO_OK;
-}
-
+// db[j] = sum over the B rows of D[.][j]: sums over 32-row blocks, then over the blocks.
 int colsum(sepso_prior_ctx* h, const float* D, int B, int N, int ld, float* db) {
-  sepso::colsum_kernel<<<(N + 31) / 32, dim3(32, 8), 0, h->stream>>>(D, B, N, ld, db);
-  ++h->launches;
+  float* part = h->at<float>(h->L.cpart);
+  const int nb = (B + 31) / 32;
+  sepso::colsum_part_kernel<<<dim3((N + 31) / 32, nb), dim3(32, 8), 0, h->stream>>>(D, B, N, ld, part);
+  PCUDA(cudaGetLastError());
+  sepso::colsum_kernel<<<(N + 31) / 32, dim3(32, 8), 0, h->stream>>>(part, nb, N, N, db);
+  h->launches += 2;
   PCUDA(cudaGetLastError());
   return SEPSO_OK;
 }
 
-// Forward pass of n <= B rows x (row stride K): h1, h2 (BF16), y (FP32).
-int forward(sepso_prior_ctx* h, const bf16* x, int n) {
+// Forward pass of n <= B rows x (row pitch Kp): h1, h2 (BF16), y (FP32); for
+// training also the transposed copies h1T, h2T (n columns) the weight gradients read.
+int forward(sepso_prior_ctx* h, const bf16* x, int n, bool train) {
   const Dims& d = h->d;
   const float* prm = h->at<float>(h->L.prm);
   const bf16* wb = h->at<bf16>(h->L.wb);
   bf16* h1 = h->at<bf16>(h->L.h1);
   bf16* h2 = h->at<bf16>(h->L.h2);
-  PTRY(gemm(h, x, wb + d.off[0], n, d.H1, d.K, d.K, d.K, prm + d.off[1], 1, nullptr, 0, nullptr, 0, h1, d.H1));
-  PTRY(gemm(h, h1, wb + d.off[2], n, d.H2, d.H1, d.H1, d.H1, prm + d.off[3], 1, nullptr, 0, nullptr, 0, h2, d.H2));
+  GemmExtra e1, e2;
+  if (train) {
+    e1.CbT = h->at<bf16>(h->L.h1T);
+    e1.ldct = n;
+    e2.CbT = h->at<bf16>(h->L.h2T);
+    e2.ldct = n;
+  }
+  PTRY(gemm(h, x, h->at<bf16>(h->L.w1p), n, d.H1, d.K, d.Kp, d.Kp, prm + d.off[1], 1, nullptr, 0, nullptr, 0, h1,
+            d.H1, e1));
+  PTRY(gemm(h, h1, wb + d.off[2], n, d.H2, d.H1, d.H1, d.H1, prm + d.off[3], 1, nullptr, 0, nullptr, 0, h2, d.H2, e2));
   PTRY(gemm(h, h2, wb + d.off[4], n, d.O, d.H2, d.H2, d.H2, prm + d.off[5], 0, nullptr, 0, h->at<float>(h->L.y), d.O,
             nullptr, 0));
   return SEPSO_OK;
 }
 
-// Backward pass after forward(x, n) with targets in t: gradient into grad, the
-// loss added to loss[slot].  n is a multiple of 8 (the K of the weight GEMMs).
-int backward(sepso_prior_ctx* h, const bf16* x, int n, int slot) {
+// Backward pass after forward(x, n, true) with targets in t: gradient into grad,
+// the loss added to loss[slot].  n is a multiple of 8 (the K of the weight GEMMs).
+// The ReLU-masked products write their BF16 output transposed (the next weight
+// gradient's operand) and their column sums (the bias gradient) from the epilogue;
+// the weight gradients with few output tiles split K.
+int backward(sepso_prior_ctx* h, int n, int slot) {
   const Dims& d = h->d;
   float* grad = h->at<float>(h->L.grad);
   bf16 *h1 = h->at<bf16>(h->L.h1), *h2 = h->at<bf16>(h->L.h2);
   bf16 *dyb = h->at<bf16>(h->L.dyb), *dyT = h->at<bf16>(h->L.dyT);
   bf16 *h2T = h->at<bf16>(h->L.h2T), *h1T = h->at<bf16>(h->L.h1T), *xT = h->at<bf16>(h->L.xT);
-  bf16 *dh2b = h->at<bf16>(h->L.dh2b), *dh2T = h->at<bf16>(h->L.dh2T);
-  bf16 *dh1b = h->at<bf16>(h->L.dh1b), *dh1T = h->at<bf16>(h->L.dh1T);
-  float *dyf = h->at<float>(h->L.dyf), *dh2f = h->at<float>(h->L.dh2f), *dh1f = h->at<float>(h->L.dh1f);
+  bf16 *dh2b = h->at<bf16>(h->L.dh2b), *dh2T = h->at<bf16>(h->L.dh2T), *dh1T = h->at<bf16>(h->L.dh1T);
+  float* dyf = h->at<float>(h->L.dyf);
   const int tot = n * d.O8;
   sepso::loss_grad_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(h->at<float>(h->L.y), h->at<float>(h->L.t), n, d.O,
-                                                                    dyf, dyb, d.O8, h->at<float>(h->L.loss) + slot);
+                                                                    dyf, dyb, d.O8, dyT, h->at<float>(h->L.loss) + slot);
   ++h->launches;
   PCUDA(cudaGetLastError());
-  PTRY(transpose(h, dyb, n, d.O, d.O8, dyT, n));
-  PTRY(transpose(h, h2, n, d.H2, d.H2, h2T, n));
-  PTRY(transpose(h, h1, n, d.H1, d.H1, h1T, n));
-  PTRY(transpose(h, x, n, d.K, d.K, xT, n));
-  // layer 3: gW3 = dY^T h2, gb3 = colsum dY, dh2 = (dY W3) * [h2 > 0]
-  PTRY(gemm(h, dyT, h2T, d.O, d.H2, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[4], d.H2, nullptr, 0));
+  GemmExtra kw;  // weight gradients: K split over the partial-product scratch
+  kw.ws = h->at<float>(h->L.kpart);
+  kw.ws_bytes = (size_t)kMaxSlices * std::max(d.O * d.H2, d.H2 * d.H1) * 4;
+  GemmExtra mk;  // masked products: transposed output and column sums
+  mk.ws = h->at<float>(h->L.cpart);
+  mk.ws_bytes = (size_t)((d.B + 31) / 32) * std::max(std::max(d.H1, d.H2), d.O) * 4;
+  mk.ldct = n;
+  // layer 3: gb3 = colsum dY, gW3 = dY^T h2, dh2 = (dY W3) * [h2 > 0] (+ dh2T, gb2 = colsum dh2)
   PTRY(colsum(h, dyf, n, d.O, d.O, grad + d.off[5]));
-  PTRY(gemm(h, dyb, h->at<bf16>(h->L.w3t), n, d.H2, d.O8, d.O8, d.O8, nullptr, 0, h2, d.H2, dh2f, d.H2, dh2b, d.H2));
-  // layer 2
-  PTRY(colsum(h, dh2f, n, d.H2, d.H2, grad + d.off[3]));
-  PTRY(transpose(h, dh2b, n, d.H2, d.H2, dh2T, n));
-  PTRY(gemm(h, dh2T, h1T, d.H2, d.H1, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[2], d.H1, nullptr, 0));
-  PTRY(gemm(h, dh2b, h->at<bf16>(h->L.w2t), n, d.H1, d.H2, d.H2, d.H2, nullptr, 0, h1, d.H1, dh1f, d.H1, dh1b, d.H1));
-  // layer 1
-  PTRY(colsum(h, dh1f, n, d.H1, d.H1, grad + d.off[1]));
-  PTRY(transpose(h, dh1b, n, d.H1, d.H1, dh1T, n));
+  kw.ksplit = auto_ksplit(d.O, d.H2, n, 64);
+  PTRY(gemm(h, dyT, h2T, d.O, d.H2, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[4], d.H2, nullptr, 0, kw, -64));
+  mk.CbT = dh2T;
+  mk.colsum = grad + d.off[3];
+  PTRY(gemm(h, dyb, h->at<bf16>(h->L.w3t), n, d.H2, d.O8, d.O8, d.O8, nullptr, 0, h2, d.H2, nullptr, 0, dh2b, d.H2,
+            mk));
+  // layer 2: gW2 = dh2^T h1, dh1 = (dh2 W2) * [h1 > 0] (only dh1T, gb1 = colsum dh1)
+  kw.ksplit = auto_ksplit(d.H2, d.H1, n, 128);
+  PTRY(gemm(h, dh2T, h1T, d.H2, d.H1, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[2], d.H1, nullptr, 0, kw, -128));
+  mk.CbT = dh1T;
+  mk.colsum = grad + d.off[1];
+  PTRY(gemm(h, dh2b, h->at<bf16>(h->L.w2t), n, d.H1, d.H2, d.H2, d.H2, nullptr, 0, h1, d.H1, nullptr, 0, nullptr, 0,
+            mk));
+  // layer 1: gW1 = dh1^T x
   PTRY(gemm(h, dh1T, xT, d.H1, d.K, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[0], d.K, nullptr, 0));
   return SEPSO_OK;
 }
 
-// BF16 transposed copies of W2 (H1 x H2) and W3 (H2 x O8, columns O.. zero).
-int refresh_transposes(sepso_prior_ctx* h) {
+// The BF16 weight copies the products read: W1 at pitch Kp, W2 transposed (H1 x
+// H2), W3 transposed (H2 x O8; columns O .. O8-1 stay zero from the workspace clear).
+sepso::BfMirrors mirrors(sepso_prior_ctx* h) {
   const Dims& d = h->d;
-  const bf16* wb = h->at<bf16>(h->L.wb);
-  PTRY(transpose(h, wb + d.off[2], d.H2, d.H1, d.H1, h->at<bf16>(h->L.w2t), d.H2));
-  PTRY(transpose(h, wb + d.off[4], d.O, d.H2, d.H2, h->at<bf16>(h->L.w3t), d.O8));
-  return SEPSO_OK;
+  sepso::BfMirrors mr;
+  mr.w1p = h->at<bf16>(h->L.w1p);
+  mr.h1 = d.H1;
+  mr.k = d.K;
+  mr.ldp = d.Kp;
+  mr.w2t = h->at<bf16>(h->L.w2t);
+  mr.off2 = d.off[2];
+  mr.h2 = d.H2;
+  mr.w3t = h->at<bf16>(h->L.w3t);
+  mr.off4 = d.off[4];
+  mr.o = d.O;
+  mr.o8 = d.O8;
+  return mr;
 }
 
+// Training rows: x (n x K), its transpose xT (K x n) and the targets t.
 int gather(sepso_prior_ctx* h, const int* idx, int first, int n) {
   const Dims& d = h->d;
-  sepso::gather_kernel<<<n, 256, 0, h->stream>>>(idx, first, n, d.K, h->at<bf16>(h->L.X), h->at<float>(h->L.Y), d.O,
-                                                 h->at<bf16>(h->L.x), h->at<float>(h->L.t));
+  const dim3 grid((d.K + 127) / 128, (n + 63) / 64);
+  sepso::gather_t_kernel<<<grid, 256, 0, h->stream>>>(idx, first, n, d.K, d.Kp, h->at<bf16>(h->L.X), h->at<float>(h->L.Y),
+                                                      d.O, h->at<bf16>(h->L.x), h->at<bf16>(h->L.xT),
+                                                      h->at<float>(h->L.t));
   ++h->launches;
   PCUDA(cudaGetLastError());
   return SEPSO_OK;
@@ -1086,10 +1526,10 @@ int adam_step(sepso_prior_ctx* h) {
   const long long blocks = std::min<long long>((d.P + 255) / 256, 152LL * 16);
   sepso::adam_kernel<<<(unsigned)blocks, 256, 0, h->stream>>>(
       h->at<float>(h->L.prm), h->at<float>(h->L.m), h->at<float>(h->L.v), h->at<float>(h->L.grad), h->at<bf16>(h->L.wb),
-      d.P, h->c.lr, h->c.beta1, h->c.beta2, h->c.eps, (float)c1, (float)c2);
+      d.P, h->c.lr, h->c.beta1, h->c.beta2, h->c.eps, (float)c1, (float)c2, mirrors(h));
   ++h->launches;
   PCUDA(cudaGetLastError());
-  return refresh_transposes(h);
+  return SEPSO_OK;
 }
 
 int check_rows(const sepso_prior_ctx* h, int first, int n) {
@@ -1172,10 +1612,10 @@ int sepso_prior_set_params(sepso_prior_handle h, const float* params) {
   PCUDA(cudaMemsetAsync(h->at<float>(h->L.m), 0, n, h->stream));
   PCUDA(cudaMemsetAsync(h->at<float>(h->L.v), 0, n, h->stream));
   const long long blocks = std::min<long long>((h->d.P + 255) / 256, 152LL * 16);
-  sepso::to_bf16_kernel<<<(unsigned)blocks, 256, 0, h->stream>>>(h->at<float>(h->L.prm), h->at<bf16>(h->L.wb), h->d.P);
+  sepso::to_bf16_kernel<<<(unsigned)blocks, 256, 0, h->stream>>>(h->at<float>(h->L.prm), h->at<bf16>(h->L.wb), h->d.P,
+                                                                  mirrors(h));
   ++h->launches;
   PCUDA(cudaGetLastError());
-  PTRY(refresh_transposes(h));
   h->step = 0;
   PCUDA(cudaStreamSynchronize(h->stream));
   return SEPSO_OK;
@@ -1227,6 +1667,7 @@ int sepso_prior_add_scenes(sepso_prior_handle h, int32_t first, int32_t n, const
     a.n = m;
     a.grid = d.g;
     a.K = d.K;
+    a.ldx = d.Kp;
     a.T = h->c.T;
     a.O_max = h->c.max_circles;
     a.W = h->c.map_w;
@@ -1235,7 +1676,7 @@ int sepso_prior_add_scenes(sepso_prior_handle h, int32_t first, int32_t n, const
     a.coff = h->at<int>(h->L.scoff);
     a.pts = h->at<float>(h->L.P) + 4LL * (first + s0);
     a.wp = waypoints ? h->at<float>(h->L.swp) : nullptr;
-    a.X = h->at<bf16>(h->L.X) + (long long)(first + s0) * d.K;
+    a.X = h->at<bf16>(h->L.X) + (long long)(first + s0) * d.Kp;
     a.Y = h->at<float>(h->L.Y) + (long long)(first + s0) * d.O;
     const size_t smem = (size_t)std::max(h->c.max_circles, 1) * 16;
     if (smem > 48 * 1024)
@@ -1269,8 +1710,8 @@ int sepso_prior_get_rows(sepso_prior_handle h, int32_t first, int32_t n, float* 
   const Dims& d = h->d;
   if (features && n > 0) {
     std::vector<uint16_t> raw((size_t)n * d.K);
-    PCUDA(cudaMemcpyAsync(raw.data(), h->at<bf16>(h->L.X) + (long long)first * d.K, raw.size() * 2,
-                          cudaMemcpyDeviceToHost, h->stream));
+    PCUDA(cudaMemcpy2DAsync(raw.data(), (size_t)d.K * 2, h->at<bf16>(h->L.X) + (long long)first * d.Kp,
+                            (size_t)d.Kp * 2, (size_t)d.K * 2, (size_t)n, cudaMemcpyDeviceToHost, h->stream));
     PCUDA(cudaStreamSynchronize(h->stream));
     for (size_t i = 0; i < raw.size(); ++i) {
       const uint32_t bits = (uint32_t)raw[i] << 16;
@@ -1291,7 +1732,7 @@ int sepso_prior_forward(sepso_prior_handle h, int32_t first, int32_t n, float* y
   const Dims& d = h->d;
   for (int s0 = 0; s0 < n; s0 += d.B) {
     const int m = std::min(d.B, n - s0);
-    PTRY(forward(h, h->at<bf16>(h->L.X) + (long long)(first + s0) * d.K, m));
+    PTRY(forward(h, h->at<bf16>(h->L.X) + (long long)(first + s0) * d.Kp, m, false));
     PCUDA(cudaMemcpyAsync(y + (long long)s0 * d.O, h->at<float>(h->L.y), (size_t)m * d.O * 4, cudaMemcpyDeviceToHost,
                           h->stream));
     PTRY(read_status(h));
@@ -1307,8 +1748,8 @@ int sepso_prior_grad(sepso_prior_handle h, int32_t first, int32_t n, float* grad
   h->loss_head = (h->loss_head + 1) % kLossRing;
   PCUDA(cudaMemsetAsync(h->at<float>(h->L.loss) + slot, 0, 4, h->stream));
   PTRY(gather(h, nullptr, first, n));
-  PTRY(forward(h, h->at<bf16>(h->L.x), n));
-  PTRY(backward(h, h->at<bf16>(h->L.x), n, slot));
+  PTRY(forward(h, h->at<bf16>(h->L.x), n, true));
+  PTRY(backward(h, n, slot));
   PCUDA(cudaMemcpyAsync(grad, h->at<float>(h->L.grad), (size_t)h->d.P * 4, cudaMemcpyDeviceToHost, h->stream));
   if (loss) PCUDA(cudaMemcpyAsync(loss, h->at<float>(h->L.loss) + slot, 4, cudaMemcpyDeviceToHost, h->stream));
   return read_status(h);
@@ -1340,8 +1781,8 @@ int sepso_prior_train(sepso_prior_handle h, int32_t n_rows, int32_t first, int32
       PCUDA(cudaGetLastError());
       PTRY(gather(h, h->at<int>(h->L.idx), 0, batch));
     }
-    PTRY(forward(h, h->at<bf16>(h->L.x), batch));
-    PTRY(backward(h, h->at<bf16>(h->L.x), batch, slot));
+    PTRY(forward(h, h->at<bf16>(h->L.x), batch, true));
+    PTRY(backward(h, batch, slot));
     PTRY(adam_step(h));
   }
   if (losses && steps > 0) {
@@ -1358,7 +1799,7 @@ int sepso_prior_infer(sepso_prior_handle h, int32_t first, int32_t n, float* d_o
   if (ld < d.O) return pfail(SEPSO_EINVAL, "ld %d below 2T = %d", ld, d.O);
   for (int s0 = 0; s0 < n; s0 += d.B) {
     const int m = std::min(d.B, n - s0);
-    PTRY(forward(h, h->at<bf16>(h->L.X) + (long long)(first + s0) * d.K, m));
+    PTRY(forward(h, h->at<bf16>(h->L.X) + (long long)(first + s0) * d.Kp, m, false));
     const int tot = m * d.O;
     sepso::decode_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(h->at<float>(h->L.y), m, h->c.T,
                                                                     h->at<float>(h->L.P) + 4LL * (first + s0),
@@ -1405,6 +1846,51 @@ int sepso_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t 
   PCUDA(cudaGetSymbolAddress(&st, g_gemm_status));
   g.status = static_cast<int*>(st);
   return gemm_launch(g, static_cast<cudaStream_t>(stream), tile_n);
+}
+
+int sepso_gemm_bf16_ex_workspace(int32_t M, int32_t N, int32_t ksplit, int32_t colsum, size_t* bytes) {
+  if (!bytes || M < 1 || N < 1 || ksplit < 0) return pfail(SEPSO_EINVAL, "bad workspace query");
+  *bytes = gemm_ws_bytes(M, N, std::max(ksplit, 1), colsum != 0);
+  return SEPSO_OK;
+}
+
+int sepso_gemm_bf16_ex(const void* A, const void* B, int32_t M, int32_t N, int32_t K, int32_t lda, int32_t ldb,
+                       float alpha, const float* bias, int32_t relu, const void* mask, int32_t ldm, float* Cf,
+                       int32_t ldcf, void* Cb, int32_t ldcb, const sepso_gemm_extra* extra, int32_t tile_n,
+                       void* stream) {
+  GemmArgs g{};
+  g.A = static_cast<const bf16*>(A);
+  g.B = static_cast<const bf16*>(B);
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.lda = lda;
+  g.ldb = ldb;
+  g.alpha = alpha;
+  g.bias = bias;
+  g.relu = relu;
+  g.mask = static_cast<const bf16*>(mask);
+  g.ldm = ldm;
+  g.Cf = Cf;
+  g.ldcf = ldcf;
+  g.Cb = static_cast<bf16*>(Cb);
+  g.ldcb = ldcb;
+  GemmExtra e;
+  if (extra) {
+    e.CbT = static_cast<bf16*>(extra->Ct);
+    e.ldct = extra->ldct;
+    e.colsum = extra->colsum;
+    e.ksplit = std::max(extra->ksplit, 1);
+    e.ws = static_cast<float*>(extra->workspace);
+    e.ws_bytes = extra->workspace_bytes;
+  }
+  if (extra && extra->ksplit < 0) return pfail(SEPSO_EINVAL, "gemm: K split %d", extra->ksplit);
+  PTRY(gemm_run_check(g, e, tile_n));  // before any CUDA call
+  void* st = nullptr;
+  PCUDA(cudaGetSymbolAddress(&st, g_gemm_status));
+  g.status = static_cast<int*>(st);
+  int n = 0;
+  return gemm_run(g, e, static_cast<cudaStream_t>(stream), tile_n, &n);
 }
 
 int sepso_gemm_bf16_sync(void* stream) {

@@ -140,27 +140,45 @@ class Prior:
 
 def gemm_bf16(A: torch.Tensor, B: torch.Tensor, alpha: float = 1.0, bias: torch.Tensor | None = None,
               relu: bool = False, mask: torch.Tensor | None = None, out_f32: bool = True,
-              out_bf16: bool = False, sync: bool = True, tile_n: int = 0):
+              out_bf16: bool = False, sync: bool = True, tile_n: int = 0, out_t: bool = False,
+              colsum: bool = False, ksplit: int = 1):
     """C = epilogue(alpha * A @ B^T) on the tensor cores; A (M, K), B (N, K) BF16 CUDA.
     tile_n: 0 automatic; 64 / 128 / 256 the persistent kernel; negative, the
-    one-tile-per-CTA kernel with that width."""
+    one-tile-per-CTA kernel with that width.  out_t: also a BF16 (N, M) copy of
+    the output transposed; colsum: also the N column sums of the output; ksplit:
+    K in that many slices (FP32 products summed in slice order).  Returns
+    (Cf, Cb), or (Cf, Cb, Ct, colsum) when out_t, colsum or ksplit is asked for."""
     assert A.is_cuda and B.is_cuda and A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16
     assert A.stride(1) == 1 and B.stride(1) == 1 and A.shape[1] == B.shape[1]
     M, K = A.shape
     N = B.shape[0]
-    Cf = torch.empty((M, N), dtype=torch.float32, device=A.device) if out_f32 else None
-    Cb = torch.empty((M, N), dtype=torch.bfloat16, device=A.device) if out_bf16 else None
+    dev = A.device
+    Cf = torch.empty((M, N), dtype=torch.float32, device=dev) if out_f32 else None
+    Cb = torch.empty((M, N), dtype=torch.bfloat16, device=dev) if out_bf16 else None
     vp = ctypes.c_void_p
-    stream = torch.cuda.current_stream(A.device).cuda_stream
-    check_prior(_native.lib().sepso_gemm_bf16(
-        vp(A.data_ptr()), vp(B.data_ptr()), M, N, K, A.stride(0), B.stride(0), float(alpha),
-        vp(bias.data_ptr()) if bias is not None else None, int(relu),
-        vp(mask.data_ptr()) if mask is not None else None, mask.stride(0) if mask is not None else 0,
-        vp(Cf.data_ptr()) if Cf is not None else None, N, vp(Cb.data_ptr()) if Cb is not None else None, N,
-        int(tile_n), vp(stream)))
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    L = _native.lib()
+    args = [vp(A.data_ptr()), vp(B.data_ptr()), M, N, K, A.stride(0), B.stride(0), float(alpha),
+            vp(bias.data_ptr()) if bias is not None else None, int(relu),
+            vp(mask.data_ptr()) if mask is not None else None, mask.stride(0) if mask is not None else 0,
+            vp(Cf.data_ptr()) if Cf is not None else None, N, vp(Cb.data_ptr()) if Cb is not None else None, N]
+    extended = out_t or colsum or ksplit != 1
+    Ct = cs = None
+    if not extended:
+        check_prior(L.sepso_gemm_bf16(*args, int(tile_n), vp(stream)))
+    else:
+        Ct = torch.empty((N, M), dtype=torch.bfloat16, device=dev) if out_t else None
+        cs = torch.empty(N, dtype=torch.float32, device=dev) if colsum else None
+        size = ctypes.c_size_t()
+        check_prior(L.sepso_gemm_bf16_ex_workspace(M, N, int(ksplit), int(colsum), ctypes.byref(size)))
+        ws = torch.empty(max(size.value, 16), dtype=torch.uint8, device=dev)
+        ex = _native.GemmExtra(Ct=Ct.data_ptr() if Ct is not None else None, ldct=M,
+                               colsum=cs.data_ptr() if cs is not None else None, ksplit=int(ksplit),
+                               workspace=ws.data_ptr(), workspace_bytes=ws.numel())
+        check_prior(L.sepso_gemm_bf16_ex(*args, ctypes.byref(ex), int(tile_n), vp(stream)))
     if sync:
-        check_prior(_native.lib().sepso_gemm_bf16_sync(vp(stream)))
-    return Cf, Cb
+        check_prior(L.sepso_gemm_bf16_sync(vp(stream)))
+    return (Cf, Cb, Ct, cs) if extended else (Cf, Cb)
 
 
 # ----------------------------------------------------------------------------

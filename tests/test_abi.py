@@ -141,3 +141,28 @@ def test_gemm_rejects_bad_shapes_before_any_launch():
     assert L.sepso_gemm_bf16(None, None, 8, 8, 12, 16, 16, 1.0, None, 0, None, 0, None, 8, None, 8, 0, None) == -1
     assert L.sepso_gemm_bf16(None, None, 8, 8, 16, 16, 16, 1.0, None, 0, None, 0, None, 8, None, 8, 0, None) == -1
     assert L.sepso_prior_last_error()
+
+
+def test_gemm_extra_workspace_and_argument_checks():
+    L = _native.lib()
+    size = ctypes.c_size_t()
+    assert L.sepso_gemm_bf16_ex_workspace(100, 64, 4, 0, ctypes.byref(size)) == 0 and size.value == 4 * 100 * 64 * 4
+    assert L.sepso_gemm_bf16_ex_workspace(100, 64, 1, 1, ctypes.byref(size)) == 0 and size.value == 4 * 64 * 4
+    assert L.sepso_gemm_bf16_ex_workspace(100, 64, 0, 0, ctypes.byref(size)) == 0 and size.value == 0
+    assert L.sepso_gemm_bf16_ex_workspace(0, 64, 1, 0, ctypes.byref(size)) == -1
+    # aligned stand-in device addresses: every check below runs before any CUDA call
+    A, B, C = ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20)
+    ws = ctypes.c_void_p(4 << 20)
+
+    def ex(**kw):
+        e = _native.GemmExtra(**kw)
+        return L.sepso_gemm_bf16_ex(A, B, 100, 64, 32, 32, 32, 1.0, None, 0, None, 0, C, 64, None, 64,
+                                    ctypes.byref(e), 0, None)
+
+    assert ex(Ct=C, ldct=99) == -1                                    # transposed row stride below M
+    assert ex(ksplit=2, colsum=C, workspace=ws, workspace_bytes=1 << 20) == -1  # split with colsum
+    assert ex(ksplit=2, Ct=C, ldct=100, workspace=ws, workspace_bytes=1 << 20) == -1
+    assert ex(ksplit=-1) == -1
+    assert ex(ksplit=4, workspace=ws, workspace_bytes=4 * 100 * 64 * 4 - 1) == -3   # workspace too small
+    assert ex(colsum=C, workspace=None, workspace_bytes=0) == -3
+    assert ex(colsum=C, workspace=ctypes.c_void_p((4 << 20) + 8), workspace_bytes=1 << 20) == -3  # misaligned

@@ -77,6 +77,52 @@ def test_gemm_epilogue_bias_relu_mask_bf16(native):
     assert torch.equal(Cb.cpu(), Cf.cpu().to(torch.bfloat16))
 
 
+@pytest.mark.parametrize("tile_n", [0, 64, 128, 256, -64, -128, -256])
+@pytest.mark.parametrize("M,N,K", [(300, 260, 136), (4096, 512, 40), (77, 1000, 512)])
+def test_gemm_transposed_output_and_column_sums(native, tile_n, M, N, K):
+    # the backward pass's masked products: the BF16 output transposed and the
+    # column sums of the output, from both kernels' epilogues (ragged M and N,
+    # rows beyond M excluded from the sums, several 32-row slabs per tile)
+    g = torch.Generator().manual_seed(M + N + K + tile_n)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    bias = torch.randn(N, generator=g)
+    mask = (torch.rand(M, N, generator=g) > 0.5).to(torch.bfloat16)
+    pre = 0.5 * (A.double() @ B.double().T) + bias.double()
+    ref = torch.where(mask.double() > 0, torch.clamp(pre, min=0), torch.zeros_like(pre))
+    Cf, Cb, Ct, cs = gemm_bf16(A.cuda(), B.cuda(), alpha=0.5, bias=bias.cuda(), relu=True, mask=mask.cuda(),
+                               out_bf16=True, out_t=True, colsum=True, tile_n=tile_n)
+    assert torch.max(torch.abs(Cf.cpu().double() - ref)).item() <= 1e-4 * np.sqrt(K)
+    # the transposed copy holds exactly the BF16 output's values
+    assert torch.equal(Ct.cpu(), Cb.cpu().T)
+    # column sums of the FP32 output (32-row slabs in order, then the slabs): at most
+    # 32 + ceil(M / 32) FP32 additions per sum of non-negative terms (ReLU), so the
+    # error is below (32 + 128) * 2^-24 * sum < 1e-5 * sum
+    want = Cf.cpu().double().sum(0)
+    assert torch.allclose(cs.cpu().double(), want, rtol=2e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("M,N,K,ksplit,tile_n", [(40, 512, 4096, 16, -64), (512, 1024, 4096, 4, -128),
+                                                 (130, 70, 1000, 5, 0), (200, 300, 64, 3, -256)])
+def test_gemm_split_k_matches_reference(native, M, N, K, ksplit, tile_n):
+    # K in slices (the last one ragged; more slices asked than K has blocks), the
+    # FP32 products summed in slice order before the epilogue
+    g = torch.Generator().manual_seed(K + ksplit)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    bias = torch.randn(N, generator=g)
+    mask = (torch.rand(M, N, generator=g) > 0.3).to(torch.bfloat16)
+    pre = 2.0 * (A.double() @ B.double().T) + bias.double()
+    ref = torch.where(mask.double() > 0, torch.clamp(pre, min=0), torch.zeros_like(pre))
+    Cf, Cb, _, _ = gemm_bf16(A.cuda(), B.cuda(), alpha=2.0, bias=bias.cuda(), relu=True, mask=mask.cuda(),
+                             out_bf16=True, ksplit=ksplit, tile_n=tile_n)
+    assert torch.max(torch.abs(Cf.cpu().double() - ref)).item() <= 2e-4 * np.sqrt(K)
+    assert torch.equal(Cb.cpu(), Cf.cpu().to(torch.bfloat16))
+    one, _ = gemm_bf16(A.cuda(), B.cuda(), alpha=2.0, bias=bias.cuda(), relu=True, mask=mask.cuda(),
+                       tile_n=tile_n)
+    assert torch.max(torch.abs(Cf.cpu() - one.cpu())).item() <= 2e-4 * np.sqrt(K)
+
+
 def _scenes(seed, n):
     sc = prior_scenes(seed, n)
     return sc, [sc["circles"][i] for i in range(n)]
