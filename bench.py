@@ -50,7 +50,7 @@ L2_FLUSH_BYTES = 256 << 20
 SWARM_TRAFFIC_BYTES = 154880
 # The same for gemm_tc_kernel on the MLP's grad-W1 product (1024 x 4104 x 4096),
 # profiles/gemm_tc_kernel_mlp_gradW1.md.
-GEMM_GRADW1_TRAFFIC_BYTES = 42225920
+GEMM_GRADW1_TRAFFIC_BYTES = 42132480
 
 
 def parse():
@@ -589,18 +589,23 @@ def _bf16_peak() -> float:
 def run_gemm(B: int = 4096, H1: int = 1024, K: int = 4104, reps: int = 20):
     """The tensor-core GEMM alone on the two largest products of a training step
     (grad W1 first, then forward layer 1), each launch timed with CUDA events after
-    an L2 flush."""
+    an L2 flush.  Operand rows have the training step's pitch (the feature rows and
+    W1 are stored at a multiple of 64 elements, 128-byte rows)."""
     import torch
 
     from paper_2308_10169_gb300.prior import gemm_bf16
     gem = {}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     for name, (M, N, Kd) in {"grad_W1": (H1, K, B), "forward_layer1": (B, H1, K)}.items():
-        A = torch.randn(M, Kd, device="cuda").to(torch.bfloat16)
-        Bm = torch.randn(N, Kd, device="cuda").to(torch.bfloat16)
-        for _ in range(3):
-            gemm_bf16(A, Bm, sync=False)
-        torch.cuda.synchronize()
+        pitch = (Kd + 63) // 64 * 64
+        A = torch.randn(M, pitch, device="cuda").to(torch.bfloat16)[:, :Kd]
+        Bm = torch.randn(N, pitch, device="cuda").to(torch.bfloat16)[:, :Kd]
+        # warm-up long enough for the clocks to leave their idle state
+        t_end = time.perf_counter() + 0.3
+        while time.perf_counter() < t_end:
+            for _ in range(20):
+                gemm_bf16(A, Bm, sync=False)
+            torch.cuda.synchronize()
         ts = []
         for _ in range(reps):
             flush.zero_()

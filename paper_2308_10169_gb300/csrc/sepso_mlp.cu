@@ -1135,19 +1135,19 @@ int gemm_launch_persistent(const CUtensorMap& ta, const GemmArgs& g, cudaStream_
 }
 
 // Kernel and tile width for a product (positive: persistent; negative: one tile
-// per CTA), from sweeps of both kernels on GB300:
-//   many tiles (>= 2 per SM at width 256; 4096^3: 975 / 941 TFLOP/s) -> persistent, 256
-//   about one wave of 256-wide tiles (1024 x 4104 x 1024: 316 / 364)  -> one per CTA, 256
-//   few tiles and a long K (1024 x 1024 x 4104, width 64: 237 / 262) -> one per CTA, 64
-//   few tiles and a short K, with the eight-warp epilogue (4096 x 512 x 1024:
-//   persistent 64 22.8 us, one per CTA 128 16.6 us; 4096 x 512 x 40 with mask,
-//   transposed copy and column sums: 31.1 / 18.7 us)                  -> one per CTA, 128
-//   (64 when N <= 64: 4096 x 40 x 512, 11.0 / 8.7 us)
+// per CTA), from a sweep of both kernels on GB300 with the eight-warp epilogue
+// (TFLOP/s, best persistent / best one per CTA):
+//   8192^3 1230 / 1352, 4096^3 954 / 1051, 1024 x 4104 x 4096 639 / 849,
+//   4096 x 1024 x 4104 610 / 817 (three quarters of a wave or more of 256-wide
+//   tiles)                                                   -> one per CTA, 256
+//   4096 x 512 x 1024 194 / 252, 4096 x 1024 x 512 170 / 225; with mask,
+//   transposed copy and column sums 4096 x 512 x 40: 31.1 / 18.7 us -> one per CTA, 128
+//   long K and few tiles (1024 x 1024 x 4104 at width 64: 237 / 262), or N <= 64
+//   (4096 x 40 x 512: 11.0 / 8.7 us)                         -> one per CTA, 64
 int choose_tile_n_auto(int M, int N, int K) {
   choose_tile_n(M, N);  // fills the SM count
   const long long mt = (M + sepso::kBM - 1) / sepso::kBM;
   const long long t256 = mt * ((N + 255) / 256);
-  if (t256 >= 2LL * g_num_sms) return 256;
   if (4 * t256 >= 3LL * g_num_sms) return -256;
   return (K >= 2048 || N <= 64) ? -64 : -128;
 }
