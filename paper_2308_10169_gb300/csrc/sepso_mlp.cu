@@ -1435,7 +1435,7 @@ int gemm_run(GemmArgs g, const GemmExtra& e, cudaStream_t s, int tile_n, int* la
 
 struct PriorLayout {
   size_t prm, m, v, grad, wb, w1p, w2t, w3t, X, Y, P, scirc, scoff, spts, swp, idx, x, xT, h1, h1T, h2, h2T, y, t, dyf,
-      dyb, dyT, dh2b, dh2T, dh1T, kpart, cpart, loss, status, total;
+      dyb, dyT, dh2b, dh2T, dh1T, kpart, cpart, cpart2, loss, status, total;
 };
 
 struct Dims {
@@ -1511,6 +1511,7 @@ PriorLayout layout(const sepso_prior_config* c, const Dims& d) {
   L.dh1T = take(H1 * B * 2);
   L.kpart = take((size_t)kMaxSlices * std::max(O * H2, H2 * H1) * 4);  // K-split partial products
   L.cpart = take((B + 31) / 32 * std::max(std::max(H1, H2), O) * 4);    // column sums per 32-row slab
+  L.cpart2 = take((B + 31) / 32 * O * 4);                                // the same for dY, on the side stream
   L.loss = take((size_t)kLossRing * 4);
   L.status = take(4);
   L.total = al256(off);
@@ -1524,6 +1525,16 @@ struct sepso_prior_ctx {
   Dims d{};
   PriorLayout L{};
   cudaStream_t stream = nullptr;
+  // The backward pass forks the weight gradients that do not feed the next
+  // product onto a second stream and joins it before Adam.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_dy = nullptr, ev_dh2 = nullptr, ev_join = nullptr;
+  ~sepso_prior_ctx() {
+    if (ev_dy) cudaEventDestroy(ev_dy);
+    if (ev_dh2) cudaEventDestroy(ev_dh2);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
+  }
   char* ws = nullptr;
   int64_t step = 0;      // Adam steps taken
   int64_t launches = 0;
@@ -1541,7 +1552,7 @@ namespace {
 
 int gemm(sepso_prior_ctx* h, const bf16* A, const bf16* B, int M, int N, int K, int lda, int ldb, const float* bias,
          int relu, const bf16* mask, int ldm, float* Cf, int ldcf, bf16* Cb, int ldcb,
-         const GemmExtra& e = GemmExtra(), int tile_n = 0) {
+         const GemmExtra& e = GemmExtra(), int tile_n = 0, cudaStream_t st = nullptr) {
   GemmArgs g{};
   g.A = A;
   g.B = B;
@@ -1561,18 +1572,18 @@ int gemm(sepso_prior_ctx* h, const bf16* A, const bf16* B, int M, int N, int K, 
   g.ldcb = ldcb;
   g.status = h->at<int>(h->L.status);
   int n = 0;
-  const int r = gemm_run(g, e, h->stream, tile_n, &n);
+  const int r = gemm_run(g, e, st ? st : h->stream, tile_n, &n);
   h->launches += n;
   return r;
 }
 
-// db[j] = sum over the B rows of D[.][j]: sums over 32-row blocks, then over the blocks.
-int colsum(sepso_prior_ctx* h, const float* D, int B, int N, int ld, float* db) {
-  float* part = h->at<float>(h->L.cpart);
+// db[j] = sum over the B rows of D[.][j]: sums over 32-row blocks (into part), then
+// over the blocks.
+int colsum(sepso_prior_ctx* h, const float* D, int B, int N, int ld, float* db, float* part, cudaStream_t st) {
   const int nb = (B + 31) / 32;
-  sepso::colsum_part_kernel<<<dim3((N + 31) / 32, nb), dim3(32, 8), 0, h->stream>>>(D, B, N, ld, part);
+  sepso::colsum_part_kernel<<<dim3((N + 31) / 32, nb), dim3(32, 8), 0, st>>>(D, B, N, ld, part);
   PCUDA(cudaGetLastError());
-  sepso::colsum_kernel<<<(N + 31) / 32, dim3(32, 8), 0, h->stream>>>(part, nb, N, N, db);
+  sepso::colsum_kernel<<<(N + 31) / 32, dim3(32, 8), 0, st>>>(part, nb, N, N, db);
   h->launches += 2;
   PCUDA(cudaGetLastError());
   return SEPSO_OK;
@@ -1626,23 +1637,37 @@ int backward(sepso_prior_ctx* h, int n, int slot) {
   mk.ws = h->at<float>(h->L.cpart);
   mk.ws_bytes = (size_t)((d.B + 31) / 32) * std::max(std::max(d.H1, d.H2), d.O) * 4;
   mk.ldct = n;
-  // layer 3: gb3 = colsum dY, gW3 = dY^T h2, dh2 = (dY W3) * [h2 > 0] (+ dh2T, gb2 = colsum dh2)
-  PTRY(colsum(h, dyf, n, d.O, d.O, grad + d.off[5]));
+  // The side stream takes gb3, gW3 (after dY) and gW2 (after dh2): products no
+  // later product reads; the main stream carries dh2 -> dh1 -> gW1.  The side
+  // stream has its own column-sum scratch; both split-K products are on it.
+  cudaStream_t side = h->side;
+  PCUDA(cudaEventRecord(h->ev_dy, h->stream));
+  PCUDA(cudaStreamWaitEvent(side, h->ev_dy, 0));
+  // layer 3: gb3 = colsum dY, gW3 = dY^T h2 (side); dh2 = (dY W3) * [h2 > 0] (+ dh2T,
+  // gb2 = colsum dh2) (main)
+  PTRY(colsum(h, dyf, n, d.O, d.O, grad + d.off[5], h->at<float>(h->L.cpart2), side));
   kw.ksplit = auto_ksplit(d.O, d.H2, n, 64);
-  PTRY(gemm(h, dyT, h2T, d.O, d.H2, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[4], d.H2, nullptr, 0, kw, -64));
+  PTRY(gemm(h, dyT, h2T, d.O, d.H2, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[4], d.H2, nullptr, 0, kw, -64,
+            side));
   mk.CbT = dh2T;
   mk.colsum = grad + d.off[3];
   PTRY(gemm(h, dyb, h->at<bf16>(h->L.w3t), n, d.H2, d.O8, d.O8, d.O8, nullptr, 0, h2, d.H2, nullptr, 0, dh2b, d.H2,
             mk));
-  // layer 2: gW2 = dh2^T h1, dh1 = (dh2 W2) * [h1 > 0] (only dh1T, gb1 = colsum dh1)
+  PCUDA(cudaEventRecord(h->ev_dh2, h->stream));
+  PCUDA(cudaStreamWaitEvent(side, h->ev_dh2, 0));
+  // layer 2: gW2 = dh2^T h1 (side); dh1 = (dh2 W2) * [h1 > 0] (only dh1T, gb1 =
+  // colsum dh1) (main)
   kw.ksplit = auto_ksplit(d.H2, d.H1, n, 128);
-  PTRY(gemm(h, dh2T, h1T, d.H2, d.H1, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[2], d.H1, nullptr, 0, kw, -128));
+  PTRY(gemm(h, dh2T, h1T, d.H2, d.H1, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[2], d.H1, nullptr, 0, kw, -128,
+            side));
   mk.CbT = dh1T;
   mk.colsum = grad + d.off[1];
   PTRY(gemm(h, dh2b, h->at<bf16>(h->L.w2t), n, d.H1, d.H2, d.H2, d.H2, nullptr, 0, h1, d.H1, nullptr, 0, nullptr, 0,
             mk));
-  // layer 1: gW1 = dh1^T x
+  // layer 1: gW1 = dh1^T x (main), then join the side stream
   PTRY(gemm(h, dh1T, xT, d.H1, d.K, n, n, n, nullptr, 0, nullptr, 0, grad + d.off[0], d.K, nullptr, 0));
+  PCUDA(cudaEventRecord(h->ev_join, side));
+  PCUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   return SEPSO_OK;
 }
 
@@ -1666,10 +1691,10 @@ sepso::BfMirrors mirrors(sepso_prior_ctx* h) {
 }
 
 // Training rows: x (n x K), its transpose xT (K x n) and the targets t.
-int gather(sepso_prior_ctx* h, const int* idx, int first, int n) {
+int gather(sepso_prior_ctx* h, const int* idx, int first, int n, cudaStream_t st = nullptr) {
   const Dims& d = h->d;
   const dim3 grid((d.K + 127) / 128, (n + 63) / 64);
-  sepso::gather_t_kernel<<<grid, 256, 0, h->stream>>>(idx, first, n, d.K, d.Kp, h->at<bf16>(h->L.X), h->at<float>(h->L.Y),
+  sepso::gather_t_kernel<<<grid, 256, 0, st ? st : h->stream>>>(idx, first, n, d.K, d.Kp, h->at<bf16>(h->L.X), h->at<float>(h->L.Y),
                                                       d.O, h->at<bf16>(h->L.x), h->at<bf16>(h->L.xT),
                                                       h->at<float>(h->L.t));
   ++h->launches;
@@ -1750,7 +1775,11 @@ int sepso_prior_create(const sepso_prior_config* cfg, void* d_workspace, size_t 
   h->L = L;
   h->ws = static_cast<char*>(d_workspace);
   h->stream = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);
+  cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_dy, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_dh2, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws, 0, L.total, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     delete h;
@@ -1926,23 +1955,34 @@ int sepso_prior_train(sepso_prior_handle h, int32_t n_rows, int32_t first, int32
     return pfail(SEPSO_EINVAL, "n_rows %d outside [1, %d]", n_rows, h->c.capacity);
   }
   const int slot0 = h->loss_head;
+  // A step's minibatch (row indices drawn with the Adam step count as the counter)
+  // gathered on stream st.
+  auto stage_rows = [&](cudaStream_t st, int64_t counter) -> int {
+    if (first >= 0) return gather(h, nullptr, first, batch, st);
+    sepso::sample_kernel<<<(batch + 255) / 256, 256, 0, st>>>(h->at<int>(h->L.idx), batch, n_rows, (uint32_t)seed,
+                                                              (uint32_t)(seed >> 32), (uint32_t)counter);
+    ++h->launches;
+    PCUDA(cudaGetLastError());
+    return gather(h, h->at<int>(h->L.idx), 0, batch, st);
+  };
+  if (steps > 0) PTRY(stage_rows(h->stream, h->step));
   for (int s = 0; s < steps; ++s) {
     const int slot = h->loss_head;
     h->loss_head = (h->loss_head + 1) % kLossRing;
     PCUDA(cudaMemsetAsync(h->at<float>(h->L.loss) + slot, 0, 4, h->stream));
-    if (first >= 0) {
-      PTRY(gather(h, nullptr, first, batch));
-    } else {
-      sepso::sample_kernel<<<(batch + 255) / 256, 256, 0, h->stream>>>(h->at<int>(h->L.idx), batch, n_rows,
-                                                                        (uint32_t)seed, (uint32_t)(seed >> 32),
-                                                                        (uint32_t)h->step);
-      ++h->launches;
-      PCUDA(cudaGetLastError());
-      PTRY(gather(h, h->at<int>(h->L.idx), 0, batch));
-    }
     PTRY(forward(h, h->at<bf16>(h->L.x), batch, true));
     PTRY(backward(h, batch, slot));
+    // The next minibatch is gathered on the side stream while Adam runs: both
+    // stream through memory, and the rows are free once the backward pass is done.
+    const bool more = s + 1 < steps;
+    if (more) {
+      PCUDA(cudaEventRecord(h->ev_dy, h->stream));
+      PCUDA(cudaStreamWaitEvent(h->side, h->ev_dy, 0));
+      PTRY(stage_rows(h->side, h->step + 1));
+      PCUDA(cudaEventRecord(h->ev_join, h->side));
+    }
     PTRY(adam_step(h));
+    if (more) PCUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   }
   if (losses && steps > 0) {
     h->pending.push_back({losses, steps, slot0});
