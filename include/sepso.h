@@ -462,7 +462,11 @@ int sepso_prior_workspace_size(const sepso_prior_config* cfg, size_t* bytes);
 
 /* Lay out the prior in the caller's workspace (device, 256-byte aligned, owned by
  * the caller, at least sepso_prior_workspace_size bytes) on the caller's stream
- * (cudaStream_t).  Parameters start at zero.  Errors: EINVAL, ENOSPC, ECUDA, ENOMEM. */
+ * (cudaStream_t).  Parameters start at zero.  The handle also owns a second,
+ * non-blocking stream and three events (created here, destroyed by
+ * sepso_prior_destroy): training forks work onto that stream from the caller's
+ * stream and joins it back before each call's work ends on the caller's stream,
+ * so the caller sees one ordered stream.  Errors: EINVAL, ENOSPC, ECUDA, ENOMEM. */
 int sepso_prior_create(const sepso_prior_config* cfg, void* d_workspace, size_t bytes, void* stream,
                        sepso_prior_handle* out);
 void sepso_prior_destroy(sepso_prior_handle h);
