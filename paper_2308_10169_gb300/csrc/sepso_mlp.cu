@@ -6,12 +6,13 @@
 //                      producer lane fills a ring of 128-byte-swizzled operand
 //                      stages, an MMA lane issues tcgen05.mma (kind::f16, BF16
 //                      inputs, FP32 accumulator in tensor memory) and frees each
-//                      stage with tcgen05.commit, and the four warps read the
+//                      stage with tcgen05.commit, and eight warps read the
 //                      accumulator back with tcgen05.ld for a fused epilogue
 //                      (scale, bias, ReLU, the backward pass's ReLU mask, FP32
 //                      and/or BF16 output, a transposed BF16 copy, column
 //                      sums; K split into slices summed in order).  Tile N
-//                      (64 / 128 / 256) per launch.
+//                      (64 / 128 / 256) per launch; a persistent form and a
+//                      CTA-pair form (B box shared by TMA multicast).
 //   raster_kernel      occupancy raster of the circles (cell centre inside a disk).
 //   small kernels      row gather with a transposed copy, column sums (bias
 //                      gradients), MSE loss gradient, split-K sums, Adam with the
