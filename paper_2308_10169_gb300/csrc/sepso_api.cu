@@ -46,7 +46,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // Byte offsets of every array in the caller's workspace.
 struct WsLayout {
-  size_t circ, cvel, pts, hyper, X, V, P, Pfit, PQ, Gb, Gfit, GQ, Tb, prevT, res_wp, ctl, res, win,
+  size_t circ, pairs, cvel, pts, hyper, X, V, P, Pfit, PQ, Gb, Gfit, GQ, Tb, prevT, res_wp, ctl, res, win,
       gword, counter, crows, hhyper, HX, HV, HP, HPfit, HGb, HGfit, HTb, HTfit, estatus, total;
 };
 
@@ -63,6 +63,7 @@ WsLayout make_ws(const sepso_config& c) {
     return o;
   };
   L.circ = take(Omax * 16);
+  L.pairs = take((size_t)pair_block_f4(std::max((int)Omax, 1)) * 16);
   L.cvel = take(Omax * 8);
   L.pts = take(8 * 4);
   L.hyper = take(R * G * 6 * 4);
@@ -194,6 +195,7 @@ SwarmParams swarm_params(const sepso_ctx* h, int mode, int step_iters) {
   p.mode = mode;
   p.step_iters = step_iters;
   p.circ = h->at<float4>(h->L.circ);
+  p.pairs = h->at<float4>(h->L.pairs);
   p.pts = h->at<float>(h->L.pts);
   p.hyper = h->at<float>(h->L.hyper);
   p.X = h->at<float>(h->L.X);
@@ -474,6 +476,8 @@ int sepso_set_scene(sepso_handle h, const float* start, const float* target, con
   if (O > 0) {
     CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.circ, c4, (size_t)O * 16, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(cudaMemsetAsync(h->ws + h->L.cvel, 0, (size_t)O * 8, h->stream));
+    CUDA_TRY(launch_pairs(h->at<float4>(h->L.circ), O, h->at<float4>(h->L.pairs), h->stream));
+    h->launches += 1;
   }
   CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.pts, pts, 8 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(cudaEventRecord(h->staging_free, h->stream));
@@ -504,7 +508,8 @@ int sepso_advance_scene(sepso_handle h, int32_t steps) {
   if (!h->has_scene) return fail(SEPSO_ESTATE, "advance before set_scene");
   if (steps < 0) return fail(SEPSO_EINVAL, "steps < 0");
   if (steps == 0) return SEPSO_OK;
-  CUDA_TRY(launch_advance(h->at<float4>(h->L.circ), h->at<float2>(h->L.cvel), h->at<float>(h->L.pts), h->O,
+  CUDA_TRY(launch_advance(h->at<float4>(h->L.circ), h->at<float2>(h->L.cvel), h->at<float>(h->L.pts),
+                          h->at<float4>(h->L.pairs), h->O,
                           h->cfg.map_w, h->cfg.map_h, steps, h->stream));
   h->launches += 1;
   return SEPSO_OK;
@@ -967,6 +972,7 @@ extern "C" int sepso_plan_static(const sepso_config* cfg, const float* hyper, co
   }
   const float pts[8] = {start[0], start[1], target[0], target[1], 0.f, 0.f, 0.f, 0.f};
   CUDA_TRY(cudaMemcpyAsync(h.ws + L.pts, pts, sizeof pts, cudaMemcpyHostToDevice, h.stream));
+  CUDA_TRY(launch_pairs(h.at<float4>(L.circ), O, h.at<float4>(L.pairs), h.stream));
 
   const SwarmParams p = swarm_params(&h, kModePlan, 0);
   CUDA_TRY(launch_swarm(p, h.grid, h.threads, h.smem, h.stream));

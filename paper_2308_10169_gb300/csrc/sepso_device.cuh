@@ -90,6 +90,7 @@ struct SwarmParams {
   int mode, step_iters;
   // device pointers
   const float4* circ;         // Omax x (cx, cy, r, 4 r^2)
+  const float4* pairs;        // the same circles as pair blocks (pair_block_f4(O) float4)
   const float* pts;           // start xy, target xy, start vel, target vel
   const float* hyper;         // R x G x 6
   float *X, *V, *P, *Pfit;    // R x M x D (X, V, P), R x M
@@ -433,19 +434,6 @@ __device__ __forceinline__ void group_fitness_pairs(const float* x, bool live, i
   }
   *len_out = len;
   *q_out = hits;
-}
-
-// Pairs of a float4 circle list (cx, cy, r, .) into a pair block (cooperative,
-// all threads of the block; the caller synchronises before use).
-__device__ __forceinline__ void circles_to_pairs(const float4* circ, int O, float4* block) {
-  const int K = circle_pairs(O);
-  float2* nr2 = reinterpret_cast<float2*>(block + K);
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const float4 a = circ[2 * k];
-    const float4 b = (2 * k + 1 < O) ? circ[2 * k + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    block[k] = make_float4(a.x, b.x, a.y, b.y);
-    nr2[k] = make_float2(-(a.z * a.z), (2 * k + 1 < O) ? -(b.z * b.z) : 0.0f);
-  }
 }
 
 // Circle chunks per segment for a warp (32 lanes) evaluating one particle of T

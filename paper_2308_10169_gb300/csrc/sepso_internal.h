@@ -14,7 +14,7 @@ struct RunCtl;
 
 // Shared-memory carve of swarm_kernel (byte offsets); identical on host and device.
 struct SmemLayout {
-  int circ, pairs, win, X, V, P, R, Gown, Tb, Pfit, PQ, Q, Imp, Len, Gfit, GQ, Gsrc, total;
+  int pairs, win, X, V, P, R, Gown, Tb, Pfit, PQ, Q, Imp, Len, Gfit, GQ, Gsrc, total;
   __host__ __device__ static SmemLayout make(int Omax, int ppc, int D, int T, int G, int tw);
 };
 
@@ -48,8 +48,10 @@ cudaError_t configure_swarm_kernel(size_t smem_bytes);
 cudaError_t swarm_occupancy(int threads, size_t smem_bytes, int* blocks_per_sm);
 cudaError_t launch_swarm(const SwarmParams& p, int grid, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_evaluate(const EvalParams& p, cudaStream_t s);
-cudaError_t launch_advance(float4* circ, float2* cvel, float* pts, int O, float W, float H, int steps,
-                           cudaStream_t s);
+cudaError_t launch_advance(float4* circ, float2* cvel, float* pts, float4* pairs, int O, float W, float H,
+                           int steps, cudaStream_t s);
+// Circle-pair blocks of the scene's circles (after the circles change on the host side).
+cudaError_t launch_pairs(const float4* circ, int O, float4* pairs, cudaStream_t s);
 cudaError_t launch_hsef_init(const HsefParams& p, cudaStream_t s);
 cudaError_t launch_hsef_update(const HsefParams& p, int e, cudaStream_t s);
 cudaError_t launch_watchdog_selftest(const unsigned int* never, unsigned long long limit_ns, int* fired,

@@ -64,6 +64,48 @@ def test_fitness_matches_oracle(native, T, O, n):
     np.testing.assert_allclose(L, Lo, rtol=1e-5)
 
 
+def _near_tangent_pairs(scene, X, T, margin):
+    """Per path: the (segment, circle) pairs with | dist(centre, segment) - r | <=
+    margin, in FP64 (the pairs whose intersection an FP32 test may decide either way)."""
+    c = np.asarray(scene.circles, np.float64)
+    out = np.zeros(X.shape[0], np.int64)
+    for p in range(X.shape[0]):
+        xs = np.concatenate([[scene.start[0]], X[p, :T], [scene.target[0]]]).astype(np.float64)
+        ys = np.concatenate([[scene.start[1]], X[p, T:], [scene.target[1]]]).astype(np.float64)
+        ax, ay, bx, by = xs[:-1, None], ys[:-1, None], xs[1:, None], ys[1:, None]
+        dx, dy = bx - ax, by - ay
+        ll = np.maximum(dx * dx + dy * dy, 1e-300)
+        t = np.clip(((c[None, :, 0] - ax) * dx + (c[None, :, 1] - ay) * dy) / ll, 0.0, 1.0)
+        d = np.hypot(c[None, :, 0] - (ax + t * dx), c[None, :, 1] - (ay + t * dy))
+        out[p] = int(np.count_nonzero(np.abs(d - c[None, :, 2]) <= margin))
+    return out
+
+
+def test_fitness_at_maximum_sizes(native):
+    # T = 64 waypoints and the largest obstacle count (8192 circles): 532,480
+    # segment-circle tests per path, so nearly every random path has a few pairs
+    # within the tangency margin; the counts agree exactly on the others, and
+    # differ by at most the number of such pairs on the rest
+    T, O, n = 64, 8192, 24
+    rng = np.random.default_rng(64)
+    cfg = SepsoConfig(T=T, G=1, N=1, max_obstacles=O, alpha=30.0, beta=4)
+    scene = Scene(start=(20, 20), target=(380, 380), circles=random_circles(rng, O, r_lo=1, r_hi=4))
+    X = random_paths(99, n, T)
+    pl = make(cfg, scene, sample_hyper(0, 1))
+    F, Q, L = pl.evaluate(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    F, Q, L = F.cpu().numpy(), Q.cpu().numpy(), L.cpu().numpy()
+    Fo, Qo, Lo = oracle.evaluate(cfg, osc(scene), X)
+    near = _near_tangent_pairs(scene, X, T, TANGENCY)
+    assert np.all(np.abs(Q.astype(np.int64) - Qo.astype(np.int64)) <= near)
+    exact = near == 0
+    np.testing.assert_array_equal(Q[exact], Qo[exact])
+    same = Q == Qo
+    assert same.mean() > 0.5
+    np.testing.assert_allclose(F[same], Fo[same], rtol=1e-4)
+    np.testing.assert_allclose(L, Lo, rtol=1e-5)
+
+
 # ---------------------------------------------------------------------------
 # Initialisation and Priori Initialization
 # ---------------------------------------------------------------------------
