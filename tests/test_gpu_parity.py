@@ -106,6 +106,26 @@ def test_fitness_at_maximum_sizes(native):
     np.testing.assert_allclose(L, Lo, rtol=1e-5)
 
 
+def test_plan_at_maximum_sizes(native):
+    # the largest single-scene configuration: G = 32 groups, T = 64 waypoints, 8192
+    # circles (staged into shared memory as pair blocks); the returned path's cost is
+    # the oracle's fitness of that path (Q exact away from tangency)
+    T, G, N, O = 64, 32, 6, 8192
+    rng = np.random.default_rng(8192)
+    cfg = SepsoConfig(T=T, G=G, N=N, max_obstacles=O, alpha=30.0, beta=4, max_iters=3, seed=5)
+    scene = Scene(start=(20, 20), target=(380, 380), circles=random_circles(rng, O, r_lo=1, r_hi=4))
+    r = make(cfg, scene, sample_hyper(7, G)).plan()
+    wp = np.asarray(r["waypoints"], np.float32)[None, :]
+    Fo, Qo, Lo = oracle.evaluate(cfg, osc(scene), wp)
+    near = _near_tangent_pairs(scene, wp, T, TANGENCY)[0]
+    assert r["iters"] == 3
+    assert abs(int(r["Q"]) - int(Qo[0])) <= near
+    assert r["length"] == pytest.approx(float(Lo[0]), rel=1e-5)
+    if near == 0:
+        assert r["Q"] == Qo[0]
+        assert r["cost"] == pytest.approx(float(Fo[0]), rel=1e-4)
+
+
 # ---------------------------------------------------------------------------
 # Initialisation and Priori Initialization
 # ---------------------------------------------------------------------------
