@@ -23,9 +23,12 @@ What each function follows (paper: arXiv 2308.10169):
   learned prior (``prior_oracle.c``): occupancy raster features, label encoding,
   MLP forward, loss gradient and the Adam step (Kingma and Ba, 2015).
 
-Parity status of each function is recorded in the header of ``sepso_oracle.c``
-and in the tests that pin it (``tests/test_oracle_*.py``); HSEF's absolute values
-are "parity unpinned" (the paper gives only a figure), its invariants are pinned.
+Parity status of each function is recorded in the tests that pin it
+(``tests/test_oracle_*.py``).  HSEF is pinned by its invariants, by Eq. fit_h (the
+best H-fitness is the LFV of an L-run with the best hyper-parameters) and by its
+H-swarm update (inertia, the three attractors with their own rows and distinct
+factors, velocity and box clipping, through ``hsef_state``); the paper prints no
+HSEF values to compare with (only a figure).
 """
 from __future__ import annotations
 
@@ -133,6 +136,9 @@ def lib():
                                        _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
         L.so_hsef.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene),
                               ctypes.POINTER(_HsefCfg), _f64p, _f64p, _f64p]
+        L.so_hsef_state.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene),
+                                    ctypes.POINTER(_HsefCfg), _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                    _f64p, _f64p]
         L.so_mlp_num_params.argtypes = [ctypes.POINTER(_MlpDims)]
         L.so_mlp_num_params.restype = ctypes.c_long
         L.so_raster.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _f64p,
@@ -359,6 +365,31 @@ def hsef(lcfg, scene: Scene, HG: int, HN: int, E: int, hhyper, lo, hi, l_vlimit:
     lib().so_hsef(ctypes.byref(c), ctypes.byref(s), ctypes.byref(hc), _p64(best), _p64(bf),
                   _p64(hist))
     return best, float(bf[0]), hist
+
+
+def hsef_state(lcfg, scene: Scene, HG: int, HN: int, E: int, hhyper, lo, hi, l_vlimit: float,
+               hseed: int) -> dict:
+    """hsef() and the H-swarm state after its last update: HX, HV, HP (HG*HN x 3G),
+    HGb (HG x 3G), HTb (3G), with best, bf and hist as hsef() returns them."""
+    G = lcfg.G
+    if G > 64:
+        raise ValueError("oracle HSEF supports G <= 64")
+    HM, DH = HG * HN, 3 * G
+    hh = np.ascontiguousarray(np.asarray(hhyper, np.float64).reshape(HG, 6))
+    hc = _HsefCfg(HG=HG, HN=HN, E=E, hhyper=_p64(hh),
+                  lo=(ctypes.c_double * 3)(*[float(np.float32(x)) for x in lo]),
+                  hi=(ctypes.c_double * 3)(*[float(np.float32(x)) for x in hi]),
+                  l_vlimit=float(np.float32(l_vlimit)), hseed=hseed)
+    out = {"best": np.zeros(DH), "bf": np.zeros(1), "hist": np.zeros(E), "HX": np.zeros((HM, DH)),
+           "HV": np.zeros((HM, DH)), "HP": np.zeros((HM, DH)), "HGb": np.zeros((HG, DH)),
+           "HTb": np.zeros(DH)}
+    c = _cfg(lcfg)
+    s = scene.c()
+    lib().so_hsef_state(ctypes.byref(c), ctypes.byref(s), ctypes.byref(hc), _p64(out["best"]),
+                        _p64(out["bf"]), _p64(out["hist"]), _p64(out["HX"]), _p64(out["HV"]),
+                        _p64(out["HP"]), _p64(out["HGb"]), _p64(out["HTb"]))
+    out["bf"] = float(out["bf"][0])
+    return out
 
 
 

@@ -491,8 +491,30 @@ typedef struct {
   uint64_t hseed;          /* Philox key of the H-swarm                       */
 } so_hsef_cfg;
 
+/* The final H-swarm state (after the last H update), for the pins: HM x DH
+ * positions, velocities and personal bests, HG x DH group bests, DH global best;
+ * any pointer may be NULL. */
+typedef struct {
+  double *hx, *hv, *hp, *hgb, *htb;
+} so_hsef_out;
+
+static void hsef_run(const so_config* lcfg, const so_scene* sc, const so_hsef_cfg* hc, double* best_pos,
+                     double* best_fit, double* history, const so_hsef_out* out);
+
 void so_hsef(const so_config* lcfg, const so_scene* sc, const so_hsef_cfg* hc, double* best_pos,
              double* best_fit, double* history) {
+  hsef_run(lcfg, sc, hc, best_pos, best_fit, history, NULL);
+}
+
+void so_hsef_state(const so_config* lcfg, const so_scene* sc, const so_hsef_cfg* hc, double* best_pos,
+                   double* best_fit, double* history, double* hx, double* hv, double* hp, double* hgb,
+                   double* htb) {
+  const so_hsef_out out = {hx, hv, hp, hgb, htb};
+  hsef_run(lcfg, sc, hc, best_pos, best_fit, history, &out);
+}
+
+static void hsef_run(const so_config* lcfg, const so_scene* sc, const so_hsef_cfg* hc, double* best_pos,
+                     double* best_fit, double* history, const so_hsef_out* out) {
   const int32_t G = lcfg->G, DH = 3 * G, HM = hc->HG * hc->HN;
   const int32_t T = lcfg->T, D = 2 * T, M = lcfg->G * lcfg->N;
   double* HX = (double*)calloc((size_t)HM * DH, sizeof(double));
@@ -619,6 +641,13 @@ void so_hsef(const so_config* lcfg, const so_scene* sc, const so_hsef_cfg* hc, d
   }
   for (int32_t j = 0; j < DH; ++j) best_pos[j] = HTb[j];
   *best_fit = HTfit;
+  if (out) {
+    if (out->hx) memcpy(out->hx, HX, sizeof(double) * (size_t)HM * DH);
+    if (out->hv) memcpy(out->hv, HV, sizeof(double) * (size_t)HM * DH);
+    if (out->hp) memcpy(out->hp, HP, sizeof(double) * (size_t)HM * DH);
+    if (out->hgb) memcpy(out->hgb, HGb, sizeof(double) * (size_t)hc->HG * DH);
+    if (out->htb) memcpy(out->htb, HTb, sizeof(double) * (size_t)DH);
+  }
   free(HX); free(HV); free(HP); free(HPfit); free(HGb); free(HGfit); free(HF); free(lhyper);
   free(X); free(V); free(P); free(Pfit); free(PQ); free(Gb); free(Gfit); free(GQ); free(Tb);
   free(prevT); free(win); free(res);

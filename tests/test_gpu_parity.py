@@ -366,6 +366,14 @@ def test_hsef_first_evolution_matches_oracle(native):
     assert hist[0] == lfv
 
 
+def test_hsef_history_matches_oracle(native):
+    # three evolutions: the H-swarm updates in between (Eqs. TOF_omega, TOF_V, TOF_X in
+    # the hyper-parameter space) move the H-particles the same way on both sides, so
+    # the best LFV of every evolution agrees
+    lcfg, hist, best, lfv, ohist, olfv = _hsef_setup(3)
+    np.testing.assert_allclose(hist, ohist, rtol=1e-3)
+
+
 def test_hsef_invariants(native):
     lcfg, hist, best, lfv, ohist, olfv = _hsef_setup(6)
     assert np.all(np.diff(hist) <= 0)

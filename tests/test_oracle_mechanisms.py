@@ -271,3 +271,99 @@ def test_hsef_fitness_is_the_lfv_of_an_l_run():
     h[:, 3], h[:, 4], h[:, 5] = best[:G], best[:G], float(np.float32(0.05))
     res = oracle.Swarm(lcfg, h).plan(sc)
     assert res["cost"] == bf
+
+
+# H-swarm update (Eqs. TOF_omega, TOF_V, TOF_X in the (w, C1, C2) space of Sec. 3.2.1),
+# read from the H state after the last update.  After the first evolution every
+# H-particle's personal best is its position, so the first update exercises inertia,
+# the H-group best and the global best; the C1 term is pinned on the second update.
+
+def _hsef_state(E, c1=0.0, c2=0.0, c3=0.0, w=0.0, vlim=50.0):
+    lcfg = SepsoConfig(T=3, G=2, N=6, max_iters=8, alpha=30.0, beta=4)
+    rng = np.random.default_rng(9)
+    circ = np.column_stack([rng.uniform(60, 340, (6, 2)), rng.uniform(10, 30, 6)])
+    sc = oracle.Scene((20, 20), (380, 380), circ)
+    hh = np.zeros((4, 6))
+    hh[:, 0], hh[:, 1], hh[:, 2], hh[:, 3], hh[:, 4], hh[:, 5] = c1, c2, c3, w, w, vlim
+    return oracle.hsef_state(lcfg, sc, HG=4, HN=2, E=E, hhyper=hh, lo=HSEF_BOX_LO, hi=HSEF_BOX_HI,
+                             l_vlimit=0.05, hseed=77)
+
+
+def _box(G):
+    lo = np.repeat(np.float32(HSEF_BOX_LO).astype(np.float64), G)
+    hi = np.repeat(np.float32(HSEF_BOX_HI).astype(np.float64), G)
+    return lo, hi
+
+
+def _ratio(dv, toward):
+    """Per H-particle: dv / toward over the coordinates where toward != 0."""
+    out = []
+    for h in range(dv.shape[0]):
+        m = np.abs(toward[h]) > 1e-9
+        out.append(dv[h, m] / toward[h, m] if m.any() else np.zeros(0))
+    return out
+
+
+def test_hsef_inertia_scales_the_velocity():
+    v1 = _hsef_state(1, w=1.0)["HV"]
+    v6 = _hsef_state(1, w=0.6)["HV"]
+    assert np.abs(v1).max() > 0
+    np.testing.assert_allclose(v6, 0.6 * v1, rtol=1e-12, atol=1e-12)
+
+
+def test_hsef_group_and_global_attractors():
+    # C2 pulls towards the H-particle's own H-group best, C3 towards the global best,
+    # each with one random factor in [0, 1) per H-particle, the two factors distinct
+    factors = {}
+    for kw, row in (({"c2": 1.0}, "HGb"), ({"c3": 1.0}, "HTb")):
+        st = _hsef_state(1, **kw)
+        x0 = st["HP"]  # the first fitness improves every personal best from +inf
+        target = st["HGb"][np.arange(8) // 2] if row == "HGb" else np.broadcast_to(st["HTb"], x0.shape)
+        f = {}
+        for h, r in enumerate(_ratio(st["HV"], target - x0)):
+            if r.size:
+                assert np.ptp(r) < 1e-9 and 0.0 <= r[0] < 1.0
+                f[h] = r[0]
+        assert f and max(f.values()) > 0.0  # the attractor acts
+        factors[row] = f
+        # a row that is the particle's own position gives no pull
+        same = np.all(np.abs(target - x0) < 1e-12, axis=1)
+        assert same.any() and np.all(st["HV"][same] == 0.0)
+    both = set(factors["HGb"]) & set(factors["HTb"])
+    assert both and all(factors["HGb"][h] != factors["HTb"][h] for h in both)
+
+
+def test_hsef_velocity_is_the_sum_of_its_terms():
+    parts = [_hsef_state(1, w=0.7)["HV"], _hsef_state(1, c2=0.9)["HV"], _hsef_state(1, c3=1.7)["HV"]]
+    whole = _hsef_state(1, w=0.7, c2=0.9, c3=1.7)["HV"]
+    np.testing.assert_allclose(whole, sum(parts), rtol=1e-12, atol=1e-12)
+
+
+def test_hsef_personal_best_attractor_on_the_second_update():
+    # C1 does not act on the first update (personal best = position), so two runs
+    # that differ only in C1 reach the second update in the same state; the
+    # velocity difference is C1 r1 (HP - HX) with one factor per H-particle
+    # (w is constant, so the state after the first update is that of a one-evolution
+    # run; the large V_limit keeps every velocity unclipped)
+    base = dict(c2=0.8, c3=0.6, w=0.5)
+    a, b = _hsef_state(2, **base), _hsef_state(2, c1=1.3, **base)
+    x1 = _hsef_state(1, **base)["HX"]
+    np.testing.assert_array_equal(a["HP"], b["HP"])
+    dv = b["HV"] - a["HV"]
+    ratios = _ratio(dv, a["HP"] - x1)
+    seen = []
+    for r in ratios:
+        if r.size:
+            assert np.ptp(r) < 1e-9 and 0.0 <= r[0] < 1.3
+            seen.append(r[0])
+    assert seen and max(seen) > 0.0
+
+
+def test_hsef_positions_and_velocities_are_clipped():
+    st = _hsef_state(1, w=0.7, c2=0.9, c3=1.7)
+    lo, hi = _box(2)
+    np.testing.assert_allclose(st["HX"], np.clip(st["HP"] + st["HV"], lo, hi), rtol=0, atol=1e-12)
+    small = _hsef_state(1, w=0.7, c2=0.9, c3=1.7, vlim=0.01)
+    assert np.all(np.abs(small["HV"]) <= 0.01 * (hi - lo) + 1e-12)
+    assert np.any(np.abs(small["HV"]) >= 0.01 * (hi - lo) - 1e-12)
+
