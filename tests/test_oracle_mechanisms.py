@@ -21,6 +21,18 @@ def test_u01_hand_values():
     assert oracle.u01(0x80000000) == 0.5
 
 
+def test_philox_known_answers():
+    # the generator's published known-answer vectors (tests/golden/philox4x32_10_kat.json)
+    import json
+    from pathlib import Path
+    kat = json.loads((Path(__file__).parent / "golden" / "philox4x32_10_kat.json").read_text())
+    for case in kat["cases"]:
+        ctr = np.array([[int(w, 16) for w in case["counter"]]], np.uint32)
+        k0, k1 = (int(w, 16) for w in case["key"])
+        out = oracle.philox(ctr, seed=(k1 << 32) | k0)
+        assert [f"{v:08x}" for v in out[0]] == case["output"]
+
+
 def test_philox_outputs_are_uniform_and_distinct():
     n = 200_000
     ctr = np.zeros((n, 4), np.uint32)
