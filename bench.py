@@ -78,8 +78,10 @@ def parse():
     ap.add_argument("--prior-rounds", type=int, default=3)
     ap.add_argument("--prior-epochs", type=int, default=30)
     ap.add_argument("--prior-batch", type=int, default=4096, help="rows per Adam step")
-    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve",
-                    help="comma list of main, cpu, batch, prior, serve, gemm (gemm: the tensor-core GEMM alone)")
+    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper",
+                    help="comma list of main, cpu, batch, prior, serve, paper, gemm (paper: the "
+                         "ablation variants of the path-planning comparison; gemm: the tensor-core "
+                         "GEMM alone)")
     return ap.parse_args()
 
 
@@ -431,6 +433,61 @@ def run_batch(n: int, iters: int):
             "l2": f"inputs larger than L2 ({bp.workspace.numel() / 1e9:.1f} GB of batch state)"}
 
 
+def run_paper(frames: int = 100, seed: int = 0):
+    """The path-planning comparison of Sec. 4.3 (Table ppresult) with the ablation
+    switches: SEPSO, SEPSO(NoAT), SEPSO(NoPI), DTPSO, each over the same seeded
+    sequence of ``frames`` frames (one planning cycle each, cap 30 iterations).
+    Time per frame = CUDA-event time of scene advance + plan on the device; the
+    result is read back after every frame (outside the events)."""
+    import torch
+
+    from paper_2308_10169_gb300 import Planner
+    from paper_2308_10169_gb300.inputs import PAPER_VARIANTS, paper_workload
+    paper = {"SEPSO": (412.0, 0.015, 12.9), "SEPSO(NoAT)": (408.3, 0.036, 30.0),
+             "SEPSO(NoPI)": (415.8, 0.033, 26.8), "DTPSO": (413.9, 0.036, 30.0)}
+    out = {}
+    for var in PAPER_VARIANTS:
+        cfg, scene, hyper = paper_workload(seed, var)
+        warm = Planner(cfg)
+        warm.set_hyper(hyper)
+        warm.set_scene(scene)
+        for _ in range(3):
+            warm.plan()
+        del warm
+        pl = Planner(cfg)
+        pl.set_hyper(hyper)
+        pl.set_scene(scene)
+        stream = torch.cuda.current_stream()
+        l0 = pl.launch_count()
+        ms, wall, L, I, Q = [], [], [], [], []
+        torch.cuda.synchronize()
+        for f in range(frames):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            a.record(stream)
+            if f:
+                pl.advance(1)
+            pl.plan_async()
+            b.record(stream)
+            r = pl.read_result()
+            wall.append(time.perf_counter() - t0)
+            ms.append(a.elapsed_time(b))
+            L.append(r["length"]); I.append(r["iters"]); Q.append(r["Q"])
+        out[var] = {"path_length": float(np.mean(L)), "ms_per_frame": float(np.mean(ms)),
+                    "wall_ms_per_frame_with_readback": 1e3 * float(np.mean(wall)),
+                    "iters_per_frame": float(np.mean(I)),
+                    "collision_free_frames": float(np.mean(np.array(Q) == 0)),
+                    "gpu_launches": pl.launch_count() - l0,
+                    "paper_context": {"path_length": paper[var][0], "s_per_frame": paper[var][1],
+                                      "iters_per_frame": paper[var][2],
+                                      "note": "RTX 2070 SUPER, the paper's own (unpublished) scene"}}
+    return {"workload": "366x366 map, 8 circles r~U[15,30] (2 static, 6 moving |v|~U(0,5]/frame, "
+                        "wall bounce), start/target moving 3 and 8 per frame vertically, T=8 (D=16), "
+                        "G=8 x N=170, alpha=30 beta=4, PI gamma=0.25, std-window AT TW=20 delta=10, "
+                        f"cap 30 iterations per frame, {frames} frames, seed {seed}",
+            "variants": out}
+
+
 def _world_step(ag):
     """The client's simulated world between two requests of an agent: circles and
     start/target move by their velocity and bounce off the map border."""
@@ -683,6 +740,8 @@ def main():
         if world == 1 and "prior" in sections and args.prior_train > 0:
             line["prior"] = run_prior(args.prior_train, args.prior_eval, args.prior_rounds, args.prior_epochs,
                                       line, args.prior_batch)
+        if world == 1 and "paper" in sections:
+            line["paper_ablation"] = run_paper()
         if world == 1 and "gemm" in sections:
             line["gemm"] = run_gemm()
         if world == 1 and "serve" in sections and args.serve_rates:

@@ -594,6 +594,20 @@ int64_t sepso_launch_count(sepso_handle h);
 const char* sepso_strerror(int code);
 const char* sepso_last_error(void);
 
+/* Auto Truncation window criterion (Sec. 3.3.4, first criterion) on its own, for
+ * checking: for each of `count` windows, whether the population standard deviation
+ * of the ns[i] newest entries of the ring win[i*tw .. i*tw+tw) (head heads[i], the
+ * slot the next entry would take; entries oldest first at (head - n + j) mod tw)
+ * is below delta, as a two-pass FP64 computation decides it.  Evaluated on the
+ * device by the code sepso_plan runs (an FP32 warp pass with a rounding-error
+ * bound, FP64 sums near the threshold or for entries that are not FP32 values).
+ * win: host double[count*tw]; ns, heads: host int32[count] with 1 <= ns[i] <= tw,
+ * 0 <= heads[i] < tw; tw in [1, 64]; out: host int32[count] gets 1 (below) or 0.
+ * delta <= 0 or NaN gives 0.  Allocates and frees a device buffer; syncs stream.
+ * Errors: EINVAL (counts, ranges, null pointers), ECUDA. */
+int sepso_at_window_test(const double* win, const int32_t* ns, const int32_t* heads, int32_t count,
+                         int32_t tw, float delta, int32_t* out, void* stream);
+
 /* Watchdog self-test (failure detection without a fault): one kernel runs the two
  * kinds of bounded wait the library's kernels use -- an mbarrier that no copy
  * completes, and the inter-CTA counter that no CTA increments -- with a limit of

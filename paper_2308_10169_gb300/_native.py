@@ -190,6 +190,7 @@ SIGNATURES = {
     "sepso_gemm_bf16_ex": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _i32, _i32, ctypes.c_float, _vp, _i32,
                                           _vp, _i32, _vp, _i32, _vp, _i32, ctypes.POINTER(GemmExtra), _i32,
                                           _vp]),
+    "sepso_at_window_test": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp]),
     "sepso_watchdog_selftest": (ctypes.c_int, [_i32, ctypes.POINTER(_i32), _vp]),
     "sepso_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sepso_last_error": (ctypes.c_char_p, []),

@@ -868,6 +868,39 @@ extern "C" int sepso_watchdog_selftest(int32_t limit_us, int32_t* fired, void* s
 }
 
 // ---------------------------------------------------------------------------
+// The Auto Truncation window criterion, evaluated on the device by the planner's code.
+// ---------------------------------------------------------------------------
+extern "C" int sepso_at_window_test(const double* win, const int32_t* ns, const int32_t* heads, int32_t count,
+                                    int32_t tw, float delta, int32_t* out, void* stream) {
+  if (count < 0 || (count > 0 && (!win || !ns || !heads || !out)))
+    return fail(SEPSO_EINVAL, "null argument or negative count");
+  if (tw < 1 || tw > 64) return fail(SEPSO_EINVAL, "tw=%d outside [1, 64]", tw);
+  if (count > (1 << 20)) return fail(SEPSO_EINVAL, "count=%d above 2^20", count);
+  for (int32_t i = 0; i < count; ++i) {
+    if (ns[i] < 1 || ns[i] > tw) return fail(SEPSO_EINVAL, "ns[%d]=%d outside [1, tw]", i, ns[i]);
+    if (heads[i] < 0 || heads[i] >= tw) return fail(SEPSO_EINVAL, "heads[%d]=%d outside [0, tw)", i, heads[i]);
+  }
+  if (count == 0) return SEPSO_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t wb = (size_t)count * tw * sizeof(double), ib = (size_t)count * sizeof(int32_t);
+  char* d = nullptr;
+  CUDA_TRY(cudaMalloc(&d, wb + 3 * ib));
+  double* dw = reinterpret_cast<double*>(d);
+  int32_t* dn = reinterpret_cast<int32_t*>(d + wb);
+  int32_t* dh = dn + count;
+  int32_t* dout = dh + count;
+  cudaError_t e = cudaMemcpyAsync(dw, win, wb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dn, ns, ib, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dh, heads, ib, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_at_window(dw, dn, dh, count, tw, delta, dout, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, ib, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  CUDA_TRY(e);
+  return SEPSO_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Planning without any device allocation.
 //
 // Some callers cannot call cudaMalloc at all: code that runs inside another

@@ -74,6 +74,73 @@ __host__ __device__ SmemLayout SmemLayout::make(int Omax, int ppc, int D, int T,
 }
 
 // ---------------------------------------------------------------------------
+// The Auto Truncation window test (Sec. 3.3.4, first criterion), run by one warp.
+//
+// The decision is the one a two-pass FP64 population standard deviation of the n
+// newest ring entries (oldest first) takes against delta.  Each lane holds at most
+// two entries (tw <= 64), FP32 values held as doubles; an FP32 pass over the warp
+// gives the sum of squared deviations ss together with a bound on its rounding
+// error, and settles every window whose deviation is not within that bound (plus
+// a 1e-6 relative margin, far above the FP64 computation's own error) of the
+// threshold n * delta^2; the rest, and windows with non-finite values, take the
+// FP64 two-pass sums in ring order on lane 0.
+//
+// Error bound.  With u = 2^-24, L = adds on a summation path (<= 1 + 5 here) and
+// g = (L + 4) u: |s - sum x| <= g A, A = sum |x|;  m = rn(s / n) is within
+// e = (g + 2u) A / n of the true mean mu;  sum (x - m)^2 = SS + n (mu - m)^2 for
+// the true SS; each rounded square carries at most 3u and the sum g, so
+// ss (1 - 2g) - n e^2 <= SS <= ss (1 + 2g).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ bool window_std_below(const double* win, int tw, int n, int head, float delta,
+                                 int lane) {
+  if (!(delta > 0.0f)) return false;  // a standard deviation is never below 0 (or NaN)
+  const int i0 = lane, i1 = lane + 32;
+  const double w0 = i0 < n ? win[(head - n + i0 + 2 * tw) % tw] : 0.0;
+  const double w1 = i1 < n ? win[(head - n + i1 + 2 * tw) % tw] : 0.0;
+  const float x0 = (float)w0, x1 = (float)w1;
+  // entries the kernel records are FP32 values; a window loaded with other doubles
+  // goes to the FP64 sums
+  const bool exact = __all_sync(0xffffffffu, (double)x0 == w0 && (double)x1 == w1);
+  const float s = warp_sum_f32(x0 + x1);
+  const float a = warp_sum_f32(fabsf(x0) + fabsf(x1));
+  const float nf = (float)n;
+  const float m = __fdiv_rn(s, nf);
+  const float d0 = i0 < n ? __fsub_rn(x0, m) : 0.0f;
+  const float d1 = i1 < n ? __fsub_rn(x1, m) : 0.0f;
+  const float ss = warp_sum_f32(__fadd_rn(__fmul_rn(d0, d0), __fmul_rn(d1, d1)));
+  const float u = 5.9604645e-8f, g = 10.0f * u;
+  const float A = a * (1.0f + g);
+  const float e = (g + 2.0f * u) * A / nf;
+  const float e64 = (nf + 2.0f) * 1.2e-16f * A / nf;
+  const float thr = nf * delta * delta;
+  const float hi = ss * (1.0f + 2.0f * g) + nf * e64 * e64;
+  const float lo = ss * (1.0f - 2.0f * g) - nf * e * e;
+  if (exact && isfinite(ss) && isfinite(A) && isfinite(thr) && isfinite(hi)) {
+    if (hi < thr * (1.0f - 1e-6f)) return true;
+    if (lo > thr * (1.0f + 1e-6f)) return false;
+  }
+  bool below = false;
+  if (lane == 0) {
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i) sum += win[(head - n + i + 2 * tw) % tw];
+    const double mean = sum / (double)n;
+    double sq = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double d = win[(head - n + i + 2 * tw) % tw] - mean;
+      sq += d * d;
+    }
+    below = sqrt(sq / (double)n) < (double)delta;
+  }
+  return __shfl_sync(0xffffffffu, below ? 1 : 0, 0) != 0;
+}
+
+// ---------------------------------------------------------------------------
 // The fused persistent iteration.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
@@ -136,7 +203,7 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
 
   float Tfit;
   int TQ, k;
-  // AT state, tracked by thread 0 only
+  // AT state, tracked by the lanes of warp 0
   int win_n = 0, win_head = 0, stall = 0;
   float prev_lfv = INFINITY;
 
@@ -183,11 +250,11 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
     Tfit = INFINITY;
     TQ = 0;
     k = 0;
-    if (tid == 0 && p.at_mode == SEPSO_AT_STD_WINDOW) {
+    if (tid < 32 && p.at_mode == SEPSO_AT_STD_WINDOW) {
       if (cycle != 0) {
         win_n = ctl->win_n;
         win_head = ctl->win_head;
-        for (int i = 0; i < p.tw; ++i) sWin[i] = p.win[(size_t)r * p.tw + i];
+        for (int i = lane; i < p.tw; i += 32) sWin[i] = p.win[(size_t)r * p.tw + i];
       }
     }
   } else {
@@ -398,25 +465,18 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
     last_tg = tg;
     last_rbase = rbase;
 
-    // Auto Truncation (Sec. 3.3.4) and the iteration cap.
-    if (tid == 0) {
+    // Auto Truncation (Sec. 3.3.4) and the iteration cap, decided by warp 0 (its
+    // lanes track the same window fill, head and stall counter).
+    if (tid < 32) {
       int stop = 0;
       if (p.mode == kModePlan) {
         if (p.at_mode == SEPSO_AT_STD_WINDOW) {
-          sWin[win_head] = (double)Tfit;
+          if (lane == 0) sWin[win_head] = (double)Tfit;
+          __syncwarp();
           win_head = (win_head + 1) % p.tw;
           if (win_n < p.tw) ++win_n;
-          if (win_n >= 2) {
-            double sum = 0.0;
-            for (int i = 0; i < win_n; ++i) sum += sWin[(win_head - win_n + i + 2 * p.tw) % p.tw];
-            const double mean = sum / (double)win_n;
-            double ss = 0.0;
-            for (int i = 0; i < win_n; ++i) {
-              const double d = sWin[(win_head - win_n + i + 2 * p.tw) % p.tw] - mean;
-              ss += d * d;
-            }
-            if (sqrt(ss / (double)win_n) < (double)p.delta && TQ == 0) stop = 1;
-          }
+          if (win_n >= 2 && TQ == 0 && window_std_below(sWin, p.tw, win_n, win_head, p.delta, lane))
+            stop = 1;
         } else if (p.at_mode == SEPSO_AT_STALL) {
           if (Tfit < prev_lfv - p.stall_tol) stall = 0;
           else ++stall;
@@ -425,7 +485,7 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
         }
         if (k >= p.max_iters) stop = 1;
       }
-      s_stop = stop;
+      if (tid == 0) s_stop = stop;
     }
     __syncthreads();
     if (s_stop) break;
@@ -810,6 +870,20 @@ __global__ void watchdog_selftest_kernel(const unsigned int* never, unsigned lon
     if (!counter_wait_bounded(never, 1u, limit_ns)) f |= 2;
     *fired = f;
   }
+}
+
+// The Auto Truncation window test on its own: one warp per window.
+__global__ void at_window_kernel(const double* win, const int32_t* ns, const int32_t* heads, int tw,
+                                 float delta, int32_t* out) {
+  const int i = blockIdx.x;
+  const bool below = window_std_below(win + (size_t)i * tw, tw, ns[i], heads[i], delta, threadIdx.x);
+  if (threadIdx.x == 0) out[i] = below ? 1 : 0;
+}
+
+cudaError_t launch_at_window(const double* win, const int32_t* ns, const int32_t* heads, int count, int tw,
+                             float delta, int32_t* out, cudaStream_t s) {
+  at_window_kernel<<<count, 32, 0, s>>>(win, ns, heads, tw, delta, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_watchdog_selftest(const unsigned int* never, unsigned long long limit_ns, int* fired,

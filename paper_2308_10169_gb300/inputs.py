@@ -15,6 +15,9 @@ Workload shapes (all synthetic; the paper's own simulator scenes are not publish
   bouncing off the walls), start/target drifting 1 unit per cycle vertically,
   Priori Initialization (gamma=0.25) and Auto Truncation by stall counter (10
   stalled iterations, cap 300), alpha=30, beta=4 (Table params_path).
+* ``paper_workload``   -- the path-planning setting of Sec. 4.3 with the ablation
+  switches of Table ppresult (366x366 map, 8 obstacles of which 6 move, T=8,
+  G=8 x N=170, std-window AT, 30 iterations per frame at most).
 
 Paper tables reproduced as data (they are inputs of the method):
 Table hyper8 (DTPSO / H-SEPSO / DPPSO hyper-parameters) and Table hyper8path
@@ -179,6 +182,50 @@ def dynamic_workload(seed: int = 0, n_static: int = 32, n_moving: int = 32, T: i
                   start_vel=(0.0, 1.0), target_vel=(0.0, -1.0))
     hyper = sample_hyper(4000 + seed, cfg.G)
     return cfg, scene, hyper
+
+
+# Ablation variants of the path-planning comparison (Table ppresult): hyper-parameter
+# table, Priori Initialization, Auto Truncation.  Without AT a frame runs the cap of
+# 30 iterations; with AT the cap stays 30 and the std-window rule may stop earlier.
+PAPER_VARIANTS = {
+    "SEPSO": dict(hyper="hyper8path", use_pi=True, at=True),
+    "SEPSO(NoAT)": dict(hyper="hyper8path", use_pi=True, at=False),
+    "SEPSO(NoPI)": dict(hyper="hyper8path", use_pi=False, at=True),
+    "DTPSO": dict(hyper="hyper8", use_pi=False, at=False),
+}
+
+
+def paper_workload(seed: int = 0, variant: str = "SEPSO", frame_cap: int = 30):
+    """The path-planning setting of Sec. 4.3: (config, scene with velocities, hyper).
+
+    366 x 366 map; 8 obstacles (2 static, 6 moving at speed U(0, 5] per frame in a
+    random direction, bouncing off the borders) drawn as circles with centres
+    U[60, 306]^2 and radii U[15, 30]; start (20, 40) moving 3 per frame and target
+    (346, 326) moving 8 per frame along the vertical axis; T = 8 waypoints (D = 16),
+    G = 8 groups x N = 170; alpha = 30, beta = 4, gamma = 0.25, delta = 10, TW = 20
+    (Table params_path); a frame is one planning cycle with a cap of ``frame_cap``
+    iterations.  ``variant`` is a key of ``PAPER_VARIANTS``: SEPSO uses the evolved
+    Table hyper8path rows (linear inertia w_init -> w_end, C3 > 0), DTPSO the
+    unevolved Table hyper8 rows.
+    """
+    v = PAPER_VARIANTS[variant]
+    cfg = SepsoConfig(T=8, G=8, N=170, max_obstacles=8, map_w=366.0, map_h=366.0,
+                      alpha=PARAMS_PATH["alpha"], beta=PARAMS_PATH["beta"], max_iters=frame_cap,
+                      at_mode=AT_STD_WINDOW if v["at"] else AT_OFF, tw=PARAMS_PATH["tw"],
+                      delta=PARAMS_PATH["delta"], use_pi=v["use_pi"],
+                      pi_gamma=PARAMS_PATH["pi_gamma"], pi_halfwidth=20.0, seed=seed)
+    rng = np.random.default_rng(5000 + seed)
+    n_static, n_moving = 2, 6
+    circles = random_circles(rng, n_static + n_moving, lo=60.0, hi=306.0, r_lo=15.0, r_hi=30.0)
+    vel = np.zeros((n_static + n_moving, 2), np.float32)
+    speed = 5.0 - rng.uniform(0.0, 5.0, n_moving)      # (0, 5]
+    ang = rng.uniform(0.0, 2.0 * np.pi, n_moving)
+    vel[n_static:, 0] = speed * np.cos(ang)
+    vel[n_static:, 1] = speed * np.sin(ang)
+    scene = Scene(start=(20, 40), target=(346, 326), circles=circles, circle_vel=vel,
+                  start_vel=(0.0, 3.0), target_vel=(0.0, -8.0))
+    table = TABLE_HYPER8_PATH if v["hyper"] == "hyper8path" else TABLE_HYPER8
+    return cfg, scene, np.ascontiguousarray(table[:cfg.G], dtype=np.float32)
 
 
 def random_paths(seed: int, n: int, T: int, W: float = 400.0, H: float = 400.0) -> np.ndarray:

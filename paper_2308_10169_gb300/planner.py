@@ -42,6 +42,22 @@ def state_layout(cfg: SepsoConfig) -> dict:
     return out
 
 
+def at_window_test(win, ns, heads, delta: float) -> np.ndarray:
+    """The Auto Truncation window criterion (Sec. 3.3.4) evaluated on the device by
+    the planner's own code: ``win`` (count, tw) float64 rings, ``ns``/``heads`` the
+    fill and head of each; returns bool[count], std of the newest entries < delta."""
+    w = np.ascontiguousarray(win, np.float64)
+    count, tw = w.shape
+    n = np.ascontiguousarray(ns, np.int32).reshape(count)
+    h = np.ascontiguousarray(heads, np.int32).reshape(count)
+    out = np.zeros(count, np.int32)
+    stream = torch.cuda.current_stream().cuda_stream
+    check(_native.lib().sepso_at_window_test(w.ctypes.data, n.ctypes.data, h.ctypes.data, count, tw,
+                                             ctypes.c_float(delta), out.ctypes.data,
+                                             ctypes.c_void_p(stream)))
+    return out.astype(bool)
+
+
 class Planner:
     """One SEPSO planner (``cfg.runs`` swarms sharing one scene) on one GPU."""
 

@@ -4,6 +4,7 @@ import ctypes
 import re
 from pathlib import Path
 
+import numpy as np
 import pytest
 
 from paper_2308_10169_gb300 import _native
@@ -166,3 +167,24 @@ def test_gemm_extra_workspace_and_argument_checks():
     assert ex(ksplit=4, workspace=ws, workspace_bytes=4 * 100 * 64 * 4 - 1) == -3   # workspace too small
     assert ex(colsum=C, workspace=None, workspace_bytes=0) == -3
     assert ex(colsum=C, workspace=ctypes.c_void_p((4 << 20) + 8), workspace_bytes=1 << 20) == -3  # misaligned
+
+
+def test_at_window_test_rejects_bad_arguments_before_any_launch():
+    L = _native.lib()
+    win = np.zeros((2, 20), np.float64)
+    ns = np.array([5, 20], np.int32)
+    heads = np.array([5, 0], np.int32)
+    out = np.zeros(2, np.int32)
+
+    def call(w=win, n=ns, h=heads, count=2, tw=20, delta=10.0):
+        return L.sepso_at_window_test(w.ctypes.data, n.ctypes.data, h.ctypes.data, count, tw,
+                                      ctypes.c_float(delta), out.ctypes.data, None)
+
+    assert call(tw=0) == -1 and call(tw=65) == -1
+    assert call(n=np.array([5, 21], np.int32)) == -1          # fill above tw
+    assert call(n=np.array([0, 5], np.int32)) == -1           # empty window
+    assert call(h=np.array([20, 0], np.int32)) == -1          # head outside the ring
+    assert call(h=np.array([-1, 0], np.int32)) == -1
+    assert call(count=-1) == -1
+    assert L.sepso_at_window_test(None, None, None, 3, 20, ctypes.c_float(1.0), None, None) == -1
+    assert call(count=0) == 0                                  # nothing to do, no device call

@@ -16,8 +16,9 @@ import torch
 import oracle
 from paper_2308_10169_gb300 import Planner, Scene, SepsoConfig, sample_hyper, static_workload
 from paper_2308_10169_gb300.inputs import (AT_STALL, AT_STD_WINDOW, HSEF_BOX_HI, HSEF_BOX_LO,
-                                           TABLE_HYPER8, dynamic_workload, random_circles,
-                                           random_paths, random_state)
+                                           PAPER_VARIANTS, TABLE_HYPER8, dynamic_workload,
+                                           paper_workload, random_circles, random_paths,
+                                           random_state)
 
 pytestmark = pytest.mark.gpu
 
@@ -305,6 +306,138 @@ def test_scene_advance_matches_oracle(native):
     np.testing.assert_allclose(g.circle_vel, v, atol=0)
     np.testing.assert_allclose(g.start, st, atol=1e-4)
     np.testing.assert_allclose(g.target, tg, atol=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# Path-planning comparison of Sec. 4.3 with the ablation switches (Table ppresult)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", list(PAPER_VARIANTS))
+def test_paper_variant_single_step_matches_oracle(native, variant):
+    # one iteration from an identical state at the full configuration: 366 x 366 map,
+    # G = 8 x N = 170, Table hyper8path (C3 > 0, linear inertia over the cap of 30) or
+    # Table hyper8
+    cfg, scene, hyper = paper_workload(1, variant)
+    st = _decisive_state(cfg, scene, hyper, seed=40)
+    st["k"] = np.full_like(st["k"], 7)
+    pl = make(cfg, scene, hyper)
+    pl.set_state(st)
+    pl.step(1)
+    pl.sync()
+    s = pl.get_state()
+    sw = oracle.Swarm(cfg, hyper)
+    sw.load(st)
+    sw.step(osc(scene), 1)
+    o = sw.state()
+    assert s["k"][0] == o["k"][0] == 8
+    np.testing.assert_array_equal(s["PQ"], o["PQ"])
+    np.testing.assert_allclose(s["Pfit"], o["Pfit"], rtol=1e-4)
+    np.testing.assert_allclose(s["Gfit"], o["Gfit"], rtol=1e-4)
+    np.testing.assert_allclose(s["Tfit"], o["Tfit"], rtol=1e-4)
+    close_pos(s["Tb"], o["Tb"], 366.0)
+    close_pos(s["V"], o["V"], float(np.max(hyper[:, 5])) * 366.0)
+    close_pos(s["X"], o["X"], 366.0)
+
+
+def _ordered(w, n, head):
+    tw = len(w)
+    return np.array([w[(head - n + j + 2 * tw) % tw] for j in range(n)], np.float64)
+
+
+def test_at_window_criterion_matches_fp64(native):
+    # The planner's window test (FP32 warp pass with an error bound, FP64 sums near
+    # the threshold) takes the decision of the oracle's two-pass FP64 std on every
+    # window: random fills and heads, deviations scaled to put the std at
+    # delta * (1 + eps) for eps down to 1e-9 (FP32 rounding of the entries then
+    # moves it by about 1e-7), doubles that are not FP32 values, infinities, NaN.
+    from paper_2308_10169_gb300.planner import at_window_test
+    rng = np.random.default_rng(77)
+    for tw in (64, 20, 7, 2, 1):
+        count = 4000
+        W = np.zeros((count, tw))
+        ns = rng.integers(1, tw + 1, count).astype(np.int32)
+        heads = rng.integers(0, tw, count).astype(np.int32)
+        delta = np.float32(10.0)
+        eps = np.array([0, 1e-9, -1e-9, 1e-7, -1e-7, 1e-6, -1e-6, 1e-5, -1e-5, 1e-3, -1e-3, 0.5, -0.5])
+        for i in range(count):
+            n = ns[i]
+            kind = i % 20
+            base = rng.uniform(300, 500) if kind < 18 else rng.uniform(1e5, 1e9)
+            dev = rng.standard_normal(n)
+            dev -= dev.mean()
+            sd = np.sqrt(np.mean(dev ** 2))
+            if sd > 0:
+                dev *= float(delta) * (1 + eps[i % len(eps)]) / sd
+            vals = (base + dev).astype(np.float32).astype(np.float64)
+            if kind == 17:
+                vals = base + dev                          # not FP32 values
+            if i % 97 == 0:
+                vals[rng.integers(0, n)] = np.inf
+            if i % 101 == 0:
+                vals[rng.integers(0, n)] = np.nan
+            ring = rng.uniform(0, 1e6, tw)                 # stale slots outside the window
+            for j in range(n):
+                ring[(heads[i] - n + j + 2 * tw) % tw] = vals[j]
+            W[i] = ring
+        got = at_window_test(W, ns, heads, float(delta))
+        want = np.array([oracle.window_std(_ordered(W[i], ns[i], heads[i])) < float(delta)
+                         for i in range(count)])
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, (tw, bad[:5])
+        if tw >= 7:
+            assert 0.2 < want.mean() < 0.8
+    W = np.full((3, 4), 400.0)
+    n3, h3 = np.array([4, 4, 4], np.int32), np.zeros(3, np.int32)
+    assert not at_window_test(W, n3, h3, 0.0).any()
+    assert not at_window_test(W, n3, h3, -1.0).any()
+    assert not at_window_test(W, n3, h3, float("nan")).any()
+    assert at_window_test(W, n3, h3, 1e-30).all()             # std exactly 0
+
+
+def _paper_frames(variant, keys, frames, gpu):
+    L, I = [], []
+    for key in keys:
+        cfg, scene, hyper = paper_workload(0, variant)
+        cfg = cfg.with_(seed=key)
+        if gpu:
+            pl = make(cfg, scene, hyper)
+        else:
+            sw = oracle.Swarm(cfg, hyper)
+            c, v, st, sv, tg, tv = (scene.circles, scene.circle_vel, scene.start, scene.start_vel,
+                                    scene.target, scene.target_vel)
+        for f in range(frames):
+            if gpu:
+                if f:
+                    pl.advance(1)
+                r = pl.plan()
+            else:
+                if f:
+                    c, v, st, sv, tg, tv = oracle.advance_scene(cfg.map_w, cfg.map_h, c, v, st, sv,
+                                                                tg, tv)
+                r = sw.plan(oracle.Scene(st, tg, c))
+            assert 1 <= r["iters"] <= 30
+            L.append(r["length"])
+            I.append(r["iters"])
+    return np.array(L), np.array(I)
+
+
+@pytest.mark.parametrize("variant", list(PAPER_VARIANTS))
+def test_paper_variant_frames_match_oracle(native, variant):
+    # 4 Philox keys x 25 frames of the moving scene.  FP32 and FP64 trajectories part
+    # after a few iterations, so the means are compared; the bounds are about twice
+    # the spread of the oracle's own means over keys (mean length +-2% without AT,
+    # +-3% with it; AT iterations per frame 11.7 .. 17.1 for SEPSO, 27.7 .. 28.3
+    # without PI).
+    keys = range(100, 104)
+    gL, gI = _paper_frames(variant, keys, 25, gpu=True)
+    oL, oI = _paper_frames(variant, keys, 25, gpu=False)
+    at = PAPER_VARIANTS[variant]["at"]
+    if not at:
+        assert np.all(gI == 30) and np.all(oI == 30)
+    assert abs(gL.mean() - oL.mean()) <= (0.06 if at else 0.03) * oL.mean(), (gL.mean(), oL.mean())
+    if at:
+        tol = 0.5 * oI.mean() + 2 if PAPER_VARIANTS[variant]["use_pi"] else 3.0
+        assert abs(gI.mean() - oI.mean()) <= tol, (gI.mean(), oI.mean())
 
 
 # ---------------------------------------------------------------------------
