@@ -17,6 +17,9 @@ What each function follows (paper: arXiv 2308.10169):
   Eq. TOF_omega, Eq. TOF_V (clip), Eq. TOF_X (clip).
 * ``Swarm.plan``            -- one planning cycle with Auto Truncation (Sec. 3.3.4).
 * ``advance_scene``         -- the dynamic simulator step (Fig. PP caption).
+* ``bf_value`` / ``BFSwarm`` -- the benchmark functions BF1-BF4 (Table BFs, their
+  textbook definitions) and DTPSO on them: the same Algorithm 1 iteration as
+  ``Swarm`` with that objective over the box [lo, hi]^D.
 * ``hsef``                  -- the hierarchical self-evolving framework
   (Sec. 3.2.1, Eq. fit_h).
 * ``raster`` / ``prior_encode`` / ``prior_decode`` / ``Mlp`` / ``adam`` -- the
@@ -73,6 +76,8 @@ class _Config(ctypes.Structure):
         ("stall_iters", ctypes.c_int32), ("stall_tol", ctypes.c_double),
         ("use_pi", ctypes.c_int32), ("pi_gamma", ctypes.c_double), ("pi_h", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32),
+        ("problem", ctypes.c_int32), ("Dbf", ctypes.c_int32),
+        ("lo", ctypes.c_double), ("hi", ctypes.c_double),
     ]
 
 
@@ -122,6 +127,8 @@ def lib():
         L.so_pi_count.restype = ctypes.c_int32
         L.so_init_swarm.argtypes = [ctypes.POINTER(_Config), _f64p, ctypes.POINTER(_State)]
         L.so_window_std.argtypes = [_f64p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+        L.so_bf_value.argtypes = [ctypes.c_int32, ctypes.c_int32, _f64p]
+        L.so_bf_value.restype = ctypes.c_double
         L.so_window_std.restype = ctypes.c_double
         L.so_at_update.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_State)]
         L.so_at_update.restype = ctypes.c_int32
@@ -327,6 +334,72 @@ class Swarm:
                       _p64(res))
         return {"waypoints": res[:D].copy(), "cost": float(res[D]), "length": float(res[D + 1]),
                 "Q": int(res[D + 2]), "iters": int(res[D + 3])}
+
+
+# ----------------------------------------------------------------------------
+# Benchmark functions (Table BFs) and DTPSO on them
+# ----------------------------------------------------------------------------
+
+def bf_value(fn: int, x) -> float:
+    """BF1..BF4 (Sphere, Rosenbrock, Rastrigin, Griewank) at one point, FP64."""
+    v = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1))
+    return lib().so_bf_value(int(fn), v.size, _p64(v))
+
+
+def _bf_cfg(c) -> _Config:
+    """The C config of a benchmark-function run (any object with BFConfig's fields)."""
+    return _Config(T=0, G=c.G, N=c.N, W=0.0, H=0.0, alpha=0.0, beta=1, max_iters=c.max_iters,
+                   at_mode=0, tw=1, delta=0.0, stall_iters=0, stall_tol=0.0, use_pi=0,
+                   pi_gamma=0.0, pi_h=0.0, seed=c.seed, run_id=c.run_id, problem=c.fn, Dbf=c.D,
+                   lo=float(np.float32(c.lo)), hi=float(np.float32(c.hi)))
+
+
+class BFSwarm(Swarm):
+    """DTPSO (Algorithm 1 with Table hyper8-style rows) on a benchmark function:
+    the iteration of ``Swarm`` with objective BF``fn`` over [lo, hi]^D, no PI, no AT,
+    a fixed number of iterations (``max_iters`` is also the T of Eq. TOF_omega)."""
+
+    _EMPTY = None
+
+    def __init__(self, cfg, hyper):
+        self.cfg = cfg
+        G, N, D = cfg.G, cfg.N, cfg.D
+        M = G * N
+        self.hyper = np.ascontiguousarray(np.asarray(hyper, dtype=np.float64).reshape(G, 6))
+        f = np.zeros
+        self.s = {
+            "X": f(M * D), "V": f(M * D), "P": f(M * D), "Pfit": np.full(M, np.inf),
+            "PQ": f(M, np.int32), "Gb": f(G * D), "Gfit": np.full(G, np.inf), "GQ": f(G, np.int32),
+            "Tb": f(D), "Tfit": np.full(1, np.inf), "TQ": f(1, np.int32), "k": f(1, np.int32),
+            "cycle": f(1, np.int32), "has_prev": f(1, np.int32), "prevT": f(D), "win": f(1),
+            "win_n": f(1, np.int32), "win_head": f(1, np.int32), "stall": f(1, np.int32),
+            "prev_lfv": np.full(1, np.inf), "n_prior": f(1, np.int32), "priorT": f(D),
+        }
+        self._c = _bf_cfg(cfg)
+        self._none = Scene((0.0, 0.0), (0.0, 0.0), np.zeros((0, 3)))
+
+    def evaluate(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, self.cfg.D))
+        F = np.zeros(X.shape[0])
+        s = self._none.c()
+        lib().so_evaluate(ctypes.byref(self._c), ctypes.byref(s), X.shape[0], _p64(X), _p64(F),
+                          None, None)
+        return F
+
+    def iteration(self, scene=None, check_stop: bool = False) -> bool:
+        return super().iteration(self._none, False)
+
+    def step(self, scene=None, iters: int = 1):
+        super().step(self._none, iters)
+
+    def run(self, iters: int) -> np.ndarray:
+        """Initialise, then ``iters`` iterations; returns Tfit after each one."""
+        self.init()
+        hist = np.zeros(iters)
+        for i in range(iters):
+            super().iteration(self._none, False)
+            hist[i] = self.s["Tfit"][0]
+        return hist
 
 
 # ----------------------------------------------------------------------------

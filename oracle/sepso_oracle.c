@@ -106,6 +106,12 @@ typedef struct {
   double pi_h;           /* half-width of the PI interval                     */
   uint64_t seed;         /* Philox key                                        */
   uint32_t run_id;       /* Philox counter word 3                             */
+  /* The objective: 0 = path planning (Sec. 3.3: D = 2T waypoint coordinates in
+   * the map); 1..4 = benchmark functions BF1..BF4 (Table BFs: Sphere,
+   * Rosenbrock, Rastrigin, Griewank) over the box [lo, hi]^D, D = Dbf.        */
+  int32_t problem;
+  int32_t Dbf;
+  double lo, hi;
 } so_config;
 
 typedef struct {
@@ -211,9 +217,57 @@ void so_tangency_margin(const so_config* cfg, const so_scene* sc, int32_t n, con
 }
 
 /* Eq. path_fit = Length + alpha * Q^beta for n particles (rows of X). */
+/* ------------------------------------------------------------------------- */
+/* Benchmark functions BF1-BF4 (Table BFs), their textbook definitions with  */
+/* 1-based coordinate index i = 1..D:                                        */
+/*   Sphere      sum x_i^2                                                   */
+/*   Rosenbrock  sum_{i<D} 100 (x_{i+1} - x_i^2)^2 + (x_i - 1)^2             */
+/*   Rastrigin   10 D + sum x_i^2 - 10 cos(2 pi x_i)                         */
+/*   Griewank    1 + sum x_i^2 / 4000 - prod cos(x_i / sqrt(i))              */
+/* All four have minimum 0 (at x = 0; Rosenbrock at x = 1).                  */
+/* ------------------------------------------------------------------------- */
+double so_bf_value(int32_t fn, int32_t D, const double* x) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double s = 0.0;
+  if (fn == 1) {
+    for (int32_t i = 0; i < D; ++i) s += x[i] * x[i];
+    return s;
+  }
+  if (fn == 2) {
+    for (int32_t i = 0; i + 1 < D; ++i) {
+      const double a = x[i + 1] - x[i] * x[i], b = x[i] - 1.0;
+      s += 100.0 * a * a + b * b;
+    }
+    return s;
+  }
+  if (fn == 3) {
+    for (int32_t i = 0; i < D; ++i) s += x[i] * x[i] - 10.0 * cos(two_pi * x[i]);
+    return 10.0 * (double)D + s;
+  }
+  if (fn == 4) {
+    double prod = 1.0;
+    for (int32_t i = 0; i < D; ++i) {
+      s += x[i] * x[i];
+      prod *= cos(x[i] / sqrt((double)(i + 1)));
+    }
+    return 1.0 + s / 4000.0 - prod;
+  }
+  return NAN;
+}
+
+static int32_t so_dim(const so_config* cfg) { return cfg->problem ? cfg->Dbf : 2 * cfg->T; }
+
 void so_evaluate(const so_config* cfg, const so_scene* sc, int32_t n, const double* X, double* F,
                  int32_t* Q, double* len) {
-  const int32_t T = cfg->T, D = 2 * T;
+  const int32_t T = cfg->T, D = so_dim(cfg);
+  if (cfg->problem) {
+    for (int32_t p = 0; p < n; ++p) {
+      if (F) F[p] = so_bf_value(cfg->problem, D, X + (int64_t)p * D);
+      if (Q) Q[p] = 0;
+      if (len) len[p] = 0.0;
+    }
+    return;
+  }
   for (int32_t p = 0; p < n; ++p) {
     const double* x = X + (int64_t)p * D;
     double l = so_length(T, x, sc->sx, sc->sy, sc->tx, sc->ty);
@@ -236,13 +290,19 @@ int32_t so_pi_count(double gamma, int32_t N) {
   return (int32_t)v;
 }
 
-static double so_extent(const so_config* cfg, int32_t j) { return (j < cfg->T) ? cfg->W : cfg->H; }
+/* X_range of coordinate j: [so_lo, so_lo + so_extent]; the map for a path. */
+static double so_extent(const so_config* cfg, int32_t j) {
+  if (cfg->problem) return cfg->hi - cfg->lo;
+  return (j < cfg->T) ? cfg->W : cfg->H;
+}
+static double so_lo(const so_config* cfg) { return cfg->problem ? cfg->lo : 0.0; }
+static double so_hi(const so_config* cfg, int32_t j) { return cfg->problem ? cfg->hi : so_extent(cfg, j); }
 
 static double so_clip(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 /* hyper: G x 6 rows (C1, C2, C3, w_init, w_end, V_limit), Table hyper8 layout. */
 void so_init_swarm(const so_config* cfg, const double* hyper, so_state* st) {
-  const int32_t T = cfg->T, G = cfg->G, N = cfg->N, D = 2 * T;
+  const int32_t G = cfg->G, N = cfg->N, D = so_dim(cfg);
   const uint32_t cyc = (uint32_t)*st->cycle;
   const int32_t n_pi = (cfg->use_pi && *st->has_prev) ? so_pi_count(cfg->pi_gamma, N) : 0;
   /* A second seed of the same kind as PI (the learned prior's proposal) takes the
@@ -264,7 +324,7 @@ void so_init_swarm(const so_config* cfg, const double* hyper, so_state* st) {
           x = so_clip(st->prevT[j] + (2.0 * u[j % 4] - 1.0) * cfg->pi_h, 0.0, ext);
         } else {
           so_draw4(cfg->seed, (uint32_t)(j / 4), (uint32_t)p, SO_STREAM_INIT_X, cyc, cfg->run_id, u);
-          x = 0.0 + u[j % 4] * (ext - 0.0);
+          x = so_lo(cfg) + u[j % 4] * ext;
         }
         so_draw4(cfg->seed, (uint32_t)(j / 4), (uint32_t)p, SO_STREAM_INIT_V, cyc, cfg->run_id, u);
         const double vmax = vlim * ext; /* V_range = V_limit * X_range */
@@ -333,7 +393,7 @@ int32_t so_at_update(const so_config* cfg, so_state* st) {
  *                 when AT fires or k reaches the cap.                       */
 int32_t so_iteration(const so_config* cfg, const so_scene* sc, const double* hyper, so_state* st,
                      int32_t check_stop) {
-  const int32_t T = cfg->T, G = cfg->G, N = cfg->N, D = 2 * T, M = G * N;
+  const int32_t G = cfg->G, N = cfg->N, D = so_dim(cfg), M = G * N;
   double* F = (double*)malloc(sizeof(double) * (size_t)M);
   int32_t* Q = (int32_t*)malloc(sizeof(int32_t) * (size_t)M);
 
@@ -412,7 +472,7 @@ int32_t so_iteration(const so_config* cfg, const so_scene* sc, const double* hyp
                    c3 * r3 * (st->Tb[j] - x);
         v = so_clip(v, -vmax, vmax);
         st->V[i] = v;
-        st->X[i] = so_clip(x + v, 0.0, ext);
+        st->X[i] = so_clip(x + v, so_lo(cfg), so_hi(cfg, j));
       }
     }
   }

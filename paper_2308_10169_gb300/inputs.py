@@ -18,6 +18,9 @@ Workload shapes (all synthetic; the paper's own simulator scenes are not publish
 * ``paper_workload``   -- the path-planning setting of Sec. 4.3 with the ablation
   switches of Table ppresult (366x366 map, 8 obstacles of which 6 move, T=8,
   G=8 x N=170, std-window AT, 30 iterations per frame at most).
+* ``bf_standard`` / ``bf_large`` -- the benchmark functions of Table BFs: D=30 with
+  8 x 10 particles (Sec. 4.1.1) and D=1000 with 8 x 2048 particles (Sec. 4.1.2),
+  over [-600, 600]^D, Table hyper8 rows, 1400 iterations.
 
 Paper tables reproduced as data (they are inputs of the method):
 Table hyper8 (DTPSO / H-SEPSO / DPPSO hyper-parameters) and Table hyper8path
@@ -226,6 +229,47 @@ def paper_workload(seed: int = 0, variant: str = "SEPSO", frame_cap: int = 30):
                   start_vel=(0.0, 3.0), target_vel=(0.0, -8.0))
     table = TABLE_HYPER8_PATH if v["hyper"] == "hyper8path" else TABLE_HYPER8
     return cfg, scene, np.ascontiguousarray(table[:cfg.G], dtype=np.float32)
+
+
+# Benchmark functions of Table BFs.
+BF_SPHERE, BF_ROSENBROCK, BF_RASTRIGIN, BF_GRIEWANK = 1, 2, 3, 4
+BF_NAMES = {BF_SPHERE: "Sphere", BF_ROSENBROCK: "Rosenbrock", BF_RASTRIGIN: "Rastrigin",
+            BF_GRIEWANK: "Griewank"}
+
+
+@dataclass
+class BFConfig:
+    """DTPSO on a benchmark function (mirrors ``sepso_bf_config`` in include/sepso.h):
+    ``runs`` independent swarms of G groups x N particles over [lo, hi]^D, a fixed
+    number of iterations (also the T of Eq. TOF_omega), no PI and no AT."""
+    fn: int = BF_SPHERE
+    D: int = 30
+    G: int = 8
+    N: int = 10
+    lo: float = -600.0
+    hi: float = 600.0
+    max_iters: int = 1400
+    seed: int = 0
+    run_id: int = 0            # Philox counter word 3 of run 0; run r uses run_id + r
+    runs: int = 1
+
+    def with_(self, **kw) -> "BFConfig":
+        return replace(self, **kw)
+
+
+def bf_standard(fn: int, seed: int = 0, trials: int = 50):
+    """Standard benchmark run of Sec. 4.1.1: D = 30 over [-600, 600]^30 (Table BFs),
+    80 particles as 8 groups x 10 with the Table hyper8 rows, 1400 iterations,
+    ``trials`` independent trials as runs of one launch -> (config, hyper)."""
+    cfg = BFConfig(fn=fn, D=30, G=8, N=10, max_iters=1400, seed=seed, runs=trials)
+    return cfg, np.ascontiguousarray(TABLE_HYPER8, dtype=np.float32)
+
+
+def bf_large(fn: int, seed: int = 0, iters: int = 1400):
+    """Large-scale run of Sec. 4.1.2: N = 16K particles (8 groups x 2048) of D = 1K
+    over [-600, 600]^D, Table hyper8 rows, 1400 iterations -> (config, hyper)."""
+    cfg = BFConfig(fn=fn, D=1000, G=8, N=2048, max_iters=iters, seed=seed, runs=1)
+    return cfg, np.ascontiguousarray(TABLE_HYPER8, dtype=np.float32)
 
 
 def random_paths(seed: int, n: int, T: int, W: float = 400.0, H: float = 400.0) -> np.ndarray:
