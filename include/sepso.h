@@ -594,6 +594,75 @@ int64_t sepso_launch_count(sepso_handle h);
 const char* sepso_strerror(int code);
 const char* sepso_last_error(void);
 
+/* ------------------------------------------------------------------------- */
+/* Benchmark functions (Table BFs; Secs. 4.1.1 and 4.1.2): DTPSO with the     */
+/* objective BF1 Sphere, BF2 Rosenbrock, BF3 Rastrigin or BF4 Griewank over   */
+/* the box [lo, hi]^D.  The iteration is the planner's (Algorithm 1: fitness, */
+/* Pbest/Gbest/Tbest with the strictly-better rule and lowest-index ties,     */
+/* Eq. TOF_omega over max_iters, Eq. TOF_V with C3 and clipping to            */
+/* V_range = V_limit (hi - lo), Eq. TOF_X clipped to the box); no PI, no AT.  */
+/* Textbook definitions, index i = 1..D:                                      */
+/*   BF1 sum x_i^2;  BF2 sum_{i<D} 100 (x_{i+1} - x_i^2)^2 + (x_i - 1)^2;     */
+/*   BF3 10 D + sum x_i^2 - 10 cos(2 pi x_i);                                  */
+/*   BF4 1 + sum x_i^2 / 4000 - prod cos(x_i / sqrt i).                        */
+/* ------------------------------------------------------------------------- */
+typedef struct sepso_bf_config {
+  int32_t fn;         /* 1..4: BF1..BF4                                         */
+  int32_t D;          /* coordinates per particle, 1..16384                     */
+  int32_t G;          /* groups, 1..32                                          */
+  int32_t N;          /* particles per group (G x N + G + 1 < 2^30)             */
+  float lo, hi;       /* X_range per coordinate, lo < hi, finite                */
+  int32_t max_iters;  /* iterations of sepso_bf_run_async; T of Eq. TOF_omega   */
+  int32_t runs;       /* independent swarms (trials); runs x G <= 4096          */
+  uint64_t seed;      /* Philox key                                             */
+  uint32_t run_id;    /* Philox counter word 3 of run 0; run r uses run_id + r  */
+} sepso_bf_config;
+
+typedef struct sepso_bf_ctx* sepso_bf_handle;
+
+/* Device workspace for a configuration: about runs x G x N x D x 20 bytes (X, V
+ * and two Pbest buffers, FP32) plus small tables.  Errors: EINVAL. */
+int sepso_bf_workspace_size(const sepso_bf_config* c, size_t* bytes);
+/* Create a handle on a caller-owned device workspace (256-byte aligned, at least
+ * sepso_bf_workspace_size bytes; cleared here) and stream.  The caller keeps both
+ * alive until sepso_bf_destroy.  Errors: EINVAL, ENOSPC (size or alignment),
+ * ERANGE (the iteration kernel does not fit an SM), ECUDA, ENOMEM. */
+int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, void* stream, sepso_bf_handle* out);
+int sepso_bf_destroy(sepso_bf_handle h);
+/* hyper: host G x 6 rows (C1, C2, C3, w_init, w_end, V_limit), Table hyper8
+ * layout, for one run or (run = -1) for every run; finite, V_limit >= 0.  Syncs
+ * the stream.  Errors: EINVAL, ECUDA. */
+int sepso_bf_set_hyper(sepso_bf_handle h, const float* hyper, int32_t run);
+/* One whole run of every swarm on the stream: initialisation (X uniform over the
+ * box, V uniform in +-V_range; Philox streams as the planner's), max_iters
+ * iterations, then the bests.  use_graph != 0 captures the launches once into a
+ * CUDA graph and replays it.  Errors: ESTATE (no hyper-parameters), ECUDA. */
+int sepso_bf_run_async(sepso_bf_handle h, int32_t use_graph);
+/* Continue every swarm for iters more iterations (after a run or a loaded state). */
+int sepso_bf_step(sepso_bf_handle h, int32_t iters);
+int sepso_bf_sync(sepso_bf_handle h);
+/* Tbest of a run: best_x host float[D] (or NULL), best_fit host float (or NULL),
+ * iterations done.  Syncs the stream.  Errors: EINVAL, ESTATE, ECUDA. */
+int sepso_bf_read(sepso_bf_handle h, int32_t run, float* best_x, float* best_fit, int32_t* iters);
+/* Tbest fitness after each of the first max_iters iterations: host float[max_iters]. */
+int sepso_bf_history(sepso_bf_handle h, int32_t run, float* hist);
+/* Swarm state of one run in host arrays (any may be NULL): X, V, P float[G*N*D]
+ * (particle-major), Pfit float[G*N], Gb float[G*D], Gfit float[G], Tb float[D],
+ * Tfit float[1], k = iterations done.  Syncs.  Errors: EINVAL, ESTATE, ECUDA. */
+int sepso_bf_get_state(sepso_bf_handle h, int32_t run, float* X, float* V, float* P, float* Pfit, float* Gb,
+                       float* Gfit, float* Tb, float* Tfit, int32_t* k);
+/* Load the same arrays (all required; X, V, P finite, no NaN fitness) as the state
+ * after k iterations; with several runs, k must match theirs.  The next step
+ * continues with iteration k + 1.  Syncs.  Errors: EINVAL, ECUDA. */
+int sepso_bf_set_state(sepso_bf_handle h, int32_t run, const float* X, const float* V, const float* P,
+                       const float* Pfit, const float* Gb, const float* Gfit, const float* Tb, const float* Tfit,
+                       int32_t k);
+/* Fitness of n rows of a device array X (row pitch ldx >= D floats) into device
+ * F[n], on stream.  Errors: EINVAL, ECUDA. */
+int sepso_bf_evaluate(int32_t fn, int32_t D, int32_t n, const float* X, int32_t ldx, float* F, void* stream);
+int64_t sepso_bf_launch_count(sepso_bf_handle h);
+const char* sepso_bf_last_error(void);
+
 /* Auto Truncation window criterion (Sec. 3.3.4, first criterion) on its own, for
  * checking: for each of `count` windows, whether the population standard deviation
  * of the ns[i] newest entries of the ring win[i*tw .. i*tw+tw) (head heads[i], the

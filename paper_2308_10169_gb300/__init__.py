@@ -8,7 +8,7 @@ The CUDA library is required: nothing here falls back to a CPU implementation.
 from .inputs import (AT_OFF, AT_STALL, AT_STD_WINDOW, TABLE_HYPER8, TABLE_HYPER8_PATH, Scene,
                      SepsoConfig, dynamic_workload, sample_hyper, static_workload)
 
-__all__ = ["Planner", "BatchPlanner", "Server", "Prior", "SepsoConfig", "Scene", "static_workload", "dynamic_workload",
+__all__ = ["Planner", "BatchPlanner", "BFPlanner", "Server", "Prior", "SepsoConfig", "Scene", "static_workload", "dynamic_workload",
            "sample_hyper", "TABLE_HYPER8", "TABLE_HYPER8_PATH", "AT_OFF", "AT_STALL",
            "AT_STD_WINDOW"]
 
@@ -26,4 +26,7 @@ def __getattr__(name):
     if name == "BatchPlanner":
         from .planner import BatchPlanner
         return BatchPlanner
+    if name == "BFPlanner":
+        from .planner import BFPlanner
+        return BFPlanner
     raise AttributeError(name)

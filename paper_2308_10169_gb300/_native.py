@@ -103,6 +103,19 @@ def make_config(cfg) -> Config:
                   circle_split=cfg.circle_split, fitness_mode=cfg.fitness_mode)
 
 
+class BFConfig(ctypes.Structure):
+    """``sepso_bf_config`` of include/sepso.h."""
+    _fields_ = [("fn", ctypes.c_int32), ("D", ctypes.c_int32), ("G", ctypes.c_int32),
+                ("N", ctypes.c_int32), ("lo", ctypes.c_float), ("hi", ctypes.c_float),
+                ("max_iters", ctypes.c_int32), ("runs", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32)]
+
+
+def bf_config_struct(cfg) -> BFConfig:
+    return BFConfig(fn=cfg.fn, D=cfg.D, G=cfg.G, N=cfg.N, lo=cfg.lo, hi=cfg.hi,
+                    max_iters=cfg.max_iters, runs=cfg.runs, seed=cfg.seed, run_id=cfg.run_id)
+
+
 # Every exported entry point with (restype, argtypes); the tests check the list
 # against include/sepso.h.
 _vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
@@ -191,6 +204,20 @@ SIGNATURES = {
                                           _vp, _i32, _vp, _i32, _vp, _i32, ctypes.POINTER(GemmExtra), _i32,
                                           _vp]),
     "sepso_at_window_test": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp]),
+    "sepso_bf_workspace_size": (ctypes.c_int, [ctypes.POINTER(BFConfig), ctypes.POINTER(_sz)]),
+    "sepso_bf_create": (ctypes.c_int, [ctypes.POINTER(BFConfig), _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    "sepso_bf_destroy": (ctypes.c_int, [_vp]),
+    "sepso_bf_set_hyper": (ctypes.c_int, [_vp, _vp, _i32]),
+    "sepso_bf_run_async": (ctypes.c_int, [_vp, _i32]),
+    "sepso_bf_step": (ctypes.c_int, [_vp, _i32]),
+    "sepso_bf_sync": (ctypes.c_int, [_vp]),
+    "sepso_bf_read": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "sepso_bf_history": (ctypes.c_int, [_vp, _i32, _vp]),
+    "sepso_bf_get_state": (ctypes.c_int, [_vp, _i32] + [_vp] * 9),
+    "sepso_bf_set_state": (ctypes.c_int, [_vp, _i32] + [_vp] * 8 + [_i32]),
+    "sepso_bf_evaluate": (ctypes.c_int, [_i32, _i32, _i32, _vp, _i32, _vp, _vp]),
+    "sepso_bf_launch_count": (ctypes.c_int64, [_vp]),
+    "sepso_bf_last_error": (ctypes.c_char_p, []),
     "sepso_watchdog_selftest": (ctypes.c_int, [_i32, ctypes.POINTER(_i32), _vp]),
     "sepso_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sepso_last_error": (ctypes.c_char_p, []),
@@ -234,6 +261,13 @@ def check_server(code: int):
 def check_prior(code: int):
     if code != SEPSO_OK:
         msg = lib().sepso_prior_last_error()
+        raise SepsoError(code, msg.decode() if msg else "")
+    return code
+
+
+def check_bf(code: int):
+    if code != SEPSO_OK:
+        msg = lib().sepso_bf_last_error()
         raise SepsoError(code, msg.decode() if msg else "")
     return code
 

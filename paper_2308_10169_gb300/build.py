@@ -16,7 +16,8 @@ INCLUDE = ROOT / "include"
 BUILD = PKG / "_build"
 LIB = BUILD / "libsepso.so"
 
-SOURCES = ["sepso_kernels.cu", "sepso_api.cu", "sepso_batch.cu", "sepso_server.cu", "sepso_mlp.cu"]
+SOURCES = ["sepso_kernels.cu", "sepso_api.cu", "sepso_batch.cu", "sepso_server.cu", "sepso_mlp.cu",
+           "sepso_bf.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -1,0 +1,797 @@
+// sepso_bf.cu -- DTPSO on the benchmark functions of Table BFs (BF1 Sphere, BF2
+// Rosenbrock, BF3 Rastrigin, BF4 Griewank): the tensor-form iteration of Sec. 3.1 /
+// Algorithm 1 with a closed-form objective over the box [lo, hi]^D.  Sized for the
+// large-scale case of Sec. 4.1.2 (16K particles x 1K coordinates: 16M scalars per
+// tensor, about 330 MB of HBM traffic per iteration) as well as the standard case of
+// Sec. 4.1.1 (80 particles x 30 coordinates, many independent trials as runs).
+//
+// One launch per iteration; a CUDA graph holds a whole run.  Launch j (1-based):
+//   1. (kUpdate) the velocity and position update of iteration j - 1 (Eqs.
+//      TOF_omega, TOF_V with clipping to V_range, TOF_X with clipping to X_range),
+//      from the bests of iteration j - 1;
+//   2. (kEval) the fitness of the positions (iteration j) and the Pbest update,
+//      and this launch's candidates for iteration j's Gbest.
+// A run of K iterations is: init, launch 1 (kEval), launches 2..K (both), launch
+// K + 1 (kUpdate only), so that the state after it is the state of Algorithm 1
+// after K whole iterations (positions updated K times); a later step starts with
+// a kEval-only launch.
+// One warp owns one particle: its row of X, V and Pbest streams through once
+// (float4), the new position row is kept in shared memory for the fitness, and an
+// improved Pbest row is written from there.
+//
+// Bests cross the kernel boundary as 64-bit keys
+//   ordered fitness (32) | priority (1) | particle (30) | Pbest parity (1),
+// so that an atomicMin picks the lowest fitness, then the previous holder (priority
+// 0: Eq. DPPSO's "strictly better" rule keeps the old best on a tie), then the
+// lowest particle index -- the oracle's order.  A particle's Pbest row alternates
+// between two buffers (its parity bit) each time it improves, so the row a key names
+// is never overwritten in the launch that reads it: the holder of a best can only
+// write the other parity, and it must improve again (and so replace itself as the
+// holder) before it writes the first one again.  Keys of three consecutive
+// iterations rotate (read j - 1, write j, clear j + 1); the Tbest holder is kept
+// in two slots.  Rows of a loaded state live in an "external" table addressed by
+// particle numbers >= M.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sepso.h"
+#include "sepso_device.cuh"
+
+namespace sepso {
+namespace {
+
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr int kUpdate = 1, kEval = 2;
+constexpr int kMaxD = 16384;
+constexpr int kMaxRG = 4096;           // runs x groups: the CTA's key table
+constexpr int kSmemRows = 160 * 1024;  // shared-memory budget of the row buffers
+
+struct BfParams {
+  int fn, D, Dp, G, N, M, R, K, hist_len;
+  float lo, hi;
+  uint32_t key0, key1, run_id;
+  float* X;                   // R*M rows of Dp
+  float* V;                   // R*M rows of Dp
+  float* P;                   // 2 parities x R*M rows of Dp
+  float* Pfit;                // R*M
+  unsigned char* pcur;        // R*M: parity of the current Pbest row
+  unsigned long long* keys;   // 3 x R*G
+  unsigned long long* thold;  // 2 x R
+  const float* hyper;         // R*G*6 (C1, C2, C3, w_init, w_end, V_limit)
+  float* ext;                 // R x (G+1) rows of Dp: loaded Gbest rows, then Tbest
+  float* hist;                // R x hist_len: Tbest fitness after each iteration
+  float *Gb, *Gfit, *Tb, *Tfit;  // bests after the last launch (finish kernel)
+};
+
+// Order-preserving map of a float onto uint32 (any sign; NaN is never posted).
+__device__ __forceinline__ uint32_t ord_of(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float float_of_ord(uint32_t o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+__device__ __forceinline__ unsigned long long make_key(float fit, uint32_t prio, uint32_t idx, uint32_t par) {
+  return ((unsigned long long)ord_of(fit) << 32) | ((unsigned long long)prio << 31) |
+         ((unsigned long long)(idx & 0x3fffffffu) << 1) | (unsigned long long)(par & 1u);
+}
+__device__ __forceinline__ uint32_t key_idx(unsigned long long k) { return (uint32_t)(k >> 1) & 0x3fffffffu; }
+__device__ __forceinline__ uint32_t key_par(unsigned long long k) { return (uint32_t)k & 1u; }
+
+// The row a key names (null: no best yet, a zero row).
+__device__ __forceinline__ const float* key_row(const BfParams& p, int r, unsigned long long k) {
+  if (k == kEmpty) return nullptr;
+  const uint32_t idx = key_idx(k);
+  if ((int)idx < p.M)
+    return p.P + ((size_t)key_par(k) * p.R * p.M + (size_t)r * p.M + idx) * p.Dp;
+  return p.ext + ((size_t)r * (p.G + 1) + (idx - p.M)) * p.Dp;
+}
+
+// Tbest after an iteration: the best group key (lowest fitness, then lowest group)
+// if strictly better than the previous holder, else the previous holder.
+__device__ __forceinline__ unsigned long long resolve_T(const unsigned long long* gk, int G,
+                                                        unsigned long long told) {
+  unsigned long long best = kEmpty;
+  for (int g = 0; g < G; ++g) {
+    const unsigned long long k = gk[g];
+    if (k != kEmpty && (best == kEmpty || (k >> 32) < (best >> 32))) best = k;
+  }
+  if (best != kEmpty && (told == kEmpty || (best >> 32) < (told >> 32))) return best;
+  return told;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_prod(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// BF1..BF4 of one row (any address space), the whole warp; every lane gets the value.
+//   Sphere      sum x_i^2
+//   Rosenbrock  sum_{i<D} 100 (x_{i+1} - x_i^2)^2 + (x_i - 1)^2
+//   Rastrigin   10 D + sum x_i^2 - 10 cos(2 pi x_i)
+//   Griewank    1 + sum x_i^2 / 4000 - prod cos(x_i / sqrt(i)),  i = 1..D
+template <int FN>
+__device__ __forceinline__ float bf_row(const float* s, int D, int lane) {
+  float acc = 0.0f;
+  if (FN == 1) {
+    for (int i = lane; i < D; i += 32) acc = fmaf(s[i], s[i], acc);
+    return warp_sum(acc);
+  } else if (FN == 2) {
+    for (int i = lane; i + 1 < D; i += 32) {
+      const float x = s[i];
+      const float a = fmaf(-x, x, s[i + 1]), b = x - 1.0f;
+      acc += fmaf(100.0f * a, a, b * b);
+    }
+    return warp_sum(acc);
+  } else if (FN == 3) {
+    for (int i = lane; i < D; i += 32) {
+      const float x = s[i];
+      acc += fmaf(x, x, -10.0f * cospif(2.0f * x));
+    }
+    return fmaf(10.0f, (float)D, warp_sum(acc));
+  } else {
+    float prod = 1.0f;
+    for (int i = lane; i < D; i += 32) {
+      const float x = s[i];
+      acc = fmaf(x, x, acc);
+      prod *= cosf(__fdiv_rn(x, sqrtf((float)(i + 1))));
+    }
+    const float sum = warp_sum(acc);
+    prod = warp_prod(prod);
+    return 1.0f + sum / 4000.0f - prod;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Initialisation (Algorithm 1): X uniform over [lo, hi]^D, V uniform in +-V_range
+// with V_range = V_limit (hi - lo), Pbest row = X (parity 0), Pbest fitness +inf, no
+// bests.  Four coordinates per Philox draw (counter: coordinate chunk, particle,
+// stream, run), as in the path planner.
+// ---------------------------------------------------------------------------
+__global__ void bf_init_kernel(const BfParams p) {
+  const size_t nch = (size_t)p.Dp / 4;
+  const size_t total = (size_t)p.R * p.M * nch;
+  const float ext = p.hi - p.lo;
+  for (size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+       it += (size_t)gridDim.x * blockDim.x) {
+    const size_t q = it / nch;
+    const int c = (int)(it - q * nch);
+    const int r = (int)(q / p.M), pi = (int)(q - (size_t)r * p.M);
+    const int g = pi / p.N;
+    const float vmax = p.hyper[((size_t)r * p.G + g) * 6 + 5] * ext;
+    const uint4 ux = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitX, 0u, p.run_id + (uint32_t)r);
+    const uint4 uv = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitV, 0u, p.run_id + (uint32_t)r);
+    float xs[4], vs[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const bool in = 4 * c + e < p.D;
+      xs[e] = in ? p.lo + lane_of(ux, e) * ext : 0.0f;
+      vs[e] = in ? (2.0f * lane_of(uv, e) - 1.0f) * vmax : 0.0f;
+    }
+    const float4 x4 = make_float4(xs[0], xs[1], xs[2], xs[3]);
+    const float4 v4 = make_float4(vs[0], vs[1], vs[2], vs[3]);
+    reinterpret_cast<float4*>(p.X + q * p.Dp)[c] = x4;
+    reinterpret_cast<float4*>(p.V + q * p.Dp)[c] = v4;
+    reinterpret_cast<float4*>(p.P + q * p.Dp)[c] = x4;
+    reinterpret_cast<float4*>(p.P + ((size_t)p.R * p.M + q) * p.Dp)[c] = x4;
+    if (c == 0) {
+      p.Pfit[q] = INFINITY;
+      p.pcur[q] = 0;
+    }
+  }
+  const size_t nk = (size_t)3 * p.R * p.G;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += (size_t)gridDim.x * blockDim.x) {
+    p.keys[i] = kEmpty;
+    if (i < (size_t)2 * p.R) p.thold[i] = kEmpty;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One iteration launch (see the file comment).  j is the iteration whose fitness
+// this launch evaluates; the update it applies first is iteration j - 1's.
+// ---------------------------------------------------------------------------
+template <int FN>
+__global__ void __launch_bounds__(256) bf_iter_kernel(const BfParams p, int j, int mode) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int RG = p.R * p.G;
+  unsigned long long* ck = reinterpret_cast<unsigned long long*>(smem);
+  float* srow = reinterpret_cast<float*>(smem + ((size_t)RG * 8 + 15) / 16 * 16) + (size_t)warp * p.Dp;
+  for (int i = threadIdx.x; i < RG; i += blockDim.x) ck[i] = kEmpty;
+
+  const unsigned long long* kprev = p.keys + (size_t)((j + 2) % 3) * RG;  // iteration j - 1
+  unsigned long long* kcur = p.keys + (size_t)(j % 3) * RG;
+  if (blockIdx.x == 0) {
+    unsigned long long* knext = p.keys + (size_t)((j + 1) % 3) * RG;   // read last in launch j - 1
+    for (int i = threadIdx.x; i < RG; i += blockDim.x) knext[i] = kEmpty;
+  }
+  __syncthreads();
+
+  const float ext = p.hi - p.lo;
+  const int nch = p.Dp >> 2;
+  const size_t total = (size_t)p.R * p.M;
+  for (size_t q = (size_t)blockIdx.x * nwarps + warp; q < total; q += (size_t)gridDim.x * nwarps) {
+    const int r = (int)(q / p.M), pi = (int)(q - (size_t)r * p.M);
+    const int g = pi / p.N;
+    float4* xr = reinterpret_cast<float4*>(p.X + q * p.Dp);
+    float4* s4 = reinterpret_cast<float4*>(srow);
+    const unsigned par = p.pcur[q];
+    if (mode & kUpdate) {
+      // Bests of iteration j - 1: this group's key, and Tbest from all group keys
+      // and the previous Tbest holder.
+      const unsigned long long* gk = kprev + (size_t)r * p.G;
+      const unsigned long long told = p.thold[(size_t)(j % 2) * p.R + r];   // iteration j - 2
+      const unsigned long long tk = resolve_T(gk, p.G, told);
+      if (pi == 0 && lane == 0) {
+        p.thold[(size_t)((j + 1) % 2) * p.R + r] = tk;                      // iteration j - 1
+        if (j - 2 < p.hist_len)
+          p.hist[(size_t)r * p.hist_len + (j - 2)] = tk == kEmpty ? INFINITY : float_of_ord((uint32_t)(tk >> 32));
+      }
+      const float4* gr = reinterpret_cast<const float4*>(key_row(p, r, gk[g]));
+      const float4* tr = reinterpret_cast<const float4*>(key_row(p, r, tk));
+      const float* hy = p.hyper + ((size_t)r * p.G + g) * 6;
+      const float c1 = hy[0], c2 = hy[1], c3 = hy[2], w_init = hy[3], w_end = hy[4];
+      const float vmax = hy[5] * ext;
+      const int k = j - 1;
+      const float w = w_init - (w_init - w_end) / (float)p.K * (float)k;
+      const uint4 rr = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)pi, kStreamVel, 0u, p.run_id + (uint32_t)r);
+      const float a1 = c1 * u01(rr.x), a2 = c2 * u01(rr.y), a3 = c3 * u01(rr.z);
+      const bool need_T = c3 != 0.0f;
+      float4* vr = reinterpret_cast<float4*>(p.V + q * p.Dp);
+      const float4* pr = reinterpret_cast<const float4*>(p.P + ((size_t)par * total + q) * p.Dp);
+      const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      for (int c = lane; c < nch; c += 32) {
+        float4 x = xr[c], v = vr[c];
+        const float4 pb = pr[c];
+        const float4 gb = gr ? gr[c] : zero;
+        const float4 tb = (need_T && tr) ? tr[c] : zero;
+        float* xe = &x.x;
+        float* ve = &v.x;
+        const float* pe = &pb.x;
+        const float* ge = &gb.x;
+        const float* te = &tb.x;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (4 * c + e < p.D) {
+            float vv = w * ve[e];
+            vv = fmaf(a1, pe[e] - xe[e], vv);
+            vv = fmaf(a2, ge[e] - xe[e], vv);
+            if (need_T) vv = fmaf(a3, te[e] - xe[e], vv);
+            vv = fminf(fmaxf(vv, -vmax), vmax);
+            ve[e] = vv;
+            xe[e] = fminf(fmaxf(xe[e] + vv, p.lo), p.hi);
+          }
+        }
+        xr[c] = x;
+        vr[c] = v;
+        s4[c] = x;
+      }
+      // The previous holder of this group's best keeps it on a tie (priority 0).
+      if (pi == 0 && lane < p.G) {
+        const unsigned long long k0 = gk[lane];
+        if (k0 != kEmpty) atomicMin(&ck[r * p.G + lane], k0 & ~(1ull << 31));
+      }
+    } else {
+      for (int c = lane; c < nch; c += 32) s4[c] = xr[c];
+    }
+    __syncwarp();
+    if (!(mode & kEval)) continue;
+
+    // Fitness of iteration j, Pbest update (strictly better only).
+    const float F = bf_row<FN>(srow, p.D, lane);
+    float pf = p.Pfit[q];
+    unsigned npar = par;
+    if (F < pf) {
+      npar = par ^ 1u;
+      float4* dst = reinterpret_cast<float4*>(p.P + ((size_t)npar * total + q) * p.Dp);
+      for (int c = lane; c < nch; c += 32) dst[c] = s4[c];
+      pf = F;
+      if (lane == 0) {
+        p.Pfit[q] = F;
+        p.pcur[q] = (unsigned char)npar;
+      }
+    }
+    if (lane == 0 && isfinite(pf)) atomicMin(&ck[r * p.G + g], make_key(pf, 1u, (uint32_t)pi, npar));
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < RG; i += blockDim.x)
+    if (ck[i] != kEmpty) atomicMin(&kcur[i], ck[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Bests after iteration k (the last launch): Gbest rows and fitness per group, the
+// Tbest row and fitness, the last history entry.  One block per (run, slot), slot
+// G = Tbest.  Reads only; a later launch continues from the same keys.
+// ---------------------------------------------------------------------------
+__global__ void bf_finish_kernel(const BfParams p, int k) {
+  const int r = blockIdx.x / (p.G + 1), s = blockIdx.x - r * (p.G + 1);
+  const int RG = p.R * p.G;
+  const unsigned long long* gk = p.keys + (size_t)(k % 3) * RG + (size_t)r * p.G;
+  unsigned long long key;
+  float* out;
+  if (s < p.G) {
+    key = k > 0 ? gk[s] : kEmpty;
+    out = p.Gb + ((size_t)r * p.G + s) * p.Dp;
+    if (threadIdx.x == 0) p.Gfit[(size_t)r * p.G + s] = key == kEmpty ? INFINITY : float_of_ord((uint32_t)(key >> 32));
+  } else {
+    key = k > 0 ? resolve_T(gk, p.G, p.thold[(size_t)((k + 1) % 2) * p.R + r]) : kEmpty;
+    out = p.Tb + (size_t)r * p.Dp;
+    const float tf = key == kEmpty ? INFINITY : float_of_ord((uint32_t)(key >> 32));
+    if (threadIdx.x == 0) {
+      p.Tfit[r] = tf;
+      if (k >= 1 && k - 1 < p.hist_len) p.hist[(size_t)r * p.hist_len + (k - 1)] = tf;
+    }
+  }
+  const float* src = key_row(p, r, key);
+  for (int i = threadIdx.x; i < p.Dp; i += blockDim.x) out[i] = src ? src[i] : 0.0f;
+}
+
+// Fitness of n rows (pitch ldx floats), one warp per row.
+template <int FN>
+__global__ void bf_eval_kernel(const float* X, int ldx, int D, int n, float* F) {
+  const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  for (int i = blockIdx.x * nwarps + (threadIdx.x >> 5); i < n; i += gridDim.x * nwarps) {
+    const float f = bf_row<FN>(X + (size_t)i * ldx, D, lane);
+    if (lane == 0) F[i] = f;
+  }
+}
+
+}  // namespace sepso
+
+// ===========================================================================
+// Host side: the sepso_bf_* C ABI.
+// ===========================================================================
+namespace sepso {
+namespace {
+
+thread_local std::string g_bf_error;
+
+int bffail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int bffail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_bf_error = buf;
+  return code;
+}
+
+#define BFCUDA(expr)                                                                         \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) return bffail(SEPSO_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct BfLayout {
+  size_t X, V, P, Pfit, pcur, keys, thold, hyper, ext, hist, Gb, Gfit, Tb, Tfit, total;
+};
+
+int padded(int D) { return (D + 3) & ~3; }
+
+BfLayout bf_layout(const sepso_bf_config& c) {
+  const size_t Dp = (size_t)padded(c.D), R = (size_t)c.runs, G = (size_t)c.G;
+  const size_t RM = R * G * (size_t)c.N;
+  BfLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += a256(bytes);
+    return at;
+  };
+  L.X = take(RM * Dp * 4);
+  L.V = take(RM * Dp * 4);
+  L.P = take(2 * RM * Dp * 4);
+  L.Pfit = take(RM * 4);
+  L.pcur = take(RM);
+  L.keys = take(3 * R * G * 8);
+  L.thold = take(2 * R * 8);
+  L.hyper = take(R * G * 6 * 4);
+  L.ext = take(R * (G + 1) * Dp * 4);
+  L.hist = take(R * (size_t)c.max_iters * 4);
+  L.Gb = take(R * G * Dp * 4);
+  L.Gfit = take(R * G * 4);
+  L.Tb = take(R * Dp * 4);
+  L.Tfit = take(R * 4);
+  L.total = off;
+  return L;
+}
+
+int bf_validate(const sepso_bf_config* c) {
+  if (!c) return bffail(SEPSO_EINVAL, "NULL config");
+  if (c->fn < 1 || c->fn > 4) return bffail(SEPSO_EINVAL, "fn=%d is not one of BF1..BF4", c->fn);
+  if (c->D < 1 || c->D > kMaxD) return bffail(SEPSO_EINVAL, "D=%d outside [1, %d]", c->D, kMaxD);
+  if (c->G < 1 || c->G > 32) return bffail(SEPSO_EINVAL, "G=%d outside [1, 32]", c->G);
+  if (c->N < 1) return bffail(SEPSO_EINVAL, "N=%d below 1", c->N);
+  if (c->runs < 1) return bffail(SEPSO_EINVAL, "runs=%d below 1", c->runs);
+  if (c->max_iters < 1) return bffail(SEPSO_EINVAL, "max_iters=%d below 1", c->max_iters);
+  if (!std::isfinite(c->lo) || !std::isfinite(c->hi) || !(c->lo < c->hi))
+    return bffail(SEPSO_EINVAL, "box [%g, %g] is empty or not finite", (double)c->lo, (double)c->hi);
+  if ((long long)c->runs * c->G > kMaxRG)
+    return bffail(SEPSO_EINVAL, "runs x G = %lld above %d", (long long)c->runs * c->G, kMaxRG);
+  const long long M = (long long)c->G * c->N;
+  if (M + c->G + 1 >= (1ll << 30)) return bffail(SEPSO_EINVAL, "G x N = %lld above 2^30", M);
+  if ((long long)c->runs * M > (1ll << 31) - 1) return bffail(SEPSO_EINVAL, "runs x G x N above 2^31");
+  return SEPSO_OK;
+}
+
+template <int FN>
+cudaError_t iter_attr(size_t smem) {
+  return cudaFuncSetAttribute(bf_iter_kernel<FN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+template <int FN>
+cudaError_t iter_occ(int* bps, int threads, size_t smem) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, bf_iter_kernel<FN>, threads, smem);
+}
+
+}  // namespace
+}  // namespace sepso
+
+using namespace sepso;
+
+struct sepso_bf_ctx {
+  sepso_bf_config c;
+  BfLayout L;
+  BfParams p;
+  char* ws = nullptr;
+  cudaStream_t stream = nullptr;
+  int threads = 0, grid = 0, init_grid = 0;
+  size_t smem = 0;
+  int64_t k = -1;  // iterations done; -1 before the first run or state
+  int64_t launches = 0;
+  bool hyper_set = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+cudaError_t launch_iter(sepso_bf_ctx* h, int j, int mode) {
+  switch (h->c.fn) {
+    case 1: bf_iter_kernel<1><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
+    case 2: bf_iter_kernel<2><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
+    case 3: bf_iter_kernel<3><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
+    default: bf_iter_kernel<4><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(sepso_bf_ctx* h, int k) {
+  bf_finish_kernel<<<h->c.runs * (h->c.G + 1), 128, 0, h->stream>>>(h->p, k);
+  return cudaGetLastError();
+}
+
+// Iterations k0 + 1 .. k0 + n from a whole-iteration boundary, then the bests.
+int enqueue_iterations(sepso_bf_ctx* h, int k0, int n) {
+  for (int i = 1; i <= n; ++i) BFCUDA(launch_iter(h, k0 + i, i == 1 ? kEval : (kUpdate | kEval)));
+  BFCUDA(launch_iter(h, k0 + n + 1, kUpdate));
+  BFCUDA(launch_finish(h, k0 + n));
+  return SEPSO_OK;
+}
+
+// init + iterations 1..K + the bests, on h->stream.
+int enqueue_run(sepso_bf_ctx* h) {
+  bf_init_kernel<<<h->init_grid, 256, 0, h->stream>>>(h->p);
+  BFCUDA(cudaGetLastError());
+  return enqueue_iterations(h, 0, h->c.max_iters);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sepso_bf_last_error(void) { return g_bf_error.c_str(); }
+
+int sepso_bf_workspace_size(const sepso_bf_config* c, size_t* bytes) {
+  const int rc = bf_validate(c);
+  if (rc) return rc;
+  if (!bytes) return bffail(SEPSO_EINVAL, "NULL bytes");
+  *bytes = bf_layout(*c).total;
+  return SEPSO_OK;
+}
+
+int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, void* stream, sepso_bf_handle* out) {
+  int rc = bf_validate(c);
+  if (rc) return rc;
+  if (!out) return bffail(SEPSO_EINVAL, "NULL handle pointer");
+  const BfLayout L = bf_layout(*c);
+  if (!workspace || bytes < L.total)
+    return bffail(SEPSO_ENOSPC, "workspace of %zu bytes below the %zu needed", bytes, L.total);
+  if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return bffail(SEPSO_ENOSPC, "workspace not 256-byte aligned");
+  const int Dp = padded(c->D);
+  const int nwarps = std::max(1, std::min(8, kSmemRows / (Dp * 4)));
+  const size_t smem = ((size_t)c->runs * c->G * 8 + 15) / 16 * 16 + (size_t)nwarps * Dp * 4;
+  int dev = 0, sms = 0, bps = 0;
+  BFCUDA(cudaGetDevice(&dev));
+  BFCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaError_t e = cudaSuccess;
+  switch (c->fn) {
+    case 1: e = iter_attr<1>(smem); if (e == cudaSuccess) e = iter_occ<1>(&bps, nwarps * 32, smem); break;
+    case 2: e = iter_attr<2>(smem); if (e == cudaSuccess) e = iter_occ<2>(&bps, nwarps * 32, smem); break;
+    case 3: e = iter_attr<3>(smem); if (e == cudaSuccess) e = iter_occ<3>(&bps, nwarps * 32, smem); break;
+    default: e = iter_attr<4>(smem); if (e == cudaSuccess) e = iter_occ<4>(&bps, nwarps * 32, smem); break;
+  }
+  if (e != cudaSuccess) return bffail(SEPSO_ECUDA, "iteration kernel attributes: %s", cudaGetErrorString(e));
+  if (bps < 1) return bffail(SEPSO_ERANGE, "iteration kernel does not fit an SM (%zu bytes of shared memory)", smem);
+  sepso_bf_ctx* h = new (std::nothrow) sepso_bf_ctx();
+  if (!h) return bffail(SEPSO_ENOMEM, "host allocation");
+  h->c = *c;
+  h->L = L;
+  h->ws = static_cast<char*>(workspace);
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->threads = nwarps * 32;
+  h->smem = smem;
+  const long long RM = (long long)c->runs * c->G * c->N;
+  h->grid = (int)std::min<long long>((RM + nwarps - 1) / nwarps, (long long)bps * sms);
+  const long long init_items = RM * (Dp / 4);
+  h->init_grid = (int)std::max<long long>(1, std::min<long long>((init_items + 255) / 256, 8ll * sms));
+  BfParams& p = h->p;
+  p.fn = c->fn;
+  p.D = c->D;
+  p.Dp = Dp;
+  p.G = c->G;
+  p.N = c->N;
+  p.M = c->G * c->N;
+  p.R = c->runs;
+  p.K = c->max_iters;
+  p.hist_len = c->max_iters;
+  p.lo = c->lo;
+  p.hi = c->hi;
+  p.key0 = (uint32_t)(c->seed & 0xffffffffu);
+  p.key1 = (uint32_t)(c->seed >> 32);
+  p.run_id = c->run_id;
+  char* w = h->ws;
+  p.X = reinterpret_cast<float*>(w + L.X);
+  p.V = reinterpret_cast<float*>(w + L.V);
+  p.P = reinterpret_cast<float*>(w + L.P);
+  p.Pfit = reinterpret_cast<float*>(w + L.Pfit);
+  p.pcur = reinterpret_cast<unsigned char*>(w + L.pcur);
+  p.keys = reinterpret_cast<unsigned long long*>(w + L.keys);
+  p.thold = reinterpret_cast<unsigned long long*>(w + L.thold);
+  p.hyper = reinterpret_cast<const float*>(w + L.hyper);
+  p.ext = reinterpret_cast<float*>(w + L.ext);
+  p.hist = reinterpret_cast<float*>(w + L.hist);
+  p.Gb = reinterpret_cast<float*>(w + L.Gb);
+  p.Gfit = reinterpret_cast<float*>(w + L.Gfit);
+  p.Tb = reinterpret_cast<float*>(w + L.Tb);
+  p.Tfit = reinterpret_cast<float*>(w + L.Tfit);
+  e = cudaMemsetAsync(workspace, 0, L.total, h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return bffail(SEPSO_ECUDA, "workspace clear: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return SEPSO_OK;
+}
+
+int sepso_bf_destroy(sepso_bf_handle h) {
+  if (!h) return SEPSO_OK;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  delete h;
+  return SEPSO_OK;
+}
+
+int sepso_bf_set_hyper(sepso_bf_handle h, const float* hyper, int32_t run) {
+  if (!h || !hyper) return bffail(SEPSO_EINVAL, "NULL argument");
+  if (run < -1 || run >= h->c.runs) return bffail(SEPSO_EINVAL, "run=%d outside [-1, %d)", run, h->c.runs);
+  const int G = h->c.G;
+  for (int i = 0; i < G * 6; ++i)
+    if (!std::isfinite(hyper[i])) return bffail(SEPSO_EINVAL, "hyper-parameter %d is not finite", i);
+  for (int g = 0; g < G; ++g)
+    if (hyper[g * 6 + 5] < 0.0f) return bffail(SEPSO_EINVAL, "V_limit of group %d is negative", g);
+  float* dst = reinterpret_cast<float*>(h->ws + h->L.hyper);
+  const int r0 = run < 0 ? 0 : run, r1 = run < 0 ? h->c.runs : run + 1;
+  for (int r = r0; r < r1; ++r)
+    BFCUDA(cudaMemcpyAsync(dst + (size_t)r * G * 6, hyper, (size_t)G * 6 * 4, cudaMemcpyHostToDevice, h->stream));
+  BFCUDA(cudaStreamSynchronize(h->stream));
+  if (run < 0) h->hyper_set = true;
+  return SEPSO_OK;
+}
+
+int sepso_bf_run_async(sepso_bf_handle h, int32_t use_graph) {
+  if (!h) return bffail(SEPSO_EINVAL, "NULL handle");
+  if (!h->hyper_set) return bffail(SEPSO_ESTATE, "run before set_hyper for every run");
+  if (!use_graph) {
+    const int rc = enqueue_run(h);
+    if (rc) return rc;
+  } else {
+    if (!h->exec) {
+      cudaStream_t cap = nullptr;
+      BFCUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      cudaStream_t keep = h->stream;
+      h->stream = cap;
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      int rc = SEPSO_OK;
+      if (e == cudaSuccess) rc = enqueue_run(h);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+      h->stream = keep;
+      cudaStreamDestroy(cap);
+      if (e != cudaSuccess || e2 != cudaSuccess || rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : bffail(SEPSO_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      h->graph = g;
+      BFCUDA(cudaGraphInstantiate(&h->exec, g, 0));
+    }
+    BFCUDA(cudaGraphLaunch(h->exec, h->stream));
+  }
+  h->launches += h->c.max_iters + 3;
+  h->k = h->c.max_iters;
+  return SEPSO_OK;
+}
+
+int sepso_bf_step(sepso_bf_handle h, int32_t iters) {
+  if (!h) return bffail(SEPSO_EINVAL, "NULL handle");
+  if (iters < 0) return bffail(SEPSO_EINVAL, "iters=%d is negative", iters);
+  if (h->k < 0) return bffail(SEPSO_ESTATE, "step before a run or a loaded state");
+  if (h->k + iters > (1ll << 30)) return bffail(SEPSO_EINVAL, "iteration count above 2^30");
+  if (iters == 0) return SEPSO_OK;
+  const int rc = enqueue_iterations(h, (int)h->k, iters);
+  if (rc) return rc;
+  h->k += iters;
+  h->launches += iters + 2;
+  return SEPSO_OK;
+}
+
+int sepso_bf_sync(sepso_bf_handle h) {
+  if (!h) return bffail(SEPSO_EINVAL, "NULL handle");
+  BFCUDA(cudaStreamSynchronize(h->stream));
+  return SEPSO_OK;
+}
+
+int sepso_bf_read(sepso_bf_handle h, int32_t run, float* best_x, float* best_fit, int32_t* iters) {
+  if (!h) return bffail(SEPSO_EINVAL, "NULL handle");
+  if (run < 0 || run >= h->c.runs) return bffail(SEPSO_EINVAL, "run=%d outside [0, %d)", run, h->c.runs);
+  if (h->k < 0) return bffail(SEPSO_ESTATE, "read before a run");
+  if (best_x)
+    BFCUDA(cudaMemcpyAsync(best_x, h->p.Tb + (size_t)run * h->p.Dp, (size_t)h->c.D * 4, cudaMemcpyDeviceToHost,
+                           h->stream));
+  if (best_fit) BFCUDA(cudaMemcpyAsync(best_fit, h->p.Tfit + run, 4, cudaMemcpyDeviceToHost, h->stream));
+  BFCUDA(cudaStreamSynchronize(h->stream));
+  if (iters) *iters = (int32_t)h->k;
+  return SEPSO_OK;
+}
+
+int sepso_bf_history(sepso_bf_handle h, int32_t run, float* hist) {
+  if (!h || !hist) return bffail(SEPSO_EINVAL, "NULL argument");
+  if (run < 0 || run >= h->c.runs) return bffail(SEPSO_EINVAL, "run=%d outside [0, %d)", run, h->c.runs);
+  BFCUDA(cudaMemcpyAsync(hist, h->p.hist + (size_t)run * h->p.hist_len, (size_t)h->p.hist_len * 4,
+                         cudaMemcpyDeviceToHost, h->stream));
+  BFCUDA(cudaStreamSynchronize(h->stream));
+  return SEPSO_OK;
+}
+
+int64_t sepso_bf_launch_count(sepso_bf_handle h) { return h ? h->launches : -1; }
+
+int sepso_bf_get_state(sepso_bf_handle h, int32_t run, float* X, float* V, float* P, float* Pfit, float* Gb,
+                       float* Gfit, float* Tb, float* Tfit, int32_t* k) {
+  if (!h) return bffail(SEPSO_EINVAL, "NULL handle");
+  if (run < 0 || run >= h->c.runs) return bffail(SEPSO_EINVAL, "run=%d outside [0, %d)", run, h->c.runs);
+  if (h->k < 0) return bffail(SEPSO_ESTATE, "no state before a run");
+  const BfParams& p = h->p;
+  const size_t D4 = (size_t)p.D * 4, Dp4 = (size_t)p.Dp * 4, M = (size_t)p.M, RM = (size_t)p.R * M;
+  const size_t q0 = (size_t)run * M;
+  cudaStream_t s = h->stream;
+  if (X) BFCUDA(cudaMemcpy2DAsync(X, D4, p.X + q0 * p.Dp, Dp4, D4, M, cudaMemcpyDeviceToHost, s));
+  if (V) BFCUDA(cudaMemcpy2DAsync(V, D4, p.V + q0 * p.Dp, Dp4, D4, M, cudaMemcpyDeviceToHost, s));
+  std::vector<float> P0, P1;
+  std::vector<unsigned char> par;
+  if (P) {
+    P0.resize(M * p.D);
+    P1.resize(M * p.D);
+    par.resize(M);
+    BFCUDA(cudaMemcpy2DAsync(P0.data(), D4, p.P + q0 * p.Dp, Dp4, D4, M, cudaMemcpyDeviceToHost, s));
+    BFCUDA(cudaMemcpy2DAsync(P1.data(), D4, p.P + (RM + q0) * p.Dp, Dp4, D4, M, cudaMemcpyDeviceToHost, s));
+    BFCUDA(cudaMemcpyAsync(par.data(), p.pcur + q0, M, cudaMemcpyDeviceToHost, s));
+  }
+  if (Pfit) BFCUDA(cudaMemcpyAsync(Pfit, p.Pfit + q0, M * 4, cudaMemcpyDeviceToHost, s));
+  if (Gb)
+    BFCUDA(cudaMemcpy2DAsync(Gb, D4, p.Gb + (size_t)run * p.G * p.Dp, Dp4, D4, p.G, cudaMemcpyDeviceToHost, s));
+  if (Gfit) BFCUDA(cudaMemcpyAsync(Gfit, p.Gfit + (size_t)run * p.G, (size_t)p.G * 4, cudaMemcpyDeviceToHost, s));
+  if (Tb) BFCUDA(cudaMemcpyAsync(Tb, p.Tb + (size_t)run * p.Dp, D4, cudaMemcpyDeviceToHost, s));
+  if (Tfit) BFCUDA(cudaMemcpyAsync(Tfit, p.Tfit + run, 4, cudaMemcpyDeviceToHost, s));
+  BFCUDA(cudaStreamSynchronize(s));
+  if (P)
+    for (size_t i = 0; i < M; ++i)
+      std::memcpy(P + i * p.D, (par[i] ? P1 : P0).data() + i * p.D, D4);
+  if (k) *k = (int32_t)h->k;
+  return SEPSO_OK;
+}
+
+int sepso_bf_set_state(sepso_bf_handle h, int32_t run, const float* X, const float* V, const float* P,
+                       const float* Pfit, const float* Gb, const float* Gfit, const float* Tb, const float* Tfit,
+                       int32_t k) {
+  if (!h || !X || !V || !P || !Pfit || !Gb || !Gfit || !Tb || !Tfit) return bffail(SEPSO_EINVAL, "NULL argument");
+  if (run < 0 || run >= h->c.runs) return bffail(SEPSO_EINVAL, "run=%d outside [0, %d)", run, h->c.runs);
+  if (k < 0) return bffail(SEPSO_EINVAL, "k=%d is negative", k);
+  if (h->k >= 0 && h->c.runs > 1 && k != h->k)
+    return bffail(SEPSO_EINVAL, "k=%d differs from the other runs' %lld", k, (long long)h->k);
+  const BfParams& p = h->p;
+  const size_t M = (size_t)p.M;
+  for (size_t i = 0; i < M * p.D; ++i)
+    if (!std::isfinite(X[i]) || !std::isfinite(V[i]) || !std::isfinite(P[i]))
+      return bffail(SEPSO_EINVAL, "X, V or P holds a non-finite value at %zu", i);
+  for (size_t i = 0; i < M; ++i)
+    if (std::isnan(Pfit[i])) return bffail(SEPSO_EINVAL, "Pfit[%zu] is NaN", i);
+  for (int g = 0; g < p.G; ++g)
+    if (std::isnan(Gfit[g])) return bffail(SEPSO_EINVAL, "Gfit[%d] is NaN", g);
+  if (std::isnan(Tfit[0])) return bffail(SEPSO_EINVAL, "Tfit is NaN");
+  const size_t D4 = (size_t)p.D * 4, Dp4 = (size_t)p.Dp * 4, RM = (size_t)p.R * M;
+  const size_t q0 = (size_t)run * M;
+  const int RG = p.R * p.G;
+  cudaStream_t s = h->stream;
+  BFCUDA(cudaMemcpy2DAsync(p.X + q0 * p.Dp, Dp4, X, D4, D4, M, cudaMemcpyHostToDevice, s));
+  BFCUDA(cudaMemcpy2DAsync(p.V + q0 * p.Dp, Dp4, V, D4, D4, M, cudaMemcpyHostToDevice, s));
+  BFCUDA(cudaMemcpy2DAsync(p.P + q0 * p.Dp, Dp4, P, D4, D4, M, cudaMemcpyHostToDevice, s));
+  BFCUDA(cudaMemcpy2DAsync(p.P + (RM + q0) * p.Dp, Dp4, P, D4, D4, M, cudaMemcpyHostToDevice, s));
+  BFCUDA(cudaMemsetAsync(p.pcur + q0, 0, M, s));
+  BFCUDA(cudaMemcpyAsync(p.Pfit + q0, Pfit, M * 4, cudaMemcpyHostToDevice, s));
+  float* ext = p.ext + (size_t)run * (p.G + 1) * p.Dp;
+  BFCUDA(cudaMemcpy2DAsync(ext, Dp4, Gb, D4, D4, p.G, cudaMemcpyHostToDevice, s));
+  BFCUDA(cudaMemcpyAsync(ext + (size_t)p.G * p.Dp, Tb, D4, cudaMemcpyHostToDevice, s));
+  // Keys naming the external rows: iteration k's group keys, the same keys already
+  // posted (as previous holders) into iteration k + 1's table, and Tbest in both
+  // holder slots (the next launches read it as iteration k's).
+  auto host_key = [](float fit, uint32_t idx) -> unsigned long long {
+    if (!(fit < INFINITY)) return kEmpty;
+    uint32_t u;
+    std::memcpy(&u, &fit, 4);
+    const uint32_t o = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)o << 32) | ((unsigned long long)(idx & 0x3fffffffu) << 1);
+  };
+  std::vector<unsigned long long> gk((size_t)p.G);
+  for (int g = 0; g < p.G; ++g) gk[g] = host_key(Gfit[g], (uint32_t)(p.M + g));
+  const unsigned long long tk = host_key(Tfit[0], (uint32_t)(p.M + p.G));
+  unsigned long long* keys = p.keys;
+  BFCUDA(cudaMemcpyAsync(keys + (size_t)(k % 3) * RG + (size_t)run * p.G, gk.data(), (size_t)p.G * 8,
+                         cudaMemcpyHostToDevice, s));
+  BFCUDA(cudaMemcpyAsync(keys + (size_t)((k + 1) % 3) * RG + (size_t)run * p.G, gk.data(), (size_t)p.G * 8,
+                         cudaMemcpyHostToDevice, s));
+  BFCUDA(cudaMemcpyAsync(p.thold + run, &tk, 8, cudaMemcpyHostToDevice, s));
+  BFCUDA(cudaMemcpyAsync(p.thold + (size_t)p.R + run, &tk, 8, cudaMemcpyHostToDevice, s));
+  h->k = k;
+  BFCUDA(launch_finish(h, k));
+  BFCUDA(cudaStreamSynchronize(s));
+  h->launches += 1;
+  return SEPSO_OK;
+}
+
+int sepso_bf_evaluate(int32_t fn, int32_t D, int32_t n, const float* X, int32_t ldx, float* F, void* stream) {
+  if (fn < 1 || fn > 4) return bffail(SEPSO_EINVAL, "fn=%d is not one of BF1..BF4", fn);
+  if (D < 1 || n < 0 || ldx < D) return bffail(SEPSO_EINVAL, "D=%d, n=%d, ldx=%d", D, n, ldx);
+  if (n == 0) return SEPSO_OK;
+  if (!X || !F) return bffail(SEPSO_EINVAL, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = std::min((n + 7) / 8, 4096);
+  switch (fn) {
+    case 1: bf_eval_kernel<1><<<grid, 256, 0, s>>>(X, ldx, D, n, F); break;
+    case 2: bf_eval_kernel<2><<<grid, 256, 0, s>>>(X, ldx, D, n, F); break;
+    case 3: bf_eval_kernel<3><<<grid, 256, 0, s>>>(X, ldx, D, n, F); break;
+    default: bf_eval_kernel<4><<<grid, 256, 0, s>>>(X, ldx, D, n, F); break;
+  }
+  BFCUDA(cudaGetLastError());
+  return SEPSO_OK;
+}
+
+}  // extern "C"

@@ -12,7 +12,7 @@ import numpy as np
 import torch
 
 from . import _native
-from ._native import HsefConfig, Result, check, fptr
+from ._native import HsefConfig, Result, check, check_bf, fptr
 from .inputs import Scene, SepsoConfig
 
 
@@ -227,6 +227,98 @@ class Planner:
 
     def launch_count(self) -> int:
         return int(self.lib.sepso_launch_count(self._h))
+
+
+class BFPlanner:
+    """DTPSO on a benchmark function of Table BFs (``sepso_bf_*``): ``cfg.runs``
+    independent swarms of G x N particles over [lo, hi]^D on one GPU."""
+
+    def __init__(self, cfg, device=None, stream: torch.cuda.Stream | None = None):
+        self.lib = _native.lib()
+        self.cfg = cfg
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        c = _native.bf_config_struct(cfg)
+        size = ctypes.c_size_t()
+        check_bf(self.lib.sepso_bf_workspace_size(ctypes.byref(c), ctypes.byref(size)))
+        self.workspace = torch.empty(size.value, dtype=torch.uint8, device=self.device)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check_bf(self.lib.sepso_bf_create(ctypes.byref(c), ctypes.c_void_p(self.workspace.data_ptr()),
+                                              size.value, ctypes.c_void_p(self.stream.cuda_stream),
+                                              ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            self.lib.sepso_bf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_hyper(self, hyper, run: int = -1):
+        h = _f32(hyper, (self.cfg.G, 6))
+        check_bf(self.lib.sepso_bf_set_hyper(self._h, h.ctypes.data, run))
+
+    def run_async(self, use_graph: bool = True):
+        check_bf(self.lib.sepso_bf_run_async(self._h, int(use_graph)))
+
+    def step(self, iters: int = 1):
+        check_bf(self.lib.sepso_bf_step(self._h, iters))
+
+    def sync(self):
+        check_bf(self.lib.sepso_bf_sync(self._h))
+
+    def read(self, run: int = 0) -> dict:
+        x = np.zeros(self.cfg.D, np.float32)
+        f = np.zeros(1, np.float32)
+        k = ctypes.c_int32()
+        check_bf(self.lib.sepso_bf_read(self._h, run, x.ctypes.data, f.ctypes.data, ctypes.byref(k)))
+        return {"x": x, "fit": float(f[0]), "iters": k.value}
+
+    def history(self, run: int = 0) -> np.ndarray:
+        h = np.zeros(self.cfg.max_iters, np.float32)
+        check_bf(self.lib.sepso_bf_history(self._h, run, h.ctypes.data))
+        return h
+
+    def get_state(self, run: int = 0) -> dict:
+        G, N, D = self.cfg.G, self.cfg.N, self.cfg.D
+        M = G * N
+        st = {"X": np.zeros(M * D, np.float32), "V": np.zeros(M * D, np.float32),
+              "P": np.zeros(M * D, np.float32), "Pfit": np.zeros(M, np.float32),
+              "Gb": np.zeros(G * D, np.float32), "Gfit": np.zeros(G, np.float32),
+              "Tb": np.zeros(D, np.float32), "Tfit": np.zeros(1, np.float32)}
+        k = ctypes.c_int32()
+        check_bf(self.lib.sepso_bf_get_state(self._h, run, *[st[n].ctypes.data for n in
+                                                             ("X", "V", "P", "Pfit", "Gb", "Gfit", "Tb", "Tfit")],
+                                             ctypes.byref(k)))
+        st["k"] = np.array([k.value], np.int32)
+        return st
+
+    def set_state(self, state: dict, run: int = 0):
+        G, N, D = self.cfg.G, self.cfg.N, self.cfg.D
+        M = G * N
+        shapes = {"X": M * D, "V": M * D, "P": M * D, "Pfit": M, "Gb": G * D, "Gfit": G, "Tb": D, "Tfit": 1}
+        arrs = {n: _f32(state[n], (sz,)) for n, sz in shapes.items()}
+        check_bf(self.lib.sepso_bf_set_state(self._h, run, *[arrs[n].ctypes.data for n in shapes],
+                                             int(np.asarray(state["k"]).reshape(-1)[0])))
+
+    def launch_count(self) -> int:
+        return int(self.lib.sepso_bf_launch_count(self._h))
+
+
+def bf_evaluate(fn: int, X: torch.Tensor) -> torch.Tensor:
+    """BF``fn`` of the rows of a CUDA float32 tensor (n, D), on the current stream."""
+    assert X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
+    F = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    stream = torch.cuda.current_stream(X.device).cuda_stream
+    check_bf(_native.lib().sepso_bf_evaluate(fn, X.shape[1], X.shape[0], ctypes.c_void_p(X.data_ptr()),
+                                             X.stride(0), ctypes.c_void_p(F.data_ptr()),
+                                             ctypes.c_void_p(stream)))
+    return F
 
 
 class BatchPlanner:

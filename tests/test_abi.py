@@ -188,3 +188,36 @@ def test_at_window_test_rejects_bad_arguments_before_any_launch():
     assert call(count=-1) == -1
     assert L.sepso_at_window_test(None, None, None, 3, 20, ctypes.c_float(1.0), None, None) == -1
     assert call(count=0) == 0                                  # nothing to do, no device call
+
+
+def test_bf_workspace_size_and_bad_configs():
+    L = _native.lib()
+    from paper_2308_10169_gb300.inputs import BFConfig
+
+    def size(**kw):
+        c = _native.bf_config_struct(BFConfig(**kw))
+        out = ctypes.c_size_t()
+        rc = L.sepso_bf_workspace_size(ctypes.byref(c), ctypes.byref(out))
+        return rc, out.value
+
+    rc, s1 = size(fn=1, D=30, G=8, N=10, runs=1)
+    assert rc == 0
+    rc, s2 = size(fn=1, D=30, G=8, N=10, runs=50)
+    assert rc == 0 and s2 > 40 * s1
+    rc, big = size(fn=3, D=1000, G=8, N=2048, runs=1)
+    assert rc == 0 and big >= 16384 * 1000 * 16        # X, V and two Pbest buffers
+    for bad in (dict(fn=0), dict(fn=5), dict(D=0), dict(D=16385), dict(G=0), dict(G=33), dict(N=0),
+                dict(runs=0), dict(max_iters=0), dict(lo=1.0, hi=1.0), dict(lo=float("nan")),
+                dict(hi=float("inf")), dict(runs=600, G=8)):
+        assert size(**bad)[0] == -1, bad
+    # workspace checks come before any CUDA call
+    c = _native.bf_config_struct(BFConfig(fn=1, D=30, G=8, N=10))
+    h = ctypes.c_void_p()
+    assert L.sepso_bf_create(ctypes.byref(c), ctypes.c_void_p(1 << 20), s1 - 1, None, ctypes.byref(h)) == -3
+    assert L.sepso_bf_create(ctypes.byref(c), ctypes.c_void_p((1 << 20) + 16), s1, None, ctypes.byref(h)) == -3
+    assert L.sepso_bf_create(ctypes.byref(c), None, s1, None, ctypes.byref(h)) == -3
+    X = ctypes.c_void_p(1 << 20)
+    assert L.sepso_bf_evaluate(0, 30, 4, X, 30, X, None) == -1
+    assert L.sepso_bf_evaluate(1, 30, 4, X, 29, X, None) == -1     # pitch below D
+    assert L.sepso_bf_evaluate(1, 30, 0, None, 30, None, None) == 0  # nothing to do
+    assert L.sepso_bf_step(None, 1) == -1 and L.sepso_bf_run_async(None, 1) == -1
