@@ -78,10 +78,14 @@ def parse():
     ap.add_argument("--prior-rounds", type=int, default=3)
     ap.add_argument("--prior-epochs", type=int, default=30)
     ap.add_argument("--prior-batch", type=int, default=4096, help="rows per Adam step")
-    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper",
-                    help="comma list of main, cpu, batch, prior, serve, paper, gemm (paper: the "
-                         "ablation variants of the path-planning comparison; gemm: the tensor-core "
-                         "GEMM alone)")
+    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper,bf",
+                    help="comma list of main, cpu, batch, prior, serve, paper, bf, gemm (paper: the "
+                         "ablation variants of the path-planning comparison; bf: the benchmark "
+                         "functions; gemm: the tensor-core GEMM alone)")
+    ap.add_argument("--bf-fns", type=str, default="1,2,3,4", help="benchmark functions (1..4) of section bf")
+    ap.add_argument("--bf-iters", type=int, default=1400, help="iterations per benchmark-function run")
+    ap.add_argument("--bf-trials", type=int, default=50,
+                    help="trials of the standard D=30 runs (0 = only the large-scale runs)")
     return ap.parse_args()
 
 
@@ -488,6 +492,71 @@ def run_paper(frames: int = 100, seed: int = 0):
             "variants": out}
 
 
+def run_bf(fns, iters: int, trials: int, peak_gbs: float):
+    """Benchmark functions (Table BFs): the large-scale runs of Sec. 4.1.2 (16K
+    particles x 1K coordinates) and the standard runs of Sec. 4.1.1 (80 particles x
+    30 coordinates, ``trials`` trials as the runs of one launch), Table hyper8 rows.
+    Each run is one CUDA graph (init, iterations, bests), timed with CUDA events after
+    one untimed run; the swarm tensors (262 MB at the large size) exceed L2."""
+    import torch
+
+    from paper_2308_10169_gb300 import BFPlanner
+    from paper_2308_10169_gb300.inputs import BF_NAMES, bf_large, bf_standard
+    paper_large = {1: 23.8, 2: 30.3, 3: 29.6, 4: 30.2}
+    paper_standard = {1: 0.37, 2: 0.44, 3: 0.42, 4: 0.46}
+    out = {"large": {}, "standard": {}}
+    for fn in fns:
+        cfg, hy = bf_large(fn, iters=iters)
+        pl = BFPlanner(cfg)
+        pl.set_hyper(hy)
+        pl.run_async()
+        pl.sync()
+        l0 = pl.launch_count()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(pl.stream)
+        pl.run_async()
+        b.record(pl.stream)
+        pl.sync()
+        ms = a.elapsed_time(b)
+        coords = cfg.G * cfg.N * cfg.D
+        algo = 20 * coords                      # X, V, Pbest read + X, V written, per iteration
+        # launch 1 reads X and writes every Pbest row (8 B); launches 2..K+1 are updates
+        gbs = coords * (20 * iters + 8) / (ms / 1e3) / 1e9
+        r = pl.read(0)
+        out["large"][BF_NAMES[fn]] = {
+            "s_per_run": ms / 1e3, "us_per_iteration": 1e3 * ms / iters, "best": r["fit"],
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s",
+                         "frac": gbs / peak_gbs, "kernel": "bf_iter_kernel",
+                         "bytes_per_iteration": algo,
+                         "note": "20 B per coordinate; Pbest rows written on improvement not counted"},
+            "gpu_launches": pl.launch_count() - l0,
+            "paper_dtpso_gpu_s": paper_large[fn]}
+        del pl
+    if trials > 0:
+        for fn in fns:
+            cfg, hy = bf_standard(fn, trials=trials)
+            cfg = cfg.with_(max_iters=iters)
+            pl = BFPlanner(cfg)
+            pl.set_hyper(hy)
+            pl.run_async()
+            pl.sync()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(pl.stream)
+            pl.run_async()
+            b.record(pl.stream)
+            pl.sync()
+            ms = a.elapsed_time(b)
+            fits = [pl.read(r)["fit"] for r in range(trials)]
+            out["standard"][BF_NAMES[fn]] = {
+                "s_all_trials": ms / 1e3, "s_per_trial_equivalent": ms / 1e3 / trials,
+                "us_per_iteration": 1e3 * ms / iters, "median_best": float(np.median(fits)),
+                "paper_dtpso_s_per_trial": paper_standard[fn]}
+    out["workload"] = (f"large: D=1000, 8 x 2048 particles, {iters} iterations; standard: D=30, 8 x 10 "
+                       f"particles, {trials} trials in one launch; [-600,600]^D, Table hyper8 rows; "
+                       "paper numbers are other hardware (context only)")
+    return out
+
+
 def _world_step(ag):
     """The client's simulated world between two requests of an agent: circles and
     start/target move by their velocity and bounce off the map border."""
@@ -638,6 +707,11 @@ def run_prior(n_train: int, n_eval: int, rounds: int, epochs: int, single: dict,
             "gpu_launches": pr.launch_count() - l0}
 
 
+def _hbm_peak() -> float:
+    path = ROOT / "MEASURED_PEAKS.json"
+    return float(json.loads(path.read_text()).get("hbm_gbs", 6800.0)) if path.exists() else 6800.0
+
+
 def _bf16_peak() -> float:
     path = ROOT / "MEASURED_PEAKS.json"
     return float(json.loads(path.read_text()).get("bf16_tflops", 1900.0)) if path.exists() else 1900.0
@@ -742,6 +816,9 @@ def main():
                                       line, args.prior_batch)
         if world == 1 and "paper" in sections:
             line["paper_ablation"] = run_paper()
+        if world == 1 and "bf" in sections:
+            line["bf"] = run_bf([int(x) for x in args.bf_fns.split(",") if x.strip()], args.bf_iters,
+                                args.bf_trials, _hbm_peak())
         if world == 1 and "gemm" in sections:
             line["gemm"] = run_gemm()
         if world == 1 and "serve" in sections and args.serve_rates:

@@ -50,6 +50,7 @@ namespace {
 
 constexpr unsigned long long kEmpty = ~0ull;
 constexpr int kUpdate = 1, kEval = 2;
+constexpr int kUnroll = 4;
 constexpr int kMaxD = 16384;
 constexpr int kMaxRG = 4096;           // runs x groups: the CTA's key table
 constexpr int kSmemRows = 160 * 1024;  // shared-memory budget of the row buffers
@@ -256,31 +257,46 @@ __global__ void __launch_bounds__(256) bf_iter_kernel(const BfParams p, int j, i
       float4* vr = reinterpret_cast<float4*>(p.V + q * p.Dp);
       const float4* pr = reinterpret_cast<const float4*>(p.P + ((size_t)par * total + q) * p.Dp);
       const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      for (int c = lane; c < nch; c += 32) {
-        float4 x = xr[c], v = vr[c];
-        const float4 pb = pr[c];
-        const float4 gb = gr ? gr[c] : zero;
-        const float4 tb = (need_T && tr) ? tr[c] : zero;
-        float* xe = &x.x;
-        float* ve = &v.x;
-        const float* pe = &pb.x;
-        const float* ge = &gb.x;
-        const float* te = &tb.x;
+      // kUnroll chunks per lane in flight: all their loads are issued before any use.
+      for (int c0 = lane; c0 < nch; c0 += 32 * kUnroll) {
+        float4 x[kUnroll], v[kUnroll], pb[kUnroll], gb[kUnroll], tb[kUnroll];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          if (4 * c + e < p.D) {
-            float vv = w * ve[e];
-            vv = fmaf(a1, pe[e] - xe[e], vv);
-            vv = fmaf(a2, ge[e] - xe[e], vv);
-            if (need_T) vv = fmaf(a3, te[e] - xe[e], vv);
-            vv = fminf(fmaxf(vv, -vmax), vmax);
-            ve[e] = vv;
-            xe[e] = fminf(fmaxf(xe[e] + vv, p.lo), p.hi);
+        for (int u = 0; u < kUnroll; ++u) {
+          const int c = c0 + 32 * u;
+          if (c < nch) {
+            x[u] = xr[c];
+            v[u] = vr[c];
+            pb[u] = __ldg(pr + c);
+            gb[u] = gr ? __ldg(gr + c) : zero;
+            tb[u] = (need_T && tr) ? __ldg(tr + c) : zero;
           }
         }
-        xr[c] = x;
-        vr[c] = v;
-        s4[c] = x;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int c = c0 + 32 * u;
+          if (c < nch) {
+            float* xe = &x[u].x;
+            float* ve = &v[u].x;
+            const float* pe = &pb[u].x;
+            const float* ge = &gb[u].x;
+            const float* te = &tb[u].x;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (4 * c + e < p.D) {
+                float vv = w * ve[e];
+                vv = fmaf(a1, pe[e] - xe[e], vv);
+                vv = fmaf(a2, ge[e] - xe[e], vv);
+                if (need_T) vv = fmaf(a3, te[e] - xe[e], vv);
+                vv = fminf(fmaxf(vv, -vmax), vmax);
+                ve[e] = vv;
+                xe[e] = fminf(fmaxf(xe[e] + vv, p.lo), p.hi);
+              }
+            }
+            xr[c] = x[u];
+            vr[c] = v[u];
+            s4[c] = x[u];
+          }
+        }
       }
       // The previous holder of this group's best keeps it on a tie (priority 0).
       if (pi == 0 && lane < p.G) {
