@@ -19,7 +19,9 @@ What each function follows (paper: arXiv 2308.10169):
 * ``advance_scene``         -- the dynamic simulator step (Fig. PP caption).
 * ``bf_value`` / ``BFSwarm`` -- the benchmark functions BF1-BF4 (Table BFs, their
   textbook definitions) and DTPSO on them: the same Algorithm 1 iteration as
-  ``Swarm`` with that objective over the box [lo, hi]^D.
+  ``Swarm`` with that objective over the box [lo, hi]^D; with ``fn = 5`` the
+  objective is a path among polygon obstacles (Sec. 3.3.1, Eq. penalty with Q the
+  number of path-segment / obstacle-edge crossings, ``seg_cross``).
 * ``hsef``                  -- the hierarchical self-evolving framework
   (Sec. 3.2.1, Eq. fit_h).
 * ``raster`` / ``prior_encode`` / ``prior_decode`` / ``Mlp`` / ``adam`` -- the
@@ -84,7 +86,8 @@ class _Config(ctypes.Structure):
 class _Scene(ctypes.Structure):
     _fields_ = [("sx", ctypes.c_double), ("sy", ctypes.c_double),
                 ("tx", ctypes.c_double), ("ty", ctypes.c_double),
-                ("O", ctypes.c_int32), ("circ", _f64p)]
+                ("O", ctypes.c_int32), ("circ", _f64p),
+                ("E", ctypes.c_int32), ("edges", _f64p)]
 
 
 class _State(ctypes.Structure):
@@ -129,6 +132,10 @@ def lib():
         L.so_window_std.argtypes = [_f64p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
         L.so_bf_value.argtypes = [ctypes.c_int32, ctypes.c_int32, _f64p]
         L.so_bf_value.restype = ctypes.c_double
+        L.so_seg_cross.argtypes = [ctypes.c_double] * 8
+        L.so_seg_cross.restype = ctypes.c_int32
+        L.so_poly_margin.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene), ctypes.c_int32,
+                                     _f64p, _f64p]
         L.so_window_std.restype = ctypes.c_double
         L.so_at_update.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_State)]
         L.so_at_update.restype = ctypes.c_int32
@@ -187,14 +194,17 @@ def _cfg(c) -> _Config:
 class Scene:
     """A static scene in FP64 (converted exactly from the FP32 inputs)."""
 
-    def __init__(self, start, target, circles):
+    def __init__(self, start, target, circles, edges=None):
         self.start = np.asarray(start, dtype=np.float64).reshape(2).copy()
         self.target = np.asarray(target, dtype=np.float64).reshape(2).copy()
         self.circles = np.ascontiguousarray(np.asarray(circles, dtype=np.float64).reshape(-1, 3))
+        e = np.zeros((0, 4)) if edges is None else edges
+        self.edges = np.ascontiguousarray(np.asarray(e, dtype=np.float64).reshape(-1, 4))
 
     def c(self) -> _Scene:
         return _Scene(sx=self.start[0], sy=self.start[1], tx=self.target[0], ty=self.target[1],
-                      O=self.circles.shape[0], circ=_p64(self.circles))
+                      O=self.circles.shape[0], circ=_p64(self.circles),
+                      E=self.edges.shape[0], edges=_p64(self.edges))
 
 
 # ----------------------------------------------------------------------------
@@ -347,11 +357,30 @@ def bf_value(fn: int, x) -> float:
 
 
 def _bf_cfg(c) -> _Config:
-    """The C config of a benchmark-function run (any object with BFConfig's fields)."""
-    return _Config(T=0, G=c.G, N=c.N, W=0.0, H=0.0, alpha=0.0, beta=1, max_iters=c.max_iters,
+    """The C config of a run of the generic engine (any object with BFConfig's fields):
+    a benchmark function (fn 1..4) or a path among polygons (fn 5, D = 2T)."""
+    f32 = lambda v: float(np.float32(v))
+    return _Config(T=c.D // 2 if c.fn == 5 else 0, G=c.G, N=c.N, W=f32(c.map_w), H=f32(c.map_h),
+                   alpha=f32(c.alpha), beta=c.beta, max_iters=c.max_iters,
                    at_mode=0, tw=1, delta=0.0, stall_iters=0, stall_tol=0.0, use_pi=0,
                    pi_gamma=0.0, pi_h=0.0, seed=c.seed, run_id=c.run_id, problem=c.fn, Dbf=c.D,
-                   lo=float(np.float32(c.lo)), hi=float(np.float32(c.hi)))
+                   lo=f32(c.lo), hi=f32(c.hi))
+
+
+def seg_cross(a, b, c, d) -> bool:
+    """Proper crossing of segments ab and cd (Sec. 3.3.1's segment intersection)."""
+    return bool(lib().so_seg_cross(float(a[0]), float(a[1]), float(b[0]), float(b[1]),
+                                   float(c[0]), float(c[1]), float(d[0]), float(d[1])))
+
+
+def poly_margin(cfg, scene: "Scene", X) -> np.ndarray:
+    """Per path: distance of its crossing decisions from a flip (parity tests)."""
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, cfg.D))
+    m = np.zeros(X.shape[0])
+    c = _bf_cfg(cfg)
+    s = scene.c()
+    lib().so_poly_margin(ctypes.byref(c), ctypes.byref(s), X.shape[0], _p64(X), _p64(m))
+    return m
 
 
 class BFSwarm(Swarm):
@@ -361,7 +390,7 @@ class BFSwarm(Swarm):
 
     _EMPTY = None
 
-    def __init__(self, cfg, hyper):
+    def __init__(self, cfg, hyper, scene: "Scene" = None):
         self.cfg = cfg
         G, N, D = cfg.G, cfg.N, cfg.D
         M = G * N
@@ -376,15 +405,16 @@ class BFSwarm(Swarm):
             "prev_lfv": np.full(1, np.inf), "n_prior": f(1, np.int32), "priorT": f(D),
         }
         self._c = _bf_cfg(cfg)
-        self._none = Scene((0.0, 0.0), (0.0, 0.0), np.zeros((0, 3)))
+        self._none = scene if scene is not None else Scene((0.0, 0.0), (0.0, 0.0), np.zeros((0, 3)))
 
-    def evaluate(self, X) -> np.ndarray:
+    def evaluate(self, X, with_q: bool = False):
         X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, self.cfg.D))
         F = np.zeros(X.shape[0])
+        Q = np.zeros(X.shape[0], np.int32)
         s = self._none.c()
         lib().so_evaluate(ctypes.byref(self._c), ctypes.byref(s), X.shape[0], _p64(X), _p64(F),
-                          None, None)
-        return F
+                          _p32(Q), None)
+        return (F, Q) if with_q else F
 
     def iteration(self, scene=None, check_stop: bool = False) -> bool:
         return super().iteration(self._none, False)

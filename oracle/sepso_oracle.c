@@ -106,9 +106,11 @@ typedef struct {
   double pi_h;           /* half-width of the PI interval                     */
   uint64_t seed;         /* Philox key                                        */
   uint32_t run_id;       /* Philox counter word 3                             */
-  /* The objective: 0 = path planning (Sec. 3.3: D = 2T waypoint coordinates in
-   * the map); 1..4 = benchmark functions BF1..BF4 (Table BFs: Sphere,
-   * Rosenbrock, Rastrigin, Griewank) over the box [lo, hi]^D, D = Dbf.        */
+  /* The objective: 0 = path planning among circles (Sec. 3.3: D = 2T waypoint
+   * coordinates in the map); 1..4 = benchmark functions BF1..BF4 (Table BFs:
+   * Sphere, Rosenbrock, Rastrigin, Griewank) over the box [lo, hi]^D, D = Dbf;
+   * 5 = path planning among polygons (Sec. 3.3.1: Q counts crossings of path
+   * segments with obstacle edges).                                          */
   int32_t problem;
   int32_t Dbf;
   double lo, hi;
@@ -118,6 +120,8 @@ typedef struct {
   double sx, sy, tx, ty; /* start and target                                 */
   int32_t O;             /* number of circles                                 */
   const double* circ;    /* O x 3: cx, cy, r                                  */
+  int32_t E;             /* polygon edges (problem 5)                         */
+  const double* edges;   /* E x 4: x0, y0, x1, y1                             */
 } so_scene;
 
 typedef struct {
@@ -175,6 +179,70 @@ static double so_length(int32_t T, const double* x, double sx, double sy, double
   len += sqrt((sx - x[0]) * (sx - x[0]) + (sy - x[T]) * (sy - x[T]));
   len += sqrt((tx - x[T - 1]) * (tx - x[T - 1]) + (ty - x[2 * T - 1]) * (ty - x[2 * T - 1]));
   return len;
+}
+
+/* Orientation of r relative to the directed line p -> q (twice the signed area). */
+static double so_orient(double px, double py, double qx, double qy, double rx, double ry) {
+  return (qx - px) * (ry - py) - (qy - py) * (rx - px);
+}
+
+/* Segments ab and cd cross properly: c and d strictly on opposite sides of line
+ * ab, and a and b strictly on opposite sides of line cd (touching and collinear
+ * contacts are not crossings). */
+int32_t so_seg_cross(double ax, double ay, double bx, double by, double cx, double cy, double dx, double dy) {
+  const double o1 = so_orient(ax, ay, bx, by, cx, cy), o2 = so_orient(ax, ay, bx, by, dx, dy);
+  const double o3 = so_orient(cx, cy, dx, dy, ax, ay), o4 = so_orient(cx, cy, dx, dy, bx, by);
+  return (o1 * o2 < 0.0) && (o3 * o4 < 0.0);
+}
+
+/* Q among polygons (Sec. 3.3.1, Eq. penalty): the number of (path segment,
+ * obstacle edge) pairs that cross. */
+static int32_t so_poly_crossings(int32_t T, const double* x, const so_scene* sc) {
+  int32_t q = 0;
+  for (int32_t s = 0; s <= T; ++s) {
+    const double ax = (s == 0) ? sc->sx : x[s - 1];
+    const double ay = (s == 0) ? sc->sy : x[T + s - 1];
+    const double bx = (s == T) ? sc->tx : x[s];
+    const double by = (s == T) ? sc->ty : x[T + s];
+    for (int32_t e = 0; e < sc->E; ++e) {
+      const double* d = sc->edges + 4 * e;
+      q += so_seg_cross(ax, ay, bx, by, d[0], d[1], d[2], d[3]);
+    }
+  }
+  return q;
+}
+
+/* For the parity tests: per particle, how far its crossing decisions are from
+ * flipping -- the smallest |orientation| / (|ab| |cd|) over the pairs whose result
+ * hangs on a near-zero orientation (a pair decided by a clear "no" of the other
+ * side test, at 1e-3, does not count). */
+void so_poly_margin(const so_config* cfg, const so_scene* sc, int32_t n, const double* X, double* margin) {
+  const int32_t T = cfg->T, D = 2 * T;
+  for (int32_t p = 0; p < n; ++p) {
+    const double* x = X + (int64_t)p * D;
+    double m = INFINITY;
+    for (int32_t s = 0; s <= T; ++s) {
+      const double ax = (s == 0) ? sc->sx : x[s - 1];
+      const double ay = (s == 0) ? sc->sy : x[T + s - 1];
+      const double bx = (s == T) ? sc->tx : x[s];
+      const double by = (s == T) ? sc->ty : x[T + s];
+      for (int32_t e = 0; e < sc->E; ++e) {
+        const double* d = sc->edges + 4 * e;
+        const double L = sqrt((bx - ax) * (bx - ax) + (by - ay) * (by - ay)) *
+                         sqrt((d[2] - d[0]) * (d[2] - d[0]) + (d[3] - d[1]) * (d[3] - d[1]));
+        if (!(L > 0.0)) {
+          m = 0.0;
+          continue;
+        }
+        const double o1 = so_orient(ax, ay, bx, by, d[0], d[1]), o2 = so_orient(ax, ay, bx, by, d[2], d[3]);
+        const double o3 = so_orient(d[0], d[1], d[2], d[3], ax, ay), o4 = so_orient(d[0], d[1], d[2], d[3], bx, by);
+        const double m12 = fmin(fabs(o1), fabs(o2)) / L, m34 = fmin(fabs(o3), fabs(o4)) / L;
+        if ((m12 >= 1e-3 && o1 * o2 > 0.0) || (m34 >= 1e-3 && o3 * o4 > 0.0)) continue;
+        m = fmin(m, fmin(m12, m34));
+      }
+    }
+    margin[p] = m;
+  }
 }
 
 /* Q: number of (path segment, circle) pairs whose distance is below the radius. */
@@ -255,16 +323,28 @@ double so_bf_value(int32_t fn, int32_t D, const double* x) {
   return NAN;
 }
 
-static int32_t so_dim(const so_config* cfg) { return cfg->problem ? cfg->Dbf : 2 * cfg->T; }
+static int32_t so_is_bf(const so_config* cfg) { return cfg->problem >= 1 && cfg->problem <= 4; }
+static int32_t so_dim(const so_config* cfg) { return so_is_bf(cfg) ? cfg->Dbf : 2 * cfg->T; }
 
 void so_evaluate(const so_config* cfg, const so_scene* sc, int32_t n, const double* X, double* F,
                  int32_t* Q, double* len) {
   const int32_t T = cfg->T, D = so_dim(cfg);
-  if (cfg->problem) {
+  if (so_is_bf(cfg)) {
     for (int32_t p = 0; p < n; ++p) {
       if (F) F[p] = so_bf_value(cfg->problem, D, X + (int64_t)p * D);
       if (Q) Q[p] = 0;
       if (len) len[p] = 0.0;
+    }
+    return;
+  }
+  if (cfg->problem == 5) {
+    for (int32_t p = 0; p < n; ++p) {
+      const double* x = X + (int64_t)p * D;
+      const double l = so_length(T, x, sc->sx, sc->sy, sc->tx, sc->ty);
+      const int32_t q = so_poly_crossings(T, x, sc);
+      if (F) F[p] = l + cfg->alpha * so_pow_int((double)q, cfg->beta);
+      if (Q) Q[p] = q;
+      if (len) len[p] = l;
     }
     return;
   }
@@ -292,11 +372,11 @@ int32_t so_pi_count(double gamma, int32_t N) {
 
 /* X_range of coordinate j: [so_lo, so_lo + so_extent]; the map for a path. */
 static double so_extent(const so_config* cfg, int32_t j) {
-  if (cfg->problem) return cfg->hi - cfg->lo;
+  if (so_is_bf(cfg)) return cfg->hi - cfg->lo;
   return (j < cfg->T) ? cfg->W : cfg->H;
 }
-static double so_lo(const so_config* cfg) { return cfg->problem ? cfg->lo : 0.0; }
-static double so_hi(const so_config* cfg, int32_t j) { return cfg->problem ? cfg->hi : so_extent(cfg, j); }
+static double so_lo(const so_config* cfg) { return so_is_bf(cfg) ? cfg->lo : 0.0; }
+static double so_hi(const so_config* cfg, int32_t j) { return so_is_bf(cfg) ? cfg->hi : so_extent(cfg, j); }
 
 static double so_clip(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 

@@ -18,6 +18,8 @@ Workload shapes (all synthetic; the paper's own simulator scenes are not publish
 * ``paper_workload``   -- the path-planning setting of Sec. 4.3 with the ablation
   switches of Table ppresult (366x366 map, 8 obstacles of which 6 move, T=8,
   G=8 x N=170, std-window AT, 30 iterations per frame at most).
+* ``polygon_workload`` -- path planning among polygon obstacles (12 boxes and 4
+  U-shaped non-convex polygons, 80 edges) on the same engine, 100 iterations.
 * ``bf_standard`` / ``bf_large`` -- the benchmark functions of Table BFs: D=30 with
   8 x 10 particles (Sec. 4.1.1) and D=1000 with 8 x 2048 particles (Sec. 4.1.2),
   over [-600, 600]^D, Table hyper8 rows, 1400 iterations.
@@ -233,6 +235,7 @@ def paper_workload(seed: int = 0, variant: str = "SEPSO", frame_cap: int = 30):
 
 # Benchmark functions of Table BFs.
 BF_SPHERE, BF_ROSENBROCK, BF_RASTRIGIN, BF_GRIEWANK = 1, 2, 3, 4
+POLYGON_PATH = 5   # the same engine with a path among polygon obstacles as objective
 BF_NAMES = {BF_SPHERE: "Sphere", BF_ROSENBROCK: "Rosenbrock", BF_RASTRIGIN: "Rastrigin",
             BF_GRIEWANK: "Griewank"}
 
@@ -252,6 +255,12 @@ class BFConfig:
     seed: int = 0
     run_id: int = 0            # Philox counter word 3 of run 0; run r uses run_id + r
     runs: int = 1
+    # objective POLYGON_PATH only: D = 2T waypoint coordinates in [0, map_w] x [0, map_h],
+    # fitness = length + alpha * Q^beta (Eqs. path_fit, lenth, penalty)
+    map_w: float = 400.0
+    map_h: float = 400.0
+    alpha: float = 30.0
+    beta: int = 4
 
     def with_(self, **kw) -> "BFConfig":
         return replace(self, **kw)
@@ -270,6 +279,49 @@ def bf_large(fn: int, seed: int = 0, iters: int = 1400):
     over [-600, 600]^D, Table hyper8 rows, 1400 iterations -> (config, hyper)."""
     cfg = BFConfig(fn=fn, D=1000, G=8, N=2048, max_iters=iters, seed=seed, runs=1)
     return cfg, np.ascontiguousarray(TABLE_HYPER8, dtype=np.float32)
+
+
+def polygon_edges(polygons) -> np.ndarray:
+    """Closed polygons (lists of (x, y) vertices in order) -> (E, 4) float32 edges
+    (x0, y0, x1, y1), the last vertex joined back to the first."""
+    out = []
+    for poly in polygons:
+        v = np.asarray(poly, np.float32).reshape(-1, 2)
+        for i in range(len(v)):
+            a, b = v[i], v[(i + 1) % len(v)]
+            out.append((a[0], a[1], b[0], b[1]))
+    return np.asarray(out, np.float32).reshape(-1, 4)
+
+
+def polygon_workload(seed: int = 0, T: int = 8, N: int = 170, n_boxes: int = 12, n_u: int = 4,
+                     iters: int = 100, runs: int = 1):
+    """Static path planning among polygon obstacles (Sec. 3.3.1's map model: bounding
+    boxes and non-convex outlines): 400 x 400 map, start (20, 20), target (380, 380),
+    ``n_boxes`` axis-aligned boxes (centres U[60, 340]^2, half-sizes U[10, 30]) and
+    ``n_u`` U-shaped non-convex polygons (8 vertices, 60 x 60, opening towards a random
+    side); T waypoints, G = 8 x N, Table hyper8path rows, alpha = 30, beta = 4 (Table
+    params_path), ``iters`` iterations -> (config, start, target, polygons, edges, hyper)."""
+    rng = np.random.default_rng(6000 + seed)
+    polys = []
+    for _ in range(n_boxes):
+        cx, cy = rng.uniform(60, 340, 2)
+        hw, hh = rng.uniform(10, 30, 2)
+        polys.append([(cx - hw, cy - hh), (cx + hw, cy - hh), (cx + hw, cy + hh), (cx - hw, cy + hh)])
+    for _ in range(n_u):
+        cx, cy = rng.uniform(80, 320, 2)
+        u = np.array([(-30, -30), (30, -30), (30, 30), (15, 30), (15, -15), (-15, -15), (-15, 30), (-30, 30)],
+                     np.float64)
+        rot = int(rng.integers(0, 4))
+        for _ in range(rot):
+            u = np.stack([-u[:, 1], u[:, 0]], axis=1)
+        polys.append([(cx + a, cy + b) for a, b in u])
+    cfg = BFConfig(fn=POLYGON_PATH, D=2 * T, G=8, N=N, lo=0.0, hi=400.0, max_iters=iters, seed=seed,
+                   runs=runs, map_w=400.0, map_h=400.0, alpha=PARAMS_PATH["alpha"],
+                   beta=PARAMS_PATH["beta"])
+    start = np.array([20.0, 20.0], np.float32)
+    target = np.array([380.0, 380.0], np.float32)
+    hyper = np.ascontiguousarray(TABLE_HYPER8_PATH, dtype=np.float32)
+    return cfg, start, target, polys, polygon_edges(polys), hyper
 
 
 def random_paths(seed: int, n: int, T: int, W: float = 400.0, H: float = 400.0) -> np.ndarray:

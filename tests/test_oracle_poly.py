@@ -1,0 +1,107 @@
+"""The oracle's polygon-obstacle objective (Sec. 3.3.1 map model, Eq. penalty with Q
+the number of crossings between path segments and obstacle edges), pinned without a
+GPU: hand cases of the segment test, a parametric solver as an independent check,
+the crossing counts of hand-made paths (Fig. path: a path through two boxes has Q = 4;
+Fig. obstype: a path through the notch of a non-convex obstacle has Q = 0), and run
+invariants of DTPSO on a polygon scene.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_10169_gb300.inputs import (POLYGON_PATH, TABLE_HYPER8_PATH, BFConfig, polygon_edges,
+                                           polygon_workload)
+
+
+def test_segment_crossing_hand_cases():
+    assert oracle.seg_cross((0, 0), (2, 2), (0, 2), (2, 0))           # an X
+    assert not oracle.seg_cross((0, 0), (1, 1), (1, 1), (2, 0))       # shared endpoint
+    assert not oracle.seg_cross((0, 0), (2, 0), (1, 0), (3, 0))       # collinear overlap
+    assert not oracle.seg_cross((0, 0), (1, 0), (0, 1), (1, 1))       # parallel
+    assert not oracle.seg_cross((0, 0), (2, 0), (1, 0), (1, 5))       # T-junction on the segment
+    assert not oracle.seg_cross((0, 0), (1, 1), (2, 0), (3, -5))      # lines cross beyond the ends
+    assert oracle.seg_cross((0, 0), (4, 1), (1, -3), (2, 3))
+
+
+def _param_cross(a, b, c, d):
+    """Independent check: solve a + t (b - a) = c + u (d - c); a proper crossing has
+    0 < t < 1 and 0 < u < 1."""
+    A = np.array([[b[0] - a[0], -(d[0] - c[0])], [b[1] - a[1], -(d[1] - c[1])]])
+    det = np.linalg.det(A)
+    if abs(det) < 1e-9:
+        return None
+    t, u = np.linalg.solve(A, np.array([c[0] - a[0], c[1] - a[1]]))
+    if min(abs(t), abs(t - 1), abs(u), abs(u - 1)) < 1e-9:
+        return None
+    return bool(0 < t < 1 and 0 < u < 1)
+
+
+def test_segment_crossing_matches_parametric_solver():
+    rng = np.random.default_rng(3)
+    n = 0
+    for _ in range(4000):
+        a, b, c, d = rng.uniform(0, 10, (4, 2))
+        want = _param_cross(a, b, c, d)
+        if want is None:
+            continue
+        assert oracle.seg_cross(a, b, c, d) == want
+        n += want
+    assert n > 300                                   # both outcomes exercised
+
+
+def _eval(edges, start, target, waypoints, alpha=30.0, beta=4):
+    T = len(waypoints)
+    cfg = BFConfig(fn=POLYGON_PATH, D=2 * T, G=1, N=1, map_w=400.0, map_h=400.0, alpha=alpha,
+                   beta=beta)
+    sc = oracle.Scene(start, target, np.zeros((0, 3)), edges)
+    w = np.asarray(waypoints, np.float64)
+    x = np.concatenate([w[:, 0], w[:, 1]])
+    F, Q = oracle.BFSwarm(cfg, TABLE_HYPER8_PATH[:1], sc).evaluate(x[None], with_q=True)
+    return float(F[0]), int(Q[0])
+
+
+BOX = [(100, 100), (200, 100), (200, 200), (100, 200)]
+BOX2 = [(260, 100), (320, 100), (320, 200), (260, 200)]
+U = [(100, 100), (200, 100), (200, 200), (170, 200), (170, 130), (130, 130), (130, 200), (100, 200)]
+
+
+def test_crossing_counts_of_hand_paths():
+    e1 = polygon_edges([BOX])
+    line = [(50 + 37 * i, 150.0) for i in range(1, 8)]             # on y = 150, off every edge
+    F, Q = _eval(e1, (40, 150), (390, 150), line)
+    assert Q == 2                                                   # in and out of the box
+    assert F == pytest.approx(350.0 + 30.0 * 2 ** 4, rel=1e-12)
+    F, Q = _eval(polygon_edges([BOX, BOX2]), (40, 150), (390, 150), line)
+    assert Q == 4                                                   # through two boxes
+    below = [(50 + 37 * i, 60.0) for i in range(1, 8)]
+    assert _eval(e1, (40, 60), (390, 60), below)[1] == 0            # around the box
+    inside = [(120, 150), (180, 150)]
+    assert _eval(e1, (110, 150), (190, 150), inside)[1] == 0        # wholly inside: no crossing
+
+
+def test_non_convex_obstacle():
+    eu = polygon_edges([U])
+    # down into the notch and back out through its mouth: no edge crossed
+    notch = [(150, 210), (150, 150), (150, 140), (150, 210)]
+    assert _eval(eu, (150, 260), (150, 260), notch)[1] == 0
+    # straight across both arms and the notch: four crossings
+    across = [(60 + 43 * i, 170.0) for i in range(1, 7)]
+    assert _eval(eu, (40, 170), (390, 170), across)[1] == 4
+    # across the base of the U: two crossings
+    base = [(60 + 43 * i, 115.0) for i in range(1, 7)]
+    assert _eval(eu, (40, 115), (390, 115), base)[1] == 2
+
+
+def test_workload_shape_and_run_invariants():
+    cfg, start, target, polys, edges, hy = polygon_workload(0, N=12, iters=40)
+    assert edges.shape == (12 * 4 + 4 * 8, 4)
+    assert cfg.D == 16 and cfg.fn == POLYGON_PATH
+    sc = oracle.Scene(start, target, np.zeros((0, 3)), edges)
+    sw = oracle.BFSwarm(cfg, hy, sc)
+    hist = sw.run(40)
+    assert np.all(np.diff(hist) <= 0)
+    F, Q = sw.evaluate(sw.s["Tb"][None], with_q=True)
+    assert F[0] == pytest.approx(sw.s["Tfit"][0], rel=1e-12)
+    X = sw.s["X"].reshape(-1, cfg.D)
+    assert X.min() >= 0.0 and X.max() <= 400.0
+    assert hist[-1] < hist[0]
