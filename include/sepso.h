@@ -607,7 +607,7 @@ const char* sepso_last_error(void);
 /*   BF4 1 + sum x_i^2 / 4000 - prod cos(x_i / sqrt i).                        */
 /* ------------------------------------------------------------------------- */
 typedef struct sepso_bf_config {
-  int32_t fn;         /* 1..4: BF1..BF4                                         */
+  int32_t fn;         /* 1..4: BF1..BF4; 5: a path among polygons (below)       */
   int32_t D;          /* coordinates per particle, 1..16384                     */
   int32_t G;          /* groups, 1..32                                          */
   int32_t N;          /* particles per group (G x N + G + 1 < 2^30)             */
@@ -616,6 +616,12 @@ typedef struct sepso_bf_config {
   int32_t runs;       /* independent swarms (trials); runs x G <= 4096          */
   uint64_t seed;      /* Philox key                                             */
   uint32_t run_id;    /* Philox counter word 3 of run 0; run r uses run_id + r  */
+  /* objective 5 only (lo and hi are then unused): D = 2T waypoint coordinates,  */
+  /* x in [0, map_w], y in [0, map_h]; fitness = Eq. lenth + alpha * Q^beta     */
+  float map_w, map_h; /* > 0                                                     */
+  float alpha;        /* >= 0                                                    */
+  int32_t beta;       /* 1..8                                                    */
+  int32_t max_edges;  /* capacity for obstacle edges, 0..4096                    */
 } sepso_bf_config;
 
 typedef struct sepso_bf_ctx* sepso_bf_handle;
@@ -638,6 +644,23 @@ int sepso_bf_set_hyper(sepso_bf_handle h, const float* hyper, int32_t run);
  * iterations, then the bests.  use_graph != 0 captures the launches once into a
  * CUDA graph and replays it.  Errors: ESTATE (no hyper-parameters), ECUDA. */
 int sepso_bf_run_async(sepso_bf_handle h, int32_t use_graph);
+/* Objective 5 (Sec. 3.3.1 map model): obstacles are polygons given by their edges
+ * (host float[E*4]: x0, y0, x1, y1; a closed polygon lists each side once, convex
+ * or not), start and target host float[2].  Q = the number of (path segment,
+ * edge) pairs that cross properly (the endpoints of each strictly on opposite
+ * sides of the other; touching and collinear contacts do not count).  Required
+ * before sepso_bf_run_async; a new edge count re-captures the graph.  Syncs.
+ * Errors: EINVAL (objective, E > max_edges, non-finite values), ECUDA. */
+int sepso_bf_set_polygons(sepso_bf_handle h, const float* start, const float* target, const float* edges,
+                          int32_t E);
+/* Objective 5 of n paths X (device, row pitch ldx >= 2T floats: x of the T
+ * waypoints, then y) among E device edges (float4 x0, y0, x1, y1; 16-byte
+ * aligned): fitness into device F[n] and, if Q is not NULL, the crossing counts
+ * into device Q[n].  start/target: host float[2].  On stream.
+ * Errors: EINVAL, ECUDA. */
+int sepso_poly_evaluate(int32_t T, int32_t n, const float* X, int32_t ldx, const float* start, const float* target,
+                        const float* edges, int32_t E, float alpha, int32_t beta, float* F, int32_t* Q,
+                        void* stream);
 /* Continue every swarm for iters more iterations (after a run or a loaded state). */
 int sepso_bf_step(sepso_bf_handle h, int32_t iters);
 int sepso_bf_sync(sepso_bf_handle h);

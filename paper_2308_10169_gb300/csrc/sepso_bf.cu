@@ -54,10 +54,18 @@ constexpr int kUnroll = 4;
 constexpr int kMaxD = 16384;
 constexpr int kMaxRG = 4096;           // runs x groups: the CTA's key table
 constexpr int kSmemRows = 160 * 1024;  // shared-memory budget of the row buffers
+constexpr int kMaxEdges = 4096;        // polygon edges held in shared memory
 
 struct BfParams {
   int fn, D, Dp, G, N, M, R, K, hist_len;
   float lo, hi;
+  // objective 5 (a path among polygons): coordinates j >= half lie in [lo2, hi2]
+  // (y), the others in [lo, hi] (x); half = D for the benchmark functions
+  int half;
+  float lo2, hi2, alpha;
+  int beta, E;
+  const float4* edges;        // E polygon edges (x0, y0, x1, y1)
+  const float* pts;           // start x, y, target x, y
   uint32_t key0, key1, run_id;
   float* X;                   // R*M rows of Dp
   float* V;                   // R*M rows of Dp
@@ -157,6 +165,47 @@ __device__ __forceinline__ float bf_row(const float* s, int D, int lane) {
   }
 }
 
+// Eq. penalty's Q^beta for an integer beta >= 1, by repeated multiplication.
+__device__ __forceinline__ float pow_int(float q, int beta) {
+  float r = q;
+  for (int b = 1; b < beta; ++b) r *= q;
+  return r;
+}
+
+// Objective 5 (Sec. 3.3.1 map model; Eqs. path_fit, lenth, penalty): length of the
+// path start -> waypoints -> target plus alpha * Q^beta, Q = the number of proper
+// crossings (strict orientation tests) between its T + 1 segments and the E obstacle
+// edges.  Waypoint i is (s[i], s[T + i]).  The whole warp; every lane gets the value.
+__device__ __forceinline__ float poly_row(const float* s, int T, const float* pts, const float4* edges, int E,
+                                          float alpha, int beta, int lane, int& qout) {
+  float len = 0.0f;
+  for (int k = lane; k <= T; k += 32) {
+    const float ax = k == 0 ? pts[0] : s[k - 1], ay = k == 0 ? pts[1] : s[T + k - 1];
+    const float bx = k == T ? pts[2] : s[k], by = k == T ? pts[3] : s[T + k];
+    const float dx = bx - ax, dy = by - ay;
+    len += sqrtf(fmaf(dx, dx, dy * dy));
+  }
+  len = warp_sum(len);
+  int q = 0;
+  for (int k = 0; k <= T; ++k) {
+    const float ax = k == 0 ? pts[0] : s[k - 1], ay = k == 0 ? pts[1] : s[T + k - 1];
+    const float bx = k == T ? pts[2] : s[k], by = k == T ? pts[3] : s[T + k];
+    const float ux = bx - ax, uy = by - ay;
+    for (int e = lane; e < E; e += 32) {
+      const float4 d = edges[e];
+      const float vx = d.z - d.x, vy = d.w - d.y;
+      const float o1 = ux * (d.y - ay) - uy * (d.x - ax);
+      const float o2 = ux * (d.w - ay) - uy * (d.z - ax);
+      const float o3 = vx * (ay - d.y) - vy * (ax - d.x);
+      const float o4 = vx * (by - d.y) - vy * (bx - d.x);
+      q += (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
+    }
+  }
+  q = __reduce_add_sync(0xffffffffu, q);
+  qout = q;
+  return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -175,15 +224,17 @@ __global__ void bf_init_kernel(const BfParams p) {
     const int c = (int)(it - q * nch);
     const int r = (int)(q / p.M), pi = (int)(q - (size_t)r * p.M);
     const int g = pi / p.N;
-    const float vmax = p.hyper[((size_t)r * p.G + g) * 6 + 5] * ext;
+    const float vlim = p.hyper[((size_t)r * p.G + g) * 6 + 5];
     const uint4 ux = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitX, 0u, p.run_id + (uint32_t)r);
     const uint4 uv = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitV, 0u, p.run_id + (uint32_t)r);
     float xs[4], vs[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const bool in = 4 * c + e < p.D;
-      xs[e] = in ? p.lo + lane_of(ux, e) * ext : 0.0f;
-      vs[e] = in ? (2.0f * lane_of(uv, e) - 1.0f) * vmax : 0.0f;
+      const int jj = 4 * c + e;
+      const bool in = jj < p.D, second = jj >= p.half;
+      const float lo = second ? p.lo2 : p.lo, ex = second ? p.hi2 - p.lo2 : ext;
+      xs[e] = in ? lo + lane_of(ux, e) * ex : 0.0f;
+      vs[e] = in ? (2.0f * lane_of(uv, e) - 1.0f) * (vlim * ex) : 0.0f;
     }
     const float4 x4 = make_float4(xs[0], xs[1], xs[2], xs[3]);
     const float4 v4 = make_float4(vs[0], vs[1], vs[2], vs[3]);
@@ -213,8 +264,12 @@ __global__ void __launch_bounds__(256) bf_iter_kernel(const BfParams p, int j, i
   const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int RG = p.R * p.G;
   unsigned long long* ck = reinterpret_cast<unsigned long long*>(smem);
-  float* srow = reinterpret_cast<float*>(smem + ((size_t)RG * 8 + 15) / 16 * 16) + (size_t)warp * p.Dp;
+  const size_t keys_b = ((size_t)RG * 8 + 15) / 16 * 16;
+  float4* sedges = reinterpret_cast<float4*>(smem + keys_b);
+  const int E = FN == 5 ? p.E : 0;
+  float* srow = reinterpret_cast<float*>(smem + keys_b + (size_t)E * 16) + (size_t)warp * p.Dp;
   for (int i = threadIdx.x; i < RG; i += blockDim.x) ck[i] = kEmpty;
+  for (int i = threadIdx.x; i < E; i += blockDim.x) sedges[i] = p.edges[i];
 
   const unsigned long long* kprev = p.keys + (size_t)((j + 2) % 3) * RG;  // iteration j - 1
   unsigned long long* kcur = p.keys + (size_t)(j % 3) * RG;
@@ -248,7 +303,7 @@ __global__ void __launch_bounds__(256) bf_iter_kernel(const BfParams p, int j, i
       const float4* tr = reinterpret_cast<const float4*>(key_row(p, r, tk));
       const float* hy = p.hyper + ((size_t)r * p.G + g) * 6;
       const float c1 = hy[0], c2 = hy[1], c3 = hy[2], w_init = hy[3], w_end = hy[4];
-      const float vmax = hy[5] * ext;
+      const float vmax = hy[5] * ext, vmax2 = hy[5] * (p.hi2 - p.lo2);
       const int k = j - 1;
       const float w = w_init - (w_init - w_end) / (float)p.K * (float)k;
       const uint4 rr = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)pi, kStreamVel, 0u, p.run_id + (uint32_t)r);
@@ -283,13 +338,15 @@ __global__ void __launch_bounds__(256) bf_iter_kernel(const BfParams p, int j, i
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               if (4 * c + e < p.D) {
+                const bool second = FN == 5 && 4 * c + e >= p.half;
+                const float bv = second ? vmax2 : vmax;
                 float vv = w * ve[e];
                 vv = fmaf(a1, pe[e] - xe[e], vv);
                 vv = fmaf(a2, ge[e] - xe[e], vv);
                 if (need_T) vv = fmaf(a3, te[e] - xe[e], vv);
-                vv = fminf(fmaxf(vv, -vmax), vmax);
+                vv = fminf(fmaxf(vv, -bv), bv);
                 ve[e] = vv;
-                xe[e] = fminf(fmaxf(xe[e] + vv, p.lo), p.hi);
+                xe[e] = fminf(fmaxf(xe[e] + vv, second ? p.lo2 : p.lo), second ? p.hi2 : p.hi);
               }
             }
             xr[c] = x[u];
@@ -310,7 +367,9 @@ __global__ void __launch_bounds__(256) bf_iter_kernel(const BfParams p, int j, i
     if (!(mode & kEval)) continue;
 
     // Fitness of iteration j, Pbest update (strictly better only).
-    const float F = bf_row<FN>(srow, p.D, lane);
+    int qdummy;
+    const float F = FN == 5 ? poly_row(srow, p.half, p.pts, sedges, E, p.alpha, p.beta, lane, qdummy)
+                            : bf_row<FN>(srow, p.D, lane);
     float pf = p.Pfit[q];
     unsigned npar = par;
     if (F < pf) {
@@ -359,6 +418,21 @@ __global__ void bf_finish_kernel(const BfParams p, int k) {
   for (int i = threadIdx.x; i < p.Dp; i += blockDim.x) out[i] = src ? src[i] : 0.0f;
 }
 
+// Objective 5 of n paths (pitch ldx floats): fitness and Q, one warp per path.
+__global__ void poly_eval_kernel(const float* X, int ldx, int T, int n, float4 st, const float4* edges, int E,
+                                 float alpha, int beta, float* F, int* Q) {
+  const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const float pts[4] = {st.x, st.y, st.z, st.w};
+  for (int i = blockIdx.x * nwarps + (threadIdx.x >> 5); i < n; i += gridDim.x * nwarps) {
+    int q;
+    const float f = poly_row(X + (size_t)i * ldx, T, pts, edges, E, alpha, beta, lane, q);
+    if (lane == 0) {
+      F[i] = f;
+      if (Q) Q[i] = q;
+    }
+  }
+}
+
 // Fitness of n rows (pitch ldx floats), one warp per row.
 template <int FN>
 __global__ void bf_eval_kernel(const float* X, int ldx, int D, int n, float* F) {
@@ -399,7 +473,7 @@ int bffail(int code, const char* fmt, ...) {
 size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct BfLayout {
-  size_t X, V, P, Pfit, pcur, keys, thold, hyper, ext, hist, Gb, Gfit, Tb, Tfit, total;
+  size_t X, V, P, Pfit, pcur, keys, thold, hyper, ext, hist, Gb, Gfit, Tb, Tfit, edges, pts, total;
 };
 
 int padded(int D) { return (D + 3) & ~3; }
@@ -428,19 +502,30 @@ BfLayout bf_layout(const sepso_bf_config& c) {
   L.Gfit = take(R * G * 4);
   L.Tb = take(R * Dp * 4);
   L.Tfit = take(R * 4);
+  L.edges = take((size_t)(c.fn == 5 ? c.max_edges : 0) * 16);
+  L.pts = take(16);
   L.total = off;
   return L;
 }
 
 int bf_validate(const sepso_bf_config* c) {
   if (!c) return bffail(SEPSO_EINVAL, "NULL config");
-  if (c->fn < 1 || c->fn > 4) return bffail(SEPSO_EINVAL, "fn=%d is not one of BF1..BF4", c->fn);
+  if (c->fn < 1 || c->fn > 5) return bffail(SEPSO_EINVAL, "fn=%d is not one of 1..5", c->fn);
+  if (c->fn == 5) {
+    if (c->D < 2 || c->D % 2) return bffail(SEPSO_EINVAL, "a path needs an even D >= 2 (D=%d)", c->D);
+    if (!(c->map_w > 0.0f) || !(c->map_h > 0.0f) || !std::isfinite(c->map_w) || !std::isfinite(c->map_h))
+      return bffail(SEPSO_EINVAL, "map %g x %g", (double)c->map_w, (double)c->map_h);
+    if (!std::isfinite(c->alpha) || c->alpha < 0.0f) return bffail(SEPSO_EINVAL, "alpha=%g", (double)c->alpha);
+    if (c->beta < 1 || c->beta > 8) return bffail(SEPSO_EINVAL, "beta=%d outside [1, 8]", c->beta);
+    if (c->max_edges < 0 || c->max_edges > kMaxEdges)
+      return bffail(SEPSO_EINVAL, "max_edges=%d outside [0, %d]", c->max_edges, kMaxEdges);
+  }
   if (c->D < 1 || c->D > kMaxD) return bffail(SEPSO_EINVAL, "D=%d outside [1, %d]", c->D, kMaxD);
   if (c->G < 1 || c->G > 32) return bffail(SEPSO_EINVAL, "G=%d outside [1, 32]", c->G);
   if (c->N < 1) return bffail(SEPSO_EINVAL, "N=%d below 1", c->N);
   if (c->runs < 1) return bffail(SEPSO_EINVAL, "runs=%d below 1", c->runs);
   if (c->max_iters < 1) return bffail(SEPSO_EINVAL, "max_iters=%d below 1", c->max_iters);
-  if (!std::isfinite(c->lo) || !std::isfinite(c->hi) || !(c->lo < c->hi))
+  if (c->fn != 5 && (!std::isfinite(c->lo) || !std::isfinite(c->hi) || !(c->lo < c->hi)))
     return bffail(SEPSO_EINVAL, "box [%g, %g] is empty or not finite", (double)c->lo, (double)c->hi);
   if ((long long)c->runs * c->G > kMaxRG)
     return bffail(SEPSO_EINVAL, "runs x G = %lld above %d", (long long)c->runs * c->G, kMaxRG);
@@ -475,6 +560,7 @@ struct sepso_bf_ctx {
   int64_t k = -1;  // iterations done; -1 before the first run or state
   int64_t launches = 0;
   bool hyper_set = false;
+  bool scene_set = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -486,7 +572,8 @@ cudaError_t launch_iter(sepso_bf_ctx* h, int j, int mode) {
     case 1: bf_iter_kernel<1><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
     case 2: bf_iter_kernel<2><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
     case 3: bf_iter_kernel<3><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
-    default: bf_iter_kernel<4><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
+    case 4: bf_iter_kernel<4><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
+    default: bf_iter_kernel<5><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
   }
   return cudaGetLastError();
 }
@@ -534,8 +621,9 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
     return bffail(SEPSO_ENOSPC, "workspace of %zu bytes below the %zu needed", bytes, L.total);
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return bffail(SEPSO_ENOSPC, "workspace not 256-byte aligned");
   const int Dp = padded(c->D);
-  const int nwarps = std::max(1, std::min(8, kSmemRows / (Dp * 4)));
-  const size_t smem = ((size_t)c->runs * c->G * 8 + 15) / 16 * 16 + (size_t)nwarps * Dp * 4;
+  const int edge_b = c->fn == 5 ? c->max_edges * 16 : 0;
+  const int nwarps = std::max(1, std::min(8, (kSmemRows - edge_b) / (Dp * 4)));
+  const size_t smem = ((size_t)c->runs * c->G * 8 + 15) / 16 * 16 + (size_t)edge_b + (size_t)nwarps * Dp * 4;
   int dev = 0, sms = 0, bps = 0;
   BFCUDA(cudaGetDevice(&dev));
   BFCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -544,7 +632,8 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
     case 1: e = iter_attr<1>(smem); if (e == cudaSuccess) e = iter_occ<1>(&bps, nwarps * 32, smem); break;
     case 2: e = iter_attr<2>(smem); if (e == cudaSuccess) e = iter_occ<2>(&bps, nwarps * 32, smem); break;
     case 3: e = iter_attr<3>(smem); if (e == cudaSuccess) e = iter_occ<3>(&bps, nwarps * 32, smem); break;
-    default: e = iter_attr<4>(smem); if (e == cudaSuccess) e = iter_occ<4>(&bps, nwarps * 32, smem); break;
+    case 4: e = iter_attr<4>(smem); if (e == cudaSuccess) e = iter_occ<4>(&bps, nwarps * 32, smem); break;
+    default: e = iter_attr<5>(smem); if (e == cudaSuccess) e = iter_occ<5>(&bps, nwarps * 32, smem); break;
   }
   if (e != cudaSuccess) return bffail(SEPSO_ECUDA, "iteration kernel attributes: %s", cudaGetErrorString(e));
   if (bps < 1) return bffail(SEPSO_ERANGE, "iteration kernel does not fit an SM (%zu bytes of shared memory)", smem);
@@ -570,8 +659,15 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   p.R = c->runs;
   p.K = c->max_iters;
   p.hist_len = c->max_iters;
-  p.lo = c->lo;
-  p.hi = c->hi;
+  const bool path = c->fn == 5;
+  p.lo = path ? 0.0f : c->lo;
+  p.hi = path ? c->map_w : c->hi;
+  p.half = path ? c->D / 2 : c->D;
+  p.lo2 = path ? 0.0f : c->lo;
+  p.hi2 = path ? c->map_h : c->hi;
+  p.alpha = c->alpha;
+  p.beta = c->beta;
+  p.E = 0;
   p.key0 = (uint32_t)(c->seed & 0xffffffffu);
   p.key1 = (uint32_t)(c->seed >> 32);
   p.run_id = c->run_id;
@@ -590,6 +686,8 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   p.Gfit = reinterpret_cast<float*>(w + L.Gfit);
   p.Tb = reinterpret_cast<float*>(w + L.Tb);
   p.Tfit = reinterpret_cast<float*>(w + L.Tfit);
+  p.edges = reinterpret_cast<const float4*>(w + L.edges);
+  p.pts = reinterpret_cast<const float*>(w + L.pts);
   e = cudaMemsetAsync(workspace, 0, L.total, h->stream);
   if (e != cudaSuccess) {
     delete h;
@@ -624,9 +722,52 @@ int sepso_bf_set_hyper(sepso_bf_handle h, const float* hyper, int32_t run) {
   return SEPSO_OK;
 }
 
+int sepso_bf_set_polygons(sepso_bf_handle h, const float* start, const float* target, const float* edges,
+                          int32_t E) {
+  if (!h || !start || !target || (E > 0 && !edges)) return bffail(SEPSO_EINVAL, "NULL argument");
+  if (h->c.fn != 5) return bffail(SEPSO_EINVAL, "polygons belong to objective 5 (fn=%d)", h->c.fn);
+  if (E < 0 || E > h->c.max_edges) return bffail(SEPSO_EINVAL, "E=%d outside [0, max_edges=%d]", E, h->c.max_edges);
+  for (int i = 0; i < 2; ++i)
+    if (!std::isfinite(start[i]) || !std::isfinite(target[i])) return bffail(SEPSO_EINVAL, "start/target not finite");
+  for (int i = 0; i < 4 * E; ++i)
+    if (!std::isfinite(edges[i])) return bffail(SEPSO_EINVAL, "edge coordinate %d is not finite", i);
+  const float pts[4] = {start[0], start[1], target[0], target[1]};
+  if (E > 0)
+    BFCUDA(cudaMemcpyAsync(h->ws + h->L.edges, edges, (size_t)E * 16, cudaMemcpyHostToDevice, h->stream));
+  BFCUDA(cudaMemcpyAsync(h->ws + h->L.pts, pts, 16, cudaMemcpyHostToDevice, h->stream));
+  BFCUDA(cudaStreamSynchronize(h->stream));
+  if (h->p.E != E && h->exec) {   // the captured launches carry the old edge count
+    cudaGraphExecDestroy(h->exec);
+    cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+  }
+  h->p.E = E;
+  h->scene_set = true;
+  return SEPSO_OK;
+}
+
+int sepso_poly_evaluate(int32_t T, int32_t n, const float* X, int32_t ldx, const float* start, const float* target,
+                        const float* edges, int32_t E, float alpha, int32_t beta, float* F, int32_t* Q,
+                        void* stream) {
+  if (T < 1 || n < 0 || ldx < 2 * T || E < 0 || beta < 1 || beta > 8 || !std::isfinite(alpha))
+    return bffail(SEPSO_EINVAL, "T=%d, n=%d, ldx=%d, E=%d, beta=%d", T, n, ldx, E, beta);
+  if (!start || !target) return bffail(SEPSO_EINVAL, "NULL start/target");
+  if (n == 0) return SEPSO_OK;
+  if (!X || !F || (E > 0 && !edges)) return bffail(SEPSO_EINVAL, "NULL argument");
+  if (E > 0 && reinterpret_cast<uintptr_t>(edges) % 16) return bffail(SEPSO_EINVAL, "edges not 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = std::min((n + 7) / 8, 4096);
+  poly_eval_kernel<<<grid, 256, 0, s>>>(X, ldx, T, n, make_float4(start[0], start[1], target[0], target[1]),
+                                        reinterpret_cast<const float4*>(edges), E, alpha, beta, F, Q);
+  BFCUDA(cudaGetLastError());
+  return SEPSO_OK;
+}
+
 int sepso_bf_run_async(sepso_bf_handle h, int32_t use_graph) {
   if (!h) return bffail(SEPSO_EINVAL, "NULL handle");
   if (!h->hyper_set) return bffail(SEPSO_ESTATE, "run before set_hyper for every run");
+  if (h->c.fn == 5 && !h->scene_set) return bffail(SEPSO_ESTATE, "run before set_polygons");
   if (!use_graph) {
     const int rc = enqueue_run(h);
     if (rc) return rc;
@@ -794,7 +935,7 @@ int sepso_bf_set_state(sepso_bf_handle h, int32_t run, const float* X, const flo
 }
 
 int sepso_bf_evaluate(int32_t fn, int32_t D, int32_t n, const float* X, int32_t ldx, float* F, void* stream) {
-  if (fn < 1 || fn > 4) return bffail(SEPSO_EINVAL, "fn=%d is not one of BF1..BF4", fn);
+  if (fn < 1 || fn > 4) return bffail(SEPSO_EINVAL, "fn=%d is not one of BF1..BF4 (paths: sepso_poly_evaluate)", fn);
   if (D < 1 || n < 0 || ldx < D) return bffail(SEPSO_EINVAL, "D=%d, n=%d, ldx=%d", D, n, ldx);
   if (n == 0) return SEPSO_OK;
   if (!X || !F) return bffail(SEPSO_EINVAL, "NULL argument");

@@ -261,6 +261,7 @@ class BFConfig:
     map_h: float = 400.0
     alpha: float = 30.0
     beta: int = 4
+    max_edges: int = 0
 
     def with_(self, **kw) -> "BFConfig":
         return replace(self, **kw)
@@ -315,13 +316,14 @@ def polygon_workload(seed: int = 0, T: int = 8, N: int = 170, n_boxes: int = 12,
         for _ in range(rot):
             u = np.stack([-u[:, 1], u[:, 0]], axis=1)
         polys.append([(cx + a, cy + b) for a, b in u])
+    edges = polygon_edges(polys)
     cfg = BFConfig(fn=POLYGON_PATH, D=2 * T, G=8, N=N, lo=0.0, hi=400.0, max_iters=iters, seed=seed,
                    runs=runs, map_w=400.0, map_h=400.0, alpha=PARAMS_PATH["alpha"],
-                   beta=PARAMS_PATH["beta"])
+                   beta=PARAMS_PATH["beta"], max_edges=max(len(edges), 1))
     start = np.array([20.0, 20.0], np.float32)
     target = np.array([380.0, 380.0], np.float32)
     hyper = np.ascontiguousarray(TABLE_HYPER8_PATH, dtype=np.float32)
-    return cfg, start, target, polys, polygon_edges(polys), hyper
+    return cfg, start, target, polys, edges, hyper
 
 
 def random_paths(seed: int, n: int, T: int, W: float = 400.0, H: float = 400.0) -> np.ndarray:

@@ -263,6 +263,13 @@ class BFPlanner:
         h = _f32(hyper, (self.cfg.G, 6))
         check_bf(self.lib.sepso_bf_set_hyper(self._h, h.ctypes.data, run))
 
+    def set_polygons(self, start, target, edges):
+        """Objective 5: obstacle edges (E, 4) float32 (x0, y0, x1, y1), start, target."""
+        e = _f32(edges, (-1, 4))
+        st, tg = _f32(start, (2,)), _f32(target, (2,))
+        check_bf(self.lib.sepso_bf_set_polygons(self._h, st.ctypes.data, tg.ctypes.data,
+                                                e.ctypes.data if e.size else None, e.shape[0]))
+
     def run_async(self, use_graph: bool = True):
         check_bf(self.lib.sepso_bf_run_async(self._h, int(use_graph)))
 
@@ -308,6 +315,24 @@ class BFPlanner:
 
     def launch_count(self) -> int:
         return int(self.lib.sepso_bf_launch_count(self._h))
+
+
+def poly_evaluate(X: torch.Tensor, start, target, edges: torch.Tensor, alpha: float, beta: int):
+    """Objective 5 of the rows of a CUDA float32 tensor (n, 2T) among CUDA float32
+    edges (E, 4): (fitness, Q) tensors."""
+    assert X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
+    assert edges.is_cuda and edges.dtype == torch.float32 and edges.is_contiguous()
+    n, D = X.shape
+    F = torch.empty(n, dtype=torch.float32, device=X.device)
+    Q = torch.empty(n, dtype=torch.int32, device=X.device)
+    st, tg = _f32(start, (2,)), _f32(target, (2,))
+    stream = torch.cuda.current_stream(X.device).cuda_stream
+    check_bf(_native.lib().sepso_poly_evaluate(D // 2, n, ctypes.c_void_p(X.data_ptr()), X.stride(0),
+                                               st.ctypes.data, tg.ctypes.data,
+                                               ctypes.c_void_p(edges.data_ptr()), edges.shape[0],
+                                               ctypes.c_float(alpha), beta, ctypes.c_void_p(F.data_ptr()),
+                                               ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(stream)))
+    return F, Q
 
 
 def bf_evaluate(fn: int, X: torch.Tensor) -> torch.Tensor:

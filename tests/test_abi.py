@@ -206,7 +206,9 @@ def test_bf_workspace_size_and_bad_configs():
     assert rc == 0 and s2 > 40 * s1
     rc, big = size(fn=3, D=1000, G=8, N=2048, runs=1)
     assert rc == 0 and big >= 16384 * 1000 * 16        # X, V and two Pbest buffers
-    for bad in (dict(fn=0), dict(fn=5), dict(D=0), dict(D=16385), dict(G=0), dict(G=33), dict(N=0),
+    assert size(fn=5, D=16, G=8, N=170, max_edges=80)[0] == 0     # a path among polygons
+    for bad in (dict(fn=5, D=15), dict(fn=5, beta=0), dict(fn=5, beta=9), dict(fn=5, max_edges=4097),
+                dict(fn=5, map_w=0.0), dict(fn=5, alpha=-1.0), dict(fn=6), dict(fn=0), dict(D=0), dict(D=16385), dict(G=0), dict(G=33), dict(N=0),
                 dict(runs=0), dict(max_iters=0), dict(lo=1.0, hi=1.0), dict(lo=float("nan")),
                 dict(hi=float("inf")), dict(runs=600, G=8)):
         assert size(**bad)[0] == -1, bad
@@ -221,3 +223,13 @@ def test_bf_workspace_size_and_bad_configs():
     assert L.sepso_bf_evaluate(1, 30, 4, X, 29, X, None) == -1     # pitch below D
     assert L.sepso_bf_evaluate(1, 30, 0, None, 30, None, None) == 0  # nothing to do
     assert L.sepso_bf_step(None, 1) == -1 and L.sepso_bf_run_async(None, 1) == -1
+    st = np.zeros(2, np.float32)
+    assert L.sepso_bf_set_polygons(None, st.ctypes.data, st.ctypes.data, None, 0) == -1
+    P = st.ctypes.data
+    assert L.sepso_poly_evaluate(0, 4, X, 16, P, P, X, 4, ctypes.c_float(30.0), 4, X, None, None) == -1
+    assert L.sepso_poly_evaluate(8, 4, X, 15, P, P, X, 4, ctypes.c_float(30.0), 4, X, None, None) == -1
+    assert L.sepso_poly_evaluate(8, 4, X, 16, P, P, X, 4, ctypes.c_float(30.0), 0, X, None, None) == -1
+    assert L.sepso_poly_evaluate(8, 4, X, 16, P, P, ctypes.c_void_p((1 << 20) + 4), 4, ctypes.c_float(30.0),
+                                 4, X, None, None) == -1                 # edges misaligned
+    assert L.sepso_poly_evaluate(8, 0, None, 16, P, P, None, 0, ctypes.c_float(30.0), 4, None, None,
+                                 None) == 0
