@@ -78,10 +78,11 @@ def parse():
     ap.add_argument("--prior-rounds", type=int, default=3)
     ap.add_argument("--prior-epochs", type=int, default=30)
     ap.add_argument("--prior-batch", type=int, default=4096, help="rows per Adam step")
-    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper,bf",
-                    help="comma list of main, cpu, batch, prior, serve, paper, bf, gemm (paper: the "
-                         "ablation variants of the path-planning comparison; bf: the benchmark "
-                         "functions; gemm: the tensor-core GEMM alone)")
+    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper,bf,poly",
+                    help="comma list of main, cpu, batch, prior, serve, paper, bf, poly, gemm (paper: "
+                         "the ablation variants of the path-planning comparison; bf: the benchmark "
+                         "functions; poly: planning among polygon obstacles; gemm: the tensor-core "
+                         "GEMM alone)")
     ap.add_argument("--bf-fns", type=str, default="1,2,3,4", help="benchmark functions (1..4) of section bf")
     ap.add_argument("--bf-iters", type=int, default=1400, help="iterations per benchmark-function run")
     ap.add_argument("--bf-trials", type=int, default=50,
@@ -557,6 +558,51 @@ def run_bf(fns, iters: int, trials: int, peak_gbs: float):
     return out
 
 
+def run_poly(runs: int = 64, iters: int = 100):
+    """Path planning among polygon obstacles (Sec. 3.3.1's map model): ``runs``
+    independent plans of one static scene (12 boxes + 4 non-convex U shapes, 80
+    edges), T = 8, G = 8 x 170, Table hyper8path, alpha = 30, beta = 4, ``iters``
+    iterations, one CUDA graph per batch of runs; also one plan alone (latency)."""
+    import torch
+
+    from paper_2308_10169_gb300 import BFPlanner
+    from paper_2308_10169_gb300.inputs import polygon_workload
+    from paper_2308_10169_gb300.planner import poly_evaluate
+    out = {}
+    for R in (runs, 1):
+        cfg, start, target, polys, edges, hy = polygon_workload(0, iters=iters, runs=R)
+        pl = BFPlanner(cfg)
+        pl.set_hyper(hy)
+        pl.set_polygons(start, target, edges)
+        pl.run_async()
+        pl.sync()
+        l0 = pl.launch_count()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(pl.stream)
+        pl.run_async()
+        b.record(pl.stream)
+        pl.sync()
+        ms = a.elapsed_time(b)
+        best = np.stack([pl.read(r)["x"] for r in range(R)])
+        F, Q = poly_evaluate(torch.from_numpy(best).cuda(), start, target, torch.from_numpy(edges).cuda(),
+                             cfg.alpha, cfg.beta)
+        Q = Q.cpu().numpy()
+        M, T, E = cfg.G * cfg.N, cfg.D // 2, edges.shape[0]
+        pairs = R * M * (T + 1) * E * iters
+        achieved = pairs * 20 / (ms / 1e3) / 1e12
+        out["batch" if R == runs else "single"] = {
+            "runs": R, "ms": ms, "plans_per_s": R / (ms / 1e3), "us_per_iteration": 1e3 * ms / iters,
+            "median_cost": float(np.median(F.cpu().numpy())), "collision_free": float(np.mean(Q == 0)),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "kernel": "bf_iter_kernel<5>",
+                         "flops_per_pair": 20},
+            "gpu_launches": pl.launch_count() - l0}
+        del pl
+    out["workload"] = (f"400x400 map, 12 boxes + 4 U-shaped polygons (80 edges), T=8, G=8 x 170, "
+                       f"{iters} iterations, Table hyper8path, alpha=30 beta=4, {runs} plans per graph")
+    return out
+
+
 def _world_step(ag):
     """The client's simulated world between two requests of an agent: circles and
     start/target move by their velocity and bounce off the map border."""
@@ -816,6 +862,8 @@ def main():
                                       line, args.prior_batch)
         if world == 1 and "paper" in sections:
             line["paper_ablation"] = run_paper()
+        if world == 1 and "poly" in sections:
+            line["poly"] = run_poly()
         if world == 1 and "bf" in sections:
             line["bf"] = run_bf([int(x) for x in args.bf_fns.split(",") if x.strip()], args.bf_iters,
                                 args.bf_trials, _hbm_peak())

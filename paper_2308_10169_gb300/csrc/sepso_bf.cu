@@ -53,7 +53,7 @@ constexpr int kUpdate = 1, kEval = 2;
 constexpr int kUnroll = 4;
 constexpr int kMaxD = 16384;
 constexpr int kMaxRG = 4096;           // runs x groups: the CTA's key table
-constexpr int kSmemRows = 160 * 1024;  // shared-memory budget of the row buffers
+constexpr int kSmemTotal = 200 * 1024;  // shared-memory budget of the iteration kernel
 constexpr int kMaxEdges = 4096;        // polygon edges held in shared memory
 
 struct BfParams {
@@ -259,46 +259,69 @@ __global__ void bf_init_kernel(const BfParams p) {
 // this launch evaluates; the update it applies first is iteration j - 1's.
 // ---------------------------------------------------------------------------
 template <int FN>
-__global__ void __launch_bounds__(256) bf_iter_kernel(const BfParams p, int j, int mode) {
+__global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j, int mode) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int RG = p.R * p.G;
+  // shared memory: this launch's candidate keys, iteration j - 1's group keys and
+  // Tbest keys (copied once per CTA), the polygon edges, one row per warp
   unsigned long long* ck = reinterpret_cast<unsigned long long*>(smem);
-  const size_t keys_b = ((size_t)RG * 8 + 15) / 16 * 16;
+  unsigned long long* sgk = ck + RG;
+  unsigned long long* stk = sgk + RG;
+  const size_t keys_b = ((size_t)(2 * RG + p.R) * 8 + 15) / 16 * 16;
   float4* sedges = reinterpret_cast<float4*>(smem + keys_b);
   const int E = FN == 5 ? p.E : 0;
   float* srow = reinterpret_cast<float*>(smem + keys_b + (size_t)E * 16) + (size_t)warp * p.Dp;
-  for (int i = threadIdx.x; i < RG; i += blockDim.x) ck[i] = kEmpty;
-  for (int i = threadIdx.x; i < E; i += blockDim.x) sedges[i] = p.edges[i];
-
   const unsigned long long* kprev = p.keys + (size_t)((j + 2) % 3) * RG;  // iteration j - 1
   unsigned long long* kcur = p.keys + (size_t)(j % 3) * RG;
+  for (int i = threadIdx.x; i < RG; i += blockDim.x) {
+    ck[i] = kEmpty;
+    if (mode & kUpdate) sgk[i] = kprev[i];
+  }
+  for (int i = threadIdx.x; i < E; i += blockDim.x) sedges[i] = p.edges[i];
   if (blockIdx.x == 0) {
     unsigned long long* knext = p.keys + (size_t)((j + 1) % 3) * RG;   // read last in launch j - 1
     for (int i = threadIdx.x; i < RG; i += blockDim.x) knext[i] = kEmpty;
   }
   __syncthreads();
+  if (mode & kUpdate) {
+    // Tbest of iteration j - 1 per run: the group keys and the previous holder.
+    for (int r = threadIdx.x; r < p.R; r += blockDim.x) {
+      const unsigned long long tk = resolve_T(sgk + (size_t)r * p.G, p.G, p.thold[(size_t)(j % 2) * p.R + r]);
+      stk[r] = tk;
+      if (blockIdx.x == 0) {
+        p.thold[(size_t)((j + 1) % 2) * p.R + r] = tk;
+        if (j - 2 < p.hist_len)
+          p.hist[(size_t)r * p.hist_len + (j - 2)] = tk == kEmpty ? INFINITY : float_of_ord((uint32_t)(tk >> 32));
+      }
+    }
+    __syncthreads();
+  }
 
   const float ext = p.hi - p.lo;
   const int nch = p.Dp >> 2;
   const size_t total = (size_t)p.R * p.M;
-  for (size_t q = (size_t)blockIdx.x * nwarps + warp; q < total; q += (size_t)gridDim.x * nwarps) {
+  const size_t stride = (size_t)gridDim.x * nwarps;
+  const size_t q0 = (size_t)blockIdx.x * nwarps + warp;
+  // this particle's Pbest parity and fitness, loaded one particle ahead (only this
+  // warp writes them)
+  unsigned par_next = q0 < total ? p.pcur[q0] : 0u;
+  float pf_next = q0 < total ? p.Pfit[q0] : 0.0f;
+  for (size_t q = q0; q < total; q += stride) {
     const int r = (int)(q / p.M), pi = (int)(q - (size_t)r * p.M);
     const int g = pi / p.N;
     float4* xr = reinterpret_cast<float4*>(p.X + q * p.Dp);
     float4* s4 = reinterpret_cast<float4*>(srow);
-    const unsigned par = p.pcur[q];
+    const unsigned par = par_next;
+    float pf = pf_next;
+    if (q + stride < total) {
+      par_next = p.pcur[q + stride];
+      pf_next = p.Pfit[q + stride];
+    }
     if (mode & kUpdate) {
-      // Bests of iteration j - 1: this group's key, and Tbest from all group keys
-      // and the previous Tbest holder.
-      const unsigned long long* gk = kprev + (size_t)r * p.G;
-      const unsigned long long told = p.thold[(size_t)(j % 2) * p.R + r];   // iteration j - 2
-      const unsigned long long tk = resolve_T(gk, p.G, told);
-      if (pi == 0 && lane == 0) {
-        p.thold[(size_t)((j + 1) % 2) * p.R + r] = tk;                      // iteration j - 1
-        if (j - 2 < p.hist_len)
-          p.hist[(size_t)r * p.hist_len + (j - 2)] = tk == kEmpty ? INFINITY : float_of_ord((uint32_t)(tk >> 32));
-      }
+      // Bests of iteration j - 1: this group's key and the run's Tbest key.
+      const unsigned long long* gk = sgk + (size_t)r * p.G;
+      const unsigned long long tk = stk[r];
       const float4* gr = reinterpret_cast<const float4*>(key_row(p, r, gk[g]));
       const float4* tr = reinterpret_cast<const float4*>(key_row(p, r, tk));
       const float* hy = p.hyper + ((size_t)r * p.G + g) * 6;
@@ -370,7 +393,6 @@ __global__ void __launch_bounds__(256) bf_iter_kernel(const BfParams p, int j, i
     int qdummy;
     const float F = FN == 5 ? poly_row(srow, p.half, p.pts, sedges, E, p.alpha, p.beta, lane, qdummy)
                             : bf_row<FN>(srow, p.D, lane);
-    float pf = p.Pfit[q];
     unsigned npar = par;
     if (F < pf) {
       npar = par ^ 1u;
@@ -622,8 +644,14 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return bffail(SEPSO_ENOSPC, "workspace not 256-byte aligned");
   const int Dp = padded(c->D);
   const int edge_b = c->fn == 5 ? c->max_edges * 16 : 0;
-  const int nwarps = std::max(1, std::min(8, (kSmemRows - edge_b) / (Dp * 4)));
-  const size_t smem = ((size_t)c->runs * c->G * 8 + 15) / 16 * 16 + (size_t)edge_b + (size_t)nwarps * Dp * 4;
+  const size_t RG = (size_t)c->runs * c->G;
+  const size_t keys_b = ((2 * RG + c->runs) * 8 + 15) / 16 * 16;
+  const long long rows_budget = (long long)kSmemTotal - (long long)keys_b - edge_b;
+  if (rows_budget < (long long)Dp * 4)
+    return bffail(SEPSO_ERANGE, "D=%d with %d edges and %zu group keys exceeds shared memory", c->D,
+                  c->fn == 5 ? c->max_edges : 0, RG);
+  const int nwarps = (int)std::min<long long>(8, rows_budget / ((long long)Dp * 4));
+  const size_t smem = keys_b + (size_t)edge_b + (size_t)nwarps * Dp * 4;
   int dev = 0, sms = 0, bps = 0;
   BFCUDA(cudaGetDevice(&dev));
   BFCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
