@@ -574,6 +574,7 @@ def run_poly(runs: int = 64, iters: int = 100):
         pl = BFPlanner(cfg)
         pl.set_hyper(hy)
         pl.set_polygons(start, target, edges)
+        kname = pl.kernel_name()
         pl.run_async()
         pl.sync()
         l0 = pl.launch_count()
@@ -594,7 +595,7 @@ def run_poly(runs: int = 64, iters: int = 100):
             "runs": R, "ms": ms, "plans_per_s": R / (ms / 1e3), "us_per_iteration": 1e3 * ms / iters,
             "median_cost": float(np.median(F.cpu().numpy())), "collision_free": float(np.mean(Q == 0)),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "kernel": "bf_iter_kernel<5>",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "kernel": kname,
                          "flops_per_pair": 20},
             "gpu_launches": pl.launch_count() - l0}
         del pl

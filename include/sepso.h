@@ -684,6 +684,10 @@ int sepso_bf_set_state(sepso_bf_handle h, int32_t run, const float* X, const flo
  * F[n], on stream.  Errors: EINVAL, ECUDA. */
 int sepso_bf_evaluate(int32_t fn, int32_t D, int32_t n, const float* X, int32_t ldx, float* F, void* stream);
 int64_t sepso_bf_launch_count(sepso_bf_handle h);
+/* Name of the iteration kernel this handle launches: bf_iter_kernel<fn> (a warp per
+ * particle), or poly_lane_kernel (objective 5, D <= 64, at least 256 particles per
+ * SM: a lane per particle).  Static string. */
+const char* sepso_bf_kernel_name(sepso_bf_handle h);
 const char* sepso_bf_last_error(void);
 
 /* Auto Truncation window criterion (Sec. 3.3.4, first criterion) on its own, for

@@ -224,6 +224,7 @@ SIGNATURES = {
     "sepso_poly_evaluate": (ctypes.c_int, [_i32, _i32, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.c_float,
                                            _i32, _vp, _vp, _vp]),
     "sepso_bf_launch_count": (ctypes.c_int64, [_vp]),
+    "sepso_bf_kernel_name": (ctypes.c_char_p, [_vp]),
     "sepso_bf_last_error": (ctypes.c_char_p, []),
     "sepso_watchdog_selftest": (ctypes.c_int, [_i32, ctypes.POINTER(_i32), _vp]),
     "sepso_strerror": (ctypes.c_char_p, [ctypes.c_int]),

@@ -413,6 +413,142 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
 }
 
 // ---------------------------------------------------------------------------
+// Objective 5 with a lane per particle: the iteration of bf_iter_kernel for short
+// rows (paths of D = 2T <= kLaneMaxD coordinates), where a warp per particle would
+// leave most lanes idle in the update and spread each path's few segments over the
+// lanes.  Lane l of a warp owns one particle: it updates its row coordinate by
+// coordinate, keeps the new row in shared memory (stride D + 1: the lanes' rows fall
+// in different banks) and tests its T + 1 segments against every edge, the edge
+// read by all lanes at once (a broadcast).  Bests, keys and Pbest parities as in
+// bf_iter_kernel.
+// ---------------------------------------------------------------------------
+constexpr int kLaneMaxD = 64;
+constexpr int kLaneThreads = 256;
+constexpr int kLaneMinPerSm = 256;   // particles per SM from which objective 5 uses a lane each
+
+__device__ __forceinline__ float poly_lane(const float* s, int T, const float* pts, const float4* edges, int E,
+                                           float alpha, int beta) {
+  float len = 0.0f;
+  int q = 0;
+  for (int k = 0; k <= T; ++k) {
+    const float ax = k == 0 ? pts[0] : s[k - 1], ay = k == 0 ? pts[1] : s[T + k - 1];
+    const float bx = k == T ? pts[2] : s[k], by = k == T ? pts[3] : s[T + k];
+    const float ux = bx - ax, uy = by - ay;
+    len += sqrtf(fmaf(ux, ux, uy * uy));
+    for (int e = 0; e < E; ++e) {
+      const float4 d = edges[e];
+      const float vx = d.z - d.x, vy = d.w - d.y;
+      const float o1 = ux * (d.y - ay) - uy * (d.x - ax);
+      const float o2 = ux * (d.w - ay) - uy * (d.z - ax);
+      const float o3 = vx * (ay - d.y) - vy * (ax - d.x);
+      const float o4 = vx * (by - d.y) - vy * (bx - d.x);
+      q += (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
+    }
+  }
+  return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
+}
+
+__global__ void __launch_bounds__(256) poly_lane_kernel(const BfParams p, int j, int mode) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int RG = p.R * p.G;
+  const int D = p.D, T = p.half;
+  unsigned long long* ck = reinterpret_cast<unsigned long long*>(smem);
+  unsigned long long* sgk = ck + RG;
+  unsigned long long* stk = sgk + RG;
+  const size_t keys_b = ((size_t)(2 * RG + p.R) * 8 + 15) / 16 * 16;
+  float4* sedges = reinterpret_cast<float4*>(smem + keys_b);
+  const int E = p.E;
+  float* srow = reinterpret_cast<float*>(smem + keys_b + (size_t)E * 16) +
+                ((size_t)warp * 32 + lane) * (D + 1);
+  const unsigned long long* kprev = p.keys + (size_t)((j + 2) % 3) * RG;
+  unsigned long long* kcur = p.keys + (size_t)(j % 3) * RG;
+  for (int i = threadIdx.x; i < RG; i += blockDim.x) {
+    ck[i] = kEmpty;
+    if (mode & kUpdate) sgk[i] = kprev[i];
+  }
+  for (int i = threadIdx.x; i < E; i += blockDim.x) sedges[i] = p.edges[i];
+  if (blockIdx.x == 0) {
+    unsigned long long* knext = p.keys + (size_t)((j + 1) % 3) * RG;
+    for (int i = threadIdx.x; i < RG; i += blockDim.x) knext[i] = kEmpty;
+  }
+  __syncthreads();
+  if (mode & kUpdate) {
+    for (int r = threadIdx.x; r < p.R; r += blockDim.x) {
+      const unsigned long long tk = resolve_T(sgk + (size_t)r * p.G, p.G, p.thold[(size_t)(j % 2) * p.R + r]);
+      stk[r] = tk;
+      if (blockIdx.x == 0) {
+        p.thold[(size_t)((j + 1) % 2) * p.R + r] = tk;
+        if (j - 2 < p.hist_len)
+          p.hist[(size_t)r * p.hist_len + (j - 2)] = tk == kEmpty ? INFINITY : float_of_ord((uint32_t)(tk >> 32));
+      }
+    }
+    __syncthreads();
+  }
+
+  const size_t total = (size_t)p.R * p.M;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+    const int r = (int)(q / p.M), pi = (int)(q - (size_t)r * p.M);
+    const int g = pi / p.N;
+    float* xr = p.X + q * p.Dp;
+    const unsigned par = p.pcur[q];
+    float pf = p.Pfit[q];
+    if (mode & kUpdate) {
+      const unsigned long long* gk = sgk + (size_t)r * p.G;
+      const float* gr = key_row(p, r, gk[g]);
+      const float* tr = key_row(p, r, stk[r]);
+      const float* hy = p.hyper + ((size_t)r * p.G + g) * 6;
+      const float c1 = hy[0], c2 = hy[1], c3 = hy[2], w_init = hy[3], w_end = hy[4];
+      const float vmax = hy[5] * (p.hi - p.lo), vmax2 = hy[5] * (p.hi2 - p.lo2);
+      const int k = j - 1;
+      const float w = w_init - (w_init - w_end) / (float)p.K * (float)k;
+      const uint4 rr = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)pi, kStreamVel, 0u, p.run_id + (uint32_t)r);
+      const float a1 = c1 * u01(rr.x), a2 = c2 * u01(rr.y), a3 = c3 * u01(rr.z);
+      const bool need_T = c3 != 0.0f;
+      float* vr = p.V + q * p.Dp;
+      const float* pr = p.P + ((size_t)par * total + q) * p.Dp;
+      for (int i = 0; i < D; ++i) {
+        const bool second = i >= T;
+        const float bv = second ? vmax2 : vmax;
+        float x = xr[i];
+        float vv = w * vr[i];
+        vv = fmaf(a1, pr[i] - x, vv);
+        vv = fmaf(a2, (gr ? gr[i] : 0.0f) - x, vv);
+        if (need_T) vv = fmaf(a3, (tr ? tr[i] : 0.0f) - x, vv);
+        vv = fminf(fmaxf(vv, -bv), bv);
+        vr[i] = vv;
+        x = fminf(fmaxf(x + vv, second ? p.lo2 : p.lo), second ? p.hi2 : p.hi);
+        xr[i] = x;
+        srow[i] = x;
+      }
+      if (pi == 0)
+        for (int gg = 0; gg < p.G; ++gg) {
+          const unsigned long long kk = gk[gg];
+          if (kk != kEmpty) atomicMin(&ck[r * p.G + gg], kk & ~(1ull << 31));
+        }
+    } else {
+      for (int i = 0; i < D; ++i) srow[i] = xr[i];
+    }
+    if (!(mode & kEval)) continue;
+    const float F = poly_lane(srow, T, p.pts, sedges, E, p.alpha, p.beta);
+    unsigned npar = par;
+    if (F < pf) {
+      npar = par ^ 1u;
+      float* dst = p.P + ((size_t)npar * total + q) * p.Dp;
+      for (int i = 0; i < D; ++i) dst[i] = srow[i];
+      pf = F;
+      p.Pfit[q] = F;
+      p.pcur[q] = (unsigned char)npar;
+    }
+    if (isfinite(pf)) atomicMin(&ck[r * p.G + g], make_key(pf, 1u, (uint32_t)pi, npar));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < RG; i += blockDim.x)
+    if (ck[i] != kEmpty) atomicMin(&kcur[i], ck[i]);
+}
+
+// ---------------------------------------------------------------------------
 // Bests after iteration k (the last launch): Gbest rows and fitness per group, the
 // Tbest row and fitness, the last history entry.  One block per (run, slot), slot
 // G = Tbest.  Reads only; a later launch continues from the same keys.
@@ -579,6 +715,8 @@ struct sepso_bf_ctx {
   cudaStream_t stream = nullptr;
   int threads = 0, grid = 0, init_grid = 0;
   size_t smem = 0;
+  int grid_lane = 0;  // > 0: objective 5 runs on poly_lane_kernel
+  size_t smem_lane = 0;
   int64_t k = -1;  // iterations done; -1 before the first run or state
   int64_t launches = 0;
   bool hyper_set = false;
@@ -590,6 +728,10 @@ struct sepso_bf_ctx {
 namespace {
 
 cudaError_t launch_iter(sepso_bf_ctx* h, int j, int mode) {
+  if (h->grid_lane > 0) {
+    poly_lane_kernel<<<h->grid_lane, kLaneThreads, h->smem_lane, h->stream>>>(h->p, j, mode);
+    return cudaGetLastError();
+  }
   switch (h->c.fn) {
     case 1: bf_iter_kernel<1><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
     case 2: bf_iter_kernel<2><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
@@ -675,6 +817,22 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   h->smem = smem;
   const long long RM = (long long)c->runs * c->G * c->N;
   h->grid = (int)std::min<long long>((RM + nwarps - 1) / nwarps, (long long)bps * sms);
+  // A lane per particle pays once there are enough particles to give every SM's
+  // lanes work (below that, one path's tests spread over a warp finish sooner).
+  if (c->fn == 5 && c->D <= kLaneMaxD && RM >= (long long)kLaneMinPerSm * sms) {
+    const size_t sl = keys_b + (size_t)edge_b + (size_t)kLaneThreads * (c->D + 1) * 4;
+    int bl = 0;
+    e = cudaFuncSetAttribute(poly_lane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, poly_lane_kernel, kLaneThreads, sl);
+    if (e != cudaSuccess) {
+      delete h;
+      return bffail(SEPSO_ECUDA, "lane kernel attributes: %s", cudaGetErrorString(e));
+    }
+    if (bl > 0) {
+      h->smem_lane = sl;
+      h->grid_lane = (int)std::min<long long>((RM + kLaneThreads - 1) / kLaneThreads, (long long)bl * sms);
+    }
+  }
   const long long init_items = RM * (Dp / 4);
   h->init_grid = (int)std::max<long long>(1, std::min<long long>((init_items + 255) / 256, 8ll * sms));
   BfParams& p = h->p;
@@ -868,6 +1026,14 @@ int sepso_bf_history(sepso_bf_handle h, int32_t run, float* hist) {
 }
 
 int64_t sepso_bf_launch_count(sepso_bf_handle h) { return h ? h->launches : -1; }
+
+const char* sepso_bf_kernel_name(sepso_bf_handle h) {
+  if (!h) return "";
+  if (h->grid_lane > 0) return "poly_lane_kernel";
+  static const char* names[] = {"", "bf_iter_kernel<1>", "bf_iter_kernel<2>", "bf_iter_kernel<3>",
+                                "bf_iter_kernel<4>", "bf_iter_kernel<5>"};
+  return names[h->c.fn];
+}
 
 int sepso_bf_get_state(sepso_bf_handle h, int32_t run, float* X, float* V, float* P, float* Pfit, float* Gb,
                        float* Gfit, float* Tb, float* Tfit, int32_t* k) {

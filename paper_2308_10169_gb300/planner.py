@@ -316,6 +316,9 @@ class BFPlanner:
     def launch_count(self) -> int:
         return int(self.lib.sepso_bf_launch_count(self._h))
 
+    def kernel_name(self) -> str:
+        return self.lib.sepso_bf_kernel_name(self._h).decode()
+
 
 def poly_evaluate(X: torch.Tensor, start, target, edges: torch.Tensor, alpha: float, beta: int):
     """Objective 5 of the rows of a CUDA float32 tensor (n, 2T) among CUDA float32

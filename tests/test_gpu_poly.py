@@ -130,3 +130,39 @@ def test_new_polygons_recapture_the_graph(native):
     b.run_async(use_graph=False)
     for r in range(2):
         np.testing.assert_array_equal(a.read(r)["x"], b.read(r)["x"])
+
+
+def test_lane_per_particle_kernel_matches_oracle(native):
+    # enough particles (32 plans x 8 x 170) for the lane-per-particle kernel; two
+    # iterations of every plan vs the oracle, on the plans whose evaluated positions
+    # stay clear of flipping crossing decisions
+    cfg, start, target, polys, edges, hy = polygon_workload(4, iters=2, runs=32)
+    pl = BFPlanner(cfg)
+    assert pl.kernel_name() == "poly_lane_kernel"
+    small = BFPlanner(cfg.with_(runs=1))
+    assert small.kernel_name() == "bf_iter_kernel<5>"
+    pl.set_hyper(hy)
+    pl.set_polygons(start, target, edges)
+    pl.run_async()
+    sc = _scene(start, target, edges)
+    checked = 0
+    for r in range(0, 32, 4):
+        sw = oracle.BFSwarm(cfg.with_(runs=1, run_id=r), hy, sc)
+        sw.init()
+        ok = True
+        for _ in range(2):
+            if not _margins_ok(cfg, sc, sw.s["X"]):
+                ok = False
+                break
+            sw.iteration()
+        if not ok:
+            continue
+        checked += 1
+        s, o = pl.get_state(r), sw.state()
+        _close(s["X"], o["X"], 400.0)
+        _close(s["V"], o["V"], float(hy[:, 5].max()) * 400.0)
+        np.testing.assert_allclose(s["Pfit"], o["Pfit"], rtol=1e-5)
+        np.testing.assert_allclose(s["Gfit"], o["Gfit"], rtol=1e-5)
+        assert s["Tfit"][0] == pytest.approx(o["Tfit"][0], rel=1e-5)
+        _close(s["Tb"], o["Tb"], 400.0)
+    assert checked >= 2
