@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one swarm_kernel launch of this
 # workload (ncu --set full capture summarised in profiles/swarm_kernel_dynamic_workload.md);
 # set to None whenever the kernel changes until it is captured again.
-SWARM_TRAFFIC_BYTES = 165888
+SWARM_TRAFFIC_BYTES = 157184
 # The same for gemm_tc_kernel on the MLP's grad-W1 product (1024 x 4104 x 4096),
 # profiles/gemm_tc_kernel_mlp_gradW1.md.
 GEMM_GRADW1_TRAFFIC_BYTES = 42132480
