@@ -413,6 +413,171 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
 }
 
 // ---------------------------------------------------------------------------
+// A whole run of a small swarm in one launch: one CTA per run holds X, V, Pbest,
+// the Gbest rows and the Tbest row in shared memory and steps through all
+// iterations with block barriers instead of kernel boundaries (the standard runs
+// of Sec. 4.1.1: 80 particles x 30 coordinates per trial, one trial per CTA).
+// Warp w owns groups w, w + nwarps, ...: it updates and evaluates their particles
+// and keeps their Gbest rows; the Tbest decision is taken after a barrier.  The
+// update and fitness expressions, the Philox draws and the best-key rules are
+// bf_iter_kernel's.  At the end the state is written back in the engine's layout
+// (Pbest rows in parity 0, keys naming them, Tbest in both holder slots) so that
+// sepso_bf_step, the bests kernel and the state calls continue from it.
+// ---------------------------------------------------------------------------
+template <int FN>
+__global__ void __launch_bounds__(256) bf_small_kernel(const BfParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x;
+  const int D = p.D, Dp = p.Dp, G = p.G, N = p.N, M = p.M, K = p.K;
+  float* sX = reinterpret_cast<float*>(smem);
+  float* sV = sX + (size_t)M * Dp;
+  float* sP = sV + (size_t)M * Dp;
+  float* sG = sP + (size_t)M * Dp;
+  float* sT = sG + (size_t)G * Dp;
+  float* sPf = sT + Dp;
+  unsigned long long* gkey = reinterpret_cast<unsigned long long*>(sPf + ((M + 1) & ~1));
+  unsigned long long* s_tk = gkey + G;
+  const float ext = p.hi - p.lo;
+  const uint32_t run = p.run_id + (uint32_t)r;
+
+  // Initialisation, as bf_init_kernel.
+  const int nch = Dp >> 2;
+  for (int it = threadIdx.x; it < M * nch; it += blockDim.x) {
+    const int pi = it / nch, c = it - pi * nch;
+    const int g = pi / N;
+    const float vlim = p.hyper[((size_t)r * G + g) * 6 + 5];
+    const uint4 ux = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitX, 0u, run);
+    const uint4 uv = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitV, 0u, run);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const bool in = 4 * c + e < D;
+      const float x = in ? p.lo + lane_of(ux, e) * ext : 0.0f;
+      sX[pi * Dp + 4 * c + e] = x;
+      sP[pi * Dp + 4 * c + e] = x;
+      sV[pi * Dp + 4 * c + e] = in ? (2.0f * lane_of(uv, e) - 1.0f) * (vlim * ext) : 0.0f;
+    }
+  }
+  for (int i = threadIdx.x; i < M; i += blockDim.x) sPf[i] = INFINITY;
+  for (int i = threadIdx.x; i < G * Dp + Dp; i += blockDim.x) sG[i] = 0.0f;  // sG then sT
+  for (int i = threadIdx.x; i < G; i += blockDim.x) gkey[i] = kEmpty;
+  if (threadIdx.x == 0) *s_tk = kEmpty;
+  __syncthreads();
+
+  for (int j = 1; j <= K + 1; ++j) {
+    // Update of iteration j - 1 (for j > 1); for j = K + 1 it is the last step.
+    if (j > 1) {
+      const int k = j - 1;
+      const bool have_T = *s_tk != kEmpty;
+      for (int g = warp; g < G; g += nwarps) {
+        const float* hy = p.hyper + ((size_t)r * G + g) * 6;
+        const float c1 = hy[0], c2 = hy[1], c3 = hy[2], w_init = hy[3], w_end = hy[4];
+        const float vmax = hy[5] * ext;
+        const float w = w_init - (w_init - w_end) / (float)K * (float)k;
+        const bool need_T = c3 != 0.0f;
+        const bool have_G = gkey[g] != kEmpty;
+        uint4 rl = make_uint4(0u, 0u, 0u, 0u);   // lane l draws for particle n0 + l
+        for (int n = 0; n < N; ++n) {
+          const int pi = g * N + n;
+          if ((n & 31) == 0 && n + lane < N)
+            rl = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)(pi + lane), kStreamVel, 0u, run);
+          const int src = n & 31;
+          const uint32_t rx = __shfl_sync(0xffffffffu, rl.x, src), ry = __shfl_sync(0xffffffffu, rl.y, src),
+                         rz = __shfl_sync(0xffffffffu, rl.z, src);
+          const float a1 = c1 * u01(rx), a2 = c2 * u01(ry), a3 = c3 * u01(rz);
+          float* x = sX + pi * Dp;
+          float* v = sV + pi * Dp;
+          const float* pb = sP + pi * Dp;
+          for (int i = lane; i < D; i += 32) {
+            const float xe = x[i];
+            float vv = w * v[i];
+            vv = fmaf(a1, pb[i] - xe, vv);
+            vv = fmaf(a2, (have_G ? sG[g * Dp + i] : 0.0f) - xe, vv);
+            if (need_T) vv = fmaf(a3, (have_T ? sT[i] : 0.0f) - xe, vv);
+            vv = fminf(fmaxf(vv, -vmax), vmax);
+            v[i] = vv;
+            x[i] = fminf(fmaxf(xe + vv, p.lo), p.hi);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    if (j > K) break;
+    // Fitness of iteration j, Pbest (strictly better), this iteration's group keys.
+    for (int g = warp; g < G; g += nwarps) {
+      unsigned long long best = gkey[g] == kEmpty ? kEmpty : (gkey[g] & ~(1ull << 31));  // previous holder
+      for (int n = 0; n < N; ++n) {
+        const int pi = g * N + n;
+        const float F = bf_row<FN>(sX + pi * Dp, D, lane);
+        float pf = sPf[pi];
+        __syncwarp();
+        if (F < pf) {
+          for (int i = lane; i < D; i += 32) sP[pi * Dp + i] = sX[pi * Dp + i];
+          pf = F;
+          if (lane == 0) sPf[pi] = F;
+        }
+        if (isfinite(pf)) {
+          const unsigned long long kk = make_key(pf, 1u, (uint32_t)pi, 0u);
+          if (kk < best) best = kk;
+        }
+      }
+      __syncwarp();
+      if (best != kEmpty && best != gkey[g]) {
+        const int w_idx = (int)((best >> 1) & 0x3fffffffu);
+        for (int i = lane; i < Dp; i += 32) sG[g * Dp + i] = sP[w_idx * Dp + i];
+      }
+      __syncwarp();
+      if (lane == 0) gkey[g] = best;
+    }
+    __syncthreads();
+    // Tbest of iteration j.
+    if (warp == 0) {
+      const unsigned long long told = *s_tk;
+      const unsigned long long tk = resolve_T(gkey, G, told);
+      if (tk != told) {
+        // the new holder's row is its group's Gbest row
+        int gw = 0;
+        for (int g = 0; g < G; ++g)
+          if (gkey[g] == tk) { gw = g; break; }
+        for (int i = lane; i < Dp; i += 32) sT[i] = sG[gw * Dp + i];
+      }
+      __syncwarp();
+      if (lane == 0) {
+        *s_tk = tk;
+        if (j - 1 < p.hist_len)
+          p.hist[(size_t)r * p.hist_len + (j - 1)] = tk == kEmpty ? INFINITY : float_of_ord((uint32_t)(tk >> 32));
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+
+  // Write the state back in the engine's layout.
+  const size_t RM = (size_t)p.R * M, q0 = (size_t)r * M;
+  for (int it = threadIdx.x; it < M * Dp; it += blockDim.x) {
+    const int pi = it / Dp, i = it - pi * Dp;
+    p.X[(q0 + pi) * Dp + i] = sX[it];
+    p.V[(q0 + pi) * Dp + i] = sV[it];
+    p.P[(q0 + pi) * Dp + i] = sP[it];
+  }
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    p.Pfit[q0 + i] = sPf[i];
+    p.pcur[q0 + i] = 0;
+  }
+  const int RG = p.R * G;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    const unsigned long long kk = gkey[g];
+    p.keys[(size_t)(K % 3) * RG + (size_t)r * G + g] = kk;
+    p.keys[(size_t)((K + 1) % 3) * RG + (size_t)r * G + g] = kk == kEmpty ? kEmpty : (kk & ~(1ull << 31));
+  }
+  if (threadIdx.x == 0) {
+    p.thold[r] = *s_tk;
+    p.thold[(size_t)p.R + r] = *s_tk;
+  }
+  (void)RM;
+}
+
+// ---------------------------------------------------------------------------
 // Objective 5 with a lane per particle: the iteration of bf_iter_kernel for short
 // rows (paths of D = 2T <= kLaneMaxD coordinates), where a warp per particle would
 // leave most lanes idle in the update and spread each path's few segments over the
@@ -425,6 +590,7 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
 constexpr int kLaneMaxD = 64;
 constexpr int kLaneThreads = 256;
 constexpr int kLaneMinPerSm = 256;   // particles per SM from which objective 5 uses a lane each
+constexpr long long kSmallMaxCoords = 8192;  // swarm size (G N D) up to which a run is one CTA
 
 __device__ __forceinline__ float poly_lane(const float* s, int T, const float* pts, const float4* edges, int E,
                                            float alpha, int beta) {
@@ -717,6 +883,7 @@ struct sepso_bf_ctx {
   size_t smem = 0;
   int grid_lane = 0;  // > 0: objective 5 runs on poly_lane_kernel
   size_t smem_lane = 0;
+  size_t smem_small = 0;  // > 0: whole runs go to bf_small_kernel
   int64_t k = -1;  // iterations done; -1 before the first run or state
   int64_t launches = 0;
   bool hyper_set = false;
@@ -757,6 +924,19 @@ int enqueue_iterations(sepso_bf_ctx* h, int k0, int n) {
 
 // init + iterations 1..K + the bests, on h->stream.
 int enqueue_run(sepso_bf_ctx* h) {
+  if (h->smem_small > 0) {
+    const int R = h->c.runs;
+    const size_t sm = h->smem_small;
+    switch (h->c.fn) {
+      case 1: bf_small_kernel<1><<<R, 256, sm, h->stream>>>(h->p); break;
+      case 2: bf_small_kernel<2><<<R, 256, sm, h->stream>>>(h->p); break;
+      case 3: bf_small_kernel<3><<<R, 256, sm, h->stream>>>(h->p); break;
+      default: bf_small_kernel<4><<<R, 256, sm, h->stream>>>(h->p); break;
+    }
+    BFCUDA(cudaGetLastError());
+    BFCUDA(launch_finish(h, h->c.max_iters));
+    return SEPSO_OK;
+  }
   bf_init_kernel<<<h->init_grid, 256, 0, h->stream>>>(h->p);
   BFCUDA(cudaGetLastError());
   return enqueue_iterations(h, 0, h->c.max_iters);
@@ -817,6 +997,24 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   h->smem = smem;
   const long long RM = (long long)c->runs * c->G * c->N;
   h->grid = (int)std::min<long long>((RM + nwarps - 1) / nwarps, (long long)bps * sms);
+  // Small swarms (a trial of the standard runs) run whole in one CTA per run.
+  if (c->fn <= 4 && (long long)c->G * c->N * c->D <= kSmallMaxCoords) {
+    const size_t M = (size_t)c->G * c->N;
+    const size_t ss = 4 * (3 * M * Dp + (size_t)c->G * Dp + Dp + ((M + 1) & ~size_t(1))) + 8 * ((size_t)c->G + 1);
+    if (ss <= (size_t)kSmemTotal) {
+      switch (c->fn) {
+        case 1: e = cudaFuncSetAttribute(bf_small_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss); break;
+        case 2: e = cudaFuncSetAttribute(bf_small_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss); break;
+        case 3: e = cudaFuncSetAttribute(bf_small_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss); break;
+        default: e = cudaFuncSetAttribute(bf_small_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss); break;
+      }
+      if (e != cudaSuccess) {
+        delete h;
+        return bffail(SEPSO_ECUDA, "small-swarm kernel attributes: %s", cudaGetErrorString(e));
+      }
+      h->smem_small = ss;
+    }
+  }
   // A lane per particle pays once there are enough particles to give every SM's
   // lanes work (below that, one path's tests spread over a warp finish sooner).
   if (c->fn == 5 && c->D <= kLaneMaxD && RM >= (long long)kLaneMinPerSm * sms) {
@@ -1029,6 +1227,7 @@ int64_t sepso_bf_launch_count(sepso_bf_handle h) { return h ? h->launches : -1; 
 
 const char* sepso_bf_kernel_name(sepso_bf_handle h) {
   if (!h) return "";
+  if (h->smem_small > 0) return "bf_small_kernel (runs), bf_iter_kernel (steps)";
   if (h->grid_lane > 0) return "poly_lane_kernel";
   static const char* names[] = {"", "bf_iter_kernel<1>", "bf_iter_kernel<2>", "bf_iter_kernel<3>",
                                 "bf_iter_kernel<4>", "bf_iter_kernel<5>"};
