@@ -684,9 +684,12 @@ int sepso_bf_set_state(sepso_bf_handle h, int32_t run, const float* X, const flo
  * F[n], on stream.  Errors: EINVAL, ECUDA. */
 int sepso_bf_evaluate(int32_t fn, int32_t D, int32_t n, const float* X, int32_t ldx, float* F, void* stream);
 int64_t sepso_bf_launch_count(sepso_bf_handle h);
-/* Name of the iteration kernel this handle launches: bf_iter_kernel<fn> (a warp per
- * particle), or poly_lane_kernel (objective 5, D <= 64, at least 256 particles per
- * SM: a lane per particle).  Static string. */
+/* Name of the kernels this handle launches: bf_iter_kernel<fn> (a launch per
+ * iteration, a warp per particle); poly_lane_kernel (objective 5, D <= 64, at
+ * least 256 particles per SM: a lane per particle); or, for benchmark-function
+ * swarms of at most 8192 coordinates (G x N x D), bf_small_kernel for whole runs
+ * (one CTA per run, the swarm in shared memory) with bf_iter_kernel for steps.
+ * Static string. */
 const char* sepso_bf_kernel_name(sepso_bf_handle h);
 const char* sepso_bf_last_error(void);
 
