@@ -414,54 +414,83 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
 
 // ---------------------------------------------------------------------------
 // A whole run of a small swarm in one launch: one CTA per run holds X, V, Pbest,
-// the Gbest rows and the Tbest row in shared memory and steps through all
+// the Gbest rows and the Tbest row in shared memory (rows at an odd stride, so
+// that the threads' rows fall in different banks) and steps through all
 // iterations with block barriers instead of kernel boundaries (the standard runs
 // of Sec. 4.1.1: 80 particles x 30 coordinates per trial, one trial per CTA).
-// Warp w owns groups w, w + nwarps, ...: it updates and evaluates their particles
-// and keeps their Gbest rows; the Tbest decision is taken after a barrier.  The
-// update and fitness expressions, the Philox draws and the best-key rules are
-// bf_iter_kernel's.  At the end the state is written back in the engine's layout
-// (Pbest rows in parity 0, keys naming them, Tbest in both holder slots) so that
-// sepso_bf_step, the bests kernel and the state calls continue from it.
+// Thread t owns particles t, t + blockDim, ...: it draws their random factors,
+// updates their rows and sums their fitness coordinate by coordinate.  Group keys
+// are merged with shared-memory atomics (previous holder first, at priority 0),
+// then Tbest is decided; the update expressions, the Philox draws and the best
+// rules are bf_iter_kernel's (the fitness is summed in coordinate order here, in
+// lane-strided order there).  At the end the state is written back in the engine's
+// layout (Pbest rows in parity 0, keys naming them, Tbest in both holder slots) so
+// that sepso_bf_step, the bests kernel and the state calls continue from it.
 // ---------------------------------------------------------------------------
+template <int FN>
+__device__ __forceinline__ float bf_row_serial(const float* x, int D) {
+  float acc = 0.0f, prod = 1.0f;
+  if constexpr (FN == 2) {
+    for (int i = 0; i + 1 < D; ++i) {
+      const float a = fmaf(-x[i], x[i], x[i + 1]), b = x[i] - 1.0f;
+      acc += fmaf(100.0f * a, a, b * b);
+    }
+    return acc;
+  } else {
+  for (int i = 0; i < D; ++i) {
+    const float xi = x[i];
+    if (FN == 1) {
+      acc = fmaf(xi, xi, acc);
+    } else if (FN == 3) {
+      acc += fmaf(xi, xi, -10.0f * cospif(2.0f * xi));
+    } else {
+      acc = fmaf(xi, xi, acc);
+      prod *= cosf(__fdiv_rn(xi, sqrtf((float)(i + 1))));
+    }
+  }
+  if (FN == 1) return acc;
+  if (FN == 3) return fmaf(10.0f, (float)D, acc);
+  return 1.0f + acc / 4000.0f - prod;
+  }
+}
+
 template <int FN>
 __global__ void __launch_bounds__(256) bf_small_kernel(const BfParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = blockIdx.x;
-  const int D = p.D, Dp = p.Dp, G = p.G, N = p.N, M = p.M, K = p.K;
+  const int r = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int D = p.D, G = p.G, N = p.N, M = p.M, K = p.K;
+  const int S = D + 1;  // shared-memory row stride
   float* sX = reinterpret_cast<float*>(smem);
-  float* sV = sX + (size_t)M * Dp;
-  float* sP = sV + (size_t)M * Dp;
-  float* sG = sP + (size_t)M * Dp;
-  float* sT = sG + (size_t)G * Dp;
-  float* sPf = sT + Dp;
-  unsigned long long* gkey = reinterpret_cast<unsigned long long*>(sPf + ((M + 1) & ~1));
-  unsigned long long* s_tk = gkey + G;
+  float* sV = sX + (size_t)M * S;
+  float* sP = sV + (size_t)M * S;
+  float* sG = sP + (size_t)M * S;
+  float* sT = sG + (size_t)G * S;
+  float* sPf = sT + S;
+  unsigned long long* gkey = reinterpret_cast<unsigned long long*>(
+      smem + ((size_t)(3 * M * S + G * S + S + M) * 4 + 7) / 8 * 8);
+  unsigned long long* nkey = gkey + G;
+  unsigned long long* s_tk = nkey + G;
   const float ext = p.hi - p.lo;
   const uint32_t run = p.run_id + (uint32_t)r;
 
   // Initialisation, as bf_init_kernel.
-  const int nch = Dp >> 2;
-  for (int it = threadIdx.x; it < M * nch; it += blockDim.x) {
-    const int pi = it / nch, c = it - pi * nch;
-    const int g = pi / N;
-    const float vlim = p.hyper[((size_t)r * G + g) * 6 + 5];
-    const uint4 ux = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitX, 0u, run);
-    const uint4 uv = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitV, 0u, run);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const bool in = 4 * c + e < D;
-      const float x = in ? p.lo + lane_of(ux, e) * ext : 0.0f;
-      sX[pi * Dp + 4 * c + e] = x;
-      sP[pi * Dp + 4 * c + e] = x;
-      sV[pi * Dp + 4 * c + e] = in ? (2.0f * lane_of(uv, e) - 1.0f) * (vlim * ext) : 0.0f;
+  for (int pi = tid; pi < M; pi += nt) {
+    const float vlim = p.hyper[((size_t)r * G + pi / N) * 6 + 5];
+    for (int c = 0; 4 * c < D; ++c) {
+      const uint4 ux = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitX, 0u, run);
+      const uint4 uv = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitV, 0u, run);
+      for (int e = 0; e < 4 && 4 * c + e < D; ++e) {
+        const float x = p.lo + lane_of(ux, e) * ext;
+        sX[pi * S + 4 * c + e] = x;
+        sP[pi * S + 4 * c + e] = x;
+        sV[pi * S + 4 * c + e] = (2.0f * lane_of(uv, e) - 1.0f) * (vlim * ext);
+      }
     }
+    sPf[pi] = INFINITY;
   }
-  for (int i = threadIdx.x; i < M; i += blockDim.x) sPf[i] = INFINITY;
-  for (int i = threadIdx.x; i < G * Dp + Dp; i += blockDim.x) sG[i] = 0.0f;  // sG then sT
-  for (int i = threadIdx.x; i < G; i += blockDim.x) gkey[i] = kEmpty;
-  if (threadIdx.x == 0) *s_tk = kEmpty;
+  for (int i = tid; i < G * S + S; i += nt) sG[i] = 0.0f;  // sG then sT
+  for (int i = tid; i < G; i += nt) gkey[i] = kEmpty;
+  if (tid == 0) *s_tk = kEmpty;
   __syncthreads();
 
   for (int j = 1; j <= K + 1; ++j) {
@@ -469,112 +498,102 @@ __global__ void __launch_bounds__(256) bf_small_kernel(const BfParams p) {
     if (j > 1) {
       const int k = j - 1;
       const bool have_T = *s_tk != kEmpty;
-      for (int g = warp; g < G; g += nwarps) {
+      for (int pi = tid; pi < M; pi += nt) {
+        const int g = pi / N;
         const float* hy = p.hyper + ((size_t)r * G + g) * 6;
         const float c1 = hy[0], c2 = hy[1], c3 = hy[2], w_init = hy[3], w_end = hy[4];
         const float vmax = hy[5] * ext;
         const float w = w_init - (w_init - w_end) / (float)K * (float)k;
-        const bool need_T = c3 != 0.0f;
-        const bool have_G = gkey[g] != kEmpty;
-        uint4 rl = make_uint4(0u, 0u, 0u, 0u);   // lane l draws for particle n0 + l
-        for (int n = 0; n < N; ++n) {
-          const int pi = g * N + n;
-          if ((n & 31) == 0 && n + lane < N)
-            rl = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)(pi + lane), kStreamVel, 0u, run);
-          const int src = n & 31;
-          const uint32_t rx = __shfl_sync(0xffffffffu, rl.x, src), ry = __shfl_sync(0xffffffffu, rl.y, src),
-                         rz = __shfl_sync(0xffffffffu, rl.z, src);
-          const float a1 = c1 * u01(rx), a2 = c2 * u01(ry), a3 = c3 * u01(rz);
-          float* x = sX + pi * Dp;
-          float* v = sV + pi * Dp;
-          const float* pb = sP + pi * Dp;
-          for (int i = lane; i < D; i += 32) {
-            const float xe = x[i];
-            float vv = w * v[i];
-            vv = fmaf(a1, pb[i] - xe, vv);
-            vv = fmaf(a2, (have_G ? sG[g * Dp + i] : 0.0f) - xe, vv);
-            if (need_T) vv = fmaf(a3, (have_T ? sT[i] : 0.0f) - xe, vv);
-            vv = fminf(fmaxf(vv, -vmax), vmax);
-            v[i] = vv;
-            x[i] = fminf(fmaxf(xe + vv, p.lo), p.hi);
-          }
+        const bool need_T = c3 != 0.0f, have_G = gkey[g] != kEmpty;
+        const uint4 rr = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)pi, kStreamVel, 0u, run);
+        const float a1 = c1 * u01(rr.x), a2 = c2 * u01(rr.y), a3 = c3 * u01(rr.z);
+        float* x = sX + pi * S;
+        float* v = sV + pi * S;
+        const float* pb = sP + pi * S;
+        const float* gb = sG + g * S;
+        for (int i = 0; i < D; ++i) {
+          const float xe = x[i];
+          float vv = w * v[i];
+          vv = fmaf(a1, pb[i] - xe, vv);
+          vv = fmaf(a2, (have_G ? gb[i] : 0.0f) - xe, vv);
+          if (need_T) vv = fmaf(a3, (have_T ? sT[i] : 0.0f) - xe, vv);
+          vv = fminf(fmaxf(vv, -vmax), vmax);
+          v[i] = vv;
+          x[i] = fminf(fmaxf(xe + vv, p.lo), p.hi);
         }
       }
-      __syncwarp();
     }
     if (j > K) break;
-    // Fitness of iteration j, Pbest (strictly better), this iteration's group keys.
-    for (int g = warp; g < G; g += nwarps) {
-      unsigned long long best = gkey[g] == kEmpty ? kEmpty : (gkey[g] & ~(1ull << 31));  // previous holder
-      for (int n = 0; n < N; ++n) {
-        const int pi = g * N + n;
-        const float F = bf_row<FN>(sX + pi * Dp, D, lane);
-        float pf = sPf[pi];
-        __syncwarp();
-        if (F < pf) {
-          for (int i = lane; i < D; i += 32) sP[pi * Dp + i] = sX[pi * Dp + i];
-          pf = F;
-          if (lane == 0) sPf[pi] = F;
-        }
-        if (isfinite(pf)) {
-          const unsigned long long kk = make_key(pf, 1u, (uint32_t)pi, 0u);
-          if (kk < best) best = kk;
-        }
+    // Iteration j's group keys start from the previous holders (priority 0).
+    for (int g = tid; g < G; g += nt) nkey[g] = gkey[g] == kEmpty ? kEmpty : (gkey[g] & ~(1ull << 31));
+    __syncthreads();
+    // Fitness of iteration j, Pbest (strictly better), candidates.
+    for (int pi = tid; pi < M; pi += nt) {
+      const float F = bf_row_serial<FN>(sX + pi * S, D);
+      float pf = sPf[pi];
+      if (F < pf) {
+        for (int i = 0; i < D; ++i) sP[pi * S + i] = sX[pi * S + i];
+        pf = F;
+        sPf[pi] = F;
       }
-      __syncwarp();
-      if (best != kEmpty && best != gkey[g]) {
-        const int w_idx = (int)((best >> 1) & 0x3fffffffu);
-        for (int i = lane; i < Dp; i += 32) sG[g * Dp + i] = sP[w_idx * Dp + i];
-      }
-      __syncwarp();
-      if (lane == 0) gkey[g] = best;
+      if (isfinite(pf)) atomicMin(&nkey[pi / N], make_key(pf, 1u, (uint32_t)pi, 0u));
     }
     __syncthreads();
+    // New Gbest rows where the holder changed.
+    for (int it = tid; it < G * D; it += nt) {
+      const int g = it / D, i = it - g * D;
+      const unsigned long long kk = nkey[g];
+      if (kk != kEmpty && kk != gkey[g]) sG[g * S + i] = sP[(int)((kk >> 1) & 0x3fffffffu) * S + i];
+    }
+    __syncthreads();
+    for (int g = tid; g < G; g += nt) gkey[g] = nkey[g];
+    __syncthreads();
     // Tbest of iteration j.
-    if (warp == 0) {
-      const unsigned long long told = *s_tk;
-      const unsigned long long tk = resolve_T(gkey, G, told);
-      if (tk != told) {
-        // the new holder's row is its group's Gbest row
-        int gw = 0;
-        for (int g = 0; g < G; ++g)
-          if (gkey[g] == tk) { gw = g; break; }
-        for (int i = lane; i < Dp; i += 32) sT[i] = sG[gw * Dp + i];
-      }
-      __syncwarp();
-      if (lane == 0) {
-        *s_tk = tk;
-        if (j - 1 < p.hist_len)
-          p.hist[(size_t)r * p.hist_len + (j - 1)] = tk == kEmpty ? INFINITY : float_of_ord((uint32_t)(tk >> 32));
-      }
+    const unsigned long long told = *s_tk;
+    const unsigned long long tk = resolve_T(gkey, G, told);
+    if (tk != told) {
+      int gw = 0;
+      for (int g = 0; g < G; ++g)
+        if (gkey[g] == tk) {
+          gw = g;
+          break;
+        }
+      for (int i = tid; i < D; i += nt) sT[i] = sG[gw * S + i];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      *s_tk = tk;
+      if (j - 1 < p.hist_len)
+        p.hist[(size_t)r * p.hist_len + (j - 1)] = tk == kEmpty ? INFINITY : float_of_ord((uint32_t)(tk >> 32));
     }
     __syncthreads();
   }
   __syncthreads();
 
   // Write the state back in the engine's layout.
-  const size_t RM = (size_t)p.R * M, q0 = (size_t)r * M;
-  for (int it = threadIdx.x; it < M * Dp; it += blockDim.x) {
+  const int Dp = p.Dp;
+  const size_t q0 = (size_t)r * M;
+  for (int it = tid; it < M * Dp; it += nt) {
     const int pi = it / Dp, i = it - pi * Dp;
-    p.X[(q0 + pi) * Dp + i] = sX[it];
-    p.V[(q0 + pi) * Dp + i] = sV[it];
-    p.P[(q0 + pi) * Dp + i] = sP[it];
+    const bool in = i < D;
+    p.X[(q0 + pi) * Dp + i] = in ? sX[pi * S + i] : 0.0f;
+    p.V[(q0 + pi) * Dp + i] = in ? sV[pi * S + i] : 0.0f;
+    p.P[(q0 + pi) * Dp + i] = in ? sP[pi * S + i] : 0.0f;
   }
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+  for (int i = tid; i < M; i += nt) {
     p.Pfit[q0 + i] = sPf[i];
     p.pcur[q0 + i] = 0;
   }
   const int RG = p.R * G;
-  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+  for (int g = tid; g < G; g += nt) {
     const unsigned long long kk = gkey[g];
     p.keys[(size_t)(K % 3) * RG + (size_t)r * G + g] = kk;
     p.keys[(size_t)((K + 1) % 3) * RG + (size_t)r * G + g] = kk == kEmpty ? kEmpty : (kk & ~(1ull << 31));
   }
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     p.thold[r] = *s_tk;
     p.thold[(size_t)p.R + r] = *s_tk;
   }
-  (void)RM;
 }
 
 // ---------------------------------------------------------------------------
@@ -1000,7 +1019,8 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   // Small swarms (a trial of the standard runs) run whole in one CTA per run.
   if (c->fn <= 4 && (long long)c->G * c->N * c->D <= kSmallMaxCoords) {
     const size_t M = (size_t)c->G * c->N;
-    const size_t ss = 4 * (3 * M * Dp + (size_t)c->G * Dp + Dp + ((M + 1) & ~size_t(1))) + 8 * ((size_t)c->G + 1);
+    const size_t S = (size_t)c->D + 1;
+    const size_t ss = ((3 * M * S + (size_t)c->G * S + S + M) * 4 + 7) / 8 * 8 + 8 * (2 * (size_t)c->G + 1);
     if (ss <= (size_t)kSmemTotal) {
       switch (c->fn) {
         case 1: e = cudaFuncSetAttribute(bf_small_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss); break;
