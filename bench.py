@@ -14,6 +14,12 @@ Prints one JSON line.  ``value`` is plans/s with the scene resident on the devic
 ``e2e`` is the same metric through the C ABI with host buffers (pinned scene in,
 waypoints out, every cycle).  ``--impl reference`` times the FP64 CPU oracle on
 the host cores instead (bounded sample).
+
+Further sections add objects to the same line (``--sections`` selects them): the
+batched scenes, the learned prior, the serving loop, the ablation of the paper's
+path-planning comparison (``paper_ablation``), the benchmark functions at the
+standard and large scale (``bf``), planning among polygon obstacles (``poly``) and
+the tensor-core GEMM alone (``gemm``, not in the default list).
 """
 from __future__ import annotations
 
