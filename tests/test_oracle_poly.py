@@ -105,3 +105,26 @@ def test_workload_shape_and_run_invariants():
     X = sw.s["X"].reshape(-1, cfg.D)
     assert X.min() >= 0.0 and X.max() <= 400.0
     assert hist[-1] < hist[0]
+
+
+def test_polygon_workload_shapes():
+    # 12 convex boxes and 4 non-convex U outlines; every polygon closed, inside the map
+    cfg, start, target, polys, edges, hy = polygon_workload(5)
+    assert len(polys) == 16 and edges.shape == (80, 4)
+
+    def turns(poly):
+        v = np.asarray(poly, np.float64)
+        d = np.roll(v, -1, axis=0) - v
+        return np.sign(d[:, 0] * np.roll(d, -1, axis=0)[:, 1] - d[:, 1] * np.roll(d, -1, axis=0)[:, 0])
+
+    for poly in polys[:12]:
+        t = turns(poly)
+        assert len(poly) == 4 and (np.all(t > 0) or np.all(t < 0))          # convex
+    for poly in polys[12:]:
+        t = turns(poly)
+        assert len(poly) == 8 and np.any(t > 0) and np.any(t < 0)           # non-convex
+    # consecutive edges join, and the last edge returns to the first vertex
+    e = edges[:48].reshape(12, 4, 4)                     # the boxes' edges
+    np.testing.assert_array_equal(e[:, 1:, :2], e[:, :-1, 2:])
+    np.testing.assert_array_equal(e[:, 0, :2], e[:, -1, 2:])
+    assert edges.min() >= 0.0 and edges.max() <= 400.0
