@@ -536,9 +536,7 @@ const char* sepso_prior_last_error(void);
  * and/or Cb (BF16, ldcb), device, either may be NULL.  tile_n: 64, 128 or 256
  * columns per 128-row tile on persistent CTAs (each loops over tiles, the
  * epilogue of one overlapping the main loop of the next), -64 / -128 / -256 the
- * same widths with one tile per CTA, -1064 / -1128 / -1256 one tile per CTA in
- * clusters of two CTAs (vertically adjacent tiles) that share the B box by TMA
- * multicast, 0 = chosen from the grid it gives.  Async on
+ * same widths with one tile per CTA, 0 = chosen from the grid it gives.  Async on
  * stream; a device-side timeout is reported by the next sepso_gemm_bf16_sync.
  * Errors: EINVAL, ECUDA. */
 int sepso_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, int32_t lda, int32_t ldb,

@@ -948,6 +948,8 @@ extern "C" int sepso_plan_static(const sepso_config* cfg, const float* hyper, co
     return fail(SEPSO_EINVAL, "O=%d outside [0, max_obstacles=%d]", O, cfg->max_obstacles);
   for (int i = 0; i < cfg->G * 6; ++i)
     if (!finite(hyper[i])) return fail(SEPSO_EINVAL, "hyper[%d] is not finite", i);
+  for (int g = 0; g < cfg->G; ++g)  // the same rule as sepso_set_hyper
+    if (hyper[g * 6 + 5] < 0) return fail(SEPSO_EINVAL, "V_limit of group %d is negative", g);
   if (!finite(start[0]) || !finite(start[1]) || !finite(target[0]) || !finite(target[1]))
     return fail(SEPSO_EINVAL, "start/target not finite");
   for (int o = 0; o < O; ++o) {
@@ -1002,6 +1004,8 @@ extern "C" int sepso_plan_static(const sepso_config* cfg, const float* hyper, co
     }
     CUDA_TRY(cudaMemcpyAsync(h.ws + L.circ + (size_t)o0 * 16, chunk, (size_t)n * 16, cudaMemcpyHostToDevice,
                              h.stream));
+    // the copy reads the stack buffer: let it finish before the buffer is refilled
+    if (o0 + 128 < O) CUDA_TRY(cudaStreamSynchronize(h.stream));
   }
   const float pts[8] = {start[0], start[1], target[0], target[1], 0.f, 0.f, 0.f, 0.f};
   CUDA_TRY(cudaMemcpyAsync(h.ws + L.pts, pts, sizeof pts, cudaMemcpyHostToDevice, h.stream));

@@ -11,8 +11,7 @@
 //                      (scale, bias, ReLU, the backward pass's ReLU mask, FP32
 //                      and/or BF16 output, a transposed BF16 copy, column
 //                      sums; K split into slices summed in order).  Tile N
-//                      (64 / 128 / 256) per launch; a persistent form and a
-//                      CTA-pair form (B box shared by TMA multicast).
+//                      (64 / 128 / 256) per launch, and a persistent form.
 //   raster_kernel      occupancy raster of the circles (cell centre inside a disk).
 //   small kernels      row gather with a transposed copy, column sums (bias
 //                      gradients), MSE loss gradient, split-K sums, Adam with the
@@ -91,34 +90,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
                : "memory");
-}
-
-// Cluster helpers for the CTA-pair form: the CTA's rank in its cluster, a
-// cluster-wide barrier (release / acquire), a TMA load multicast to the CTAs of
-// `mask` (same shared-memory offset and mbarrier offset in each), and a commit
-// arriving on the mbarrier at the same offset in each CTA of `mask`.
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tma_load_2d_mc(void* smem_dst, const CUtensorMap* map, int x, int y, uint64_t* bar,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(smem_dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar)), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_addr(bar)),
-      "h"(mask)
-      : "memory");
 }
 
 // 32 consecutive FP32 columns of this thread's TMEM lane.
@@ -471,103 +442,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, BN);
-}
-
-// ---------------------------------------------------------------------------
-// CTA-pair form: a cluster of two CTAs computes two vertically adjacent 128 x BN
-// tiles (same columns n0, rows m0 and m0 + 128) with one tcgen05.mma stream each.
-// Each CTA loads its own A box and one half (BN / 2 rows) of the shared B box,
-// which TMA multicasts into the same stage of both CTAs: per K-block an SM pulls
-// 128 + BN / 2 operand rows from L2 instead of 128 + BN.  A stage is free when
-// both CTAs' MMAs have released it (empty barriers count two arrivals, each MMA
-// lane commits to both CTAs); as in the one-tile form a release is committed only
-// for a load that waits for it, and the pair meets at cluster barriers after the
-// barrier initialisation and before either CTA exits, so no multicast write or
-// remote arrival can reach a CTA that has left.
-// ---------------------------------------------------------------------------
-template <int BN>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGemmThreads, 1)
-    gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBh,
-                        const GemmArgs g) {
-  using TL = GemmTile<BN>;
-  constexpr int S = TL::kStages;
-  constexpr int kHalfBytes = (BN / 2) * kBK * 2;
-  constexpr uint16_t kBoth = 0x3;
-  extern __shared__ uint8_t gsm_raw[];
-  __shared__ uint64_t full[S], empty[S], done;
-  __shared__ uint32_t tmem_base;
-  __shared__ int s_fail;
-  uint8_t* gsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~uintptr_t(1023));
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t rank = cluster_ctarank();
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-  const int nkb = (g.K + kBK - 1) / kBK;
-  constexpr uint32_t kIdesc = mma_idesc_bf16(kBM, BN);
-
-  if (warp == 0) tmem_alloc(&tmem_base, BN);
-  if (tid == 32) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 2);  // one release from each CTA of the pair
-    }
-    mbar_init(&done, 1);
-    s_fail = 0;
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  cluster_sync_all();  // both CTAs' barriers exist before any multicast or remote arrival
-  const uint32_t tmem = tmem_base;
-
-  if (warp == 0 && lane == 0) {
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      if (kb >= S && !mbar_wait_bounded(&empty[s], (uint32_t)((kb / S - 1) & 1), kWaitLimitNs)) {
-        atomicExch(&s_fail, 1);
-        break;
-      }
-      uint8_t* sa = gsm + s * TL::kStage;
-      mbar_expect_tx(&full[s], (uint32_t)TL::kStage);  // own A box + both halves of B
-      tma_load_2d(sa, &tmA, kb * kBK, m0, &full[s]);
-      tma_load_2d_mc(sa + TL::kABytes + rank * kHalfBytes, &tmBh, kb * kBK, n0 + (int)rank * (BN / 2), &full[s],
-                     kBoth);
-      issued = kb + 1;
-    }
-    if (issued < nkb)
-      for (int kb = max(0, issued - S); kb < issued; ++kb)
-        mbar_wait_bounded(&full[kb % S], (uint32_t)((kb / S) & 1), kWaitLimitNs);
-  } else if (warp == 1 && lane == 0) {
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % S;
-      if (!mbar_wait_bounded(&full[s], (uint32_t)((kb / S) & 1), kWaitLimitNs) || *(volatile int*)&s_fail) {
-        atomicExch(&s_fail, 1);
-        break;
-      }
-      tc_fence_after();
-      const uint8_t* sa = gsm + s * TL::kStage;
-      const uint8_t* sb = sa + TL::kABytes;
-#pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk)
-        mma_bf16(tmem, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32), kIdesc,
-                 (kb > 0 || kk > 0) ? 1u : 0u);
-      if (kb + S < nkb) mma_commit_mc(&empty[s], kBoth);
-    }
-    mma_commit(&done);
-  }
-  __syncwarp();
-  if (!mbar_wait_bounded(&done, 0u, kWaitLimitNs)) atomicExch(&s_fail, 1);
-  const bool fail = __syncthreads_or(*(volatile int*)&s_fail) != 0;
-  if (fail) {
-    if (tid == 0 && g.status) atomicExch(g.status, SEPSO_ETIMEOUT);
-  } else if (nkb > 0) {
-    tc_fence_after();
-    tile_epilogue_all<BN>(g, gsm, tmem, m0, n0);
-  }
-  tc_fence_before();
-  __syncthreads();
-  cluster_sync_all();  // the peer has finished every load and release that reaches this CTA
   if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
@@ -1247,28 +1121,6 @@ int gemm_launch_bn(const CUtensorMap& ta, const GemmArgs& g, cudaStream_t s, int
   return SEPSO_OK;
 }
 
-// CTA pairs (cluster 2 x 1): rows of 128-row tiles padded to an even count (a
-// tile past M loads zeros and stores nothing, its half of B still feeds the peer).
-template <int BN>
-int gemm_launch_pair(const CUtensorMap& ta, const GemmArgs& g, cudaStream_t s) {
-  CUtensorMap tb;
-  PTRY(make_map(&tb, g.B, g.N, g.K, g.ldb, BN / 2));
-  static thread_local int configured_device = -1;
-  int dev = 0;
-  PCUDA(cudaGetDevice(&dev));
-  if (configured_device != dev) {
-    PCUDA(cudaFuncSetAttribute(sepso::gemm_tc_pair_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               sepso::kGemmSmem));
-    configured_device = dev;
-  }
-  const int mt = (g.M + sepso::kBM - 1) / sepso::kBM;
-  const dim3 grid((unsigned)((mt + 1) / 2 * 2), (g.N + BN - 1) / BN);
-  if (grid.y > 65535u) return pfail(SEPSO_EINVAL, "gemm: N too large");
-  sepso::gemm_tc_pair_kernel<BN><<<grid, sepso::kGemmThreads, sepso::kGemmSmem, s>>>(ta, tb, g);
-  PCUDA(cudaGetLastError());
-  return SEPSO_OK;
-}
-
 template <int BN>
 int gemm_launch_persistent(const CUtensorMap& ta, const GemmArgs& g, cudaStream_t s) {
   CUtensorMap tb;
@@ -1317,10 +1169,8 @@ int gemm_check(const GemmArgs& g, int tile_n) {
   if ((g.Cf && g.ldcf < g.N) || (g.Cb && g.ldcb < g.N) || (g.mask && g.ldm < g.N))
     return pfail(SEPSO_EINVAL, "gemm: output or mask row stride below N");
   if (tile_n != 0 && tile_n != 64 && tile_n != 128 && tile_n != 256 && tile_n != -64 && tile_n != -128 &&
-      tile_n != -256 && tile_n != -1064 && tile_n != -1128 && tile_n != -1256)
-    return pfail(SEPSO_EINVAL,
-                 "gemm: tile N %d (64, 128 or 256; negative for one tile per CTA; -1000 - N for CTA pairs)",
-                 tile_n);
+      tile_n != -256)
+    return pfail(SEPSO_EINVAL, "gemm: tile N %d (64, 128 or 256; negative for one tile per CTA)", tile_n);
   return SEPSO_OK;
 }
 
@@ -1336,9 +1186,6 @@ int gemm_launch(const GemmArgs& g, cudaStream_t s, int tile_n = 0) {
     case -64: return gemm_launch_bn<64>(ta, g, s);
     case -128: return gemm_launch_bn<128>(ta, g, s);
     case -256: return gemm_launch_bn<256>(ta, g, s);
-    case -1064: return gemm_launch_pair<64>(ta, g, s);
-    case -1128: return gemm_launch_pair<128>(ta, g, s);
-    case -1256: return gemm_launch_pair<256>(ta, g, s);
     default: return pfail(SEPSO_EINVAL, "gemm: tile N %d", tile_n);
   }
 }
@@ -1408,7 +1255,7 @@ int gemm_run(GemmArgs g, const GemmExtra& e, cudaStream_t s, int tile_n, int* la
     r.kcb = kcb;
     CUtensorMap ta;
     PTRY(make_map(&ta, g.A, g.M, g.K, g.lda, sepso::kBM));
-    const int bn = tile_n ? std::abs(tile_n) % 1000 : 128;
+    const int bn = tile_n ? std::abs(tile_n) : 128;
     if (bn == 64) PTRY(gemm_launch_bn<64>(ta, r, s, slices));
     else if (bn == 128) PTRY(gemm_launch_bn<128>(ta, r, s, slices));
     else PTRY(gemm_launch_bn<256>(ta, r, s, slices));

@@ -47,13 +47,12 @@ def test_gemm_matches_fp32_reference(native, M, N, K):
     assert torch.max(torch.abs(got - ref)).item() <= tol
 
 
-@pytest.mark.parametrize("tile_n", [64, 128, 256, -64, -128, -256, -1064, -1128, -1256])
+@pytest.mark.parametrize("tile_n", [64, 128, 256, -64, -128, -256])
 def test_gemm_tile_widths_agree(native, tile_n):
-    # every tile width of the three kernels (positive: persistent with two
-    # accumulators; -64 .. -256: one tile per CTA; -1000 - N: CTA pairs sharing the
-    # B box by multicast) gives the same products (ragged M, N and K; K spans several
-    # pipeline stages and wraps the stage ring; several tiles per CTA; 19 row tiles,
-    # so the last pair has a tile past M)
+    # every tile width of the two kernels (positive: persistent with two
+    # accumulators; -64 .. -256: one tile per CTA) gives the same products (ragged
+    # M, N and K; K spans several pipeline stages and wraps the stage ring; several
+    # tiles per CTA; 19 row tiles)
     g = torch.Generator().manual_seed(tile_n)
     M, N, K = 2333, 1300, 1096
     A = torch.randn(M, K, generator=g).to(torch.bfloat16)
@@ -79,7 +78,7 @@ def test_gemm_epilogue_bias_relu_mask_bf16(native):
     assert torch.equal(Cb.cpu(), Cf.cpu().to(torch.bfloat16))
 
 
-@pytest.mark.parametrize("tile_n", [0, 64, 128, 256, -64, -128, -256, -1128, -1256])
+@pytest.mark.parametrize("tile_n", [0, 64, 128, 256, -64, -128, -256])
 @pytest.mark.parametrize("M,N,K", [(300, 260, 136), (4096, 512, 40), (77, 1000, 512)])
 def test_gemm_transposed_output_and_column_sums(native, tile_n, M, N, K):
     # the backward pass's masked products: the BF16 output transposed and the

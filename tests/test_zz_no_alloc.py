@@ -13,6 +13,7 @@ import ctypes
 
 import numpy as np
 import pytest
+import torch
 
 from paper_2308_10169_gb300 import Planner, static_workload
 from paper_2308_10169_gb300._native import Config, Result, fptr, make_config
@@ -21,22 +22,26 @@ from paper_2308_10169_gb300.inputs import dynamic_workload
 pytestmark = pytest.mark.gpu
 
 
-def _plan_static(lib, cfg, scene, hyper):
+def _plan_static(lib, cfg, scene, hyper, stream=None):
     c = make_config(cfg)
     h = np.ascontiguousarray(hyper, dtype=np.float32)
-    circ = np.ascontiguousarray(scene.circles, dtype=np.float32)
+    circ = np.ascontiguousarray(scene.circles, dtype=np.float32).reshape(-1, 3)
     wp = np.zeros(cfg.D, np.float32)
     res = Result()
     rc = lib.sepso_plan_static(ctypes.byref(c), fptr(h), fptr(scene.start), fptr(scene.target),
                                fptr(circ) if circ.size else None, circ.shape[0], fptr(wp),
-                               ctypes.byref(res), None)
+                               ctypes.byref(res), stream)
     return rc, wp, res
 
 
-@pytest.mark.parametrize("which", ["static", "dynamic"])
+@pytest.mark.parametrize("which", ["static", "dynamic", "no_obstacles", "side_stream"])
 def test_static_scratch_plan_matches_handle_plan_twice(native, which):
-    if which == "static":
+    stream = None
+    if which in ("static", "side_stream"):
         cfg, scene, hyper = static_workload(7)
+    elif which == "no_obstacles":
+        cfg, scene, hyper = static_workload(3)
+        scene = type(scene)(scene.start, scene.target, np.zeros((0, 3), np.float32))
     else:
         cfg, scene, hyper = dynamic_workload(1)
         cfg = cfg.with_(max_iters=40)
@@ -44,8 +49,16 @@ def test_static_scratch_plan_matches_handle_plan_twice(native, which):
     ref.set_hyper(hyper)
     ref.set_scene(scene)
     r = ref.plan()
+    side = None
+    if which == "side_stream":
+        side = torch.cuda.Stream()
+        stream = ctypes.c_void_p(side.cuda_stream)
+    free_before = None
     for call in range(2):
-        rc, wp, res = _plan_static(native, cfg, scene, hyper)
+        if call == 1:
+            torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info()[0]
+        rc, wp, res = _plan_static(native, cfg, scene, hyper, stream)
         assert rc == 0, native.sepso_last_error()
         assert res.status == 0
         assert res.iters == r["iters"]
@@ -53,6 +66,18 @@ def test_static_scratch_plan_matches_handle_plan_twice(native, which):
         assert res.cost == pytest.approx(r["cost"], rel=1e-4)
         assert res.length == pytest.approx(r["length"], rel=1e-5)
         np.testing.assert_allclose(wp, r["waypoints"], rtol=1e-5, atol=1e-5 * 400)
+    # the second call took no device memory (the first may have loaded the module)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+
+
+def test_static_scratch_rejects_negative_v_limit(native):
+    cfg, scene, hyper = static_workload(0)
+    bad = np.array(hyper, np.float32).copy()
+    bad[2 * 6 + 5] = -0.05  # group 2's V_limit, refused by sepso_set_hyper too
+    rc, _, _ = _plan_static(native, cfg, scene, bad)
+    assert rc == -1  # SEPSO_EINVAL
+    assert b"V_limit" in native.sepso_last_error()
 
 
 def test_static_scratch_rejects_oversized_config(native):
