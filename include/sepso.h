@@ -691,6 +691,18 @@ int64_t sepso_bf_launch_count(sepso_bf_handle h);
 const char* sepso_bf_kernel_name(sepso_bf_handle h);
 const char* sepso_bf_last_error(void);
 
+/* The planner's random numbers on their own, for checking: Philox4x32-10 (Salmon,
+ * Moraes, Dror and Shaw, SC'11: ten rounds of the two multipliers 0xD2511F53 and
+ * 0xCD9E8D57 with the Weyl key increments 0x9E3779B9 and 0xBB67AE85) of n counters
+ * under the key (seed low word, seed high word), computed on the device by the
+ * function the kernels draw with.  The planner's counters are (iteration or
+ * coordinate chunk, particle, stream << 24 | cycle, run); its uniforms are
+ * (word >> 8) 2^-24, and R1, R2, R3 of Eq. TOF_V are words 0, 1, 2 of counter
+ * (k, g N + n, 0 << 24 | cycle, run).  ctr, out: device uint32[n][4] (16-byte
+ * aligned, caller-owned; they may not overlap).  Async on stream; allocates nothing.
+ * Errors: EINVAL (n < 0, NULL or misaligned arrays), ECUDA. */
+int sepso_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out, void* stream);
+
 /* Auto Truncation window criterion (Sec. 3.3.4, first criterion) on its own, for
  * checking: for each of `count` windows, whether the population standard deviation
  * of the ns[i] newest entries of the ring win[i*tw .. i*tw+tw) (head heads[i], the

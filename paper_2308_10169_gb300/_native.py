@@ -207,6 +207,7 @@ SIGNATURES = {
     "sepso_gemm_bf16_ex": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _i32, _i32, ctypes.c_float, _vp, _i32,
                                           _vp, _i32, _vp, _i32, _vp, _i32, ctypes.POINTER(GemmExtra), _i32,
                                           _vp]),
+    "sepso_philox": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_uint64, _vp, _vp]),
     "sepso_at_window_test": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp]),
     "sepso_bf_workspace_size": (ctypes.c_int, [ctypes.POINTER(BFConfig), ctypes.POINTER(_sz)]),
     "sepso_bf_create": (ctypes.c_int, [ctypes.POINTER(BFConfig), _vp, _sz, _vp, ctypes.POINTER(_vp)]),

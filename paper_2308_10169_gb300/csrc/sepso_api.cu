@@ -868,6 +868,23 @@ extern "C" int sepso_watchdog_selftest(int32_t limit_us, int32_t* fired, void* s
 }
 
 // ---------------------------------------------------------------------------
+// The planner's Philox4x32-10 on caller-given counters (device arrays).
+// ---------------------------------------------------------------------------
+extern "C" int sepso_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out, void* stream) {
+  if (n < 0) return fail(SEPSO_EINVAL, "n=%lld is negative", (long long)n);
+  if (n == 0) return SEPSO_OK;
+  if (!ctr || !out) return fail(SEPSO_EINVAL, "NULL counter or output array");
+  if ((reinterpret_cast<uintptr_t>(ctr) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+    return fail(SEPSO_EINVAL, "counter and output arrays must be 16-byte aligned");
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(launch_philox(reinterpret_cast<const uint4*>(ctr), (long long)n, seed, reinterpret_cast<uint4*>(out), sms,
+                         static_cast<cudaStream_t>(stream)));
+  return SEPSO_OK;
+}
+
+// ---------------------------------------------------------------------------
 // The Auto Truncation window criterion, evaluated on the device by the planner's code.
 // ---------------------------------------------------------------------------
 extern "C" int sepso_at_window_test(const double* win, const int32_t* ns, const int32_t* heads, int32_t count,

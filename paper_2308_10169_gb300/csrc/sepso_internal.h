@@ -56,6 +56,7 @@ cudaError_t launch_hsef_init(const HsefParams& p, cudaStream_t s);
 cudaError_t launch_hsef_update(const HsefParams& p, int e, cudaStream_t s);
 cudaError_t launch_at_window(const double* win, const int32_t* ns, const int32_t* heads, int count, int tw,
                              float delta, int32_t* out, cudaStream_t s);
+cudaError_t launch_philox(const uint4* ctr, long long n, uint64_t seed, uint4* out, int num_sms, cudaStream_t s);
 cudaError_t launch_watchdog_selftest(const unsigned int* never, unsigned long long limit_ns, int* fired,
                                      cudaStream_t s);
 

@@ -21,6 +21,7 @@
 // winning rows it needs.  A slot of parity k & 1 is rewritten only at k + 2,
 // after the barrier of k + 1, i.e. after every CTA has finished reading the
 // slots of k.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <cstdint>
@@ -883,6 +884,20 @@ __global__ void at_window_kernel(const double* win, const int32_t* ns, const int
 cudaError_t launch_at_window(const double* win, const int32_t* ns, const int32_t* heads, int count, int tw,
                              float delta, int32_t* out, cudaStream_t s) {
   at_window_kernel<<<count, 32, 0, s>>>(win, ns, heads, tw, delta, out);
+  return cudaGetLastError();
+}
+
+// Philox4x32-10 on given counters: the planner's own generator (the function every
+// kernel draws R1..R3 and the initial positions with), one counter per thread.
+__global__ void philox_kernel(const uint4* ctr, long long n, uint32_t k0, uint32_t k1, uint4* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+cudaError_t launch_philox(const uint4* ctr, long long n, uint64_t seed, uint4* out, int num_sms, cudaStream_t s) {
+  const long long blocks = std::min<long long>((n + 255) / 256, 8LL * (num_sms > 0 ? num_sms : 1));
+  philox_kernel<<<(int)std::max<long long>(blocks, 1), 256, 0, s>>>(ctr, n, (uint32_t)(seed & 0xffffffffu),
+                                                                   (uint32_t)(seed >> 32), out);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,20 @@ def at_window_test(win, ns, heads, delta: float) -> np.ndarray:
     return out.astype(bool)
 
 
+def philox_device(ctr: torch.Tensor, seed: int) -> torch.Tensor:
+    """Philox4x32-10 of the counters ``ctr`` (device int32/uint32 tensor (n, 4)) under
+    the 64-bit ``seed``, computed on the device by the planner's own generator;
+    returns the (n, 4) output words (int32 tensor holding the uint32 bits)."""
+    c = ctr.contiguous()
+    if c.dim() != 2 or c.shape[1] != 4 or c.element_size() != 4 or not c.is_cuda:
+        raise ValueError("ctr must be a CUDA tensor of shape (n, 4) with 32-bit elements")
+    out = torch.empty_like(c)
+    stream = torch.cuda.current_stream(c.device).cuda_stream
+    check(_native.lib().sepso_philox(ctypes.c_void_p(c.data_ptr()), c.shape[0], ctypes.c_uint64(seed),
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream)))
+    return out
+
+
 class Planner:
     """One SEPSO planner (``cfg.runs`` swarms sharing one scene) on one GPU."""
 

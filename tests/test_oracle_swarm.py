@@ -225,3 +225,53 @@ def test_tie_goes_to_lowest_index():
         assert s["Pfit"][0] == s["Pfit"][1]
         np.testing.assert_array_equal(s["Gb"], X[0])
         np.testing.assert_array_equal(s["Tb"], X[0])
+
+
+@pytest.mark.parametrize("k0,cycle", [(0, 0), (41, 3)])
+def test_one_particle_update_reproduced_by_hand(k0, cycle):
+    # Eqs. TOF_omega, TOF_V and TOF_X for single particles, written out by hand.
+    # The factors come from the generator pinned by the published known-answer
+    # vectors, at the counter the update uses: (k, particle g N + n, VEL << 24 |
+    # cycle, run) under the 64-bit seed as key; R1, R2, R3 are words 0, 1, 2 of the
+    # output, each mapped to (word >> 8) 2^-24.  Any swap of the words, of the
+    # counter fields, of an attractor's row or of the clipping fails this.
+    seed, run_id = 0x0123_4567_89AB_CDEF, 11
+    hyper = np.array([[1.3, 1.7, 0.6, 0.9, 0.4, 0.05],
+                      [2.1, 0.8, 1.1, 0.7, 0.5, 0.02]])
+    sw = oracle.Swarm(_cfg(seed=seed, run_id=run_id), hyper)
+    rng = np.random.default_rng(17)
+    X = rng.uniform(0, 400, (M, D))
+    # particle 4's P is far away and its velocity large: its coordinates hit both
+    # the velocity clip and the map clip
+    V = rng.uniform(-15, 15, (M, D))
+    P = X + rng.uniform(-60, 60, (M, D))
+    X[4] = np.array([3.0, 398.0, 396.0, 1.5])
+    P[4] = np.array([-500.0, 900.0, 950.0, -700.0])
+    V[4] = np.array([-30.0, 30.0, 25.0, -25.0])
+    Gb = rng.uniform(0, 400, (G, D))
+    Tb = rng.uniform(0, 400, D)
+    sw.load({"X": X, "V": V, "P": P, "Pfit": np.full(M, -np.inf), "Gb": Gb, "Gfit": np.full(G, -np.inf),
+             "Tb": Tb, "Tfit": [-np.inf], "k": [k0], "cycle": [cycle]})
+    sw.step(EMPTY, 1)
+    s1 = sw.state()
+    k = k0 + 1
+    cap = 100
+    for p in range(M):
+        g = p // N
+        c1, c2, c3, w_init, w_end, vlim = hyper[g]
+        words = oracle.philox(np.array([[k, p, (0 << 24) | cycle, run_id]], np.uint32), seed)[0]
+        r1, r2, r3 = [int(wd >> 8) * 2.0 ** -24 for wd in words[:3]]
+        w = w_init - (w_init - w_end) / cap * k
+        for j in range(D):
+            ext = 400.0
+            v = w * V[p, j] + c1 * r1 * (P[p, j] - X[p, j]) + c2 * r2 * (Gb[g, j] - X[p, j]) \
+                + c3 * r3 * (Tb[j] - X[p, j])
+            v = min(max(v, -vlim * ext), vlim * ext)
+            x = min(max(X[p, j] + v, 0.0), ext)
+            assert s1["V"].reshape(M, D)[p, j] == pytest.approx(v, rel=1e-12, abs=1e-9)
+            assert s1["X"].reshape(M, D)[p, j] == pytest.approx(x, rel=1e-12, abs=1e-9)
+    # particle 4 did reach both clips
+    v4 = s1["V"].reshape(M, D)[4]
+    x4 = s1["X"].reshape(M, D)[4]
+    assert np.any(np.abs(v4) == hyper[1, 5] * 400.0)
+    assert np.any((x4 == 0.0) | (x4 == 400.0))
