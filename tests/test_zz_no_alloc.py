@@ -73,8 +73,8 @@ def test_static_scratch_plan_matches_handle_plan_twice(native, which):
 
 def test_static_scratch_rejects_negative_v_limit(native):
     cfg, scene, hyper = static_workload(0)
-    bad = np.array(hyper, np.float32).copy()
-    bad[2 * 6 + 5] = -0.05  # group 2's V_limit, refused by sepso_set_hyper too
+    bad = np.array(hyper, np.float32).reshape(-1, 6).copy()
+    bad[2, 5] = -0.05  # group 2's V_limit, refused by sepso_set_hyper too
     rc, _, _ = _plan_static(native, cfg, scene, bad)
     assert rc == -1  # SEPSO_EINVAL
     assert b"V_limit" in native.sepso_last_error()
