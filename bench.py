@@ -44,8 +44,36 @@ WORKLOAD = ("dynamic SEPSO run: 400x400 map, T=20 (D=40), G=8 x N=170, 64 circle
             "(32 static, 32 moving |v|~U[0.5,2]/cycle, wall bounce), start/target drift 1/cycle, "
             "PI gamma=0.25 + AT stall 10 / cap 300, alpha=30 beta=4, HSEF-evolved (w,C1,C2)")
 
-# FP32 peak from the unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# The kernel that runs a planning cycle, by the form of its per-iteration exchange.
+SWARM_KERNEL = {"cluster": "swarm_cluster_kernel", "grid": "swarm_kernel"}
+# FP32 lanes per SM of this architecture (the profiling recipe's unit count).
+FP32_LANES_PER_SM = 128
+_CLOCK = {}  # the SM clock sampled under load in the main section (used by the later sections)
+
+
+def fp32_peak(sm_mhz=None):
+    """(TFLOP/s, source): the FP32 FMA peak of this device from its queried SM count x
+    128 FP32 lanes x 2 flop x the SM clock -- the median sampled under load when
+    given (or sampled earlier in this run), else the device's maximum clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    src = "median sampled under load"
+    mhz = sm_mhz or _CLOCK.get("sm_mhz")
+    if sm_mhz:
+        _CLOCK["sm_mhz"] = sm_mhz
+    if not mhz:
+        mhz, src = _max_sm_mhz(), "maximum SM clock (nvidia-smi)"
+    return (sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12,
+            f"derived: {sms} SMs (queried) x {FP32_LANES_PER_SM} FP32 lanes x 2 x {mhz:.0f} MHz ({src})")
+
+
+def _max_sm_mhz() -> float:
+    try:
+        out = subprocess.run(["nvidia-smi", "--id=0", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
+        return float(out[0])
+    except Exception:
+        return 2070.0
 # Algorithmic work of one particle evaluation: (T+1) segments x (18 flops per
 # segment-circle test x O circles + 8 flops of length), per the scope table.
 FLOPS_PER_PAIR, FLOPS_PER_SEGMENT = 18, 8
@@ -65,12 +93,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ref-seconds", type=float, default=0.0,
-                    help="CPU budget of the reference arm (0 = from --steps/--warmup, 10..150 s)")
     ap.add_argument("--hsef-evolutions", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=0, help="0 = same as --steps")
     ap.add_argument("--cost-cycles", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--match-seeds", type=int, default=64,
+                    help="Philox keys of the GPU-vs-oracle cost match on the headline workload")
+    ap.add_argument("--match-cycles", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-scenes", type=int, default=4096,
                     help="scenes of the batched section (0 = skip it)")
@@ -162,30 +191,106 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# Oracle (CPU) arm
+# Hyper-parameters of the application phase, shared by both arms
 # ----------------------------------------------------------------------------
 
-def oracle_cycles(seconds: float, max_cycles: int, seed: int = 0):
-    """Run the FP64 oracle on the same dynamic workload for a bounded time."""
+HYPER_FILE = ROOT / "tests" / "golden" / "dynamic_hsef_hyper.json"
+
+
+def shared_hyper():
+    """(G x 6 hyper-parameters, description): the per-group (w, C1, C2) that the
+    oracle's HSEF evolution phase found on the dynamic workload's first scene
+    (tests/golden/make_dynamic_hsef_hyper.py writes them), so that the GPU planner
+    and the FP64 oracle plan the same configuration and their costs compare."""
+    d = json.loads(HYPER_FILE.read_text())
+    return np.asarray(d["hyper"], np.float32), "HSEF-evolved (w,C1,C2): " + d["source"]
+
+
+def run_config(K: int, world: int) -> dict:
+    """The ``config`` object of both arms' JSON lines (identical by construction)."""
+    return {"workload": WORKLOAD, "hyper": shared_hyper()[1], "cycles": K, "replicas": world,
+            "l2": "GPU arm: flushed before every step (256 MiB write outside the timed events); "
+                  "CPU arm: none"}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------
+# Oracle (CPU) arm: independent dynamic runs, one per host core
+# ----------------------------------------------------------------------------
+
+def _oracle_run_worker(seed, n_warm, n_timed, seconds, barrier, out):
+    """One process of the oracle arm: the dynamic run with Philox key ``seed`` (the
+    scene of seed 0, the shared hyper-parameters), n_warm untimed cycles, then --
+    after the barrier -- n_timed timed cycles (or cycles until ``seconds`` pass
+    when n_timed < 0).  Puts (seed, t_start, t_end, per-cycle seconds, iters,
+    costs, Q) on ``out``."""
     import oracle
     from paper_2308_10169_gb300.inputs import dynamic_workload
-    cfg, scene, hyper = dynamic_workload(seed)
+    cfg, scene, _ = dynamic_workload(0)
+    cfg = cfg.with_(seed=seed)
+    hyper, _ = shared_hyper()
     sw = oracle.Swarm(cfg, hyper)
     c, v, st, sv, tg, tv = (scene.circles, scene.circle_vel, scene.start, scene.start_vel,
                             scene.target, scene.target_vel)
-    times, iters, costs = [], [], []
-    t_all = time.perf_counter()
-    for cyc in range(max_cycles):
-        t0 = time.perf_counter()
+    cyc = 0
+
+    def one():
+        nonlocal c, v, st, sv, tg, tv, cyc
         if cyc:
             c, v, st, sv, tg, tv = oracle.advance_scene(cfg.map_w, cfg.map_h, c, v, st, sv, tg, tv)
-        r = sw.plan(oracle.Scene(st, tg, c))
-        times.append(time.perf_counter() - t0)
+        cyc += 1
+        return sw.plan(oracle.Scene(st, tg, c))
+
+    for _ in range(n_warm):
+        one()
+    if barrier is not None:
+        barrier.wait()
+    times, iters, costs, qs = [], [], [], []
+    t0 = time.time()
+    while (n_timed >= 0 and len(times) < n_timed) or (n_timed < 0 and time.time() - t0 < seconds):
+        t = time.perf_counter()
+        r = one()
+        times.append(time.perf_counter() - t)
         iters.append(r["iters"])
         costs.append(r["cost"])
-        if time.perf_counter() - t_all > seconds:
-            break
-    return cfg, times, iters, costs
+        qs.append(r["Q"])
+    out.put((seed, t0, time.time(), times, iters, costs, qs))
+
+
+def oracle_runs(n_workers: int, warm: list, timed: list, seconds: float = 0.0):
+    """Runs _oracle_run_worker in n_workers spawned processes (the GPU may already be
+    in use by this process, so no fork); returns the merged record."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    barrier = ctx.Barrier(n_workers)
+    procs = [ctx.Process(target=_oracle_run_worker, args=(w, warm[w], timed[w], seconds, barrier, out))
+             for w in range(n_workers)]
+    for p_ in procs:
+        p_.start()
+    res = [out.get() for _ in procs]
+    for p_ in procs:
+        p_.join()
+    t_start = min(r[1] for r in res)
+    t_end = max(r[2] for r in res)
+    times = [t for r in res for t in r[3]]
+    return {"wall": t_end - t_start, "times": times, "iters": [i for r in res for i in r[4]],
+            "costs": [x for r in res for x in r[5]], "Q": [x for r in res for x in r[6]],
+            "workers": n_workers}
+
+
+def plan_stats(iters, costs, qs, cap: int) -> dict:
+    """Auto Truncation and quality figures of a set of planning cycles."""
+    iters, costs, qs = np.asarray(iters), np.asarray(costs, np.float64), np.asarray(qs)
+    return {"cycles": int(iters.size), "iters_per_plan": float(iters.mean()),
+            "at_fire_rate": float(np.mean(iters < cap)), "collision_free": float(np.mean(qs == 0)),
+            "median_cost": float(np.median(costs))}
 
 
 def aggregate_timing(total_ms: float, steps: int, world: int):
@@ -201,27 +306,33 @@ def aggregate_timing(total_ms: float, steps: int, world: int):
 
 
 def run_reference(args, rank, world):
+    """The oracle on the host cores: W warm-up and K timed planning cycles in all,
+    spread over one independent dynamic run per core (each run sequential, as PI
+    needs its previous cycle); value = K / wall time of the timed phase."""
     if rank != 0:
         return
-    budget = args.ref_seconds if args.ref_seconds > 0 else max(10.0, min(150.0, 3.0 * (args.steps + args.warmup)))
-    warm = min(args.warmup, 1)
-    cfg, times, iters, costs = oracle_cycles(budget, warm + args.steps)
-    times, iters, costs = times[warm:], iters[warm:], costs[warm:]
-    n = len(times)
-    total = sum(times)
-    value = n / total
-    pe = sum(iters) * cfg.G * cfg.N / total
+    K, W = args.steps, args.warmup
+    P = max(1, min(host_cores(), K))
+    warm = [W // P + (1 if w < W % P else 0) for w in range(P)]
+    timed = [K // P + (1 if w < K % P else 0) for w in range(P)]
+    r = oracle_runs(P, warm, timed)
+    value = K / r["wall"]
+    from paper_2308_10169_gb300.inputs import dynamic_workload
+    cfg = dynamic_workload(0)[0]
+    st = plan_stats(r["iters"], r["costs"], r["Q"], cfg.max_iters)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-        "steps": n, "warmup": warm, "ms_per_step": 1e3 * total / n, "higher_is_better": True,
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * r["wall"] / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD + " (oracle: hyper-parameters as sampled, no HSEF)",
-                   "cycles_timed": n},
-        "particle_evals_per_s": pe, "iters_per_plan": float(np.mean(iters)),
-        "median_cost": float(np.median(costs)),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"cycles {warm}..{warm + n - 1} of the dynamic run, one thread, "
-                                   f"{total:.1f} s"},
+        "config": run_config(K, world),
+        "particle_evals_per_s": sum(r["iters"]) * cfg.G * cfg.N / r["wall"],
+        "latency_ms_single_thread": {"mean": 1e3 * float(np.mean(r["times"])),
+                                     "p50": 1e3 * float(np.percentile(r["times"], 50))},
+        **st,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
+                         "sample": f"{K} timed planning cycles after {W} warm-up cycles, spread over {P} "
+                                   f"independent dynamic runs (Philox keys 0..{P - 1}, one process per "
+                                   f"core, {host_cores()} cores seen), FP64, wall {r['wall']:.1f} s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -251,6 +362,7 @@ def run_ours(args, rank, world, local):
             dist.barrier()
 
     cfg, scene, hyper0 = dynamic_workload(seed=rank)
+    app_hyper, _ = shared_hyper()
 
     # -- evolution phase (HSEF): 8 H-groups x 4 H-particles, Table hyper8 --------
     HG, HN = 8, 4
@@ -269,14 +381,18 @@ def run_ours(args, rank, world, local):
                  "l_run_iters": cfg.max_iters, "ms": hsef_ms,
                  "evolutions_per_s": 1e3 * args.hsef_evolutions / hsef_ms,
                  "lfv_first": float(hist[0].item()), "lfv_best": best_lfv,
-                 "launches": hp.launch_count()}
+                 "exchange": hp.exchange_form(), "launch": hp.launch_shape(),
+                 "oracle_hsef_lfv_best": json.loads(HYPER_FILE.read_text())["lfv_best"],
+                 "launches": hp.launch_count(),
+                 "note": "the application phase plans with the oracle-evolved set (shared with the "
+                         "CPU arm); this GPU evolution phase is timed beside it"}
     del hp
 
     # -- application phase ----------------------------------------------------
     pl = Planner(cfg, device=dev)
-    pl.set_hyper(best_hyper)
+    pl.set_hyper(app_hyper)
     pl.set_scene(scene)
-    shape = pl.launch_shape()
+    shape = dict(pl.launch_shape(), exchange=pl.exchange_form())
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     for i in range(W):
@@ -313,11 +429,15 @@ def run_ours(args, rank, world, local):
     last = pl.read_result()
     iters = iters1 - iters0
     assert plans1 - plans0 == K
-    # median path cost of the same run over the next cycles (untimed: each is read back)
+    # quality of the same run over the next cycles (untimed: each is read back)
+    c_iters, c_q = [], []
     for _ in range(args.cost_cycles):
         pl.advance(1)
         pl.plan_async()
-        costs.append(pl.read_result()["cost"])
+        r_ = pl.read_result()
+        costs.append(r_["cost"])
+        c_iters.append(r_["iters"])
+        c_q.append(r_["Q"])
 
     total_max, value = aggregate_timing(total_ms, K, world)
     pe_local = iters * cfg.G * cfg.N
@@ -326,7 +446,9 @@ def run_ours(args, rank, world, local):
 
     # -- end to end through the C ABI with host buffers ----------------------------
     Ke = args.e2e_steps or K
-    e2e = run_e2e(torch, pl, cfg, scene, best_hyper, dev, Ke, W)
+    e2e = run_e2e(torch, pl, cfg, scene, app_hyper, dev, Ke, W)
+    clocks = clk.summary()
+    peak, peak_src = fp32_peak(clocks.get("sm_mhz"))
 
     line = None
     if rank == 0:
@@ -335,9 +457,8 @@ def run_ours(args, rank, world, local):
             "warmup": W, "ms_per_step": total_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded scenes shaped like the paper's dynamic environment)",
-            "config": {"workload": WORKLOAD, "cycles": K, "replicas": world,
-                       "l2": "flushed before every step (256 MiB write outside the timed events)",
-                       "launch": shape},
+            "config": run_config(K, world),
+            "launch": shape,
             "particle_evals_per_s": world * pe_local / (total_max / 1e3),
             "iters_per_plan": iters / K,
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -345,15 +466,17 @@ def run_ours(args, rank, world, local):
                            "max": float(step_ms.max())},
             "cost_last": float(last["cost"]),
             "median_cost": float(np.median(costs)) if costs else None,
-            "median_cost_sample": f"the {len(costs)} cycles after the timed ones, read back one by one",
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "quality": dict(plan_stats(c_iters, costs, c_q, cfg.max_iters),
+                            sample=f"the {len(costs)} cycles after the timed ones, read back one by one")
+            if costs else None,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": SWARM_TRAFFIC_BYTES,
-                         "kernel": "swarm_kernel",
-                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+                         "kernel": SWARM_KERNEL[shape["exchange"]],
+                         "peak_source": peak_src},
             "e2e": e2e,
             "gpu_launches": int(launches),
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "hsef": hsef_info,
             "wall_s_timed_loop": t_wall,
         }
@@ -435,8 +558,8 @@ def run_batch(n: int, iters: int):
             "plans_per_s": n / (ms / 1e3), "ms": ms,
             "particle_evals_per_s": sum(sp.G * sp.N for sp in specs) * iters / (ms / 1e3),
             "pair_tests_per_s": pairs / (ms / 1e3),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak()[0],
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak()[0], "peak_source": fp32_peak()[1],
                          "kernel": "batch_kernel"},
             "shape": bp.shape(), "autotune_ms_per_launch": tune_ms,
             "gpu_launches": bp.launch_count() - l0,
@@ -600,8 +723,8 @@ def run_poly(runs: int = 64, iters: int = 100):
         out["batch" if R == runs else "single"] = {
             "runs": R, "ms": ms, "plans_per_s": R / (ms / 1e3), "us_per_iteration": 1e3 * ms / iters,
             "median_cost": float(np.median(F.cpu().numpy())), "collision_free": float(np.mean(Q == 0)),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "kernel": kname,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak()[0], "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak()[0], "peak_source": fp32_peak()[1], "kernel": kname,
                          "flops_per_pair": 20},
             "gpu_launches": pl.launch_count() - l0}
         del pl
@@ -806,14 +929,86 @@ def run_gemm(B: int = 4096, H1: int = 1024, K: int = 4104, reps: int = 20):
 
 
 def cpu_baseline(seconds: float):
-    cfg, times, iters, costs = oracle_cycles(seconds, 10_000)
-    n, total = len(times), sum(times)
-    return {"value": n / total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n} planning cycles of the same dynamic run (hyper-parameters as "
-                      f"sampled, no HSEF), FP64, one thread, {total:.1f} s",
-            "particle_evals_per_s": sum(iters) * cfg.G * cfg.N / total,
-            "iters_per_plan": float(np.mean(iters)), "median_cost": float(np.median(costs)),
-            "_costs": [float(c) for c in costs], "_iters": [int(i) for i in iters]}
+    """The oracle on all host cores for a bounded time: one independent dynamic run
+    per core (Philox keys 0..P-1, the shared hyper-parameters), cycles until
+    ``seconds`` pass in each run; value = cycles / wall time."""
+    from paper_2308_10169_gb300.inputs import dynamic_workload
+    P = host_cores()
+    r = oracle_runs(P, [0] * P, [-1] * P, seconds)
+    cfg = dynamic_workload(0)[0]
+    n = len(r["times"])
+    return {"value": n / r["wall"], "unit": UNIT, "cores": P, "kind": "oracle",
+            "sample": f"the first cycles of {P} independent dynamic runs (Philox keys 0..{P - 1}, "
+                      f"shared hyper-parameters), one process per core, about {seconds:.0f} s each: "
+                      f"{n} cycles in {r['wall']:.1f} s wall, FP64",
+            "particle_evals_per_s": sum(r["iters"]) * cfg.G * cfg.N / r["wall"],
+            "latency_ms_single_thread": {"mean": 1e3 * float(np.mean(r["times"])),
+                                         "p50": 1e3 * float(np.percentile(r["times"], 50))},
+            **plan_stats(r["iters"], r["costs"], r["Q"], cfg.max_iters)}
+
+
+def _oracle_seed_worker(args):
+    """The oracle's first ``cycles`` cycles of the dynamic run under Philox key seed."""
+    seed, cycles = args
+    import oracle
+    from paper_2308_10169_gb300.inputs import dynamic_workload
+    cfg, scene, _ = dynamic_workload(0)
+    hyper, _ = shared_hyper()
+    sw = oracle.Swarm(cfg.with_(seed=seed), hyper)
+    c, v, st, sv, tg, tv = (scene.circles, scene.circle_vel, scene.start, scene.start_vel,
+                            scene.target, scene.target_vel)
+    out = []
+    for cyc in range(cycles):
+        if cyc:
+            c, v, st, sv, tg, tv = oracle.advance_scene(cfg.map_w, cfg.map_h, c, v, st, sv, tg, tv)
+        r = sw.plan(oracle.Scene(st, tg, c))
+        out.append((r["cost"], r["iters"], r["Q"]))
+    return out
+
+
+def cost_match_dynamic(seeds: int = 64, cycles: int = 2):
+    """GPU vs oracle path cost on the headline workload with the shared
+    hyper-parameters: under each of ``seeds`` Philox keys both plan the first
+    ``cycles`` cycles of the dynamic run (a cold start, then PI; AT by stall
+    counter, cap 300).  FP32 and FP64 trajectories separate, so the medians over
+    the seeds are compared, cycle by cycle."""
+    import multiprocessing as mp
+
+    from paper_2308_10169_gb300 import Planner
+    from paper_2308_10169_gb300.inputs import dynamic_workload
+    cfg, scene, _ = dynamic_workload(0)
+    hyper, _ = shared_hyper()
+    t0 = time.perf_counter()
+    gpu = []
+    for s_ in range(seeds):
+        pl = Planner(cfg.with_(seed=s_))
+        pl.set_hyper(hyper)
+        pl.set_scene(scene)
+        row = []
+        for cyc in range(cycles):
+            if cyc:
+                pl.advance(1)
+            r = pl.plan()
+            row.append((r["cost"], r["iters"], r["Q"]))
+        gpu.append(row)
+    t_gpu = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P = min(host_cores(), seeds)
+    with mp.get_context("spawn").Pool(P) as pool:
+        ora = pool.map(_oracle_seed_worker, [(s_, cycles) for s_ in range(seeds)], chunksize=1)
+    t_ora = time.perf_counter() - t0
+    per = []
+    for cyc in range(cycles):
+        g = [row[cyc] for row in gpu]
+        o = [row[cyc] for row in ora]
+        gm, om = float(np.median([x[0] for x in g])), float(np.median([x[0] for x in o]))
+        per.append({"cycle": cyc,
+                    "gpu": plan_stats([x[1] for x in g], [x[0] for x in g], [x[2] for x in g], cfg.max_iters),
+                    "oracle": plan_stats([x[1] for x in o], [x[0] for x in o], [x[2] for x in o], cfg.max_iters),
+                    "rel_diff_median_cost": (gm - om) / om})
+    return {"workload": "the headline dynamic run's first cycles, shared hyper-parameters",
+            "seeds": seeds, "cycles": per, "gpu_seconds": t_gpu,
+            "oracle_seconds": t_ora, "oracle_processes": P}
 
 
 def oracle_match(seeds: int = 64):
@@ -857,11 +1052,9 @@ def main():
         line = {"metric": METRIC, "unit": UNIT, "sections": sorted(sections)} if rank == 0 else None
     if rank == 0:
         if world == 1 and "cpu" in sections and not args.no_cpu_baseline:
-            cb = cpu_baseline(args.cpu_seconds)
-            cb.pop("_costs")
-            cb.pop("_iters")
-            line["cpu_baseline"] = cb
+            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
             line["oracle_match"] = oracle_match()
+            line["cost_match"] = cost_match_dynamic(args.match_seeds, args.match_cycles)
         if world == 1 and "batch" in sections and args.batch_scenes > 0:
             line["batch"] = run_batch(args.batch_scenes, args.batch_iters)
         if world == 1 and "prior" in sections and args.prior_train > 0:

@@ -85,6 +85,17 @@ typedef struct {
   int32_t fitness_mode;   /* 0 = automatic; 1 = a lane group per particle; 2 =
                              (particle, segment, circle chunk) items spread over
                              all threads of a CTA                                  */
+  int32_t exchange;       /* how the CTAs of a run trade their bests each
+                             iteration: 0 = automatic (the cluster form whenever
+                             every group's C3 is 0 and it fits, else the
+                             grid-wide form); 1 = grid-wide: one barrier of all
+                             the run's CTAs per iteration; 2 = cluster form: the
+                             CTAs of a group form one thread-block cluster and
+                             trade through distributed shared memory, groups
+                             trade only (Gfit, Q) through global memory, read one
+                             iteration later (needs C3 = 0 in every group: Eq.
+                             TOF_V then uses the own group's Gbest alone).  Both
+                             forms give identical results.                        */
 } sepso_config;
 
 /* Outcome of one planning cycle of one run. */
@@ -578,9 +589,15 @@ int sepso_gemm_bf16_ex(const void* A, const void* B, int32_t M, int32_t N, int32
  * (e.g. SEPSO_ETIMEOUT), else SEPSO_OK, and clears it. */
 int sepso_sync(sepso_handle h);
 
-/* Launch shape chosen at create: CTAs per group, threads, circle split, grid. */
+/* Launch shape chosen at create, of the form the next plan or step launches
+ * (see sepso_exchange_form): CTAs per group, threads, circle split, grid. */
 int sepso_launch_shape(sepso_handle h, int32_t* ctas_per_group, int32_t* threads,
                        int32_t* circle_split, int32_t* grid);
+
+/* The form of the exchange the next plan or step launches: 2 = one thread-block
+ * cluster per group (every group's C3 is 0 and the cluster form fits), 1 = the
+ * grid-wide barrier (sepso_config.exchange).  Negative on a bad handle. */
+int sepso_exchange_form(sepso_handle h);
 
 /* Cumulative counters of run `run` (host outputs, sync): planning cycles
  * finished and iterations of Algorithm 1 executed (plans and steps). */

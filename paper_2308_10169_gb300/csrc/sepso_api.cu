@@ -47,7 +47,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 // Byte offsets of every array in the caller's workspace.
 struct WsLayout {
   size_t circ, pairs, cvel, pts, hyper, X, V, P, Pfit, PQ, Gb, Gfit, GQ, Tb, prevT, res_wp, ctl, res, win,
-      gword, counter, crows, hhyper, HX, HV, HP, HPfit, HGb, HGfit, HTb, HTfit, estatus, total;
+      gword, counter, crows, grec, hhyper, HX, HV, HP, HPfit, HGb, HGfit, HTb, HTfit, estatus, total;
 };
 
 WsLayout make_ws(const sepso_config& c) {
@@ -84,6 +84,7 @@ WsLayout make_ws(const sepso_config& c) {
   L.gword = take(R * 3 * G * 8);
   L.counter = take(R * sizeof(RunCounter));
   L.crows = take(R * 2 * M * (D + 4) * 4);
+  L.grec = take(R * kRecDepth * G * 8);
   L.hhyper = take(32 * 6 * 4);
   L.HX = take(R * DH * 4);
   L.HV = take(R * DH * 4);
@@ -125,6 +126,7 @@ int check_config(const sepso_config* c) {
     return fail(SEPSO_EINVAL, "threads=%d must be 0 or a multiple of 32 in [64, 512]", c->threads);
   if (c->circle_split < 0) return fail(SEPSO_EINVAL, "circle_split < 0");
   if (c->fitness_mode < 0 || c->fitness_mode > 2) return fail(SEPSO_EINVAL, "fitness_mode must be 0, 1 or 2");
+  if (c->exchange < 0 || c->exchange > 2) return fail(SEPSO_EINVAL, "exchange must be 0, 1 or 2");
   return SEPSO_OK;
 }
 
@@ -141,6 +143,12 @@ struct sepso_ctx {
   bool has_scene = false;
   int cpg = 1, ppc = 1, C = 1, threads = 256, split = 1, lp = 32, grid = 1, items = 0;
   size_t smem = 0;
+  // cluster form (one thread-block cluster of cl_S CTAs per group), when it fits
+  bool cl_ok = false;
+  int cl_S = 1, cl_ppc = 1, cl_threads = 256, cl_split = 1, cl_lp = 32, cl_items = 0, cl_grid = 1;
+  size_t cl_smem = 0;
+  std::vector<char> c3_nonzero;  // per run: some group's C3 is not 0 (the update then needs Tbest)
+  bool grec_dirty = false;       // group records not written by the last launches (clear before use)
   int n_pi = 0;
   int64_t launches = 0;
   bool hsef_ready = false;
@@ -215,7 +223,96 @@ SwarmParams swarm_params(const sepso_ctx* h, int mode, int step_iters) {
   p.gword = h->at<unsigned long long>(h->L.gword);
   p.counter = h->at<RunCounter>(h->L.counter);
   p.crows = h->at<float>(h->L.crows);
+  p.grec = h->at<unsigned long long>(h->L.grec);
+  p.spec = 0;
+  p.cta_grid = h->C;
   return p;
+}
+
+// The cluster form runs when it fits and no run's update needs Tbest (C3 = 0 in
+// every group); exchange = 1 / 2 force one form.
+bool use_cluster(const sepso_ctx* h) {
+  if (h->cfg.exchange == 1 || !h->cl_ok) return false;
+  for (char nz : h->c3_nonzero)
+    if (nz) return false;
+  return true;
+}
+
+// Launch one swarm kernel for p (plan or step mode) in the form the handle uses.
+int launch_plan_kernel(sepso_ctx* h, SwarmParams p) {
+  const bool cl = use_cluster(h);
+  if (h->cfg.exchange == 2 && !cl)
+    return fail(h->cl_ok ? SEPSO_EINVAL : SEPSO_ERANGE,
+                h->cl_ok ? "exchange=2 needs C3 = 0 in every group" : "the cluster form does not fit this config");
+  if (!cl) {
+    CUDA_TRY(launch_swarm(p, h->grid, h->threads, h->smem, h->stream));
+    h->grec_dirty = true;
+    return SEPSO_OK;
+  }
+  if (h->grec_dirty) {
+    CUDA_TRY(cudaMemsetAsync(h->ws + h->L.grec, 0, (size_t)h->cfg.runs * kRecDepth * h->cfg.G * 8, h->stream));
+    h->grec_dirty = false;
+  }
+  p.cpg = h->cl_S;
+  p.C = h->cfg.G * h->cl_S;
+  p.ppc = h->cl_ppc;
+  p.split = h->cl_split;
+  p.lp = h->cl_lp;
+  p.items = h->cl_items;
+  p.spec = (p.mode == kModePlan && p.at_mode != SEPSO_AT_OFF) ? 1 : 0;
+  CUDA_TRY(launch_swarm_cluster(p, h->cl_grid, h->cl_threads, h->cl_smem, h->stream));
+  return SEPSO_OK;
+}
+
+// The cluster form: S CTAs per group in one cluster (at most 16), from one CTA
+// per SM down; every cluster of the launch must be resident at once (the groups of
+// a run wait on each other's records), which the occupancy query checks.
+template <class ItemsFor, class ItemsSplit>
+int choose_cluster_shape(sepso_ctx* h, int smem_optin, ItemsFor items_for, ItemsSplit items_split, int lp,
+                         int split) {
+  const sepso_config& c = h->cfg;
+  h->cl_ok = false;
+  if (c.exchange == 1) return SEPSO_OK;
+  const int R = c.runs, G = c.G, N = c.N, T = c.T, D = 2 * T;
+  CUDA_TRY(configure_cluster_kernel((size_t)smem_optin));
+  int S0 = c.ctas_per_group > 0 ? c.ctas_per_group : std::max(1, h->num_sms / std::max(1, R * G));
+  S0 = std::min(S0, std::min(16, N));
+  const int S_lo = c.ctas_per_group > 0 ? S0 : 1;
+  for (int S = S0; S >= S_lo; --S) {
+    const int ppc = (N + S - 1) / S;
+    // X and V are kept twice only when Auto Truncation can stop a plan
+    const ClusterLayout Lc =
+        ClusterLayout::make(c.max_obstacles, ppc, D, T, G, c.tw, S, c.at_mode != SEPSO_AT_OFF ? 1 : 0);
+    const size_t smem = (size_t)Lc.total;
+    if (smem + 256 > (size_t)smem_optin) continue;
+    const int items = items_for(ppc);
+    const int ppw = 32 / lp;
+    const int want = items ? 512 : std::min(512, std::max(64, (ppc + ppw - 1) / ppw * 32));
+    for (int threads = (c.threads ? c.threads : want); threads >= 64; threads -= 64) {
+      int nc = 0;
+      cudaError_t e = cluster_max_active(S, threads, smem, &nc);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        nc = 0;
+      }
+      if ((long long)nc >= (long long)R * G) {
+        h->cl_ok = true;
+        h->cl_S = S;
+        h->cl_ppc = ppc;
+        h->cl_threads = threads;
+        h->cl_split = items ? items_split(threads, ppc) : split;
+        h->cl_lp = items ? 32 : lp;
+        h->cl_items = items;
+        h->cl_smem = smem;
+        h->cl_grid = R * G * S;
+        return SEPSO_OK;
+      }
+      if (c.threads) break;
+    }
+  }
+  if (c.exchange == 2)
+    return fail(SEPSO_ERANGE, "the cluster form does not fit: %d runs x %d groups", R, G);
+  return SEPSO_OK;
 }
 
 // Pick CTAs per group, threads and circle split, then check co-residency: the
@@ -277,7 +374,7 @@ int choose_shape(sepso_ctx* h) {
         h->items = items;
         h->smem = smem;
         h->grid = R * G * cpg;
-        return SEPSO_OK;
+        return choose_cluster_shape(h, smem_optin, items_for, items_split, lp, split);
       }
       if (c.threads) break;
     }
@@ -397,6 +494,7 @@ int sepso_create(const sepso_config* cfg, void* d_workspace, size_t bytes, void*
     delete h;
     return rc;
   }
+  h->c3_nonzero.assign((size_t)cfg->runs, 0);  // the zeroed workspace holds C3 = 0
   e = cudaMallocHost(reinterpret_cast<void**>(&h->staging),
                      ((size_t)std::max(cfg->max_obstacles, 1) + 2) * sizeof(float4));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->staging_free, cudaEventDisableTiming);
@@ -438,11 +536,16 @@ int sepso_set_hyper(sepso_handle h, int32_t run, const float* hyper) {
   for (int g = 0; g < G; ++g)
     if (hyper[g * 6 + 5] < 0) return fail(SEPSO_EINVAL, "V_limit of group %d is negative", g);
   const size_t row = (size_t)G * 6 * sizeof(float);
+  char nz = 0;
+  for (int g = 0; g < G; ++g)
+    if (hyper[g * 6 + 2] != 0.0f) nz = 1;
   if (run >= 0) {
     if ((rc = run_ok(h, run))) return rc;
+    h->c3_nonzero[run] = nz;
     CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.hyper + run * row, hyper, row, cudaMemcpyHostToDevice, h->stream));
     return SEPSO_OK;
   }
+  std::fill(h->c3_nonzero.begin(), h->c3_nonzero.end(), nz);
   std::vector<float> all((size_t)h->cfg.runs * G * 6);
   for (int r = 0; r < h->cfg.runs; ++r) std::memcpy(all.data() + (size_t)r * G * 6, hyper, row);
   CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.hyper, all.data(), all.size() * 4, cudaMemcpyHostToDevice, h->stream));
@@ -542,8 +645,7 @@ int sepso_plan_async(sepso_handle h) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!h->has_scene) return fail(SEPSO_ESTATE, "plan before set_scene");
-  const SwarmParams p = swarm_params(h, kModePlan, 0);
-  CUDA_TRY(launch_swarm(p, h->grid, h->threads, h->smem, h->stream));
+  if ((rc = launch_plan_kernel(h, swarm_params(h, kModePlan, 0)))) return rc;
   h->launches += 1;
   return SEPSO_OK;
 }
@@ -587,8 +689,7 @@ int sepso_step(sepso_handle h, int32_t iters) {
   if (!h->has_scene) return fail(SEPSO_ESTATE, "step before set_scene");
   if (iters < 0) return fail(SEPSO_EINVAL, "iters < 0");
   if (iters == 0) return SEPSO_OK;
-  const SwarmParams p = swarm_params(h, kModeStep, iters);
-  CUDA_TRY(launch_swarm(p, h->grid, h->threads, h->smem, h->stream));
+  if ((rc = launch_plan_kernel(h, swarm_params(h, kModeStep, iters)))) return rc;
   h->launches += 1;
   return SEPSO_OK;
 }
@@ -746,8 +847,9 @@ int sepso_hsef(sepso_handle h, const sepso_hsef_config* hc, float* d_history) {
   SwarmParams sp = swarm_params(h, kModePlan, 0);
   sp.at_mode = SEPSO_AT_OFF;  // an L-run maps hyper-parameters to the LFV after max_iters
   sp.use_pi = 0;
+  std::fill(h->c3_nonzero.begin(), h->c3_nonzero.end(), 0);  // the L-runs' hyper-parameters have C3 = 0
   for (int e = 1; e <= hc->E; ++e) {
-    CUDA_TRY(launch_swarm(sp, h->grid, h->threads, h->smem, h->stream));
+    if ((rc = launch_plan_kernel(h, sp))) return rc;
     CUDA_TRY(launch_hsef_update(p, e, h->stream));
     h->launches += 2;
   }
@@ -803,7 +905,9 @@ int sepso_sync(sepso_handle h) {
     for (size_t r = 0; r < ctl.size(); ++r) {
       std::memset(&cnt[r], 0, sizeof(RunCounter));
       cnt[r].count = (unsigned int)h->C * (unsigned int)ctl[r].iters_total;
+      ctl[r].fin_launches = 0;
     }
+    h->grec_dirty = true;
     CUDA_TRY(cudaMemcpy(h->ws + h->L.ctl, ctl.data(), ctl.size() * sizeof(RunCtl), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(h->ws + h->L.counter, cnt.data(), cnt.size() * sizeof(RunCounter), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(h->ws + h->L.gword, 0xff, ctl.size() * 3 * h->cfg.G * 8));
@@ -817,11 +921,18 @@ int sepso_launch_shape(sepso_handle h, int32_t* ctas_per_group, int32_t* threads
                        int32_t* grid) {
   int rc = check_handle(h);
   if (rc) return rc;
-  if (ctas_per_group) *ctas_per_group = h->cpg;
-  if (threads) *threads = h->threads;
-  if (circle_split) *circle_split = h->split;
-  if (grid) *grid = h->grid;
+  const bool cl = use_cluster(h);
+  if (ctas_per_group) *ctas_per_group = cl ? h->cl_S : h->cpg;
+  if (threads) *threads = cl ? h->cl_threads : h->threads;
+  if (circle_split) *circle_split = cl ? h->cl_split : h->split;
+  if (grid) *grid = cl ? h->cl_grid : h->grid;
   return SEPSO_OK;
+}
+
+int sepso_exchange_form(sepso_handle h) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  return use_cluster(h) ? 2 : 1;
 }
 
 int sepso_counters(sepso_handle h, int32_t run, int64_t* plans, int64_t* iterations) {
@@ -1028,8 +1139,10 @@ extern "C" int sepso_plan_static(const sepso_config* cfg, const float* hyper, co
   CUDA_TRY(cudaMemcpyAsync(h.ws + L.pts, pts, sizeof pts, cudaMemcpyHostToDevice, h.stream));
   CUDA_TRY(launch_pairs(h.at<float4>(L.circ), O, h.at<float4>(L.pairs), h.stream));
 
-  const SwarmParams p = swarm_params(&h, kModePlan, 0);
-  CUDA_TRY(launch_swarm(p, h.grid, h.threads, h.smem, h.stream));
+  h.c3_nonzero.assign(1, 0);
+  for (int g = 0; g < cfg->G; ++g)
+    if (hyper[g * 6 + 2] != 0.0f) h.c3_nonzero[0] = 1;
+  if ((rc = launch_plan_kernel(&h, swarm_params(&h, kModePlan, 0)))) return rc;
 
   sepso_result tmp;
   if (waypoints)

@@ -847,7 +847,12 @@ int sepso_batch_autotune(sepso_batch_handle h, int32_t trial_launches, sepso_bat
         cudaEventRecord(e0, h->stream);
         for (int j = 2; j <= trials; ++j) batch_kernel<<<h->ntiles, th, h->smem, h->stream>>>(p, j);
         cudaEventRecord(e1, h->stream);
-        if (cudaStreamSynchronize(h->stream) != cudaSuccess) continue;
+        const cudaError_t se = cudaStreamSynchronize(h->stream);
+        if (se != cudaSuccess) {  // a device-side fault is sticky: report it here, not at a later call
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return bfail(SEPSO_ECUDA, "autotune trial (tile %d, threads %d): %s", tl, th, cudaGetErrorString(se));
+        }
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
         h->launches += trials + 1;

@@ -29,7 +29,7 @@ struct RunCtl {
   float Tfit;         // F(Tbest)
   float prev_lfv;     // LFV of the previous iteration (AT stall mode)
   uint32_t run_id;    // Philox counter word 3
-  int32_t pad;
+  int32_t fin_launches;  // cluster-form launches finished by this run (end-of-launch barrier target)
   long long plans_total;  // planning cycles finished by this run
   long long iters_total;  // iterations of Algorithm 1 run by this run
 };
@@ -60,7 +60,8 @@ __device__ __forceinline__ int key_q(unsigned long long key) { return (int)((uin
 // (counted across launches) is complete when the counter reaches C * gk.
 struct __align__(128) RunCounter {
   unsigned int count;
-  unsigned int pad[31];
+  unsigned int fin;   // cluster form: one arrival per group at the end of each launch
+  unsigned int pad[30];
 };
 
 enum : int { kModePlan = 0, kModeStep = 1 };
@@ -104,6 +105,9 @@ struct SwarmParams {
   unsigned long long* gword;  // R x 3 x G group best keys
   RunCounter* counter;        // R
   float* crows;               // R x 2 x M x (D + 4): candidate row, its Q, padding
+  unsigned long long* grec;   // R x kRecDepth x G group records (cluster form)
+  int spec;                   // cluster form: X, V double-buffered (Auto Truncation decided one iteration late)
+  int cta_grid;               // CTAs per run of the grid-wide form (its barrier counts C * iterations)
 };
 
 // ---------------------------------------------------------------------------
@@ -230,6 +234,63 @@ __device__ __forceinline__ bool counter_wait_bounded(const unsigned int* ctr, un
 
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+// ---------------------------------------------------------------------------
+// Cluster form of the exchange: the CTAs of one group form a thread-block
+// cluster and trade their candidates through distributed shared memory; the
+// groups of a run trade only (Gfit, Q) records through global memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Address of the same shared-memory location in CTA `rank` of this cluster.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_peer_u64(uint32_t addr, unsigned long long v) {
+  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_peer_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_peer_f32(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+// Every thread of every CTA of the cluster: the release orders this thread's
+// earlier shared-memory stores (local and remote) before the arrival, the acquire
+// makes the other CTAs' stores visible after the wait.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// A group's record of one iteration, one 64-bit word (single-copy atomic, so it
+// needs no fence): Gfit bits << 32 | Q << 12 | tag.  Q < 2^20 always holds
+// ((T + 1) * O <= 65 * 8192); the tag (iteration mod 4095) + 1 is never 0, so a
+// zeroed ring holds no valid record.
+constexpr int kRecDepth = 4;  // ring slots per group; groups of a run are at most one iteration apart
+__device__ __forceinline__ uint32_t rec_tag(unsigned long long gk) { return (uint32_t)(gk % 4095ull) + 1u; }
+__device__ __forceinline__ unsigned long long make_rec(float fit, int q, unsigned long long gk) {
+  return ((unsigned long long)__float_as_uint(fit) << 32) | ((unsigned long long)((uint32_t)q & 0xfffffu) << 12) |
+         rec_tag(gk);
+}
+__device__ __forceinline__ float rec_fit(unsigned long long v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ int rec_q(unsigned long long v) { return (int)(((uint32_t)v >> 12) & 0xfffffu); }
+__device__ __forceinline__ uint32_t rec_tag_of(unsigned long long v) { return (uint32_t)v & 0xfffu; }
 
 // ---------------------------------------------------------------------------
 // Segment-circle test (Eq. penalty's Q for circular obstacles).

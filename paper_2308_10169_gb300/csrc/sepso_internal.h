@@ -18,6 +18,15 @@ struct SmemLayout {
   __host__ __device__ static SmemLayout make(int Omax, int ppc, int D, int T, int G, int tw);
 };
 
+// Shared-memory carve of swarm_cluster_kernel: the rows of swarm_kernel (X and V
+// twice when spec), the CTA's F / Q of the current evaluation, and the cluster
+// exchange slots (two parities x S ranks: best key, decision word, candidate row
+// with its Q).
+struct ClusterLayout {
+  int pairs, win, X0, X1, V0, V1, P, R, Gown, Pfit, PQ, Q, Len, F, FQ, Imp, rec, xkey, xdec, xrow, total;
+  __host__ __device__ static ClusterLayout make(int Omax, int ppc, int D, int T, int G, int tw, int S, int spec);
+};
+
 struct EvalParams {
   int T, D, n, per_cta, split, O, Omax;
   float alpha;
@@ -47,6 +56,10 @@ struct HsefParams {
 cudaError_t configure_swarm_kernel(size_t smem_bytes);
 cudaError_t swarm_occupancy(int threads, size_t smem_bytes, int* blocks_per_sm);
 cudaError_t launch_swarm(const SwarmParams& p, int grid, int threads, size_t smem, cudaStream_t s);
+// The cluster form: clusters of p.cpg CTAs, one per (run, group).
+cudaError_t configure_cluster_kernel(size_t smem_bytes);
+cudaError_t cluster_max_active(int S, int threads, size_t smem_bytes, int* clusters);
+cudaError_t launch_swarm_cluster(const SwarmParams& p, int grid, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_evaluate(const EvalParams& p, cudaStream_t s);
 cudaError_t launch_advance(float4* circ, float2* cvel, float* pts, float4* pairs, int O, float W, float H,
                            int steps, cudaStream_t s);

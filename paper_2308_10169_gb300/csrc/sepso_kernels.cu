@@ -576,6 +576,597 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// Cluster form of the fused iteration, for swarms in which no group's update uses
+// Tbest (C3 = 0 in every group, as in the sampled and HSEF-evolved settings): Eq.
+// TOF_V then needs only the group's own Gbest, so the exchange that gates each
+// update can stay inside the group.  Run r, group g owns one thread-block cluster
+// of S = p.cpg CTAs (cluster rank q owns particles [q ppc, q ppc + ppc)).  Per
+// iteration k:
+//   1. fitness of X^k; the Pbest test is kept aside (F, Q, improved?), P is not
+//      written yet;
+//   2. warp 0 reads the G group records of iteration k - 1 (each group's Gfit and
+//      Q after its best update, published one iteration earlier), updates Tbest
+//      with them and takes the Auto Truncation decision of k - 1, as Algorithm 1
+//      takes it right after that best update;
+//   3. each CTA writes its best candidate key (the lowest-index particle of lowest
+//      post-update Pbest fitness below the group's Gfit), its decision word and
+//      the candidate's row into its slot in every CTA of the cluster (distributed
+//      shared memory), then the cluster barrier;
+//   4. the decision is the largest word of the cluster (0 go on, 1 stop at k - 1,
+//      2 failed), so every CTA takes it alike; on a stop at k - 1 iteration k is
+//      discarded: X and V of k - 1 are still in the other buffer, P and Gbest are
+//      untouched, and Tbest of k - 1 is the result (Algorithm 1 returns Tbest
+//      after the stopping iteration's best update and never applies its update);
+//   5. otherwise the Pbest updates are applied, the new Gbest is the lowest key of
+//      the cluster's slots (its row from the winner's slot), rank 0 publishes the
+//      group's record of k, and the update of Eqs. TOF_omega, TOF_V and TOF_X runs.
+// The iteration cap (or the step count) ends the loop after step 5; the groups
+// then meet once at the run's end counter, and CTA 0 of the run applies the last
+// records to Tbest and takes its row from the holder group's Gbest row.  The
+// decisions, bests and arithmetic are those of swarm_kernel, so both forms give
+// identical results.  Slots of parity k & 1 are rewritten at k + 2, after the
+// cluster barrier of k + 1, which every CTA reaches only after reading them.
+// ---------------------------------------------------------------------------
+__host__ __device__ ClusterLayout ClusterLayout::make(int Omax, int ppc, int D, int T, int G, int tw, int S,
+                                                      int spec) {
+  ClusterLayout s;
+  int off = 1024;
+  s.pairs = off;
+  off = align_up(off + pair_block_f4(Omax > 0 ? Omax : 1) * 16, 16);
+  s.win = off;
+  off = align_up(off + tw * 8, 16);
+  s.xkey = off;
+  off = align_up(off + 2 * S * 8, 16);
+  s.rec = off;
+  off = align_up(off + G * 8, 16);
+  s.X0 = off;
+  off = align_up(off + ppc * D * 4, 16);
+  s.X1 = s.X0;
+  if (spec) {
+    s.X1 = off;
+    off = align_up(off + ppc * D * 4, 16);
+  }
+  s.V0 = off;
+  off = align_up(off + ppc * D * 4, 16);
+  s.V1 = s.V0;
+  if (spec) {
+    s.V1 = off;
+    off = align_up(off + ppc * D * 4, 16);
+  }
+  s.P = off;
+  off = align_up(off + ppc * D * 4, 16);
+  s.R = off;
+  off = align_up(off + ppc * 16, 16);
+  s.Gown = off;
+  off = align_up(off + D * 4, 16);
+  s.xrow = off;
+  off = align_up(off + 2 * S * (D + 4) * 4, 16);
+  s.Pfit = off;
+  off += ppc * 4;
+  s.PQ = off;
+  off += ppc * 4;
+  s.Q = off;
+  off += ppc * 4;
+  s.F = off;
+  off += ppc * 4;
+  s.FQ = off;
+  off += ppc * 4;
+  s.Imp = off;
+  off += ppc * 4;
+  s.xdec = off;
+  off += 2 * S * 4;
+  s.Len = off;
+  off += ppc * (T + 1) * 4;
+  s.total = align_up(off, 16);
+  return s;
+}
+
+// Tbest from the G group records held by lanes 0..G-1 of warp 0 (strictly better,
+// lowest group first), then Auto Truncation of that iteration; returns the stop
+// decision.  Every lane ends with the same values.
+__device__ __forceinline__ bool cluster_tbest_at(const SwarmParams& p, unsigned long long rec, int lane, float& Tfit,
+                                                 int& TQ, int& tholder, double* sWin, int& win_n, int& win_head,
+                                                 int& stall, float& prev_lfv) {
+  const bool has = lane < p.G;
+  const float f = has ? rec_fit(rec) : INFINITY;
+  // lowest (fitness, group): fitness values are non-negative, their bits order like them
+  unsigned long long key = has ? (((unsigned long long)__float_as_uint(f) << 32) | (unsigned)lane) : ~0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+    key = other < key ? other : key;
+  }
+  const int tg = (int)(key & 0xffffffffu);
+  const float tb = __uint_as_float((uint32_t)(key >> 32));
+  const int tq = __shfl_sync(0xffffffffu, has ? rec_q(rec) : 0, tg & 31);
+  if (tb < Tfit) {
+    Tfit = tb;
+    TQ = tq;
+    tholder = tg;
+  }
+  bool stop = false;
+  if (p.mode == kModePlan) {
+    if (p.at_mode == SEPSO_AT_STD_WINDOW) {
+      if (lane == 0) sWin[win_head] = (double)Tfit;
+      __syncwarp();
+      win_head = (win_head + 1) % p.tw;
+      if (win_n < p.tw) ++win_n;
+      if (win_n >= 2 && TQ == 0 && window_std_below(sWin, p.tw, win_n, win_head, p.delta, lane)) stop = true;
+    } else if (p.at_mode == SEPSO_AT_STALL) {
+      if (Tfit < prev_lfv - p.stall_tol) stall = 0;
+      else ++stall;
+      prev_lfv = Tfit;
+      if (stall >= p.stall_iters && TQ == 0) stop = true;
+    }
+  }
+  return stop;
+}
+
+// Lanes 0..G-1 of warp 0: the records of iteration gk (prefetched in rec), waited
+// for with the time limit; true when one did not come.
+__device__ __forceinline__ bool cluster_wait_records(const unsigned long long* slot, int lane, int G,
+                                                     unsigned long long gk, unsigned long long& rec) {
+  int late = 0;
+  if (lane < G) {
+    const uint32_t want = rec_tag(gk);
+    if (rec_tag_of(rec) != want) {
+      const unsigned long long t0 = global_ns();
+      do {
+        rec = ld_relaxed_u64(slot + lane);
+      } while (rec_tag_of(rec) != want && global_ns() - t0 <= kWaitLimitNs);
+      late = rec_tag_of(rec) != want;
+    }
+  }
+  return __any_sync(0xffffffffu, late) != 0;
+}
+
+__global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t s_mbar;
+  __shared__ unsigned long long s_key;
+  __shared__ uint32_t s_dec;
+
+  const int S = p.cpg;
+  const ClusterLayout L = ClusterLayout::make(p.Omax, p.ppc, p.D, p.T, p.G, p.tw, S, p.spec);
+  float4* sPairs = reinterpret_cast<float4*>(smem + L.pairs);
+  double* sWin = reinterpret_cast<double*>(smem + L.win);
+  unsigned long long* sXkey = reinterpret_cast<unsigned long long*>(smem + L.xkey);
+  uint32_t* sXdec = reinterpret_cast<uint32_t*>(smem + L.xdec);
+  float* sXrow = reinterpret_cast<float*>(smem + L.xrow);
+  float* sX0 = reinterpret_cast<float*>(smem + L.X0);
+  float* sX1 = reinterpret_cast<float*>(smem + L.X1);
+  float* sV0 = reinterpret_cast<float*>(smem + L.V0);
+  float* sV1 = reinterpret_cast<float*>(smem + L.V1);
+  float* sP = reinterpret_cast<float*>(smem + L.P);
+  float* sR = reinterpret_cast<float*>(smem + L.R);
+  float* sG = reinterpret_cast<float*>(smem + L.Gown);
+  float* sPfit = reinterpret_cast<float*>(smem + L.Pfit);
+  int* sPQ = reinterpret_cast<int*>(smem + L.PQ);
+  int* sQi = reinterpret_cast<int*>(smem + L.Q);
+  float* sF = reinterpret_cast<float*>(smem + L.F);
+  int* sFQ = reinterpret_cast<int*>(smem + L.FQ);
+  int* sImp = reinterpret_cast<int*>(smem + L.Imp);
+  float* sLen = reinterpret_cast<float*>(smem + L.Len);
+
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  const int T = p.T, D = p.D, G = p.G, N = p.N;
+  const int b = blockIdx.x;
+  const int r = b / p.C;
+  const int cr = b - r * p.C;
+  const int g = cr / S;
+  const uint32_t q = cluster_rank();  // = cr - g * S: a cluster is S consecutive blocks
+  const int n0 = (int)q * p.ppc;
+  const int nl = max(0, min(p.ppc, N - n0));
+  RunCtl* ctl = p.ctl + r;
+
+  const float* hy = p.hyper + ((size_t)r * G + g) * 6;
+  const float c1 = hy[0], c2 = hy[1], w_init = hy[3], w_end = hy[4], vlim = hy[5];
+  const float sx = p.pts[0], sy = p.pts[1], tx = p.pts[2], ty = p.pts[3];
+  const uint32_t cycle = (uint32_t)ctl->cycle;
+  const uint32_t run = ctl->run_id;
+  // read before any group arrives at the end counter (the last arrival's reader
+  // advances it only after all arrivals)
+  const int nfin = ctl->fin_launches;
+
+  if (tid == 0) {
+    mbar_init(&s_mbar, 1);
+    s_key = kKeyEmpty;
+  }
+  __syncthreads();
+  if (tid == 0 && p.O > 0) {
+    const uint32_t bytes = (uint32_t)pair_block_f4(p.O) * 16u;
+    mbar_expect_tx(&s_mbar, bytes);
+    bulk_g2s(sPairs, p.pairs, bytes, &s_mbar);
+  }
+
+  float* gX = p.X + ((size_t)r * p.M + (size_t)g * N + n0) * D;
+  float* gV = p.V + ((size_t)r * p.M + (size_t)g * N + n0) * D;
+  float* gP = p.P + ((size_t)r * p.M + (size_t)g * N + n0) * D;
+  float* gPfit = p.Pfit + (size_t)r * p.M + (size_t)g * N + n0;
+  int32_t* gPQ = p.PQ + (size_t)r * p.M + (size_t)g * N + n0;
+  float* gGb = p.Gb + (size_t)r * G * D;
+  float* gTb = p.Tb + (size_t)r * D;
+  unsigned long long* grec = p.grec + (size_t)r * kRecDepth * G;
+
+  float Tfit, gfit;
+  int TQ, k, gq;
+  int tholder = -1;  // group whose Gbest row is Tbest's; -1: the row already in gTb
+  int win_n = 0, win_head = 0, stall = 0;
+  float prev_lfv = INFINITY;
+
+  if (p.mode == kModePlan) {
+    // Initialisation (Algorithm 1) with Priori Initialization (Sec. 3.3.3).
+    const int n_pi = (p.use_pi && ctl->has_prev) ? p.n_pi : 0;
+    const float* prevT = p.prevT + (size_t)r * D;
+    const int nch = (D + 3) >> 2;
+    for (int it = tid; it < nl * nch; it += nt) {
+      const int i = it / nch, ch = it - i * nch;
+      const int n = n0 + i;
+      const uint32_t pid = (uint32_t)(g * N + n);
+      const bool pi = n < n_pi;
+      const uint4 ux = draw(p.key0, p.key1, (uint32_t)ch, pid, pi ? kStreamPI : kStreamInitX, cycle, run);
+      const uint4 uv = draw(p.key0, p.key1, (uint32_t)ch, pid, kStreamInitV, cycle, run);
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const int j = ch * 4 + l;
+        if (j < D) {
+          const float ext = (j < T) ? p.W : p.H;
+          float x;
+          if (pi) x = fminf(fmaxf(prevT[j] + (2.0f * lane_of(ux, l) - 1.0f) * p.pi_h, 0.0f), ext);
+          else x = lane_of(ux, l) * ext;
+          sX0[i * D + j] = x;
+          sP[i * D + j] = x;
+          sV0[i * D + j] = (2.0f * lane_of(uv, l) - 1.0f) * (vlim * ext);
+        }
+      }
+    }
+    for (int i = tid; i < nl; i += nt) {
+      sPfit[i] = INFINITY;
+      sPQ[i] = 0;
+    }
+    for (int j = tid; j < D; j += nt) {
+      sG[j] = 0.0f;
+      if (q == 0) gGb[g * D + j] = 0.0f;
+      if (cr == 0) gTb[j] = 0.0f;
+    }
+    Tfit = INFINITY;
+    TQ = 0;
+    k = 0;
+    gfit = INFINITY;
+    gq = 0;
+    if (tid < 32 && p.at_mode == SEPSO_AT_STD_WINDOW && cycle != 0) {
+      win_n = ctl->win_n;
+      win_head = ctl->win_head;
+      for (int i = lane; i < p.tw; i += 32) sWin[i] = p.win[(size_t)r * p.tw + i];
+    }
+  } else {
+    for (int it = tid; it < nl * D; it += nt) {
+      sX0[it] = gX[it];
+      sV0[it] = gV[it];
+      sP[it] = gP[it];
+    }
+    for (int i = tid; i < nl; i += nt) {
+      sPfit[i] = gPfit[i];
+      sPQ[i] = gPQ[i];
+    }
+    for (int j = tid; j < D; j += nt) sG[j] = gGb[g * D + j];
+    gfit = p.Gfit[(size_t)r * G + g];
+    gq = p.GQ[(size_t)r * G + g];
+    Tfit = ctl->Tfit;
+    TQ = ctl->TQ;
+    k = ctl->k;
+  }
+
+  bool failed = false;
+  const int K = circle_pairs(p.O);
+  if (p.O > 0) {
+    const bool landed = mbar_wait_bounded(&s_mbar, 0, kWaitLimitNs);
+    if (__syncthreads_or(landed ? 0 : 1)) {
+      failed = true;
+      if (tid == 0) {
+        ctl->status = SEPSO_ETIMEOUT;
+        mbar_wait_bounded(&s_mbar, 0, kWaitLimitNs);  // once more: no copy in flight at exit
+      }
+    }
+  } else {
+    __syncthreads();
+  }
+  const float2* sNr2 = reinterpret_cast<const float2*>(sPairs + K);
+  for (int i = tid; i < nl; i += nt) sQi[i] = 0;
+
+  const unsigned long long kbase = (unsigned long long)ctl->iters_total;
+  // Every CTA of the cluster has started before any remote store; a failed copy
+  // in any of them stops the whole cluster (the slots of parity kbase & 1 are
+  // free until iteration kbase + 2).
+  cluster_barrier();
+  const int p0 = (int)(kbase & 1ull);
+  if (tid < S) st_peer_u32(peer_addr(sXdec + p0 * S + q, (uint32_t)tid), failed ? 2u : 0u);
+  cluster_barrier();
+  {
+    uint32_t any = 0;
+    for (int s2 = 0; s2 < S; ++s2) any |= sXdec[p0 * S + s2];
+    failed = any != 0;
+  }
+
+  const int nseg = T + 1;
+  int done = 0, xb = 0;
+  bool capstop = false;
+  unsigned long long gk_last = kbase;
+  while (!failed) {
+    if (p.mode == kModeStep && done >= p.step_iters) break;
+    ++k;
+    ++done;
+    const unsigned long long gk = kbase + (unsigned long long)done;
+    const int par = (int)(gk & 1ull);
+    float* cX = xb ? sX1 : sX0;
+    float* cV = xb ? sV1 : sV0;
+    const bool have_prev = done > 1;
+    const unsigned long long* prev_slot = grec + (size_t)((gk - 1ull) % (unsigned long long)kRecDepth) * G;
+    unsigned long long rec = 0;
+    if (have_prev && tid < G) rec = ld_relaxed_u64(prev_slot + tid);  // in flight during the fitness
+    for (int i = nt - 1 - tid; i < nl; i += nt) {
+      const uint4 o = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)(g * N + n0 + i), kStreamVel, cycle, run);
+      sR[i * 4 + 0] = c1 * u01(o.x);
+      sR[i * 4 + 1] = c2 * u01(o.y);
+    }
+
+    // 1. Fitness F(X^k) and the Pbest test, kept aside.
+    if (p.items) {
+      fitness_items_pairs(cX, nl, T, D, sx, sy, tx, ty, sPairs, sNr2, K, p.split, sQi, sLen);
+      __syncthreads();
+    }
+    {
+      const int lp = p.items ? 32 : p.lp;
+      const int ppw = 32 / lp;
+      const int lsub = lane & (lp - 1);
+      for (int i0 = warp * ppw; i0 < nl; i0 += nwarps * ppw) {
+        const int i = i0 + lane / lp;
+        const bool live = i < nl;
+        float len = 0.0f;
+        int qq = 0;
+        if (p.items) {
+          if (live && lsub == 0) {
+            for (int sg = 0; sg < nseg; ++sg) len += sLen[i * nseg + sg];
+            qq = sQi[i];
+            sQi[i] = 0;
+          }
+        } else {
+          group_fitness_pairs(cX + (live ? i : 0) * D, live, lp, T, p.split, K, sx, sy, tx, ty, sPairs, sNr2,
+                              &len, &qq);
+        }
+        if (live && lsub == 0) {
+          const float F = len + p.alpha * powi((float)qq, p.beta);
+          const float pf = sPfit[i];
+          const int imp = F < pf;
+          const float cf = imp ? F : pf;
+          const int cq = imp ? qq : sPQ[i];
+          sF[i] = F;
+          sFQ[i] = qq;
+          sImp[i] = imp;
+          if (cf < gfit) atomicMin(&s_key, best_key(cf, (uint32_t)(n0 + i), (uint32_t)cq));
+        }
+      }
+    }
+    // 2. Tbest and Auto Truncation of iteration k - 1 from the groups' records.
+    if (warp == 0) {
+      uint32_t dec = 0;
+      if (have_prev) {
+        const bool late = cluster_wait_records(prev_slot, lane, G, gk - 1ull, rec);
+        if (late) {
+          dec = 2;
+        } else if (cluster_tbest_at(p, rec, lane, Tfit, TQ, tholder, sWin, win_n, win_head, stall, prev_lfv)) {
+          dec = 1;
+        }
+      }
+      if (lane == 0) s_dec = dec;
+    }
+    __syncthreads();
+
+    // 3. Candidate key, decision word and candidate row into every CTA's slot.
+    const unsigned long long lkey = s_key;
+    const uint32_t mydec = s_dec;
+    if (tid < S) {
+      st_peer_u64(peer_addr(sXkey + par * S + q, (uint32_t)tid), lkey);
+      st_peer_u32(peer_addr(sXdec + par * S + q, (uint32_t)tid), mydec);
+    }
+    if (lkey != kKeyEmpty) {
+      const int iw = key_idx(lkey) - n0;
+      const bool wimp = sImp[iw] != 0;
+      const float* src = wimp ? cX + iw * D : sP + iw * D;
+      const int qx = wimp ? sFQ[iw] : sPQ[iw];
+      float* slot = sXrow + (par * S + q) * (D + 4);
+      for (int t = tid; t < S * (D + 1); t += nt) {
+        const int peer = t / (D + 1), j = t - peer * (D + 1);
+        st_peer_f32(peer_addr(slot + j, (uint32_t)peer), j < D ? src[j] : __int_as_float(qx));
+      }
+    }
+    cluster_barrier();
+    if (tid == 0) s_key = kKeyEmpty;
+
+    // 4. The cluster's decision.
+    uint32_t cdec = 0;
+    for (int s2 = 0; s2 < S; ++s2) cdec = max(cdec, sXdec[par * S + s2]);
+    if (cdec >= 2) {
+      failed = true;
+      if (tid == 0) ctl->status = SEPSO_ETIMEOUT;
+      break;
+    }
+    if (cdec == 1) {  // stop at k - 1: discard iteration k
+      if (p.spec) xb ^= 1;
+      --k;
+      --done;
+      break;
+    }
+
+    // 5. Pbest, the group's Gbest, its record; then the update.
+    for (int it = tid; it < nl * D; it += nt) {
+      const int i = it / D;
+      if (sImp[i]) sP[it] = cX[it];
+    }
+    for (int i = tid; i < nl; i += nt) {
+      if (sImp[i]) {
+        sPfit[i] = sF[i];
+        sPQ[i] = sFQ[i];
+      }
+    }
+    unsigned long long gkey = kKeyEmpty;
+    int gw = 0;
+    for (int s2 = 0; s2 < S; ++s2) {
+      const unsigned long long kk = sXkey[par * S + s2];
+      if (kk < gkey) {
+        gkey = kk;
+        gw = s2;
+      }
+    }
+    const float* grow = sG;  // this iteration's Gbest row
+    const bool gimp = gkey != kKeyEmpty && key_fit(gkey) < gfit;
+    if (gimp) {
+      grow = sXrow + (par * S + gw) * (D + 4);
+      gfit = key_fit(gkey);
+      gq = __float_as_int(grow[D]);
+    }
+    if (q == 0) {
+      if (gimp)
+        for (int j = tid; j < D; j += nt) gGb[g * D + j] = grow[j];
+      if (tid == 0) st_relaxed_u64(grec + (size_t)(gk % (unsigned long long)kRecDepth) * G + g, make_rec(gfit, gq, gk));
+    }
+    gk_last = gk;
+    if (p.mode == kModePlan && k >= p.max_iters) {  // the cap: Algorithm 1 stops before the update
+      capstop = true;
+      break;
+    }
+
+    // Eq. TOF_omega, Eq. TOF_V (+ clip to V_range), Eq. TOF_X (+ clip to X_range).
+    float* nX = p.spec ? (xb ? sX0 : sX1) : cX;
+    float* nV = p.spec ? (xb ? sV0 : sV1) : cV;
+    const float w = w_init - (w_init - w_end) / (float)p.max_iters * (float)k;
+    for (int it = tid; it < nl * D; it += nt) {
+      const int i = it / D;
+      const int j = it - i * D;
+      const float x = cX[it];
+      float v = w * cV[it];
+      v = fmaf(sR[i * 4 + 0], sP[it] - x, v);
+      v = fmaf(sR[i * 4 + 1], grow[j] - x, v);
+      const float ext = (j < T) ? p.W : p.H;
+      const float vmax = vlim * ext;
+      v = fminf(fmaxf(v, -vmax), vmax);
+      nV[it] = v;
+      nX[it] = fminf(fmaxf(x + v, 0.0f), ext);
+    }
+    if (p.spec) xb ^= 1;
+    if (gimp) {
+      __syncthreads();  // every thread has read grow from the slot
+      for (int j = tid; j < D; j += nt) sG[j] = grow[j];
+    }
+    __syncthreads();
+    if (p.mode == kModeStep && done >= p.step_iters) {  // a plain continuation ends after the update
+      capstop = true;
+      break;
+    }
+  }
+
+  // Write back the swarm (state for sepso_step / sepso_get_state).
+  {
+    const float* fX = xb ? sX1 : sX0;
+    const float* fV = xb ? sV1 : sV0;
+    for (int it = tid; it < nl * D; it += nt) {
+      gX[it] = fX[it];
+      gV[it] = fV[it];
+      gP[it] = sP[it];
+    }
+  }
+  for (int i = tid; i < nl; i += nt) {
+    gPfit[i] = sPfit[i];
+    gPQ[i] = sPQ[i];
+  }
+  if (q == 0 && tid == 0) {
+    p.Gfit[(size_t)r * G + g] = gfit;
+    p.GQ[(size_t)r * G + g] = gq;
+  }
+  __syncthreads();
+  cluster_barrier();  // no shared-memory access between the CTAs after this point
+  if (q == 0 && tid == 0) red_release_add(&p.counter[r].fin, 1u);
+  if (cr != 0) return;
+
+  // CTA 0 of the run: every group has written its rows and last record.
+  int timed_out = 0;
+  if (tid == 0) {
+    timed_out = counter_wait_bounded(&p.counter[r].fin, (unsigned int)G * (unsigned int)(nfin + 1), kWaitLimitNs)
+                    ? 0
+                    : 1;
+    fence_acq_rel_gpu();
+  }
+  if (__syncthreads_or(timed_out)) {
+    failed = true;
+    if (tid == 0) ctl->status = SEPSO_ETIMEOUT;
+  }
+  if (!failed && capstop && warp == 0) {
+    // the records of the last iteration (the loop ended after publishing them)
+    unsigned long long rec = lane < G ? ld_relaxed_u64(grec + (size_t)(gk_last % (unsigned long long)kRecDepth) * G + lane) : 0ull;
+    if (cluster_wait_records(grec + (size_t)(gk_last % (unsigned long long)kRecDepth) * G, lane, G, gk_last, rec)) {
+      if (lane == 0) ctl->status = SEPSO_ETIMEOUT;
+    } else {
+      cluster_tbest_at(p, rec, lane, Tfit, TQ, tholder, sWin, win_n, win_head, stall, prev_lfv);
+    }
+  }
+  if (tid == 0) s_dec = (uint32_t)(tholder + 1);  // Tbest is tracked by warp 0 alone
+  __syncthreads();
+  // Tbest's row: the holder group's Gbest row (which changes only together with
+  // Tbest), staged in the exchange slots (free after the last cluster barrier).
+  float* sTrow = sXrow;
+  const int holder = (int)s_dec - 1;
+  const float* src = (holder >= 0) ? gGb + (size_t)holder * D : gTb;
+  for (int j = tid; j < D; j += nt) sTrow[j] = __ldcg(src + j);
+  __syncthreads();
+  for (int j = tid; j < D; j += nt) {
+    gTb[j] = sTrow[j];
+    if (p.mode == kModePlan) {
+      p.res_wp[(size_t)r * D + j] = sTrow[j];
+      p.prevT[(size_t)r * D + j] = sTrow[j];
+    }
+  }
+  for (int j = tid; j < 3 * G; j += nt) p.gword[(size_t)r * 3 * G + j] = kKeyEmpty;
+  if (tid == 0) {
+    // the grid-wide form's barrier counts C per iteration of the run, and expects
+    // its group words empty: keep both as if it had run these iterations
+    atomicAdd(&p.counter[r].count, (unsigned int)p.cta_grid * (unsigned int)done);
+    ctl->Tfit = Tfit;
+    ctl->TQ = TQ;
+    ctl->k = k;
+    ctl->iters_total += done;
+    ctl->fin_launches = nfin + 1;
+    if (p.mode == kModePlan) {
+      ctl->plans_total += 1;
+      float len = 0.0f;
+      for (int s = 0; s < nseg; ++s) {
+        const float ax = (s == 0) ? sx : sTrow[s - 1];
+        const float ay = (s == 0) ? sy : sTrow[T + s - 1];
+        const float bx = (s == T) ? tx : sTrow[s];
+        const float by = (s == T) ? ty : sTrow[T + s];
+        const float dx = bx - ax, dy = by - ay;
+        len += sqrtf(fmaf(dx, dx, dy * dy));
+      }
+      sepso_result* res = p.res + r;
+      res->cost = Tfit;
+      res->length = len;
+      res->Q = TQ;
+      res->iters = k;
+      res->status = failed ? SEPSO_ETIMEOUT : ctl->status;
+      ctl->has_prev = 1;
+      ctl->cycle = (int32_t)cycle + 1;
+      ctl->stall = stall;
+      ctl->prev_lfv = prev_lfv;
+      if (p.at_mode == SEPSO_AT_STD_WINDOW) {
+        ctl->win_n = win_n;
+        ctl->win_head = win_head;
+        for (int i = 0; i < p.tw; ++i) p.win[(size_t)r * p.tw + i] = sWin[i];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Fitness of a batch of paths.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) evaluate_kernel(const EvalParams p) {
@@ -812,6 +1403,44 @@ cudaError_t swarm_occupancy(int threads, size_t smem_bytes, int* blocks_per_sm) 
 cudaError_t launch_swarm(const SwarmParams& p, int grid, int threads, size_t smem, cudaStream_t s) {
   void* args[] = {const_cast<SwarmParams*>(&p)};
   return cudaLaunchCooperativeKernel((const void*)swarm_kernel, dim3(grid), dim3(threads), args, smem, s);
+}
+
+cudaError_t configure_cluster_kernel(size_t smem_bytes) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, swarm_cluster_kernel);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(swarm_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(smem_bytes - a.sharedSizeBytes));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(swarm_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+static cudaLaunchConfig_t cluster_config(int S, int grid, int threads, size_t smem, cudaStream_t s,
+                                         cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)S;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+cudaError_t cluster_max_active(int S, int threads, size_t smem_bytes, int* clusters) {
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cluster_config(S, S, threads, smem_bytes, nullptr, attr);
+  return cudaOccupancyMaxActiveClusters(clusters, (void*)swarm_cluster_kernel, &cfg);
+}
+
+cudaError_t launch_swarm_cluster(const SwarmParams& p, int grid, int threads, size_t smem, cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  const cudaLaunchConfig_t cfg = cluster_config(p.cpg, grid, threads, smem, s, attr);
+  return cudaLaunchKernelEx(&cfg, swarm_cluster_kernel, p);
 }
 
 cudaError_t launch_evaluate(const EvalParams& p, cudaStream_t s) {

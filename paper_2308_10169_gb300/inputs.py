@@ -65,6 +65,7 @@ class SepsoConfig:
     threads: int = 0           # 0 = automatic
     circle_split: int = 0      # 0 = automatic
     fitness_mode: int = 0      # 0 = automatic; 1 lane group per particle; 2 items over the CTA
+    exchange: int = 0          # 0 = automatic; 1 grid-wide barrier; 2 one cluster per group (C3 = 0)
 
     @property
     def D(self) -> int:

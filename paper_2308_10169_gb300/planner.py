@@ -233,6 +233,14 @@ class Planner:
         check(self.lib.sepso_launch_shape(self._h, *[ctypes.byref(x) for x in v]))
         return dict(zip(("ctas_per_group", "threads", "circle_split", "grid"), [x.value for x in v]))
 
+    def exchange_form(self) -> str:
+        """"cluster" when the next plan runs one thread-block cluster per group,
+        "grid" for the grid-wide barrier."""
+        v = int(self.lib.sepso_exchange_form(self._h))
+        if v < 0:
+            check(v)
+        return "cluster" if v == 2 else "grid"
+
     def counters(self, run: int = 0) -> tuple[int, int]:
         """(planning cycles finished, iterations run) of one run, cumulative."""
         p, i = ctypes.c_int64(), ctypes.c_int64()

@@ -9,6 +9,8 @@ import textwrap
 from pathlib import Path
 
 ROOT = Path(__file__).resolve().parents[1]
+if str(ROOT) not in sys.path:
+    sys.path.insert(0, str(ROOT))
 
 
 def _port() -> int:
@@ -48,11 +50,16 @@ def test_timing_is_the_slowest_rank_and_value_counts_all_ranks(tmp_path):
 
 
 def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
-    out = _torchrun(["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0",
-                     "--ref-seconds", "1"], cwd=ROOT)
+    out = _torchrun(["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "1"],
+                    cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "plans/s"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # the same counts and configuration object as the GPU arm's line
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["cycles"] == 2
+    import bench
+    assert d["config"] == bench.run_config(2, 2)
+    assert d["cpu_baseline"]["cores"] == min(bench.host_cores(), 2)
