@@ -113,9 +113,10 @@ def parse():
     ap.add_argument("--prior-rounds", type=int, default=3)
     ap.add_argument("--prior-epochs", type=int, default=30)
     ap.add_argument("--prior-batch", type=int, default=4096, help="rows per Adam step")
-    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper,bf,poly",
-                    help="comma list of main, cpu, batch, prior, serve, paper, bf, poly, gemm (paper: "
-                         "the ablation variants of the path-planning comparison; bf: the benchmark "
+    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper,boxes,bf,poly",
+                    help="comma list of main, cpu, batch, prior, serve, paper, boxes, bf, poly, gemm (paper: "
+                         "the ablation variants of the path-planning comparison; boxes: the same among "
+                         "moving bounding boxes; bf: the benchmark "
                          "functions; poly: planning among polygon obstacles; gemm: the tensor-core "
                          "GEMM alone)")
     ap.add_argument("--bf-fns", type=str, default="1,2,3,4", help="benchmark functions (1..4) of section bf")
@@ -622,6 +623,83 @@ def run_paper(frames: int = 100, seed: int = 0):
             "variants": out}
 
 
+def run_paper_boxes(frames: int = 100, seed: int = 0, oracle_keys: int = 2, oracle_frames: int = 25):
+    """Table ppresult's comparison with the paper's own map model: the same variants
+    among 8 moving and static bounding boxes (Q = path-segment / box-edge crossings),
+    timed as ``run_paper``; beside each variant the FP64 oracle on the first
+    ``oracle_frames`` frames under ``oracle_keys`` Philox keys (means compared)."""
+    import torch
+
+    import oracle
+    from paper_2308_10169_gb300 import Planner
+    from paper_2308_10169_gb300.inputs import PAPER_VARIANTS, paper_box_workload
+    paper = {"SEPSO": (412.0, 0.015, 12.9), "SEPSO(NoAT)": (408.3, 0.036, 30.0),
+             "SEPSO(NoPI)": (415.8, 0.033, 26.8), "DTPSO": (413.9, 0.036, 30.0)}
+    out = {}
+    for var in PAPER_VARIANTS:
+        cfg, scene, hyper = paper_box_workload(seed, var)
+        warm = Planner(cfg)
+        warm.set_hyper(hyper)
+        warm.set_polygons(scene)
+        for _ in range(3):
+            warm.plan()
+        del warm
+        pl = Planner(cfg)
+        pl.set_hyper(hyper)
+        pl.set_polygons(scene)
+        stream = torch.cuda.current_stream()
+        l0 = pl.launch_count()
+        ms, L, I, Q = [], [], [], []
+        torch.cuda.synchronize()
+        for f in range(frames):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if f:
+                pl.advance(1)
+            pl.plan_async()
+            b.record(stream)
+            r = pl.read_result()
+            ms.append(a.elapsed_time(b))
+            L.append(r["length"]); I.append(r["iters"]); Q.append(r["Q"])
+        oL, oI, oQ, gL, gI, gQ = [], [], [], [], [], []
+        for key in range(oracle_keys):
+            c2 = cfg.with_(seed=1000 + key)
+            g2 = Planner(c2)
+            g2.set_hyper(hyper)
+            g2.set_polygons(scene)
+            sw = oracle.Swarm(c2, hyper)
+            e, v, st, sv, tg, tv = (scene.edges, scene.poly_vel, scene.start, scene.start_vel, scene.target,
+                                    scene.target_vel)
+            for f in range(oracle_frames):
+                if f:
+                    g2.advance(1)
+                    e, v, st, sv, tg, tv = oracle.advance_polygons(cfg.map_w, cfg.map_h, e, scene.offsets, v, st,
+                                                                   sv, tg, tv)
+                rg = g2.plan()
+                ro = sw.plan(oracle.Scene(st, tg, np.zeros((0, 3)), e))
+                gL.append(rg["length"]); gI.append(rg["iters"]); gQ.append(rg["Q"])
+                oL.append(ro["length"]); oI.append(ro["iters"]); oQ.append(ro["Q"])
+        out[var] = {"path_length": float(np.mean(L)), "ms_per_frame": float(np.mean(ms)),
+                    "iters_per_frame": float(np.mean(I)),
+                    "collision_free_frames": float(np.mean(np.array(Q) == 0)),
+                    "gpu_launches": pl.launch_count() - l0, "exchange": pl.exchange_form(),
+                    "vs_oracle": {"frames": len(oL), "gpu_path_length": float(np.mean(gL)),
+                                  "oracle_path_length": float(np.mean(oL)),
+                                  "gpu_iters_per_frame": float(np.mean(gI)),
+                                  "oracle_iters_per_frame": float(np.mean(oI)),
+                                  "gpu_collision_free": float(np.mean(np.array(gQ) == 0)),
+                                  "oracle_collision_free": float(np.mean(np.array(oQ) == 0))},
+                    "paper_context": {"path_length": paper[var][0], "s_per_frame": paper[var][1],
+                                      "iters_per_frame": paper[var][2],
+                                      "note": "RTX 2070 SUPER, the paper's own (unpublished) scene"}}
+    return {"workload": "366x366 map, 8 axis-aligned boxes with half-sizes U[15,30] (2 static, 6 moving "
+                        "|v|~U(0,5]/frame, bounding-box bounce), Q = path-segment / box-edge crossings, "
+                        "start/target moving 3 and 8 per frame vertically, T=8 (D=16), G=8 x N=170, alpha=30 "
+                        "beta=4, PI gamma=0.25, std-window AT TW=20 delta=10, cap 30 iterations per frame, "
+                        f"{frames} frames, seed {seed}",
+            "variants": out}
+
+
 def run_bf(fns, iters: int, trials: int, peak_gbs: float):
     """Benchmark functions (Table BFs): the large-scale runs of Sec. 4.1.2 (16K
     particles x 1K coordinates) and the standard runs of Sec. 4.1.1 (80 particles x
@@ -772,7 +850,9 @@ def run_serve(rate: float, seconds: float, n_agents: int = 2048):
     return {"offered_per_s": rate, "requests": len(arr), "plans_per_s": len(done) / span,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "iters_per_plan": float(np.mean([d["iters"] for d in done])),
-            "median_cost": float(np.median([d["cost"] for d in done])), "slots": st["slots"],
+            "median_cost": float(np.median([d["cost"] for d in done])),
+            "collision_free": float(np.mean([d["Q"] == 0 for d in done])),
+            "at_fire_rate": float(np.mean([d["iters"] < 100 for d in done])), "slots": st["slots"],
             "ticks": st["ticks"], "gpu_launches": st["launches"]}
 
 
@@ -787,7 +867,7 @@ def serve_single_scene(n: int = 256, n_agents: int = 2048):
     from paper_2308_10169_gb300 import Planner, Server
     from paper_2308_10169_gb300.inputs import AT_STALL, Scene, SepsoConfig, serving_workload
     agents = serving_workload(0, n_agents)[:n]
-    lat, costs, its = [], [], []
+    lat, costs, its, qs = [], [], [], []
     for a, ag in enumerate(agents):
         cfg = SepsoConfig(T=ag["T"], G=8, N=32, max_obstacles=256, alpha=30.0, beta=4, max_iters=100,
                           at_mode=AT_STALL, stall_iters=10, stall_tol=0.0, use_pi=True, pi_gamma=0.25,
@@ -807,6 +887,7 @@ def serve_single_scene(n: int = 256, n_agents: int = 2048):
         lat.append(time.perf_counter() - t)
         costs.append(float(r.cost))
         its.append(int(r.iters))
+        qs.append(int(r.Q))
     lat = np.array(lat) * 1e3
     sv = Server(n_agents=n_agents, max_slots=1024, G=8, N=32, Tmax=40, Omax=256, max_iters=100, stall_iters=10)
     for a, ag in enumerate(agents):
@@ -822,12 +903,14 @@ def serve_single_scene(n: int = 256, n_agents: int = 2048):
             "single_scene": {"plans_per_s": n / (lat.sum() / 1e3),
                              "latency_ms": {"p50": float(np.percentile(lat, 50)),
                                             "p99": float(np.percentile(lat, 99))},
-                             "median_cost": float(np.median(costs)), "iters_per_plan": float(np.mean(its))},
+                             "median_cost": float(np.median(costs)), "iters_per_plan": float(np.mean(its)),
+                             "collision_free": float(np.mean(np.array(qs) == 0))},
             "server_burst": {"plans_per_s": len(done) / span,
                              "latency_ms": {"p50": float(np.percentile(slat, 50)),
                                             "p99": float(np.percentile(slat, 99))},
                              "median_cost": float(np.median([d["cost"] for d in done])),
-                             "iters_per_plan": float(np.mean([d["iters"] for d in done]))}}
+                             "iters_per_plan": float(np.mean([d["iters"] for d in done])),
+                             "collision_free": float(np.mean([d["Q"] == 0 for d in done]))}}
 
 
 def run_prior(n_train: int, n_eval: int, rounds: int, epochs: int, single: dict, B: int = 4096):
@@ -1062,6 +1145,8 @@ def main():
                                       line, args.prior_batch)
         if world == 1 and "paper" in sections:
             line["paper_ablation"] = run_paper()
+        if world == 1 and "boxes" in sections:
+            line["paper_ablation_boxes"] = run_paper_boxes()
         if world == 1 and "poly" in sections:
             line["poly"] = run_poly()
         if world == 1 and "bf" in sections:
@@ -1071,7 +1156,8 @@ def main():
             line["gemm"] = run_gemm()
         if world == 1 and "serve" in sections and args.serve_rates:
             line["serve"] = {
-                "workload": "2048 agents, Poisson arrivals, T in {8,20,40}, O in {32,256} r~U[5,25], "
+                "workload": "2048 agents, Poisson arrivals, T in {8,20,40}, O in {32,256} circles, centres "
+                            "U[60,340]^2, r~U[5,25] x sqrt(32/O), "
                             "obstacles advanced per request, G=8 x N=32, PI warm start on the device, "
                             "AT stall 10 / cap 100, continuous batching (1024 slots)",
                 "runs": [run_serve(float(r), args.serve_seconds) for r in args.serve_rates.split(",")],

@@ -54,6 +54,12 @@ extern "C" {
                                    stall_iters iterations, and the best path
                                    collision-free                                    */
 
+/* Obstacle kinds (sepso_config.obstacle_kind). */
+#define SEPSO_OBST_CIRCLES 0    /* Q = (path segment, circle) pairs closer than r    */
+#define SEPSO_OBST_POLYGONS 1   /* Q = (path segment, polygon edge) pairs crossing
+                                   properly (Sec. 3.3.1's map model: bounding boxes
+                                   or outlines, Eq. penalty)                         */
+
 typedef struct sepso_ctx* sepso_handle;
 
 /* Fixed at sepso_create().  Fields follow Algorithm 1 and Tables params_path /
@@ -96,6 +102,9 @@ typedef struct {
                              iteration later (needs C3 = 0 in every group: Eq.
                              TOF_V then uses the own group's Gbest alone).  Both
                              forms give identical results.                        */
+  int32_t obstacle_kind;  /* SEPSO_OBST_*: circles (sepso_set_scene) or polygon
+                             edges (sepso_set_polygons); for polygons
+                             max_obstacles is the edge capacity                   */
 } sepso_config;
 
 /* Outcome of one planning cycle of one run. */
@@ -138,21 +147,42 @@ int sepso_set_hyper(sepso_handle h, int32_t run, const float* hyper);
 int sepso_set_scene(sepso_handle h, const float* start, const float* target,
                     const float* circles, int32_t O);
 
-/* Per-cycle velocities for the dynamic scene (host): circle_vel O x 2,
- * start_vel[2], target_vel[2].  Errors: EINVAL, ESTATE (no scene yet). */
+/* Per-cycle velocities for the dynamic scene (host): circle_vel O x 2 (for
+ * polygon obstacles: P x 2, one per polygon), start_vel[2], target_vel[2].
+ * Errors: EINVAL, ESTATE (no scene yet). */
 int sepso_set_motion(sepso_handle h, const float* circle_vel, const float* start_vel,
                      const float* target_vel);
 
 /* Advance the dynamic scene `steps` times on the device (async): every circle and
  * the start/target move by their velocity; a velocity component flips when the
- * disk crosses the border it moves towards (Fig. PP caption).
- * Errors: ESTATE, EINVAL (steps < 0). */
+ * disk crosses the border it moves towards (Fig. PP caption).  Polygon obstacles
+ * move rigidly (all edges of a polygon by its velocity) and bounce by their
+ * bounding box: a component flips when the box lies past the border it moves
+ * towards.  Errors: ESTATE, EINVAL (steps < 0). */
 int sepso_advance_scene(sepso_handle h, int32_t steps);
 
 /* Read the current scene back (host outputs, sync): start[2], target[2],
  * circles O x 3, circle_vel O x 2 (any output may be NULL). */
 int sepso_get_scene(sepso_handle h, float* start, float* target, float* circles,
                     float* circle_vel);
+
+/* Scene among polygon obstacles (Sec. 3.3.1: obstacles are bounding boxes or
+ * outlines given by their edges; Q of Eq. penalty counts the (path segment, edge)
+ * pairs that cross properly -- each segment's endpoints strictly on opposite
+ * sides of the other's line -- so touching and collinear contacts do not count,
+ * and a path wholly inside an obstacle crosses nothing).  Host inputs: start[2],
+ * target[2], edges E x 4 (x0, y0, x1, y1), 0 <= E <= max_obstacles; offsets
+ * P + 1 int32: polygon p owns edges [offsets[p], offsets[p+1]) (offsets[0] = 0,
+ * offsets[P] = E, non-decreasing), so that it moves as one body.  Polygon
+ * velocities are reset to zero (sepso_set_motion sets them, one per polygon).
+ * Only on a handle with obstacle_kind = SEPSO_OBST_POLYGONS.  Sync.
+ * Errors: EINVAL. */
+int sepso_set_polygons(sepso_handle h, const float* start, const float* target, const float* edges,
+                       int32_t E, const int32_t* offsets, int32_t P);
+
+/* Read a polygon scene back (host outputs, sync; any may be NULL): start[2],
+ * target[2], edges E x 4, polygon velocities P x 2.  Errors: EINVAL, ESTATE. */
+int sepso_get_polygons(sepso_handle h, float* start, float* target, float* edges, float* polygon_vel);
 
 /* ---- the hot path ------------------------------------------------------- */
 

@@ -148,6 +148,8 @@ def lib():
                               ctypes.POINTER(_State), ctypes.c_int32]
         L.so_advance_scene.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                                        _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+        L.so_advance_polygons.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int32, _i32p,
+                                          _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
         L.so_hsef.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene),
                               ctypes.POINTER(_HsefCfg), _f64p, _f64p, _f64p]
         L.so_hsef_state.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene),
@@ -188,7 +190,8 @@ def _cfg(c) -> _Config:
                    at_mode=c.at_mode, tw=c.tw, delta=float(np.float32(c.delta)),
                    stall_iters=c.stall_iters, stall_tol=float(np.float32(c.stall_tol)),
                    use_pi=int(c.use_pi), pi_gamma=float(np.float32(c.pi_gamma)),
-                   pi_h=float(np.float32(c.pi_halfwidth)), seed=c.seed, run_id=c.run_id)
+                   pi_h=float(np.float32(c.pi_halfwidth)), seed=c.seed, run_id=c.run_id,
+                   problem=5 if getattr(c, "obstacle_kind", 0) == 1 else 0)
 
 
 class Scene:
@@ -377,7 +380,7 @@ def poly_margin(cfg, scene: "Scene", X) -> np.ndarray:
     """Per path: distance of its crossing decisions from a flip (parity tests)."""
     X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, cfg.D))
     m = np.zeros(X.shape[0])
-    c = _bf_cfg(cfg)
+    c = _cfg(cfg) if hasattr(cfg, "obstacle_kind") else _bf_cfg(cfg)
     s = scene.c()
     lib().so_poly_margin(ctypes.byref(c), ctypes.byref(s), X.shape[0], _p64(X), _p64(m))
     return m
@@ -447,6 +450,23 @@ def advance_scene(W, H, circles, cvel, start, svel, target, tvel):
     lib().so_advance_scene(float(np.float32(W)), float(np.float32(H)), c.shape[0], _p64(c), _p64(v),
                            _p64(s), _p64(sv), _p64(t), _p64(tv))
     return c, v, s, sv, t, tv
+
+
+def advance_polygons(W, H, edges, offsets, pvel, start, svel, target, tvel):
+    """One dynamic step of polygon obstacles (rigid translation, bounding-box bounce)
+    and of start/target, on FP64 copies; returns (edges, pvel, start, svel, target, tvel)."""
+    e = np.ascontiguousarray(np.asarray(edges, np.float64).reshape(-1, 4)).copy()
+    off = np.ascontiguousarray(np.asarray(offsets, np.int32).reshape(-1))
+    v = np.ascontiguousarray(np.asarray(pvel, np.float64).reshape(-1, 2)).copy()
+    s = np.asarray(start, np.float64).reshape(2).copy()
+    sv = np.asarray(svel, np.float64).reshape(2).copy()
+    t = np.asarray(target, np.float64).reshape(2).copy()
+    tv = np.asarray(tvel, np.float64).reshape(2).copy()
+    if off.size != v.shape[0] + 1 or off[0] != 0 or off[-1] != e.shape[0] or np.any(np.diff(off) < 0):
+        raise ValueError("offsets must run from 0 to the edge count, one more entry than polygons")
+    lib().so_advance_polygons(float(np.float32(W)), float(np.float32(H)), v.shape[0],
+                              off.ctypes.data_as(_i32p), _p64(e), _p64(v), _p64(s), _p64(sv), _p64(t), _p64(tv))
+    return e, v, s, sv, t, tv
 
 
 def hsef(lcfg, scene: Scene, HG: int, HN: int, E: int, hhyper, lo, hi, l_vlimit: float,

@@ -613,6 +613,41 @@ void so_advance_scene(double W, double H, int32_t O, double* circ, double* cvel,
   so_move(&target[1], &tvel[1], 0.0, 0.0, H);
 }
 
+/* Moving polygon obstacles (Sec. 3.3.1's bounding boxes, moved as the Fig. PP
+ * caption moves the obstacles): polygon p, the edges off[p] .. off[p+1]-1
+ * (E x 4: x0, y0, x1, y1), is translated by its velocity (pvel[2p], pvel[2p+1]);
+ * then a velocity component flips when the polygon's bounding box lies past the
+ * border it is moving towards -- the circles' rule with the box's extent in place
+ * of centre -/+ radius.  Start and target move as in so_advance_scene. */
+void so_advance_polygons(double W, double H, int32_t P, const int32_t* off, double* edges, double* pvel,
+                         double* start, double* svel, double* target, double* tvel) {
+  for (int32_t p = 0; p < P; ++p) {
+    const double vx = pvel[2 * p], vy = pvel[2 * p + 1];
+    double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+    for (int32_t e = off[p]; e < off[p + 1]; ++e) {
+      double* d = edges + 4 * e;
+      d[0] += vx;
+      d[1] += vy;
+      d[2] += vx;
+      d[3] += vy;
+      xmin = fmin(xmin, fmin(d[0], d[2]));
+      xmax = fmax(xmax, fmax(d[0], d[2]));
+      ymin = fmin(ymin, fmin(d[1], d[3]));
+      ymax = fmax(ymax, fmax(d[1], d[3]));
+    }
+    if (off[p + 1] > off[p]) {
+      if (xmin < 0.0 && vx < 0.0) pvel[2 * p] = -vx;
+      if (xmax > W && vx > 0.0) pvel[2 * p] = -vx;
+      if (ymin < 0.0 && vy < 0.0) pvel[2 * p + 1] = -vy;
+      if (ymax > H && vy > 0.0) pvel[2 * p + 1] = -vy;
+    }
+  }
+  so_move(&start[0], &svel[0], 0.0, 0.0, W);
+  so_move(&start[1], &svel[1], 0.0, 0.0, H);
+  so_move(&target[0], &tvel[0], 0.0, 0.0, W);
+  so_move(&target[1], &tvel[1], 0.0, 0.0, H);
+}
+
 /* ------------------------------------------------------------------------- */
 /* HSEF, Sec. 3.2.1.  The H-swarm is DTPSO over hyper-parameter vectors;     */
 /* each H-particle's fitness is the LFV (Eq. fit_h) of an L-run of          */

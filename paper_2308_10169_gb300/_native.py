@@ -37,7 +37,7 @@ class Config(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32),
         ("runs", ctypes.c_int32), ("ctas_per_group", ctypes.c_int32), ("threads", ctypes.c_int32),
         ("circle_split", ctypes.c_int32), ("fitness_mode", ctypes.c_int32),
-        ("exchange", ctypes.c_int32),
+        ("exchange", ctypes.c_int32), ("obstacle_kind", ctypes.c_int32),
     ]
 
 
@@ -102,7 +102,7 @@ def make_config(cfg) -> Config:
                   pi_halfwidth=cfg.pi_halfwidth, seed=cfg.seed, run_id=cfg.run_id, runs=cfg.runs,
                   ctas_per_group=cfg.ctas_per_group, threads=cfg.threads,
                   circle_split=cfg.circle_split, fitness_mode=cfg.fitness_mode,
-                  exchange=cfg.exchange)
+                  exchange=cfg.exchange, obstacle_kind=cfg.obstacle_kind)
 
 
 class BFConfig(ctypes.Structure):
@@ -210,6 +210,8 @@ SIGNATURES = {
                                           _vp, _i32, _vp, _i32, _vp, _i32, ctypes.POINTER(GemmExtra), _i32,
                                           _vp]),
     "sepso_exchange_form": (ctypes.c_int, [_vp]),
+    "sepso_set_polygons": (ctypes.c_int, [_vp, _fp, _fp, _fp, _i32, ctypes.POINTER(ctypes.c_int32), _i32]),
+    "sepso_get_polygons": (ctypes.c_int, [_vp, _fp, _fp, _fp, _fp]),
     "sepso_philox": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_uint64, _vp, _vp]),
     "sepso_at_window_test": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp]),
     "sepso_bf_workspace_size": (ctypes.c_int, [ctypes.POINTER(BFConfig), ctypes.POINTER(_sz)]),

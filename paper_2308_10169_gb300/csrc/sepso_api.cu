@@ -47,7 +47,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 // Byte offsets of every array in the caller's workspace.
 struct WsLayout {
   size_t circ, pairs, cvel, pts, hyper, X, V, P, Pfit, PQ, Gb, Gfit, GQ, Tb, prevT, res_wp, ctl, res, win,
-      gword, counter, crows, grec, hhyper, HX, HV, HP, HPfit, HGb, HGfit, HTb, HTfit, estatus, total;
+      gword, counter, crows, grec, poff, hhyper, HX, HV, HP, HPfit, HGb, HGfit, HTb, HTfit, estatus, total;
 };
 
 WsLayout make_ws(const sepso_config& c) {
@@ -85,6 +85,7 @@ WsLayout make_ws(const sepso_config& c) {
   L.counter = take(R * sizeof(RunCounter));
   L.crows = take(R * 2 * M * (D + 4) * 4);
   L.grec = take(R * kRecDepth * G * 8);
+  L.poff = take((Omax + 1) * 4);  // polygon obstacles: edge offsets of the polygons
   L.hhyper = take(32 * 6 * 4);
   L.HX = take(R * DH * 4);
   L.HV = take(R * DH * 4);
@@ -127,6 +128,8 @@ int check_config(const sepso_config* c) {
   if (c->circle_split < 0) return fail(SEPSO_EINVAL, "circle_split < 0");
   if (c->fitness_mode < 0 || c->fitness_mode > 2) return fail(SEPSO_EINVAL, "fitness_mode must be 0, 1 or 2");
   if (c->exchange < 0 || c->exchange > 2) return fail(SEPSO_EINVAL, "exchange must be 0, 1 or 2");
+  if (c->obstacle_kind != SEPSO_OBST_CIRCLES && c->obstacle_kind != SEPSO_OBST_POLYGONS)
+    return fail(SEPSO_EINVAL, "obstacle_kind=%d unknown", c->obstacle_kind);
   return SEPSO_OK;
 }
 
@@ -139,7 +142,8 @@ struct sepso_ctx {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   WsLayout L{};
-  int O = 0;
+  int O = 0;   // circles, or polygon edges
+  int P = 0;   // polygons (polygon obstacles)
   bool has_scene = false;
   int cpg = 1, ppc = 1, C = 1, threads = 256, split = 1, lp = 32, grid = 1, items = 0;
   size_t smem = 0;
@@ -226,6 +230,7 @@ SwarmParams swarm_params(const sepso_ctx* h, int mode, int step_iters) {
   p.grec = h->at<unsigned long long>(h->L.grec);
   p.spec = 0;
   p.cta_grid = h->C;
+  p.poly = c.obstacle_kind == SEPSO_OBST_POLYGONS ? 1 : 0;
   return p;
 }
 
@@ -282,7 +287,8 @@ int choose_cluster_shape(sepso_ctx* h, int smem_optin, ItemsFor items_for, Items
     const int ppc = (N + S - 1) / S;
     // X and V are kept twice only when Auto Truncation can stop a plan
     const ClusterLayout Lc =
-        ClusterLayout::make(c.max_obstacles, ppc, D, T, G, c.tw, S, c.at_mode != SEPSO_AT_OFF ? 1 : 0);
+        ClusterLayout::make(obstacle_f4(c.max_obstacles, c.obstacle_kind == SEPSO_OBST_POLYGONS ? 1 : 0), ppc, D,
+                            T, G, c.tw, S, c.at_mode != SEPSO_AT_OFF ? 1 : 0);
     const size_t smem = (size_t)Lc.total;
     if (smem + 256 > (size_t)smem_optin) continue;
     const int items = items_for(ppc);
@@ -329,7 +335,8 @@ int choose_shape(sepso_ctx* h) {
   // over all threads of the CTA -- the default from 4 particles per CTA (measured:
   // 3.6% faster on the dynamic workload, 21% on 32 HSEF runs; slower with 2).
   auto items_for = [&](int ppc_) { return c.fitness_mode == 2 || (c.fitness_mode == 0 && ppc_ >= 4) ? 1 : 0; };
-  const int K = (std::max(Omax, 1) + 1) / 2;  // circle pairs
+  const bool poly = c.obstacle_kind == SEPSO_OBST_POLYGONS;
+  const int K = poly ? std::max(Omax, 1) : (std::max(Omax, 1) + 1) / 2;  // edges, or circle pairs
   int split = c.circle_split > 0 ? c.circle_split : 1;
   int lp = 1;
   while (lp < 32 && lp < (T + 1) * split) lp <<= 1;
@@ -356,7 +363,7 @@ int choose_shape(sepso_ctx* h) {
   for (int attempt = 0; attempt < 64; ++attempt) {
     const int ppc = (N + cpg - 1) / cpg;
     cpg = (N + ppc - 1) / ppc;  // no empty CTAs
-    const SmemLayout S = SmemLayout::make(Omax, ppc, D, T, G, c.tw);
+    const SmemLayout S = SmemLayout::make(obstacle_f4(Omax, poly ? 1 : 0), ppc, D, T, G, c.tw);
     smem = (size_t)S.total;
     const int ppw = 32 / lp;
     const int items = items_for(ppc);
@@ -555,6 +562,8 @@ int sepso_set_hyper(sepso_handle h, int32_t run, const float* hyper) {
 int sepso_set_scene(sepso_handle h, const float* start, const float* target, const float* circles, int32_t O) {
   int rc = check_handle(h);
   if (rc) return rc;
+  if (h->cfg.obstacle_kind != SEPSO_OBST_CIRCLES)
+    return fail(SEPSO_EINVAL, "this handle plans among polygons: use sepso_set_polygons");
   if (!start || !target) return fail(SEPSO_EINVAL, "start/target is NULL");
   if (O < 0 || O > h->cfg.max_obstacles)
     return fail(SEPSO_EINVAL, "O=%d outside [0, max_obstacles=%d]", O, h->cfg.max_obstacles);
@@ -593,14 +602,15 @@ int sepso_set_motion(sepso_handle h, const float* circle_vel, const float* start
   int rc = check_handle(h);
   if (rc) return rc;
   if (!h->has_scene) return fail(SEPSO_ESTATE, "set_motion before set_scene");
-  if (!start_vel || !target_vel || (h->O > 0 && !circle_vel)) return fail(SEPSO_EINVAL, "NULL velocity");
-  for (int i = 0; i < 2 * h->O; ++i)
-    if (!finite(circle_vel[i])) return fail(SEPSO_EINVAL, "circle_vel[%d] not finite", i);
+  const int nv = h->cfg.obstacle_kind == SEPSO_OBST_POLYGONS ? h->P : h->O;  // one velocity per moving body
+  if (!start_vel || !target_vel || (nv > 0 && !circle_vel)) return fail(SEPSO_EINVAL, "NULL velocity");
+  for (int i = 0; i < 2 * nv; ++i)
+    if (!finite(circle_vel[i])) return fail(SEPSO_EINVAL, "obstacle velocity [%d] not finite", i);
   const float vel[4] = {start_vel[0], start_vel[1], target_vel[0], target_vel[1]};
   for (float v : vel)
     if (!finite(v)) return fail(SEPSO_EINVAL, "start/target velocity not finite");
-  if (h->O > 0)
-    CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.cvel, circle_vel, (size_t)h->O * 8, cudaMemcpyHostToDevice, h->stream));
+  if (nv > 0)
+    CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.cvel, circle_vel, (size_t)nv * 8, cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.pts + 16, vel, sizeof vel, cudaMemcpyHostToDevice, h->stream));
   return SEPSO_OK;
 }
@@ -611,9 +621,13 @@ int sepso_advance_scene(sepso_handle h, int32_t steps) {
   if (!h->has_scene) return fail(SEPSO_ESTATE, "advance before set_scene");
   if (steps < 0) return fail(SEPSO_EINVAL, "steps < 0");
   if (steps == 0) return SEPSO_OK;
-  CUDA_TRY(launch_advance(h->at<float4>(h->L.circ), h->at<float2>(h->L.cvel), h->at<float>(h->L.pts),
-                          h->at<float4>(h->L.pairs), h->O,
-                          h->cfg.map_w, h->cfg.map_h, steps, h->stream));
+  if (h->cfg.obstacle_kind == SEPSO_OBST_POLYGONS)
+    CUDA_TRY(launch_advance_poly(h->at<float4>(h->L.circ), h->at<float2>(h->L.cvel), h->at<int>(h->L.poff), h->P,
+                                 h->at<float>(h->L.pts), h->cfg.map_w, h->cfg.map_h, steps, h->stream));
+  else
+    CUDA_TRY(launch_advance(h->at<float4>(h->L.circ), h->at<float2>(h->L.cvel), h->at<float>(h->L.pts),
+                            h->at<float4>(h->L.pairs), h->O,
+                            h->cfg.map_w, h->cfg.map_h, steps, h->stream));
   h->launches += 1;
   return SEPSO_OK;
 }
@@ -621,6 +635,8 @@ int sepso_advance_scene(sepso_handle h, int32_t steps) {
 int sepso_get_scene(sepso_handle h, float* start, float* target, float* circles, float* circle_vel) {
   int rc = check_handle(h);
   if (rc) return rc;
+  if (h->cfg.obstacle_kind != SEPSO_OBST_CIRCLES)
+    return fail(SEPSO_EINVAL, "this handle plans among polygons: use sepso_get_polygons");
   if (!h->has_scene) return fail(SEPSO_ESTATE, "no scene");
   std::vector<float4> c4((size_t)h->O);
   float pts[8];
@@ -638,6 +654,62 @@ int sepso_get_scene(sepso_handle h, float* start, float* target, float* circles,
       circles[3 * o + 1] = c4[o].y;
       circles[3 * o + 2] = c4[o].z;
     }
+  return SEPSO_OK;
+}
+
+int sepso_set_polygons(sepso_handle h, const float* start, const float* target, const float* edges, int32_t E,
+                       const int32_t* offsets, int32_t P) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h->cfg.obstacle_kind != SEPSO_OBST_POLYGONS)
+    return fail(SEPSO_EINVAL, "this handle plans among circles (obstacle_kind = 0)");
+  if (!start || !target) return fail(SEPSO_EINVAL, "start/target is NULL");
+  if (E < 0 || E > h->cfg.max_obstacles)
+    return fail(SEPSO_EINVAL, "E=%d outside [0, max_obstacles=%d]", E, h->cfg.max_obstacles);
+  if (P < 0 || P > E) return fail(SEPSO_EINVAL, "P=%d outside [0, E=%d]", P, E);
+  if ((E > 0 && !edges) || !offsets) return fail(SEPSO_EINVAL, "edges or offsets is NULL");
+  if (offsets[0] != 0 || offsets[P] != E) return fail(SEPSO_EINVAL, "offsets must run from 0 to E");
+  for (int q = 0; q < P; ++q)
+    if (offsets[q + 1] < offsets[q]) return fail(SEPSO_EINVAL, "offsets decrease at polygon %d", q);
+  if (!finite(start[0]) || !finite(start[1]) || !finite(target[0]) || !finite(target[1]))
+    return fail(SEPSO_EINVAL, "start/target not finite");
+  for (int i = 0; i < 4 * E; ++i)
+    if (!finite(edges[i])) return fail(SEPSO_EINVAL, "edge %d not finite", i / 4);
+  // the previous scene copy must have left the staging buffer
+  CUDA_TRY(cudaEventSynchronize(h->staging_free));
+  float4* e4 = h->staging;
+  for (int e = 0; e < E; ++e) e4[e] = make_float4(edges[4 * e], edges[4 * e + 1], edges[4 * e + 2], edges[4 * e + 3]);
+  float* pts = reinterpret_cast<float*>(h->staging + std::max(h->cfg.max_obstacles, 1));
+  const float pv[8] = {start[0], start[1], target[0], target[1], 0.f, 0.f, 0.f, 0.f};
+  std::memcpy(pts, pv, sizeof pv);
+  if (E > 0) CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.circ, e4, (size_t)E * 16, cudaMemcpyHostToDevice, h->stream));
+  if (P > 0) CUDA_TRY(cudaMemsetAsync(h->ws + h->L.cvel, 0, (size_t)P * 8, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.pts, pts, 8 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaEventRecord(h->staging_free, h->stream));
+  // the offsets come from the caller's (pageable) memory: copied before the return
+  CUDA_TRY(cudaMemcpyAsync(h->ws + h->L.poff, offsets, (size_t)(P + 1) * 4, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->O = E;
+  h->P = P;
+  h->has_scene = true;
+  return SEPSO_OK;
+}
+
+int sepso_get_polygons(sepso_handle h, float* start, float* target, float* edges, float* polygon_vel) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h->cfg.obstacle_kind != SEPSO_OBST_POLYGONS)
+    return fail(SEPSO_EINVAL, "this handle plans among circles (obstacle_kind = 0)");
+  if (!h->has_scene) return fail(SEPSO_ESTATE, "no scene");
+  float pts[8];
+  if (edges && h->O > 0)
+    CUDA_TRY(cudaMemcpyAsync(edges, h->ws + h->L.circ, (size_t)h->O * 16, cudaMemcpyDeviceToHost, h->stream));
+  if (polygon_vel && h->P > 0)
+    CUDA_TRY(cudaMemcpyAsync(polygon_vel, h->ws + h->L.cvel, (size_t)h->P * 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(pts, h->ws + h->L.pts, sizeof pts, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (start) { start[0] = pts[0]; start[1] = pts[1]; }
+  if (target) { target[0] = pts[2]; target[1] = pts[3]; }
   return SEPSO_OK;
 }
 
@@ -708,6 +780,7 @@ int sepso_evaluate(sepso_handle h, const float* d_X, int32_t n, float* d_F, int3
   p.per_cta = std::max(1, 256 / (h->cfg.T + 1));
   p.split = 1;
   p.O = h->O;
+  p.poly = h->cfg.obstacle_kind == SEPSO_OBST_POLYGONS ? 1 : 0;
   p.Omax = h->cfg.max_obstacles;
   p.alpha = h->cfg.alpha;
   p.beta = h->cfg.beta;
@@ -1070,6 +1143,7 @@ extern "C" int sepso_plan_static(const sepso_config* cfg, const float* hyper, co
   int rc = check_config(cfg);
   if (rc) return rc;
   if (cfg->runs != 1) return fail(SEPSO_EINVAL, "sepso_plan_static plans one run (runs=%d)", cfg->runs);
+  if (cfg->obstacle_kind != SEPSO_OBST_CIRCLES) return fail(SEPSO_EINVAL, "sepso_plan_static plans among circles");
   if (!hyper || !start || !target || (O > 0 && !circles))
     return fail(SEPSO_EINVAL, "NULL input to sepso_plan_static");
   if (O < 0 || O > cfg->max_obstacles)

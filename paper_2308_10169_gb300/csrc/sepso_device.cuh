@@ -108,6 +108,7 @@ struct SwarmParams {
   unsigned long long* grec;   // R x kRecDepth x G group records (cluster form)
   int spec;                   // cluster form: X, V double-buffered (Auto Truncation decided one iteration late)
   int cta_grid;               // CTAs per run of the grid-wide form (its barrier counts C * iterations)
+  int poly;                   // obstacles are polygon edges (circ holds O edges as float4), not circles
 };
 
 // ---------------------------------------------------------------------------
@@ -495,6 +496,99 @@ __device__ __forceinline__ void group_fitness_pairs(const float* x, bool live, i
   }
   *len_out = len;
   *q_out = hits;
+}
+
+// ---------------------------------------------------------------------------
+// Polygon obstacles (Sec. 3.3.1's map model: bounding boxes or outlines given by
+// their edges).  Q counts the (path segment, edge) pairs that cross properly: the
+// endpoints of each segment strictly on opposite sides of the other's line (four
+// orientation products), so touching and collinear contacts do not count.  Edges
+// are float4 (x0, y0, x1, y1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int edge_hits(float ax, float ay, float bx, float by, const float4* __restrict__ edges,
+                                         int e0, int e1) {
+  const float ux = bx - ax, uy = by - ay;
+  int hits = 0;
+#pragma unroll 4
+  for (int e = e0; e < e1; ++e) {
+    const float4 d = edges[e];
+    const float vx = d.z - d.x, vy = d.w - d.y;
+    const float o1 = ux * (d.y - ay) - uy * (d.x - ax);
+    const float o2 = ux * (d.w - ay) - uy * (d.z - ax);
+    const float o3 = vx * (ay - d.y) - vy * (ax - d.x);
+    const float o4 = vx * (by - d.y) - vy * (bx - d.x);
+    hits += (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
+  }
+  return hits;
+}
+
+// Length and Q of one particle among polygon edges by a lane group (as
+// group_fitness_pairs): lanes take (segment, edge chunk) items, the group sums
+// both with a fixed shuffle tree.
+__device__ __forceinline__ void group_fitness_edges(const float* x, bool live, int lp, int T, int split, int E,
+                                                    float sx, float sy, float tx, float ty, const float4* edges,
+                                                    float* len_out, int* q_out) {
+  const int lsub = (threadIdx.x & 31) & (lp - 1);
+  const int items = (T + 1) * split;
+  const int chunk = (E + split - 1) / split;
+  float len = 0.0f;
+  int hits = 0;
+  if (live) {
+    for (int it = lsub; it < items; it += lp) {
+      const int sg = it % (T + 1);
+      const int c = it / (T + 1);
+      const float ax = (sg == 0) ? sx : x[sg - 1];
+      const float ay = (sg == 0) ? sy : x[T + sg - 1];
+      const float bx = (sg == T) ? tx : x[sg];
+      const float by = (sg == T) ? ty : x[T + sg];
+      if (c == 0) {
+        const float dx = bx - ax, dy = by - ay;
+        len += sqrtf(fmaf(dx, dx, dy * dy));
+      }
+      hits += edge_hits(ax, ay, bx, by, edges, c * chunk, min(E, c * chunk + chunk));
+    }
+  }
+  for (int off = lp >> 1; off > 0; off >>= 1) {
+    len += __shfl_xor_sync(0xffffffffu, len, off);
+    hits += __shfl_xor_sync(0xffffffffu, hits, off);
+  }
+  *len_out = len;
+  *q_out = hits;
+}
+
+// Q and per-segment lengths of nl particles among polygon edges, as (particle,
+// segment, edge chunk) items over the block (as fitness_items_pairs); sQ must be
+// zero on entry.
+__device__ __forceinline__ void fitness_items_edges(const float* sX, int nl, int T, int D, float sx, float sy,
+                                                    float tx, float ty, const float4* edges, int E, int split,
+                                                    int* sQ, float* seg_len) {
+  const int nseg = T + 1;
+  const int chunk = (E + split - 1) / split;
+  const int per_c = nl * nseg;
+  const int items = per_c * split;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int c = it / per_c;
+    const int r = it - c * per_c;
+    const int i = r / nseg;
+    const int s = r - i * nseg;
+    const float* x = sX + i * D;
+    const float ax = (s == 0) ? sx : x[s - 1];
+    const float ay = (s == 0) ? sy : x[T + s - 1];
+    const float bx = (s == T) ? tx : x[s];
+    const float by = (s == T) ? ty : x[T + s];
+    const int hits = edge_hits(ax, ay, bx, by, edges, c * chunk, min(E, c * chunk + chunk));
+    if (hits) atomicAdd(&sQ[i], hits);
+    if (c == 0) {
+      const float dx = bx - ax, dy = by - ay;
+      seg_len[i * nseg + s] = sqrtf(fmaf(dx, dx, dy * dy));
+    }
+  }
+}
+
+// float4s of a swarm kernel's obstacle area: the circle-pair blocks, or the edges.
+__host__ __device__ inline int obstacle_f4(int Omax, int poly) {
+  const int o = Omax > 0 ? Omax : 1;
+  return poly ? o : pair_block_f4(o);
 }
 
 // Circle chunks per segment for a warp (32 lanes) evaluating one particle of T

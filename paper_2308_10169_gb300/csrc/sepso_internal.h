@@ -15,7 +15,7 @@ struct RunCtl;
 // Shared-memory carve of swarm_kernel (byte offsets); identical on host and device.
 struct SmemLayout {
   int pairs, win, X, V, P, R, Gown, Tb, Pfit, PQ, Q, Imp, Len, Gfit, GQ, Gsrc, total;
-  __host__ __device__ static SmemLayout make(int Omax, int ppc, int D, int T, int G, int tw);
+  __host__ __device__ static SmemLayout make(int obst_f4, int ppc, int D, int T, int G, int tw);
 };
 
 // Shared-memory carve of swarm_cluster_kernel: the rows of swarm_kernel (X and V
@@ -24,11 +24,12 @@ struct SmemLayout {
 // with its Q).
 struct ClusterLayout {
   int pairs, win, X0, X1, V0, V1, P, R, Gown, Pfit, PQ, Q, Len, F, FQ, Imp, rec, xkey, xdec, xrow, total;
-  __host__ __device__ static ClusterLayout make(int Omax, int ppc, int D, int T, int G, int tw, int S, int spec);
+  __host__ __device__ static ClusterLayout make(int obst_f4, int ppc, int D, int T, int G, int tw, int S, int spec);
 };
 
 struct EvalParams {
   int T, D, n, per_cta, split, O, Omax;
+  int poly;            // circ holds O polygon edges (x0, y0, x1, y1) instead of circles
   float alpha;
   int beta;
   const float* X;      // n x D (device)
@@ -63,6 +64,10 @@ cudaError_t launch_swarm_cluster(const SwarmParams& p, int grid, int threads, si
 cudaError_t launch_evaluate(const EvalParams& p, cudaStream_t s);
 cudaError_t launch_advance(float4* circ, float2* cvel, float* pts, float4* pairs, int O, float W, float H,
                            int steps, cudaStream_t s);
+// The same step for polygon obstacles: polygon p (edges poff[p] .. poff[p+1]-1)
+// translated by pvel[p], bouncing by its bounding box.
+cudaError_t launch_advance_poly(float4* edges, float2* pvel, const int* poff, int P, float* pts, float W, float H,
+                                int steps, cudaStream_t s);
 // Circle-pair blocks of the scene's circles (after the circles change on the host side).
 cudaError_t launch_pairs(const float4* circ, int O, float4* pairs, cudaStream_t s);
 cudaError_t launch_hsef_init(const HsefParams& p, cudaStream_t s);

@@ -33,13 +33,13 @@ namespace sepso {
 
 __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ SmemLayout SmemLayout::make(int Omax, int ppc, int D, int T, int G, int tw) {
+__host__ __device__ SmemLayout SmemLayout::make(int obst_f4, int ppc, int D, int T, int G, int tw) {
   SmemLayout s;
   // A 1 KB gap before the pair blocks: with the blocks at offset 0 the dynamic
   // workload's iterations measured 1% slower (same results); the cause is not known.
   int off = 1024;
   s.pairs = off;
-  off = align_up(off + pair_block_f4(Omax > 0 ? Omax : 1) * 16, 16);
+  off = align_up(off + obst_f4 * 16, 16);  // circle-pair blocks or polygon edges
   s.win = off;
   off = align_up(off + tw * 8, 16);
   s.X = off;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
   __shared__ uint64_t s_mbar;
   __shared__ int s_stop;
 
-  const SmemLayout L = SmemLayout::make(p.Omax, p.ppc, p.D, p.T, p.G, p.tw);
+  const SmemLayout L = SmemLayout::make(obstacle_f4(p.Omax, p.poly), p.ppc, p.D, p.T, p.G, p.tw);
   float4* sPairs = reinterpret_cast<float4*>(smem + L.pairs);
   double* sWin = reinterpret_cast<double*>(smem + L.win);
   float* sX = reinterpret_cast<float*>(smem + L.X);
@@ -189,9 +189,9 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
   if (tid == 0) mbar_init(&s_mbar, 1);
   __syncthreads();
   if (tid == 0 && p.O > 0) {
-    const uint32_t bytes = (uint32_t)pair_block_f4(p.O) * 16u;
+    const uint32_t bytes = (uint32_t)(p.poly ? p.O : pair_block_f4(p.O)) * 16u;
     mbar_expect_tx(&s_mbar, bytes);
-    bulk_g2s(sPairs, p.pairs, bytes, &s_mbar);
+    bulk_g2s(sPairs, p.poly ? p.circ : p.pairs, bytes, &s_mbar);
   }
 
   float* gX = p.X + ((size_t)r * p.M + (size_t)g * N + n0) * D;
@@ -332,7 +332,8 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
     if (p.items) {
       // (particle, segment, chunk) items over the whole CTA, then one warp per
       // particle sums its segment lengths in segment order and takes Q.
-      fitness_items_pairs(sX, nl, T, D, sx, sy, tx, ty, sPairs, sNr2, K, p.split, sQi, sLen);
+      if (p.poly) fitness_items_edges(sX, nl, T, D, sx, sy, tx, ty, sPairs, p.O, p.split, sQi, sLen);
+      else fitness_items_pairs(sX, nl, T, D, sx, sy, tx, ty, sPairs, sNr2, K, p.split, sQi, sLen);
       __syncthreads();
     }
     {
@@ -351,8 +352,12 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
             sQi[i] = 0;  // ready for the next iteration (read again only after two barriers)
           }
         } else {
-          group_fitness_pairs(sX + (live ? i : 0) * D, live, lp, T, p.split, K, sx, sy, tx, ty, sPairs, sNr2,
-                              &len, &qq);
+          if (p.poly)
+            group_fitness_edges(sX + (live ? i : 0) * D, live, lp, T, p.split, p.O, sx, sy, tx, ty, sPairs, &len,
+                                &qq);
+          else
+            group_fitness_pairs(sX + (live ? i : 0) * D, live, lp, T, p.split, K, sx, sy, tx, ty, sPairs, sNr2,
+                                &len, &qq);
         }
         int imp = 0, pub = 0;
         float pf = INFINITY;
@@ -607,12 +612,12 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
 // identical results.  Slots of parity k & 1 are rewritten at k + 2, after the
 // cluster barrier of k + 1, which every CTA reaches only after reading them.
 // ---------------------------------------------------------------------------
-__host__ __device__ ClusterLayout ClusterLayout::make(int Omax, int ppc, int D, int T, int G, int tw, int S,
+__host__ __device__ ClusterLayout ClusterLayout::make(int obst_f4, int ppc, int D, int T, int G, int tw, int S,
                                                       int spec) {
   ClusterLayout s;
   int off = 1024;
   s.pairs = off;
-  off = align_up(off + pair_block_f4(Omax > 0 ? Omax : 1) * 16, 16);
+  off = align_up(off + obst_f4 * 16, 16);  // circle-pair blocks or polygon edges
   s.win = off;
   off = align_up(off + tw * 8, 16);
   s.xkey = off;
@@ -727,7 +732,7 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
   __shared__ uint32_t s_dec;
 
   const int S = p.cpg;
-  const ClusterLayout L = ClusterLayout::make(p.Omax, p.ppc, p.D, p.T, p.G, p.tw, S, p.spec);
+  const ClusterLayout L = ClusterLayout::make(obstacle_f4(p.Omax, p.poly), p.ppc, p.D, p.T, p.G, p.tw, S, p.spec);
   float4* sPairs = reinterpret_cast<float4*>(smem + L.pairs);
   double* sWin = reinterpret_cast<double*>(smem + L.win);
   unsigned long long* sXkey = reinterpret_cast<unsigned long long*>(smem + L.xkey);
@@ -775,9 +780,9 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
   }
   __syncthreads();
   if (tid == 0 && p.O > 0) {
-    const uint32_t bytes = (uint32_t)pair_block_f4(p.O) * 16u;
+    const uint32_t bytes = (uint32_t)(p.poly ? p.O : pair_block_f4(p.O)) * 16u;
     mbar_expect_tx(&s_mbar, bytes);
-    bulk_g2s(sPairs, p.pairs, bytes, &s_mbar);
+    bulk_g2s(sPairs, p.poly ? p.circ : p.pairs, bytes, &s_mbar);
   }
 
   float* gX = p.X + ((size_t)r * p.M + (size_t)g * N + n0) * D;
@@ -913,7 +918,8 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
 
     // 1. Fitness F(X^k) and the Pbest test, kept aside.
     if (p.items) {
-      fitness_items_pairs(cX, nl, T, D, sx, sy, tx, ty, sPairs, sNr2, K, p.split, sQi, sLen);
+      if (p.poly) fitness_items_edges(cX, nl, T, D, sx, sy, tx, ty, sPairs, p.O, p.split, sQi, sLen);
+      else fitness_items_pairs(cX, nl, T, D, sx, sy, tx, ty, sPairs, sNr2, K, p.split, sQi, sLen);
       __syncthreads();
     }
     {
@@ -932,8 +938,12 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
             sQi[i] = 0;
           }
         } else {
-          group_fitness_pairs(cX + (live ? i : 0) * D, live, lp, T, p.split, K, sx, sy, tx, ty, sPairs, sNr2,
-                              &len, &qq);
+          if (p.poly)
+            group_fitness_edges(cX + (live ? i : 0) * D, live, lp, T, p.split, p.O, sx, sy, tx, ty, sPairs, &len,
+                                &qq);
+          else
+            group_fitness_pairs(cX + (live ? i : 0) * D, live, lp, T, p.split, K, sx, sy, tx, ty, sPairs, sNr2,
+                                &len, &qq);
         }
         if (live && lsub == 0) {
           const float F = len + p.alpha * powi((float)qq, p.beta);
@@ -1201,7 +1211,10 @@ __global__ void __launch_bounds__(256) evaluate_kernel(const EvalParams p) {
   } else {
     __syncthreads();
   }
-  fitness_items(sX, nl, T, D, p.pts[0], p.pts[1], p.pts[2], p.pts[3], sC, p.O, p.split, sQ, sLen);
+  if (p.poly)
+    fitness_items_edges(sX, nl, T, D, p.pts[0], p.pts[1], p.pts[2], p.pts[3], sC, p.O, p.split, sQ, sLen);
+  else
+    fitness_items(sX, nl, T, D, p.pts[0], p.pts[1], p.pts[2], p.pts[3], sC, p.O, p.split, sQ, sLen);
   __syncthreads();
   for (int i = tid; i < nl; i += blockDim.x) {
     float len = 0.0f;
@@ -1257,6 +1270,50 @@ __global__ void advance_kernel(float4* circ, float2* cvel, float* pts, float4* p
     float sx = pts[0], sy = pts[1], tx = pts[2], ty = pts[3];
     float svx = pts[4], svy = pts[5], tvx = pts[6], tvy = pts[7];
     for (int s = 0; s < steps; ++s) {
+      move1(sx, svx, 0.0f, W);
+      move1(sy, svy, 0.0f, H);
+      move1(tx, tvx, 0.0f, W);
+      move1(ty, tvy, 0.0f, H);
+    }
+    pts[0] = sx; pts[1] = sy; pts[2] = tx; pts[3] = ty;
+    pts[4] = svx; pts[5] = svy; pts[6] = tvx; pts[7] = tvy;
+  }
+}
+
+// Polygon obstacles (the box obstacles of Sec. 4.3, moved as the Fig. PP caption
+// moves the obstacles): one thread per polygon translates its edges by its
+// velocity, then flips a velocity component when the polygon's bounding box lies
+// past the border it is moving towards.  Start and target move as with circles.
+__global__ void advance_poly_kernel(float4* edges, float2* pvel, const int* poff, int P, float* pts, float W,
+                                    float H, int steps) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < P; q += gridDim.x * blockDim.x) {
+    float2 v = pvel[q];
+    const int e0 = poff[q], e1 = poff[q + 1];
+    for (int st = 0; st < steps; ++st) {
+      float xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+      for (int e = e0; e < e1; ++e) {
+        float4 d = edges[e];
+        d.x += v.x;
+        d.y += v.y;
+        d.z += v.x;
+        d.w += v.y;
+        edges[e] = d;
+        xmin = fminf(xmin, fminf(d.x, d.z));
+        xmax = fmaxf(xmax, fmaxf(d.x, d.z));
+        ymin = fminf(ymin, fminf(d.y, d.w));
+        ymax = fmaxf(ymax, fmaxf(d.y, d.w));
+      }
+      if (e1 > e0) {
+        if ((xmin < 0.0f && v.x < 0.0f) || (xmax > W && v.x > 0.0f)) v.x = -v.x;
+        if ((ymin < 0.0f && v.y < 0.0f) || (ymax > H && v.y > 0.0f)) v.y = -v.y;
+      }
+    }
+    pvel[q] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    float sx = pts[0], sy = pts[1], tx = pts[2], ty = pts[3];
+    float svx = pts[4], svy = pts[5], tvx = pts[6], tvy = pts[7];
+    for (int st = 0; st < steps; ++st) {
       move1(sx, svx, 0.0f, W);
       move1(sy, svy, 0.0f, H);
       move1(tx, tvx, 0.0f, W);
@@ -1441,6 +1498,12 @@ cudaError_t launch_swarm_cluster(const SwarmParams& p, int grid, int threads, si
   cudaLaunchAttribute attr[1];
   const cudaLaunchConfig_t cfg = cluster_config(p.cpg, grid, threads, smem, s, attr);
   return cudaLaunchKernelEx(&cfg, swarm_cluster_kernel, p);
+}
+
+cudaError_t launch_advance_poly(float4* edges, float2* pvel, const int* poff, int P, float* pts, float W, float H,
+                                int steps, cudaStream_t s) {
+  advance_poly_kernel<<<std::max(1, (P + 127) / 128), 128, 0, s>>>(edges, pvel, poff, P, pts, W, H, steps);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_evaluate(const EvalParams& p, cudaStream_t s) {

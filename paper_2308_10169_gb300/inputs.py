@@ -66,6 +66,7 @@ class SepsoConfig:
     circle_split: int = 0      # 0 = automatic
     fitness_mode: int = 0      # 0 = automatic; 1 lane group per particle; 2 items over the CTA
     exchange: int = 0          # 0 = automatic; 1 grid-wide barrier; 2 one cluster per group (C3 = 0)
+    obstacle_kind: int = 0     # 0 circles; 1 polygon edges (max_obstacles = edge capacity)
 
     @property
     def D(self) -> int:
@@ -230,6 +231,77 @@ def paper_workload(seed: int = 0, variant: str = "SEPSO", frame_cap: int = 30):
     vel[n_static:, 1] = speed * np.sin(ang)
     scene = Scene(start=(20, 40), target=(346, 326), circles=circles, circle_vel=vel,
                   start_vel=(0.0, 3.0), target_vel=(0.0, -8.0))
+    table = TABLE_HYPER8_PATH if v["hyper"] == "hyper8path" else TABLE_HYPER8
+    return cfg, scene, np.ascontiguousarray(table[:cfg.G], dtype=np.float32)
+
+
+@dataclass
+class PolygonScene:
+    """Start, target and polygon obstacles (closed vertex lists, the last vertex
+    joined back to the first), with per-cycle velocities: one per polygon (it moves
+    as one body) and one each for start and target."""
+    start: np.ndarray
+    target: np.ndarray
+    polygons: list
+    poly_vel: np.ndarray = field(default=None)     # (P, 2) float32
+    start_vel: np.ndarray = field(default=None)
+    target_vel: np.ndarray = field(default=None)
+
+    def __post_init__(self):
+        self.start = np.asarray(self.start, np.float32).reshape(2)
+        self.target = np.asarray(self.target, np.float32).reshape(2)
+        self.polygons = [np.asarray(p, np.float32).reshape(-1, 2) for p in self.polygons]
+        P = len(self.polygons)
+        self.poly_vel = np.zeros((P, 2), np.float32) if self.poly_vel is None else \
+            np.ascontiguousarray(np.asarray(self.poly_vel, np.float32).reshape(P, 2))
+        self.start_vel = np.zeros(2, np.float32) if self.start_vel is None else \
+            np.asarray(self.start_vel, np.float32).reshape(2)
+        self.target_vel = np.zeros(2, np.float32) if self.target_vel is None else \
+            np.asarray(self.target_vel, np.float32).reshape(2)
+
+    @property
+    def edges(self) -> np.ndarray:
+        return polygon_edges(self.polygons)
+
+    @property
+    def offsets(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum([len(p) for p in self.polygons])]).astype(np.int32)
+
+
+def box(cx: float, cy: float, hw: float, hh: float):
+    """The axis-aligned box of centre (cx, cy) and half-sizes (hw, hh) as a vertex list."""
+    return [(cx - hw, cy - hh), (cx + hw, cy - hh), (cx + hw, cy + hh), (cx - hw, cy + hh)]
+
+
+def paper_box_workload(seed: int = 0, variant: str = "SEPSO", frame_cap: int = 30):
+    """The path-planning setting of Sec. 4.3 with the paper's own map model, bounding
+    boxes (Sec. 3.3.1): 366 x 366 map; 8 axis-aligned boxes (2 static, 6 moving at
+    speed U(0, 5] per frame in a random direction, bouncing off the borders by their
+    bounding box) with centres U[60, 306]^2 and half-sizes U[15, 30] per axis; start
+    (20, 40) moving 3 per frame and target (346, 326) moving 8 per frame along the
+    vertical axis; T = 8, G = 8 x N = 170; alpha = 30, beta = 4, gamma = 0.25, delta
+    = 10, TW = 20 (Table params_path); Q counts path-segment / box-edge crossings; a
+    frame is one planning cycle with a cap of ``frame_cap`` iterations; ``variant``
+    as in ``paper_workload`` -> (config, polygon scene, hyper)."""
+    v = PAPER_VARIANTS[variant]
+    cfg = SepsoConfig(T=8, G=8, N=170, max_obstacles=32, map_w=366.0, map_h=366.0,
+                      alpha=PARAMS_PATH["alpha"], beta=PARAMS_PATH["beta"], max_iters=frame_cap,
+                      at_mode=AT_STD_WINDOW if v["at"] else AT_OFF, tw=PARAMS_PATH["tw"],
+                      delta=PARAMS_PATH["delta"], use_pi=v["use_pi"],
+                      pi_gamma=PARAMS_PATH["pi_gamma"], pi_halfwidth=20.0, seed=seed, obstacle_kind=1)
+    rng = np.random.default_rng(7000 + seed)
+    n_static, n_moving = 2, 6
+    n = n_static + n_moving
+    cx, cy = rng.uniform(60.0, 306.0, n), rng.uniform(60.0, 306.0, n)
+    hw, hh = rng.uniform(15.0, 30.0, n), rng.uniform(15.0, 30.0, n)
+    polys = [box(cx[i], cy[i], hw[i], hh[i]) for i in range(n)]
+    vel = np.zeros((n, 2), np.float32)
+    speed = 5.0 - rng.uniform(0.0, 5.0, n_moving)      # (0, 5]
+    ang = rng.uniform(0.0, 2.0 * np.pi, n_moving)
+    vel[n_static:, 0] = speed * np.cos(ang)
+    vel[n_static:, 1] = speed * np.sin(ang)
+    scene = PolygonScene(start=(20, 40), target=(346, 326), polygons=polys, poly_vel=vel,
+                         start_vel=(0.0, 3.0), target_vel=(0.0, -8.0))
     table = TABLE_HYPER8_PATH if v["hyper"] == "hyper8path" else TABLE_HYPER8
     return cfg, scene, np.ascontiguousarray(table[:cfg.G], dtype=np.float32)
 
@@ -425,18 +497,21 @@ def batch_workload(seed: int = 0, n: int = 4096, T_range=(8, 64), O_range=(16, 1
 
 
 def serving_workload(seed: int = 0, n_agents: int = 2048, T_choices=(8, 20, 40), O_choices=(32, 256),
-                     r_range=(5.0, 25.0)):
+                     r_range=(5.0, 25.0), lo: float = 60.0, hi: float = 340.0):
     """Agents of the serving workload: each has a T in T_choices, a scene of O in
-    O_choices circles (centres U[0,400]^2, radii U[r_range], velocities
-    U[0.5,2] per request in a uniform direction), start (20,20) and target
-    (380,380) drifting 1 unit per request vertically, and its own hyper-parameters
-    (w ~ U[0.4,0.9], C1, C2 ~ U[1,2.5]).  Returns a list of dicts."""
+    O_choices circles (centres U[lo,hi]^2 as in the other workloads, so that the
+    start and target start clear; radii U[r_range] x sqrt(32 / O), so that both
+    obstacle counts cover the same area of the map; velocities U[0.5,2] per request
+    in a uniform direction), start (20,20) and target (380,380) drifting 1 unit per
+    request vertically, and its own hyper-parameters (w ~ U[0.4,0.9], C1, C2 ~
+    U[1,2.5]).  Returns a list of dicts."""
     rng = np.random.default_rng(7000 + seed)
     agents = []
     for a in range(n_agents):
         T = int(rng.choice(T_choices))
         O = int(rng.choice(O_choices))
-        c = random_circles(rng, O, lo=0.0, hi=400.0, r_lo=r_range[0], r_hi=r_range[1])
+        sc = float(np.sqrt(32.0 / O))
+        c = random_circles(rng, O, lo=lo, hi=hi, r_lo=r_range[0] * sc, r_hi=r_range[1] * sc)
         sp = rng.uniform(0.5, 2.0, O)
         ang = rng.uniform(0, 2 * np.pi, O)
         v = np.stack([sp * np.cos(ang), sp * np.sin(ang)], 1).astype(np.float32)

@@ -123,6 +123,29 @@ class Planner:
             check(self.lib.sepso_set_motion(self._h, fptr(cv) if cv.size else None,
                                             fptr(_f32(scene.start_vel)), fptr(_f32(scene.target_vel))))
 
+    def set_polygons(self, scene, motion: bool = True):
+        """A scene among polygon obstacles (a handle with obstacle_kind = 1):
+        ``scene`` carries start, target, polygons (vertex lists) and velocities."""
+        e = _f32(scene.edges, (-1, 4))
+        off = np.ascontiguousarray(np.asarray(scene.offsets, np.int32))
+        check(self.lib.sepso_set_polygons(self._h, fptr(_f32(scene.start)), fptr(_f32(scene.target)),
+                                          fptr(e) if e.size else None, e.shape[0],
+                                          off.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), off.size - 1))
+        self.O = e.shape[0]
+        self.P = off.size - 1
+        if motion:
+            pv = _f32(scene.poly_vel, (-1, 2))
+            check(self.lib.sepso_set_motion(self._h, fptr(pv) if pv.size else None,
+                                            fptr(_f32(scene.start_vel)), fptr(_f32(scene.target_vel))))
+
+    def get_polygons(self):
+        """(start, target, edges (E, 4), polygon velocities (P, 2)) on the device now."""
+        s, t = np.zeros(2, np.float32), np.zeros(2, np.float32)
+        e = np.zeros((max(self.O, 1), 4), np.float32)
+        v = np.zeros((max(self.P, 1), 2), np.float32)
+        check(self.lib.sepso_get_polygons(self._h, fptr(s), fptr(t), fptr(e), fptr(v)))
+        return s, t, e[:self.O], v[:self.P]
+
     def advance(self, steps: int = 1):
         check(self.lib.sepso_advance_scene(self._h, steps))
 

@@ -128,3 +128,98 @@ def test_polygon_workload_shapes():
     np.testing.assert_array_equal(e[:, 1:, :2], e[:, :-1, 2:])
     np.testing.assert_array_equal(e[:, 0, :2], e[:, -1, 2:])
     assert edges.min() >= 0.0 and edges.max() <= 400.0
+
+
+# ---------------------------------------------------------------------------
+# Moving polygons (the box obstacles of Sec. 4.3, moved as in the Fig. PP caption)
+# ---------------------------------------------------------------------------
+
+def _box(x0, y0, x1, y1):
+    return [(x0, y0), (x1, y0), (x1, y1), (x0, y1)]
+
+
+def _adv(polys, vel, W=400.0, H=400.0, start=(20, 40), svel=(0, 3), target=(346, 326), tvel=(0, -8)):
+    edges = polygon_edges(polys)
+    off = np.concatenate([[0], np.cumsum([len(p) for p in polys])]).astype(np.int32)
+    return oracle.advance_polygons(W, H, edges, off, np.asarray(vel, np.float64), start, svel, target, tvel)
+
+
+def test_moving_boxes_hand_values():
+    # left wall: [10,30]x[100,120] moving (-15, 2) -> [-5,15]x[102,122]; the box lies
+    # past x = 0 moving left, so vx flips; vy does not
+    e, v, *_ = _adv([_box(10, 100, 30, 120)], [(-15.0, 2.0)])
+    np.testing.assert_array_equal(e, polygon_edges([_box(-5, 102, 15, 122)]))
+    np.testing.assert_array_equal(v, [[15.0, 2.0]])
+    # top-right corner: both components flip
+    e, v, *_ = _adv([_box(380, 390, 395, 398)], [(8.0, 5.0)])
+    np.testing.assert_array_equal(e, polygon_edges([_box(388, 395, 403, 403)]))
+    np.testing.assert_array_equal(v, [[-8.0, -5.0]])
+    # interior: plain translation
+    e, v, *_ = _adv([_box(100, 100, 150, 130)], [(-2.5, 4.0)])
+    np.testing.assert_array_equal(e, polygon_edges([_box(97.5, 104, 147.5, 134)]))
+    np.testing.assert_array_equal(v, [[-2.5, 4.0]])
+    # past the wall but already moving away: no flip
+    e, v, *_ = _adv([_box(-10, 100, 5, 130)], [(3.0, 0.0)])
+    np.testing.assert_array_equal(v, [[3.0, 0.0]])
+    # touching exactly (box edge at x = 0 after the move) is not past it
+    e, v, *_ = _adv([_box(2, 100, 22, 130)], [(-2.0, 0.0)])
+    np.testing.assert_array_equal(v, [[-2.0, 0.0]])
+
+
+def test_moving_polygons_keep_their_edges_and_bounce_alone():
+    # two polygons: a U outline (8 edges) bouncing off the bottom wall through a
+    # vertex that is not the first, and a box in the interior
+    u = [(100, 5), (160, 5), (160, 65), (145, 65), (145, 20), (115, 20), (115, 65), (100, 65)]
+    u = [(x, y + 1.0) for x, y in u]
+    u[5] = (115, 1.5)   # lowest vertex of the outline is not the first one
+    polys = [_box(200, 200, 240, 230), u]
+    e, v, s, sv, t, tv = _adv(polys, [(1.0, 1.0), (0.0, -2.0)])
+    e0 = polygon_edges(polys)
+    np.testing.assert_allclose(e[:4], e0[:4] + np.array([1.0, 1.0, 1.0, 1.0]), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(e[4:], e0[4:] + np.array([0.0, -2.0, 0.0, -2.0]), rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(v, [[1.0, 1.0], [0.0, 2.0]])   # only the U's vy flips (its y min is -0.5)
+    # start and target move as with circles
+    np.testing.assert_array_equal(s, [20, 43])
+    np.testing.assert_array_equal(t, [346, 318])
+
+
+def test_moving_box_follows_the_circle_rule():
+    # a square of half-size r moves like a circle of radius r centred on it (both
+    # bounce when centre -/+ r passes the border they move towards)
+    rng = np.random.default_rng(8)
+    for _ in range(50):
+        r = rng.uniform(5, 30)
+        c = rng.uniform(r, 400 - r, 2)
+        vel = rng.uniform(-6, 6, 2)
+        circ = np.array([[c[0], c[1], r]])
+        cv = vel.reshape(1, 2)
+        x0, y0, x1, y1 = c[0] - r, c[1] - r, c[0] + r, c[1] + r
+        e = np.array([[x0, y0, x1, y0], [x1, y0, x1, y1], [x1, y1, x0, y1], [x0, y1, x0, y0]])
+        off = np.array([0, 4], np.int32)
+        bv = vel.reshape(1, 2)
+        st, sv, tg, tv = (0, 0), (0, 0), (0, 0), (0, 0)
+        for _ in range(120):
+            circ, cv, *_ = oracle.advance_scene(400.0, 400.0, circ, cv, st, sv, tg, tv)
+            e, bv, *_ = oracle.advance_polygons(400.0, 400.0, e, off, bv, st, sv, tg, tv)
+        np.testing.assert_array_equal(cv, bv)
+        np.testing.assert_allclose(e[0, :2], circ[0, :2] - r, rtol=0, atol=1e-9)
+
+
+def test_planner_goes_around_a_box():
+    # one box across the straight line: the optimum runs along the box, around a
+    # corner pair; its length is |s - c1| + |c1 - c2| + |c2 - t| = 2 sqrt(100^2 + 50^2)
+    # + 100 = 323.607 (touching a corner is not a crossing)
+    from paper_2308_10169_gb300.inputs import SepsoConfig
+    edges = polygon_edges([_box(150, 150, 250, 250)])
+    cfg = SepsoConfig(T=8, G=8, N=40, alpha=30.0, beta=4, max_iters=200, obstacle_kind=1, seed=3,
+                      max_obstacles=4)
+    hy = np.ascontiguousarray(TABLE_HYPER8_PATH, np.float64)
+    sw = oracle.Swarm(cfg, hy)
+    r = sw.plan(oracle.Scene((50, 200), (350, 200), np.zeros((0, 3)), edges))
+    best = 2 * np.hypot(100, 50) + 100
+    assert r["Q"] == 0
+    assert best - 1e-9 <= r["cost"] <= best * 1.02
+    # the returned cost is the fitness of the returned path among the polygons
+    F, Q, L = oracle.evaluate(cfg, oracle.Scene((50, 200), (350, 200), np.zeros((0, 3)), edges),
+                              r["waypoints"].reshape(1, -1))
+    assert Q[0] == 0 and abs(F[0] - r["cost"]) < 1e-9
