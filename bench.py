@@ -107,16 +107,18 @@ def parse():
     ap.add_argument("--serve-rates", type=str, default="20000,5000",
                     help="offered request rates (1/s) of the serving section ('' = skip it)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-radii", type=str, default="3,15",
+                    help="circle radii U[a,b] of the serving scenes with 32 circles (scaled by sqrt(32/O))")
     ap.add_argument("--prior-train", type=int, default=16384,
                     help="training scenes of the learned-prior section (0 = skip it; 200000 = full size)")
     ap.add_argument("--prior-eval", type=int, default=2048, help="held-out scenes (10000 = full size)")
     ap.add_argument("--prior-rounds", type=int, default=3)
     ap.add_argument("--prior-epochs", type=int, default=30)
     ap.add_argument("--prior-batch", type=int, default=4096, help="rows per Adam step")
-    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper,boxes,bf,poly",
-                    help="comma list of main, cpu, batch, prior, serve, paper, boxes, bf, poly, gemm (paper: "
-                         "the ablation variants of the path-planning comparison; boxes: the same among "
-                         "moving bounding boxes; bf: the benchmark "
+    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper,boxes,agents,bf,poly",
+                    help="comma list of main, cpu, batch, prior, serve, paper, boxes, agents, bf, poly, gemm "
+                         "(paper: the ablation variants of the path-planning comparison; boxes: the same among "
+                         "moving bounding boxes; agents: multi-agent teams; bf: the benchmark "
                          "functions; poly: planning among polygon obstacles; gemm: the tensor-core "
                          "GEMM alone)")
     ap.add_argument("--bf-fns", type=str, default="1,2,3,4", help="benchmark functions (1..4) of section bf")
@@ -700,6 +702,59 @@ def run_paper_boxes(frames: int = 100, seed: int = 0, oracle_keys: int = 2, orac
             "variants": out}
 
 
+def run_agents(n_teams: int = 512, A: int = 8, rounds: int = 4, sep: float = 25.0, oracle_teams: int = 2):
+    """Multi-agent teams (the paper's stated future work) on the batch planner:
+    ``n_teams`` maps of A agents swapping sides across the centre, planned in
+    ``rounds`` rounds of simultaneous best responses (each a planning cycle with PI
+    around the agent's own previous path, its mates' previous paths counting as
+    moving obstacles).  Per round: device time (CUDA events) of the batch run,
+    agent-plans/s, the share of plans free of collisions and conflicts, median cost;
+    beside it the FP64 oracle on the first ``oracle_teams`` teams."""
+    import torch
+
+    import oracle
+    from paper_2308_10169_gb300 import BatchPlanner
+    from paper_2308_10169_gb300.inputs import team_workload
+    specs, hyper, points, circles, first, size = team_workload(0, n_teams=n_teams, A=A)
+    bp = BatchPlanner(specs)
+    bp.set_inputs(hyper, points, circles)
+    shape, _ = bp.autotune(trial_launches=3)
+    bp.set_teams(first, size, sep)
+    bp.run_async(True)        # warm-up: captures the graph; round 0 below repeats it exactly
+    bp.read()
+    per = []
+    n = len(specs)
+    for r in range(rounds):
+        if r:
+            bp.next_round(r)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(bp.stream)
+        bp.run_async(True)
+        e1.record(bp.stream)
+        res = bp.read()
+        ms = e0.elapsed_time(e1)
+        per.append({"round": r, "ms": ms, "agent_plans_per_s": n / (ms / 1e3),
+                    "free_of_collisions_and_conflicts": float(np.mean([x["Q"] == 0 for x in res])),
+                    "median_cost": float(np.median([x["cost"] for x in res])),
+                    "iters_per_plan": float(np.mean([x["iters"] for x in res]))})
+    ora = []
+    for m in range(oracle_teams):
+        s0 = m * A
+        out = oracle.multi_agent_plan(specs[s0].config(), hyper[s0], circles[s0],
+                                      [points[s0 + a, :2] for a in range(A)],
+                                      [points[s0 + a, 2:] for a in range(A)], sep, rounds)
+        ora.append(out)
+    for r in range(rounds):
+        rr = [ora[m][r][a] for m in range(oracle_teams) for a in range(A)]
+        per[r]["oracle_sample"] = {"agents": len(rr),
+                                   "free_of_collisions_and_conflicts": float(np.mean([x["Q"] == 0 for x in rr])),
+                                   "median_cost": float(np.median([x["cost"] for x in rr]))}
+    return {"workload": f"{n_teams} teams x {A} agents on 400x400 maps (16 circles r~U[8,15] in the middle), "
+                        f"agents swapping sides across the centre, separation {sep}, T=8, G=8 x N=32 per agent, "
+                        f"AT stall 10 / cap 100, {rounds} rounds of best responses",
+            "scenes": n, "shape": shape, "rounds": per}
+
+
 def run_bf(fns, iters: int, trials: int, peak_gbs: float):
     """Benchmark functions (Table BFs): the large-scale runs of Sec. 4.1.2 (16K
     particles x 1K coordinates) and the standard runs of Sec. 4.1.1 (80 particles x
@@ -826,11 +881,11 @@ def _world_step(ag):
                 ag[pv][d] *= -1
 
 
-def run_serve(rate: float, seconds: float, n_agents: int = 2048):
+def run_serve(rate: float, seconds: float, n_agents: int = 2048, radii=(3.0, 15.0)):
     """Open-loop serving: Poisson arrivals at `rate`, 2048 agents with mixed T and O."""
     from paper_2308_10169_gb300 import Server
     from paper_2308_10169_gb300.inputs import poisson_arrivals, serving_workload
-    agents = serving_workload(0, n_agents)
+    agents = serving_workload(0, n_agents, r_range=radii)
     arr = poisson_arrivals(0, rate, seconds)
     who = np.random.default_rng(11).integers(0, n_agents, len(arr))
     sv = Server(n_agents=n_agents, max_slots=1024, G=8, N=32, Tmax=40, Omax=256, max_iters=100,
@@ -856,7 +911,7 @@ def run_serve(rate: float, seconds: float, n_agents: int = 2048):
             "ticks": st["ticks"], "gpu_launches": st["launches"]}
 
 
-def serve_single_scene(n: int = 256, n_agents: int = 2048):
+def serve_single_scene(n: int = 256, n_agents: int = 2048, radii=(3.0, 15.0)):
     """The plain single-scene kernel on the serving mix: the first request of n agents
     (no previous path), one plan at a time through sepso_plan (host scene in,
     waypoints out), with the server's planner settings; and the same n requests as
@@ -866,7 +921,7 @@ def serve_single_scene(n: int = 256, n_agents: int = 2048):
 
     from paper_2308_10169_gb300 import Planner, Server
     from paper_2308_10169_gb300.inputs import AT_STALL, Scene, SepsoConfig, serving_workload
-    agents = serving_workload(0, n_agents)[:n]
+    agents = serving_workload(0, n_agents, r_range=radii)[:n]
     lat, costs, its, qs = [], [], [], []
     for a, ag in enumerate(agents):
         cfg = SepsoConfig(T=ag["T"], G=8, N=32, max_obstacles=256, alpha=30.0, beta=4, max_iters=100,
@@ -1147,6 +1202,8 @@ def main():
             line["paper_ablation"] = run_paper()
         if world == 1 and "boxes" in sections:
             line["paper_ablation_boxes"] = run_paper_boxes()
+        if world == 1 and "agents" in sections:
+            line["multi_agent"] = run_agents()
         if world == 1 and "poly" in sections:
             line["poly"] = run_poly()
         if world == 1 and "bf" in sections:
@@ -1155,13 +1212,14 @@ def main():
         if world == 1 and "gemm" in sections:
             line["gemm"] = run_gemm()
         if world == 1 and "serve" in sections and args.serve_rates:
+            radii = tuple(float(x) for x in args.serve_radii.split(","))
             line["serve"] = {
                 "workload": "2048 agents, Poisson arrivals, T in {8,20,40}, O in {32,256} circles, centres "
-                            "U[60,340]^2, r~U[5,25] x sqrt(32/O), "
+                            f"U[60,340]^2, r~U[{radii[0]:g},{radii[1]:g}] x sqrt(32/O), "
                             "obstacles advanced per request, G=8 x N=32, PI warm start on the device, "
                             "AT stall 10 / cap 100, continuous batching (1024 slots)",
-                "runs": [run_serve(float(r), args.serve_seconds) for r in args.serve_rates.split(",")],
-                "vs_single_scene": serve_single_scene()}
+                "runs": [run_serve(float(r), args.serve_seconds, radii=radii) for r in args.serve_rates.split(",")],
+                "vs_single_scene": serve_single_scene(radii=radii)}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -339,6 +339,25 @@ int sepso_batch_autotune(sepso_batch_handle h, int32_t trial_launches, sepso_bat
 int sepso_batch_set_starts(sepso_batch_handle h, const float* prev, const float* prior, int32_t ld,
                            const int32_t* has_prev);
 
+/* Multi-agent teams (the paper names multi-agent planning as future work; this is
+ * an extension).  Scenes [team_first[s], team_first[s] + team_size[s]) form scene
+ * s's team: agents sharing a map, contiguous, with one T.  All agents of a team
+ * leave their starts together and reach one point of their path per time step
+ * (start, T waypoints, target), straight in between; in each step, a pair whose
+ * relative position passes closer than sep to the origin (the relative motion is a
+ * segment) is one conflict, added to Q of Eq. penalty.  An agent's fitness counts
+ * its conflicts with its mates' current paths: moving obstacles.  Host arrays of n
+ * int32; sync.  The mates' paths count from the first sepso_batch_next_round.
+ * Errors: EINVAL. */
+int sepso_batch_set_teams(sepso_batch_handle h, const int32_t* team_first, const int32_t* team_size, float sep);
+
+/* Start the next round of best responses: every scene's last result (with its
+ * start and target) becomes its agent's path as its mates see it, and the centre
+ * of its own Priori Initialization; every scene's Philox cycle becomes `cycle`.
+ * The next sepso_batch_run_async then plans every agent against its mates' paths
+ * of the round before (device copies; sync).  Errors: ESTATE (no teams), ECUDA. */
+int sepso_batch_next_round(sepso_batch_handle h, uint32_t cycle);
+
 /* Number of scenes that will use their prior proposal (host output, sync). */
 int sepso_batch_prior_used(sepso_batch_handle h, int32_t* n_used);
 

@@ -87,7 +87,8 @@ class _Scene(ctypes.Structure):
     _fields_ = [("sx", ctypes.c_double), ("sy", ctypes.c_double),
                 ("tx", ctypes.c_double), ("ty", ctypes.c_double),
                 ("O", ctypes.c_int32), ("circ", _f64p),
-                ("E", ctypes.c_int32), ("edges", _f64p)]
+                ("E", ctypes.c_int32), ("edges", _f64p),
+                ("A", ctypes.c_int32), ("agents", _f64p), ("sep", ctypes.c_double)]
 
 
 class _State(ctypes.Structure):
@@ -197,17 +198,24 @@ def _cfg(c) -> _Config:
 class Scene:
     """A static scene in FP64 (converted exactly from the FP32 inputs)."""
 
-    def __init__(self, start, target, circles, edges=None):
+    def __init__(self, start, target, circles, edges=None, agents=None, sep: float = 0.0):
+        """agents: the other agents' timed paths, (A, 2 (T + 2)) -- x of start,
+        waypoints, target, then the y's; sep: the separation below which two agents
+        conflict (multi-agent extension)."""
         self.start = np.asarray(start, dtype=np.float64).reshape(2).copy()
         self.target = np.asarray(target, dtype=np.float64).reshape(2).copy()
         self.circles = np.ascontiguousarray(np.asarray(circles, dtype=np.float64).reshape(-1, 3))
         e = np.zeros((0, 4)) if edges is None else edges
         self.edges = np.ascontiguousarray(np.asarray(e, dtype=np.float64).reshape(-1, 4))
+        a = np.zeros((0, 2)) if agents is None else np.asarray(agents, dtype=np.float64)
+        self.agents = np.ascontiguousarray(a if a.ndim == 2 else a.reshape(1, -1))
+        self.sep = float(np.float32(sep))
 
     def c(self) -> _Scene:
         return _Scene(sx=self.start[0], sy=self.start[1], tx=self.target[0], ty=self.target[1],
                       O=self.circles.shape[0], circ=_p64(self.circles),
-                      E=self.edges.shape[0], edges=_p64(self.edges))
+                      E=self.edges.shape[0], edges=_p64(self.edges),
+                      A=self.agents.shape[0], agents=_p64(self.agents), sep=self.sep)
 
 
 # ----------------------------------------------------------------------------
@@ -450,6 +458,41 @@ def advance_scene(W, H, circles, cvel, start, svel, target, tvel):
     lib().so_advance_scene(float(np.float32(W)), float(np.float32(H)), c.shape[0], _p64(c), _p64(v),
                            _p64(s), _p64(sv), _p64(t), _p64(tv))
     return c, v, s, sv, t, tv
+
+
+def timed_path(start, target, waypoints, T: int) -> np.ndarray:
+    """An agent's timed path for Scene(agents=...): start, T waypoints ([x..., y...]),
+    target -> (2 (T + 2),) = x_0..x_{T+1}, y_0..y_{T+1}."""
+    w = np.asarray(waypoints, np.float64).reshape(2 * T)
+    xs = np.concatenate([[start[0]], w[:T], [target[0]]])
+    ys = np.concatenate([[start[1]], w[T:], [target[1]]])
+    return np.concatenate([xs, ys])
+
+
+def multi_agent_plan(cfg, hyper, circles, starts, targets, sep: float, rounds: int, seeds=None) -> list:
+    """The multi-agent extension by rounds of simultaneous best responses: in round 0
+    every agent plans alone; in round r each plans (a fresh planning cycle of
+    Algorithm 1 with PI around its own previous path) against the other agents'
+    paths of round r - 1 as moving obstacles.  Agent a uses Philox run id run_id + a
+    (its own streams).  Returns per round the list of each agent's result."""
+    A = len(starts)
+    T = cfg.T
+    sws = [Swarm(replace_cfg(cfg, run_id=cfg.run_id + a), hyper) for a in range(A)]
+    out, paths = [], None
+    for r in range(rounds):
+        res = []
+        for a in range(A):
+            others = None if paths is None else np.stack([paths[b] for b in range(A) if b != a])
+            sc = Scene(starts[a], targets[a], circles, agents=others, sep=sep if others is not None else 0.0)
+            res.append(sws[a].plan(sc))
+        paths = [timed_path(starts[a], targets[a], res[a]["waypoints"], T) for a in range(A)]
+        out.append(res)
+    return out
+
+
+def replace_cfg(cfg, **kw):
+    import dataclasses
+    return dataclasses.replace(cfg, **kw)
 
 
 def advance_polygons(W, H, edges, offsets, pvel, start, svel, target, tvel):

@@ -122,6 +122,13 @@ typedef struct {
   const double* circ;    /* O x 3: cx, cy, r                                  */
   int32_t E;             /* polygon edges (problem 5)                         */
   const double* edges;   /* E x 4: x0, y0, x1, y1                             */
+  /* Other agents sharing the scene (multi-agent extension): A timed paths of
+   * T + 2 points each, A x (2 (T + 2)): x_0..x_{T+1}, then y_0..y_{T+1} (their
+   * start, their T waypoints, their target), and the separation below which two
+   * agents conflict. */
+  int32_t A;
+  const double* agents;
+  double sep;
 } so_scene;
 
 typedef struct {
@@ -245,6 +252,32 @@ void so_poly_margin(const so_config* cfg, const so_scene* sc, int32_t n, const d
   }
 }
 
+/* Conflicts with the other agents of the scene (the multi-agent extension the
+ * paper names as future work): all agents leave their starts together and reach
+ * one point of their path per time step (start, T waypoints, target), moving
+ * straight in between.  During step s the position of this path relative to agent
+ * b's moves on a straight line, so their closest approach in that step is the
+ * distance of the origin to the segment rel(s) -> rel(s + 1), rel = own point -
+ * b's point; each (agent, step) with a closest approach below sep is one conflict,
+ * added to Q of Eq. penalty. */
+static int32_t so_agent_conflicts(int32_t T, const double* x, const so_scene* sc) {
+  int32_t q = 0;
+  const int32_t P = T + 2;
+  for (int32_t b = 0; b < sc->A; ++b) {
+    const double* w = sc->agents + (int64_t)b * 2 * P;
+    for (int32_t s = 0; s <= T; ++s) {
+      const double ax = (s == 0) ? sc->sx : x[s - 1];
+      const double ay = (s == 0) ? sc->sy : x[T + s - 1];
+      const double bx = (s == T) ? sc->tx : x[s];
+      const double by = (s == T) ? sc->ty : x[T + s];
+      const double r0x = ax - w[s], r0y = ay - w[P + s];
+      const double r1x = bx - w[s + 1], r1y = by - w[P + s + 1];
+      if (so_seg_point_dist(r0x, r0y, r1x, r1y, 0.0, 0.0) < sc->sep) ++q;
+    }
+  }
+  return q;
+}
+
 /* Q: number of (path segment, circle) pairs whose distance is below the radius. */
 static int32_t so_collisions(int32_t T, const double* x, const so_scene* sc) {
   int32_t q = 0;
@@ -341,7 +374,7 @@ void so_evaluate(const so_config* cfg, const so_scene* sc, int32_t n, const doub
     for (int32_t p = 0; p < n; ++p) {
       const double* x = X + (int64_t)p * D;
       const double l = so_length(T, x, sc->sx, sc->sy, sc->tx, sc->ty);
-      const int32_t q = so_poly_crossings(T, x, sc);
+      const int32_t q = so_poly_crossings(T, x, sc) + (sc->A > 0 ? so_agent_conflicts(T, x, sc) : 0);
       if (F) F[p] = l + cfg->alpha * so_pow_int((double)q, cfg->beta);
       if (Q) Q[p] = q;
       if (len) len[p] = l;
@@ -351,7 +384,7 @@ void so_evaluate(const so_config* cfg, const so_scene* sc, int32_t n, const doub
   for (int32_t p = 0; p < n; ++p) {
     const double* x = X + (int64_t)p * D;
     double l = so_length(T, x, sc->sx, sc->sy, sc->tx, sc->ty);
-    int32_t q = so_collisions(T, x, sc);
+    int32_t q = so_collisions(T, x, sc) + (sc->A > 0 ? so_agent_conflicts(T, x, sc) : 0);
     if (F) F[p] = l + cfg->alpha * so_pow_int((double)q, cfg->beta);
     if (Q) Q[p] = q;
     if (len) len[p] = l;

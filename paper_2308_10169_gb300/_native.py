@@ -210,6 +210,9 @@ SIGNATURES = {
                                           _vp, _i32, _vp, _i32, _vp, _i32, ctypes.POINTER(GemmExtra), _i32,
                                           _vp]),
     "sepso_exchange_form": (ctypes.c_int, [_vp]),
+    "sepso_batch_set_teams": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.c_float]),
+    "sepso_batch_next_round": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "sepso_set_polygons": (ctypes.c_int, [_vp, _fp, _fp, _fp, _i32, ctypes.POINTER(ctypes.c_int32), _i32]),
     "sepso_get_polygons": (ctypes.c_int, [_vp, _fp, _fp, _fp, _fp]),
     "sepso_philox": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_uint64, _vp, _vp]),

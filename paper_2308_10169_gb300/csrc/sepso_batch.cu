@@ -317,6 +317,9 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchParams p, int 
       float len;
       int qq;
       group_fitness_pairs(sX + (live ? i : 0) * D, live, lp, T, split, K, sx, sy, tx, ty, sC, sNr2, &len, &qq);
+      if (S.nteam > 1)  // the team mates' paths as moving obstacles
+        qq += agent_conflicts(sX + (live ? i : 0) * D, T, sx, sy, tx, ty, p.agent_rows + (long long)S.team0 * (p.Dmax + 4),
+                              p.Dmax + 4, S.nteam, s - S.team0, S.sep2, lane);
       int imp = 0, pub = 0;
       float pf = INFINITY;
       int pq = 0;
@@ -419,6 +422,31 @@ __global__ void batch_gate_kernel(const BatchParams p) {
   if (lane == 0) use[s] = ok;
 }
 
+// Timed paths of the agents from the scenes' results: start, the result's
+// waypoints, target (one scene per warp lane group).
+__global__ void agent_rows_kernel(const BatchParams p) {
+  const int ld = p.Dmax + 4;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < (long long)p.nscenes * ld;
+       it += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(it / ld), j = (int)(it - (long long)s * ld);
+    const BatchScene S = p.sc[s];
+    const int T = S.T, P = T + 2;
+    if (j >= 2 * P) continue;
+    const int xy = j / P, k = j - xy * P;  // coordinate, point
+    float v;
+    if (k == 0) v = p.pts[4 * s + xy];
+    else if (k == P - 1) v = p.pts[4 * s + 2 + xy];
+    else v = p.res_wp[S.to + xy * T + (k - 1)];
+    p.agent_rows[(long long)s * ld + j] = v;
+  }
+}
+
+cudaError_t launch_agent_rows(const BatchParams& p, cudaStream_t s) {
+  const long long total = (long long)p.nscenes * (p.Dmax + 4);
+  agent_rows_kernel<<<(int)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_gate(const BatchParams& p, cudaStream_t s) {
   const int threads = 128;
   const int blocks = (p.nscenes * 32 + threads - 1) / threads;
@@ -460,7 +488,7 @@ constexpr int kMinTile = 8;
 
 struct BatchLayout {
   size_t sc, tiles, X, V, P, Pfit, PQ, slots, Gb, Tb, circ, hyper, pts, words, Gfit2, GQ2, Tfit2, TQ2, res_wp, res,
-      stall2, plv2, done, prevT, priorT, prior_use, status, total;
+      stall2, plv2, done, prevT, priorT, prior_use, status, arows, total;
   long long nX, nM, nS, nG, nT, nC, nH, nW, nGS, ntiles_max, Dmax;
 };
 
@@ -528,6 +556,7 @@ BatchLayout batch_layout(const sepso_batch_scene* sc, int32_t n) {
   L.priorT = take((size_t)n * L.Dmax * 4);
   L.prior_use = take((size_t)n * 4);
   L.status = take(4);
+  L.arows = take((size_t)n * (L.Dmax + 4) * 4);  // multi-agent timed paths
   L.total = al256(off);
   return L;
 }
@@ -551,6 +580,8 @@ struct sepso_batch_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0;
+  std::vector<int> team_size;  // per scene, when teams are set
+  float sep2 = 0.0f;
 
   ~sepso_batch_ctx() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -599,6 +630,7 @@ BatchParams batch_params(const sepso_batch_ctx* h) {
   p.agent_prevT = h->at<float>(h->L.prevT);
   p.prior_path = h->at<float>(h->L.priorT);
   p.prior_use = h->at<int32_t>(h->L.prior_use);
+  p.agent_rows = h->at<float>(h->L.arows);
   return p;
 }
 
@@ -747,6 +779,10 @@ int sepso_batch_create(const sepso_batch_scene* scenes, int32_t n, float map_w, 
     d.cycle = c.cycle;
     d.agent = s;  // row of the scene's previous path (PI centre, written by every run)
     d.has_prev = 0;
+    d.team0 = s;
+    d.nteam = 0;
+    d.sep2 = 0.0f;
+    d.pad_team = 0;
     h->Omax = std::max(h->Omax, c.O);
     h->Dmax = std::max(h->Dmax, 2 * c.T);
     h->Gmax = std::max(h->Gmax, c.G);
@@ -894,6 +930,45 @@ int sepso_batch_set_starts(sepso_batch_handle h, const float* prev, const float*
   } else {
     BCUDA(cudaMemsetAsync(h->ws + h->L.prior_use, 0, (size_t)h->n * 4, h->stream));
   }
+  BCUDA(cudaStreamSynchronize(h->stream));
+  return SEPSO_OK;
+}
+
+int sepso_batch_set_teams(sepso_batch_handle h, const int32_t* team_first, const int32_t* team_size, float sep) {
+  if (!h || !team_first || !team_size) return bfail(SEPSO_EINVAL, "NULL argument");
+  if (!(sep >= 0.0f) || !std::isfinite(sep)) return bfail(SEPSO_EINVAL, "sep must be finite and >= 0");
+  for (int s = 0; s < h->n; ++s) {
+    const int f = team_first[s], z = team_size[s];
+    if (z < 1 || f < 0 || f > s || s >= f + z || f + z > h->n)
+      return bfail(SEPSO_EINVAL, "scene %d: team [%d, %d) does not hold it", s, f, f + z);
+    if (team_first[f] != f || team_size[f] != z || h->desc[f].T != h->desc[s].T)
+      return bfail(SEPSO_EINVAL, "scene %d: its team must be contiguous with one T", s);
+  }
+  h->team_size.assign(team_size, team_size + h->n);
+  h->sep2 = sep * sep;
+  for (int s = 0; s < h->n; ++s) {
+    h->desc[s].team0 = team_first[s];
+    h->desc[s].nteam = 0;  // the mates' paths count from the first sepso_batch_next_round
+    h->desc[s].sep2 = h->sep2;
+  }
+  BCUDA(cudaMemcpyAsync(h->ws + h->L.sc, h->desc.data(), h->desc.size() * sizeof(BatchScene), cudaMemcpyHostToDevice,
+                        h->stream));
+  BCUDA(cudaStreamSynchronize(h->stream));
+  return SEPSO_OK;
+}
+
+int sepso_batch_next_round(sepso_batch_handle h, uint32_t cycle) {
+  if (!h) return bfail(SEPSO_EINVAL, "NULL handle");
+  if (h->team_size.empty()) return bfail(SEPSO_ESTATE, "no teams (sepso_batch_set_teams first)");
+  BCUDA(launch_agent_rows(batch_params(h), h->stream));
+  ++h->launches;
+  for (int s = 0; s < h->n; ++s) {
+    h->desc[s].nteam = h->team_size[s];
+    h->desc[s].cycle = cycle;
+    h->desc[s].has_prev = 1;  // each run stores its result as the scene's PI centre
+  }
+  BCUDA(cudaMemcpyAsync(h->ws + h->L.sc, h->desc.data(), h->desc.size() * sizeof(BatchScene), cudaMemcpyHostToDevice,
+                        h->stream));
   BCUDA(cudaStreamSynchronize(h->stream));
   return SEPSO_OK;
 }

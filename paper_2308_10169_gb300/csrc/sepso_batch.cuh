@@ -33,6 +33,11 @@ struct BatchScene {
   uint32_t cycle;  // Philox counter word 2 (low 24 bits): the agent's planning cycle
   int agent;       // row of the warm-start table (-1: none)
   int has_prev;    // the agent has a previous best path
+  // Multi-agent teams (a plain batch or a request: nteam = 0):
+  int team0;       // first scene of this scene's team (scenes team0 .. team0 + nteam - 1)
+  int nteam;       // agents in the team whose paths count, 0 until their first paths exist
+  float sep2;      // squared separation below which two agents conflict
+  int pad_team;
 };
 
 struct BatchParams {
@@ -64,7 +69,41 @@ struct BatchParams {
   // Learned prior (null for the server):
   const float* prior_path;   // Dmax floats per scene: the prior's proposal
   const int32_t* prior_use;  // 1 per scene: the proposal seeds the scene's first n_pr particles
+  // Multi-agent teams (null without teams): per scene its agent's timed path, Dmax + 4
+  // floats: x of start, waypoints, target, then the y's (T + 2 each)
+  float* agent_rows;
 };
+
+// Conflicts of one path with its team mates' timed paths (multi-agent extension):
+// all agents leave their starts together and reach one point of their path per
+// step, straight in between; in step s the relative position moves on a segment,
+// and the pair conflicts when that segment passes closer than sep to the origin.
+// The lanes of a warp take (mate, step) items; returns the warp's sum (all lanes).
+__device__ __forceinline__ int agent_conflicts(const float* x, int T, float sx, float sy, float tx, float ty,
+                                               const float* rows, int ld, int nteam, int self, float sep2,
+                                               int lane) {
+  const int P = T + 2;
+  const int items = nteam * (T + 1);
+  int q = 0;
+  for (int it = lane; it < items; it += 32) {
+    const int b = it / (T + 1);
+    const int s = it - b * (T + 1);
+    if (b == self) continue;
+    const float* w = rows + (long long)b * ld;
+    const float ax = (s == 0) ? sx : x[s - 1];
+    const float ay = (s == 0) ? sy : x[T + s - 1];
+    const float bx = (s == T) ? tx : x[s];
+    const float by = (s == T) ? ty : x[T + s];
+    const float r0x = ax - w[s], r0y = ay - w[P + s];
+    const float dx = (bx - w[s + 1]) - r0x, dy = (by - w[P + s + 1]) - r0y;
+    const float L2 = fmaf(dx, dx, dy * dy);
+    float t = 0.0f;
+    if (L2 > 0.0f) t = fminf(fmaxf(-fmaf(r0x, dx, r0y * dy) / L2, 0.0f), 1.0f);
+    const float px = fmaf(t, dx, r0x), py = fmaf(t, dy, r0y);
+    q += fmaf(px, px, py * py) < sep2;
+  }
+  return __reduce_add_sync(0xffffffffu, q);
+}
 
 struct BatchSmem {
   int circ, X, V, P, R, G, T, Pfit, PQ, Gfit, GQ, Gsrc, total;
@@ -94,5 +133,7 @@ cudaError_t batch_configure(int* smem_optin_out);
 cudaError_t launch_batch_reset(const BatchParams& p, cudaStream_t s);
 cudaError_t launch_batch_iter(const BatchParams& p, int j, int ntiles, int threads, size_t smem, cudaStream_t s);
 cudaError_t launch_batch_gate(const BatchParams& p, cudaStream_t s);
+// Each scene's current result (with its start and target) becomes its agent's timed path.
+cudaError_t launch_agent_rows(const BatchParams& p, cudaStream_t s);
 
 }  // namespace sepso

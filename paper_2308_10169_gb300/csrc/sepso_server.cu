@@ -269,6 +269,7 @@ struct sepso_server_ctx {
     p.done = at<int32_t>(L.done);
     p.agent_prevT = at<float>(L.prevT);
     p.prior_path = nullptr;
+    p.agent_rows = nullptr;
     p.prior_use = nullptr;
     return p;
   }

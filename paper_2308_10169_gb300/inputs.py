@@ -496,8 +496,41 @@ def batch_workload(seed: int = 0, n: int = 4096, T_range=(8, 64), O_range=(16, 1
     return specs, hyper, points, circles
 
 
+def team_workload(seed: int = 0, n_teams: int = 512, A: int = 8, T: int = 8, G: int = 8, N: int = 32, O: int = 16,
+                  max_iters: int = 100, stall_iters: int = 10, ring: float = 170.0):
+    """Multi-agent teams (the paper's stated future work): ``n_teams`` maps of 400 x
+    400, each shared by A agents that swap sides -- agent a starts at angle 2 pi a /
+    A (+ a small jitter) on a circle of radius ``ring`` about the map centre and
+    targets the opposite point, so every path crosses the centre -- among O static
+    circles (centres U[100,300]^2, radii U[8,15]).  Per agent: T waypoints, G x N
+    particles, Table hyper8path rows, AT stall ``stall_iters`` / cap ``max_iters``,
+    PI with ceil(0.25 N) particles from the second round on; Philox key = seed, run
+    id = team * A + a.  Returns (specs, hyper list, points (n, 4), circle list,
+    team_first (n,), team_size (n,))."""
+    rng = np.random.default_rng(8000 + seed)
+    n = n_teams * A
+    specs, hyper, circles = [], [], []
+    points = np.zeros((n, 4), np.float32)
+    n_pi = int(np.ceil(0.25 * N))
+    first = np.repeat(np.arange(n_teams) * A, A).astype(np.int32)
+    size = np.full(n, A, np.int32)
+    for m in range(n_teams):
+        cs = random_circles(rng, O, lo=100.0, hi=300.0, r_lo=8.0, r_hi=15.0)
+        ang0 = rng.uniform(0.0, 2.0 * np.pi)
+        for a in range(A):
+            s = m * A + a
+            th = ang0 + 2.0 * np.pi * a / A + rng.uniform(-0.05, 0.05)
+            points[s] = (200.0 + ring * np.cos(th), 200.0 + ring * np.sin(th),
+                         200.0 - ring * np.cos(th), 200.0 - ring * np.sin(th))
+            specs.append(BatchSceneSpec(T=T, G=G, N=N, O=O, max_iters=max_iters, seed=seed, run_id=s,
+                                        stall_iters=stall_iters, n_pi=n_pi))
+            hyper.append(np.ascontiguousarray(TABLE_HYPER8_PATH[:G], dtype=np.float32))
+            circles.append(cs)
+    return specs, hyper, points, circles, first, size
+
+
 def serving_workload(seed: int = 0, n_agents: int = 2048, T_choices=(8, 20, 40), O_choices=(32, 256),
-                     r_range=(5.0, 25.0), lo: float = 60.0, hi: float = 340.0):
+                     r_range=(3.0, 15.0), lo: float = 60.0, hi: float = 340.0):
     """Agents of the serving workload: each has a T in T_choices, a scene of O in
     O_choices circles (centres U[lo,hi]^2 as in the other workloads, so that the
     start and target start clear; radii U[r_range] x sqrt(32 / O), so that both

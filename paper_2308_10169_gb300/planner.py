@@ -483,6 +483,20 @@ class BatchPlanner:
             ctypes.c_void_p(prior.data_ptr()) if prior is not None else None, ld or self.Dmax,
             hp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if hp is not None else None))
 
+    def set_teams(self, team_first, team_size, sep: float):
+        """Multi-agent teams: scene s's team is scenes [team_first[s], team_first[s] +
+        team_size[s]); agents closer than sep during a step conflict."""
+        f = np.ascontiguousarray(np.asarray(team_first, np.int32).reshape(self.n))
+        z = np.ascontiguousarray(np.asarray(team_size, np.int32).reshape(self.n))
+        self._check(self.lib.sepso_batch_set_teams(self._h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                   z.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                                   ctypes.c_float(sep)))
+
+    def next_round(self, cycle: int):
+        """Each scene's last result becomes its agent's path for the mates and its
+        PI centre; the next run plans round ``cycle``."""
+        self._check(self.lib.sepso_batch_next_round(self._h, ctypes.c_uint32(cycle)))
+
     def prior_used(self) -> int:
         n = ctypes.c_int32()
         self._check(self.lib.sepso_batch_prior_used(self._h, ctypes.byref(n)))
