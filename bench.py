@@ -40,9 +40,9 @@ import numpy as np  # noqa: E402
 
 METRIC = "plans/sec and particle-evals/sec at oracle-matched cost; p50/p99 plan latency"
 UNIT = "plans/s"
-WORKLOAD = ("dynamic SEPSO run: 400x400 map, T=20 (D=40), G=8 x N=170, 64 circles r~U[10,30] "
+WORKLOAD = ("dynamic SEPSO run: 400x400 map, T=20 (D=40), G=8 x N=170, 64 circles r~U[5,15] "
             "(32 static, 32 moving |v|~U[0.5,2]/cycle, wall bounce), start/target drift 1/cycle, "
-            "PI gamma=0.25 + AT stall 10 / cap 300, alpha=30 beta=4, HSEF-evolved (w,C1,C2)")
+            "PI gamma=0.25 + AT stall 10 (tolerance 1.0) / cap 300, alpha=30 beta=4, HSEF-evolved (w,C1,C2)")
 
 # The kernel that runs a planning cycle, by the form of its per-iteration exchange.
 SWARM_KERNEL = {"cluster": "swarm_cluster_kernel", "grid": "swarm_kernel"}

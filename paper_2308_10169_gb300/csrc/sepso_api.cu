@@ -283,18 +283,20 @@ int choose_cluster_shape(sepso_ctx* h, int smem_optin, ItemsFor items_for, Items
   int S0 = c.ctas_per_group > 0 ? c.ctas_per_group : std::max(1, h->num_sms / std::max(1, R * G));
   S0 = std::min(S0, std::min(16, N));
   const int S_lo = c.ctas_per_group > 0 ? S0 : 1;
-  for (int S = S0; S >= S_lo; --S) {
-    const int ppc = (N + S - 1) / S;
-    // X and V are kept twice only when Auto Truncation can stop a plan
-    const ClusterLayout Lc =
-        ClusterLayout::make(obstacle_f4(c.max_obstacles, c.obstacle_kind == SEPSO_OBST_POLYGONS ? 1 : 0), ppc, D,
-                            T, G, c.tw, S, c.at_mode != SEPSO_AT_OFF ? 1 : 0);
-    const size_t smem = (size_t)Lc.total;
-    if (smem + 256 > (size_t)smem_optin) continue;
-    const int items = items_for(ppc);
-    const int ppw = 32 / lp;
-    const int want = items ? 512 : std::min(512, std::max(64, (ppc + ppw - 1) / ppw * 32));
-    for (int threads = (c.threads ? c.threads : want); threads >= 64; threads -= 64) {
+  // Widest CTAs first (one CTA per SM keeps every cluster on its own SMs), then the
+  // most CTAs per group that still fit.
+  const int want = c.threads ? c.threads : 512;
+  for (int threads = want; threads >= 64; threads -= 64) {
+    for (int S = S0; S >= S_lo; --S) {
+      const int ppc = (N + S - 1) / S;
+      // X and V are kept twice only when Auto Truncation can stop a plan
+      const ClusterLayout Lc =
+          ClusterLayout::make(obstacle_f4(c.max_obstacles, c.obstacle_kind == SEPSO_OBST_POLYGONS ? 1 : 0), ppc, D,
+                              T, G, c.tw, S, c.at_mode != SEPSO_AT_OFF ? 1 : 0);
+      const size_t smem = (size_t)Lc.total;
+      if (smem + 256 > (size_t)smem_optin) continue;
+      const int items = items_for(ppc);
+      if (!items && threads > std::max(64, (ppc + 32 / lp - 1) / (32 / lp) * 32)) continue;
       int nc = 0;
       cudaError_t e = cluster_max_active(S, threads, smem, &nc);
       if (e != cudaSuccess) {
@@ -313,8 +315,8 @@ int choose_cluster_shape(sepso_ctx* h, int smem_optin, ItemsFor items_for, Items
         h->cl_grid = R * G * S;
         return SEPSO_OK;
       }
-      if (c.threads) break;
     }
+    if (c.threads) break;
   }
   if (c.exchange == 2)
     return fail(SEPSO_ERANGE, "the cluster form does not fit: %d runs x %d groups", R, G);

@@ -263,6 +263,17 @@ __device__ __forceinline__ void st_peer_f32(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_peer_v4(uint32_t addr, float a, float b, float c, float d) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+// The cluster barrier for a warp that made no remote store this round: its arrival
+// needs no release order (the wait still acquires the other CTAs' stores).
+__device__ __forceinline__ void cluster_barrier_relaxed_arrive() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Every thread of every CTA of the cluster: the release orders this thread's
 // earlier shared-memory stores (local and remote) before the arrival, the acquire
 // makes the other CTAs' stores visible after the wait.
@@ -583,6 +594,17 @@ __device__ __forceinline__ void fitness_items_edges(const float* sX, int nl, int
       seg_len[i * nseg + s] = sqrtf(fmaf(dx, dx, dy * dy));
     }
   }
+}
+
+// A particle's path length from its per-segment lengths seg[0 .. nseg), summed by a
+// whole warp in a fixed order: lane l adds segments l, l + 32, l + 64 in turn, then
+// a butterfly over the lanes.  Every lane returns the same value.
+__device__ __forceinline__ float warp_len_sum(const float* seg, int nseg, int lane) {
+  float v = 0.0f;
+  for (int s = lane; s < nseg; s += 32) v += seg[s];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // float4s of a swarm kernel's obstacle area: the circle-pair blocks, or the edges.

@@ -346,8 +346,8 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
         float len = 0.0f;
         int qq = 0;
         if (p.items) {
-          if (live && lsub == 0) {
-            for (int sg = 0; sg < nseg; ++sg) len += sLen[i * nseg + sg];
+          len = warp_len_sum(sLen + i * nseg, nseg, lane);  // lp = 32: the warp's one particle
+          if (lsub == 0) {
             qq = sQi[i];
             sQi[i] = 0;  // ready for the next iteration (read again only after two barriers)
           }
@@ -612,6 +612,10 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
 // identical results.  Slots of parity k & 1 are rewritten at k + 2, after the
 // cluster barrier of k + 1, which every CTA reaches only after reading them.
 // ---------------------------------------------------------------------------
+// Floats of one exchange slot: D row values, Q, the decision word and the 64-bit key,
+// rounded up to whole 16-byte vectors.
+__host__ __device__ inline int cluster_slot_stride(int D) { return (D + 4 + 3) & ~3; }
+
 __host__ __device__ ClusterLayout ClusterLayout::make(int obst_f4, int ppc, int D, int T, int G, int tw, int S,
                                                       int spec) {
   ClusterLayout s;
@@ -620,8 +624,6 @@ __host__ __device__ ClusterLayout ClusterLayout::make(int obst_f4, int ppc, int 
   off = align_up(off + obst_f4 * 16, 16);  // circle-pair blocks or polygon edges
   s.win = off;
   off = align_up(off + tw * 8, 16);
-  s.xkey = off;
-  off = align_up(off + 2 * S * 8, 16);
   s.rec = off;
   off = align_up(off + G * 8, 16);
   s.X0 = off;
@@ -644,8 +646,8 @@ __host__ __device__ ClusterLayout ClusterLayout::make(int obst_f4, int ppc, int 
   off = align_up(off + ppc * 16, 16);
   s.Gown = off;
   off = align_up(off + D * 4, 16);
-  s.xrow = off;
-  off = align_up(off + 2 * S * (D + 4) * 4, 16);
+  s.xrow = off;  // slots: the candidate row, its Q, the decision word, the key (cluster_slot_stride floats)
+  off = align_up(off + 2 * S * cluster_slot_stride(D) * 4, 16);
   s.Pfit = off;
   off += ppc * 4;
   s.PQ = off;
@@ -735,7 +737,6 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
   const ClusterLayout L = ClusterLayout::make(obstacle_f4(p.Omax, p.poly), p.ppc, p.D, p.T, p.G, p.tw, S, p.spec);
   float4* sPairs = reinterpret_cast<float4*>(smem + L.pairs);
   double* sWin = reinterpret_cast<double*>(smem + L.win);
-  unsigned long long* sXkey = reinterpret_cast<unsigned long long*>(smem + L.xkey);
   uint32_t* sXdec = reinterpret_cast<uint32_t*>(smem + L.xdec);
   float* sXrow = reinterpret_cast<float*>(smem + L.xrow);
   float* sX0 = reinterpret_cast<float*>(smem + L.X0);
@@ -923,38 +924,43 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
       __syncthreads();
     }
     {
+      // In item mode warp 0 leaves the particles to the other warps and reads the
+      // groups' records meanwhile (step 2).
+      const bool skip0 = p.items && nwarps > 1;
       const int lp = p.items ? 32 : p.lp;
       const int ppw = 32 / lp;
       const int lsub = lane & (lp - 1);
-      for (int i0 = warp * ppw; i0 < nl; i0 += nwarps * ppw) {
-        const int i = i0 + lane / lp;
-        const bool live = i < nl;
-        float len = 0.0f;
-        int qq = 0;
-        if (p.items) {
-          if (live && lsub == 0) {
-            for (int sg = 0; sg < nseg; ++sg) len += sLen[i * nseg + sg];
-            qq = sQi[i];
-            sQi[i] = 0;
-          }
-        } else {
-          if (p.poly)
+      const int w0 = skip0 ? warp - 1 : warp, nw = skip0 ? nwarps - 1 : nwarps;
+      if (w0 >= 0) {
+        for (int i0 = w0 * ppw; i0 < nl; i0 += nw * ppw) {
+          const int i = i0 + lane / lp;
+          const bool live = i < nl;
+          float len = 0.0f;
+          int qq = 0;
+          if (p.items) {
+            len = warp_len_sum(sLen + i * nseg, nseg, lane);
+            if (lsub == 0) {
+              qq = sQi[i];
+              sQi[i] = 0;
+            }
+          } else if (p.poly) {
             group_fitness_edges(cX + (live ? i : 0) * D, live, lp, T, p.split, p.O, sx, sy, tx, ty, sPairs, &len,
                                 &qq);
-          else
+          } else {
             group_fitness_pairs(cX + (live ? i : 0) * D, live, lp, T, p.split, K, sx, sy, tx, ty, sPairs, sNr2,
                                 &len, &qq);
-        }
-        if (live && lsub == 0) {
-          const float F = len + p.alpha * powi((float)qq, p.beta);
-          const float pf = sPfit[i];
-          const int imp = F < pf;
-          const float cf = imp ? F : pf;
-          const int cq = imp ? qq : sPQ[i];
-          sF[i] = F;
-          sFQ[i] = qq;
-          sImp[i] = imp;
-          if (cf < gfit) atomicMin(&s_key, best_key(cf, (uint32_t)(n0 + i), (uint32_t)cq));
+          }
+          if (live && lsub == 0) {
+            const float F = len + p.alpha * powi((float)qq, p.beta);
+            const float pf = sPfit[i];
+            const int imp = F < pf;
+            const float cf = imp ? F : pf;
+            const int cq = imp ? qq : sPQ[i];
+            sF[i] = F;
+            sFQ[i] = qq;
+            sImp[i] = imp;
+            if (cf < gfit) atomicMin(&s_key, best_key(cf, (uint32_t)(n0 + i), (uint32_t)cq));
+          }
         }
       }
     }
@@ -973,30 +979,69 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
     }
     __syncthreads();
 
-    // 3. Candidate key, decision word and candidate row into every CTA's slot.
+    // 3. Candidate row, its Q, the decision word and the key into this CTA's slot in
+    // every CTA of the cluster, as 16-byte vectors (the row only when there is a
+    // candidate); only the warps that store remotely arrive with release order.
     const unsigned long long lkey = s_key;
     const uint32_t mydec = s_dec;
-    if (tid < S) {
-      st_peer_u64(peer_addr(sXkey + par * S + q, (uint32_t)tid), lkey);
-      st_peer_u32(peer_addr(sXdec + par * S + q, (uint32_t)tid), mydec);
-    }
-    if (lkey != kKeyEmpty) {
-      const int iw = key_idx(lkey) - n0;
-      const bool wimp = sImp[iw] != 0;
+    const int XS = cluster_slot_stride(D);
+    const int nv = XS / 4;           // vectors per slot
+    const int v_tail = (D + 3) / 4;  // first vector past the row: Q, decision, key live in the slot tail
+    bool pushed = false;
+    {
+      const bool have = lkey != kKeyEmpty;
+      const int iw = have ? key_idx(lkey) - n0 : 0;
+      const bool wimp = have && sImp[iw] != 0;
       const float* src = wimp ? cX + iw * D : sP + iw * D;
-      const int qx = wimp ? sFQ[iw] : sPQ[iw];
-      float* slot = sXrow + (par * S + q) * (D + 4);
-      for (int t = tid; t < S * (D + 1); t += nt) {
-        const int peer = t / (D + 1), j = t - peer * (D + 1);
-        st_peer_f32(peer_addr(slot + j, (uint32_t)peer), j < D ? src[j] : __int_as_float(qx));
+      const int qx = have ? (wimp ? sFQ[iw] : sPQ[iw]) : 0;
+      const int v0 = have ? 0 : (D / 4);  // without a candidate only the vectors holding the tail
+      const int per = nv - v0;
+      float* slot = sXrow + (par * S + q) * XS;
+      for (int t = tid; t < S * per; t += nt) {
+        const int peer = t / per, v = v0 + (t - peer * per);
+        float e[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int j = 4 * v + c;
+          float x = 0.0f;
+          if (j < D) x = src[j];
+          else if (j == D) x = __int_as_float(qx);
+          else if (j == D + 1) x = __uint_as_float(mydec);
+          else if (j == D + 2) x = __uint_as_float((uint32_t)lkey);
+          else if (j == D + 3) x = __uint_as_float((uint32_t)(lkey >> 32));
+          e[c] = x;
+        }
+        st_peer_v4(peer_addr(slot + 4 * v, (uint32_t)peer), e[0], e[1], e[2], e[3]);
+        pushed = true;
       }
+      (void)v_tail;
     }
-    cluster_barrier();
+    if (__any_sync(0xffffffffu, pushed)) cluster_barrier();
+    else cluster_barrier_relaxed_arrive();
     if (tid == 0) s_key = kKeyEmpty;
 
-    // 4. The cluster's decision.
+    // 4. The cluster's decision and best key, reduced by every warp over the S slots.
     uint32_t cdec = 0;
-    for (int s2 = 0; s2 < S; ++s2) cdec = max(cdec, sXdec[par * S + s2]);
+    unsigned long long gkey = kKeyEmpty;
+    int gw = 0;
+    {
+      const float* sl = sXrow + (par * S + (lane < S ? lane : 0)) * XS;
+      if (lane < S) {
+        cdec = __float_as_uint(sl[D + 1]);
+        gkey = ((unsigned long long)__float_as_uint(sl[D + 3]) << 32) | __float_as_uint(sl[D + 2]);
+        gw = lane;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        cdec = max(cdec, __shfl_xor_sync(0xffffffffu, cdec, o));
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, gkey, o);
+        const int ow = __shfl_xor_sync(0xffffffffu, gw, o);
+        if (ok < gkey || (ok == gkey && ow < gw)) {
+          gkey = ok;
+          gw = ow;
+        }
+      }
+    }
     if (cdec >= 2) {
       failed = true;
       if (tid == 0) ctl->status = SEPSO_ETIMEOUT;
@@ -1009,30 +1054,11 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
       break;
     }
 
-    // 5. Pbest, the group's Gbest, its record; then the update.
-    for (int it = tid; it < nl * D; it += nt) {
-      const int i = it / D;
-      if (sImp[i]) sP[it] = cX[it];
-    }
-    for (int i = tid; i < nl; i += nt) {
-      if (sImp[i]) {
-        sPfit[i] = sF[i];
-        sPQ[i] = sFQ[i];
-      }
-    }
-    unsigned long long gkey = kKeyEmpty;
-    int gw = 0;
-    for (int s2 = 0; s2 < S; ++s2) {
-      const unsigned long long kk = sXkey[par * S + s2];
-      if (kk < gkey) {
-        gkey = kk;
-        gw = s2;
-      }
-    }
+    // 5. The group's Gbest and its record; Pbest and the update (one pass).
     const float* grow = sG;  // this iteration's Gbest row
     const bool gimp = gkey != kKeyEmpty && key_fit(gkey) < gfit;
     if (gimp) {
-      grow = sXrow + (par * S + gw) * (D + 4);
+      grow = sXrow + (par * S + gw) * XS;
       gfit = key_fit(gkey);
       gq = __float_as_int(grow[D]);
     }
@@ -1042,12 +1068,21 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
       if (tid == 0) st_relaxed_u64(grec + (size_t)(gk % (unsigned long long)kRecDepth) * G + g, make_rec(gfit, gq, gk));
     }
     gk_last = gk;
+    for (int i = tid; i < nl; i += nt) {
+      if (sImp[i]) {
+        sPfit[i] = sF[i];
+        sPQ[i] = sFQ[i];
+      }
+    }
     if (p.mode == kModePlan && k >= p.max_iters) {  // the cap: Algorithm 1 stops before the update
+      for (int it = tid; it < nl * D; it += nt)
+        if (sImp[it / D]) sP[it] = cX[it];
       capstop = true;
       break;
     }
 
-    // Eq. TOF_omega, Eq. TOF_V (+ clip to V_range), Eq. TOF_X (+ clip to X_range).
+    // Eq. TOF_omega, Eq. TOF_V (+ clip to V_range), Eq. TOF_X (+ clip to X_range),
+    // with the Pbest rows of this iteration (each element by the thread that updates it).
     float* nX = p.spec ? (xb ? sX0 : sX1) : cX;
     float* nV = p.spec ? (xb ? sV0 : sV1) : cV;
     const float w = w_init - (w_init - w_end) / (float)p.max_iters * (float)k;
@@ -1055,6 +1090,7 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
       const int i = it / D;
       const int j = it - i * D;
       const float x = cX[it];
+      if (sImp[i]) sP[it] = x;
       float v = w * cV[it];
       v = fmaf(sR[i * 4 + 0], sP[it] - x, v);
       v = fmaf(sR[i * 4 + 1], grow[j] - x, v);
@@ -1065,10 +1101,11 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
       nX[it] = fminf(fmaxf(x + v, 0.0f), ext);
     }
     if (p.spec) xb ^= 1;
-    if (gimp) {
-      __syncthreads();  // every thread has read grow from the slot
+    // the next iterations read this Gbest row from sG; nobody reads sG in this one
+    // when it changed (the update above read the slot), and the slot stays valid
+    // until the next cluster barrier
+    if (gimp)
       for (int j = tid; j < D; j += nt) sG[j] = grow[j];
-    }
     __syncthreads();
     if (p.mode == kModeStep && done >= p.step_iters) {  // a plain continuation ends after the update
       capstop = true;
