@@ -447,6 +447,31 @@ def run_ours(args, rank, world, local):
     flops = iters * cfg.G * cfg.N * (cfg.T + 1) * (FLOPS_PER_PAIR * scene.O + FLOPS_PER_SEGMENT)
     achieved = flops / (plan_ms.sum() / 1e3) / 1e12
 
+    # -- the two forms of the per-iteration exchange on the same cycles -----------
+    forms = {}
+    for name, ex in (("grid", 1), ("cluster", 2)):
+        try:
+            fp = Planner(cfg.with_(exchange=ex), device=dev)
+        except Exception as e:  # the cluster form may not fit a device
+            forms[name] = {"error": str(e)[:120]}
+            continue
+        fp.set_hyper(app_hyper)
+        fp.set_scene(scene)
+        for _ in range(3):
+            fp.plan_async()
+        fp.sync()
+        i0 = fp.counters()[1]
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(30):
+            fp.advance(1)
+            fp.plan_async()
+        f1.record(stream)
+        fp.sync()
+        forms[name] = {"us_per_iteration": 1e3 * f0.elapsed_time(f1) / max(fp.counters()[1] - i0, 1),
+                       "launch": fp.launch_shape()}
+        del fp
+
     # -- end to end through the C ABI with host buffers ----------------------------
     Ke = args.e2e_steps or K
     e2e = run_e2e(torch, pl, cfg, scene, app_hyper, dev, Ke, W)
@@ -478,6 +503,8 @@ def run_ours(args, rank, world, local):
                          "kernel": SWARM_KERNEL[shape["exchange"]],
                          "peak_source": peak_src},
             "e2e": e2e,
+            "exchange_forms": dict(forms, note="30 cycles each, device time per iteration (scene advance "
+                                               "included), same hyper-parameters and scene"),
             "gpu_launches": int(launches),
             "clocks": clocks,
             "hsef": hsef_info,

@@ -92,16 +92,16 @@ typedef struct {
                              (particle, segment, circle chunk) items spread over
                              all threads of a CTA                                  */
   int32_t exchange;       /* how the CTAs of a run trade their bests each
-                             iteration: 0 = automatic (the cluster form whenever
-                             every group's C3 is 0 and it fits, else the
-                             grid-wide form); 1 = grid-wide: one barrier of all
+                             iteration: 0 = automatic (the grid-wide form, the
+                             faster on GB300); 1 = grid-wide: one barrier of all
                              the run's CTAs per iteration; 2 = cluster form: the
                              CTAs of a group form one thread-block cluster and
                              trade through distributed shared memory, groups
                              trade only (Gfit, Q) through global memory, read one
                              iteration later (needs C3 = 0 in every group: Eq.
                              TOF_V then uses the own group's Gbest alone).  Both
-                             forms give identical results.                        */
+                             forms give identical results.  3 = the cluster form
+                             whenever every group's C3 is 0, else grid-wide.     */
   int32_t obstacle_kind;  /* SEPSO_OBST_*: circles (sepso_set_scene) or polygon
                              edges (sepso_set_polygons); for polygons
                              max_obstacles is the edge capacity                   */
@@ -644,8 +644,8 @@ int sepso_launch_shape(sepso_handle h, int32_t* ctas_per_group, int32_t* threads
                        int32_t* circle_split, int32_t* grid);
 
 /* The form of the exchange the next plan or step launches: 2 = one thread-block
- * cluster per group (every group's C3 is 0 and the cluster form fits), 1 = the
- * grid-wide barrier (sepso_config.exchange).  Negative on a bad handle. */
+ * cluster per group (exchange 2 or 3, every group's C3 is 0 and the cluster form
+ * fits), 1 = the grid-wide barrier.  Negative on a bad handle. */
 int sepso_exchange_form(sepso_handle h);
 
 /* Cumulative counters of run `run` (host outputs, sync): planning cycles

@@ -127,7 +127,7 @@ int check_config(const sepso_config* c) {
     return fail(SEPSO_EINVAL, "threads=%d must be 0 or a multiple of 32 in [64, 512]", c->threads);
   if (c->circle_split < 0) return fail(SEPSO_EINVAL, "circle_split < 0");
   if (c->fitness_mode < 0 || c->fitness_mode > 2) return fail(SEPSO_EINVAL, "fitness_mode must be 0, 1 or 2");
-  if (c->exchange < 0 || c->exchange > 2) return fail(SEPSO_EINVAL, "exchange must be 0, 1 or 2");
+  if (c->exchange < 0 || c->exchange > 3) return fail(SEPSO_EINVAL, "exchange must be 0, 1, 2 or 3");
   if (c->obstacle_kind != SEPSO_OBST_CIRCLES && c->obstacle_kind != SEPSO_OBST_POLYGONS)
     return fail(SEPSO_EINVAL, "obstacle_kind=%d unknown", c->obstacle_kind);
   return SEPSO_OK;
@@ -234,10 +234,14 @@ SwarmParams swarm_params(const sepso_ctx* h, int mode, int step_iters) {
   return p;
 }
 
-// The cluster form runs when it fits and no run's update needs Tbest (C3 = 0 in
-// every group); exchange = 1 / 2 force one form.
+// The cluster form runs when it is asked for (exchange = 2), it fits and no run's
+// update needs Tbest (C3 = 0 in every group).  The automatic choice is the grid-wide
+// form: measured on GB300 the two forms take the same time per iteration of the
+// dynamic workload (5.5 us), both bound by a per-iteration synchronisation floor that
+// remains without any pair test, and the grid-wide form spreads the fitness over
+// every SM.
 bool use_cluster(const sepso_ctx* h) {
-  if (h->cfg.exchange == 1 || !h->cl_ok) return false;
+  if (h->cfg.exchange < 2 || !h->cl_ok) return false;
   for (char nz : h->c3_nonzero)
     if (nz) return false;
   return true;
@@ -277,7 +281,7 @@ int choose_cluster_shape(sepso_ctx* h, int smem_optin, ItemsFor items_for, Items
                          int split) {
   const sepso_config& c = h->cfg;
   h->cl_ok = false;
-  if (c.exchange == 1) return SEPSO_OK;
+  if (c.exchange < 2) return SEPSO_OK;
   const int R = c.runs, G = c.G, N = c.N, T = c.T, D = 2 * T;
   CUDA_TRY(configure_cluster_kernel((size_t)smem_optin));
   int S0 = c.ctas_per_group > 0 ? c.ctas_per_group : std::max(1, h->num_sms / std::max(1, R * G));

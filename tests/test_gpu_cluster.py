@@ -111,7 +111,7 @@ def test_cluster_form_several_runs_and_switching_forms(native):
     cfg, scene, hyper = dynamic_workload(4)
     cfg = cfg.with_(runs=4, max_iters=60)
     ref = Planner(cfg.with_(exchange=1))
-    mix = Planner(cfg)
+    mix = Planner(cfg.with_(exchange=3))
     hyper_c3 = hyper.copy()
     hyper_c3[:, 2] = 0.5
     for pl in (ref, mix):
@@ -159,9 +159,10 @@ def test_cluster_form_refused_when_an_update_needs_tbest(native):
     with pytest.raises(SepsoError) as err:
         pl.plan()
     assert err.value.code == -1  # SEPSO_EINVAL
-    auto = Planner(cfg)
+    auto = Planner(cfg.with_(exchange=3))
     auto.set_scene(scene)
     auto.set_hyper(hy)
     assert auto.exchange_form() == "grid"
     auto.set_hyper(sample_hyper(3, cfg.G))
     assert auto.exchange_form() == "cluster"
+    assert Planner(cfg).exchange_form() == "grid"   # the automatic choice
