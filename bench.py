@@ -81,7 +81,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one swarm_kernel launch of this
 # workload (ncu --set full capture summarised in profiles/swarm_kernel_dynamic_workload.md);
 # set to None whenever the kernel changes until it is captured again.
-SWARM_TRAFFIC_BYTES = 157184
+SWARM_TRAFFIC_BYTES = 117504
 # The same for gemm_tc_kernel on the MLP's grad-W1 product (1024 x 4104 x 4096),
 # profiles/gemm_tc_kernel_mlp_gradW1.md.
 GEMM_GRADW1_TRAFFIC_BYTES = 42132480
@@ -594,6 +594,12 @@ def run_batch(n: int, iters: int):
             "shape": bp.shape(), "autotune_ms_per_launch": tune_ms,
             "gpu_launches": bp.launch_count() - l0,
             "median_cost": float(np.median([r["cost"] for r in res])),
+            "collision_free": float(np.mean([r["Q"] == 0 for r in res])),
+            "collision_free_by_circles": {f"O<={hi}": float(np.mean([r["Q"] == 0 for r, sp in zip(res, specs)
+                                                                     if lo < sp.O <= hi]))
+                                          for lo, hi in ((0, 64), (64, 256), (256, 1024))},
+            "quality_note": "radii U[5,30] (the configuration's) with up to 1024 circles on 400x400: "
+                            "the dense scenes admit no collision-free path",
             "l2": f"inputs larger than L2 ({bp.workspace.numel() / 1e9:.1f} GB of batch state)"}
 
 
@@ -934,6 +940,9 @@ def run_serve(rate: float, seconds: float, n_agents: int = 2048, radii=(3.0, 15.
             "iters_per_plan": float(np.mean([d["iters"] for d in done])),
             "median_cost": float(np.median([d["cost"] for d in done])),
             "collision_free": float(np.mean([d["Q"] == 0 for d in done])),
+            "collision_free_by_T_O": {f"T{T}_O{O}": float(np.mean([d["Q"] == 0 for d in done
+                                                                  if d["T"] == T and agents[d["agent"]]["O"] == O]))
+                                      for T in (8, 20, 40) for O in (32, 256)},
             "at_fire_rate": float(np.mean([d["iters"] < 100 for d in done])), "slots": st["slots"],
             "ticks": st["ticks"], "gpu_launches": st["launches"]}
 
@@ -1163,14 +1172,19 @@ def cost_match_dynamic(seeds: int = 64, cycles: int = 2):
         ora = pool.map(_oracle_seed_worker, [(s_, cycles) for s_ in range(seeds)], chunksize=1)
     t_ora = time.perf_counter() - t0
     per = []
+    rng = np.random.default_rng(0)
     for cyc in range(cycles):
         g = [row[cyc] for row in gpu]
         o = [row[cyc] for row in ora]
-        gm, om = float(np.median([x[0] for x in g])), float(np.median([x[0] for x in o]))
+        gc, oc = np.array([x[0] for x in g]), np.array([x[0] for x in o])
+        gm, om = float(np.median(gc)), float(np.median(oc))
+        # the spread of the two medians over the seeds: a bootstrap of both samples
+        boot = [(np.median(rng.choice(gc, gc.size)) - np.median(rng.choice(oc, oc.size))) / om for _ in range(2000)]
         per.append({"cycle": cyc,
                     "gpu": plan_stats([x[1] for x in g], [x[0] for x in g], [x[2] for x in g], cfg.max_iters),
                     "oracle": plan_stats([x[1] for x in o], [x[0] for x in o], [x[2] for x in o], cfg.max_iters),
-                    "rel_diff_median_cost": (gm - om) / om})
+                    "rel_diff_median_cost": (gm - om) / om,
+                    "rel_diff_bootstrap_95": [float(np.percentile(boot, 2.5)), float(np.percentile(boot, 97.5))]})
     return {"workload": "the headline dynamic run's first cycles, shared hyper-parameters",
             "seeds": seeds, "cycles": per, "gpu_seconds": t_gpu,
             "oracle_seconds": t_ora, "oracle_processes": P}
