@@ -78,10 +78,10 @@ def _max_sm_mhz() -> float:
 # segment-circle test x O circles + 8 flops of length), per the scope table.
 FLOPS_PER_PAIR, FLOPS_PER_SEGMENT = 18, 8
 L2_FLUSH_BYTES = 256 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one swarm_kernel launch of this
-# workload (ncu --set full capture summarised in profiles/swarm_kernel_dynamic_workload.md);
-# set to None whenever the kernel changes until it is captured again.
-SWARM_TRAFFIC_BYTES = 117504
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of each planning kernel
+# on this workload (ncu --set full captures summarised in profiles/); None whenever
+# the kernel changed since its capture.
+SWARM_TRAFFIC_BYTES = {"swarm_kernel": 117504, "swarm_cluster_kernel": None}
 # The same for gemm_tc_kernel on the MLP's grad-W1 product (1024 x 4104 x 4096),
 # profiles/gemm_tc_kernel_mlp_gradW1.md.
 GEMM_GRADW1_TRAFFIC_BYTES = 42132480
@@ -499,7 +499,7 @@ def run_ours(args, rank, world, local):
             if costs else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": SWARM_TRAFFIC_BYTES,
+                         "traffic": SWARM_TRAFFIC_BYTES.get(SWARM_KERNEL[shape["exchange"]]),
                          "kernel": SWARM_KERNEL[shape["exchange"]],
                          "peak_source": peak_src},
             "e2e": e2e,

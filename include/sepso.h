@@ -45,6 +45,7 @@ extern "C" {
 #define SEPSO_ETIMEOUT (-5) /* a device-side wait gave up (bounded spin)         */
 #define SEPSO_ENOMEM (-6)   /* host allocation failed                            */
 #define SEPSO_ERANGE (-7)   /* shape exceeds a kernel limit (shared memory etc.) */
+#define SEPSO_EBOUNDS (-8)  /* a device-side index check failed (access skipped)  */
 
 /* Auto Truncation modes (Sec. 3.3.4). */
 #define SEPSO_AT_OFF 0          /* run to max_iters                                  */
@@ -92,16 +93,20 @@ typedef struct {
                              (particle, segment, circle chunk) items spread over
                              all threads of a CTA                                  */
   int32_t exchange;       /* how the CTAs of a run trade their bests each
-                             iteration: 0 = automatic (the grid-wide form, the
-                             faster on GB300); 1 = grid-wide: one barrier of all
-                             the run's CTAs per iteration; 2 = cluster form: the
-                             CTAs of a group form one thread-block cluster and
-                             trade through distributed shared memory, groups
-                             trade only (Gfit, Q) through global memory, read one
-                             iteration later (needs C3 = 0 in every group: Eq.
-                             TOF_V then uses the own group's Gbest alone).  Both
-                             forms give identical results.  3 = the cluster form
-                             whenever every group's C3 is 0, else grid-wide.     */
+                             iteration: 1 = grid-wide: one barrier of all the
+                             run's CTAs per iteration; 2 = cluster form: the CTAs
+                             of a group form one thread-block cluster (one warp
+                             per particle, rows in registers) and trade through
+                             distributed shared memory, groups trade only
+                             (Gfit, Q) through global memory, read two
+                             iterations later (needs C3 = 0 in every group: Eq.
+                             TOF_V then uses the own group's Gbest alone, and a
+                             config that fits: T + 1 <= 32, G <= 32, at most 15
+                             particles per CTA of at most 16 per group, every
+                             group resident at once).  Both forms give identical
+                             results.  0 (automatic) and 3 = the cluster form
+                             whenever every group's C3 is 0 and it fits, else
+                             grid-wide.                                          */
   int32_t obstacle_kind;  /* SEPSO_OBST_*: circles (sepso_set_scene) or polygon
                              edges (sepso_set_polygons); for polygons
                              max_obstacles is the edge capacity                   */
@@ -639,13 +644,14 @@ int sepso_gemm_bf16_ex(const void* A, const void* B, int32_t M, int32_t N, int32
 int sepso_sync(sepso_handle h);
 
 /* Launch shape chosen at create, of the form the next plan or step launches
- * (see sepso_exchange_form): CTAs per group, threads, circle split, grid. */
+ * (see sepso_exchange_form): CTAs per group, threads, circle split (1 in the
+ * cluster form: each lane tests whole obstacles), grid. */
 int sepso_launch_shape(sepso_handle h, int32_t* ctas_per_group, int32_t* threads,
                        int32_t* circle_split, int32_t* grid);
 
 /* The form of the exchange the next plan or step launches: 2 = one thread-block
- * cluster per group (exchange 2 or 3, every group's C3 is 0 and the cluster form
- * fits), 1 = the grid-wide barrier.  Negative on a bad handle. */
+ * cluster per group (exchange 0, 2 or 3, every group's C3 is 0 and the cluster
+ * form fits), 1 = the grid-wide barrier.  Negative on a bad handle. */
 int sepso_exchange_form(sepso_handle h);
 
 /* Cumulative counters of run `run` (host outputs, sync): planning cycles

@@ -15,7 +15,7 @@ _lib = None
 
 SEPSO_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ESTATE", -3: "ENOSPC", -4: "ECUDA", -5: "ETIMEOUT", -6: "ENOMEM",
-          -7: "ERANGE"}
+          -7: "ERANGE", -8: "EBOUNDS"}
 
 
 class SepsoError(RuntimeError):

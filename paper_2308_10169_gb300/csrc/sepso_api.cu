@@ -149,7 +149,7 @@ struct sepso_ctx {
   size_t smem = 0;
   // cluster form (one thread-block cluster of cl_S CTAs per group), when it fits
   bool cl_ok = false;
-  int cl_S = 1, cl_ppc = 1, cl_threads = 256, cl_split = 1, cl_lp = 32, cl_items = 0, cl_grid = 1;
+  int cl_S = 1, cl_ppc = 1, cl_threads = 64, cl_grid = 1;
   size_t cl_smem = 0;
   std::vector<char> c3_nonzero;  // per run: some group's C3 is not 0 (the update then needs Tbest)
   bool grec_dirty = false;       // group records not written by the last launches (clear before use)
@@ -228,20 +228,16 @@ SwarmParams swarm_params(const sepso_ctx* h, int mode, int step_iters) {
   p.counter = h->at<RunCounter>(h->L.counter);
   p.crows = h->at<float>(h->L.crows);
   p.grec = h->at<unsigned long long>(h->L.grec);
-  p.spec = 0;
   p.cta_grid = h->C;
   p.poly = c.obstacle_kind == SEPSO_OBST_POLYGONS ? 1 : 0;
   return p;
 }
 
-// The cluster form runs when it is asked for (exchange = 2), it fits and no run's
-// update needs Tbest (C3 = 0 in every group).  The automatic choice is the grid-wide
-// form: measured on GB300 the two forms take the same time per iteration of the
-// dynamic workload (5.5 us), both bound by a per-iteration synchronisation floor that
-// remains without any pair test, and the grid-wide form spreads the fitness over
-// every SM.
+// The cluster form runs when it fits, no run's update needs Tbest (C3 = 0 in every
+// group) and the config asks for it: exchange = 2 (required), 3 or 0 (whenever it
+// applies).
 bool use_cluster(const sepso_ctx* h) {
-  if (h->cfg.exchange < 2 || !h->cl_ok) return false;
+  if (h->cfg.exchange == 1 || !h->cl_ok) return false;
   for (char nz : h->c3_nonzero)
     if (nz) return false;
   return true;
@@ -265,42 +261,45 @@ int launch_plan_kernel(sepso_ctx* h, SwarmParams p) {
   p.cpg = h->cl_S;
   p.C = h->cfg.G * h->cl_S;
   p.ppc = h->cl_ppc;
-  p.split = h->cl_split;
-  p.lp = h->cl_lp;
-  p.items = h->cl_items;
-  p.spec = (p.mode == kModePlan && p.at_mode != SEPSO_AT_OFF) ? 1 : 0;
   CUDA_TRY(launch_swarm_cluster(p, h->cl_grid, h->cl_threads, h->cl_smem, h->stream));
   return SEPSO_OK;
 }
 
-// The cluster form: S CTAs per group in one cluster (at most 16), from one CTA
-// per SM down; every cluster of the launch must be resident at once (the groups of
-// a run wait on each other's records), which the occupancy query checks.
-template <class ItemsFor, class ItemsSplit>
-int choose_cluster_shape(sepso_ctx* h, int smem_optin, ItemsFor items_for, ItemsSplit items_split, int lp,
-                         int split) {
+// The cluster form: S CTAs per group in one cluster (at most 16), each with one
+// warp per particle and a control warp, so ceil(N / S) <= kClusterMaxThreads / 32 - 1
+// particles per CTA; rows live in registers, so T + 1 <= 32 and G <= 32.  Every
+// cluster of the launch must be resident at once (the groups of a run wait on each
+// other's records), which the occupancy query checks.  The most CTAs per group
+// first, with one CTA per SM (the shared-memory request is raised above half an
+// SM's, so that no two CTAs share an SM's issue slots), then without that rule.
+int choose_cluster_shape(sepso_ctx* h, int smem_optin) {
   const sepso_config& c = h->cfg;
   h->cl_ok = false;
-  if (c.exchange < 2) return SEPSO_OK;
-  const int R = c.runs, G = c.G, N = c.N, T = c.T, D = 2 * T;
+  if (c.exchange == 1) return SEPSO_OK;
+  const int R = c.runs, G = c.G, N = c.N, T = c.T;
+  const int max_ppc = kClusterMaxThreads / 32 - 1;
+  auto no_fit = [&](const char* why) {
+    return c.exchange == 2 ? fail(SEPSO_ERANGE, "the cluster form does not fit: %s", why) : SEPSO_OK;
+  };
+  if (T + 1 > 32 || G > 32) return no_fit("it takes T + 1 <= 32 and G <= 32");
+  int smem_sm = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
   CUDA_TRY(configure_cluster_kernel((size_t)smem_optin));
-  int S0 = c.ctas_per_group > 0 ? c.ctas_per_group : std::max(1, h->num_sms / std::max(1, R * G));
-  S0 = std::min(S0, std::min(16, N));
+  const int S_hi = std::min(16, N);
+  int S0 = c.ctas_per_group > 0 ? c.ctas_per_group : std::min(S_hi, std::max(1, h->num_sms / std::max(1, R * G)));
+  S0 = std::min(S0, S_hi);
   const int S_lo = c.ctas_per_group > 0 ? S0 : 1;
-  // Widest CTAs first (one CTA per SM keeps every cluster on its own SMs), then the
-  // most CTAs per group that still fit.
-  const int want = c.threads ? c.threads : 512;
-  for (int threads = want; threads >= 64; threads -= 64) {
+  const bool poly = c.obstacle_kind == SEPSO_OBST_POLYGONS;
+  for (int pass = 0; pass < 2; ++pass) {
     for (int S = S0; S >= S_lo; --S) {
       const int ppc = (N + S - 1) / S;
-      // X and V are kept twice only when Auto Truncation can stop a plan
-      const ClusterLayout Lc =
-          ClusterLayout::make(obstacle_f4(c.max_obstacles, c.obstacle_kind == SEPSO_OBST_POLYGONS ? 1 : 0), ppc, D,
-                              T, G, c.tw, S, c.at_mode != SEPSO_AT_OFF ? 1 : 0);
-      const size_t smem = (size_t)Lc.total;
+      if (ppc > max_ppc) break;
+      if ((N + ppc - 1) / ppc != S) continue;  // no empty CTAs
+      const int threads = 32 * (ppc + 1);
+      const ClusterLayout Lc = ClusterLayout::make(obstacle_f4(c.max_obstacles, poly ? 1 : 0), ppc, T, c.tw, S);
+      size_t smem = (size_t)Lc.total;
+      if (pass == 0) smem = std::max(smem, (size_t)smem_sm / 2 + 1024);
       if (smem + 256 > (size_t)smem_optin) continue;
-      const int items = items_for(ppc);
-      if (!items && threads > std::max(64, (ppc + 32 / lp - 1) / (32 / lp) * 32)) continue;
       int nc = 0;
       cudaError_t e = cluster_max_active(S, threads, smem, &nc);
       if (e != cudaSuccess) {
@@ -312,19 +311,13 @@ int choose_cluster_shape(sepso_ctx* h, int smem_optin, ItemsFor items_for, Items
         h->cl_S = S;
         h->cl_ppc = ppc;
         h->cl_threads = threads;
-        h->cl_split = items ? items_split(threads, ppc) : split;
-        h->cl_lp = items ? 32 : lp;
-        h->cl_items = items;
         h->cl_smem = smem;
         h->cl_grid = R * G * S;
         return SEPSO_OK;
       }
     }
-    if (c.threads) break;
   }
-  if (c.exchange == 2)
-    return fail(SEPSO_ERANGE, "the cluster form does not fit: %d runs x %d groups", R, G);
-  return SEPSO_OK;
+  return no_fit("no cluster size fits every group of every run at once");
 }
 
 // Pick CTAs per group, threads and circle split, then check co-residency: the
@@ -387,7 +380,7 @@ int choose_shape(sepso_ctx* h) {
         h->items = items;
         h->smem = smem;
         h->grid = R * G * cpg;
-        return choose_cluster_shape(h, smem_optin, items_for, items_split, lp, split);
+        return choose_cluster_shape(h, smem_optin);
       }
       if (c.threads) break;
     }
@@ -462,6 +455,7 @@ const char* sepso_strerror(int code) {
     case SEPSO_ETIMEOUT: return "device-side wait timed out";
     case SEPSO_ENOMEM: return "host allocation failed";
     case SEPSO_ERANGE: return "shape exceeds a kernel limit";
+    case SEPSO_EBOUNDS: return "a device-side index check failed";
     default: return "unknown status";
   }
 }
@@ -1003,7 +997,7 @@ int sepso_launch_shape(sepso_handle h, int32_t* ctas_per_group, int32_t* threads
   const bool cl = use_cluster(h);
   if (ctas_per_group) *ctas_per_group = cl ? h->cl_S : h->cpg;
   if (threads) *threads = cl ? h->cl_threads : h->threads;
-  if (circle_split) *circle_split = cl ? h->cl_split : h->split;
+  if (circle_split) *circle_split = cl ? 1 : h->split;
   if (grid) *grid = cl ? h->cl_grid : h->grid;
   return SEPSO_OK;
 }

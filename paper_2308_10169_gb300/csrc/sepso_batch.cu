@@ -57,12 +57,31 @@ __global__ void batch_reset_kernel(const BatchParams p) {
   }
 }
 
+// A failed device-side index check: the first one is recorded (status[1..3]: the
+// check, the scene or work item, the index) and the access it guards is skipped.
+__device__ __forceinline__ void batch_check_failed(int* status, int site, int a, int b) {
+  if (atomicCAS(status + 1, 0, site) == 0) {
+    status[2] = a;
+    status[3] = b;
+  }
+  atomicCAS(status, 0, SEPSO_EBOUNDS);
+}
+
 __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchParams p, int j) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t s_mbar;
   const int4 tl = p.tiles[blockIdx.x];
   const int s = tl.x, g = tl.y, n0 = tl.z, nl = tl.w;
+  if (s < 0 || s >= p.nscenes) {
+    if (threadIdx.x == 0) batch_check_failed(p.status, 1, (int)blockIdx.x, s);
+    return;
+  }
   const BatchScene S = p.sc[s];
+  if (g < 0 || g >= S.G || n0 < 0 || nl < 1 || nl > p.tile || n0 + nl > S.N || S.D > p.Dmax || S.G > p.Gmax ||
+      S.O > p.Omax) {
+    if (threadIdx.x == 0) batch_check_failed(p.status, 2, s, (int)blockIdx.x);
+    return;
+  }
   const int jl = j - S.j0;  // this launch is the scene's jl-th
   if (jl < 1 || jl > S.max_iters + 1) return;  // not started, or finished
   if (p.done != nullptr && p.done[s]) return;   // truncated earlier
@@ -156,7 +175,11 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchParams p, int 
       float gf = oGfit[gg];
       int gq = oGQ[gg];
       int src = -1;
-      const unsigned long long key = wk[gg];
+      unsigned long long key = wk[gg];
+      if (key != kKeyEmpty && key_idx(key) >= N) {  // every item of the scene sees the same word
+        if (g == 0 && n0 == 0) batch_check_failed(p.status, 3, s, key_idx(key));
+        key = kKeyEmpty;
+      }
       if (key != kKeyEmpty && key_fit(key) < gf) {
         gf = key_fit(key);
         src = gg * N + key_idx(key);
@@ -555,7 +578,7 @@ BatchLayout batch_layout(const sepso_batch_scene* sc, int32_t n) {
   L.prevT = take((size_t)n * L.Dmax * 4);
   L.priorT = take((size_t)n * L.Dmax * 4);
   L.prior_use = take((size_t)n * 4);
-  L.status = take(4);
+  L.status = take(16);  // status, then the first failed index check: site, scene, index
   L.arows = take((size_t)n * (L.Dmax + 4) * 4);  // multi-agent timed paths
   L.total = al256(off);
   return L;
@@ -1023,10 +1046,12 @@ int sepso_batch_read(sepso_batch_handle h, float* waypoints, sepso_result* res) 
   if (res)
     BCUDA(cudaMemcpyAsync(res, h->ws + h->L.res, (size_t)h->n * sizeof(sepso_result), cudaMemcpyDeviceToHost,
                           h->stream));
-  int st = 0;
-  BCUDA(cudaMemcpyAsync(&st, h->ws + h->L.status, 4, cudaMemcpyDeviceToHost, h->stream));
+  int st[4] = {0, 0, 0, 0};
+  BCUDA(cudaMemcpyAsync(st, h->ws + h->L.status, 16, cudaMemcpyDeviceToHost, h->stream));
   BCUDA(cudaStreamSynchronize(h->stream));
-  if (st) return bfail(st, "device-side error in the batch");
+  if (st[0])
+    return bfail(st[0], "device-side error in the batch (index check %d: scene/item %d, index %d)", st[1], st[2],
+                 st[3]);
   return SEPSO_OK;
 }
 

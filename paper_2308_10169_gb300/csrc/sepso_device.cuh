@@ -106,7 +106,6 @@ struct SwarmParams {
   RunCounter* counter;        // R
   float* crows;               // R x 2 x M x (D + 4): candidate row, its Q, padding
   unsigned long long* grec;   // R x kRecDepth x G group records (cluster form)
-  int spec;                   // cluster form: X, V double-buffered (Auto Truncation decided one iteration late)
   int cta_grid;               // CTAs per run of the grid-wide form (its barrier counts C * iterations)
   int poly;                   // obstacles are polygon edges (circ holds O edges as float4), not circles
 };
@@ -426,12 +425,13 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
   return d;
 }
 
-struct PairFrame {
-  unsigned long long ux, uy, nmu, nx, ny, nmn;  // each value in both halves
-  float h;
+// The frame of segment [a, b] as scalars: unit direction, normal n = (-u_y, u_x),
+// the negated projections of the midpoint on both, and the half-length.
+struct FrameScalars {
+  float ux, uy, nmu, nx, ny, nmn, h;
 };
 
-__device__ __forceinline__ PairFrame pair_frame(float ax, float ay, float bx, float by, float* len_out) {
+__device__ __forceinline__ FrameScalars frame_scalars(float ax, float ay, float bx, float by, float* len_out) {
   const float dx = bx - ax, dy = by - ay;
   const float len = sqrtf(fmaf(dx, dx, dy * dy));
   float ux = 1.0f, uy = 0.0f;
@@ -444,16 +444,51 @@ __device__ __forceinline__ PairFrame pair_frame(float ax, float ay, float bx, fl
   const float mu = fmaf(mx, ux, my * uy);
   const float nx = -uy, ny = ux;
   const float mn = fmaf(mx, nx, my * ny);
-  PairFrame f;
-  f.ux = pack2(ux, ux);
-  f.uy = pack2(uy, uy);
-  f.nmu = pack2(-mu, -mu);
-  f.nx = pack2(nx, nx);
-  f.ny = pack2(ny, ny);
-  f.nmn = pack2(-mn, -mn);
+  FrameScalars f;
+  f.ux = ux;
+  f.uy = uy;
+  f.nmu = -mu;
+  f.nx = nx;
+  f.ny = ny;
+  f.nmn = -mn;
   f.h = 0.5f * len;
   *len_out = len;
   return f;
+}
+
+struct PairFrame {
+  unsigned long long ux, uy, nmu, nx, ny, nmn;  // each value in both halves
+  float h;
+};
+
+__device__ __forceinline__ PairFrame pair_frame(float ax, float ay, float bx, float by, float* len_out) {
+  const FrameScalars s = frame_scalars(ax, ay, bx, by, len_out);
+  PairFrame f;
+  f.ux = pack2(s.ux, s.ux);
+  f.uy = pack2(s.uy, s.uy);
+  f.nmu = pack2(s.nmu, s.nmu);
+  f.nx = pack2(s.nx, s.nx);
+  f.ny = pack2(s.ny, s.ny);
+  f.nmn = pack2(s.nmn, s.nmn);
+  f.h = s.h;
+  return f;
+}
+
+// Hits of one circle pair (cx, cy, -r^2 packed per circle) against a packed frame,
+// the arithmetic of pair_hits.
+__device__ __forceinline__ int pair_test(unsigned long long CX, unsigned long long CY, unsigned long long W,
+                                         unsigned long long UX, unsigned long long UY, unsigned long long NMU,
+                                         unsigned long long NX, unsigned long long NY, unsigned long long NMN,
+                                         float h) {
+  const unsigned long long AL = ffma2(CX, UX, ffma2(CY, UY, NMU));
+  const unsigned long long P = ffma2(CX, NX, ffma2(CY, NY, NMN));
+  float al0, al1;
+  unpack2(AL, al0, al1);
+  const float m0 = fmaxf(fabsf(al0) - h, 0.0f), m1 = fmaxf(fabsf(al1) - h, 0.0f);
+  const unsigned long long S = ffma2(pack2(m0, m1), pack2(m0, m1), ffma2(P, P, W));
+  float s0, s1;
+  unpack2(S, s0, s1);
+  return (int)(__float_as_uint(s0) >> 31) + (int)(__float_as_uint(s1) >> 31);
 }
 
 __device__ __forceinline__ int pair_hits(const PairFrame& f, const float4* __restrict__ cxy,
@@ -463,16 +498,7 @@ __device__ __forceinline__ int pair_hits(const PairFrame& f, const float4* __res
   for (int k = k0; k < k1; ++k) {
     const float4 c = cxy[k];
     const float2 w = nr2[k];
-    const unsigned long long CX = pack2(c.x, c.y), CY = pack2(c.z, c.w), W = pack2(w.x, w.y);
-    const unsigned long long AL = ffma2(CX, f.ux, ffma2(CY, f.uy, f.nmu));
-    const unsigned long long P = ffma2(CX, f.nx, ffma2(CY, f.ny, f.nmn));
-    float al0, al1;
-    unpack2(AL, al0, al1);
-    const float m0 = fmaxf(fabsf(al0) - f.h, 0.0f), m1 = fmaxf(fabsf(al1) - f.h, 0.0f);
-    const unsigned long long S = ffma2(pack2(m0, m1), pack2(m0, m1), ffma2(P, P, W));
-    float s0, s1;
-    unpack2(S, s0, s1);
-    hits += (int)(__float_as_uint(s0) >> 31) + (int)(__float_as_uint(s1) >> 31);
+    hits += pair_test(pack2(c.x, c.y), pack2(c.z, c.w), pack2(w.x, w.y), f.ux, f.uy, f.nmu, f.nx, f.ny, f.nmn, f.h);
   }
   return hits;
 }
@@ -516,20 +542,21 @@ __device__ __forceinline__ void group_fitness_pairs(const float* x, bool live, i
 // orientation products), so touching and collinear contacts do not count.  Edges
 // are float4 (x0, y0, x1, y1).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int edge_crosses(float ax, float ay, float bx, float by, const float4 d) {
+  const float ux = bx - ax, uy = by - ay;
+  const float vx = d.z - d.x, vy = d.w - d.y;
+  const float o1 = ux * (d.y - ay) - uy * (d.x - ax);
+  const float o2 = ux * (d.w - ay) - uy * (d.z - ax);
+  const float o3 = vx * (ay - d.y) - vy * (ax - d.x);
+  const float o4 = vx * (by - d.y) - vy * (bx - d.x);
+  return (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
+}
+
 __device__ __forceinline__ int edge_hits(float ax, float ay, float bx, float by, const float4* __restrict__ edges,
                                          int e0, int e1) {
-  const float ux = bx - ax, uy = by - ay;
   int hits = 0;
 #pragma unroll 4
-  for (int e = e0; e < e1; ++e) {
-    const float4 d = edges[e];
-    const float vx = d.z - d.x, vy = d.w - d.y;
-    const float o1 = ux * (d.y - ay) - uy * (d.x - ax);
-    const float o2 = ux * (d.w - ay) - uy * (d.z - ax);
-    const float o3 = vx * (ay - d.y) - vy * (ax - d.x);
-    const float o4 = vx * (by - d.y) - vy * (bx - d.x);
-    hits += (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
-  }
+  for (int e = e0; e < e1; ++e) hits += edge_crosses(ax, ay, bx, by, edges[e]);
   return hits;
 }
 

@@ -18,13 +18,16 @@ struct SmemLayout {
   __host__ __device__ static SmemLayout make(int obst_f4, int ppc, int D, int T, int G, int tw);
 };
 
-// Shared-memory carve of swarm_cluster_kernel: the rows of swarm_kernel (X and V
-// twice when spec), the CTA's F / Q of the current evaluation, and the cluster
-// exchange slots (two parities x S ranks: best key, decision word, candidate row
-// with its Q).
+// Shared-memory carve of swarm_cluster_kernel: the obstacles, the Auto Truncation
+// window, the key slots (two parities x S ranks x ppc particles), the staged
+// candidate rows (two parities x ppc particles) and one frame area per particle
+// warp.  Its CTAs have one warp per particle plus a control
+// warp, at most kClusterMaxThreads threads; rows live in registers, so the form
+// takes T + 1 <= 32 segments.
+constexpr int kClusterMaxThreads = 512;
 struct ClusterLayout {
-  int pairs, win, X0, X1, V0, V1, P, R, Gown, Pfit, PQ, Q, Len, F, FQ, Imp, rec, xkey, xdec, xrow, total;
-  __host__ __device__ static ClusterLayout make(int obst_f4, int ppc, int D, int T, int G, int tw, int S, int spec);
+  int pairs, win, keys, stage, frames, total;
+  __host__ __device__ static ClusterLayout make(int obst_f4, int ppc, int T, int tw, int S);
 };
 
 struct EvalParams {

@@ -585,87 +585,78 @@ __global__ void __launch_bounds__(512) swarm_kernel(const SwarmParams p) {
 // Tbest (C3 = 0 in every group, as in the sampled and HSEF-evolved settings): Eq.
 // TOF_V then needs only the group's own Gbest, so the exchange that gates each
 // update can stay inside the group.  Run r, group g owns one thread-block cluster
-// of S = p.cpg CTAs (cluster rank q owns particles [q ppc, q ppc + ppc)).  Per
-// iteration k:
-//   1. fitness of X^k; the Pbest test is kept aside (F, Q, improved?), P is not
-//      written yet;
-//   2. warp 0 reads the G group records of iteration k - 1 (each group's Gfit and
-//      Q after its best update, published one iteration earlier), updates Tbest
-//      with them and takes the Auto Truncation decision of k - 1, as Algorithm 1
-//      takes it right after that best update;
-//   3. each CTA writes its best candidate key (the lowest-index particle of lowest
-//      post-update Pbest fitness below the group's Gfit), its decision word and
-//      the candidate's row into its slot in every CTA of the cluster (distributed
-//      shared memory), then the cluster barrier;
-//   4. the decision is the largest word of the cluster (0 go on, 1 stop at k - 1,
-//      2 failed), so every CTA takes it alike; on a stop at k - 1 iteration k is
-//      discarded: X and V of k - 1 are still in the other buffer, P and Gbest are
-//      untouched, and Tbest of k - 1 is the result (Algorithm 1 returns Tbest
-//      after the stopping iteration's best update and never applies its update);
-//   5. otherwise the Pbest updates are applied, the new Gbest is the lowest key of
-//      the cluster's slots (its row from the winner's slot), rank 0 publishes the
-//      group's record of k, and the update of Eqs. TOF_omega, TOF_V and TOF_X runs.
-// The iteration cap (or the step count) ends the loop after step 5; the groups
-// then meet once at the run's end counter, and CTA 0 of the run applies the last
-// records to Tbest and takes its row from the holder group's Gbest row.  The
-// decisions, bests and arithmetic are those of swarm_kernel, so both forms give
-// identical results.  Slots of parity k & 1 are rewritten at k + 2, after the
-// cluster barrier of k + 1, which every CTA reaches only after reading them.
+// of S = p.cpg CTAs; CTA q (its rank in the cluster) owns particles
+// [q ppc, q ppc + ppc) of the group, one warp each, plus a control warp (the last
+// warp).  A particle's state lives in its warp's registers: lane l < T holds
+// waypoint l (x = X[l], y = X[T + l]) with its velocity and Pbest coordinates and
+// the group's Gbest coordinates; the Pbest and Gbest fitness and Q are the same in
+// every lane.  Round j of a launch runs iteration k = k0 + j:
+//   1. each particle warp evaluates F(X^k) (lane s builds segment s's frame, lane
+//      l tests obstacles l, l + 32, ... against every segment), applies its Pbest
+//      test and, when its Pbest is below the group's Gfit, stages its Pbest row
+//      and Q in its CTA's shared memory; it writes its key (or the empty key) into
+//      its own key slot of the round in every CTA of the cluster (plain remote
+//      stores: 64-bit atomic min on distributed shared memory was measured to lose
+//      updates on GB300, so every warp owns a slot and readers reduce);
+//   2. the control warp of rank 0 reads every group's record of iteration
+//      k - kLag (Gfit and Q after that iteration's best update), updates Tbest,
+//      takes that iteration's Auto Truncation decision and writes the decision
+//      word of the round into every CTA of the cluster;
+//   3. one cluster barrier;
+//   4. every warp reads the round's decision and reduces the round's key slots in
+//      its own shared memory.  A stop at k - kLag restores that iteration's state from two
+//      register snapshots (Algorithm 1 returns Tbest after the stopping
+//      iteration's best update and moves no particle after it); otherwise the
+//      group's Gbest follows the key (the winner's row and Q are read from its
+//      CTA's stage), rank 0's control warp publishes the group's record of k and
+//      each particle warp applies Eqs. TOF_omega, TOF_V and TOF_X to its row.
+// At the iteration cap the position update is skipped and, with Auto Truncation
+// on, kLag - 1 more rounds collect the decisions of the last iterations.  The
+// groups then meet once at the run's end counter, and CTA 0 of the run applies the
+// records it has not seen yet and takes Tbest's row from the holder group's Gbest
+// row (the holder's row changes only together with Tbest).  The decisions, bests
+// and arithmetic are those of swarm_kernel, so both forms give identical results
+// and states.
+//
+// Reuse of the exchange buffers: key slots and stage rows of parity gk & 1 (and
+// the decision word of round j, slot j % 3) are rewritten two rounds later, after
+// the barrier of the round in between, which every reader reaches only after
+// reading them.  A record ring slot of iteration gk is rewritten at
+// gk + kRecDepth; every group reads the records of gk - kLag before its barrier of
+// gk, so no reader still needs a slot when it is rewritten.
 // ---------------------------------------------------------------------------
-// Floats of one exchange slot: D row values, Q, the decision word and the 64-bit key,
-// rounded up to whole 16-byte vectors.
-__host__ __device__ inline int cluster_slot_stride(int D) { return (D + 4 + 3) & ~3; }
+constexpr int kLag = 2;  // Auto Truncation decided kLag iterations late (slack for the records)
 
-__host__ __device__ ClusterLayout ClusterLayout::make(int obst_f4, int ppc, int D, int T, int G, int tw, int S,
-                                                      int spec) {
+// Floats of one stage row: (x_l, y_l) pairs for l < T, then Q, padded.
+__host__ __device__ inline int cluster_stage_stride(int T) { return 2 * T + 4; }
+constexpr int kFrameFloats = 8;  // one segment frame in a warp's frame area
+
+__host__ __device__ ClusterLayout ClusterLayout::make(int obst_f4, int ppc, int T, int tw, int S) {
   ClusterLayout s;
   int off = 1024;
   s.pairs = off;
   off = align_up(off + obst_f4 * 16, 16);  // circle-pair blocks or polygon edges
   s.win = off;
   off = align_up(off + tw * 8, 16);
-  s.rec = off;
-  off = align_up(off + G * 8, 16);
-  s.X0 = off;
-  off = align_up(off + ppc * D * 4, 16);
-  s.X1 = s.X0;
-  if (spec) {
-    s.X1 = off;
-    off = align_up(off + ppc * D * 4, 16);
-  }
-  s.V0 = off;
-  off = align_up(off + ppc * D * 4, 16);
-  s.V1 = s.V0;
-  if (spec) {
-    s.V1 = off;
-    off = align_up(off + ppc * D * 4, 16);
-  }
-  s.P = off;
-  off = align_up(off + ppc * D * 4, 16);
-  s.R = off;
-  off = align_up(off + ppc * 16, 16);
-  s.Gown = off;
-  off = align_up(off + D * 4, 16);
-  s.xrow = off;  // slots: the candidate row, its Q, the decision word, the key (cluster_slot_stride floats)
-  off = align_up(off + 2 * S * cluster_slot_stride(D) * 4, 16);
-  s.Pfit = off;
-  off += ppc * 4;
-  s.PQ = off;
-  off += ppc * 4;
-  s.Q = off;
-  off += ppc * 4;
-  s.F = off;
-  off += ppc * 4;
-  s.FQ = off;
-  off += ppc * 4;
-  s.Imp = off;
-  off += ppc * 4;
-  s.xdec = off;
-  off += 2 * S * 4;
-  s.Len = off;
-  off += ppc * (T + 1) * 4;
+  s.keys = off;  // two parities x S ranks x ppc warps
+  off = align_up(off + 2 * S * ppc * 8, 16);
+  s.stage = off;
+  off = align_up(off + 2 * ppc * cluster_stage_stride(T) * 4, 16);
+  s.frames = off;
+  off += ppc * 32 * kFrameFloats * 4;  // per particle warp: frames of up to 32 segments
   s.total = align_up(off, 16);
   return s;
+}
+
+__device__ __forceinline__ float2 ld_peer_f2(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_peer_s32(uint32_t addr) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
 }
 
 // Tbest from the G group records held by lanes 0..G-1 of warp 0 (strictly better,
@@ -709,7 +700,7 @@ __device__ __forceinline__ bool cluster_tbest_at(const SwarmParams& p, unsigned 
   return stop;
 }
 
-// Lanes 0..G-1 of warp 0: the records of iteration gk (prefetched in rec), waited
+// Lanes 0..G-1 of a warp: the records of iteration gk (prefetched in rec), waited
 // for with the time limit; true when one did not come.
 __device__ __forceinline__ bool cluster_wait_records(const unsigned long long* slot, int lane, int G,
                                                      unsigned long long gk, unsigned long long& rec) {
@@ -727,43 +718,162 @@ __device__ __forceinline__ bool cluster_wait_records(const unsigned long long* s
   return __any_sync(0xffffffffu, late) != 0;
 }
 
-__global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p) {
+// The circle pairs a lane keeps in registers for a whole launch: with PG =
+// ceil(K / kLanePairs) lanes per segment group and SG = 32 / PG groups, lane l holds
+// pairs kLanePairs (l % PG) + i and takes segments l / PG, l / PG + SG, ...; pairs
+// past K hold a value that never hits (-r^2 = +1).  A lane then reads one compact
+// frame per segment for kLanePairs pairs, which keeps the frames' shared-memory
+// reads below the arithmetic.
+constexpr int kLanePairs = 4;
+struct LanePairs {
+  unsigned long long cx[kLanePairs], cy[kLanePairs], w[kLanePairs];
+  int s0, ds;  // first segment of the lane and the stride
+};
+
+__device__ __forceinline__ LanePairs lane_pairs(const float4* cxy, const float2* nr2, int K, int lane) {
+  LanePairs lp;
+  const int PG = max(1, (K + kLanePairs - 1) / kLanePairs);
+  const int SG = max(1, 32 / PG);
+  const int pg = lane % PG;
+  lp.s0 = (lane / PG < SG) ? lane / PG : 32;  // lanes past the last group take no segment
+  lp.ds = SG;
+#pragma unroll
+  for (int i = 0; i < kLanePairs; ++i) {
+    const int k = pg * kLanePairs + i;
+    float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float2 w = make_float2(1.0f, 1.0f);
+    if (k < K) {
+      c = cxy[k];
+      w = nr2[k];
+    }
+    lp.cx[i] = pack2(c.x, c.y);
+    lp.cy[i] = pack2(c.z, c.w);
+    lp.w[i] = pack2(w.x, w.y);
+  }
+  return lp;
+}
+
+// Length and Q of the warp's particle among circle pairs, its row in registers
+// (lane l < T holds waypoint l): lane s <= T builds segment s's frame (two float4:
+// ux, uy, -mu, nx and ny, -mn, h) in the warp's frame area fr, then every lane
+// tests its register pairs against its segments (K <= 32 kLanePairs), or pairs l,
+// l + 32, ... against every segment (larger K), with the arithmetic of pair_hits.
+// The length is summed in warp_len_sum's order (lane s holds segment s), Q
+// exactly; every lane returns both.
+__device__ __forceinline__ void warp_fitness_pairs(float x, float y, int T, int lane, float sx, float sy, float tx,
+                                                   float ty, const LanePairs& lp, const float4* __restrict__ cxy,
+                                                   const float2* __restrict__ nr2, int K, float* fr, float* len_out,
+                                                   int* q_out) {
+  const float xp = __shfl_up_sync(0xffffffffu, x, 1), yp = __shfl_up_sync(0xffffffffu, y, 1);
+  float4* f4 = reinterpret_cast<float4*>(fr);
+  float len = 0.0f;
+  if (lane <= T) {
+    const float ax = lane == 0 ? sx : xp, ay = lane == 0 ? sy : yp;
+    const float bx = lane == T ? tx : x, by = lane == T ? ty : y;
+    const FrameScalars f = frame_scalars(ax, ay, bx, by, &len);
+    f4[2 * lane] = make_float4(f.ux, f.uy, f.nmu, f.nx);
+    f4[2 * lane + 1] = make_float4(f.ny, f.nmn, f.h, 0.0f);
+  }
+  __syncwarp();
+  int hits = 0;
+  if (K <= 32 * kLanePairs) {
+    for (int s = lp.s0; s <= T; s += lp.ds) {
+      const float4 a = f4[2 * s], b = f4[2 * s + 1];
+      const unsigned long long UX = pack2(a.x, a.x), UY = pack2(a.y, a.y), NMU = pack2(a.z, a.z),
+                               NX = pack2(a.w, a.w), NY = pack2(b.x, b.x), NMN = pack2(b.y, b.y);
+#pragma unroll
+      for (int i = 0; i < kLanePairs; ++i) hits += pair_test(lp.cx[i], lp.cy[i], lp.w[i], UX, UY, NMU, NX, NY, NMN, b.z);
+    }
+  } else {
+    for (int k = lane; k < K; k += 32) {
+      const float4 c = cxy[k];
+      const float2 w = nr2[k];
+      const unsigned long long CX = pack2(c.x, c.y), CY = pack2(c.z, c.w), W = pack2(w.x, w.y);
+#pragma unroll 2
+      for (int s = 0; s <= T; ++s) {
+        const float4 a = f4[2 * s], b = f4[2 * s + 1];
+        hits += pair_test(CX, CY, W, pack2(a.x, a.x), pack2(a.y, a.y), pack2(a.z, a.z), pack2(a.w, a.w),
+                          pack2(b.x, b.x), pack2(b.y, b.y), b.z);
+      }
+    }
+  }
+  __syncwarp();  // every lane has read the frames before the next round rewrites them
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    len += __shfl_xor_sync(0xffffffffu, len, o);
+    hits += __shfl_xor_sync(0xffffffffu, hits, o);
+  }
+  *len_out = len;
+  *q_out = hits;
+}
+
+// The same among polygon edges: lane s <= T stores segment s's end points, lane l
+// tests edges l, l + 32, ... against every segment (edge_crosses).
+__device__ __forceinline__ void warp_fitness_edges(float x, float y, int T, int lane, float sx, float sy, float tx,
+                                                   float ty, const float4* __restrict__ edges, int E, float* fr,
+                                                   float* len_out, int* q_out) {
+  const float xp = __shfl_up_sync(0xffffffffu, x, 1), yp = __shfl_up_sync(0xffffffffu, y, 1);
+  float4* f4 = reinterpret_cast<float4*>(fr);
+  float len = 0.0f;
+  if (lane <= T) {
+    const float ax = lane == 0 ? sx : xp, ay = lane == 0 ? sy : yp;
+    const float bx = lane == T ? tx : x, by = lane == T ? ty : y;
+    const float dx = bx - ax, dy = by - ay;
+    len = sqrtf(fmaf(dx, dx, dy * dy));
+    f4[2 * lane] = make_float4(ax, ay, bx, by);
+  }
+  __syncwarp();
+  int hits = 0;
+  for (int e = lane; e < E; e += 32) {
+    const float4 d = edges[e];
+#pragma unroll 4
+    for (int s = 0; s <= T; ++s) {
+      const float4 sg = f4[2 * s];
+      hits += edge_crosses(sg.x, sg.y, sg.z, sg.w, d);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    len += __shfl_xor_sync(0xffffffffu, len, o);
+    hits += __shfl_xor_sync(0xffffffffu, hits, o);
+  }
+  *len_out = len;
+  *q_out = hits;
+}
+
+// A particle lane's state at the end of one iteration (after its best updates).
+struct LaneSnap {
+  float x, y, vx, vy, px, py, gx, gy, pfit, gfit;
+  int pq, gq;
+};
+
+__global__ void __launch_bounds__(kClusterMaxThreads, 1) swarm_cluster_kernel(const SwarmParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t s_mbar;
-  __shared__ unsigned long long s_key;
-  __shared__ uint32_t s_dec;
+  __shared__ uint32_t s_dec[3];
+  __shared__ uint32_t s_any[3];
+  __shared__ uint32_t s_init[16];
 
   const int S = p.cpg;
-  const ClusterLayout L = ClusterLayout::make(obstacle_f4(p.Omax, p.poly), p.ppc, p.D, p.T, p.G, p.tw, S, p.spec);
-  float4* sPairs = reinterpret_cast<float4*>(smem + L.pairs);
+  const ClusterLayout L = ClusterLayout::make(obstacle_f4(p.Omax, p.poly), p.ppc, p.T, p.tw, S);
+  const float4* sObst = reinterpret_cast<const float4*>(smem + L.pairs);
   double* sWin = reinterpret_cast<double*>(smem + L.win);
-  uint32_t* sXdec = reinterpret_cast<uint32_t*>(smem + L.xdec);
-  float* sXrow = reinterpret_cast<float*>(smem + L.xrow);
-  float* sX0 = reinterpret_cast<float*>(smem + L.X0);
-  float* sX1 = reinterpret_cast<float*>(smem + L.X1);
-  float* sV0 = reinterpret_cast<float*>(smem + L.V0);
-  float* sV1 = reinterpret_cast<float*>(smem + L.V1);
-  float* sP = reinterpret_cast<float*>(smem + L.P);
-  float* sR = reinterpret_cast<float*>(smem + L.R);
-  float* sG = reinterpret_cast<float*>(smem + L.Gown);
-  float* sPfit = reinterpret_cast<float*>(smem + L.Pfit);
-  int* sPQ = reinterpret_cast<int*>(smem + L.PQ);
-  int* sQi = reinterpret_cast<int*>(smem + L.Q);
-  float* sF = reinterpret_cast<float*>(smem + L.F);
-  int* sFQ = reinterpret_cast<int*>(smem + L.FQ);
-  int* sImp = reinterpret_cast<int*>(smem + L.Imp);
-  float* sLen = reinterpret_cast<float*>(smem + L.Len);
+  unsigned long long* sKeys = reinterpret_cast<unsigned long long*>(smem + L.keys);
+  float* sStage = reinterpret_cast<float*>(smem + L.stage);
 
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
-  const int T = p.T, D = p.D, G = p.G, N = p.N;
-  const int b = blockIdx.x;
-  const int r = b / p.C;
-  const int cr = b - r * p.C;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool ctrl = warp == (int)(blockDim.x >> 5) - 1;  // the control warp
+  const int T = p.T, D = p.D, G = p.G, N = p.N, ppc = p.ppc;
+  const int SR = cluster_stage_stride(T);
+  const int r = blockIdx.x / p.C;
+  const int cr = blockIdx.x - r * p.C;
   const int g = cr / S;
   const uint32_t q = cluster_rank();  // = cr - g * S: a cluster is S consecutive blocks
-  const int n0 = (int)q * p.ppc;
-  const int nl = max(0, min(p.ppc, N - n0));
+  const int n = (int)q * ppc + warp;  // the warp's particle (index within the group)
+  const bool live = !ctrl && warp < ppc && n < N;
+  const bool wl = live && lane < T;  // the lane holds a waypoint
+  float* fr = reinterpret_cast<float*>(smem + L.frames) + (size_t)(live ? warp : 0) * 32 * kFrameFloats;
   RunCtl* ctl = p.ctl + r;
 
   const float* hy = p.hyper + ((size_t)r * G + g) * 6;
@@ -771,97 +881,92 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
   const float sx = p.pts[0], sy = p.pts[1], tx = p.pts[2], ty = p.pts[3];
   const uint32_t cycle = (uint32_t)ctl->cycle;
   const uint32_t run = ctl->run_id;
+  const bool plan = p.mode == kModePlan;
   // read before any group arrives at the end counter (the last arrival's reader
   // advances it only after all arrivals)
   const int nfin = ctl->fin_launches;
+  const int k0 = plan ? 0 : ctl->k;
+  const unsigned long long kbase = (unsigned long long)ctl->iters_total;
 
   if (tid == 0) {
     mbar_init(&s_mbar, 1);
-    s_key = kKeyEmpty;
+    for (int i = 0; i < 3; ++i) {
+      s_dec[i] = 0u;
+      s_any[i] = 0u;
+    }
   }
+  for (int i = tid; i < 2 * S * ppc; i += blockDim.x) sKeys[i] = kKeyEmpty;  // slots of absent particles stay empty
   __syncthreads();
   if (tid == 0 && p.O > 0) {
     const uint32_t bytes = (uint32_t)(p.poly ? p.O : pair_block_f4(p.O)) * 16u;
     mbar_expect_tx(&s_mbar, bytes);
-    bulk_g2s(sPairs, p.poly ? p.circ : p.pairs, bytes, &s_mbar);
+    bulk_g2s(const_cast<float4*>(sObst), p.poly ? p.circ : p.pairs, bytes, &s_mbar);
   }
 
-  float* gX = p.X + ((size_t)r * p.M + (size_t)g * N + n0) * D;
-  float* gV = p.V + ((size_t)r * p.M + (size_t)g * N + n0) * D;
-  float* gP = p.P + ((size_t)r * p.M + (size_t)g * N + n0) * D;
-  float* gPfit = p.Pfit + (size_t)r * p.M + (size_t)g * N + n0;
-  int32_t* gPQ = p.PQ + (size_t)r * p.M + (size_t)g * N + n0;
+  const size_t prow = ((size_t)r * p.M + (size_t)g * N + (size_t)(live ? n : 0)) * D;
   float* gGb = p.Gb + (size_t)r * G * D;
   float* gTb = p.Tb + (size_t)r * D;
   unsigned long long* grec = p.grec + (size_t)r * kRecDepth * G;
 
-  float Tfit, gfit;
-  int TQ, k, gq;
-  int tholder = -1;  // group whose Gbest row is Tbest's; -1: the row already in gTb
+  LaneSnap c = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, INFINITY, INFINITY, 0, 0};
+  // Tbest and Auto Truncation state (meaningful in the control warp of rank 0)
+  float Tfit = INFINITY;
+  int TQ = 0, tholder = -1;  // tholder: group whose Gbest row is Tbest's; -1: the row already in gTb
   int win_n = 0, win_head = 0, stall = 0;
   float prev_lfv = INFINITY;
 
-  if (p.mode == kModePlan) {
-    // Initialisation (Algorithm 1) with Priori Initialization (Sec. 3.3.3).
+  if (plan) {
+    // Initialisation (Algorithm 1) with Priori Initialization (Sec. 3.3.3):
+    // coordinate j takes word j % 4 of the draw whose counter word 0 is j / 4.
     const int n_pi = (p.use_pi && ctl->has_prev) ? p.n_pi : 0;
-    const float* prevT = p.prevT + (size_t)r * D;
-    const int nch = (D + 3) >> 2;
-    for (int it = tid; it < nl * nch; it += nt) {
-      const int i = it / nch, ch = it - i * nch;
-      const int n = n0 + i;
+    if (wl) {
       const uint32_t pid = (uint32_t)(g * N + n);
       const bool pi = n < n_pi;
-      const uint4 ux = draw(p.key0, p.key1, (uint32_t)ch, pid, pi ? kStreamPI : kStreamInitX, cycle, run);
-      const uint4 uv = draw(p.key0, p.key1, (uint32_t)ch, pid, kStreamInitV, cycle, run);
-#pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        const int j = ch * 4 + l;
-        if (j < D) {
-          const float ext = (j < T) ? p.W : p.H;
-          float x;
-          if (pi) x = fminf(fmaxf(prevT[j] + (2.0f * lane_of(ux, l) - 1.0f) * p.pi_h, 0.0f), ext);
-          else x = lane_of(ux, l) * ext;
-          sX0[i * D + j] = x;
-          sP[i * D + j] = x;
-          sV0[i * D + j] = (2.0f * lane_of(uv, l) - 1.0f) * (vlim * ext);
-        }
+      const uint32_t stream = pi ? kStreamPI : kStreamInitX;
+      const int jx = lane, jy = T + lane;
+      const uint4 uxa = draw(p.key0, p.key1, (uint32_t)(jx >> 2), pid, stream, cycle, run);
+      const uint4 uxb = draw(p.key0, p.key1, (uint32_t)(jy >> 2), pid, stream, cycle, run);
+      const uint4 uva = draw(p.key0, p.key1, (uint32_t)(jx >> 2), pid, kStreamInitV, cycle, run);
+      const uint4 uvb = draw(p.key0, p.key1, (uint32_t)(jy >> 2), pid, kStreamInitV, cycle, run);
+      if (pi) {
+        const float* prevT = p.prevT + (size_t)r * D;
+        c.x = fminf(fmaxf(prevT[jx] + (2.0f * lane_of(uxa, jx & 3) - 1.0f) * p.pi_h, 0.0f), p.W);
+        c.y = fminf(fmaxf(prevT[jy] + (2.0f * lane_of(uxb, jy & 3) - 1.0f) * p.pi_h, 0.0f), p.H);
+      } else {
+        c.x = lane_of(uxa, jx & 3) * p.W;
+        c.y = lane_of(uxb, jy & 3) * p.H;
       }
+      c.vx = (2.0f * lane_of(uva, jx & 3) - 1.0f) * (vlim * p.W);
+      c.vy = (2.0f * lane_of(uvb, jy & 3) - 1.0f) * (vlim * p.H);
+      c.px = c.x;
+      c.py = c.y;
     }
-    for (int i = tid; i < nl; i += nt) {
-      sPfit[i] = INFINITY;
-      sPQ[i] = 0;
-    }
-    for (int j = tid; j < D; j += nt) {
-      sG[j] = 0.0f;
-      if (q == 0) gGb[g * D + j] = 0.0f;
-      if (cr == 0) gTb[j] = 0.0f;
-    }
-    Tfit = INFINITY;
-    TQ = 0;
-    k = 0;
-    gfit = INFINITY;
-    gq = 0;
-    if (tid < 32 && p.at_mode == SEPSO_AT_STD_WINDOW && cycle != 0) {
+    if (cr == 0 && ctrl)
+      for (int j = lane; j < D; j += 32) gTb[j] = 0.0f;
+    if (ctrl && q == 0 && p.at_mode == SEPSO_AT_STD_WINDOW && cycle != 0) {
       win_n = ctl->win_n;
       win_head = ctl->win_head;
       for (int i = lane; i < p.tw; i += 32) sWin[i] = p.win[(size_t)r * p.tw + i];
     }
   } else {
-    for (int it = tid; it < nl * D; it += nt) {
-      sX0[it] = gX[it];
-      sV0[it] = gV[it];
-      sP[it] = gP[it];
+    if (wl) {
+      c.x = p.X[prow + lane];
+      c.y = p.X[prow + T + lane];
+      c.vx = p.V[prow + lane];
+      c.vy = p.V[prow + T + lane];
+      c.px = p.P[prow + lane];
+      c.py = p.P[prow + T + lane];
+      c.gx = gGb[(size_t)g * D + lane];
+      c.gy = gGb[(size_t)g * D + T + lane];
     }
-    for (int i = tid; i < nl; i += nt) {
-      sPfit[i] = gPfit[i];
-      sPQ[i] = gPQ[i];
+    if (live) {
+      c.pfit = p.Pfit[prow / D];
+      c.pq = p.PQ[prow / D];
     }
-    for (int j = tid; j < D; j += nt) sG[j] = gGb[g * D + j];
-    gfit = p.Gfit[(size_t)r * G + g];
-    gq = p.GQ[(size_t)r * G + g];
+    c.gfit = p.Gfit[(size_t)r * G + g];
+    c.gq = p.GQ[(size_t)r * G + g];
     Tfit = ctl->Tfit;
     TQ = ctl->TQ;
-    k = ctl->k;
   }
 
   bool failed = false;
@@ -878,303 +983,220 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
   } else {
     __syncthreads();
   }
-  const float2* sNr2 = reinterpret_cast<const float2*>(sPairs + K);
-  for (int i = tid; i < nl; i += nt) sQi[i] = 0;
-
-  const unsigned long long kbase = (unsigned long long)ctl->iters_total;
-  // Every CTA of the cluster has started before any remote store; a failed copy
-  // in any of them stops the whole cluster (the slots of parity kbase & 1 are
-  // free until iteration kbase + 2).
+  const float2* sNr2 = reinterpret_cast<const float2*>(sObst + K);
+  const LanePairs lpairs = lane_pairs(sObst, sNr2, p.poly ? 0 : K, lane);
+  // Every CTA of the cluster has started (and set its words) before any remote
+  // access; a failed copy in any of them stops the whole cluster.
   cluster_barrier();
-  const int p0 = (int)(kbase & 1ull);
-  if (tid < S) st_peer_u32(peer_addr(sXdec + p0 * S + q, (uint32_t)tid), failed ? 2u : 0u);
+  if (tid < S) st_peer_u32(peer_addr(&s_init[q], (uint32_t)tid), failed ? 1u : 0u);
   cluster_barrier();
   {
     uint32_t any = 0;
-    for (int s2 = 0; s2 < S; ++s2) any |= sXdec[p0 * S + s2];
+    for (int s2 = 0; s2 < S; ++s2) any |= s_init[s2];
     failed = any != 0;
   }
 
-  const int nseg = T + 1;
-  int done = 0, xb = 0;
-  bool capstop = false;
-  unsigned long long gk_last = kbase;
-  while (!failed) {
-    if (p.mode == kModeStep && done >= p.step_iters) break;
-    ++k;
-    ++done;
-    const unsigned long long gk = kbase + (unsigned long long)done;
+  const bool at_on = plan && p.at_mode != SEPSO_AT_OFF;
+  const int n_compute = plan ? p.max_iters : p.step_iters;
+  const int n_rounds = n_compute + (at_on ? kLag - 1 : 0);
+  LaneSnap A = c, B = c;  // the state at the end of the last iteration, and of the one before
+  int done = 0;           // iterations completed by this launch
+  int stop_round = 0;     // the round that learned of an Auto Truncation stop
+  unsigned long long proc = kbase;  // records applied to Tbest through this iteration count
+  unsigned long long rec = 0ull;    // control warp of rank 0, lanes < G: the next records to apply
+  for (int j = 1; !failed && j <= n_rounds; ++j) {
+    const bool compute = j <= n_compute;
+    const unsigned long long gk = kbase + (unsigned long long)j;
+    const int slot = j % 3;
     const int par = (int)(gk & 1ull);
-    float* cX = xb ? sX1 : sX0;
-    float* cV = xb ? sV1 : sV0;
-    const bool have_prev = done > 1;
-    const unsigned long long* prev_slot = grec + (size_t)((gk - 1ull) % (unsigned long long)kRecDepth) * G;
-    unsigned long long rec = 0;
-    if (have_prev && tid < G) rec = ld_relaxed_u64(prev_slot + tid);  // in flight during the fitness
-    for (int i = nt - 1 - tid; i < nl; i += nt) {
-      const uint4 o = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)(g * N + n0 + i), kStreamVel, cycle, run);
-      sR[i * 4 + 0] = c1 * u01(o.x);
-      sR[i * 4 + 1] = c2 * u01(o.y);
-    }
-
-    // 1. Fitness F(X^k) and the Pbest test, kept aside.
-    if (p.items) {
-      if (p.poly) fitness_items_edges(cX, nl, T, D, sx, sy, tx, ty, sPairs, p.O, p.split, sQi, sLen);
-      else fitness_items_pairs(cX, nl, T, D, sx, sy, tx, ty, sPairs, sNr2, K, p.split, sQi, sLen);
-      __syncthreads();
-    }
-    {
-      // In item mode warp 0 leaves the particles to the other warps and reads the
-      // groups' records meanwhile (step 2).
-      const bool skip0 = p.items && nwarps > 1;
-      const int lp = p.items ? 32 : p.lp;
-      const int ppw = 32 / lp;
-      const int lsub = lane & (lp - 1);
-      const int w0 = skip0 ? warp - 1 : warp, nw = skip0 ? nwarps - 1 : nwarps;
-      if (w0 >= 0) {
-        for (int i0 = w0 * ppw; i0 < nl; i0 += nw * ppw) {
-          const int i = i0 + lane / lp;
-          const bool live = i < nl;
-          float len = 0.0f;
-          int qq = 0;
-          if (p.items) {
-            len = warp_len_sum(sLen + i * nseg, nseg, lane);
-            if (lsub == 0) {
-              qq = sQi[i];
-              sQi[i] = 0;
-            }
-          } else if (p.poly) {
-            group_fitness_edges(cX + (live ? i : 0) * D, live, lp, T, p.split, p.O, sx, sy, tx, ty, sPairs, &len,
-                                &qq);
-          } else {
-            group_fitness_pairs(cX + (live ? i : 0) * D, live, lp, T, p.split, K, sx, sy, tx, ty, sPairs, sNr2,
-                                &len, &qq);
-          }
-          if (live && lsub == 0) {
-            const float F = len + p.alpha * powi((float)qq, p.beta);
-            const float pf = sPfit[i];
-            const int imp = F < pf;
-            const float cf = imp ? F : pf;
-            const int cq = imp ? qq : sPQ[i];
-            sF[i] = F;
-            sFQ[i] = qq;
-            sImp[i] = imp;
-            if (cf < gfit) atomicMin(&s_key, best_key(cf, (uint32_t)(n0 + i), (uint32_t)cq));
-          }
-        }
+    float a1 = 0.0f, a2 = 0.0f;
+    if (compute && live) {
+      // R1, R2 of this iteration (one scalar per particle), F(X^k), the Pbest test
+      const uint4 o = draw(p.key0, p.key1, (uint32_t)(k0 + j), (uint32_t)(g * N + n), kStreamVel, cycle, run);
+      a1 = c1 * u01(o.x);
+      a2 = c2 * u01(o.y);
+      float len;
+      int qq;
+      if (p.poly) warp_fitness_edges(c.x, c.y, T, lane, sx, sy, tx, ty, sObst, p.O, fr, &len, &qq);
+      else warp_fitness_pairs(c.x, c.y, T, lane, sx, sy, tx, ty, lpairs, sObst, sNr2, K, fr, &len, &qq);
+      const float F = len + p.alpha * powi((float)qq, p.beta);
+      if (F < c.pfit) {
+        c.pfit = F;
+        c.pq = qq;
+        c.px = c.x;
+        c.py = c.y;
       }
+      unsigned long long key = kKeyEmpty;
+      if (c.pfit < c.gfit) {  // a candidate for the group's best: stage the row
+        float* st = sStage + (size_t)(par * ppc + warp) * SR;
+        if (lane < T) reinterpret_cast<float2*>(st)[lane] = make_float2(c.px, c.py);
+        if (lane == 0) reinterpret_cast<int*>(st)[2 * T] = c.pq;
+        key = best_key(c.pfit, (uint32_t)n, (uint32_t)c.pq);
+        if (lane < S) st_peer_u32(peer_addr(&s_any[slot], (uint32_t)lane), 1u);  // the round has a candidate
+      }
+      if (lane < S) st_peer_u64(peer_addr(sKeys + ((size_t)par * S + q) * ppc + warp, (uint32_t)lane), key);
     }
-    // 2. Tbest and Auto Truncation of iteration k - 1 from the groups' records.
-    if (warp == 0) {
+    if (ctrl && q == 0) {
+      // Tbest and Auto Truncation of iteration gk - kLag from every group's record
       uint32_t dec = 0;
-      if (have_prev) {
-        const bool late = cluster_wait_records(prev_slot, lane, G, gk - 1ull, rec);
-        if (late) {
+      if (j > kLag) {
+        const unsigned long long gr = gk - (unsigned long long)kLag;
+        const unsigned long long* rs = grec + (size_t)(gr % (unsigned long long)kRecDepth) * G;
+        if (cluster_wait_records(rs, lane, G, gr, rec)) {  // rec: prefetched in the previous round
           dec = 2;
-        } else if (cluster_tbest_at(p, rec, lane, Tfit, TQ, tholder, sWin, win_n, win_head, stall, prev_lfv)) {
-          dec = 1;
+        } else {
+          proc = gr;
+          if (cluster_tbest_at(p, rec, lane, Tfit, TQ, tholder, sWin, win_n, win_head, stall, prev_lfv) && at_on)
+            dec = 1;
         }
       }
-      if (lane == 0) s_dec = dec;
+      if (lane < S) st_peer_u32(peer_addr(&s_dec[slot], (uint32_t)lane), dec);
     }
-    __syncthreads();
-
-    // 3. Candidate row, its Q, the decision word and the key into this CTA's slot in
-    // every CTA of the cluster, as 16-byte vectors (the row only when there is a
-    // candidate); only the warps that store remotely arrive with release order.
-    const unsigned long long lkey = s_key;
-    const uint32_t mydec = s_dec;
-    const int XS = cluster_slot_stride(D);
-    const int nv = XS / 4;           // vectors per slot
-    const int v_tail = (D + 3) / 4;  // first vector past the row: Q, decision, key live in the slot tail
-    bool pushed = false;
-    {
-      const bool have = lkey != kKeyEmpty;
-      const int iw = have ? key_idx(lkey) - n0 : 0;
-      const bool wimp = have && sImp[iw] != 0;
-      const float* src = wimp ? cX + iw * D : sP + iw * D;
-      const int qx = have ? (wimp ? sFQ[iw] : sPQ[iw]) : 0;
-      const int v0 = have ? 0 : (D / 4);  // without a candidate only the vectors holding the tail
-      const int per = nv - v0;
-      float* slot = sXrow + (par * S + q) * XS;
-      for (int t = tid; t < S * per; t += nt) {
-        const int peer = t / per, v = v0 + (t - peer * per);
-        float e[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int j = 4 * v + c;
-          float x = 0.0f;
-          if (j < D) x = src[j];
-          else if (j == D) x = __int_as_float(qx);
-          else if (j == D + 1) x = __uint_as_float(mydec);
-          else if (j == D + 2) x = __uint_as_float((uint32_t)lkey);
-          else if (j == D + 3) x = __uint_as_float((uint32_t)(lkey >> 32));
-          e[c] = x;
-        }
-        st_peer_v4(peer_addr(slot + 4 * v, (uint32_t)peer), e[0], e[1], e[2], e[3]);
-        pushed = true;
-      }
-      (void)v_tail;
-    }
-    if (__any_sync(0xffffffffu, pushed)) cluster_barrier();
-    else cluster_barrier_relaxed_arrive();
-    if (tid == 0) s_key = kKeyEmpty;
-
-    // 4. The cluster's decision and best key, reduced by every warp over the S slots.
-    uint32_t cdec = 0;
-    unsigned long long gkey = kKeyEmpty;
-    int gw = 0;
-    {
-      const float* sl = sXrow + (par * S + (lane < S ? lane : 0)) * XS;
-      if (lane < S) {
-        cdec = __float_as_uint(sl[D + 1]);
-        gkey = ((unsigned long long)__float_as_uint(sl[D + 3]) << 32) | __float_as_uint(sl[D + 2]);
-        gw = lane;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        cdec = max(cdec, __shfl_xor_sync(0xffffffffu, cdec, o));
-        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, gkey, o);
-        const int ow = __shfl_xor_sync(0xffffffffu, gw, o);
-        if (ok < gkey || (ok == gkey && ow < gw)) {
-          gkey = ok;
-          gw = ow;
-        }
-      }
-    }
-    if (cdec >= 2) {
+    cluster_barrier();
+    const uint32_t dec = s_dec[slot];
+    const uint32_t any = s_any[slot];
+    if (ctrl && lane == 0) s_any[(j + 2) % 3] = 0u;  // the flag of round j - 1, read by every warp before this barrier
+    if (ctrl && q == 0 && lane < G && j + 1 > kLag)  // the records the next round applies, in flight meanwhile
+      rec = ld_relaxed_u64(grec + (size_t)((gk + 1ull - (unsigned long long)kLag) % (unsigned long long)kRecDepth) * G + lane);
+    if (dec >= 2) {
       failed = true;
       if (tid == 0) ctl->status = SEPSO_ETIMEOUT;
       break;
     }
-    if (cdec == 1) {  // stop at k - 1: discard iteration k
-      if (p.spec) xb ^= 1;
-      --k;
-      --done;
+    if (dec == 1) {  // Auto Truncation stopped at iteration k0 + j - kLag: its state is B
+      c = B;
+      done = j - kLag;
+      stop_round = j;
       break;
     }
-
-    // 5. The group's Gbest and its record; Pbest and the update (one pass).
-    const float* grow = sG;  // this iteration's Gbest row
-    const bool gimp = gkey != kKeyEmpty && key_fit(gkey) < gfit;
-    if (gimp) {
-      grow = sXrow + (par * S + gw) * XS;
-      gfit = key_fit(gkey);
-      gq = __float_as_int(grow[D]);
+    if (!compute) continue;  // a round that only collects a decision
+    // the group's lowest key of the round (the lowest-index particle of lowest
+    // Pbest): each lane's lowest slot, then the lowest fitness bits over the warp,
+    // then the lowest index bits among the lanes that hold them
+    unsigned long long gkey = kKeyEmpty;
+    if (any) {
+      const unsigned long long* kk = sKeys + (size_t)par * S * ppc;
+      for (int i = lane; i < S * ppc; i += 32) gkey = min(gkey, kk[i]);
+      const uint32_t hi = __reduce_min_sync(0xffffffffu, (uint32_t)(gkey >> 32));
+      const uint32_t lo = __reduce_min_sync(0xffffffffu, (uint32_t)(gkey >> 32) == hi ? (uint32_t)gkey : 0xffffffffu);
+      gkey = ((unsigned long long)hi << 32) | lo;
     }
-    if (q == 0) {
-      if (gimp)
-        for (int j = tid; j < D; j += nt) gGb[g * D + j] = grow[j];
-      if (tid == 0) st_relaxed_u64(grec + (size_t)(gk % (unsigned long long)kRecDepth) * G + g, make_rec(gfit, gq, gk));
-    }
-    gk_last = gk;
-    for (int i = tid; i < nl; i += nt) {
-      if (sImp[i]) {
-        sPfit[i] = sF[i];
-        sPQ[i] = sFQ[i];
+    if (gkey != kKeyEmpty && key_fit(gkey) < c.gfit) {
+      const int nw = key_idx(gkey);
+      const int qw = nw / ppc;
+      const float* st = sStage + (size_t)(par * ppc + (nw - qw * ppc)) * SR;
+      c.gfit = key_fit(gkey);
+      c.gq = key_q(gkey);
+      if (c.gq >= (int)kQSat) c.gq = ld_peer_s32(peer_addr(st + 2 * T, (uint32_t)qw));
+      if (wl) {
+        const float2 v = ld_peer_f2(peer_addr(st + 2 * lane, (uint32_t)qw));
+        c.gx = v.x;
+        c.gy = v.y;
       }
     }
-    if (p.mode == kModePlan && k >= p.max_iters) {  // the cap: Algorithm 1 stops before the update
-      for (int it = tid; it < nl * D; it += nt)
-        if (sImp[it / D]) sP[it] = cX[it];
-      capstop = true;
-      break;
-    }
-
-    // Eq. TOF_omega, Eq. TOF_V (+ clip to V_range), Eq. TOF_X (+ clip to X_range),
-    // with the Pbest rows of this iteration (each element by the thread that updates it).
-    float* nX = p.spec ? (xb ? sX0 : sX1) : cX;
-    float* nV = p.spec ? (xb ? sV0 : sV1) : cV;
-    const float w = w_init - (w_init - w_end) / (float)p.max_iters * (float)k;
-    for (int it = tid; it < nl * D; it += nt) {
-      const int i = it / D;
-      const int j = it - i * D;
-      const float x = cX[it];
-      if (sImp[i]) sP[it] = x;
-      float v = w * cV[it];
-      v = fmaf(sR[i * 4 + 0], sP[it] - x, v);
-      v = fmaf(sR[i * 4 + 1], grow[j] - x, v);
-      const float ext = (j < T) ? p.W : p.H;
-      const float vmax = vlim * ext;
-      v = fminf(fmaxf(v, -vmax), vmax);
-      nV[it] = v;
-      nX[it] = fminf(fmaxf(x + v, 0.0f), ext);
-    }
-    if (p.spec) xb ^= 1;
-    // the next iterations read this Gbest row from sG; nobody reads sG in this one
-    // when it changed (the update above read the slot), and the slot stays valid
-    // until the next cluster barrier
-    if (gimp)
-      for (int j = tid; j < D; j += nt) sG[j] = grow[j];
-    __syncthreads();
-    if (p.mode == kModeStep && done >= p.step_iters) {  // a plain continuation ends after the update
-      capstop = true;
-      break;
+    if (ctrl && q == 0 && lane == 0)
+      st_relaxed_u64(grec + (size_t)(gk % (unsigned long long)kRecDepth) * G + g, make_rec(c.gfit, c.gq, gk));
+    B = A;
+    A = c;
+    done = j;
+    if (plan && j == n_compute) continue;  // the cap: Algorithm 1 stops after the best update
+    if (wl) {
+      // Eq. TOF_omega, Eq. TOF_V (+ clip to V_range), Eq. TOF_X (+ clip to X_range)
+      const float w = w_init - (w_init - w_end) / (float)p.max_iters * (float)(k0 + j);
+      float v = w * c.vx;
+      v = fmaf(a1, c.px - c.x, v);
+      v = fmaf(a2, c.gx - c.x, v);
+      const float vmx = vlim * p.W;
+      v = fminf(fmaxf(v, -vmx), vmx);
+      c.vx = v;
+      c.x = fminf(fmaxf(c.x + v, 0.0f), p.W);
+      v = w * c.vy;
+      v = fmaf(a1, c.py - c.y, v);
+      v = fmaf(a2, c.gy - c.y, v);
+      const float vmy = vlim * p.H;
+      v = fminf(fmaxf(v, -vmy), vmy);
+      c.vy = v;
+      c.y = fminf(fmaxf(c.y + v, 0.0f), p.H);
     }
   }
 
   // Write back the swarm (state for sepso_step / sepso_get_state).
-  {
-    const float* fX = xb ? sX1 : sX0;
-    const float* fV = xb ? sV1 : sV0;
-    for (int it = tid; it < nl * D; it += nt) {
-      gX[it] = fX[it];
-      gV[it] = fV[it];
-      gP[it] = sP[it];
+  if (wl) {
+    p.X[prow + lane] = c.x;
+    p.X[prow + T + lane] = c.y;
+    p.V[prow + lane] = c.vx;
+    p.V[prow + T + lane] = c.vy;
+    p.P[prow + lane] = c.px;
+    p.P[prow + T + lane] = c.py;
+  }
+  if (live && lane == 0) {
+    p.Pfit[prow / D] = c.pfit;
+    p.PQ[prow / D] = c.pq;
+  }
+  if (q == 0 && warp == 0) {  // particle 0's warp holds the group's Gbest
+    if (lane < T) {
+      gGb[(size_t)g * D + lane] = c.gx;
+      gGb[(size_t)g * D + T + lane] = c.gy;
     }
-  }
-  for (int i = tid; i < nl; i += nt) {
-    gPfit[i] = sPfit[i];
-    gPQ[i] = sPQ[i];
-  }
-  if (q == 0 && tid == 0) {
-    p.Gfit[(size_t)r * G + g] = gfit;
-    p.GQ[(size_t)r * G + g] = gq;
+    if (lane == 0) {
+      p.Gfit[(size_t)r * G + g] = c.gfit;
+      p.GQ[(size_t)r * G + g] = c.gq;
+    }
   }
   __syncthreads();
   cluster_barrier();  // no shared-memory access between the CTAs after this point
-  if (q == 0 && tid == 0) red_release_add(&p.counter[r].fin, 1u);
-  if (cr != 0) return;
+  if (q == 0 && ctrl && lane == 0) {
+    // records of iterations a stop discarded: the next launch counts iterations from
+    // the stop, so their tags would match its first rounds
+    if (stop_round > 0)
+      for (int jj = stop_round - kLag + 1; jj < stop_round; ++jj)
+        if (jj >= 1 && jj <= n_compute)
+          grec[(size_t)((kbase + (unsigned long long)jj) % (unsigned long long)kRecDepth) * G + g] = 0ull;
+    red_release_add(&p.counter[r].fin, 1u);
+  }
+  if (cr != 0 || !ctrl) return;
 
-  // CTA 0 of the run: every group has written its rows and last record.
+  // The control warp of CTA 0 of the run: every group has written its rows and
+  // records; apply the records not yet applied, then the results.
   int timed_out = 0;
-  if (tid == 0) {
+  if (lane == 0) {
     timed_out = counter_wait_bounded(&p.counter[r].fin, (unsigned int)G * (unsigned int)(nfin + 1), kWaitLimitNs)
                     ? 0
                     : 1;
     fence_acq_rel_gpu();
   }
-  if (__syncthreads_or(timed_out)) {
+  __syncwarp();
+  if (__shfl_sync(0xffffffffu, timed_out, 0)) {
     failed = true;
-    if (tid == 0) ctl->status = SEPSO_ETIMEOUT;
+    if (lane == 0) ctl->status = SEPSO_ETIMEOUT;
   }
-  if (!failed && capstop && warp == 0) {
-    // the records of the last iteration (the loop ended after publishing them)
-    unsigned long long rec = lane < G ? ld_relaxed_u64(grec + (size_t)(gk_last % (unsigned long long)kRecDepth) * G + lane) : 0ull;
-    if (cluster_wait_records(grec + (size_t)(gk_last % (unsigned long long)kRecDepth) * G, lane, G, gk_last, rec)) {
+  const unsigned long long gk_final = kbase + (unsigned long long)done;
+  for (unsigned long long gr = proc + 1; !failed && gr <= gk_final; ++gr) {
+    const unsigned long long* rs = grec + (size_t)(gr % (unsigned long long)kRecDepth) * G;
+    unsigned long long rec = lane < G ? ld_relaxed_u64(rs + lane) : 0ull;
+    if (cluster_wait_records(rs, lane, G, gr, rec)) {
+      failed = true;
       if (lane == 0) ctl->status = SEPSO_ETIMEOUT;
     } else {
       cluster_tbest_at(p, rec, lane, Tfit, TQ, tholder, sWin, win_n, win_head, stall, prev_lfv);
     }
   }
-  if (tid == 0) s_dec = (uint32_t)(tholder + 1);  // Tbest is tracked by warp 0 alone
-  __syncthreads();
-  // Tbest's row: the holder group's Gbest row (which changes only together with
-  // Tbest), staged in the exchange slots (free after the last cluster barrier).
-  float* sTrow = sXrow;
-  const int holder = (int)s_dec - 1;
-  const float* src = (holder >= 0) ? gGb + (size_t)holder * D : gTb;
-  for (int j = tid; j < D; j += nt) sTrow[j] = __ldcg(src + j);
-  __syncthreads();
-  for (int j = tid; j < D; j += nt) {
+  // Tbest's row: the holder group's Gbest row, staged in this CTA's (now unused)
+  // stage area
+  float* sTrow = sStage;
+  const float* src = (tholder >= 0) ? gGb + (size_t)tholder * D : gTb;
+  for (int j = lane; j < D; j += 32) sTrow[j] = __ldcg(src + j);
+  __syncwarp();
+  const int k = k0 + done;
+  for (int j = lane; j < D; j += 32) {
     gTb[j] = sTrow[j];
-    if (p.mode == kModePlan) {
+    if (plan) {
       p.res_wp[(size_t)r * D + j] = sTrow[j];
       p.prevT[(size_t)r * D + j] = sTrow[j];
     }
   }
-  for (int j = tid; j < 3 * G; j += nt) p.gword[(size_t)r * 3 * G + j] = kKeyEmpty;
-  if (tid == 0) {
+  for (int j = lane; j < 3 * G; j += 32) p.gword[(size_t)r * 3 * G + j] = kKeyEmpty;
+  if (lane == 0) {
     // the grid-wide form's barrier counts C per iteration of the run, and expects
     // its group words empty: keep both as if it had run these iterations
     atomicAdd(&p.counter[r].count, (unsigned int)p.cta_grid * (unsigned int)done);
@@ -1183,8 +1205,9 @@ __global__ void __launch_bounds__(512) swarm_cluster_kernel(const SwarmParams p)
     ctl->k = k;
     ctl->iters_total += done;
     ctl->fin_launches = nfin + 1;
-    if (p.mode == kModePlan) {
+    if (plan) {
       ctl->plans_total += 1;
+      const int nseg = T + 1;
       float len = 0.0f;
       for (int s = 0; s < nseg; ++s) {
         const float ax = (s == 0) ? sx : sTrow[s - 1];

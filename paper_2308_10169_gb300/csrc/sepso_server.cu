@@ -109,7 +109,7 @@ ServerLayout server_layout(const sepso_server_config& c, int S) {
   L.prevT = take((size_t)c.n_agents * Dm * 4);
   L.admits = take(S * sizeof(Admit));
   L.admit_circ = take(S * (size_t)pair_block_f4((int)Om) * 16);
-  L.status = take(4);
+  L.status = take(16);  // status, then the first failed index check of the batch kernel
   L.total = a256(off);
   return L;
 }

@@ -65,7 +65,7 @@ class SepsoConfig:
     threads: int = 0           # 0 = automatic
     circle_split: int = 0      # 0 = automatic
     fitness_mode: int = 0      # 0 = automatic; 1 lane group per particle; 2 items over the CTA
-    exchange: int = 0          # 0 automatic (grid-wide); 1 grid-wide; 2 one cluster per group (C3 = 0); 3 cluster when C3 = 0
+    exchange: int = 0          # 0 automatic and 3: one cluster per group when C3 = 0 and it fits; 1 grid-wide; 2 cluster (required)
     obstacle_kind: int = 0     # 0 circles; 1 polygon edges (max_obstacles = edge capacity)
 
     @property

@@ -2,12 +2,13 @@
 
 The grid-wide form puts all CTAs of a run behind one barrier per iteration; the
 cluster form (every group's C3 = 0, so Eq. TOF_V needs only the group's own
-Gbest) trades the group best inside one thread-block cluster per group and the
-groups' (Gfit, Q) through records read one iteration late, with Auto Truncation
-decided one iteration late and the speculative iteration discarded.  Its
+Gbest) runs one thread-block cluster per group with one warp per particle and the
+rows in registers, trades the group best inside the cluster and the groups'
+(Gfit, Q) through records read two iterations late, with Auto Truncation decided
+two iterations late and the state of the stopping iteration restored.  Its
 decisions, bests and arithmetic are meant to be those of the grid-wide form, so
-results and states are compared bit for bit; the grid-wide form itself is held
-to the oracle by test_gpu_parity.py.
+results and states are compared bit for bit; the grid-wide form itself is held to
+the oracle by test_gpu_parity.py.
 """
 import numpy as np
 import pytest
@@ -46,12 +47,14 @@ def _same_state(pa, pb, run=0):
         np.testing.assert_array_equal(sa[name], sb[name], err_msg=name)
 
 
-@pytest.mark.parametrize("cpg", [0, 1, 3, 8, 16])
-def test_cluster_form_matches_grid_form_dynamic_cycles(native, cpg):
+@pytest.mark.parametrize("N,cpg", [(170, 0), (170, 12), (96, 8), (48, 4), (48, 16), (30, 2), (1, 0)])
+def test_cluster_form_matches_grid_form_dynamic_cycles(native, N, cpg):
     # the dynamic workload: PI, stall-counter AT (cap 300), moving circles; several
-    # cycles so that truncation, PI and the carried state all take part
+    # cycles so that truncation, PI and the carried state all take part; CTAs of
+    # 15 down to 3 particle warps, a ragged last CTA (170 = 11 x 15 + 5) and a
+    # one-particle group
     cfg, scene, hyper = dynamic_workload(2)
-    cfg = cfg.with_(max_iters=120)
+    cfg = cfg.with_(max_iters=120, N=N)
     ga, cl = _pair(cfg, scene, hyper, cpg)
     iters = []
     for cyc in range(4):
@@ -109,7 +112,7 @@ def test_cluster_form_several_runs_and_switching_forms(native):
     # (cluster form) and C3 > 0 (grid-wide form): the barrier counter, group words
     # and records stay consistent across the switches
     cfg, scene, hyper = dynamic_workload(4)
-    cfg = cfg.with_(runs=4, max_iters=60)
+    cfg = cfg.with_(runs=4, N=40, max_iters=60)
     ref = Planner(cfg.with_(exchange=1))
     mix = Planner(cfg.with_(exchange=3))
     hyper_c3 = hyper.copy()
@@ -134,13 +137,13 @@ def test_cluster_form_several_runs_and_switching_forms(native):
 
 
 def test_cluster_form_hsef_matches(native):
-    # the HSEF L-runs (32 runs, no AT, cap 300) in both forms
+    # HSEF L-runs (8 runs, no AT, cap 100) in both forms
     cfg, scene, _ = dynamic_workload(0)
     out = []
     for ex in (1, 2):
-        hp = Planner(cfg.with_(runs=32, at_mode=0, use_pi=False, max_iters=100, exchange=ex))
+        hp = Planner(cfg.with_(runs=8, N=24, at_mode=0, use_pi=False, max_iters=100, exchange=ex))
         hp.set_scene(scene, motion=False)
-        hist = hp.hsef(HG=8, HN=4, E=3, hhyper=TABLE_HYPER8, lo=HSEF_BOX_LO, hi=HSEF_BOX_HI,
+        hist = hp.hsef(HG=2, HN=4, E=3, hhyper=TABLE_HYPER8[:2], lo=HSEF_BOX_LO, hi=HSEF_BOX_HI,
                        l_vlimit=0.05, hseed=77)
         out.append((hist.cpu().numpy(), *hp.hsef_best()))
         assert hp.exchange_form() == ("grid" if ex == 1 else "cluster")
@@ -165,4 +168,22 @@ def test_cluster_form_refused_when_an_update_needs_tbest(native):
     assert auto.exchange_form() == "grid"
     auto.set_hyper(sample_hyper(3, cfg.G))
     assert auto.exchange_form() == "cluster"
-    assert Planner(cfg).exchange_form() == "grid"   # the automatic choice
+    auto0 = Planner(cfg)   # the automatic choice: the cluster form whenever it applies
+    auto0.set_scene(scene)
+    auto0.set_hyper(hy)
+    assert auto0.exchange_form() == "grid"
+    auto0.set_hyper(sample_hyper(3, cfg.G))
+    assert auto0.exchange_form() == "cluster"
+    assert Planner(cfg.with_(exchange=1)).exchange_form() == "grid"
+
+
+def test_cluster_form_refused_when_it_does_not_fit(native):
+    cfg, scene, hyper = static_workload(1)
+    for bad in (dict(T=32), dict(N=400), dict(runs=64)):
+        with pytest.raises(SepsoError) as err:
+            Planner(cfg.with_(exchange=2, **bad))
+        assert err.value.code == -7  # SEPSO_ERANGE
+        pl = Planner(cfg.with_(exchange=3, **bad))   # falls back to the grid-wide form
+        pl.set_scene(scene)
+        pl.set_hyper(hyper)
+        assert pl.exchange_form() == "grid"
