@@ -81,7 +81,7 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of each planning kernel
 # on this workload (ncu --set full captures summarised in profiles/); None whenever
 # the kernel changed since its capture.
-SWARM_TRAFFIC_BYTES = {"swarm_kernel": 117504, "swarm_cluster_kernel": None}
+SWARM_TRAFFIC_BYTES = {"swarm_kernel": None, "swarm_cluster_kernel": 85760}
 # The same for gemm_tc_kernel on the MLP's grad-W1 product (1024 x 4104 x 4096),
 # profiles/gemm_tc_kernel_mlp_gradW1.md.
 GEMM_GRADW1_TRAFFIC_BYTES = 42132480
@@ -136,23 +136,78 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clock and clock-event (throttle) reasons sampled during the timed region.
+
+    NVML is read directly (the driver's libnvidia-ml, through ctypes) every
+    ``period`` seconds from a thread, so that even a timed region of a few
+    milliseconds gets samples; the first sample is taken as the region starts.
+    Where NVML cannot be loaded, ``nvidia-smi -lms 50`` is read instead."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # nvmlClocksEventReasons bits (NVML API): SwPowerCap, HwSlowdown, SwThermal, HwThermal
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40}
+    NVML_CLOCK_SM = 1
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period: float = 0.001):
         self.gpu = gpu_index
+        self.period = period
         self.proc = None
         self.lines = []
+        self.samples = []  # (sm_mhz, sm_max_mhz, reason bits)
+        self.source = None
+        self._stop = threading.Event()
+        self.t = None
+
+    def _nvml(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2")
+        h = ctypes.c_void_p()
+        uuid = None
+        try:  # the CUDA device this rank runs on, whatever CUDA_VISIBLE_DEVICES maps
+            import torch
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(self.gpu).uuid)
+        except Exception:
+            pass
+        if not (uuid and lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) == 0):
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) != 0:
+                raise RuntimeError("nvmlDeviceGetHandleByIndex_v2")
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint(0)
+        lib.nvmlDeviceGetMaxClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(mx))
+        return lib, h, reasons, mx.value
+
+    def _poll(self, lib, h, reasons, mx):
+        import ctypes
+        clk, bits = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        while True:
+            ok = lib.nvmlDeviceGetClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(clk)) == 0
+            ok = ok and reasons(h, ctypes.byref(bits)) == 0
+            if ok:
+                self.samples.append((float(clk.value), float(mx), int(bits.value)))
+            if self._stop.wait(self.period):
+                break
 
     def __enter__(self):
+        try:
+            lib, h, reasons, mx = self._nvml()
+            self.source = "NVML, every 1 ms"
+            self.t = threading.Thread(target=self._poll, args=(lib, h, reasons, mx), daemon=True)
+            self.t.start()
+            return self
+        except Exception:
+            pass
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi -lms 50"
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
@@ -164,16 +219,22 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        self._stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if self.t is not None:
             self.t.join(timeout=2)
 
     def summary(self):
         sm, mx, reasons = [], [], set()
+        for c, m, bits in self.samples:
+            sm.append(c)
+            mx.append(m)
+            reasons.update(n for n, b in self.REASON_BITS.items() if bits & b)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -188,9 +249,9 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "source": self.source}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": self.source}
 
 
 # ----------------------------------------------------------------------------
