@@ -107,6 +107,9 @@ def parse():
     ap.add_argument("--serve-rates", type=str, default="20000,5000",
                     help="offered request rates (1/s) of the serving section ('' = skip it)")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-prior-train", type=int, default=8192,
+                    help="training snapshots per circle count of the serving prior (0: serve without one)")
+    ap.add_argument("--serve-prior-rounds", type=int, default=2)
     ap.add_argument("--serve-radii", type=str, default="3,15",
                     help="circle radii U[a,b] of the serving scenes with 32 circles (scaled by sqrt(32/O))")
     ap.add_argument("--prior-train", type=int, default=16384,
@@ -975,15 +978,52 @@ def _world_step(ag):
                 ag[pv][d] *= -1
 
 
-def run_serve(rate: float, seconds: float, n_agents: int = 2048, radii=(3.0, 15.0)):
-    """Open-loop serving: Poisson arrivals at `rate`, 2048 agents with mixed T and O."""
+SERVE_SLOTS = 1024
+
+
+def train_serving_prior(radii, n_per_set: int, rounds: int, epochs: int = 30):
+    """The learned prior that seeds served requests: T = 20 proposals, trained by
+    self-training (fit_prior_sets) on snapshots shaped like the serving scenes, both
+    circle counts, labelled by the planner itself (G = 8 x N = 170, cap 300, stall AT
+    tolerance 1.0, the shared evolved hyper-parameters).  Its rows after the training
+    ones are the server's scratch."""
+    import torch
+
+    from paper_2308_10169_gb300.inputs import prior_init_params, serving_prior_scenes
+    from paper_2308_10169_gb300.prior import Prior, fit_prior_sets
+    sets = [serving_prior_scenes(100 + k, n_per_set, O, r_range=radii) for k, O in enumerate((32, 256))]
+    n = 2 * n_per_set
+    pr = Prior(T=20, hidden1=1024, hidden2=512, capacity=n + SERVE_SLOTS, max_batch=4096, max_circles=256)
+    pr.set_params(prior_init_params(0, pr.K, 1024, 512, 40))
+    hy, _ = shared_hyper()
+    t0 = time.perf_counter()
+    hist = fit_prior_sets(pr, sets, rounds=rounds, epochs=epochs, batch=4096, seed=5, n_prior=43, T=20, G=8, N=170,
+                          hyper=hy, max_iters=300, stall_iters=10, stall_tol=1.0)
+    torch.cuda.synchronize()
+    info = {"workload": f"{n} serving-like snapshots ({n_per_set} with 32 circles, {n_per_set} with 256; radii "
+                        f"U[{radii[0]:g},{radii[1]:g}] x sqrt(32/O), start/target drift U{{0..99}}), T=20 labels "
+                        "by the planner (G=8 x N=170, cap 300, AT stall 10 tolerance 1.0, shared evolved hyper), "
+                        f"{rounds} self-training rounds x {epochs} epochs, MLP 4104 -> 1024 -> 512 -> 40",
+            "label_median_cost_per_round": hist["label_cost"],
+            "label_collision_free_per_round": hist["label_collision_free"],
+            "loss_first_last_per_round": hist["losses"], "train_steps": hist["steps"],
+            "train_s": hist["train_s"], "label_plan_s": hist["plan_s"], "wall_s": time.perf_counter() - t0}
+    return pr, n, info
+
+
+def run_serve(rate: float, seconds: float, n_agents: int = 2048, radii=(3.0, 15.0), prior=None, prior_row: int = 0,
+              n_prior: int = 8):
+    """Open-loop serving: Poisson arrivals at `rate`, 2048 agents with mixed T and O;
+    with a learned prior attached when one is given."""
     from paper_2308_10169_gb300 import Server
     from paper_2308_10169_gb300.inputs import poisson_arrivals, serving_workload
     agents = serving_workload(0, n_agents, r_range=radii)
     arr = poisson_arrivals(0, rate, seconds)
     who = np.random.default_rng(11).integers(0, n_agents, len(arr))
-    sv = Server(n_agents=n_agents, max_slots=1024, G=8, N=32, Tmax=40, Omax=256, max_iters=100,
+    sv = Server(n_agents=n_agents, max_slots=SERVE_SLOTS, G=8, N=32, Tmax=40, Omax=256, max_iters=100,
                 stall_iters=10)
+    if prior is not None:
+        sv.set_prior(prior, n_prior, first_row=prior_row)
     for a, ag in enumerate(agents):
         sv.set_hyper(ag["hyper"], agent=a)
     for i, (t, a) in enumerate(zip(arr, who)):
@@ -1005,15 +1045,18 @@ def run_serve(rate: float, seconds: float, n_agents: int = 2048, radii=(3.0, 15.
                                                                   if d["T"] == T and agents[d["agent"]]["O"] == O]))
                                       for T in (8, 20, 40) for O in (32, 256)},
             "at_fire_rate": float(np.mean([d["iters"] < 100 for d in done])), "slots": st["slots"],
-            "ticks": st["ticks"], "gpu_launches": st["launches"]}
+            "ticks": st["ticks"], "gpu_launches": st["launches"],
+            "prior": None if prior is None else {"n_prior": n_prior, "proposal_T": 20}}
 
 
-def serve_single_scene(n: int = 256, n_agents: int = 2048, radii=(3.0, 15.0)):
+def serve_single_scene(n: int = 256, n_agents: int = 2048, radii=(3.0, 15.0), prior=None, prior_row: int = 0,
+                       n_prior: int = 8):
     """The plain single-scene kernel on the serving mix: the first request of n agents
     (no previous path), one plan at a time through sepso_plan (host scene in,
     waypoints out), with the server's planner settings; and the same n requests as
     one burst through the server.  Same algorithm and random streams, so the median
-    costs agree; throughput and latency are the comparison."""
+    costs agree; throughput and latency are the comparison.  With a prior, the burst
+    once more with it attached (its proposals seed the requests)."""
     import torch
 
     from paper_2308_10169_gb300 import Planner, Server
@@ -1041,28 +1084,37 @@ def serve_single_scene(n: int = 256, n_agents: int = 2048, radii=(3.0, 15.0)):
         its.append(int(r.iters))
         qs.append(int(r.Q))
     lat = np.array(lat) * 1e3
-    sv = Server(n_agents=n_agents, max_slots=1024, G=8, N=32, Tmax=40, Omax=256, max_iters=100, stall_iters=10)
-    for a, ag in enumerate(agents):
-        sv.set_hyper(ag["hyper"], agent=a)
-    for a, ag in enumerate(agents):
-        sv.submit_at(a, ag["T"], ag["start"], ag["target"], ag["circles"], tag=a, arrival_s=0.0)
-    sv.clock(restart=True)
-    sv.run()
-    done = sv.poll(max_n=n + 1)
-    slat = np.array([d["finish_s"] - d["arrival_s"] for d in done]) * 1e3
-    span = max(d["finish_s"] for d in done)
-    return {"requests": n,
-            "single_scene": {"plans_per_s": n / (lat.sum() / 1e3),
-                             "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                                            "p99": float(np.percentile(lat, 99))},
-                             "median_cost": float(np.median(costs)), "iters_per_plan": float(np.mean(its)),
-                             "collision_free": float(np.mean(np.array(qs) == 0))},
-            "server_burst": {"plans_per_s": len(done) / span,
-                             "latency_ms": {"p50": float(np.percentile(slat, 50)),
-                                            "p99": float(np.percentile(slat, 99))},
-                             "median_cost": float(np.median([d["cost"] for d in done])),
-                             "iters_per_plan": float(np.mean([d["iters"] for d in done])),
-                             "collision_free": float(np.mean([d["Q"] == 0 for d in done]))}}
+
+    def burst(pr):
+        sv = Server(n_agents=n_agents, max_slots=SERVE_SLOTS, G=8, N=32, Tmax=40, Omax=256, max_iters=100,
+                    stall_iters=10)
+        if pr is not None:
+            sv.set_prior(pr, n_prior, first_row=prior_row)
+        for a, ag in enumerate(agents):
+            sv.set_hyper(ag["hyper"], agent=a)
+        for a, ag in enumerate(agents):
+            sv.submit_at(a, ag["T"], ag["start"], ag["target"], ag["circles"], tag=a, arrival_s=0.0)
+        sv.clock(restart=True)
+        sv.run()
+        done = sv.poll(max_n=n + 1)
+        slat = np.array([d["finish_s"] - d["arrival_s"] for d in done]) * 1e3
+        span = max(d["finish_s"] for d in done)
+        return {"plans_per_s": len(done) / span,
+                "latency_ms": {"p50": float(np.percentile(slat, 50)), "p99": float(np.percentile(slat, 99))},
+                "median_cost": float(np.median([d["cost"] for d in done])),
+                "iters_per_plan": float(np.mean([d["iters"] for d in done])),
+                "collision_free": float(np.mean([d["Q"] == 0 for d in done]))}
+
+    out = {"requests": n,
+           "single_scene": {"plans_per_s": n / (lat.sum() / 1e3),
+                            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                           "p99": float(np.percentile(lat, 99))},
+                            "median_cost": float(np.median(costs)), "iters_per_plan": float(np.mean(its)),
+                            "collision_free": float(np.mean(np.array(qs) == 0))},
+           "server_burst": burst(None)}
+    if prior is not None:
+        out["server_burst_prior"] = burst(prior)
+    return out
 
 
 def run_prior(n_train: int, n_eval: int, rounds: int, epochs: int, single: dict, B: int = 4096):
@@ -1315,13 +1367,19 @@ def main():
             line["gemm"] = run_gemm()
         if world == 1 and "serve" in sections and args.serve_rates:
             radii = tuple(float(x) for x in args.serve_radii.split(","))
+            rates = [float(r) for r in args.serve_rates.split(",")]
+            pr, prow, pinfo = (train_serving_prior(radii, args.serve_prior_train, args.serve_prior_rounds)
+                               if args.serve_prior_train > 0 else (None, 0, None))
             line["serve"] = {
                 "workload": "2048 agents, Poisson arrivals, T in {8,20,40}, O in {32,256} circles, centres "
                             f"U[60,340]^2, r~U[{radii[0]:g},{radii[1]:g}] x sqrt(32/O), "
                             "obstacles advanced per request, G=8 x N=32, PI warm start on the device, "
                             "AT stall 10 / cap 100, continuous batching (1024 slots)",
-                "runs": [run_serve(float(r), args.serve_seconds, radii=radii) for r in args.serve_rates.split(",")],
-                "vs_single_scene": serve_single_scene(radii=radii)}
+                "runs": [run_serve(r, args.serve_seconds, radii=radii) for r in rates],
+                "prior": pinfo,
+                "runs_prior": [run_serve(r, args.serve_seconds, radii=radii, prior=pr, prior_row=prow)
+                               for r in rates] if pr is not None else None,
+                "vs_single_scene": serve_single_scene(radii=radii, prior=pr, prior_row=prow)}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

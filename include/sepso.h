@@ -427,6 +427,25 @@ int sepso_server_create(const sepso_server_config* cfg, void* d_workspace, size_
 void sepso_server_destroy(sepso_server_handle h);
 /* Hyper-parameters (host G x 6) of one agent, or of all when agent < 0 (sync). */
 int sepso_server_set_hyper(sepso_server_handle h, int32_t agent, const float* hyper);
+/* Attach a learned prior (sepso_prior_*; an extension: the paper has no learned
+ * component) to the server, or detach it (prior NULL).  From the next admission on,
+ * each admitted request's scene is rasterised into the prior's dataset rows
+ * [first_row, first_row + S) (S = the server's slots; they are overwritten), the
+ * prior proposes a path of its own T_p waypoints, and that path becomes the
+ * request's: itself when T = T_p, else the T points at arc-length fractions
+ * 1/(T+1) .. T/(T+1) of the polyline start -> proposal -> target.  The first n_prior
+ * particles of every group then start around it (the PI half-width), before the PI
+ * particles, when its fitness (Sec. 3.3.2, FP32) on the request's scene is below
+ * that of the agent's previous path, or the agent has none -- the gate of
+ * sepso_batch_set_starts.  All of it runs on the device: the rasteriser and the
+ * network on a side stream of the server, beside the tick that is running, the
+ * resampling and the gate on the server's stream before the next tick.  The prior
+ * must have been created on the server's stream and map, with max_circles >= Omax,
+ * T_p <= 64 and capacity >= first_row + S; it must outlive its attachment, and the
+ * caller must not use it while it is attached.  The server does not train it.
+ * Errors: EINVAL, ECUDA (pinned staging). */
+struct sepso_prior_ctx; /* sepso_prior_handle, below */
+int sepso_server_set_prior(sepso_server_handle h, struct sepso_prior_ctx* prior, int32_t n_prior, int32_t first_row);
 /* Queue a request (host inputs, copied): T waypoints (<= Tmax), start[2],
  * target[2], circles O x 3 (O <= Omax).  Errors: EINVAL. */
 int sepso_server_submit(sepso_server_handle h, int32_t agent, int32_t T, const float* start,

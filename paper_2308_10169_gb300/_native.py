@@ -175,6 +175,7 @@ SIGNATURES = {
                                            ctypes.POINTER(_vp)]),
     "sepso_server_destroy": (None, [_vp]),
     "sepso_server_set_hyper": (ctypes.c_int, [_vp, _i32, _fp]),
+    "sepso_server_set_prior": (ctypes.c_int, [_vp, _vp, _i32, _i32]),
     "sepso_server_submit": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp, _fp, _i32, _i64]),
     "sepso_server_submit_at": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp, _fp, _i32, _i64,
                                               ctypes.c_double]),

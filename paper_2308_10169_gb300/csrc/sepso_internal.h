@@ -81,4 +81,17 @@ cudaError_t launch_philox(const uint4* ctr, long long n, uint64_t seed, uint4* o
 cudaError_t launch_watchdog_selftest(const unsigned int* never, unsigned long long limit_ns, int* fired,
                                      cudaStream_t s);
 
+// The learned prior as the request server uses it (sepso_mlp.cu).  prior_shape:
+// the proposal's waypoints, the circles a scene may have, the dataset rows, the map
+// and the stream the handle runs on.  prior_propose_device: rasterise n scenes given on the
+// device -- circles (cx, cy, r, 0) with n + 1 prefix offsets into circ, points n x 4
+// -- into dataset rows [first, first + n) and write their proposals (2 T_p floats
+// per row, row stride ld) to out, all on the handle's stream (async).
+int prior_shape(const sepso_prior_ctx* h, int* T, int* max_circles, int* capacity, float* map_w, float* map_h,
+                cudaStream_t* stream);
+int prior_propose_device(sepso_prior_ctx* h, int first, int n, const float4* circ, const int* coff, const float* pts,
+                         float* out, int ld);
+// Replace the stream the prior's work is issued on; returns the previous one.
+cudaStream_t prior_swap_stream(sepso_prior_ctx* h, cudaStream_t s);
+
 }  // namespace sepso

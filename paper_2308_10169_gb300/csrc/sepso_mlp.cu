@@ -12,7 +12,8 @@
 //                      and/or BF16 output, a transposed BF16 copy, column
 //                      sums; K split into slices summed in order).  Tile N
 //                      (64 / 128 / 256) per launch, and a persistent form.
-//   raster_kernel      occupancy raster of the circles (cell centre inside a disk).
+//   raster_kernel      occupancy raster of the circles (cell centre inside a disk), each
+//                      circle testing only the cells of its bounding box.
 //   small kernels      row gather with a transposed copy, column sums (bias
 //                      gradients), MSE loss gradient, split-K sums, Adam with the
 //                      BF16 weight copies the products read.
@@ -681,26 +682,40 @@ struct RasterArgs {
 };
 
 __global__ void __launch_bounds__(256) raster_kernel(const RasterArgs a) {
-  extern __shared__ float4 rc[];
+  // Occupancy in shared memory, one byte per cell.  Each thread takes circles and
+  // tests only the cells of the circle's bounding box (widened by one cell); the
+  // test of a (cell, circle) pair is the same as over the whole grid, so a cell is
+  // set exactly when its centre lies in some disk.
+  extern __shared__ unsigned char occ[];
   const int s = blockIdx.x;
   const int c0 = a.coff[s], O = a.coff[s + 1] - c0;
-  for (int i = threadIdx.x; i < O; i += blockDim.x) rc[i] = a.circ[c0 + i];
+  const int G = a.grid, g2 = G * G;
+  for (int c = threadIdx.x; c < g2; c += blockDim.x) occ[c] = 0;
   __syncthreads();
-  const float cw = a.W / (float)a.grid, ch = a.H / (float)a.grid;
-  __nv_bfloat16* row = a.X + (size_t)s * a.ldx;
-  const int g2 = a.grid * a.grid;
-  for (int c = threadIdx.x; c < g2; c += blockDim.x) {
-    const int i = c / a.grid, j = c - i * a.grid;
-    const float x = __fmul_rn((float)j + 0.5f, cw), y = __fmul_rn((float)i + 0.5f, ch);
-    bool occ = false;
-    for (int o = 0; o < O; ++o) {
-      const float4 q = rc[o];
-      const float dx = __fsub_rn(x, q.x), dy = __fsub_rn(y, q.y);
-      const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
-      occ |= d2 <= __fmul_rn(q.z, q.z);
+  const float cw = a.W / (float)G, ch = a.H / (float)G;
+  for (int o = threadIdx.x; o < O; o += blockDim.x) {
+    const float4 q = a.circ[c0 + o];
+    const float r2 = __fmul_rn(q.z, q.z);
+    // cell index bounds, clamped in FP32 before the conversion (any finite circle)
+    const float lim = (float)(G + 1);
+    const int j0 = max(0, (int)fminf(fmaxf(floorf((q.x - q.z) / cw - 0.5f) - 1.0f, -1.0f), lim));
+    const int j1 = min(G - 1, (int)fminf(fmaxf(ceilf((q.x + q.z) / cw - 0.5f) + 1.0f, -1.0f), lim));
+    const int i0 = max(0, (int)fminf(fmaxf(floorf((q.y - q.z) / ch - 0.5f) - 1.0f, -1.0f), lim));
+    const int i1 = min(G - 1, (int)fminf(fmaxf(ceilf((q.y + q.z) / ch - 0.5f) + 1.0f, -1.0f), lim));
+    for (int i = i0; i <= i1; ++i) {
+      const float y = __fmul_rn((float)i + 0.5f, ch);
+      const float dy = __fsub_rn(y, q.y);
+      const float dy2 = __fmul_rn(dy, dy);
+      for (int j = j0; j <= j1; ++j) {
+        const float x = __fmul_rn((float)j + 0.5f, cw);
+        const float dx = __fsub_rn(x, q.x);
+        if (__fadd_rn(__fmul_rn(dx, dx), dy2) <= r2) occ[i * G + j] = 1;
+      }
     }
-    row[c] = __float2bfloat16_rn(occ ? 1.0f : 0.0f);
   }
+  __syncthreads();
+  __nv_bfloat16* row = a.X + (size_t)s * a.ldx;
+  for (int c = threadIdx.x; c < g2; c += blockDim.x) row[c] = __float2bfloat16_rn(occ[c] ? 1.0f : 0.0f);
   const float* p = a.pts + 4 * s;
   for (int k = g2 + threadIdx.x; k < a.ldx; k += blockDim.x) {
     const int e = k - g2;
@@ -1714,7 +1729,7 @@ int sepso_prior_add_scenes(sepso_prior_handle h, int32_t first, int32_t n, const
     a.wp = waypoints ? h->at<float>(h->L.swp) : nullptr;
     a.X = h->at<bf16>(h->L.X) + (long long)(first + s0) * d.Kp;
     a.Y = h->at<float>(h->L.Y) + (long long)(first + s0) * d.O;
-    const size_t smem = (size_t)std::max(h->c.max_circles, 1) * 16;
+    const size_t smem = (size_t)d.g * d.g;  // occupancy bytes
     if (smem > 48 * 1024)
       PCUDA(cudaFuncSetAttribute(sepso::raster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     sepso::raster_kernel<<<m, 256, smem, h->stream>>>(a);
@@ -1953,3 +1968,63 @@ int sepso_gemm_bf16_sync(void* stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The prior as the request server uses it (declared in sepso_internal.h).
+// ---------------------------------------------------------------------------
+namespace sepso {
+
+int prior_shape(const sepso_prior_ctx* h, int* T, int* max_circles, int* capacity, float* map_w, float* map_h,
+                cudaStream_t* stream) {
+  if (!h) return pfail(SEPSO_EINVAL, "NULL prior handle");
+  if (T) *T = h->c.T;
+  if (max_circles) *max_circles = h->c.max_circles;
+  if (capacity) *capacity = h->c.capacity;
+  if (map_w) *map_w = h->c.map_w;
+  if (map_h) *map_h = h->c.map_h;
+  if (stream) *stream = h->stream;
+  return SEPSO_OK;
+}
+
+cudaStream_t prior_swap_stream(sepso_prior_ctx* h, cudaStream_t s) {
+  const cudaStream_t old = h->stream;
+  h->stream = s;
+  return old;
+}
+
+int prior_propose_device(sepso_prior_ctx* h, int first, int n, const float4* circ, const int* coff, const float* pts,
+                         float* out, int ld) {
+  if (!h || (n > 0 && (!circ || !coff || !pts || !out))) return pfail(SEPSO_EINVAL, "NULL argument");
+  if (n == 0) return SEPSO_OK;
+  PTRY(check_rows(h, first, n));
+  const Dims& d = h->d;
+  PCUDA(cudaMemcpyAsync(h->at<float>(h->L.P) + 4LL * first, pts, (size_t)n * 16, cudaMemcpyDeviceToDevice,
+                        h->stream));
+  const size_t smem = (size_t)d.g * d.g;  // occupancy bytes
+  if (smem > 48 * 1024)
+    PCUDA(cudaFuncSetAttribute(sepso::raster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int s0 = 0; s0 < n; s0 += d.B) {
+    const int m = std::min(d.B, n - s0);
+    sepso::RasterArgs a;
+    a.n = m;
+    a.grid = d.g;
+    a.K = d.K;
+    a.ldx = d.Kp;
+    a.T = h->c.T;
+    a.O_max = h->c.max_circles;
+    a.W = h->c.map_w;
+    a.H = h->c.map_h;
+    a.circ = circ;        // the offsets are absolute into circ
+    a.coff = coff + s0;
+    a.pts = h->at<float>(h->L.P) + 4LL * (first + s0);
+    a.wp = nullptr;
+    a.X = h->at<bf16>(h->L.X) + (long long)(first + s0) * d.Kp;
+    a.Y = nullptr;
+    sepso::raster_kernel<<<m, 256, smem, h->stream>>>(a);
+    ++h->launches;
+    PCUDA(cudaGetLastError());
+  }
+  return sepso_prior_infer(h, first, n, out, ld);
+}
+
+}  // namespace sepso

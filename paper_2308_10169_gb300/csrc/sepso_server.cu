@@ -69,8 +69,10 @@ struct Admit {
 
 struct ServerLayout {
   size_t sc, tiles, X, V, P, Pfit, PQ, slots, Gb, Tb, circ, hyper, pts, words, Gfit2, GQ2, Tfit2, TQ2, stall2, plv2,
-      done, res_wp, res, prevT, admits, admit_circ, status, total;
+      done, res_wp, res, prevT, admits, admit_circ, status, priorT, prior_use, praw, rcirc, rcoff, rpts, total;
 };
+
+constexpr int kPriorMaxT = 64;  // largest proposal of an attached prior (waypoints)
 
 ServerLayout server_layout(const sepso_server_config& c, int S) {
   const size_t G = c.G, N = c.N, M = G * N, Dm = 2 * (size_t)c.Tmax, Om = std::max(c.Omax, 1);
@@ -110,6 +112,15 @@ ServerLayout server_layout(const sepso_server_config& c, int S) {
   L.admits = take(S * sizeof(Admit));
   L.admit_circ = take(S * (size_t)pair_block_f4((int)Om) * 16);
   L.status = take(16);  // status, then the first failed index check of the batch kernel
+  // learned prior (used once one is attached): the slots' proposals at their own T,
+  // the gate flags, the raw proposals of one admission batch, and its scenes as the
+  // rasteriser reads them
+  L.priorT = take(S * Dm * 4);
+  L.prior_use = take(S * 4);
+  L.praw = take(2 * S * 2 * (size_t)kPriorMaxT * 4);  // by tick parity
+  L.rcirc = take(S * Om * 16);
+  L.rcoff = take((S + 1) * 4);
+  L.rpts = take(S * 16);
   L.total = a256(off);
   return L;
 }
@@ -165,6 +176,67 @@ __global__ void server_admit_kernel(BatchParams p, const Admit* admits, const fl
   for (int g = threadIdx.x; g < 3 * S.G; g += blockDim.x) p.words[S.wo + g] = kKeyEmpty;
 }
 
+// Learned-prior seeds of one admission batch (an extension: the paper has no learned
+// component), one warp per admitted request.  Its proposal (Tp waypoints, row a of
+// praw) becomes the slot's row at the request's T: the proposal itself when T = Tp,
+// else the T points at arc-length fractions 1/(T+1), ..., T/(T+1) of the polyline
+// start -> proposal -> target (FP32, lengths summed in order on lane 0).  Then the
+// batch planner's gate: the proposal seeds the slot only when its fitness (Sec.
+// 3.3.2, FP32) on the request's scene is below that of the agent's previous path, or
+// the agent has none.  The slot's circles are in place (server_admit_kernel ran).
+__global__ void server_prior_kernel(BatchParams p, const Admit* admits, int n, const float* praw, int Tp) {
+  __shared__ float cum[kPriorMaxT + 2];
+  const int a = blockIdx.x, lane = threadIdx.x;
+  if (a >= n) return;
+  const BatchScene S = admits[a].desc;
+  const int s = admits[a].slot, T = S.T;
+  const float sx = admits[a].pts[0], sy = admits[a].pts[1], tx = admits[a].pts[2], ty = admits[a].pts[3];
+  const float* P = praw + (size_t)a * 2 * Tp;
+  float* out = const_cast<float*>(p.prior_path) + (size_t)s * p.Dmax;
+  if (T == Tp) {
+    for (int j = lane; j < 2 * T; j += 32) out[j] = P[j];
+  } else {
+    auto px = [&](int k) { return k == 0 ? sx : (k == Tp + 1 ? tx : P[k - 1]); };
+    auto py = [&](int k) { return k == 0 ? sy : (k == Tp + 1 ? ty : P[Tp + k - 1]); };
+    if (lane == 0) {
+      float c = 0.0f;
+      cum[0] = 0.0f;
+      for (int k = 0; k <= Tp; ++k) {
+        const float dx = px(k + 1) - px(k), dy = py(k + 1) - py(k);
+        c += sqrtf(fmaf(dx, dx, dy * dy));
+        cum[k + 1] = c;
+      }
+    }
+    __syncwarp();
+    const float total = cum[Tp + 1];
+    for (int i = lane; i < T; i += 32) {
+      const float t = total * ((float)(i + 1) / (float)(T + 1));
+      int k = 0;
+      while (k < Tp && cum[k + 1] < t) ++k;  // segment k holds arc length t
+      const float L = cum[k + 1] - cum[k];
+      const float f = L > 0.0f ? fminf(fmaxf((t - cum[k]) / L, 0.0f), 1.0f) : 0.0f;
+      out[i] = fmaf(f, px(k + 1) - px(k), px(k));
+      out[T + i] = fmaf(f, py(k + 1) - py(k), py(k));
+    }
+  }
+  __syncwarp();
+  const int K = circle_pairs(S.O);
+  const int split = warp_split(T, K);
+  const float4* cxy = p.circ + S.co;
+  const float2* nr2 = reinterpret_cast<const float2*>(cxy + K);
+  float len;
+  int q;
+  group_fitness_pairs(out, true, 32, T, split, K, sx, sy, tx, ty, cxy, nr2, &len, &q);
+  const float f_prior = len + S.alpha * powi((float)q, S.beta);
+  int ok = 1;
+  if (S.has_prev && S.n_pi > 0) {
+    group_fitness_pairs(p.agent_prevT + (size_t)S.agent * p.Dmax, true, 32, T, split, K, sx, sy, tx, ty, cxy, nr2,
+                        &len, &q);
+    ok = f_prior < len + S.alpha * powi((float)q, S.beta);
+  }
+  if (lane == 0) const_cast<int32_t*>(p.prior_use)[s] = ok;
+}
+
 struct Request {
   int agent, T, O;
   float pts[4];
@@ -218,6 +290,19 @@ struct sepso_server_ctx {
   int ntiles = 0;
   long long admitted = 0, completed = 0, launches = 0;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  // learned prior (sepso_server_set_prior): its handle, seeds per group, first
+  // dataset row, proposal waypoints, and the admissions' scenes staged for its
+  // rasteriser (pinned, by tick parity)
+  sepso_prior_ctx* prior = nullptr;
+  int n_prior = 0, prior_first = 0, prior_T = 0;
+  // the prior's work runs on a side stream beside the tick's batch kernel: it waits
+  // for ev_tick (main stream, before the tick's launch), the main stream waits for
+  // ev_prop before the seed / gate kernel
+  cudaStream_t pside = nullptr;
+  cudaEvent_t ev_tick = nullptr, ev_prop = nullptr;
+  float4* h_rcirc[2] = {nullptr, nullptr};
+  int* h_rcoff[2] = {nullptr, nullptr};
+  float* h_rpts[2] = {nullptr, nullptr};
 
   ~sepso_server_ctx() {
     for (int i = 0; i < 2; ++i) {
@@ -228,7 +313,13 @@ struct sepso_server_ctx {
       if (h_admit[i]) cudaFreeHost(h_admit[i]);
       if (h_acirc[i]) cudaFreeHost(h_acirc[i]);
       if (h_tiles[i]) cudaFreeHost(h_tiles[i]);
+      if (h_rcirc[i]) cudaFreeHost(h_rcirc[i]);
+      if (h_rcoff[i]) cudaFreeHost(h_rcoff[i]);
+      if (h_rpts[i]) cudaFreeHost(h_rpts[i]);
     }
+    if (ev_tick) cudaEventDestroy(ev_tick);
+    if (ev_prop) cudaEventDestroy(ev_prop);
+    if (pside) cudaStreamDestroy(pside);
   }
   template <class T>
   T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
@@ -268,9 +359,9 @@ struct sepso_server_ctx {
     p.plv2 = at<float>(L.plv2);
     p.done = at<int32_t>(L.done);
     p.agent_prevT = at<float>(L.prevT);
-    p.prior_path = nullptr;
+    p.prior_path = prior ? at<float>(L.priorT) : nullptr;
     p.agent_rows = nullptr;
-    p.prior_use = nullptr;
+    p.prior_use = prior ? at<int32_t>(L.prior_use) : nullptr;
     return p;
   }
 };
@@ -302,7 +393,7 @@ void retire(sepso_server_ctx* h, int b) {
 
 int admit(sepso_server_ctx* h, int b) {
   const sepso_server_config& c = h->cfg;
-  int n = 0, c0 = 0;
+  int n = 0, c0 = 0, rc0 = 0;
   size_t free_slot = 0;
   const double now = now_s(h->t0);
   for (auto it = h->queue.begin(); it != h->queue.end();) {
@@ -344,7 +435,7 @@ int admit(sepso_server_ctx* h, int b) {
     d.at_stall = c.stall_iters;
     d.stall_tol = c.stall_tol;
     d.n_pi = (int)std::min<double>(std::max(std::ceil((double)c.pi_gamma * c.N), 0.0), (double)c.N);
-    d.n_pr = 0;
+    d.n_pr = h->prior ? h->n_prior : 0;
     d.pi_h = c.pi_halfwidth;
     d.cycle = (uint32_t)h->agent_cycle[r.agent];
     d.agent = r.agent;
@@ -366,6 +457,13 @@ int admit(sepso_server_ctx* h, int b) {
         nr2[o] = -(rr * rr);
       }
       c0 += nf4;
+    }
+    if (h->prior) {  // the scene as the prior's rasteriser reads it
+      float4* rc = h->h_rcirc[b] + rc0;
+      for (int o = 0; o < r.O; ++o) rc[o] = make_float4(r.circ[3 * o], r.circ[3 * o + 1], r.circ[3 * o + 2], 0.0f);
+      h->h_rcoff[b][n] = rc0;
+      std::memcpy(h->h_rpts[b] + 4 * n, r.pts, sizeof r.pts);
+      rc0 += r.O;
     }
     Slot& sl = h->slots[i];
     sl.busy = true;
@@ -391,6 +489,30 @@ int admit(sepso_server_ctx* h, int b) {
                                                 h->at<float4>(h->L.admit_circ), n, h->Om);
   SCUDA(cudaGetLastError());
   ++h->launches;
+  if (h->prior) {
+    // The prior's proposals for the admitted scenes on the side stream, beside the
+    // running tick (they touch only the prior's rows and this parity's staging);
+    // then, on the main stream, each slot's seed row and gate.
+    h->h_rcoff[b][n] = rc0;
+    const cudaStream_t ps = h->pside;
+    float* praw = h->at<float>(h->L.praw) + (size_t)b * h->S * 2 * kPriorMaxT;
+    SCUDA(cudaStreamWaitEvent(ps, h->ev_tick, 0));
+    if (rc0 > 0) SCUDA(cudaMemcpyAsync(h->ws + h->L.rcirc, h->h_rcirc[b], (size_t)rc0 * 16, cudaMemcpyHostToDevice, ps));
+    SCUDA(cudaMemcpyAsync(h->ws + h->L.rcoff, h->h_rcoff[b], (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, ps));
+    SCUDA(cudaMemcpyAsync(h->ws + h->L.rpts, h->h_rpts[b], (size_t)n * 16, cudaMemcpyHostToDevice, ps));
+    const long long l0 = sepso_prior_launch_count(h->prior);
+    const cudaStream_t keep = prior_swap_stream(h->prior, ps);
+    const int rc = prior_propose_device(h->prior, h->prior_first, n, h->at<float4>(h->L.rcirc),
+                                        h->at<int>(h->L.rcoff), h->at<float>(h->L.rpts), praw, 2 * h->prior_T);
+    prior_swap_stream(h->prior, keep);
+    if (rc) return sfail(rc, "learned prior: %s", sepso_prior_last_error());
+    h->launches += sepso_prior_launch_count(h->prior) - l0;
+    SCUDA(cudaEventRecord(h->ev_prop, ps));
+    SCUDA(cudaStreamWaitEvent(h->stream, h->ev_prop, 0));
+    server_prior_kernel<<<n, 32, 0, h->stream>>>(h->params(), h->at<Admit>(h->L.admits), n, praw, h->prior_T);
+    SCUDA(cudaGetLastError());
+    ++h->launches;
+  }
   return SEPSO_OK;
 }
 
@@ -506,6 +628,40 @@ int sepso_server_set_hyper(sepso_server_handle h, int32_t agent, const float* hy
   return SEPSO_OK;
 }
 
+int sepso_server_set_prior(sepso_server_handle h, sepso_prior_handle prior, int32_t n_prior, int32_t first_row) {
+  if (!h) return sfail(SEPSO_EINVAL, "NULL handle");
+  if (!prior) {
+    h->prior = nullptr;
+    h->n_prior = 0;
+    return SEPSO_OK;
+  }
+  int T = 0, mc = 0, cap = 0;
+  float W = 0.0f, H = 0.0f;
+  cudaStream_t st = nullptr;
+  if (prior_shape(prior, &T, &mc, &cap, &W, &H, &st) != SEPSO_OK) return sfail(SEPSO_EINVAL, "bad prior handle");
+  if (T < 1 || T > kPriorMaxT) return sfail(SEPSO_EINVAL, "the prior proposes %d waypoints (1..%d)", T, kPriorMaxT);
+  if (n_prior < 0 || n_prior > h->cfg.N) return sfail(SEPSO_EINVAL, "n_prior %d outside [0, N=%d]", n_prior, h->cfg.N);
+  if (mc < h->cfg.Omax)
+    return sfail(SEPSO_EINVAL, "the prior rasterises at most %d circles, requests have up to %d", mc, h->cfg.Omax);
+  if (first_row < 0 || (long long)first_row + h->S > cap)
+    return sfail(SEPSO_EINVAL, "rows [%d, %d) outside the prior's %d", first_row, first_row + h->S, cap);
+  if (W != h->cfg.map_w || H != h->cfg.map_h) return sfail(SEPSO_EINVAL, "the prior's map differs from the server's");
+  if (st != h->stream) return sfail(SEPSO_EINVAL, "the prior must run on the server's stream");
+  if (!h->pside) SCUDA(cudaStreamCreateWithFlags(&h->pside, cudaStreamNonBlocking));
+  if (!h->ev_tick) SCUDA(cudaEventCreateWithFlags(&h->ev_tick, cudaEventDisableTiming));
+  if (!h->ev_prop) SCUDA(cudaEventCreateWithFlags(&h->ev_prop, cudaEventDisableTiming));
+  for (int i = 0; i < 2; ++i) {
+    if (!h->h_rcirc[i]) SCUDA(cudaMallocHost(reinterpret_cast<void**>(&h->h_rcirc[i]), (size_t)h->S * h->Om * 16));
+    if (!h->h_rcoff[i]) SCUDA(cudaMallocHost(reinterpret_cast<void**>(&h->h_rcoff[i]), (size_t)(h->S + 1) * 4));
+    if (!h->h_rpts[i]) SCUDA(cudaMallocHost(reinterpret_cast<void**>(&h->h_rpts[i]), (size_t)h->S * 16));
+  }
+  h->prior = prior;
+  h->n_prior = n_prior;
+  h->prior_first = first_row;
+  h->prior_T = T;
+  return SEPSO_OK;
+}
+
 int sepso_server_submit_at(sepso_server_handle h, int32_t agent, int32_t T, const float* start,
                            const float* target, const float* circles, int32_t O, int64_t tag, double arrival_s) {
   if (!h || !start || !target) return sfail(SEPSO_EINVAL, "NULL argument");
@@ -553,7 +709,9 @@ int sepso_server_tick(sepso_server_handle h, int32_t* active, int32_t* queued) {
   if (!h) return sfail(SEPSO_EINVAL, "NULL handle");
   const long long j = ++h->tick;
   const int b = (int)(j & 1);
-  // (1) one iteration of every occupied slot
+  // (1) one iteration of every occupied slot (after the point the prior's work of this
+  // tick's admissions may start from)
+  if (h->prior) SCUDA(cudaEventRecord(h->ev_tick, h->stream));
   if (h->ntiles > 0) {
     SCUDA(launch_batch_iter(h->params(), (int)j, h->ntiles, h->threads, h->smem, h->stream));
     ++h->launches;

@@ -565,6 +565,21 @@ def serving_workload(seed: int = 0, n_agents: int = 2048, T_choices=(8, 20, 40),
     return agents
 
 
+def serving_prior_scenes(seed: int, n: int, O: int, r_range=(3.0, 15.0), drift: int = 100) -> dict:
+    """n snapshots shaped like the serving workload's scenes with O circles (centres
+    U[60,340]^2, radii U[r_range] x sqrt(32 / O)), start (20, 20 + c) and target
+    (380, 380 - c) for a drift c ~ U{0..drift-1}: the training and held-out scenes of
+    the prior that seeds served requests.  Returns float32 arrays points (n, 4) and
+    circles (n, O, 3)."""
+    rng = np.random.default_rng(11000 + seed)
+    sc = float(np.sqrt(32.0 / O))
+    circ = np.stack([random_circles(rng, O, lo=60.0, hi=340.0, r_lo=r_range[0] * sc, r_hi=r_range[1] * sc)
+                     for _ in range(n)]).astype(np.float32)
+    c = rng.integers(0, drift, n).astype(np.float32)
+    pts = np.stack([np.full(n, 20.0), 20.0 + c, np.full(n, 380.0), 380.0 - c], 1).astype(np.float32)
+    return {"points": pts, "circles": circ}
+
+
 def poisson_arrivals(seed: int, rate: float, duration: float) -> np.ndarray:
     """Arrival times (s) of a Poisson process of the given rate over [0, duration)."""
     rng = np.random.default_rng(9000 + seed)

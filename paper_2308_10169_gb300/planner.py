@@ -575,6 +575,14 @@ class Server:
         h = _f32(hyper, (self.G, 6))
         self._check(self.lib.sepso_server_set_hyper(self._h, agent, fptr(h)))
 
+    def set_prior(self, prior, n_prior: int, first_row: int = 0):
+        """Attach a learned prior (``prior.Prior`` on this server's stream and map) whose
+        proposals seed n_prior particles per group of every admitted request, using
+        its dataset rows [first_row, first_row + slots); ``None`` detaches it."""
+        h = prior._h if prior is not None else None
+        self._check(self.lib.sepso_server_set_prior(self._h, h, int(n_prior), int(first_row)))
+        self._prior = prior  # the prior must outlive its attachment
+
     def submit(self, agent: int, T: int, start, target, circles, tag: int):
         c = _f32(circles, (-1, 3))
         self._check(self.lib.sepso_server_submit(self._h, agent, T, fptr(_f32(start)), fptr(_f32(target)),

@@ -278,6 +278,52 @@ def fit_prior(prior: Prior, scenes: dict, rounds: int = 3, epochs: int = 30, bat
     return hist
 
 
+def fit_prior_sets(prior: Prior, sets: list, rounds: int = 2, epochs: int = 30, batch: int = 4096, seed: int = 0,
+                   n_prior: int = 43, **plan_kw) -> dict:
+    """fit_prior over several scene sets (each with its own circle count), laid out
+    back to back from row 0: every set is labelled by the planner, the prior trains
+    on all rows, and after each training phase every set is planned again with the
+    proposals as a second seed, a scene's label becoming the new plan when it is
+    cheaper.  Returns the per-round median label cost and collision-free share."""
+    offs = np.cumsum([0] + [d["points"].shape[0] for d in sets])
+    n = int(offs[-1])
+    for d, o in zip(sets, offs[:-1]):
+        m = d["points"].shape[0]
+        prior.add_scenes(int(o), d["points"], [d["circles"][i] for i in range(m)])
+    labs = [plan_scenes(d, seed=seed, run0=int(o), **plan_kw) for d, o in zip(sets, offs[:-1])]
+    labels = torch.cat([l_["waypoints"] for l_ in labs])
+    cost = np.concatenate([l_["cost"] for l_ in labs])
+    q = np.concatenate([l_["Q"] for l_ in labs])
+    hist = dict(label_cost=[float(np.median(cost))], label_collision_free=[float(np.mean(q == 0))], losses=[],
+                plan_s=sum(l_["seconds"] for l_ in labs), train_s=0.0, steps=0)
+    steps = max(1, epochs * n // batch)
+    for r in range(rounds):
+        prior.set_labels(0, labels)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(prior.stream)
+        loss = np.concatenate([prior.train(steps=min(65536, steps - s0), batch=batch, n_rows=n,
+                                           seed=seed * 1000 + r) for s0 in range(0, steps, 65536)])
+        ev1.record(prior.stream)
+        ev1.synchronize()
+        hist["train_s"] += ev0.elapsed_time(ev1) / 1e3
+        hist["steps"] += steps
+        hist["losses"].append([float(loss[:10].mean()), float(loss[-10:].mean())])
+        if r + 1 < rounds:
+            prop = prior.infer(0, n)
+            new = [plan_scenes(d, seed=seed, run0=int(o), cycle=r + 1, prior=prop[int(o):int(o) + d["points"].shape[0]],
+                               n_prior=n_prior, **plan_kw) for d, o in zip(sets, offs[:-1])]
+            hist["plan_s"] += sum(l_["seconds"] for l_ in new)
+            ncost = np.concatenate([l_["cost"] for l_ in new])
+            better = ncost < cost
+            labels = torch.where(torch.from_numpy(better).to(labels.device)[:, None],
+                                 torch.cat([l_["waypoints"] for l_ in new]), labels)
+            cost = np.where(better, ncost, cost)
+            q = np.where(better, np.concatenate([l_["Q"] for l_ in new]), q)
+            hist["label_cost"].append(float(np.median(cost)))
+            hist["label_collision_free"].append(float(np.mean(q == 0)))
+    return hist
+
+
 def propose(prior: Prior, scenes: dict, first: int) -> torch.Tensor:
     """The prior's proposals (device (n, 2T)) for scenes loaded into rows [first, first + n)."""
     n = scenes["points"].shape[0]
