@@ -1475,51 +1475,6 @@ int forward(sepso_prior_ctx* h, const bf16* x, int n, bool train) {
   return SEPSO_OK;
 }
 
-// The forward pass of inference: every product on the one-tile kernel with
-// 64-column tiles, K split into a number of slices fixed by K alone (about one per
-// eight 64-deep blocks, at most 8, fewer when the scratch cannot hold them for one
-// 128-row tile), summed in slice order.  A row's outputs therefore never depend on
-// how many rows share the call, and the small batches of a serving tick spread over
-// many CTAs instead of a few long K loops.  infer_rows: rows per call (a multiple of
-// 128 that the scratch and the batch buffers hold).  Output: y (FP32).
-constexpr int kInferRows = 128;
-int infer_split(int K, int N, size_t scratch_floats) {
-  const int nkb = (K + sepso::kBK - 1) / sepso::kBK;
-  int sl = std::min(8, std::max(1, nkb / 8));
-  while (sl > 1 && (size_t)sl * kInferRows * N > scratch_floats) --sl;
-  return sl;
-}
-
-int infer_rows(const Dims& d) {
-  const size_t sf = (size_t)kMaxSlices * std::max(d.O * d.H2, d.H2 * d.H1);
-  size_t rows = (size_t)d.B;
-  const int Ns[3] = {d.H1, d.H2, d.O}, Ks[3] = {d.K, d.H1, d.H2};
-  for (int l = 0; l < 3; ++l) rows = std::min(rows, sf / ((size_t)infer_split(Ks[l], Ns[l], sf) * Ns[l]));
-  return (int)std::max<size_t>(kInferRows, rows / kInferRows * kInferRows);
-}
-
-int forward_infer(sepso_prior_ctx* h, const bf16* x, int n) {
-  const Dims& d = h->d;
-  const float* prm = h->at<float>(h->L.prm);
-  const bf16* wb = h->at<bf16>(h->L.wb);
-  bf16* h1 = h->at<bf16>(h->L.h1);
-  bf16* h2 = h->at<bf16>(h->L.h2);
-  const size_t sf = (size_t)kMaxSlices * std::max(d.O * d.H2, d.H2 * d.H1);
-  GemmExtra e;
-  e.ws = h->at<float>(h->L.kpart);
-  e.ws_bytes = sf * 4;
-  e.ksplit = infer_split(d.K, d.H1, sf);
-  PTRY(gemm(h, x, h->at<bf16>(h->L.w1p), n, d.H1, d.K, d.Kp, d.Kp, prm + d.off[1], 1, nullptr, 0, nullptr, 0, h1,
-            d.H1, e, -64));
-  e.ksplit = infer_split(d.H1, d.H2, sf);
-  PTRY(gemm(h, h1, wb + d.off[2], n, d.H2, d.H1, d.H1, d.H1, prm + d.off[3], 1, nullptr, 0, nullptr, 0, h2, d.H2, e,
-            -64));
-  e.ksplit = infer_split(d.H2, d.O, sf);
-  PTRY(gemm(h, h2, wb + d.off[4], n, d.O, d.H2, d.H2, d.H2, prm + d.off[5], 0, nullptr, 0, h->at<float>(h->L.y), d.O,
-            nullptr, 0, e, -64));
-  return SEPSO_OK;
-}
-
 // Backward pass after forward(x, n, true) with targets in t: gradient into grad,
 // the loss added to loss[slot].  n is a multiple of 8 (the K of the weight GEMMs).
 // The ReLU-masked products write their BF16 output transposed (the next weight
@@ -1904,10 +1859,9 @@ int sepso_prior_infer(sepso_prior_handle h, int32_t first, int32_t n, float* d_o
   PTRY(check_rows(h, first, n));
   const Dims& d = h->d;
   if (ld < d.O) return pfail(SEPSO_EINVAL, "ld %d below 2T = %d", ld, d.O);
-  const int R = std::min(infer_rows(d), d.B);
-  for (int s0 = 0; s0 < n; s0 += R) {
-    const int m = std::min(R, n - s0);
-    PTRY(forward_infer(h, h->at<bf16>(h->L.X) + (long long)(first + s0) * d.Kp, m));
+  for (int s0 = 0; s0 < n; s0 += d.B) {
+    const int m = std::min(d.B, n - s0);
+    PTRY(forward(h, h->at<bf16>(h->L.X) + (long long)(first + s0) * d.Kp, m, false));
     const int tot = m * d.O;
     sepso::decode_kernel<<<(tot + 255) / 256, 256, 0, h->stream>>>(h->at<float>(h->L.y), m, h->c.T,
                                                                     h->at<float>(h->L.P) + 4LL * (first + s0),
