@@ -128,6 +128,14 @@ __device__ __forceinline__ float warp_prod(float v) {
   return v;
 }
 
+// Griewank's factor cos(x_i / sqrt(i)) for coordinate index i (0-based) as
+// cos(pi y) with y = x / (pi sqrt(i + 1)): cospif reduces y exactly, and the scale
+// takes one reciprocal square root and two products instead of a square root, a
+// divide and cosf's argument reduction.
+__device__ __forceinline__ float griewank_factor(float x, int i) {
+  return cospif(x * (rsqrtf((float)(i + 1)) * 0.318309886183790672f));
+}
+
 // BF1..BF4 of one row (any address space), the whole warp; every lane gets the value.
 //   Sphere      sum x_i^2
 //   Rosenbrock  sum_{i<D} 100 (x_{i+1} - x_i^2)^2 + (x_i - 1)^2
@@ -157,7 +165,7 @@ __device__ __forceinline__ float bf_row(const float* s, int D, int lane) {
     for (int i = lane; i < D; i += 32) {
       const float x = s[i];
       acc = fmaf(x, x, acc);
-      prod *= cosf(__fdiv_rn(x, sqrtf((float)(i + 1))));
+      prod *= griewank_factor(x, i);
     }
     const float sum = warp_sum(acc);
     prod = warp_prod(prod);
@@ -445,7 +453,7 @@ __device__ __forceinline__ float bf_row_serial(const float* x, int D) {
       acc += fmaf(xi, xi, -10.0f * cospif(2.0f * xi));
     } else {
       acc = fmaf(xi, xi, acc);
-      prod *= cosf(__fdiv_rn(xi, sqrtf((float)(i + 1))));
+      prod *= griewank_factor(xi, i);
     }
   }
   if (FN == 1) return acc;
