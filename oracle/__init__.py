@@ -21,7 +21,11 @@ What each function follows (paper: arXiv 2308.10169):
   textbook definitions) and DTPSO on them: the same Algorithm 1 iteration as
   ``Swarm`` with that objective over the box [lo, hi]^D; with ``fn = 5`` the
   objective is a path among polygon obstacles (Sec. 3.3.1, Eq. penalty with Q the
-  number of path-segment / obstacle-edge crossings, ``seg_cross``).
+  number of path-segment / obstacle-edge crossings, ``seg_cross``); with ``fn = 6``
+  it is a path in three dimensions among spheres (the Conclusion's extension from
+  2D to 3D planning: Eqs. path_fit / lenth / penalty with a third coordinate and Q
+  the number of (segment, sphere) pairs closer than the radius,
+  ``seg_point_dist3``, ``Scene3``).
 * ``hsef``                  -- the hierarchical self-evolving framework
   (Sec. 3.2.1, Eq. fit_h).
 * ``raster`` / ``prior_encode`` / ``prior_decode`` / ``Mlp`` / ``adam`` -- the
@@ -80,6 +84,7 @@ class _Config(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32),
         ("problem", ctypes.c_int32), ("Dbf", ctypes.c_int32),
         ("lo", ctypes.c_double), ("hi", ctypes.c_double),
+        ("Z", ctypes.c_double),
     ]
 
 
@@ -88,7 +93,9 @@ class _Scene(ctypes.Structure):
                 ("tx", ctypes.c_double), ("ty", ctypes.c_double),
                 ("O", ctypes.c_int32), ("circ", _f64p),
                 ("E", ctypes.c_int32), ("edges", _f64p),
-                ("A", ctypes.c_int32), ("agents", _f64p), ("sep", ctypes.c_double)]
+                ("A", ctypes.c_int32), ("agents", _f64p), ("sep", ctypes.c_double),
+                ("sz", ctypes.c_double), ("tz", ctypes.c_double),
+                ("S", ctypes.c_int32), ("spheres", _f64p)]
 
 
 class _State(ctypes.Structure):
@@ -123,6 +130,10 @@ def lib():
         L.so_u01.restype = ctypes.c_double
         L.so_seg_point_dist.argtypes = [ctypes.c_double] * 6
         L.so_seg_point_dist.restype = ctypes.c_double
+        L.so_seg_point_dist3.argtypes = [_f64p, _f64p, _f64p]
+        L.so_seg_point_dist3.restype = ctypes.c_double
+        L.so_sphere_margin.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene), ctypes.c_int32,
+                                       _f64p, _f64p]
         L.so_evaluate.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene), ctypes.c_int32,
                                   _f64p, _f64p, _i32p, _f64p]
         L.so_tangency_margin.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Scene),
@@ -218,6 +229,23 @@ class Scene:
                       A=self.agents.shape[0], agents=_p64(self.agents), sep=self.sep)
 
 
+class Scene3:
+    """A static 3D scene in FP64 (the Conclusion's 3D extension): start and target
+    (3,), spheres (S, 4) rows (cx, cy, cz, r)."""
+
+    def __init__(self, start, target, spheres):
+        self.start = np.asarray(start, dtype=np.float64).reshape(3).copy()
+        self.target = np.asarray(target, dtype=np.float64).reshape(3).copy()
+        self.spheres = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
+        self._none = np.zeros((1, 4))
+
+    def c(self) -> _Scene:
+        return _Scene(sx=self.start[0], sy=self.start[1], tx=self.target[0], ty=self.target[1],
+                      O=0, circ=_p64(self._none), E=0, edges=_p64(self._none), A=0,
+                      agents=_p64(self._none), sep=0.0, sz=self.start[2], tz=self.target[2],
+                      S=self.spheres.shape[0], spheres=_p64(self.spheres))
+
+
 # ----------------------------------------------------------------------------
 # Philox and uniforms
 # ----------------------------------------------------------------------------
@@ -241,6 +269,12 @@ def u01(x: int) -> float:
 def seg_point_dist(a, b, c) -> float:
     return lib().so_seg_point_dist(float(a[0]), float(a[1]), float(b[0]), float(b[1]),
                                    float(c[0]), float(c[1]))
+
+
+def seg_point_dist3(a, b, c) -> float:
+    """Distance from point c to the closed segment [a, b] in three dimensions."""
+    v = [np.ascontiguousarray(np.asarray(u, np.float64).reshape(3)) for u in (a, b, c)]
+    return lib().so_seg_point_dist3(_p64(v[0]), _p64(v[1]), _p64(v[2]))
 
 
 def evaluate(cfg, scene: Scene, X: np.ndarray):
@@ -369,13 +403,17 @@ def bf_value(fn: int, x) -> float:
 
 def _bf_cfg(c) -> _Config:
     """The C config of a run of the generic engine (any object with BFConfig's fields):
-    a benchmark function (fn 1..4) or a path among polygons (fn 5, D = 2T)."""
+    a benchmark function (fn 1..4), a path among polygons (fn 5, D = 2T) or a 3D
+    path among spheres (fn 6, D = 3T); Priori Initialization when pi_gamma > 0."""
     f32 = lambda v: float(np.float32(v))
-    return _Config(T=c.D // 2 if c.fn == 5 else 0, G=c.G, N=c.N, W=f32(c.map_w), H=f32(c.map_h),
+    T = c.D // 2 if c.fn == 5 else (c.D // 3 if c.fn == 6 else 0)
+    return _Config(T=T, G=c.G, N=c.N, W=f32(c.map_w), H=f32(c.map_h),
                    alpha=f32(c.alpha), beta=c.beta, max_iters=c.max_iters,
-                   at_mode=0, tw=1, delta=0.0, stall_iters=0, stall_tol=0.0, use_pi=0,
-                   pi_gamma=0.0, pi_h=0.0, seed=c.seed, run_id=c.run_id, problem=c.fn, Dbf=c.D,
-                   lo=f32(c.lo), hi=f32(c.hi))
+                   at_mode=0, tw=1, delta=0.0, stall_iters=0, stall_tol=0.0, seed=c.seed,
+                   run_id=c.run_id, problem=c.fn, Dbf=c.D,
+                   lo=f32(c.lo), hi=f32(c.hi), Z=f32(getattr(c, "map_d", 0.0)),
+                   use_pi=int(getattr(c, "pi_gamma", 0.0) > 0.0), pi_gamma=f32(getattr(c, "pi_gamma", 0.0)),
+                   pi_h=f32(getattr(c, "pi_halfwidth", 0.0)))
 
 
 def seg_cross(a, b, c, d) -> bool:
@@ -391,6 +429,16 @@ def poly_margin(cfg, scene: "Scene", X) -> np.ndarray:
     c = _cfg(cfg) if hasattr(cfg, "obstacle_kind") else _bf_cfg(cfg)
     s = scene.c()
     lib().so_poly_margin(ctypes.byref(c), ctypes.byref(s), X.shape[0], _p64(X), _p64(m))
+    return m
+
+
+def sphere_margin(cfg, scene: "Scene3", X) -> np.ndarray:
+    """Per 3D path (rows of X, D = 3T): min over its (segment, sphere) pairs of |dist - r|."""
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, cfg.D))
+    m = np.zeros(X.shape[0])
+    c = _bf_cfg(cfg)
+    s = scene.c()
+    lib().so_sphere_margin(ctypes.byref(c), ctypes.byref(s), X.shape[0], _p64(X), _p64(m))
     return m
 
 
@@ -417,6 +465,14 @@ class BFSwarm(Swarm):
         }
         self._c = _bf_cfg(cfg)
         self._none = scene if scene is not None else Scene((0.0, 0.0), (0.0, 0.0), np.zeros((0, 3)))
+
+    def set_previous(self, prevT, cycle: int):
+        """Priori Initialization for the next ``init`` (Sec. 3.3.3): the first
+        ceil(pi_gamma N) particles of each group start within +-pi_halfwidth of the
+        previous best path ``prevT``; ``cycle`` enters every Philox counter."""
+        self.s["prevT"][...] = np.asarray(prevT, np.float64).reshape(-1)
+        self.s["has_prev"][0] = 1
+        self.s["cycle"][0] = int(cycle)
 
     def evaluate(self, X, with_q: bool = False):
         X = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, self.cfg.D))

@@ -23,6 +23,9 @@
  *   - The hierarchical self-evolving framework (Sec. 3.2.1, Eq. fit_h).
  *   - The dynamic scene step of the simulator (Fig. PP caption: obstacles
  *     reverse velocity at the map border; start/target move vertically).
+ *   - The paper's stated extension from 2D to 3D planning (Conclusion, item
+ *     (iii)): the same fitness for a path of T waypoints in a box among
+ *     spheres, Q counting the (segment, sphere) pairs closer than the radius.
  *
  * Compile with -ffp-contract=off so that x86 and Arm give identical results.
  */
@@ -110,10 +113,13 @@ typedef struct {
    * coordinates in the map); 1..4 = benchmark functions BF1..BF4 (Table BFs:
    * Sphere, Rosenbrock, Rastrigin, Griewank) over the box [lo, hi]^D, D = Dbf;
    * 5 = path planning among polygons (Sec. 3.3.1: Q counts crossings of path
-   * segments with obstacle edges).                                          */
+   * segments with obstacle edges); 6 = path planning in three dimensions among
+   * spheres (the 3D extension of the Conclusion: D = 3T coordinates
+   * [x1..xT, y1..yT, z1..zT] in [0,W] x [0,H] x [0,Z]).                     */
   int32_t problem;
   int32_t Dbf;
   double lo, hi;
+  double Z;              /* problem 6: depth of the box (z in [0,Z])          */
 } so_config;
 
 typedef struct {
@@ -129,6 +135,10 @@ typedef struct {
   int32_t A;
   const double* agents;
   double sep;
+  /* Problem 6: the z of start and target, and S spheres (S x 4: cx, cy, cz, r). */
+  double sz, tz;
+  int32_t S;
+  const double* spheres;
 } so_scene;
 
 typedef struct {
@@ -317,6 +327,96 @@ void so_tangency_margin(const so_config* cfg, const so_scene* sc, int32_t n, con
   }
 }
 
+
+/* ------------------------------------------------------------------------- */
+/* Three dimensions (the Conclusion's extension from 2D to 3D planning): the */
+/* fitness of Eqs. path_fit / lenth / penalty for a path start -> T          */
+/* waypoints -> target in a box, with spheres as obstacles.  A row holds     */
+/* [x1..xT, y1..yT, z1..zT].                                                 */
+/* ------------------------------------------------------------------------- */
+
+/* Euclidean distance from point c to the closed segment [a, b] in 3D: the
+ * closest point is a + t (b - a), t the projection parameter clamped to [0, 1]
+ * (t = 0 for a zero-length segment). */
+double so_seg_point_dist3(const double* a, const double* b, const double* c) {
+  const double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+  const double L2 = dx * dx + dy * dy + dz * dz;
+  double t = 0.0;
+  if (L2 > 0.0) {
+    t = ((c[0] - a[0]) * dx + (c[1] - a[1]) * dy + (c[2] - a[2]) * dz) / L2;
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+  }
+  const double px = a[0] + t * dx - c[0], py = a[1] + t * dy - c[1], pz = a[2] + t * dz - c[2];
+  return sqrt(px * px + py * py + pz * pz);
+}
+
+/* Point s of the path (s = 0: start, 1..T: waypoint s, T + 1: target). */
+static void so_point3(int32_t T, const double* x, const so_scene* sc, int32_t s, double* out) {
+  if (s == 0) {
+    out[0] = sc->sx;
+    out[1] = sc->sy;
+    out[2] = sc->sz;
+  } else if (s == T + 1) {
+    out[0] = sc->tx;
+    out[1] = sc->ty;
+    out[2] = sc->tz;
+  } else {
+    out[0] = x[s - 1];
+    out[1] = x[T + s - 1];
+    out[2] = x[2 * T + s - 1];
+  }
+}
+
+/* Eq. lenth in 3D: the T + 1 segment lengths in path order. */
+static double so_length3(int32_t T, const double* x, const so_scene* sc) {
+  double len = 0.0;
+  for (int32_t s = 0; s <= T; ++s) {
+    double a[3], b[3];
+    so_point3(T, x, sc, s, a);
+    so_point3(T, x, sc, s + 1, b);
+    len += sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]) + (b[2] - a[2]) * (b[2] - a[2]));
+  }
+  return len;
+}
+
+/* Q in 3D: the number of (path segment, sphere) pairs whose distance is below
+ * the radius (the circles' reading with a third coordinate). */
+static int32_t so_sphere_collisions(int32_t T, const double* x, const so_scene* sc) {
+  int32_t q = 0;
+  for (int32_t s = 0; s <= T; ++s) {
+    double a[3], b[3];
+    so_point3(T, x, sc, s, a);
+    so_point3(T, x, sc, s + 1, b);
+    for (int32_t o = 0; o < sc->S; ++o) {
+      const double* c = sc->spheres + 4 * o;
+      if (so_seg_point_dist3(a, b, c) < c[3]) ++q;
+    }
+  }
+  return q;
+}
+
+/* For the parity tests: per path, the smallest |dist - r| over its (segment,
+ * sphere) pairs; pairs this close to tangency may flip in FP32. */
+void so_sphere_margin(const so_config* cfg, const so_scene* sc, int32_t n, const double* X, double* margin) {
+  const int32_t T = cfg->T, D = 3 * T;
+  for (int32_t p = 0; p < n; ++p) {
+    const double* x = X + (int64_t)p * D;
+    double m = INFINITY;
+    for (int32_t s = 0; s <= T; ++s) {
+      double a[3], b[3];
+      so_point3(T, x, sc, s, a);
+      so_point3(T, x, sc, s + 1, b);
+      for (int32_t o = 0; o < sc->S; ++o) {
+        const double* c = sc->spheres + 4 * o;
+        const double d = fabs(so_seg_point_dist3(a, b, c) - c[3]);
+        if (d < m) m = d;
+      }
+    }
+    margin[p] = m;
+  }
+}
+
 /* Eq. path_fit = Length + alpha * Q^beta for n particles (rows of X). */
 /* ------------------------------------------------------------------------- */
 /* Benchmark functions BF1-BF4 (Table BFs), their textbook definitions with  */
@@ -357,7 +457,16 @@ double so_bf_value(int32_t fn, int32_t D, const double* x) {
 }
 
 static int32_t so_is_bf(const so_config* cfg) { return cfg->problem >= 1 && cfg->problem <= 4; }
-static int32_t so_dim(const so_config* cfg) { return so_is_bf(cfg) ? cfg->Dbf : 2 * cfg->T; }
+static int32_t so_dim(const so_config* cfg) {
+  if (so_is_bf(cfg)) return cfg->Dbf;
+  return cfg->problem == 6 ? 3 * cfg->T : 2 * cfg->T;
+}
+
+/* Eq. lenth of one row, in the problem's dimension. */
+static double so_path_length(const so_config* cfg, const so_scene* sc, const double* x) {
+  if (cfg->problem == 6) return so_length3(cfg->T, x, sc);
+  return so_length(cfg->T, x, sc->sx, sc->sy, sc->tx, sc->ty);
+}
 
 void so_evaluate(const so_config* cfg, const so_scene* sc, int32_t n, const double* X, double* F,
                  int32_t* Q, double* len) {
@@ -367,6 +476,17 @@ void so_evaluate(const so_config* cfg, const so_scene* sc, int32_t n, const doub
       if (F) F[p] = so_bf_value(cfg->problem, D, X + (int64_t)p * D);
       if (Q) Q[p] = 0;
       if (len) len[p] = 0.0;
+    }
+    return;
+  }
+  if (cfg->problem == 6) {
+    for (int32_t p = 0; p < n; ++p) {
+      const double* x = X + (int64_t)p * D;
+      const double l = so_length3(T, x, sc);
+      const int32_t q = so_sphere_collisions(T, x, sc);
+      if (F) F[p] = l + cfg->alpha * so_pow_int((double)q, cfg->beta);
+      if (Q) Q[p] = q;
+      if (len) len[p] = l;
     }
     return;
   }
@@ -406,7 +526,8 @@ int32_t so_pi_count(double gamma, int32_t N) {
 /* X_range of coordinate j: [so_lo, so_lo + so_extent]; the map for a path. */
 static double so_extent(const so_config* cfg, int32_t j) {
   if (so_is_bf(cfg)) return cfg->hi - cfg->lo;
-  return (j < cfg->T) ? cfg->W : cfg->H;
+  if (j < cfg->T) return cfg->W;
+  return (cfg->problem == 6 && j >= 2 * cfg->T) ? cfg->Z : cfg->H;
 }
 static double so_lo(const so_config* cfg) { return so_is_bf(cfg) ? cfg->lo : 0.0; }
 static double so_hi(const so_config* cfg, int32_t j) { return so_is_bf(cfg) ? cfg->hi : so_extent(cfg, j); }
@@ -598,7 +719,7 @@ int32_t so_iteration(const so_config* cfg, const so_scene* sc, const double* hyp
 
 /* result: D waypoints, then cost, length, Q, iterations. */
 void so_plan(const so_config* cfg, const so_scene* sc, const double* hyper, so_state* st, double* result) {
-  const int32_t T = cfg->T, D = 2 * T;
+  const int32_t D = so_dim(cfg);
   if (*st->cycle == 0) {
     *st->win_n = 0;
     *st->win_head = 0;
@@ -610,7 +731,7 @@ void so_plan(const so_config* cfg, const so_scene* sc, const double* hyper, so_s
   }
   for (int32_t j = 0; j < D; ++j) result[j] = st->Tb[j];
   result[D + 0] = *st->Tfit;
-  result[D + 1] = so_length(T, st->Tb, sc->sx, sc->sy, sc->tx, sc->ty);
+  result[D + 1] = so_path_length(cfg, sc, st->Tb);
   result[D + 2] = (double)*st->TQ;
   result[D + 3] = (double)*st->k;
   for (int32_t j = 0; j < D; ++j) st->prevT[j] = st->Tb[j];

@@ -318,6 +318,7 @@ def paper_box_workload(seed: int = 0, variant: str = "SEPSO", frame_cap: int = 3
 # Benchmark functions of Table BFs.
 BF_SPHERE, BF_ROSENBROCK, BF_RASTRIGIN, BF_GRIEWANK = 1, 2, 3, 4
 POLYGON_PATH = 5   # the same engine with a path among polygon obstacles as objective
+SPHERE_PATH = 6    # ... and with a path in three dimensions among spheres
 BF_NAMES = {BF_SPHERE: "Sphere", BF_ROSENBROCK: "Rosenbrock", BF_RASTRIGIN: "Rastrigin",
             BF_GRIEWANK: "Griewank"}
 
@@ -344,6 +345,13 @@ class BFConfig:
     alpha: float = 30.0
     beta: int = 4
     max_edges: int = 0
+    # objective SPHERE_PATH only: D = 3T coordinates, z in [0, map_d]
+    map_d: float = 400.0
+    max_spheres: int = 0
+    # path objectives: Priori Initialization of a run that has a previous path (Sec.
+    # 3.3.3), ceil(pi_gamma N) particles per group within +-pi_halfwidth of it
+    pi_gamma: float = 0.0
+    pi_halfwidth: float = 20.0
 
     def with_(self, **kw) -> "BFConfig":
         return replace(self, **kw)
@@ -406,6 +414,58 @@ def polygon_workload(seed: int = 0, T: int = 8, N: int = 170, n_boxes: int = 12,
     target = np.array([380.0, 380.0], np.float32)
     hyper = np.ascontiguousarray(TABLE_HYPER8_PATH, dtype=np.float32)
     return cfg, start, target, polys, edges, hyper
+
+
+def sphere_workload(seed: int = 0, T: int = 16, N: int = 170, S: int = 64, n_moving: int = 32,
+                    iters: int = 100, runs: int = 1, pi_gamma: float = 0.25):
+    """Path planning in three dimensions among spheres (the paper's Conclusion names
+    the extension from 2D to 3D planning): a 400^3 box, start (20, 20, 20), target
+    (380, 380, 380), ``S`` spheres with centres U[60, 340]^3 and radii U[10, 30] (the
+    2D circles' make-up with a third coordinate), of which the last ``n_moving`` move
+    at |v| ~ U[0.5, 2] per cycle in a uniformly random direction; T waypoints (D = 3T),
+    G = 8 x N with the Table hyper8path rows, alpha = 30, beta = 4 (Table params_path),
+    ``iters`` iterations per plan, ``runs`` independent swarms (Philox runs) on the
+    same scene, PI with ``pi_gamma`` and a half-width of 20 once a run has a previous
+    path -> (config, scene dict: start, target, spheres (S, 4), vel (S, 3); hyper)."""
+    rng = np.random.default_rng(8000 + seed)
+    sph = np.empty((S, 4), np.float32)
+    sph[:, :3] = rng.uniform(60.0, 340.0, (S, 3))
+    sph[:, 3] = rng.uniform(10.0, 30.0, S)
+    vel = np.zeros((S, 3), np.float32)
+    m = min(n_moving, S)
+    if m:
+        d = rng.normal(size=(m, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        vel[S - m:] = d * rng.uniform(0.5, 2.0, (m, 1))
+    cfg = BFConfig(fn=SPHERE_PATH, D=3 * T, G=8, N=N, lo=0.0, hi=400.0, max_iters=iters, seed=seed, runs=runs,
+                   map_w=400.0, map_h=400.0, map_d=400.0, alpha=PARAMS_PATH["alpha"], beta=PARAMS_PATH["beta"],
+                   max_spheres=max(S, 1), pi_gamma=pi_gamma, pi_halfwidth=20.0)
+    scene = {"start": np.array([20.0, 20.0, 20.0], np.float32),
+             "target": np.array([380.0, 380.0, 380.0], np.float32), "spheres": sph, "vel": vel}
+    return cfg, scene, np.ascontiguousarray(TABLE_HYPER8_PATH, dtype=np.float32)
+
+
+def advance_spheres(spheres: np.ndarray, vel: np.ndarray, box=(400.0, 400.0, 400.0)):
+    """The 3D scene's simulator step (the Fig. PP caption's rule with a third axis):
+    each sphere moves by its velocity; a velocity component flips when the sphere
+    passes the wall it is moving towards.  FP32, returns new arrays."""
+    c = np.array(spheres, np.float32, copy=True)
+    v = np.array(vel, np.float32, copy=True)
+    for a in range(3):
+        c[:, a] += v[:, a]
+        lo = (c[:, a] - c[:, 3] < 0.0) & (v[:, a] < 0.0)
+        hi = (c[:, a] + c[:, 3] > np.float32(box[a])) & (v[:, a] > 0.0)
+        v[lo | hi, a] = -v[lo | hi, a]
+    return c, v
+
+
+def random_paths3(seed: int, n: int, T: int, box=(400.0, 400.0, 400.0)) -> np.ndarray:
+    """n random 3D paths (n, 3T) uniform over the box, FP32."""
+    rng = np.random.default_rng(seed)
+    X = np.empty((n, 3 * T), np.float32)
+    for a in range(3):
+        X[:, a * T:(a + 1) * T] = rng.uniform(0.0, box[a], (n, T))
+    return X
 
 
 def random_paths(seed: int, n: int, T: int, W: float = 400.0, H: float = 400.0) -> np.ndarray:
