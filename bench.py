@@ -18,8 +18,9 @@ the host cores instead (bounded sample).
 Further sections add objects to the same line (``--sections`` selects them): the
 batched scenes, the learned prior, the serving loop, the ablation of the paper's
 path-planning comparison (``paper_ablation``), the benchmark functions at the
-standard and large scale (``bf``), planning among polygon obstacles (``poly``) and
-the tensor-core GEMM alone (``gemm``, not in the default list).
+standard and large scale (``bf``), planning among polygon obstacles (``poly``),
+planning in three dimensions among spheres (``plan3d``) and the tensor-core GEMM
+alone (``gemm``, not in the default list).
 """
 from __future__ import annotations
 
@@ -118,7 +119,7 @@ def parse():
     ap.add_argument("--prior-rounds", type=int, default=3)
     ap.add_argument("--prior-epochs", type=int, default=30)
     ap.add_argument("--prior-batch", type=int, default=4096, help="rows per Adam step")
-    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper,boxes,agents,bf,poly",
+    ap.add_argument("--sections", type=str, default="main,cpu,batch,prior,serve,paper,boxes,agents,bf,poly,plan3d",
                     help="comma list of main, cpu, batch, prior, serve, paper, boxes, agents, bf, poly, gemm "
                          "(paper: the ablation variants of the path-planning comparison; boxes: the same among "
                          "moving bounding boxes; agents: multi-agent teams; bf: the benchmark "
@@ -963,6 +964,100 @@ def run_poly(runs: int = 64, iters: int = 100):
     return out
 
 
+# Algorithmic work of a 3D path evaluation: per (segment, sphere) test 24 flops
+# (w = c - m: 3; along = w.u: 5; w - along u: 6; max(|along| - h, 0): 2; squared
+# distance: 7; compare: 1), per segment 20 (direction 3, squared length 5, square
+# root 1, reciprocal 1, unit vector 3, midpoint 6, half-length 1).
+FLOPS_PER_PAIR_3D, FLOPS_PER_SEGMENT_3D = 24, 20
+
+
+def run_plan3d(runs: int = 64, iters: int = 100, cycles: int = 20):
+    """Path planning in three dimensions among spheres (the paper's Conclusion names
+    the 2D-to-3D extension as future work): 400^3 box, 64 spheres r~U[10,30] (32
+    moving), T = 16 (D = 48), G = 8 x 170, Table hyper8path, alpha = 30, beta = 4,
+    ``iters`` iterations.  ``batch``: ``runs`` independent plans of the static scene
+    in one CUDA graph; ``single``: one plan alone; ``dynamic``: ``cycles`` planning
+    cycles of all runs among the moving spheres, each run warm-started (PI) from its
+    own previous best path, through the host API (scene and warm start in, best
+    paths out, every cycle)."""
+    import torch
+
+    from paper_2308_10169_gb300 import BFPlanner
+    from paper_2308_10169_gb300.inputs import advance_spheres, sphere_workload
+    from paper_2308_10169_gb300.planner import sphere_evaluate
+    out = {}
+
+    def quality(cfg, sc, sph, best):
+        F, Q = sphere_evaluate(torch.from_numpy(best).cuda(), sc["start"], sc["target"],
+                               torch.from_numpy(np.ascontiguousarray(sph)).cuda(), cfg.alpha, cfg.beta)
+        return float(np.median(F.cpu().numpy())), float(np.mean(Q.cpu().numpy() == 0))
+
+    for R in (runs, 1):
+        cfg, sc, hy = sphere_workload(0, iters=iters, runs=R)
+        pl = BFPlanner(cfg)
+        pl.set_hyper(hy)
+        pl.set_spheres(sc["start"], sc["target"], sc["spheres"])
+        kname = pl.kernel_name()
+        pl.run_async()
+        pl.sync()
+        l0 = pl.launch_count()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(pl.stream)
+        pl.run_async()
+        b.record(pl.stream)
+        pl.sync()
+        ms = a.elapsed_time(b)
+        best, _ = pl.read_all()
+        med, cf = quality(cfg, sc, sc["spheres"], best)
+        M, T, S = cfg.G * cfg.N, cfg.D // 3, sc["spheres"].shape[0]
+        flops = R * M * (T + 1) * (FLOPS_PER_PAIR_3D * S + FLOPS_PER_SEGMENT_3D) * iters
+        achieved = flops / (ms / 1e3) / 1e12
+        out["batch" if R == runs else "single"] = {
+            "runs": R, "ms": ms, "plans_per_s": R / (ms / 1e3), "us_per_iteration": 1e3 * ms / iters,
+            "particle_evals_per_s": R * M * iters / (ms / 1e3),
+            "median_cost": med, "collision_free": cf,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak()[0], "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak()[0], "peak_source": fp32_peak()[1], "kernel": kname,
+                         "flops_per_pair": FLOPS_PER_PAIR_3D, "flops_per_segment": FLOPS_PER_SEGMENT_3D},
+            "gpu_launches": pl.launch_count() - l0}
+        del pl
+    # dynamic cycles with PI, through the host API
+    cfg, sc, hy = sphere_workload(0, iters=iters, runs=runs)
+    pl = BFPlanner(cfg)
+    pl.set_hyper(hy)
+    sph, vel = sc["spheres"], sc["vel"]
+    prev, meds, cfs = None, [], []
+    pl.set_spheres(sc["start"], sc["target"], sph)
+    pl.run_async()
+    pl.sync()
+    cms = []
+    t0 = time.perf_counter()
+    for cycle in range(cycles):
+        if cycle:
+            sph, vel = advance_spheres(sph, vel)
+        c0 = time.perf_counter()
+        pl.set_spheres(sc["start"], sc["target"], sph)
+        pl.set_warm_start(prev, cycle=cycle)
+        pl.run_async()
+        prev, fit = pl.read_all()
+        cms.append(1e3 * (time.perf_counter() - c0))
+        med, cf = quality(cfg, sc, sph, prev)
+        meds.append(med)
+        cfs.append(cf)
+    wall = time.perf_counter() - t0
+    out["dynamic"] = {"runs": runs, "cycles": cycles, "plans_per_s": runs * cycles / wall,
+                      "ms_per_cycle": {"p50": float(np.percentile(cms, 50)), "p99": float(np.percentile(cms, 99))},
+                      "median_cost_first_last": [meds[0], meds[-1]],
+                      "collision_free_first_last": [cfs[0], cfs[-1]],
+                      "collision_free_mean": float(np.mean(cfs)),
+                      "note": "host API per cycle: set_spheres + set_warm_start (PI from each run's previous "
+                              "best) + the run's CUDA graph + best paths read back; the sphere motion on the host"}
+    out["workload"] = (f"400^3 box, 64 spheres r~U[10,30] (32 moving |v|~U[0.5,2]), T=16 (D=48), G=8 x 170, "
+                       f"{iters} iterations, Table hyper8path, alpha=30 beta=4, PI gamma=0.25 h=20, "
+                       f"{runs} plans per graph")
+    return out
+
+
 def _world_step(ag):
     """The client's simulated world between two requests of an agent: circles and
     start/target move by their velocity and bounce off the map border."""
@@ -1360,6 +1455,8 @@ def main():
             line["multi_agent"] = run_agents()
         if world == 1 and "poly" in sections:
             line["poly"] = run_poly()
+        if world == 1 and "plan3d" in sections:
+            line["plan3d"] = run_plan3d()
         if world == 1 and "bf" in sections:
             line["bf"] = run_bf([int(x) for x in args.bf_fns.split(",") if x.strip()], args.bf_iters,
                                 args.bf_trials, _hbm_peak())

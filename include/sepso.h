@@ -696,7 +696,8 @@ const char* sepso_last_error(void);
 /*   BF4 1 + sum x_i^2 / 4000 - prod cos(x_i / sqrt i).                        */
 /* ------------------------------------------------------------------------- */
 typedef struct sepso_bf_config {
-  int32_t fn;         /* 1..4: BF1..BF4; 5: a path among polygons (below)       */
+  int32_t fn;         /* 1..4: BF1..BF4; 5: a path among polygons; 6: a 3D path */
+                      /* among spheres (both below)                             */
   int32_t D;          /* coordinates per particle, 1..16384                     */
   int32_t G;          /* groups, 1..32                                          */
   int32_t N;          /* particles per group (G x N + G + 1 < 2^30)             */
@@ -711,6 +712,11 @@ typedef struct sepso_bf_config {
   float alpha;        /* >= 0                                                    */
   int32_t beta;       /* 1..8                                                    */
   int32_t max_edges;  /* capacity for obstacle edges, 0..4096                    */
+  /* objective 6 only (the Conclusion's extension from 2D to 3D planning): D = 3T */
+  /* coordinates [x1..xT, y1..yT, z1..zT], x in [0, map_w], y in [0, map_h], z   */
+  /* in [0, map_d]; fitness = 3D length + alpha * Q^beta (alpha, beta as above)  */
+  float map_d;        /* > 0                                                     */
+  int32_t max_spheres; /* capacity for spheres, 0..4096                          */
 } sepso_bf_config;
 
 typedef struct sepso_bf_ctx* sepso_bf_handle;
@@ -750,6 +756,35 @@ int sepso_bf_set_polygons(sepso_bf_handle h, const float* start, const float* ta
 int sepso_poly_evaluate(int32_t T, int32_t n, const float* X, int32_t ldx, const float* start, const float* target,
                         const float* edges, int32_t E, float alpha, int32_t beta, float* F, int32_t* Q,
                         void* stream);
+/* Objective 6, a path in three dimensions among spheres (the paper's Conclusion
+ * names the extension from 2D to 3D planning as future work; this is Eqs.
+ * path_fit, lenth and penalty with a third coordinate).  spheres: host
+ * float[S*4] (cx, cy, cz, r; r >= 0), start and target host float[3].  Q = the
+ * number of (path segment, sphere) pairs whose distance is below the radius (the
+ * circles' rule of Sec. 3.3.2 in 3D; a segment inside a sphere counts).  Required
+ * before sepso_bf_run_async; a new sphere count re-captures the graph.  Syncs.
+ * Errors: EINVAL (objective, S > max_spheres, non-finite values, negative radius),
+ * ECUDA. */
+int sepso_bf_set_spheres(sepso_bf_handle h, const float* start, const float* target, const float* spheres,
+                         int32_t S);
+/* Priori Initialization for the path objectives 5 and 6 (Sec. 3.3.3): the next
+ * run initialises the first ceil(pi_gamma N) particles of each group (computed in
+ * double precision) around that run's previous best path, X = clip(prevT +
+ * (2u - 1) pi_h) with u from the PI stream, and every Philox counter of the run
+ * carries `cycle` (the planning cycle, < 2^24) as the planner's do.  prevT: host
+ * float[runs*D], one previous path per run, or NULL with pi_gamma = 0 (a cold start
+ * that still sets the cycle).  The values live in the workspace, so a captured
+ * run graph stays valid.  Syncs.  Errors: EINVAL (objective, gamma outside [0, 1],
+ * negative or non-finite pi_h, non-finite prevT, cycle too large), ECUDA. */
+int sepso_bf_set_warm_start(sepso_bf_handle h, const float* prevT, float pi_gamma, float pi_h, uint32_t cycle);
+/* Objective 6 of n paths X (device, row pitch ldx >= 3T floats: x of the T
+ * waypoints, then y, then z) among S device spheres (float4 cx, cy, cz, r;
+ * 16-byte aligned): fitness into device F[n] and, if Q is not NULL, the collision
+ * counts into device Q[n].  start/target: host float[3].  On stream.
+ * Errors: EINVAL, ECUDA. */
+int sepso_sphere_evaluate(int32_t T, int32_t n, const float* X, int32_t ldx, const float* start, const float* target,
+                          const float* spheres, int32_t S, float alpha, int32_t beta, float* F, int32_t* Q,
+                          void* stream);
 /* Continue every swarm for iters more iterations (after a run or a loaded state). */
 int sepso_bf_step(sepso_bf_handle h, int32_t iters);
 int sepso_bf_sync(sepso_bf_handle h);
@@ -774,8 +809,9 @@ int sepso_bf_set_state(sepso_bf_handle h, int32_t run, const float* X, const flo
 int sepso_bf_evaluate(int32_t fn, int32_t D, int32_t n, const float* X, int32_t ldx, float* F, void* stream);
 int64_t sepso_bf_launch_count(sepso_bf_handle h);
 /* Name of the kernels this handle launches: bf_iter_kernel<fn> (a launch per
- * iteration, a warp per particle); poly_lane_kernel (objective 5, D <= 64, at
- * least 256 particles per SM: a lane per particle); or, for benchmark-function
+ * iteration, a warp per particle); poly_lane_kernel or sphere_lane_kernel
+ * (objective 5 or 6, D <= 64, at least 256 particles per SM: a lane per
+ * particle); or, for benchmark-function
  * swarms of at most 8192 coordinates (G x N x D), bf_small_kernel for whole runs
  * (one CTA per run, the swarm in shared memory) with bf_iter_kernel for steps.
  * Static string. */

@@ -466,6 +466,10 @@ class BFSwarm(Swarm):
         self._c = _bf_cfg(cfg)
         self._none = scene if scene is not None else Scene((0.0, 0.0), (0.0, 0.0), np.zeros((0, 3)))
 
+    def set_scene(self, scene):
+        """The scene of the next iterations (a dynamic run's new obstacle positions)."""
+        self._none = scene
+
     def set_previous(self, prevT, cycle: int):
         """Priori Initialization for the next ``init`` (Sec. 3.3.3): the first
         ceil(pi_gamma N) particles of each group start within +-pi_halfwidth of the

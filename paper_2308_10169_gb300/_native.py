@@ -112,14 +112,15 @@ class BFConfig(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("runs", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32),
                 ("map_w", ctypes.c_float), ("map_h", ctypes.c_float), ("alpha", ctypes.c_float),
-                ("beta", ctypes.c_int32), ("max_edges", ctypes.c_int32)]
+                ("beta", ctypes.c_int32), ("max_edges", ctypes.c_int32),
+                ("map_d", ctypes.c_float), ("max_spheres", ctypes.c_int32)]
 
 
 def bf_config_struct(cfg) -> BFConfig:
     return BFConfig(fn=cfg.fn, D=cfg.D, G=cfg.G, N=cfg.N, lo=cfg.lo, hi=cfg.hi,
                     max_iters=cfg.max_iters, runs=cfg.runs, seed=cfg.seed, run_id=cfg.run_id,
                     map_w=cfg.map_w, map_h=cfg.map_h, alpha=cfg.alpha, beta=cfg.beta,
-                    max_edges=cfg.max_edges)
+                    max_edges=cfg.max_edges, map_d=cfg.map_d, max_spheres=cfg.max_spheres)
 
 
 # Every exported entry point with (restype, argtypes); the tests check the list
@@ -231,6 +232,10 @@ SIGNATURES = {
     "sepso_bf_set_state": (ctypes.c_int, [_vp, _i32] + [_vp] * 8 + [_i32]),
     "sepso_bf_evaluate": (ctypes.c_int, [_i32, _i32, _i32, _vp, _i32, _vp, _vp]),
     "sepso_bf_set_polygons": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32]),
+    "sepso_bf_set_spheres": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32]),
+    "sepso_bf_set_warm_start": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_uint32]),
+    "sepso_sphere_evaluate": (ctypes.c_int, [_i32, _i32, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.c_float,
+                                             _i32, _vp, _vp, _vp]),
     "sepso_poly_evaluate": (ctypes.c_int, [_i32, _i32, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.c_float,
                                            _i32, _vp, _vp, _vp]),
     "sepso_bf_launch_count": (ctypes.c_int64, [_vp]),

@@ -31,6 +31,13 @@
 // iterations rotate (read j - 1, write j, clear j + 1); the Tbest holder is kept
 // in two slots.  Rows of a loaded state live in an "external" table addressed by
 // particle numbers >= M.
+//
+// Path objectives: 5 is a path among polygons (Sec. 3.3.1), 6 a path in three
+// dimensions among spheres (the Conclusion's extension from 2D to 3D planning).
+// Their rows are waypoint coordinates by axis ([x1..xT, y1..yT(, z1..zT)]), each
+// axis with its own box, and a run may start with Priori Initialization (Sec.
+// 3.3.3) around its previous best path; the planning cycle then enters every
+// Philox counter, as in the planner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,17 +62,23 @@ constexpr int kMaxD = 16384;
 constexpr int kMaxRG = 4096;           // runs x groups: the CTA's key table
 constexpr int kSmemTotal = 200 * 1024;  // shared-memory budget of the iteration kernel
 constexpr int kMaxEdges = 4096;        // polygon edges held in shared memory
+constexpr int kMaxSpheres = 4096;      // spheres held in shared memory
 
 struct BfParams {
   int fn, D, Dp, G, N, M, R, K, hist_len;
   float lo, hi;
-  // objective 5 (a path among polygons): coordinates j >= half lie in [lo2, hi2]
-  // (y), the others in [lo, hi] (x); half = D for the benchmark functions
-  int half;
-  float lo2, hi2, alpha;
+  // path objectives: coordinate j lies on axis (j >= half) + (j >= half2), x in
+  // [lo, hi], y in [lo2, hi2], z in [lo3, hi3]; half = half2 = D for the benchmark
+  // functions, half2 = D for objective 5
+  int half, half2;
+  float lo2, hi2, lo3, hi3, alpha;
   int beta, E;
-  const float4* edges;        // E polygon edges (x0, y0, x1, y1)
-  const float* pts;           // start x, y, target x, y
+  const float4* edges;        // objective 5: E polygon edges (x0, y0, x1, y1);
+                              // objective 6: E spheres (cx, cy, cz, r)
+  const float* pts;           // start, then target: 2 coordinates each (objective 5), 3 (objective 6)
+  const int* warm;            // path objectives, device words: PI particles per group, PI
+                              // half-width (float bits), planning cycle
+  const float* prevT;         // R rows of Dp: each run's previous best path (the PI centre)
   uint32_t key0, key1, run_id;
   float* X;                   // R*M rows of Dp
   float* V;                   // R*M rows of Dp
@@ -180,6 +193,77 @@ __device__ __forceinline__ float pow_int(float q, int beta) {
   return r;
 }
 
+// Box of coordinate j of a path objective: its axis (x, y or z) picks the bounds.
+__device__ __forceinline__ int coord_axis(const BfParams& p, int j) { return (j >= p.half) + (j >= p.half2); }
+__device__ __forceinline__ float axis_sel(int ax, float a, float b, float c) { return ax == 0 ? a : (ax == 1 ? b : c); }
+
+// Objective 6 (the Conclusion's extension to 3D planning of Eqs. path_fit, lenth,
+// penalty): a segment as its midpoint m, unit direction u (zero for a zero-length
+// segment), half-length h and length.  For a sphere centre c, with w = c - m and
+// along = w.u, the squared distance from c to the segment is
+// max(|along| - h, 0)^2 + |w - along u|^2 (the perpendicular part is formed as a
+// vector, not as |w|^2 - along^2, so that it keeps its precision for long segments).
+struct Seg3 {
+  float mx, my, mz, ux, uy, uz, h, len;
+};
+__device__ __forceinline__ Seg3 seg3(float ax, float ay, float az, float bx, float by, float bz) {
+  Seg3 g;
+  const float dx = bx - ax, dy = by - ay, dz = bz - az;
+  const float l2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  g.len = sqrtf(l2);
+  const float inv = l2 > 0.0f ? 1.0f / g.len : 0.0f;
+  g.ux = dx * inv;
+  g.uy = dy * inv;
+  g.uz = dz * inv;
+  g.mx = 0.5f * (ax + bx);
+  g.my = 0.5f * (ay + by);
+  g.mz = 0.5f * (az + bz);
+  g.h = 0.5f * g.len;
+  return g;
+}
+// 1 when the segment passes closer than the radius to the sphere (cx, cy, cz, r^2).
+__device__ __forceinline__ int sphere_hit(const Seg3& g, float4 c) {
+  const float wx = c.x - g.mx, wy = c.y - g.my, wz = c.z - g.mz;
+  const float al = fmaf(wx, g.ux, fmaf(wy, g.uy, wz * g.uz));
+  const float px = fmaf(-al, g.ux, wx), py = fmaf(-al, g.uy, wy), pz = fmaf(-al, g.uz, wz);
+  const float e = fmaxf(fabsf(al) - g.h, 0.0f);
+  return fmaf(e, e, fmaf(px, px, fmaf(py, py, pz * pz))) < c.w;
+}
+
+// Objective 6 of one row, the whole warp (every lane gets the value): the T + 1
+// segment lengths over the lanes, then per segment the spheres over the lanes.
+// Waypoint i is (s[i], s[T + i], s[2T + i]); pts = start x, y, z, target x, y, z.
+// kSquared: the spheres' fourth value already holds r^2 (shared-memory copies).
+template <bool kSquared>
+__device__ __forceinline__ float sphere_row(const float* s, int T, const float* pts, const float4* sph, int S,
+                                            float alpha, int beta, int lane, int& qout) {
+  float len = 0.0f;
+  for (int k = lane; k <= T; k += 32) {
+    const float ax = k == 0 ? pts[0] : s[k - 1], ay = k == 0 ? pts[1] : s[T + k - 1];
+    const float az = k == 0 ? pts[2] : s[2 * T + k - 1];
+    const float bx = k == T ? pts[3] : s[k], by = k == T ? pts[4] : s[T + k], bz = k == T ? pts[5] : s[2 * T + k];
+    const float dx = bx - ax, dy = by - ay, dz = bz - az;
+    len += sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  }
+  len = warp_sum(len);
+  int q = 0;
+  for (int k = 0; k <= T; ++k) {
+    const float ax = k == 0 ? pts[0] : s[k - 1], ay = k == 0 ? pts[1] : s[T + k - 1];
+    const float az = k == 0 ? pts[2] : s[2 * T + k - 1];
+    const float bx = k == T ? pts[3] : s[k], by = k == T ? pts[4] : s[T + k], bz = k == T ? pts[5] : s[2 * T + k];
+    const Seg3 g = seg3(ax, ay, az, bx, by, bz);
+#pragma unroll 4
+    for (int o = lane; o < S; o += 32) {
+      float4 c = sph[o];
+      if (!kSquared) c.w = c.w * c.w;
+      q += sphere_hit(g, c);
+    }
+  }
+  q = __reduce_add_sync(0xffffffffu, q);
+  qout = q;
+  return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
+}
+
 // Objective 5 (Sec. 3.3.1 map model; Eqs. path_fit, lenth, penalty): length of the
 // path start -> waypoints -> target plus alpha * Q^beta, Q = the number of proper
 // crossings (strict orientation tests) between its T + 1 segments and the E obstacle
@@ -220,12 +304,18 @@ __device__ __forceinline__ float poly_row(const float* s, int T, const float* pt
 // Initialisation (Algorithm 1): X uniform over [lo, hi]^D, V uniform in +-V_range
 // with V_range = V_limit (hi - lo), Pbest row = X (parity 0), Pbest fitness +inf, no
 // bests.  Four coordinates per Philox draw (counter: coordinate chunk, particle,
-// stream, run), as in the path planner.
+// stream, run), as in the path planner.  Path objectives: each axis its own box;
+// with Priori Initialization (Sec. 3.3.3) the first n_pi particles of each group
+// take X = clip(prevT + (2u - 1) h_PI) from the PI stream instead, and the planning
+// cycle enters the counters.
 // ---------------------------------------------------------------------------
 __global__ void bf_init_kernel(const BfParams p) {
   const size_t nch = (size_t)p.Dp / 4;
   const size_t total = (size_t)p.R * p.M * nch;
-  const float ext = p.hi - p.lo;
+  const bool path = p.fn >= 5;
+  const int n_pi = path ? p.warm[0] : 0;
+  const float pi_h = path ? __int_as_float(p.warm[1]) : 0.0f;
+  const uint32_t cyc = path ? (uint32_t)p.warm[2] : 0u;
   for (size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
        it += (size_t)gridDim.x * blockDim.x) {
     const size_t q = it / nch;
@@ -233,15 +323,22 @@ __global__ void bf_init_kernel(const BfParams p) {
     const int r = (int)(q / p.M), pi = (int)(q - (size_t)r * p.M);
     const int g = pi / p.N;
     const float vlim = p.hyper[((size_t)r * p.G + g) * 6 + 5];
-    const uint4 ux = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitX, 0u, p.run_id + (uint32_t)r);
-    const uint4 uv = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitV, 0u, p.run_id + (uint32_t)r);
+    const bool by_pi = pi - g * p.N < n_pi;
+    const uint4 ux = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, by_pi ? kStreamPI : kStreamInitX, cyc,
+                          p.run_id + (uint32_t)r);
+    const uint4 uv = draw(p.key0, p.key1, (uint32_t)c, (uint32_t)pi, kStreamInitV, cyc, p.run_id + (uint32_t)r);
     float xs[4], vs[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int jj = 4 * c + e;
-      const bool in = jj < p.D, second = jj >= p.half;
-      const float lo = second ? p.lo2 : p.lo, ex = second ? p.hi2 - p.lo2 : ext;
-      xs[e] = in ? lo + lane_of(ux, e) * ex : 0.0f;
+      const bool in = jj < p.D;
+      const int ax = coord_axis(p, jj);
+      const float lo = axis_sel(ax, p.lo, p.lo2, p.lo3), hi = axis_sel(ax, p.hi, p.hi2, p.hi3);
+      const float ex = hi - lo;
+      float x = lo + lane_of(ux, e) * ex;
+      if (by_pi && in)
+        x = fminf(fmaxf(p.prevT[(size_t)r * p.Dp + jj] + (2.0f * lane_of(ux, e) - 1.0f) * pi_h, lo), hi);
+      xs[e] = in ? x : 0.0f;
       vs[e] = in ? (2.0f * lane_of(uv, e) - 1.0f) * (vlim * ex) : 0.0f;
     }
     const float4 x4 = make_float4(xs[0], xs[1], xs[2], xs[3]);
@@ -278,15 +375,20 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
   unsigned long long* stk = sgk + RG;
   const size_t keys_b = ((size_t)(2 * RG + p.R) * 8 + 15) / 16 * 16;
   float4* sedges = reinterpret_cast<float4*>(smem + keys_b);
-  const int E = FN == 5 ? p.E : 0;
+  const int E = FN >= 5 ? p.E : 0;
   float* srow = reinterpret_cast<float*>(smem + keys_b + (size_t)E * 16) + (size_t)warp * p.Dp;
+  const uint32_t cyc = FN >= 5 ? (uint32_t)p.warm[2] : 0u;
   const unsigned long long* kprev = p.keys + (size_t)((j + 2) % 3) * RG;  // iteration j - 1
   unsigned long long* kcur = p.keys + (size_t)(j % 3) * RG;
   for (int i = threadIdx.x; i < RG; i += blockDim.x) {
     ck[i] = kEmpty;
     if (mode & kUpdate) sgk[i] = kprev[i];
   }
-  for (int i = threadIdx.x; i < E; i += blockDim.x) sedges[i] = p.edges[i];
+  for (int i = threadIdx.x; i < E; i += blockDim.x) {
+    float4 o = p.edges[i];
+    if (FN == 6) o.w = o.w * o.w;   // spheres are tested against r^2
+    sedges[i] = o;
+  }
   if (blockIdx.x == 0) {
     unsigned long long* knext = p.keys + (size_t)((j + 1) % 3) * RG;   // read last in launch j - 1
     for (int i = threadIdx.x; i < RG; i += blockDim.x) knext[i] = kEmpty;
@@ -334,10 +436,10 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
       const float4* tr = reinterpret_cast<const float4*>(key_row(p, r, tk));
       const float* hy = p.hyper + ((size_t)r * p.G + g) * 6;
       const float c1 = hy[0], c2 = hy[1], c3 = hy[2], w_init = hy[3], w_end = hy[4];
-      const float vmax = hy[5] * ext, vmax2 = hy[5] * (p.hi2 - p.lo2);
+      const float vmax = hy[5] * ext, vmax2 = hy[5] * (p.hi2 - p.lo2), vmax3 = hy[5] * (p.hi3 - p.lo3);
       const int k = j - 1;
       const float w = w_init - (w_init - w_end) / (float)p.K * (float)k;
-      const uint4 rr = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)pi, kStreamVel, 0u, p.run_id + (uint32_t)r);
+      const uint4 rr = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)pi, kStreamVel, cyc, p.run_id + (uint32_t)r);
       const float a1 = c1 * u01(rr.x), a2 = c2 * u01(rr.y), a3 = c3 * u01(rr.z);
       const bool need_T = c3 != 0.0f;
       float4* vr = reinterpret_cast<float4*>(p.V + q * p.Dp);
@@ -369,15 +471,15 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               if (4 * c + e < p.D) {
-                const bool second = FN == 5 && 4 * c + e >= p.half;
-                const float bv = second ? vmax2 : vmax;
+                const int ax = FN >= 5 ? coord_axis(p, 4 * c + e) : 0;
+                const float bv = axis_sel(ax, vmax, vmax2, vmax3);
                 float vv = w * ve[e];
                 vv = fmaf(a1, pe[e] - xe[e], vv);
                 vv = fmaf(a2, ge[e] - xe[e], vv);
                 if (need_T) vv = fmaf(a3, te[e] - xe[e], vv);
                 vv = fminf(fmaxf(vv, -bv), bv);
                 ve[e] = vv;
-                xe[e] = fminf(fmaxf(xe[e] + vv, second ? p.lo2 : p.lo), second ? p.hi2 : p.hi);
+                xe[e] = fminf(fmaxf(xe[e] + vv, axis_sel(ax, p.lo, p.lo2, p.lo3)), axis_sel(ax, p.hi, p.hi2, p.hi3));
               }
             }
             xr[c] = x[u];
@@ -399,8 +501,9 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
 
     // Fitness of iteration j, Pbest update (strictly better only).
     int qdummy;
-    const float F = FN == 5 ? poly_row(srow, p.half, p.pts, sedges, E, p.alpha, p.beta, lane, qdummy)
-                            : bf_row<FN>(srow, p.D, lane);
+    const float F = FN == 5   ? poly_row(srow, p.half, p.pts, sedges, E, p.alpha, p.beta, lane, qdummy)
+                    : FN == 6 ? sphere_row<true>(srow, p.half, p.pts, sedges, E, p.alpha, p.beta, lane, qdummy)
+                              : bf_row<FN>(srow, p.D, lane);
     unsigned npar = par;
     if (F < pf) {
       npar = par ^ 1u;
@@ -605,17 +708,18 @@ __global__ void __launch_bounds__(256) bf_small_kernel(const BfParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// Objective 5 with a lane per particle: the iteration of bf_iter_kernel for short
-// rows (paths of D = 2T <= kLaneMaxD coordinates), where a warp per particle would
+// Path objectives with a lane per particle: the iteration of bf_iter_kernel for
+// short rows (paths of D <= kLaneMaxD coordinates), where a warp per particle would
 // leave most lanes idle in the update and spread each path's few segments over the
 // lanes.  Lane l of a warp owns one particle: it updates its row coordinate by
 // coordinate, keeps the new row in shared memory (stride D + 1: the lanes' rows fall
-// in different banks) and tests its T + 1 segments against every edge, the edge
-// read by all lanes at once (a broadcast).  Bests, keys and Pbest parities as in
-// bf_iter_kernel.
+// in different banks) and tests its T + 1 segments against every obstacle record
+// (an edge of objective 5, a sphere of objective 6), the record read by all lanes
+// at once (a broadcast).  Bests, keys and Pbest parities as in bf_iter_kernel.
+// poly_lane_kernel runs objective 5, sphere_lane_kernel objective 6.
 // ---------------------------------------------------------------------------
 constexpr int kLaneMaxD = 64;
-constexpr int kLaneThreads = 256;
+constexpr int kLaneThreads = 128;   // small CTAs: the single wave of lane CTAs spreads evenly over the SMs
 constexpr int kLaneMinPerSm = 256;   // particles per SM from which objective 5 uses a lane each
 constexpr long long kSmallMaxCoords = 8192;  // swarm size (G N D) up to which a run is one CTA
 
@@ -641,9 +745,43 @@ __device__ __forceinline__ float poly_lane(const float* s, int T, const float* p
   return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
 }
 
-__global__ void __launch_bounds__(256) poly_lane_kernel(const BfParams p, int j, int mode) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// Objective 6 of one lane's row (waypoint i = (s[i], s[T + i], s[2T + i])): the
+// segments two at a time, each sphere (cx, cy, cz, r^2) read once for both.
+__device__ __forceinline__ float sphere_lane(const float* s, int T, const float* pts, const float4* sph, int S,
+                                             float alpha, int beta) {
+  float len = 0.0f;
+  int q = 0;
+  float ax = pts[0], ay = pts[1], az = pts[2];
+  for (int k = 0; k <= T; k += 2) {
+    const float bx = k == T ? pts[3] : s[k], by = k == T ? pts[4] : s[T + k], bz = k == T ? pts[5] : s[2 * T + k];
+    const Seg3 g0 = seg3(ax, ay, az, bx, by, bz);
+    len += g0.len;
+    if (k + 1 <= T) {
+      const int k1 = k + 1;
+      const float cx = k1 == T ? pts[3] : s[k1], cy = k1 == T ? pts[4] : s[T + k1];
+      const float cz = k1 == T ? pts[5] : s[2 * T + k1];
+      const Seg3 g1 = seg3(bx, by, bz, cx, cy, cz);
+      len += g1.len;
+#pragma unroll 4
+      for (int o = 0; o < S; ++o) {
+        const float4 c = sph[o];
+        q += sphere_hit(g0, c) + sphere_hit(g1, c);
+      }
+      ax = cx;
+      ay = cy;
+      az = cz;
+    } else {
+#pragma unroll 4
+      for (int o = 0; o < S; ++o) q += sphere_hit(g0, sph[o]);
+    }
+  }
+  return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
+}
+
+template <int FN>
+__device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mode, unsigned char* smem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
   const int RG = p.R * p.G;
   const int D = p.D, T = p.half;
   unsigned long long* ck = reinterpret_cast<unsigned long long*>(smem);
@@ -652,15 +790,21 @@ __global__ void __launch_bounds__(256) poly_lane_kernel(const BfParams p, int j,
   const size_t keys_b = ((size_t)(2 * RG + p.R) * 8 + 15) / 16 * 16;
   float4* sedges = reinterpret_cast<float4*>(smem + keys_b);
   const int E = p.E;
-  float* srow = reinterpret_cast<float*>(smem + keys_b + (size_t)E * 16) +
-                ((size_t)warp * 32 + lane) * (D + 1);
+  // the warp's 32 rows (stride D + 1), and this lane's own
+  float* swarp = reinterpret_cast<float*>(smem + keys_b + (size_t)E * 16) + (size_t)warp * 32 * (D + 1);
+  float* srow = swarp + (size_t)lane * (D + 1);
   const unsigned long long* kprev = p.keys + (size_t)((j + 2) % 3) * RG;
   unsigned long long* kcur = p.keys + (size_t)(j % 3) * RG;
   for (int i = threadIdx.x; i < RG; i += blockDim.x) {
     ck[i] = kEmpty;
     if (mode & kUpdate) sgk[i] = kprev[i];
   }
-  for (int i = threadIdx.x; i < E; i += blockDim.x) sedges[i] = p.edges[i];
+  for (int i = threadIdx.x; i < E; i += blockDim.x) {
+    float4 o = p.edges[i];
+    if (FN == 6) o.w = o.w * o.w;   // spheres are tested against r^2
+    sedges[i] = o;
+  }
+  const uint32_t cyc = (uint32_t)p.warm[2];
   if (blockIdx.x == 0) {
     unsigned long long* knext = p.keys + (size_t)((j + 1) % 3) * RG;
     for (int i = threadIdx.x; i < RG; i += blockDim.x) knext[i] = kEmpty;
@@ -679,66 +823,123 @@ __global__ void __launch_bounds__(256) poly_lane_kernel(const BfParams p, int j,
     __syncthreads();
   }
 
+  // A warp takes 32 consecutive particles; lane l evaluates particle qb + l.  Rows
+  // move between global and shared memory one particle at a time over the lanes
+  // (coalesced), the fitness runs a lane per particle from the shared-memory rows.
   const size_t total = (size_t)p.R * p.M;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
-    const int r = (int)(q / p.M), pi = (int)(q - (size_t)r * p.M);
-    const int g = pi / p.N;
-    float* xr = p.X + q * p.Dp;
-    const unsigned par = p.pcur[q];
-    float pf = p.Pfit[q];
+  for (size_t qb = (size_t)blockIdx.x * blockDim.x + (size_t)warp * 32; qb < total; qb += stride) {
+    const size_t q = qb + lane;
+    const bool valid = q < total;
+    const int nv = (int)(total - qb < 32 ? total - qb : 32);
+    int r = 0, pi = 0, g = 0;
+    unsigned par = 0;
+    float pf = INFINITY;
+    if (valid) {
+      r = (int)(q / p.M);
+      pi = (int)(q - (size_t)r * p.M);
+      g = pi / p.N;
+      par = p.pcur[q];
+      pf = p.Pfit[q];
+    }
     if (mode & kUpdate) {
-      const unsigned long long* gk = sgk + (size_t)r * p.G;
-      const float* gr = key_row(p, r, gk[g]);
-      const float* tr = key_row(p, r, stk[r]);
-      const float* hy = p.hyper + ((size_t)r * p.G + g) * 6;
-      const float c1 = hy[0], c2 = hy[1], c3 = hy[2], w_init = hy[3], w_end = hy[4];
-      const float vmax = hy[5] * (p.hi - p.lo), vmax2 = hy[5] * (p.hi2 - p.lo2);
-      const int k = j - 1;
-      const float w = w_init - (w_init - w_end) / (float)p.K * (float)k;
-      const uint4 rr = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)pi, kStreamVel, 0u, p.run_id + (uint32_t)r);
-      const float a1 = c1 * u01(rr.x), a2 = c2 * u01(rr.y), a3 = c3 * u01(rr.z);
-      const bool need_T = c3 != 0.0f;
-      float* vr = p.V + q * p.Dp;
-      const float* pr = p.P + ((size_t)par * total + q) * p.Dp;
-      for (int i = 0; i < D; ++i) {
-        const bool second = i >= T;
-        const float bv = second ? vmax2 : vmax;
-        float x = xr[i];
-        float vv = w * vr[i];
-        vv = fmaf(a1, pr[i] - x, vv);
-        vv = fmaf(a2, (gr ? gr[i] : 0.0f) - x, vv);
-        if (need_T) vv = fmaf(a3, (tr ? tr[i] : 0.0f) - x, vv);
-        vv = fminf(fmaxf(vv, -bv), bv);
-        vr[i] = vv;
-        x = fminf(fmaxf(x + vv, second ? p.lo2 : p.lo), second ? p.hi2 : p.hi);
-        xr[i] = x;
-        srow[i] = x;
+      // this lane's particle: inertia and random factors (one Philox draw)
+      float w = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+      if (valid) {
+        const float* hy = p.hyper + ((size_t)r * p.G + g) * 6;
+        const float c1 = hy[0], c2 = hy[1], c3 = hy[2], w_init = hy[3], w_end = hy[4];
+        const int k = j - 1;
+        w = w_init - (w_init - w_end) / (float)p.K * (float)k;
+        const uint4 rr = draw(p.key0, p.key1, (uint32_t)k, (uint32_t)pi, kStreamVel, cyc, p.run_id + (uint32_t)r);
+        a1 = c1 * u01(rr.x);
+        a2 = c2 * u01(rr.y);
+        a3 = c3 * u01(rr.z);
       }
-      if (pi == 0)
+      for (int t = 0; t < nv; ++t) {
+        const float wt = __shfl_sync(full, w, t), a1t = __shfl_sync(full, a1, t);
+        const float a2t = __shfl_sync(full, a2, t), a3t = __shfl_sync(full, a3, t);
+        const int rt = __shfl_sync(full, r, t), gt = __shfl_sync(full, g, t);
+        const unsigned part = __shfl_sync(full, par, t);
+        const size_t qt = qb + t;
+        const float* hy = p.hyper + ((size_t)rt * p.G + gt) * 6;
+        const bool need_T = hy[2] != 0.0f;
+        const float vmax = hy[5] * (p.hi - p.lo), vmax2 = hy[5] * (p.hi2 - p.lo2), vmax3 = hy[5] * (p.hi3 - p.lo3);
+        const float* gr = key_row(p, rt, sgk[(size_t)rt * p.G + gt]);
+        const float* tr = key_row(p, rt, stk[rt]);
+        float* xr = p.X + qt * p.Dp;
+        float* vr = p.V + qt * p.Dp;
+        const float* pr = p.P + ((size_t)part * total + qt) * p.Dp;
+        float* st = swarp + (size_t)t * (D + 1);
+        for (int i = lane; i < D; i += 32) {
+          const int ax = coord_axis(p, i);
+          const float bv = axis_sel(ax, vmax, vmax2, vmax3);
+          float x = xr[i];
+          float vv = wt * vr[i];
+          vv = fmaf(a1t, pr[i] - x, vv);
+          vv = fmaf(a2t, (gr ? gr[i] : 0.0f) - x, vv);
+          if (need_T) vv = fmaf(a3t, (tr ? tr[i] : 0.0f) - x, vv);
+          vv = fminf(fmaxf(vv, -bv), bv);
+          vr[i] = vv;
+          x = fminf(fmaxf(x + vv, axis_sel(ax, p.lo, p.lo2, p.lo3)), axis_sel(ax, p.hi, p.hi2, p.hi3));
+          xr[i] = x;
+          st[i] = x;
+        }
+      }
+      if (valid && pi == 0) {
+        const unsigned long long* gk = sgk + (size_t)r * p.G;
         for (int gg = 0; gg < p.G; ++gg) {
           const unsigned long long kk = gk[gg];
           if (kk != kEmpty) atomicMin(&ck[r * p.G + gg], kk & ~(1ull << 31));
         }
+      }
     } else {
-      for (int i = 0; i < D; ++i) srow[i] = xr[i];
+      for (int t = 0; t < nv; ++t) {
+        const float* xr = p.X + (qb + t) * p.Dp;
+        float* st = swarp + (size_t)t * (D + 1);
+        for (int i = lane; i < D; i += 32) st[i] = xr[i];
+      }
     }
-    if (!(mode & kEval)) continue;
-    const float F = poly_lane(srow, T, p.pts, sedges, E, p.alpha, p.beta);
-    unsigned npar = par;
-    if (F < pf) {
-      npar = par ^ 1u;
-      float* dst = p.P + ((size_t)npar * total + q) * p.Dp;
-      for (int i = 0; i < D; ++i) dst[i] = srow[i];
-      pf = F;
-      p.Pfit[q] = F;
-      p.pcur[q] = (unsigned char)npar;
+    __syncwarp();
+    if (mode & kEval) {
+      float F = 0.0f;
+      if (valid)
+        F = FN == 5 ? poly_lane(srow, T, p.pts, sedges, E, p.alpha, p.beta)
+                    : sphere_lane(srow, T, p.pts, sedges, E, p.alpha, p.beta);
+      const bool improved = valid && F < pf;
+      unsigned npar = par;
+      if (improved) {
+        npar = par ^ 1u;
+        pf = F;
+        p.Pfit[q] = F;
+        p.pcur[q] = (unsigned char)npar;
+      }
+      // improved rows into their new Pbest buffer, one particle at a time over the lanes
+      unsigned imask = __ballot_sync(full, improved);
+      while (imask) {
+        const int t = __ffs(imask) - 1;
+        imask &= imask - 1;
+        const unsigned nt = __shfl_sync(full, npar, t);
+        float* dst = p.P + ((size_t)nt * total + qb + t) * p.Dp;
+        const float* st = swarp + (size_t)t * (D + 1);
+        for (int i = lane; i < D; i += 32) dst[i] = st[i];
+      }
+      if (valid && isfinite(pf)) atomicMin(&ck[r * p.G + g], make_key(pf, 1u, (uint32_t)pi, npar));
     }
-    if (isfinite(pf)) atomicMin(&ck[r * p.G + g], make_key(pf, 1u, (uint32_t)pi, npar));
+    __syncwarp();
   }
   __syncthreads();
   for (int i = threadIdx.x; i < RG; i += blockDim.x)
     if (ck[i] != kEmpty) atomicMin(&kcur[i], ck[i]);
+}
+
+__global__ void __launch_bounds__(kLaneThreads) poly_lane_kernel(const BfParams p, int j, int mode) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  path_lane_iter<5>(p, j, mode, smem);
+}
+
+__global__ void __launch_bounds__(kLaneThreads) sphere_lane_kernel(const BfParams p, int j, int mode) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  path_lane_iter<6>(p, j, mode, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -777,6 +978,22 @@ __global__ void poly_eval_kernel(const float* X, int ldx, int T, int n, float4 s
   for (int i = blockIdx.x * nwarps + (threadIdx.x >> 5); i < n; i += gridDim.x * nwarps) {
     int q;
     const float f = poly_row(X + (size_t)i * ldx, T, pts, edges, E, alpha, beta, lane, q);
+    if (lane == 0) {
+      F[i] = f;
+      if (Q) Q[i] = q;
+    }
+  }
+}
+
+// Objective 6 of n paths (pitch ldx floats): fitness and Q, one warp per path;
+// spheres (cx, cy, cz, r) read from global memory.
+__global__ void sphere_eval_kernel(const float* X, int ldx, int T, int n, float4 st, float2 tg, const float4* sph,
+                                   int S, float alpha, int beta, float* F, int* Q) {
+  const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  const float pts[6] = {st.x, st.y, st.z, st.w, tg.x, tg.y};
+  for (int i = blockIdx.x * nwarps + (threadIdx.x >> 5); i < n; i += gridDim.x * nwarps) {
+    int q;
+    const float f = sphere_row<false>(X + (size_t)i * ldx, T, pts, sph, S, alpha, beta, lane, q);
     if (lane == 0) {
       F[i] = f;
       if (Q) Q[i] = q;
@@ -824,8 +1041,13 @@ int bffail(int code, const char* fmt, ...) {
 size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct BfLayout {
-  size_t X, V, P, Pfit, pcur, keys, thold, hyper, ext, hist, Gb, Gfit, Tb, Tfit, edges, pts, total;
+  size_t X, V, P, Pfit, pcur, keys, thold, hyper, ext, hist, Gb, Gfit, Tb, Tfit, edges, pts, warm, prevT, total;
 };
+
+// Obstacle records a handle holds: polygon edges (objective 5) or spheres (6).
+int obstacle_capacity(const sepso_bf_config& c) {
+  return c.fn == 5 ? c.max_edges : (c.fn == 6 ? c.max_spheres : 0);
+}
 
 int padded(int D) { return (D + 3) & ~3; }
 
@@ -853,15 +1075,27 @@ BfLayout bf_layout(const sepso_bf_config& c) {
   L.Gfit = take(R * G * 4);
   L.Tb = take(R * Dp * 4);
   L.Tfit = take(R * 4);
-  L.edges = take((size_t)(c.fn == 5 ? c.max_edges : 0) * 16);
-  L.pts = take(16);
+  L.edges = take((size_t)obstacle_capacity(c) * 16);
+  L.pts = take(32);
+  L.warm = take(16);
+  L.prevT = take(c.fn >= 5 ? R * Dp * 4 : 0);
   L.total = off;
   return L;
 }
 
 int bf_validate(const sepso_bf_config* c) {
   if (!c) return bffail(SEPSO_EINVAL, "NULL config");
-  if (c->fn < 1 || c->fn > 5) return bffail(SEPSO_EINVAL, "fn=%d is not one of 1..5", c->fn);
+  if (c->fn < 1 || c->fn > 6) return bffail(SEPSO_EINVAL, "fn=%d is not one of 1..6", c->fn);
+  if (c->fn == 6) {
+    if (c->D < 3 || c->D % 3) return bffail(SEPSO_EINVAL, "a 3D path needs D = 3T >= 3 (D=%d)", c->D);
+    if (!(c->map_w > 0.0f) || !(c->map_h > 0.0f) || !(c->map_d > 0.0f) || !std::isfinite(c->map_w) ||
+        !std::isfinite(c->map_h) || !std::isfinite(c->map_d))
+      return bffail(SEPSO_EINVAL, "box %g x %g x %g", (double)c->map_w, (double)c->map_h, (double)c->map_d);
+    if (!std::isfinite(c->alpha) || c->alpha < 0.0f) return bffail(SEPSO_EINVAL, "alpha=%g", (double)c->alpha);
+    if (c->beta < 1 || c->beta > 8) return bffail(SEPSO_EINVAL, "beta=%d outside [1, 8]", c->beta);
+    if (c->max_spheres < 0 || c->max_spheres > kMaxSpheres)
+      return bffail(SEPSO_EINVAL, "max_spheres=%d outside [0, %d]", c->max_spheres, kMaxSpheres);
+  }
   if (c->fn == 5) {
     if (c->D < 2 || c->D % 2) return bffail(SEPSO_EINVAL, "a path needs an even D >= 2 (D=%d)", c->D);
     if (!(c->map_w > 0.0f) || !(c->map_h > 0.0f) || !std::isfinite(c->map_w) || !std::isfinite(c->map_h))
@@ -876,7 +1110,7 @@ int bf_validate(const sepso_bf_config* c) {
   if (c->N < 1) return bffail(SEPSO_EINVAL, "N=%d below 1", c->N);
   if (c->runs < 1) return bffail(SEPSO_EINVAL, "runs=%d below 1", c->runs);
   if (c->max_iters < 1) return bffail(SEPSO_EINVAL, "max_iters=%d below 1", c->max_iters);
-  if (c->fn != 5 && (!std::isfinite(c->lo) || !std::isfinite(c->hi) || !(c->lo < c->hi)))
+  if (c->fn <= 4 && (!std::isfinite(c->lo) || !std::isfinite(c->hi) || !(c->lo < c->hi)))
     return bffail(SEPSO_EINVAL, "box [%g, %g] is empty or not finite", (double)c->lo, (double)c->hi);
   if ((long long)c->runs * c->G > kMaxRG)
     return bffail(SEPSO_EINVAL, "runs x G = %lld above %d", (long long)c->runs * c->G, kMaxRG);
@@ -908,7 +1142,7 @@ struct sepso_bf_ctx {
   cudaStream_t stream = nullptr;
   int threads = 0, grid = 0, init_grid = 0;
   size_t smem = 0;
-  int grid_lane = 0;  // > 0: objective 5 runs on poly_lane_kernel
+  int grid_lane = 0;  // > 0: a path objective runs on poly_lane_kernel / sphere_lane_kernel
   size_t smem_lane = 0;
   size_t smem_small = 0;  // > 0: whole runs go to bf_small_kernel
   int64_t k = -1;  // iterations done; -1 before the first run or state
@@ -923,7 +1157,10 @@ namespace {
 
 cudaError_t launch_iter(sepso_bf_ctx* h, int j, int mode) {
   if (h->grid_lane > 0) {
-    poly_lane_kernel<<<h->grid_lane, kLaneThreads, h->smem_lane, h->stream>>>(h->p, j, mode);
+    if (h->c.fn == 6)
+      sphere_lane_kernel<<<h->grid_lane, kLaneThreads, h->smem_lane, h->stream>>>(h->p, j, mode);
+    else
+      poly_lane_kernel<<<h->grid_lane, kLaneThreads, h->smem_lane, h->stream>>>(h->p, j, mode);
     return cudaGetLastError();
   }
   switch (h->c.fn) {
@@ -931,7 +1168,8 @@ cudaError_t launch_iter(sepso_bf_ctx* h, int j, int mode) {
     case 2: bf_iter_kernel<2><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
     case 3: bf_iter_kernel<3><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
     case 4: bf_iter_kernel<4><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
-    default: bf_iter_kernel<5><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
+    case 5: bf_iter_kernel<5><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
+    default: bf_iter_kernel<6><<<h->grid, h->threads, h->smem, h->stream>>>(h->p, j, mode); break;
   }
   return cudaGetLastError();
 }
@@ -992,13 +1230,13 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
     return bffail(SEPSO_ENOSPC, "workspace of %zu bytes below the %zu needed", bytes, L.total);
   if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return bffail(SEPSO_ENOSPC, "workspace not 256-byte aligned");
   const int Dp = padded(c->D);
-  const int edge_b = c->fn == 5 ? c->max_edges * 16 : 0;
+  const int edge_b = obstacle_capacity(*c) * 16;
   const size_t RG = (size_t)c->runs * c->G;
   const size_t keys_b = ((2 * RG + c->runs) * 8 + 15) / 16 * 16;
   const long long rows_budget = (long long)kSmemTotal - (long long)keys_b - edge_b;
   if (rows_budget < (long long)Dp * 4)
-    return bffail(SEPSO_ERANGE, "D=%d with %d edges and %zu group keys exceeds shared memory", c->D,
-                  c->fn == 5 ? c->max_edges : 0, RG);
+    return bffail(SEPSO_ERANGE, "D=%d with %d obstacle records and %zu group keys exceeds shared memory", c->D,
+                  obstacle_capacity(*c), RG);
   const int nwarps = (int)std::min<long long>(8, rows_budget / ((long long)Dp * 4));
   const size_t smem = keys_b + (size_t)edge_b + (size_t)nwarps * Dp * 4;
   int dev = 0, sms = 0, bps = 0;
@@ -1010,7 +1248,8 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
     case 2: e = iter_attr<2>(smem); if (e == cudaSuccess) e = iter_occ<2>(&bps, nwarps * 32, smem); break;
     case 3: e = iter_attr<3>(smem); if (e == cudaSuccess) e = iter_occ<3>(&bps, nwarps * 32, smem); break;
     case 4: e = iter_attr<4>(smem); if (e == cudaSuccess) e = iter_occ<4>(&bps, nwarps * 32, smem); break;
-    default: e = iter_attr<5>(smem); if (e == cudaSuccess) e = iter_occ<5>(&bps, nwarps * 32, smem); break;
+    case 5: e = iter_attr<5>(smem); if (e == cudaSuccess) e = iter_occ<5>(&bps, nwarps * 32, smem); break;
+    default: e = iter_attr<6>(smem); if (e == cudaSuccess) e = iter_occ<6>(&bps, nwarps * 32, smem); break;
   }
   if (e != cudaSuccess) return bffail(SEPSO_ECUDA, "iteration kernel attributes: %s", cudaGetErrorString(e));
   if (bps < 1) return bffail(SEPSO_ERANGE, "iteration kernel does not fit an SM (%zu bytes of shared memory)", smem);
@@ -1045,11 +1284,12 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   }
   // A lane per particle pays once there are enough particles to give every SM's
   // lanes work (below that, one path's tests spread over a warp finish sooner).
-  if (c->fn == 5 && c->D <= kLaneMaxD && RM >= (long long)kLaneMinPerSm * sms) {
+  if (c->fn >= 5 && c->D <= kLaneMaxD && RM >= (long long)kLaneMinPerSm * sms) {
     const size_t sl = keys_b + (size_t)edge_b + (size_t)kLaneThreads * (c->D + 1) * 4;
     int bl = 0;
-    e = cudaFuncSetAttribute(poly_lane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, poly_lane_kernel, kLaneThreads, sl);
+    const void* lk = c->fn == 6 ? (const void*)sphere_lane_kernel : (const void*)poly_lane_kernel;
+    e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, lk, kLaneThreads, sl);
     if (e != cudaSuccess) {
       delete h;
       return bffail(SEPSO_ECUDA, "lane kernel attributes: %s", cudaGetErrorString(e));
@@ -1071,12 +1311,16 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   p.R = c->runs;
   p.K = c->max_iters;
   p.hist_len = c->max_iters;
-  const bool path = c->fn == 5;
+  const bool path = c->fn >= 5;
+  const int T = c->fn == 6 ? c->D / 3 : c->D / 2;
   p.lo = path ? 0.0f : c->lo;
   p.hi = path ? c->map_w : c->hi;
-  p.half = path ? c->D / 2 : c->D;
+  p.half = path ? T : c->D;
+  p.half2 = c->fn == 6 ? 2 * T : c->D;
   p.lo2 = path ? 0.0f : c->lo;
   p.hi2 = path ? c->map_h : c->hi;
+  p.lo3 = path ? 0.0f : c->lo;
+  p.hi3 = c->fn == 6 ? c->map_d : p.hi2;
   p.alpha = c->alpha;
   p.beta = c->beta;
   p.E = 0;
@@ -1100,6 +1344,8 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   p.Tfit = reinterpret_cast<float*>(w + L.Tfit);
   p.edges = reinterpret_cast<const float4*>(w + L.edges);
   p.pts = reinterpret_cast<const float*>(w + L.pts);
+  p.warm = reinterpret_cast<const int*>(w + L.warm);
+  p.prevT = reinterpret_cast<const float*>(w + L.prevT);
   e = cudaMemsetAsync(workspace, 0, L.total, h->stream);
   if (e != cudaSuccess) {
     delete h;
@@ -1176,10 +1422,84 @@ int sepso_poly_evaluate(int32_t T, int32_t n, const float* X, int32_t ldx, const
   return SEPSO_OK;
 }
 
+int sepso_bf_set_spheres(sepso_bf_handle h, const float* start, const float* target, const float* spheres,
+                         int32_t S) {
+  if (!h || !start || !target || (S > 0 && !spheres)) return bffail(SEPSO_EINVAL, "NULL argument");
+  if (h->c.fn != 6) return bffail(SEPSO_EINVAL, "spheres belong to objective 6 (fn=%d)", h->c.fn);
+  if (S < 0 || S > h->c.max_spheres)
+    return bffail(SEPSO_EINVAL, "S=%d outside [0, max_spheres=%d]", S, h->c.max_spheres);
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(start[i]) || !std::isfinite(target[i])) return bffail(SEPSO_EINVAL, "start/target not finite");
+  for (int i = 0; i < 4 * S; ++i)
+    if (!std::isfinite(spheres[i])) return bffail(SEPSO_EINVAL, "sphere value %d is not finite", i);
+  for (int o = 0; o < S; ++o)
+    if (spheres[4 * o + 3] < 0.0f) return bffail(SEPSO_EINVAL, "sphere %d has a negative radius", o);
+  const float pts[8] = {start[0], start[1], start[2], target[0], target[1], target[2], 0.0f, 0.0f};
+  if (S > 0)
+    BFCUDA(cudaMemcpyAsync(h->ws + h->L.edges, spheres, (size_t)S * 16, cudaMemcpyHostToDevice, h->stream));
+  BFCUDA(cudaMemcpyAsync(h->ws + h->L.pts, pts, 32, cudaMemcpyHostToDevice, h->stream));
+  BFCUDA(cudaStreamSynchronize(h->stream));
+  if (h->p.E != S && h->exec) {   // the captured launches carry the old sphere count
+    cudaGraphExecDestroy(h->exec);
+    cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+  }
+  h->p.E = S;
+  h->scene_set = true;
+  return SEPSO_OK;
+}
+
+int sepso_bf_set_warm_start(sepso_bf_handle h, const float* prevT, float pi_gamma, float pi_h, uint32_t cycle) {
+  if (!h) return bffail(SEPSO_EINVAL, "NULL handle");
+  if (h->c.fn < 5) return bffail(SEPSO_EINVAL, "warm starts belong to the path objectives (fn=%d)", h->c.fn);
+  if (!std::isfinite(pi_gamma) || pi_gamma < 0.0f || pi_gamma > 1.0f)
+    return bffail(SEPSO_EINVAL, "pi_gamma=%g outside [0, 1]", (double)pi_gamma);
+  if (!std::isfinite(pi_h) || pi_h < 0.0f) return bffail(SEPSO_EINVAL, "pi_h=%g", (double)pi_h);
+  if (cycle >= (1u << 24)) return bffail(SEPSO_EINVAL, "cycle=%u above 2^24 - 1", cycle);
+  if (pi_gamma > 0.0f && !prevT) return bffail(SEPSO_EINVAL, "PI without a previous path");
+  const int R = h->c.runs, D = h->c.D, Dp = h->p.Dp;
+  if (prevT)
+    for (long long i = 0; i < (long long)R * D; ++i)
+      if (!std::isfinite(prevT[i])) return bffail(SEPSO_EINVAL, "prevT[%lld] is not finite", i);
+  // Particles per group placed by PI: ceil(gamma N), in double precision.
+  const int n_pi = prevT ? (int)std::min<double>(h->c.N, std::ceil((double)pi_gamma * (double)h->c.N)) : 0;
+  int32_t words[4];
+  words[0] = n_pi;
+  std::memcpy(&words[1], &pi_h, 4);
+  words[2] = (int32_t)cycle;
+  words[3] = 0;
+  if (prevT)
+    BFCUDA(cudaMemcpy2DAsync(h->ws + h->L.prevT, (size_t)Dp * 4, prevT, (size_t)D * 4, (size_t)D * 4, R,
+                             cudaMemcpyHostToDevice, h->stream));
+  BFCUDA(cudaMemcpyAsync(h->ws + h->L.warm, words, 16, cudaMemcpyHostToDevice, h->stream));
+  BFCUDA(cudaStreamSynchronize(h->stream));
+  return SEPSO_OK;
+}
+
+int sepso_sphere_evaluate(int32_t T, int32_t n, const float* X, int32_t ldx, const float* start, const float* target,
+                          const float* spheres, int32_t S, float alpha, int32_t beta, float* F, int32_t* Q,
+                          void* stream) {
+  if (T < 1 || n < 0 || ldx < 3 * T || S < 0 || beta < 1 || beta > 8 || !std::isfinite(alpha))
+    return bffail(SEPSO_EINVAL, "T=%d, n=%d, ldx=%d, S=%d, beta=%d", T, n, ldx, S, beta);
+  if (!start || !target) return bffail(SEPSO_EINVAL, "NULL start/target");
+  if (n == 0) return SEPSO_OK;
+  if (!X || !F || (S > 0 && !spheres)) return bffail(SEPSO_EINVAL, "NULL argument");
+  if (S > 0 && reinterpret_cast<uintptr_t>(spheres) % 16) return bffail(SEPSO_EINVAL, "spheres not 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = std::min((n + 7) / 8, 4096);
+  sphere_eval_kernel<<<grid, 256, 0, s>>>(X, ldx, T, n, make_float4(start[0], start[1], start[2], target[0]),
+                                          make_float2(target[1], target[2]),
+                                          reinterpret_cast<const float4*>(spheres), S, alpha, beta, F, Q);
+  BFCUDA(cudaGetLastError());
+  return SEPSO_OK;
+}
+
 int sepso_bf_run_async(sepso_bf_handle h, int32_t use_graph) {
   if (!h) return bffail(SEPSO_EINVAL, "NULL handle");
   if (!h->hyper_set) return bffail(SEPSO_ESTATE, "run before set_hyper for every run");
   if (h->c.fn == 5 && !h->scene_set) return bffail(SEPSO_ESTATE, "run before set_polygons");
+  if (h->c.fn == 6 && !h->scene_set) return bffail(SEPSO_ESTATE, "run before set_spheres");
   if (!use_graph) {
     const int rc = enqueue_run(h);
     if (rc) return rc;
@@ -1256,9 +1576,9 @@ int64_t sepso_bf_launch_count(sepso_bf_handle h) { return h ? h->launches : -1; 
 const char* sepso_bf_kernel_name(sepso_bf_handle h) {
   if (!h) return "";
   if (h->smem_small > 0) return "bf_small_kernel (runs), bf_iter_kernel (steps)";
-  if (h->grid_lane > 0) return "poly_lane_kernel";
+  if (h->grid_lane > 0) return h->c.fn == 6 ? "sphere_lane_kernel" : "poly_lane_kernel";
   static const char* names[] = {"", "bf_iter_kernel<1>", "bf_iter_kernel<2>", "bf_iter_kernel<3>",
-                                "bf_iter_kernel<4>", "bf_iter_kernel<5>"};
+                                "bf_iter_kernel<4>", "bf_iter_kernel<5>", "bf_iter_kernel<6>"};
   return names[h->c.fn];
 }
 
@@ -1356,7 +1676,8 @@ int sepso_bf_set_state(sepso_bf_handle h, int32_t run, const float* X, const flo
 }
 
 int sepso_bf_evaluate(int32_t fn, int32_t D, int32_t n, const float* X, int32_t ldx, float* F, void* stream) {
-  if (fn < 1 || fn > 4) return bffail(SEPSO_EINVAL, "fn=%d is not one of BF1..BF4 (paths: sepso_poly_evaluate)", fn);
+  if (fn < 1 || fn > 4)
+    return bffail(SEPSO_EINVAL, "fn=%d is not one of BF1..BF4 (paths: sepso_poly_evaluate, sepso_sphere_evaluate)", fn);
   if (D < 1 || n < 0 || ldx < D) return bffail(SEPSO_EINVAL, "D=%d, n=%d, ldx=%d", D, n, ldx);
   if (n == 0) return SEPSO_OK;
   if (!X || !F) return bffail(SEPSO_EINVAL, "NULL argument");

@@ -315,6 +315,34 @@ class BFPlanner:
         check_bf(self.lib.sepso_bf_set_polygons(self._h, st.ctypes.data, tg.ctypes.data,
                                                 e.ctypes.data if e.size else None, e.shape[0]))
 
+    def set_spheres(self, start, target, spheres):
+        """Objective 6: spheres (S, 4) float32 (cx, cy, cz, r), start and target (3,)."""
+        sp = _f32(spheres, (-1, 4))
+        st, tg = _f32(start, (3,)), _f32(target, (3,))
+        check_bf(self.lib.sepso_bf_set_spheres(self._h, st.ctypes.data, tg.ctypes.data,
+                                               sp.ctypes.data if sp.size else None, sp.shape[0]))
+
+    def set_warm_start(self, prev_paths=None, cycle: int = 0):
+        """Path objectives: the next run's Priori Initialization around each run's
+        previous best path (``prev_paths`` (runs, D); None: a cold start) with the
+        config's pi_gamma and pi_halfwidth; ``cycle`` enters the Philox counters."""
+        if prev_paths is None:
+            check_bf(self.lib.sepso_bf_set_warm_start(self._h, None, ctypes.c_float(0.0), ctypes.c_float(0.0),
+                                                      int(cycle)))
+            return
+        pv = _f32(prev_paths, (self.cfg.runs, self.cfg.D))
+        check_bf(self.lib.sepso_bf_set_warm_start(self._h, pv.ctypes.data, ctypes.c_float(self.cfg.pi_gamma),
+                                                  ctypes.c_float(self.cfg.pi_halfwidth), int(cycle)))
+
+    def read_all(self) -> np.ndarray:
+        """Tbest rows of every run (runs, D) and their fitness (runs,)."""
+        R, D = self.cfg.runs, self.cfg.D
+        out, fit = np.zeros((R, D), np.float32), np.zeros(R, np.float32)
+        for r in range(R):
+            res = self.read(r)
+            out[r], fit[r] = res["x"], res["fit"]
+        return out, fit
+
     def run_async(self, use_graph: bool = True):
         check_bf(self.lib.sepso_bf_run_async(self._h, int(use_graph)))
 
@@ -380,6 +408,24 @@ def poly_evaluate(X: torch.Tensor, start, target, edges: torch.Tensor, alpha: fl
                                                ctypes.c_void_p(edges.data_ptr()), edges.shape[0],
                                                ctypes.c_float(alpha), beta, ctypes.c_void_p(F.data_ptr()),
                                                ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(stream)))
+    return F, Q
+
+
+def sphere_evaluate(X: torch.Tensor, start, target, spheres: torch.Tensor, alpha: float, beta: int):
+    """Objective 6 of the rows of a CUDA float32 tensor (n, 3T) among CUDA float32
+    spheres (S, 4) (cx, cy, cz, r): (fitness, Q) tensors."""
+    assert X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1
+    assert spheres.is_cuda and spheres.dtype == torch.float32 and spheres.is_contiguous()
+    n, D = X.shape
+    F = torch.empty(n, dtype=torch.float32, device=X.device)
+    Q = torch.empty(n, dtype=torch.int32, device=X.device)
+    st, tg = _f32(start, (3,)), _f32(target, (3,))
+    stream = torch.cuda.current_stream(X.device).cuda_stream
+    check_bf(_native.lib().sepso_sphere_evaluate(D // 3, n, ctypes.c_void_p(X.data_ptr()), X.stride(0),
+                                                 st.ctypes.data, tg.ctypes.data,
+                                                 ctypes.c_void_p(spheres.data_ptr()), spheres.shape[0],
+                                                 ctypes.c_float(alpha), beta, ctypes.c_void_p(F.data_ptr()),
+                                                 ctypes.c_void_p(Q.data_ptr()), ctypes.c_void_p(stream)))
     return F, Q
 
 
