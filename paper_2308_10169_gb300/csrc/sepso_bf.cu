@@ -719,6 +719,7 @@ __global__ void __launch_bounds__(256) bf_small_kernel(const BfParams p) {
 // poly_lane_kernel runs objective 5, sphere_lane_kernel objective 6.
 // ---------------------------------------------------------------------------
 constexpr int kLaneMaxD = 64;
+constexpr int kLaneBatch = 2;     // particles whose rows a lane-kernel warp moves at once
 constexpr int kLaneThreads = 128;   // small CTAs: the single wave of lane CTAs spreads evenly over the SMs
 constexpr int kLaneMinPerSm = 256;   // particles per SM from which objective 5 uses a lane each
 constexpr long long kSmallMaxCoords = 8192;  // swarm size (G N D) up to which a run is one CTA
@@ -745,9 +746,58 @@ __device__ __forceinline__ float poly_lane(const float* s, int T, const float* p
   return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
 }
 
-// Objective 6 of one lane's row (waypoint i = (s[i], s[T + i], s[2T + i])): the
-// segments two at a time, each sphere (cx, cy, cz, r^2) read once for both.
-__device__ __forceinline__ float sphere_lane(const float* s, int T, const float* pts, const float4* sph, int S,
+// Objective 6 in the lane kernel, on sphere pairs: shared memory holds the spheres
+// two by two as float4 (cx0, cx1, cy0, cy1) and float4 (cz0, cz1, -r0^2, -r1^2) (an
+// odd count padded with a sphere of radius 0, which nothing hits), so that packed
+// FP32x2 instructions test a segment against two spheres at once: w = c - m,
+// -along = w.(-u), p = w + (-along) u, and S = max(|along| - h, 0)^2 + |p|^2 - r^2
+// per sphere, whose sign bit is the hit (S is never -0: the sum of -r^2 and
+// squares is +0 at the least when it vanishes).
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+struct Seg3P {
+  unsigned long long nmx, nmy, nmz, ux, uy, uz, nux, nuy, nuz;
+  float h;
+};
+__device__ __forceinline__ Seg3P seg3p(const Seg3& g) {
+  Seg3P f;
+  f.nmx = pack2(-g.mx, -g.mx);
+  f.nmy = pack2(-g.my, -g.my);
+  f.nmz = pack2(-g.mz, -g.mz);
+  f.ux = pack2(g.ux, g.ux);
+  f.uy = pack2(g.uy, g.uy);
+  f.uz = pack2(g.uz, g.uz);
+  f.nux = pack2(-g.ux, -g.ux);
+  f.nuy = pack2(-g.uy, -g.uy);
+  f.nuz = pack2(-g.uz, -g.uz);
+  f.h = g.h;
+  return f;
+}
+__device__ __forceinline__ int sphere_pair_hits(const Seg3P& g, ulonglong2 a, ulonglong2 b) {
+  const unsigned long long WX = fadd2(a.x, g.nmx), WY = fadd2(a.y, g.nmy), WZ = fadd2(b.x, g.nmz);
+  const unsigned long long NAL = ffma2(WX, g.nux, ffma2(WY, g.nuy, fmul2(WZ, g.nuz)));
+  const unsigned long long PX = ffma2(NAL, g.ux, WX), PY = ffma2(NAL, g.uy, WY), PZ = ffma2(NAL, g.uz, WZ);
+  float n0, n1;
+  unpack2(NAL, n0, n1);
+  const float e0 = fmaxf(fabsf(n0) - g.h, 0.0f), e1 = fmaxf(fabsf(n1) - g.h, 0.0f);
+  const unsigned long long E = pack2(e0, e1);
+  const unsigned long long S = ffma2(E, E, ffma2(PX, PX, ffma2(PY, PY, ffma2(PZ, PZ, b.y))));
+  float s0, s1;
+  unpack2(S, s0, s1);
+  return (int)(__float_as_uint(s0) >> 31) + (int)(__float_as_uint(s1) >> 31);
+}
+
+// Objective 6 of one lane's row (waypoint i = (s[i], s[T + i], s[2T + i])) against K
+// sphere pairs: the segments two at a time, each pair read once for both.
+__device__ __forceinline__ float sphere_lane(const float* s, int T, const float* pts, const ulonglong2* sp, int K,
                                              float alpha, int beta) {
   float len = 0.0f;
   int q = 0;
@@ -756,26 +806,33 @@ __device__ __forceinline__ float sphere_lane(const float* s, int T, const float*
     const float bx = k == T ? pts[3] : s[k], by = k == T ? pts[4] : s[T + k], bz = k == T ? pts[5] : s[2 * T + k];
     const Seg3 g0 = seg3(ax, ay, az, bx, by, bz);
     len += g0.len;
+    const Seg3P f0 = seg3p(g0);
     if (k + 1 <= T) {
       const int k1 = k + 1;
       const float cx = k1 == T ? pts[3] : s[k1], cy = k1 == T ? pts[4] : s[T + k1];
       const float cz = k1 == T ? pts[5] : s[2 * T + k1];
       const Seg3 g1 = seg3(bx, by, bz, cx, cy, cz);
       len += g1.len;
-#pragma unroll 4
-      for (int o = 0; o < S; ++o) {
-        const float4 c = sph[o];
-        q += sphere_hit(g0, c) + sphere_hit(g1, c);
+      const Seg3P f1 = seg3p(g1);
+#pragma unroll 2
+      for (int o = 0; o < K; ++o) {
+        const ulonglong2 a = sp[2 * o], b = sp[2 * o + 1];
+        q += sphere_pair_hits(f0, a, b) + sphere_pair_hits(f1, a, b);
       }
       ax = cx;
       ay = cy;
       az = cz;
     } else {
-#pragma unroll 4
-      for (int o = 0; o < S; ++o) q += sphere_hit(g0, sph[o]);
+#pragma unroll 2
+      for (int o = 0; o < K; ++o) q += sphere_pair_hits(f0, sp[2 * o], sp[2 * o + 1]);
     }
   }
   return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
+}
+
+// Bytes of the obstacle records the lane kernel stages for n records.
+__host__ __device__ inline size_t lane_obstacle_bytes(int fn, int n) {
+  return fn == 6 ? (size_t)((n + 1) / 2) * 32 : (size_t)n * 16;
 }
 
 template <int FN>
@@ -791,7 +848,7 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
   float4* sedges = reinterpret_cast<float4*>(smem + keys_b);
   const int E = p.E;
   // the warp's 32 rows (stride D + 1), and this lane's own
-  float* swarp = reinterpret_cast<float*>(smem + keys_b + (size_t)E * 16) + (size_t)warp * 32 * (D + 1);
+  float* swarp = reinterpret_cast<float*>(smem + keys_b + lane_obstacle_bytes(FN, E)) + (size_t)warp * 32 * (D + 1);
   float* srow = swarp + (size_t)lane * (D + 1);
   const unsigned long long* kprev = p.keys + (size_t)((j + 2) % 3) * RG;
   unsigned long long* kcur = p.keys + (size_t)(j % 3) * RG;
@@ -799,10 +856,16 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
     ck[i] = kEmpty;
     if (mode & kUpdate) sgk[i] = kprev[i];
   }
-  for (int i = threadIdx.x; i < E; i += blockDim.x) {
-    float4 o = p.edges[i];
-    if (FN == 6) o.w = o.w * o.w;   // spheres are tested against r^2
-    sedges[i] = o;
+  if (FN == 6) {
+    // sphere pairs (cx0, cx1, cy0, cy1), (cz0, cz1, -r0^2, -r1^2); the pad has r = 0
+    for (int i = threadIdx.x; i < (E + 1) / 2; i += blockDim.x) {
+      const float4 c0 = p.edges[2 * i];
+      const float4 c1 = 2 * i + 1 < E ? p.edges[2 * i + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      sedges[2 * i] = make_float4(c0.x, c1.x, c0.y, c1.y);
+      sedges[2 * i + 1] = make_float4(c0.z, c1.z, -(c0.w * c0.w), -(c1.w * c1.w));
+    }
+  } else {
+    for (int i = threadIdx.x; i < E; i += blockDim.x) sedges[i] = p.edges[i];
   }
   const uint32_t cyc = (uint32_t)p.warm[2];
   if (blockIdx.x == 0) {
@@ -855,34 +918,60 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
         a2 = c2 * u01(rr.y);
         a3 = c3 * u01(rr.z);
       }
-      for (int t = 0; t < nv; ++t) {
-        const float wt = __shfl_sync(full, w, t), a1t = __shfl_sync(full, a1, t);
-        const float a2t = __shfl_sync(full, a2, t), a3t = __shfl_sync(full, a3, t);
-        const int rt = __shfl_sync(full, r, t), gt = __shfl_sync(full, g, t);
-        const unsigned part = __shfl_sync(full, par, t);
-        const size_t qt = qb + t;
-        const float* hy = p.hyper + ((size_t)rt * p.G + gt) * 6;
-        const bool need_T = hy[2] != 0.0f;
-        const float vmax = hy[5] * (p.hi - p.lo), vmax2 = hy[5] * (p.hi2 - p.lo2), vmax3 = hy[5] * (p.hi3 - p.lo3);
-        const float* gr = key_row(p, rt, sgk[(size_t)rt * p.G + gt]);
-        const float* tr = key_row(p, rt, stk[rt]);
-        float* xr = p.X + qt * p.Dp;
-        float* vr = p.V + qt * p.Dp;
-        const float* pr = p.P + ((size_t)part * total + qt) * p.Dp;
-        float* st = swarp + (size_t)t * (D + 1);
+      // kLaneBatch particles at a time, all their loads issued before any is used
+      for (int t0 = 0; t0 < nv; t0 += kLaneBatch) {
+        float wt[kLaneBatch], a1t[kLaneBatch], a2t[kLaneBatch], a3t[kLaneBatch], vl[kLaneBatch];
+        bool need_T[kLaneBatch];
+        const float *gr[kLaneBatch], *tr[kLaneBatch], *pr[kLaneBatch];
+        float *xr[kLaneBatch], *vr[kLaneBatch], *st[kLaneBatch];
+#pragma unroll
+        for (int u = 0; u < kLaneBatch; ++u) {
+          const int t = min(t0 + u, nv - 1);
+          wt[u] = __shfl_sync(full, w, t);
+          a1t[u] = __shfl_sync(full, a1, t);
+          a2t[u] = __shfl_sync(full, a2, t);
+          a3t[u] = __shfl_sync(full, a3, t);
+          const int rt = __shfl_sync(full, r, t), gt = __shfl_sync(full, g, t);
+          const unsigned part = __shfl_sync(full, par, t);
+          const size_t qt = qb + t;
+          const float* hy = p.hyper + ((size_t)rt * p.G + gt) * 6;
+          need_T[u] = hy[2] != 0.0f;
+          vl[u] = hy[5];
+          gr[u] = key_row(p, rt, sgk[(size_t)rt * p.G + gt]);
+          tr[u] = key_row(p, rt, stk[rt]);
+          xr[u] = p.X + qt * p.Dp;
+          vr[u] = p.V + qt * p.Dp;
+          pr[u] = p.P + ((size_t)part * total + qt) * p.Dp;
+          st[u] = swarp + (size_t)t * (D + 1);
+        }
         for (int i = lane; i < D; i += 32) {
           const int ax = coord_axis(p, i);
-          const float bv = axis_sel(ax, vmax, vmax2, vmax3);
-          float x = xr[i];
-          float vv = wt * vr[i];
-          vv = fmaf(a1t, pr[i] - x, vv);
-          vv = fmaf(a2t, (gr ? gr[i] : 0.0f) - x, vv);
-          if (need_T) vv = fmaf(a3t, (tr ? tr[i] : 0.0f) - x, vv);
-          vv = fminf(fmaxf(vv, -bv), bv);
-          vr[i] = vv;
-          x = fminf(fmaxf(x + vv, axis_sel(ax, p.lo, p.lo2, p.lo3)), axis_sel(ax, p.hi, p.hi2, p.hi3));
-          xr[i] = x;
-          st[i] = x;
+          const float ext = axis_sel(ax, p.hi - p.lo, p.hi2 - p.lo2, p.hi3 - p.lo3);
+          const float blo = axis_sel(ax, p.lo, p.lo2, p.lo3), bhi = axis_sel(ax, p.hi, p.hi2, p.hi3);
+          float x[kLaneBatch], v[kLaneBatch], pb[kLaneBatch], gb[kLaneBatch], tb[kLaneBatch];
+#pragma unroll
+          for (int u = 0; u < kLaneBatch; ++u) {
+            x[u] = xr[u][i];
+            v[u] = vr[u][i];
+            pb[u] = pr[u][i];
+            gb[u] = gr[u] ? gr[u][i] : 0.0f;
+            tb[u] = (need_T[u] && tr[u]) ? tr[u][i] : 0.0f;
+          }
+#pragma unroll
+          for (int u = 0; u < kLaneBatch; ++u) {
+            if (t0 + u < nv) {
+              const float bv = vl[u] * ext;
+              float vv = wt[u] * v[u];
+              vv = fmaf(a1t[u], pb[u] - x[u], vv);
+              vv = fmaf(a2t[u], gb[u] - x[u], vv);
+              if (need_T[u]) vv = fmaf(a3t[u], tb[u] - x[u], vv);
+              vv = fminf(fmaxf(vv, -bv), bv);
+              vr[u][i] = vv;
+              const float xn = fminf(fmaxf(x[u] + vv, blo), bhi);
+              xr[u][i] = xn;
+              st[u][i] = xn;
+            }
+          }
         }
       }
       if (valid && pi == 0) {
@@ -904,7 +993,8 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
       float F = 0.0f;
       if (valid)
         F = FN == 5 ? poly_lane(srow, T, p.pts, sedges, E, p.alpha, p.beta)
-                    : sphere_lane(srow, T, p.pts, sedges, E, p.alpha, p.beta);
+                    : sphere_lane(srow, T, p.pts, reinterpret_cast<const ulonglong2*>(sedges), (E + 1) / 2, p.alpha,
+                                  p.beta);
       const bool improved = valid && F < pf;
       unsigned npar = par;
       if (improved) {
@@ -932,12 +1022,12 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
     if (ck[i] != kEmpty) atomicMin(&kcur[i], ck[i]);
 }
 
-__global__ void __launch_bounds__(kLaneThreads) poly_lane_kernel(const BfParams p, int j, int mode) {
+__global__ void __launch_bounds__(kLaneThreads, 5) poly_lane_kernel(const BfParams p, int j, int mode) {
   extern __shared__ __align__(16) unsigned char smem[];
   path_lane_iter<5>(p, j, mode, smem);
 }
 
-__global__ void __launch_bounds__(kLaneThreads) sphere_lane_kernel(const BfParams p, int j, int mode) {
+__global__ void __launch_bounds__(kLaneThreads, 5) sphere_lane_kernel(const BfParams p, int j, int mode) {
   extern __shared__ __align__(16) unsigned char smem[];
   path_lane_iter<6>(p, j, mode, smem);
 }
@@ -1285,7 +1375,7 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   // A lane per particle pays once there are enough particles to give every SM's
   // lanes work (below that, one path's tests spread over a warp finish sooner).
   if (c->fn >= 5 && c->D <= kLaneMaxD && RM >= (long long)kLaneMinPerSm * sms) {
-    const size_t sl = keys_b + (size_t)edge_b + (size_t)kLaneThreads * (c->D + 1) * 4;
+    const size_t sl = keys_b + lane_obstacle_bytes(c->fn, obstacle_capacity(*c)) + (size_t)kLaneThreads * (c->D + 1) * 4;
     int bl = 0;
     const void* lk = c->fn == 6 ? (const void*)sphere_lane_kernel : (const void*)poly_lane_kernel;
     e = cudaFuncSetAttribute(lk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sl);
