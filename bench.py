@@ -969,6 +969,9 @@ def run_poly(runs: int = 64, iters: int = 100):
 # distance: 7; compare: 1), per segment 20 (direction 3, squared length 5, square
 # root 1, reciprocal 1, unit vector 3, midpoint 6, half-length 1).
 FLOPS_PER_PAIR_3D, FLOPS_PER_SEGMENT_3D = 24, 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one sphere_lane_kernel launch of the
+# 64-plan batch (profiles/sphere_lane_kernel_3d_batch.md).
+SPHERE_LANE_TRAFFIC_BYTES = 54078464
 
 
 def run_plan3d(runs: int = 64, iters: int = 100, cycles: int = 20):
@@ -1018,7 +1021,8 @@ def run_plan3d(runs: int = 64, iters: int = 100, cycles: int = 20):
             "median_cost": med, "collision_free": cf,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak()[0], "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak()[0], "peak_source": fp32_peak()[1], "kernel": kname,
-                         "flops_per_pair": FLOPS_PER_PAIR_3D, "flops_per_segment": FLOPS_PER_SEGMENT_3D},
+                         "flops_per_pair": FLOPS_PER_PAIR_3D, "flops_per_segment": FLOPS_PER_SEGMENT_3D,
+                         "traffic": SPHERE_LANE_TRAFFIC_BYTES if kname == "sphere_lane_kernel" else None},
             "gpu_launches": pl.launch_count() - l0}
         del pl
     # dynamic cycles with PI, through the host API
