@@ -1010,7 +1010,7 @@ def run_plan3d(runs: int = 64, iters: int = 100, cycles: int = 20):
         b.record(pl.stream)
         pl.sync()
         ms = a.elapsed_time(b)
-        best, _ = pl.read_all()
+        best, _, _ = pl.read_all()
         med, cf = quality(cfg, sc, sc["spheres"], best)
         M, T, S = cfg.G * cfg.N, cfg.D // 3, sc["spheres"].shape[0]
         flops = R * M * (T + 1) * (FLOPS_PER_PAIR_3D * S + FLOPS_PER_SEGMENT_3D) * iters
@@ -1025,37 +1025,43 @@ def run_plan3d(runs: int = 64, iters: int = 100, cycles: int = 20):
                          "traffic": SPHERE_LANE_TRAFFIC_BYTES if kname == "sphere_lane_kernel" else None},
             "gpu_launches": pl.launch_count() - l0}
         del pl
-    # dynamic cycles with PI, through the host API
-    cfg, sc, hy = sphere_workload(0, iters=iters, runs=runs)
-    pl = BFPlanner(cfg)
-    pl.set_hyper(hy)
-    sph, vel = sc["spheres"], sc["vel"]
-    prev, meds, cfs = None, [], []
-    pl.set_spheres(sc["start"], sc["target"], sph)
-    pl.run_async()
-    pl.sync()
-    cms = []
-    t0 = time.perf_counter()
-    for cycle in range(cycles):
-        if cycle:
-            sph, vel = advance_spheres(sph, vel)
-        c0 = time.perf_counter()
+    # dynamic cycles with PI, through the host API; then the same with Auto Truncation
+    def dynamic(at_stall):
+        cfg, sc, hy = sphere_workload(0, iters=iters, runs=runs, at_stall=at_stall, stall_tol=1.0)
+        pl = BFPlanner(cfg)
+        pl.set_hyper(hy)
+        sph, vel = sc["spheres"], sc["vel"]
+        prev, meds, cfs, its = None, [], [], []
         pl.set_spheres(sc["start"], sc["target"], sph)
-        pl.set_warm_start(prev, cycle=cycle)
         pl.run_async()
-        prev, fit = pl.read_all()
-        cms.append(1e3 * (time.perf_counter() - c0))
-        med, cf = quality(cfg, sc, sph, prev)
-        meds.append(med)
-        cfs.append(cf)
-    wall = time.perf_counter() - t0
-    out["dynamic"] = {"runs": runs, "cycles": cycles, "plans_per_s": runs * cycles / wall,
-                      "ms_per_cycle": {"p50": float(np.percentile(cms, 50)), "p99": float(np.percentile(cms, 99))},
-                      "median_cost_first_last": [meds[0], meds[-1]],
-                      "collision_free_first_last": [cfs[0], cfs[-1]],
-                      "collision_free_mean": float(np.mean(cfs)),
-                      "note": "host API per cycle: set_spheres + set_warm_start (PI from each run's previous "
-                              "best) + the run's CUDA graph + best paths read back; the sphere motion on the host"}
+        pl.sync()
+        cms = []
+        for cycle in range(cycles):
+            if cycle:
+                sph, vel = advance_spheres(sph, vel)
+            c0 = time.perf_counter()
+            pl.set_spheres(sc["start"], sc["target"], sph)
+            pl.set_warm_start(prev, cycle=cycle)
+            pl.run_async()
+            prev, fit, it = pl.read_all()
+            cms.append(1e3 * (time.perf_counter() - c0))
+            its.append(float(np.mean(it)))
+            med, cf = quality(cfg, sc, sph, prev)
+            meds.append(med)
+            cfs.append(cf)
+        return {"runs": runs, "cycles": cycles, "plans_per_s": runs * cycles / (sum(cms) / 1e3),
+                "ms_per_cycle": {"p50": float(np.percentile(cms, 50)), "p99": float(np.percentile(cms, 99))},
+                "iters_per_plan": float(np.mean(its)),
+                "median_cost_first_last": [meds[0], meds[-1]],
+                "collision_free_first_last": [cfs[0], cfs[-1]],
+                "collision_free_mean": float(np.mean(cfs)),
+                "note": "host API per cycle: set_spheres + set_warm_start (PI from each run's previous best) + "
+                        "the run's CUDA graph + best paths read back; the sphere motion on the host"
+                        + ("; Auto Truncation by stall counter 10, tolerance 1.0 (a stopped plan's later "
+                           "launches skip it)" if at_stall else "")}
+
+    out["dynamic"] = dynamic(0)
+    out["dynamic_at"] = dynamic(10)
     out["workload"] = (f"400^3 box, 64 spheres r~U[10,30] (32 moving |v|~U[0.5,2]), T=16 (D=48), G=8 x 170, "
                        f"{iters} iterations, Table hyper8path, alpha=30 beta=4, PI gamma=0.25 h=20, "
                        f"{runs} plans per graph")

@@ -717,6 +717,14 @@ typedef struct sepso_bf_config {
   /* in [0, map_d]; fitness = 3D length + alpha * Q^beta (alpha, beta as above)  */
   float map_d;        /* > 0                                                     */
   int32_t max_spheres; /* capacity for spheres, 0..4096                          */
+  /* objectives 5 and 6: Auto Truncation (Sec. 3.3.4, stall-counter reading): a   */
+  /* run stops after at_stall iterations in which its Tbest fitness did not drop  */
+  /* by more than stall_tol while its Tbest path collides with nothing; it then   */
+  /* keeps Tbest of the stopping iteration and moves no particle after it (a      */
+  /* loaded state counts as colliding until a particle of the swarm holds Tbest). */
+  /* 0 = off (max_iters iterations).                                              */
+  int32_t at_stall;   /* >= 0                                                    */
+  float stall_tol;    /* >= 0, finite                                            */
 } sepso_bf_config;
 
 typedef struct sepso_bf_ctx* sepso_bf_handle;
@@ -789,7 +797,8 @@ int sepso_sphere_evaluate(int32_t T, int32_t n, const float* X, int32_t ldx, con
 int sepso_bf_step(sepso_bf_handle h, int32_t iters);
 int sepso_bf_sync(sepso_bf_handle h);
 /* Tbest of a run: best_x host float[D] (or NULL), best_fit host float (or NULL),
- * iterations done.  Syncs the stream.  Errors: EINVAL, ESTATE, ECUDA. */
+ * iterations done (with Auto Truncation, the run's stopping iteration if it
+ * stopped).  Syncs the stream.  Errors: EINVAL, ESTATE, ECUDA. */
 int sepso_bf_read(sepso_bf_handle h, int32_t run, float* best_x, float* best_fit, int32_t* iters);
 /* Tbest fitness after each of the first max_iters iterations: host float[max_iters]. */
 int sepso_bf_history(sepso_bf_handle h, int32_t run, float* hist);

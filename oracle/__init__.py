@@ -409,7 +409,8 @@ def _bf_cfg(c) -> _Config:
     T = c.D // 2 if c.fn == 5 else (c.D // 3 if c.fn == 6 else 0)
     return _Config(T=T, G=c.G, N=c.N, W=f32(c.map_w), H=f32(c.map_h),
                    alpha=f32(c.alpha), beta=c.beta, max_iters=c.max_iters,
-                   at_mode=0, tw=1, delta=0.0, stall_iters=0, stall_tol=0.0, seed=c.seed,
+                   at_mode=2 if getattr(c, "at_stall", 0) > 0 else 0, tw=1, delta=0.0,
+                   stall_iters=getattr(c, "at_stall", 0), stall_tol=f32(getattr(c, "stall_tol", 0.0)), seed=c.seed,
                    run_id=c.run_id, problem=c.fn, Dbf=c.D,
                    lo=f32(c.lo), hi=f32(c.hi), Z=f32(getattr(c, "map_d", 0.0)),
                    use_pi=int(getattr(c, "pi_gamma", 0.0) > 0.0), pi_gamma=f32(getattr(c, "pi_gamma", 0.0)),
@@ -490,8 +491,28 @@ class BFSwarm(Swarm):
     def iteration(self, scene=None, check_stop: bool = False) -> bool:
         return super().iteration(self._none, False)
 
+    def iteration_stop(self) -> bool:
+        """One iteration in planning mode (Auto Truncation and the cap); True when the
+        cycle ends here (the update of this iteration is then not applied)."""
+        return super().iteration(self._none, True)
+
     def step(self, scene=None, iters: int = 1):
         super().step(self._none, iters)
+
+    def plan(self) -> dict:
+        """One planning cycle (Algorithm 1 with Auto Truncation when the config sets
+        at_stall, else max_iters iterations): initialise (PI when set_previous gave a
+        previous path), iterate until AT fires or the cap is reached; the stopping
+        iteration's bests are kept and no particle moves after it."""
+        self.s["stall"][0] = 0
+        self.s["prev_lfv"][0] = np.inf
+        self.init()
+        st = self._st()
+        s = self._none.c()
+        while not lib().so_iteration(ctypes.byref(self._c), ctypes.byref(s), _p64(self.hyper), ctypes.byref(st), 1):
+            pass
+        return {"iters": int(self.s["k"][0]), "cost": float(self.s["Tfit"][0]), "Q": int(self.s["TQ"][0]),
+                "waypoints": self.s["Tb"].copy()}
 
     def run(self, iters: int) -> np.ndarray:
         """Initialise, then ``iters`` iterations; returns Tfit after each one."""

@@ -113,14 +113,16 @@ class BFConfig(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32),
                 ("map_w", ctypes.c_float), ("map_h", ctypes.c_float), ("alpha", ctypes.c_float),
                 ("beta", ctypes.c_int32), ("max_edges", ctypes.c_int32),
-                ("map_d", ctypes.c_float), ("max_spheres", ctypes.c_int32)]
+                ("map_d", ctypes.c_float), ("max_spheres", ctypes.c_int32),
+                ("at_stall", ctypes.c_int32), ("stall_tol", ctypes.c_float)]
 
 
 def bf_config_struct(cfg) -> BFConfig:
     return BFConfig(fn=cfg.fn, D=cfg.D, G=cfg.G, N=cfg.N, lo=cfg.lo, hi=cfg.hi,
                     max_iters=cfg.max_iters, runs=cfg.runs, seed=cfg.seed, run_id=cfg.run_id,
                     map_w=cfg.map_w, map_h=cfg.map_h, alpha=cfg.alpha, beta=cfg.beta,
-                    max_edges=cfg.max_edges, map_d=cfg.map_d, max_spheres=cfg.max_spheres)
+                    max_edges=cfg.max_edges, map_d=cfg.map_d, max_spheres=cfg.max_spheres,
+                    at_stall=cfg.at_stall, stall_tol=cfg.stall_tol)
 
 
 # Every exported entry point with (restype, argtypes); the tests check the list

@@ -79,6 +79,14 @@ struct BfParams {
   const int* warm;            // path objectives, device words: PI particles per group, PI
                               // half-width (float bits), planning cycle
   const float* prevT;         // R rows of Dp: each run's previous best path (the PI centre)
+  // path objectives: Auto Truncation by stall counter (Sec. 3.3.4 with the stall
+  // reading): a run stops after at_stall iterations without an improvement of its
+  // Tbest fitness by more than stall_tol while its Tbest collides with nothing;
+  // at_stall = 0: off
+  int at_stall;
+  float stall_tol;
+  int* pq;                    // 2 x R*M: the collision count of each Pbest row, by parity
+  int* at_state;              // 2 slots x R x {stall, previous Tbest fitness bits, stopped, stop iteration}
   uint32_t key0, key1, run_id;
   float* X;                   // R*M rows of Dp
   float* V;                   // R*M rows of Dp
@@ -196,6 +204,58 @@ __device__ __forceinline__ float pow_int(float q, int beta) {
 // Box of coordinate j of a path objective: its axis (x, y or z) picks the bounds.
 __device__ __forceinline__ int coord_axis(const BfParams& p, int j) { return (j >= p.half) + (j >= p.half2); }
 __device__ __forceinline__ float axis_sel(int ax, float a, float b, float c) { return ax == 0 ? a : (ax == 1 ? b : c); }
+
+// Shared memory of an iteration CTA before its obstacles and rows: this launch's
+// candidate keys and the previous group keys (RG each), the Tbest keys (R) and the
+// runs' stop flags (R).
+__host__ __device__ inline size_t bf_keys_bytes(int RG, int R) {
+  return ((size_t)(2 * RG + R) * 8 + (size_t)R * 4 + 15) / 16 * 16;
+}
+
+// Auto Truncation of the runs in launch j (path objectives).  With kUpdate, every
+// CTA decides iteration j - 1 for each run from the run's Tbest key, the state the
+// previous launch left in slot (j + 1) % 2 and the collision count of the Tbest row
+// (its holder's Pbest count; unknown, so no stop, for a row of a loaded state); CTA 0
+// writes the new state into slot j % 2.  Without kUpdate the flags come from slot
+// j % 2 (written by the last whole launch).  sdone[r] != 0: run r has stopped --
+// its particles neither move nor are evaluated again.
+__device__ __forceinline__ void at_decide(const BfParams& p, int j, int mode, const unsigned long long* stk, int* sdone) {
+  const int RM = p.R * p.M;
+  for (int r = threadIdx.x; r < p.R; r += blockDim.x) {
+    if (p.at_stall <= 0) {
+      sdone[r] = 0;
+      continue;
+    }
+    if (!(mode & kUpdate)) {
+      sdone[r] = p.at_state[((size_t)(j % 2) * p.R + r) * 4 + 2];
+      continue;
+    }
+    const int* in = p.at_state + ((size_t)((j + 1) % 2) * p.R + r) * 4;
+    int stall = in[0], done = in[2], stop = in[3];
+    float prev = __int_as_float(in[1]);
+    if (!done) {
+      const unsigned long long tk = stk[r];
+      const float tf = tk == kEmpty ? INFINITY : float_of_ord((uint32_t)(tk >> 32));
+      stall = tf < prev - p.stall_tol ? 0 : stall + 1;
+      prev = tf;
+      int tq = -1;
+      if (tk != kEmpty && (int)key_idx(tk) < p.M)
+        tq = p.pq[(size_t)key_par(tk) * RM + (size_t)r * p.M + key_idx(tk)];
+      if (stall >= p.at_stall && tq == 0) {
+        done = 1;
+        stop = j - 1;
+      }
+    }
+    sdone[r] = done;
+    if (blockIdx.x == 0) {
+      int* out = p.at_state + ((size_t)(j % 2) * p.R + r) * 4;
+      out[0] = stall;
+      out[1] = __float_as_int(prev);
+      out[2] = done;
+      out[3] = stop;
+    }
+  }
+}
 
 // Objective 6 (the Conclusion's extension to 3D planning of Eqs. path_fit, lenth,
 // penalty): a segment as its midpoint m, unit direction u (zero for a zero-length
@@ -357,6 +417,16 @@ __global__ void bf_init_kernel(const BfParams p) {
     p.keys[i] = kEmpty;
     if (i < (size_t)2 * p.R) p.thold[i] = kEmpty;
   }
+  // Auto Truncation: no stall, no previous Tbest, not stopped (both slots)
+  if (path && p.at_stall > 0)
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)2 * p.R;
+         i += (size_t)gridDim.x * blockDim.x) {
+      int* st = p.at_state + i * 4;
+      st[0] = 0;
+      st[1] = __float_as_int(INFINITY);
+      st[2] = 0;
+      st[3] = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -373,7 +443,8 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
   unsigned long long* ck = reinterpret_cast<unsigned long long*>(smem);
   unsigned long long* sgk = ck + RG;
   unsigned long long* stk = sgk + RG;
-  const size_t keys_b = ((size_t)(2 * RG + p.R) * 8 + 15) / 16 * 16;
+  int* sdone = reinterpret_cast<int*>(stk + p.R);
+  const size_t keys_b = bf_keys_bytes(RG, p.R);
   float4* sedges = reinterpret_cast<float4*>(smem + keys_b);
   const int E = FN >= 5 ? p.E : 0;
   float* srow = reinterpret_cast<float*>(smem + keys_b + (size_t)E * 16) + (size_t)warp * p.Dp;
@@ -407,6 +478,10 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
     }
     __syncthreads();
   }
+  if (FN >= 5) {
+    at_decide(p, j, mode, stk, sdone);
+    __syncthreads();
+  }
 
   const float ext = p.hi - p.lo;
   const int nch = p.Dp >> 2;
@@ -427,6 +502,15 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
     if (q + stride < total) {
       par_next = p.pcur[q + stride];
       pf_next = p.Pfit[q + stride];
+    }
+    const bool stopped = FN >= 5 && sdone[r] != 0;
+    if (stopped) {
+      // a stopped run: only its group keys carry over (previous holders, priority 0)
+      if ((mode & kUpdate) && pi == 0 && lane < p.G) {
+        const unsigned long long k0 = sgk[(size_t)r * p.G + lane];
+        if (k0 != kEmpty) atomicMin(&ck[r * p.G + lane], k0 & ~(1ull << 31));
+      }
+      continue;
     }
     if (mode & kUpdate) {
       // Bests of iteration j - 1: this group's key and the run's Tbest key.
@@ -500,9 +584,9 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
     if (!(mode & kEval)) continue;
 
     // Fitness of iteration j, Pbest update (strictly better only).
-    int qdummy;
-    const float F = FN == 5   ? poly_row(srow, p.half, p.pts, sedges, E, p.alpha, p.beta, lane, qdummy)
-                    : FN == 6 ? sphere_row<true>(srow, p.half, p.pts, sedges, E, p.alpha, p.beta, lane, qdummy)
+    int qcount = 0;
+    const float F = FN == 5   ? poly_row(srow, p.half, p.pts, sedges, E, p.alpha, p.beta, lane, qcount)
+                    : FN == 6 ? sphere_row<true>(srow, p.half, p.pts, sedges, E, p.alpha, p.beta, lane, qcount)
                               : bf_row<FN>(srow, p.D, lane);
     unsigned npar = par;
     if (F < pf) {
@@ -513,6 +597,7 @@ __global__ void __launch_bounds__(256, 2) bf_iter_kernel(const BfParams p, int j
       if (lane == 0) {
         p.Pfit[q] = F;
         p.pcur[q] = (unsigned char)npar;
+        if (FN >= 5) p.pq[(size_t)npar * total + q] = qcount;
       }
     }
     if (lane == 0 && isfinite(pf)) atomicMin(&ck[r * p.G + g], make_key(pf, 1u, (uint32_t)pi, npar));
@@ -725,7 +810,7 @@ constexpr int kLaneMinPerSm = 256;   // particles per SM from which objective 5 
 constexpr long long kSmallMaxCoords = 8192;  // swarm size (G N D) up to which a run is one CTA
 
 __device__ __forceinline__ float poly_lane(const float* s, int T, const float* pts, const float4* edges, int E,
-                                           float alpha, int beta) {
+                                           float alpha, int beta, int& qout) {
   float len = 0.0f;
   int q = 0;
   for (int k = 0; k <= T; ++k) {
@@ -743,6 +828,7 @@ __device__ __forceinline__ float poly_lane(const float* s, int T, const float* p
       q += (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
     }
   }
+  qout = q;
   return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
 }
 
@@ -798,7 +884,7 @@ __device__ __forceinline__ int sphere_pair_hits(const Seg3P& g, ulonglong2 a, ul
 // Objective 6 of one lane's row (waypoint i = (s[i], s[T + i], s[2T + i])) against K
 // sphere pairs: the segments two at a time, each pair read once for both.
 __device__ __forceinline__ float sphere_lane(const float* s, int T, const float* pts, const ulonglong2* sp, int K,
-                                             float alpha, int beta) {
+                                             float alpha, int beta, int& qout) {
   float len = 0.0f;
   int q = 0;
   float ax = pts[0], ay = pts[1], az = pts[2];
@@ -827,6 +913,7 @@ __device__ __forceinline__ float sphere_lane(const float* s, int T, const float*
       for (int o = 0; o < K; ++o) q += sphere_pair_hits(f0, sp[2 * o], sp[2 * o + 1]);
     }
   }
+  qout = q;
   return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
 }
 
@@ -844,7 +931,8 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
   unsigned long long* ck = reinterpret_cast<unsigned long long*>(smem);
   unsigned long long* sgk = ck + RG;
   unsigned long long* stk = sgk + RG;
-  const size_t keys_b = ((size_t)(2 * RG + p.R) * 8 + 15) / 16 * 16;
+  int* sdone = reinterpret_cast<int*>(stk + p.R);
+  const size_t keys_b = bf_keys_bytes(RG, p.R);
   float4* sedges = reinterpret_cast<float4*>(smem + keys_b);
   const int E = p.E;
   // the warp's 32 rows (stride D + 1), and this lane's own
@@ -885,6 +973,10 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
     }
     __syncthreads();
   }
+  if (FN >= 5) {
+    at_decide(p, j, mode, stk, sdone);
+    __syncthreads();
+  }
 
   // A warp takes 32 consecutive particles; lane l evaluates particle qb + l.  Rows
   // move between global and shared memory one particle at a time over the lanes
@@ -898,12 +990,14 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
     int r = 0, pi = 0, g = 0;
     unsigned par = 0;
     float pf = INFINITY;
+    bool live = false;   // a particle of a run that has not stopped
     if (valid) {
       r = (int)(q / p.M);
       pi = (int)(q - (size_t)r * p.M);
       g = pi / p.N;
       par = p.pcur[q];
       pf = p.Pfit[q];
+      live = sdone[r] == 0;
     }
     if (mode & kUpdate) {
       // this lane's particle: inertia and random factors (one Philox draw)
@@ -921,7 +1015,7 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
       // kLaneBatch particles at a time, all their loads issued before any is used
       for (int t0 = 0; t0 < nv; t0 += kLaneBatch) {
         float wt[kLaneBatch], a1t[kLaneBatch], a2t[kLaneBatch], a3t[kLaneBatch], vl[kLaneBatch];
-        bool need_T[kLaneBatch];
+        bool need_T[kLaneBatch], move[kLaneBatch];
         const float *gr[kLaneBatch], *tr[kLaneBatch], *pr[kLaneBatch];
         float *xr[kLaneBatch], *vr[kLaneBatch], *st[kLaneBatch];
 #pragma unroll
@@ -933,6 +1027,7 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
           a3t[u] = __shfl_sync(full, a3, t);
           const int rt = __shfl_sync(full, r, t), gt = __shfl_sync(full, g, t);
           const unsigned part = __shfl_sync(full, par, t);
+          move[u] = t0 + u < nv && __shfl_sync(full, (int)live, t) != 0;
           const size_t qt = qb + t;
           const float* hy = p.hyper + ((size_t)rt * p.G + gt) * 6;
           need_T[u] = hy[2] != 0.0f;
@@ -959,7 +1054,7 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
           }
 #pragma unroll
           for (int u = 0; u < kLaneBatch; ++u) {
-            if (t0 + u < nv) {
+            if (move[u]) {
               const float bv = vl[u] * ext;
               float vv = wt[u] * v[u];
               vv = fmaf(a1t[u], pb[u] - x[u], vv);
@@ -991,17 +1086,19 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
     __syncwarp();
     if (mode & kEval) {
       float F = 0.0f;
-      if (valid)
-        F = FN == 5 ? poly_lane(srow, T, p.pts, sedges, E, p.alpha, p.beta)
+      int qcount = 0;
+      if (live)
+        F = FN == 5 ? poly_lane(srow, T, p.pts, sedges, E, p.alpha, p.beta, qcount)
                     : sphere_lane(srow, T, p.pts, reinterpret_cast<const ulonglong2*>(sedges), (E + 1) / 2, p.alpha,
-                                  p.beta);
-      const bool improved = valid && F < pf;
+                                  p.beta, qcount);
+      const bool improved = live && F < pf;
       unsigned npar = par;
       if (improved) {
         npar = par ^ 1u;
         pf = F;
         p.Pfit[q] = F;
         p.pcur[q] = (unsigned char)npar;
+        p.pq[(size_t)npar * total + q] = qcount;
       }
       // improved rows into their new Pbest buffer, one particle at a time over the lanes
       unsigned imask = __ballot_sync(full, improved);
@@ -1013,7 +1110,7 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
         const float* st = swarp + (size_t)t * (D + 1);
         for (int i = lane; i < D; i += 32) dst[i] = st[i];
       }
-      if (valid && isfinite(pf)) atomicMin(&ck[r * p.G + g], make_key(pf, 1u, (uint32_t)pi, npar));
+      if (live && isfinite(pf)) atomicMin(&ck[r * p.G + g], make_key(pf, 1u, (uint32_t)pi, npar));
     }
     __syncwarp();
   }
@@ -1131,7 +1228,7 @@ int bffail(int code, const char* fmt, ...) {
 size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct BfLayout {
-  size_t X, V, P, Pfit, pcur, keys, thold, hyper, ext, hist, Gb, Gfit, Tb, Tfit, edges, pts, warm, prevT, total;
+  size_t X, V, P, Pfit, pcur, keys, thold, hyper, ext, hist, Gb, Gfit, Tb, Tfit, edges, pts, warm, prevT, pq, at, total;
 };
 
 // Obstacle records a handle holds: polygon edges (objective 5) or spheres (6).
@@ -1169,6 +1266,8 @@ BfLayout bf_layout(const sepso_bf_config& c) {
   L.pts = take(32);
   L.warm = take(16);
   L.prevT = take(c.fn >= 5 ? R * Dp * 4 : 0);
+  L.pq = take(c.fn >= 5 ? 2 * RM * 4 : 0);
+  L.at = take(2 * R * 16);
   L.total = off;
   return L;
 }
@@ -1186,6 +1285,11 @@ int bf_validate(const sepso_bf_config* c) {
     if (c->max_spheres < 0 || c->max_spheres > kMaxSpheres)
       return bffail(SEPSO_EINVAL, "max_spheres=%d outside [0, %d]", c->max_spheres, kMaxSpheres);
   }
+  if (c->at_stall < 0) return bffail(SEPSO_EINVAL, "at_stall=%d is negative", c->at_stall);
+  if (c->at_stall > 0 && c->fn < 5)
+    return bffail(SEPSO_EINVAL, "Auto Truncation belongs to the path objectives (fn=%d)", c->fn);
+  if (c->at_stall > 0 && (!std::isfinite(c->stall_tol) || c->stall_tol < 0.0f))
+    return bffail(SEPSO_EINVAL, "stall_tol=%g", (double)c->stall_tol);
   if (c->fn == 5) {
     if (c->D < 2 || c->D % 2) return bffail(SEPSO_EINVAL, "a path needs an even D >= 2 (D=%d)", c->D);
     if (!(c->map_w > 0.0f) || !(c->map_h > 0.0f) || !std::isfinite(c->map_w) || !std::isfinite(c->map_h))
@@ -1322,7 +1426,7 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   const int Dp = padded(c->D);
   const int edge_b = obstacle_capacity(*c) * 16;
   const size_t RG = (size_t)c->runs * c->G;
-  const size_t keys_b = ((2 * RG + c->runs) * 8 + 15) / 16 * 16;
+  const size_t keys_b = bf_keys_bytes((int)RG, c->runs);
   const long long rows_budget = (long long)kSmemTotal - (long long)keys_b - edge_b;
   if (rows_budget < (long long)Dp * 4)
     return bffail(SEPSO_ERANGE, "D=%d with %d obstacle records and %zu group keys exceeds shared memory", c->D,
@@ -1436,6 +1540,10 @@ int sepso_bf_create(const sepso_bf_config* c, void* workspace, size_t bytes, voi
   p.pts = reinterpret_cast<const float*>(w + L.pts);
   p.warm = reinterpret_cast<const int*>(w + L.warm);
   p.prevT = reinterpret_cast<const float*>(w + L.prevT);
+  p.at_stall = c->at_stall;
+  p.stall_tol = c->stall_tol;
+  p.pq = reinterpret_cast<int*>(w + L.pq);
+  p.at_state = reinterpret_cast<int*>(w + L.at);
   e = cudaMemsetAsync(workspace, 0, L.total, h->stream);
   if (e != cudaSuccess) {
     delete h;
@@ -1647,8 +1755,12 @@ int sepso_bf_read(sepso_bf_handle h, int32_t run, float* best_x, float* best_fit
     BFCUDA(cudaMemcpyAsync(best_x, h->p.Tb + (size_t)run * h->p.Dp, (size_t)h->c.D * 4, cudaMemcpyDeviceToHost,
                            h->stream));
   if (best_fit) BFCUDA(cudaMemcpyAsync(best_fit, h->p.Tfit + run, 4, cudaMemcpyDeviceToHost, h->stream));
+  int32_t st[4] = {0, 0, 0, 0};
+  if (h->c.at_stall > 0)   // the state the last whole launch (k + 1) left
+    BFCUDA(cudaMemcpyAsync(st, h->p.at_state + ((size_t)((h->k + 1) % 2) * h->c.runs + run) * 4, 16,
+                           cudaMemcpyDeviceToHost, h->stream));
   BFCUDA(cudaStreamSynchronize(h->stream));
-  if (iters) *iters = (int32_t)h->k;
+  if (iters) *iters = st[2] ? st[3] : (int32_t)h->k;
   return SEPSO_OK;
 }
 
@@ -1758,6 +1870,13 @@ int sepso_bf_set_state(sepso_bf_handle h, int32_t run, const float* X, const flo
                          cudaMemcpyHostToDevice, s));
   BFCUDA(cudaMemcpyAsync(p.thold + run, &tk, 8, cudaMemcpyHostToDevice, s));
   BFCUDA(cudaMemcpyAsync(p.thold + (size_t)p.R + run, &tk, 8, cudaMemcpyHostToDevice, s));
+  if (h->c.at_stall > 0) {   // a loaded state starts with no stall and no stop
+    float inf = INFINITY;
+    int32_t fresh[4] = {0, 0, 0, 0};
+    std::memcpy(&fresh[1], &inf, 4);
+    for (int slot = 0; slot < 2; ++slot)
+      BFCUDA(cudaMemcpyAsync(p.at_state + ((size_t)slot * p.R + run) * 4, fresh, 16, cudaMemcpyHostToDevice, s));
+  }
   h->k = k;
   BFCUDA(launch_finish(h, k));
   BFCUDA(cudaStreamSynchronize(s));

@@ -352,6 +352,11 @@ class BFConfig:
     # 3.3.3), ceil(pi_gamma N) particles per group within +-pi_halfwidth of it
     pi_gamma: float = 0.0
     pi_halfwidth: float = 20.0
+    # path objectives: Auto Truncation by stall counter (Sec. 3.3.4): stop after
+    # at_stall iterations without an improvement of Tbest by more than stall_tol while
+    # Tbest collides with nothing (0: off)
+    at_stall: int = 0
+    stall_tol: float = 0.0
 
     def with_(self, **kw) -> "BFConfig":
         return replace(self, **kw)
@@ -417,7 +422,8 @@ def polygon_workload(seed: int = 0, T: int = 8, N: int = 170, n_boxes: int = 12,
 
 
 def sphere_workload(seed: int = 0, T: int = 16, N: int = 170, S: int = 64, n_moving: int = 32,
-                    iters: int = 100, runs: int = 1, pi_gamma: float = 0.25):
+                    iters: int = 100, runs: int = 1, pi_gamma: float = 0.25, at_stall: int = 0,
+                    stall_tol: float = 1.0):
     """Path planning in three dimensions among spheres (the paper's Conclusion names
     the extension from 2D to 3D planning): a 400^3 box, start (20, 20, 20), target
     (380, 380, 380), ``S`` spheres with centres U[60, 340]^3 and radii U[10, 30] (the
@@ -426,7 +432,9 @@ def sphere_workload(seed: int = 0, T: int = 16, N: int = 170, S: int = 64, n_mov
     G = 8 x N with the Table hyper8path rows, alpha = 30, beta = 4 (Table params_path),
     ``iters`` iterations per plan, ``runs`` independent swarms (Philox runs) on the
     same scene, PI with ``pi_gamma`` and a half-width of 20 once a run has a previous
-    path -> (config, scene dict: start, target, spheres (S, 4), vel (S, 3); hyper)."""
+    path, Auto Truncation by a stall counter of ``at_stall`` iterations (tolerance
+    ``stall_tol``; 0: ``iters`` iterations) -> (config, scene dict: start, target,
+    spheres (S, 4), vel (S, 3); hyper)."""
     rng = np.random.default_rng(8000 + seed)
     sph = np.empty((S, 4), np.float32)
     sph[:, :3] = rng.uniform(60.0, 340.0, (S, 3))
@@ -439,7 +447,8 @@ def sphere_workload(seed: int = 0, T: int = 16, N: int = 170, S: int = 64, n_mov
         vel[S - m:] = d * rng.uniform(0.5, 2.0, (m, 1))
     cfg = BFConfig(fn=SPHERE_PATH, D=3 * T, G=8, N=N, lo=0.0, hi=400.0, max_iters=iters, seed=seed, runs=runs,
                    map_w=400.0, map_h=400.0, map_d=400.0, alpha=PARAMS_PATH["alpha"], beta=PARAMS_PATH["beta"],
-                   max_spheres=max(S, 1), pi_gamma=pi_gamma, pi_halfwidth=20.0)
+                   max_spheres=max(S, 1), pi_gamma=pi_gamma, pi_halfwidth=20.0, at_stall=at_stall,
+                   stall_tol=stall_tol)
     scene = {"start": np.array([20.0, 20.0, 20.0], np.float32),
              "target": np.array([380.0, 380.0, 380.0], np.float32), "spheres": sph, "vel": vel}
     return cfg, scene, np.ascontiguousarray(TABLE_HYPER8_PATH, dtype=np.float32)

@@ -334,14 +334,15 @@ class BFPlanner:
         check_bf(self.lib.sepso_bf_set_warm_start(self._h, pv.ctypes.data, ctypes.c_float(self.cfg.pi_gamma),
                                                   ctypes.c_float(self.cfg.pi_halfwidth), int(cycle)))
 
-    def read_all(self) -> np.ndarray:
-        """Tbest rows of every run (runs, D) and their fitness (runs,)."""
+    def read_all(self):
+        """Tbest rows of every run (runs, D), their fitness (runs,) and iteration
+        counts (runs,; with Auto Truncation, each run's stopping iteration)."""
         R, D = self.cfg.runs, self.cfg.D
-        out, fit = np.zeros((R, D), np.float32), np.zeros(R, np.float32)
+        out, fit, its = np.zeros((R, D), np.float32), np.zeros(R, np.float32), np.zeros(R, np.int32)
         for r in range(R):
             res = self.read(r)
-            out[r], fit[r] = res["x"], res["fit"]
-        return out, fit
+            out[r], fit[r], its[r] = res["x"], res["fit"], res["iters"]
+        return out, fit, its
 
     def run_async(self, use_graph: bool = True):
         check_bf(self.lib.sepso_bf_run_async(self._h, int(use_graph)))

@@ -211,7 +211,8 @@ def test_bf_workspace_size_and_bad_configs():
     for bad in (dict(fn=5, D=15), dict(fn=5, beta=0), dict(fn=5, beta=9), dict(fn=5, max_edges=4097),
                 dict(fn=5, map_w=0.0), dict(fn=5, alpha=-1.0), dict(fn=6, D=31), dict(fn=6, D=2),
                 dict(fn=6, map_d=0.0), dict(fn=6, map_d=float("inf")), dict(fn=6, max_spheres=4097),
-                dict(fn=6, beta=0), dict(fn=7), dict(fn=0), dict(D=0), dict(D=16385), dict(G=0), dict(G=33), dict(N=0),
+                dict(fn=6, beta=0), dict(fn=6, at_stall=-1), dict(fn=6, at_stall=5, stall_tol=-1.0),
+                dict(fn=6, at_stall=5, stall_tol=float("nan")), dict(fn=1, at_stall=5), dict(fn=7), dict(fn=0), dict(D=0), dict(D=16385), dict(G=0), dict(G=33), dict(N=0),
                 dict(runs=0), dict(max_iters=0), dict(lo=1.0, hi=1.0), dict(lo=float("nan")),
                 dict(hi=float("inf")), dict(runs=600, G=8)):
         assert size(**bad)[0] == -1, bad

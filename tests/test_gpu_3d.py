@@ -205,7 +205,7 @@ def test_dynamic_cycles_match_oracle_statistically(native):
         pl.set_spheres(sc["start"], sc["target"], sph)
         pl.set_warm_start(prev_g, cycle=cycle)
         pl.run_async()
-        prev_g, gfit = pl.read_all()
+        prev_g, gfit, _ = pl.read_all()
         ofit, prev_o_new = [], []
         for r, sw in enumerate(swarms):
             sw.set_scene(scene)
@@ -261,3 +261,102 @@ def test_errors(native):
     with pytest.raises(RuntimeError, match="objective 6"):
         BFPlanner(pcfg).set_spheres(sc["start"], sc["target"], sc["spheres"])
     assert _native.lib() is not None
+
+
+def _oracle_plan_clear(cfg, s3, hy, margin_fn):
+    """The oracle's planning cycle with Auto Truncation, or None when a position it
+    evaluated came within the margin of a flipping collision decision."""
+    sw = oracle.BFSwarm(cfg, hy, s3)
+    sw.s["stall"][0] = 0
+    sw.s["prev_lfv"][0] = np.inf
+    sw.init()
+    for _ in range(cfg.max_iters):
+        if not margin_fn(sw.s["X"]):
+            return None
+        if sw.iteration_stop():
+            break
+    return sw
+
+
+@pytest.mark.parametrize("runs,S", [(4, 48), (32, 4)])
+def test_auto_truncation_stop_matches_oracle(native, runs, S):
+    """Stall limit 1, unreachable tolerance: a run stops at the first iteration after
+    the first whose Tbest collides with nothing.  The stopping iteration, the bests
+    and the positions it evaluated (nothing moves after it) vs the oracle, on the
+    runs whose evaluations stay clear of tangency; warp kernel (4 runs of 3 x 12) and
+    lane kernel (32 runs of 8 x 170)."""
+    if runs == 4:
+        cfg, sc, hy = sphere_workload(6, T=6, N=12, S=S, iters=40, runs=runs)
+        cfg, hy = cfg.with_(G=3), np.array(hy[:3])
+    else:
+        cfg, sc, hy = sphere_workload(7, T=6, S=S, iters=40, runs=runs)
+    cfg = cfg.with_(at_stall=1, stall_tol=1e30)
+    pl = BFPlanner(cfg)
+    assert pl.kernel_name() == ("bf_iter_kernel<6>" if runs == 4 else "sphere_lane_kernel")
+    pl.set_hyper(hy)
+    pl.set_spheres(sc["start"], sc["target"], sc["spheres"])
+    pl.run_async()
+    s3 = _scene(sc)
+    checked = early = 0
+    for r in range(runs):
+        sw = _oracle_plan_clear(cfg.with_(runs=1, run_id=r), s3, hy, lambda X: _margins_ok(cfg, s3, X))
+        if sw is None:
+            continue
+        checked += 1
+        got = pl.read(r)
+        assert got["iters"] == int(sw.s["k"][0]), r
+        early += got["iters"] < cfg.max_iters
+        st = pl.get_state(r)
+        _close(st["X"], sw.s["X"], 400.0)
+        _close(st["Tb"], sw.s["Tb"], 400.0)
+        assert st["Tfit"][0] == pytest.approx(sw.s["Tfit"][0], rel=1e-5)
+    assert checked >= 2 and early >= 1
+
+
+def test_auto_truncation_matches_oracle_statistically(native):
+    """Stall limit 10, tolerance 1 (the dynamic workload's reading): over 16 runs the
+    median stopping iteration within 15% + 1 and the median cost within 5% of the
+    oracle's."""
+    cfg, sc, hy = sphere_workload(8, T=8, N=40, iters=100, runs=16, at_stall=10, stall_tol=1.0)
+    pl = BFPlanner(cfg)
+    pl.set_hyper(hy)
+    pl.set_spheres(sc["start"], sc["target"], sc["spheres"])
+    pl.run_async()
+    g_it, g_cost, o_it, o_cost = [], [], [], []
+    s3 = _scene(sc)
+    for r in range(16):
+        got = pl.read(r)
+        g_it.append(got["iters"])
+        g_cost.append(got["fit"])
+        res = oracle.BFSwarm(cfg.with_(runs=1, run_id=r), hy, s3).plan()
+        o_it.append(res["iters"])
+        o_cost.append(res["cost"])
+    assert min(o_it) < cfg.max_iters            # AT acts on this scene
+    assert abs(np.median(g_it) - np.median(o_it)) <= 0.15 * np.median(o_it) + 1, (g_it, o_it)
+    assert abs(np.median(g_cost) - np.median(o_cost)) <= 0.05 * np.median(o_cost)
+
+
+def test_polygon_auto_truncation_stop_matches_oracle(native):
+    """The same stop rule on objective 5 (paths among polygons)."""
+    from paper_2308_10169_gb300.inputs import polygon_workload
+    cfg, start, target, polys, edges, hy = polygon_workload(2, N=12, iters=40, runs=4)
+    cfg = cfg.with_(G=3, at_stall=1, stall_tol=1e30)
+    hy = np.array(hy[:3])
+    pl = BFPlanner(cfg)
+    pl.set_hyper(hy)
+    pl.set_polygons(start, target, edges)
+    pl.run_async()
+    sc = oracle.Scene(start, target, np.zeros((0, 3)), edges)
+    checked = 0
+    for r in range(4):
+        c1 = cfg.with_(runs=1, run_id=r)
+        sw = _oracle_plan_clear(c1, sc, hy, lambda X: np.all(oracle.poly_margin(c1, sc, X.reshape(-1, c1.D)) > 1e-6))
+        if sw is None:
+            continue
+        checked += 1
+        got = pl.read(r)
+        assert got["iters"] == int(sw.s["k"][0])
+        st = pl.get_state(r)
+        _close(st["X"], sw.s["X"], 400.0)
+        assert st["Tfit"][0] == pytest.approx(sw.s["Tfit"][0], rel=1e-5)
+    assert checked >= 2

@@ -186,3 +186,47 @@ def test_priori_initialization_in_3d():
     assert n_pi == 5
     near = np.all(np.abs(X - prev[None, None]) <= 20.0 + 1e-9, axis=2)
     assert near[:, :n_pi].all() and not near[:, n_pi:].any()
+
+
+def test_auto_truncation_stops_at_the_first_collision_free_tbest():
+    """With a stall limit of 1 and an unreachable improvement tolerance, Auto
+    Truncation (Sec. 3.3.4, stall reading) fires at the first iteration after the
+    first (whose Tbest always improves on none) in which Tbest collides with nothing:
+    the iteration found by stepping without AT and reading Q(Tbest) after each
+    iteration.  The planned state is that iteration's: its bests, and the positions it
+    evaluated (no particle moved after it)."""
+    stopped = 0
+    for seed in range(4):
+        cfg, sc, hy = sphere_workload(seed, T=6, N=12, S=48, iters=40)
+        cfg = cfg.with_(G=3, at_stall=1, stall_tol=1e30)
+        scene = oracle.Scene3(sc["start"], sc["target"], sc["spheres"])
+        ref = oracle.BFSwarm(cfg.with_(at_stall=0), hy[:3], scene)
+        ref.init()
+        want, X_eval, Tb = cfg.max_iters, None, None
+        for k in range(1, cfg.max_iters + 1):
+            Xk = ref.s["X"].copy()
+            ref.iteration()
+            if k >= 2 and ref.s["TQ"][0] == 0:
+                want, X_eval, Tb = k, Xk, ref.s["Tb"].copy()
+                break
+        res = oracle.BFSwarm(cfg, hy[:3], scene).plan()
+        assert res["iters"] == want
+        if X_eval is not None:
+            stopped += 1
+            sw = oracle.BFSwarm(cfg, hy[:3], scene)
+            res = sw.plan()
+            assert res["Q"] == 0
+            np.testing.assert_array_equal(sw.s["X"], X_eval)
+            np.testing.assert_array_equal(sw.s["Tb"], Tb)
+    assert stopped >= 2
+
+
+def test_auto_truncation_needs_a_collision_free_tbest():
+    """A scene whose target sits inside a sphere: every path collides, so the stall
+    counter alone never stops a run and it reaches the cap."""
+    cfg, sc, hy = sphere_workload(0, T=4, N=10, S=8, iters=25)
+    cfg = cfg.with_(G=2, at_stall=2, stall_tol=1e30)
+    sph = sc["spheres"].copy()
+    sph[0] = (380.0, 380.0, 380.0, 15.0)
+    res = oracle.BFSwarm(cfg, hy[:2], oracle.Scene3(sc["start"], sc["target"], sph)).plan()
+    assert res["iters"] == cfg.max_iters and res["Q"] > 0
