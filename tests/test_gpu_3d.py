@@ -140,12 +140,14 @@ def test_warm_start_matches_oracle(native):
         np.testing.assert_array_equal(pl.read(r)["x"], cold.read(r)["x"])
 
 
-def test_lane_per_particle_kernel_matches_oracle(native):
+@pytest.mark.parametrize("S", [4, 5])
+def test_lane_per_particle_kernel_matches_oracle(native, S):
     # 32 plans x 8 x 170 particles: the lane-per-particle kernel; two iterations of
     # the plans whose evaluated positions stay clear of tangency, cold and warm.  Four
-    # spheres, so that a good share of the 1360-particle plans keeps every one of its
-    # evaluations more than 1e-3 from tangency.
-    cfg, sc, hy = sphere_workload(4, iters=2, runs=32, S=4)
+    # or five spheres (an odd count exercises the pair staging's padding), so that a
+    # good share of the 1360-particle plans keeps every one of its evaluations more
+    # than 1e-3 from tangency.
+    cfg, sc, hy = sphere_workload(4, iters=2, runs=32, S=S)
     pl = BFPlanner(cfg)
     assert pl.kernel_name() == "sphere_lane_kernel"
     assert BFPlanner(cfg.with_(runs=1)).kernel_name() == "bf_iter_kernel<6>"
