@@ -1398,11 +1398,17 @@ def cost_match_dynamic(seeds: int = 64, cycles: int = 2):
         gm, om = float(np.median(gc)), float(np.median(oc))
         # the spread of the two medians over the seeds: a bootstrap of both samples
         boot = [(np.median(rng.choice(gc, gc.size)) - np.median(rng.choice(oc, oc.size))) / om for _ in range(2000)]
+        # the same Philox key on both sides: the per-key differences pair the samples
+        d = (gc - oc) / oc
+        gq, oq = np.array([x[2] for x in g]), np.array([x[2] for x in o])
         per.append({"cycle": cyc,
                     "gpu": plan_stats([x[1] for x in g], [x[0] for x in g], [x[2] for x in g], cfg.max_iters),
                     "oracle": plan_stats([x[1] for x in o], [x[0] for x in o], [x[2] for x in o], cfg.max_iters),
                     "rel_diff_median_cost": (gm - om) / om,
-                    "rel_diff_bootstrap_95": [float(np.percentile(boot, 2.5)), float(np.percentile(boot, 97.5))]})
+                    "rel_diff_bootstrap_95": [float(np.percentile(boot, 2.5)), float(np.percentile(boot, 97.5))],
+                    "paired": {"median_rel_diff": float(np.median(d)),
+                               "share_within_1pct": float(np.mean(np.abs(d) <= 0.01)),
+                               "share_same_collision_outcome": float(np.mean((gq == 0) == (oq == 0)))}})
     return {"workload": "the headline dynamic run's first cycles, shared hyper-parameters",
             "seeds": seeds, "cycles": per, "gpu_seconds": t_gpu,
             "oracle_seconds": t_ora, "oracle_processes": P}
