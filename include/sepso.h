@@ -438,8 +438,10 @@ int sepso_server_set_hyper(sepso_server_handle h, int32_t agent, const float* hy
  * particles, when its fitness (Sec. 3.3.2, FP32) on the request's scene is below
  * that of the agent's previous path, or the agent has none -- the gate of
  * sepso_batch_set_starts.  All of it runs on the device: the rasteriser and the
- * network on a side stream of the server, beside the tick that is running, the
- * resampling and the gate on the server's stream before the next tick.  The prior
+ * network on a side stream of the server, beside the tick that is running and the
+ * next one, the resampling and the gate on the server's stream in the next tick;
+ * a request admitted with a prior attached therefore starts one tick later than
+ * without (its first iteration is the second launch after its admission).  The prior
  * must have been created on the server's stream and map, with max_circles >= Omax,
  * T_p <= 64 and capacity >= first_row + S; it must outlive its attachment, and the
  * caller must not use it while it is attached.  The server does not train it.

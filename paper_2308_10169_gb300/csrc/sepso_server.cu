@@ -300,6 +300,12 @@ struct sepso_server_ctx {
   // ev_prop before the seed / gate kernel
   cudaStream_t pside = nullptr;
   cudaEvent_t ev_tick = nullptr, ev_prop = nullptr;
+  // The seeds of a tick's admissions are applied in the next tick, after that tick's
+  // batch launch: the proposals then run beside it instead of holding up the main
+  // stream, and the admitted slots start one tick later.  Pending: the tick parity
+  // of the admissions, their number and the proposals' waypoint count.
+  bool seed_pending = false;
+  int seed_b = 0, seed_n = 0, seed_T = 0;
   float4* h_rcirc[2] = {nullptr, nullptr};
   int* h_rcoff[2] = {nullptr, nullptr};
   float* h_rpts[2] = {nullptr, nullptr};
@@ -391,8 +397,29 @@ void retire(sepso_server_ctx* h, int b) {
   }
 }
 
+// The previous tick's seeds (resampling and gate of each admitted slot's proposal),
+// on the main stream once its proposals are done; the admissions' descriptors are
+// still in the device buffer (this tick's upload comes after).
+int flush_seeds(sepso_server_ctx* h) {
+  if (!h->seed_pending) return SEPSO_OK;
+  h->seed_pending = false;
+  float* praw = h->at<float>(h->L.praw) + (size_t)h->seed_b * h->S * 2 * kPriorMaxT;
+  SCUDA(cudaStreamWaitEvent(h->stream, h->ev_prop, 0));
+  server_prior_kernel<<<h->seed_n, 32, 0, h->stream>>>(h->params(), h->at<Admit>(h->L.admits), h->seed_n, praw,
+                                                         h->seed_T);
+  SCUDA(cudaGetLastError());
+  ++h->launches;
+  return SEPSO_OK;
+}
+
 int admit(sepso_server_ctx* h, int b) {
   const sepso_server_config& c = h->cfg;
+  {
+    const int rc = flush_seeds(h);
+    if (rc) return rc;
+  }
+  // with a prior, a slot's first iteration waits one more tick for its seed
+  const int defer = h->prior ? 1 : 0;
   int n = 0, c0 = 0, rc0 = 0;
   size_t free_slot = 0;
   const double now = now_s(h->t0);
@@ -431,7 +458,7 @@ int admit(sepso_server_ctx* h, int b) {
     d.ho = (long long)r.agent * c.G * 6;
     d.wo = (long long)i * 3 * c.G;
     d.gso = (long long)i * 2 * c.G;
-    d.j0 = (int)h->tick;  // its first iteration is the next launch
+    d.j0 = (int)h->tick + defer;  // its first iteration is the next launch (with a prior, the one after)
     d.at_stall = c.stall_iters;
     d.stall_tol = c.stall_tol;
     d.n_pi = (int)std::min<double>(std::max(std::ceil((double)c.pi_gamma * c.N), 0.0), (double)c.N);
@@ -471,7 +498,7 @@ int admit(sepso_server_ctx* h, int b) {
     sl.T = r.T;
     sl.O = r.O;
     sl.tag = r.tag;
-    sl.start_tick = h->tick + 1;
+    sl.start_tick = h->tick + 1 + defer;
     sl.arrival = r.arrival;
     h->agent_busy[r.agent] = 1;
     ++n;
@@ -491,8 +518,8 @@ int admit(sepso_server_ctx* h, int b) {
   ++h->launches;
   if (h->prior) {
     // The prior's proposals for the admitted scenes on the side stream, beside the
-    // running tick (they touch only the prior's rows and this parity's staging);
-    // then, on the main stream, each slot's seed row and gate.
+    // running tick and the next one (they touch only the prior's rows and this
+    // parity's staging); each slot's seed row and gate follow in the next tick.
     h->h_rcoff[b][n] = rc0;
     const cudaStream_t ps = h->pside;
     float* praw = h->at<float>(h->L.praw) + (size_t)b * h->S * 2 * kPriorMaxT;
@@ -508,10 +535,10 @@ int admit(sepso_server_ctx* h, int b) {
     if (rc) return sfail(rc, "learned prior: %s", sepso_prior_last_error());
     h->launches += sepso_prior_launch_count(h->prior) - l0;
     SCUDA(cudaEventRecord(h->ev_prop, ps));
-    SCUDA(cudaStreamWaitEvent(h->stream, h->ev_prop, 0));
-    server_prior_kernel<<<n, 32, 0, h->stream>>>(h->params(), h->at<Admit>(h->L.admits), n, praw, h->prior_T);
-    SCUDA(cudaGetLastError());
-    ++h->launches;
+    h->seed_pending = true;
+    h->seed_b = b;
+    h->seed_n = n;
+    h->seed_T = h->prior_T;
   }
   return SEPSO_OK;
 }
@@ -630,6 +657,10 @@ int sepso_server_set_hyper(sepso_server_handle h, int32_t agent, const float* hy
 
 int sepso_server_set_prior(sepso_server_handle h, sepso_prior_handle prior, int32_t n_prior, int32_t first_row) {
   if (!h) return sfail(SEPSO_EINVAL, "NULL handle");
+  {
+    const int rc = flush_seeds(h);  // seeds of admissions made under the previous setting
+    if (rc) return rc;
+  }
   if (!prior) {
     h->prior = nullptr;
     h->n_prior = 0;
