@@ -665,7 +665,46 @@ def run_batch(n: int, iters: int):
                                           for lo, hi in ((0, 64), (64, 256), (256, 1024))},
             "quality_note": "radii U[5,30] (the configuration's) with up to 1024 circles on 400x400: "
                             "the dense scenes admit no collision-free path",
-            "l2": f"inputs larger than L2 ({bp.workspace.numel() / 1e9:.1f} GB of batch state)"}
+            "l2": f"inputs larger than L2 ({bp.workspace.numel() / 1e9:.1f} GB of batch state)",
+            "cpu_baseline": batch_oracle_baseline(specs, hyper, points, circles, n / (ms / 1e3),
+                                                  pairs / n)}
+
+
+def _batch_oracle_worker(args):
+    """One sampled scene of the batch on the oracle: initialisation and one
+    iteration (Algorithm 1), timed; returns (seconds, pair tests of the iteration)."""
+    import oracle
+    spec, hyper, pts, circ = args
+    sw = oracle.Swarm(spec.config(), hyper)
+    scene = oracle.Scene(pts[:2], pts[2:], circ)
+    sw.init()
+    t0 = time.perf_counter()
+    sw.iteration(scene)
+    return time.perf_counter() - t0, spec.G * spec.N * (spec.T + 1) * spec.O
+
+
+def batch_oracle_baseline(specs, hyper, points, circles, gpu_plans_per_s: float, pairs_per_plan: float,
+                          sample: int = 64):
+    """The FP64 oracle on the batched workload, on every host core: one iteration of
+    each of ``sample`` scenes spread over the batch (every n/sample-th), timed in a
+    spawned process pool; the batch's plans/s is extrapolated from the pair tests per
+    second the oracle sustained and the batch's pair tests per plan."""
+    import multiprocessing as mp
+    n = len(specs)
+    idx = [int(i * n / sample) for i in range(sample)]
+    P = min(host_cores(), sample)
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(P) as pool:
+        res = pool.map(_batch_oracle_worker, [(specs[i], hyper[i], points[i], circles[i]) for i in idx], chunksize=1)
+    wall = time.perf_counter() - t0
+    pairs = sum(r[1] for r in res)
+    busy = sum(r[0] for r in res)
+    rate = pairs / busy * P   # pair tests per second on P cores, each process busy
+    value = rate / pairs_per_plan
+    return {"value": value, "unit": UNIT, "cores": P, "kind": "oracle",
+            "sample": f"one iteration of each of {sample} scenes spread over the batch, FP64, one process per core; "
+                      f"extrapolated to whole plans by pair-test count ({pairs_per_plan:.3g} per plan)",
+            "pair_tests_per_s": rate, "sample_wall_s": wall, "gpu_vs_oracle": gpu_plans_per_s / value}
 
 
 def run_paper(frames: int = 100, seed: int = 0):
