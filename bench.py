@@ -928,6 +928,7 @@ def run_bf(fns, iters: int, trials: int, peak_gbs: float):
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s",
                          "frac": gbs / peak_gbs, "kernel": "bf_iter_kernel",
                          "bytes_per_iteration": algo,
+                         "traffic": BF_SPHERE_TRAFFIC_BYTES if fn == 1 else None,
                          "note": "20 B per coordinate; Pbest rows written on improvement not counted"},
             "gpu_launches": pl.launch_count() - l0,
             "paper_dtpso_gpu_s": paper_large[fn]}
@@ -1011,6 +1012,8 @@ FLOPS_PER_PAIR_3D, FLOPS_PER_SEGMENT_3D = 24, 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one sphere_lane_kernel launch of the
 # 64-plan batch (profiles/sphere_lane_kernel_3d_batch.md).
 SPHERE_LANE_TRAFFIC_BYTES = 54078464
+# The same for bf_iter_kernel<1>, large-scale Sphere (profiles/bf_iter_kernel_large_sphere.md).
+BF_SPHERE_TRAFFIC_BYTES = 302956544
 
 
 def run_plan3d(runs: int = 64, iters: int = 100, cycles: int = 20):
