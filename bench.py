@@ -604,7 +604,7 @@ def run_e2e(torch, pl_dev, cfg, scene, hyper, dev, K, W):
     lat = []
 
     def one(i):
-        pl.set_scene(Scene(start=pn[i, :2], target=pn[i, 2:], circles=cn[i]), motion=False)
+        pl.set_scene_arrays(pn[i, :2], pn[i, 2:], cn[i])
         pl.plan_into(wp)
 
     for i in range(W):

@@ -91,6 +91,15 @@ class Planner:
                                         ctypes.byref(self._h)))
         self.D = 2 * cfg.T
         self.O = 0
+        # host buffers of the per-cycle calls (set_scene_arrays, plan_into) and their
+        # pointers, made once
+        self._st = np.zeros(2, np.float32)
+        self._tg = np.zeros(2, np.float32)
+        self._ci = np.zeros((max(cfg.max_obstacles, 1), 3), np.float32)
+        self._pst, self._ptg, self._pci = fptr(self._st), fptr(self._tg), fptr(self._ci)
+        self._res = Result()
+        self._pres = ctypes.byref(self._res)
+        self._wp_addr, self._pwp = None, None
 
     # -- lifetime ---------------------------------------------------------
     def close(self):
@@ -122,6 +131,19 @@ class Planner:
             cv = _f32(scene.circle_vel, (-1, 2))
             check(self.lib.sepso_set_motion(self._h, fptr(cv) if cv.size else None,
                                             fptr(_f32(scene.start_vel)), fptr(_f32(scene.target_vel))))
+
+    def set_scene_arrays(self, start, target, circles):
+        """The per-cycle form of set_scene for a caller that holds plain arrays: start
+        (2,), target (2,), circles (O, 3) (cx, cy, r) are copied into host buffers the
+        planner keeps, then sepso_set_scene uploads them; the velocities stay as they
+        are."""
+        O = len(circles)
+        self._st[:] = start
+        self._tg[:] = target
+        if O:
+            self._ci[:O] = circles
+        check(self.lib.sepso_set_scene(self._h, self._pst, self._ptg, self._pci if O else None, O))
+        self.O = O
 
     def set_polygons(self, scene, motion: bool = True):
         """A scene among polygon obstacles (a handle with obstacle_kind = 1):
@@ -172,10 +194,15 @@ class Planner:
         return self.read_result(0)
 
     def plan_into(self, waypoints: np.ndarray) -> Result:
-        """One synchronous planning cycle writing into a caller-owned host array."""
-        res = Result()
-        check(self.lib.sepso_plan(self._h, fptr(waypoints), ctypes.byref(res)))
-        return res
+        """One synchronous planning cycle writing into a caller-owned host float32
+        array of 2T waypoints; returns the planner's result record (overwritten by the
+        next call)."""
+        addr = waypoints.ctypes.data
+        if addr != self._wp_addr:
+            assert waypoints.dtype == np.float32 and waypoints.flags.c_contiguous and waypoints.size >= self.D
+            self._wp_addr, self._pwp = addr, fptr(waypoints)
+        check(self.lib.sepso_plan(self._h, self._pwp, self._pres))
+        return self._res
 
     def result_device(self, run: int = 0):
         wp, rr = ctypes.c_void_p(), ctypes.c_void_p()

@@ -605,3 +605,25 @@ def test_device_philox_bit_exact_on_a_million_counters(native):
         want = oracle.philox(ctr, seed)
         bad = np.nonzero(np.any(got != want, axis=1))[0]
         assert bad.size == 0, (seed, bad[:5])
+
+
+def test_per_cycle_calls_equal_the_scene_calls(native):
+    # set_scene_arrays + plan_into (reused host buffers) against set_scene + plan on
+    # the same sequence of scenes: identical plans, cycle after cycle, also when the
+    # circle count changes
+    from paper_2308_10169_gb300.inputs import dynamic_workload
+    cfg, scene, hyper = dynamic_workload(3)
+    a, b = Planner(cfg), Planner(cfg)
+    for pl in (a, b):
+        pl.set_hyper(hyper)
+    wp = np.zeros(cfg.D, np.float32)
+    rng = np.random.default_rng(4)
+    for k in range(4):
+        O = scene.O - 8 * k
+        circ = scene.circles[:O] + rng.uniform(-2, 2, (O, 3)).astype(np.float32) * np.array([1, 1, 0], np.float32)
+        a.set_scene(Scene(start=scene.start, target=scene.target, circles=circ), motion=False)
+        ra = a.plan()
+        b.set_scene_arrays(scene.start, scene.target, circ)
+        rb = b.plan_into(wp)
+        assert ra["cost"] == rb.cost and ra["iters"] == rb.iters and ra["Q"] == rb.Q
+        np.testing.assert_array_equal(ra["waypoints"], wp)
