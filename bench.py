@@ -574,6 +574,10 @@ def run_ours(args, rank, world, local):
             "clocks": clocks,
             "hsef": hsef_info,
             "wall_s_timed_loop": t_wall,
+            "paper_context": {"plans_per_s": 67, "s_per_plan": 0.015,
+                              "note": "the paper's SEPSO on an i9-10850K + RTX 2070 SUPER, 8 box obstacles, "
+                                      "8 waypoints, its own (unpublished) scene: another workload and machine, "
+                                      "context only (vs_baseline stays null)"},
         }
     return line
 
