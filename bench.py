@@ -415,7 +415,7 @@ def run_ours(args, rank, world, local):
     import torch.distributed as dist
 
     from paper_2308_10169_gb300 import Planner
-    from paper_2308_10169_gb300.inputs import (HSEF_BOX_HI, HSEF_BOX_LO, TABLE_HYPER8,
+    from paper_2308_10169_gb300.inputs import (HSEF_BOX_HI, HSEF_BOX_LO, TABLE_HYPER8, Scene,
                                                dynamic_workload)
 
     torch.cuda.set_device(local)
@@ -537,6 +537,34 @@ def run_ours(args, rank, world, local):
                        "launch": fp.launch_shape()}
         del fp
 
+    # -- the planning kernel's per-iteration floor: fixed-length launches (200
+    # iterations each) of the same swarm with the scene's circles and with none (no
+    # pair test at all), so that the time the exchange takes shows beside the fitness
+    floor = {}
+    try:
+        fl = Planner(cfg.with_(exchange=2 if shape["exchange"] == "cluster" else 1), device=dev)
+        fl.set_hyper(app_hyper)
+        for label, sc in (("with_circles", scene),
+                          ("no_obstacles", Scene(start=scene.start, target=scene.target,
+                                                 circles=np.zeros((0, 3), np.float32)))):
+            fl.set_scene(sc, motion=False)
+            fl.plan()
+            for _ in range(3):
+                fl.step(200)
+            fl.sync()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(10):
+                fl.step(200)
+            f1.record(stream)
+            fl.sync()
+            floor[label] = 1e3 * f0.elapsed_time(f1) / 2000
+        floor["note"] = ("us per iteration in fixed-length launches of 200 iterations; the difference is what "
+                         "the pair tests cost, the rest is the per-iteration exchange")
+        del fl
+    except Exception as e:
+        floor = {"error": str(e)[:120]}
+
     # -- end to end through the C ABI with host buffers ----------------------------
     Ke = args.e2e_steps or K
     e2e = run_e2e(torch, pl, cfg, scene, app_hyper, dev, Ke, W)
@@ -570,6 +598,7 @@ def run_ours(args, rank, world, local):
             "e2e": e2e,
             "exchange_forms": dict(forms, note="30 cycles each, device time per iteration (scene advance "
                                                "included), same hyper-parameters and scene"),
+            "iteration_floor": floor,
             "gpu_launches": int(launches),
             "clocks": clocks,
             "hsef": hsef_info,
