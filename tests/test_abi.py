@@ -237,3 +237,17 @@ def test_bf_workspace_size_and_bad_configs():
                                  4, X, None, None) == -1                 # edges misaligned
     assert L.sepso_poly_evaluate(8, 0, None, 16, P, P, None, 0, ctypes.c_float(30.0), 4, None, None,
                                  None) == 0
+    # the 3D objective's calls: argument checks before any CUDA call
+    p3 = np.zeros(3, np.float32)
+    P3 = p3.ctypes.data
+    assert L.sepso_bf_set_spheres(None, P3, P3, None, 0) == -1
+    assert L.sepso_bf_set_warm_start(None, None, ctypes.c_float(0.0), ctypes.c_float(0.0), 0) == -1
+    assert L.sepso_sphere_evaluate(0, 4, X, 24, P3, P3, X, 4, ctypes.c_float(30.0), 4, X, None, None) == -1
+    assert L.sepso_sphere_evaluate(8, 4, X, 23, P3, P3, X, 4, ctypes.c_float(30.0), 4, X, None, None) == -1
+    assert L.sepso_sphere_evaluate(8, 4, X, 24, P3, P3, X, 4, ctypes.c_float(30.0), 9, X, None, None) == -1
+    assert L.sepso_sphere_evaluate(8, 4, X, 24, P3, P3, X, -1, ctypes.c_float(30.0), 4, X, None, None) == -1
+    assert L.sepso_sphere_evaluate(8, 4, X, 24, P3, P3, ctypes.c_void_p((1 << 20) + 8), 4, ctypes.c_float(30.0),
+                                   4, X, None, None) == -1               # spheres misaligned
+    assert L.sepso_sphere_evaluate(8, 4, X, 24, None, P3, X, 4, ctypes.c_float(30.0), 4, X, None, None) == -1
+    assert L.sepso_sphere_evaluate(8, 0, None, 24, P3, P3, None, 0, ctypes.c_float(30.0), 4, None, None,
+                                   None) == 0

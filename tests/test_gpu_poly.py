@@ -166,3 +166,40 @@ def test_lane_per_particle_kernel_matches_oracle(native):
         assert s["Tfit"][0] == pytest.approx(o["Tfit"][0], rel=1e-5)
         _close(s["Tb"], o["Tb"], 400.0)
     assert checked >= 2
+
+
+def test_polygon_warm_start_matches_oracle(native):
+    # Priori Initialization on objective 5 (Sec. 3.3.3): each run's first
+    # ceil(gamma N) particles per group around its previous path, the planning cycle
+    # in the counters; two iterations of each run vs the oracle
+    cfg, start, target, polys, edges, hy = polygon_workload(5, N=12, iters=2, runs=4)
+    cfg = cfg.with_(G=3, pi_gamma=0.25, pi_halfwidth=20.0)
+    hy = np.array(hy[:3])
+    prev = random_paths(31, 4, cfg.D // 2).astype(np.float32) * np.float32(0.5) + np.float32(100.0)
+    pl = BFPlanner(cfg)
+    pl.set_hyper(hy)
+    pl.set_polygons(start, target, edges)
+    pl.set_warm_start(prev, cycle=5)
+    pl.run_async()
+    sc = _scene(start, target, edges)
+    checked = 0
+    for r in range(4):
+        c1 = cfg.with_(runs=1, run_id=r)
+        sw = oracle.BFSwarm(c1, hy, sc)
+        sw.set_previous(prev[r], 5)
+        sw.init()
+        ok = True
+        for _ in range(2):
+            if not _margins_ok(c1, sc, sw.s["X"]):
+                ok = False
+                break
+            sw.iteration()
+        if not ok:
+            continue
+        checked += 1
+        s, o = pl.get_state(r), sw.state()
+        _close(s["X"], o["X"], 400.0)
+        _close(s["V"], o["V"], float(hy[:, 5].max()) * 400.0)
+        np.testing.assert_allclose(s["Pfit"], o["Pfit"], rtol=1e-5)
+        assert s["Tfit"][0] == pytest.approx(o["Tfit"][0], rel=1e-5)
+    assert checked >= 2
