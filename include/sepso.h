@@ -293,6 +293,8 @@ typedef struct {
   int32_t n_prior;      /* particles per group started around the prior's proposal   */
   float pi_halfwidth;   /* half-width of both start intervals                         */
   uint32_t cycle;       /* Philox counter word 2 (low 24 bits): the planning cycle    */
+  int32_t obstacle_kind; /* 0: O circles; 1: O polygon edges (Sec. 3.3.1: Q = the
+                            number of proper crossings of path segments and edges) */
 } sepso_batch_scene;
 
 /* Launch shape: particles per work item (8..256), threads per CTA (64..512, a
@@ -314,7 +316,9 @@ void sepso_batch_destroy(sepso_batch_handle h);
 
 /* Inputs (host, copied; sync): hyper = the scenes' G x 6 rows back to back (Table
  * hyper8 layout), points = n x 4 (start x, y, target x, y), circles = the scenes'
- * O x 3 rows back to back.  Errors: EINVAL. */
+ * obstacle rows back to back: O x 3 (cx, cy, r) for a circle scene, O x 4 (x0, y0,
+ * x1, y1; a closed polygon lists each side once) for a polygon scene.
+ * Errors: EINVAL. */
 int sepso_batch_set_inputs(sepso_batch_handle h, const float* hyper, const float* points,
                            const float* circles);
 

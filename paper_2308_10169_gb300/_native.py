@@ -58,7 +58,8 @@ class BatchScene(ctypes.Structure):
                 ("O", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("alpha", ctypes.c_float),
                 ("beta", ctypes.c_int32), ("seed", ctypes.c_uint64), ("run_id", ctypes.c_uint32),
                 ("stall_iters", ctypes.c_int32), ("stall_tol", ctypes.c_float), ("n_pi", ctypes.c_int32),
-                ("n_prior", ctypes.c_int32), ("pi_halfwidth", ctypes.c_float), ("cycle", ctypes.c_uint32)]
+                ("n_prior", ctypes.c_int32), ("pi_halfwidth", ctypes.c_float), ("cycle", ctypes.c_uint32),
+                ("obstacle_kind", ctypes.c_int32)]
 
 
 class BatchShape(ctypes.Structure):

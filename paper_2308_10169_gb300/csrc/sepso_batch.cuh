@@ -38,6 +38,8 @@ struct BatchScene {
   int nteam;       // agents in the team whose paths count, 0 until their first paths exist
   float sep2;      // squared separation below which two agents conflict
   int pad_team;
+  int poly;        // 1: the obstacle block holds O polygon edges (x0, y0, x1, y1), not circle pairs
+  int pad_poly;
 };
 
 struct BatchParams {

@@ -534,6 +534,7 @@ class BatchSceneSpec:
     n_prior: int = 0          # particles per group around the learned prior's proposal
     pi_halfwidth: float = 20.0
     cycle: int = 0
+    obstacle_kind: int = 0    # 0: O circles; 1: O polygon edges (Sec. 3.3.1)
 
     @property
     def D(self) -> int:
@@ -550,7 +551,7 @@ class BatchSceneSpec:
                            at_mode=AT_STALL if self.stall_iters > 0 else AT_OFF,
                            stall_iters=max(self.stall_iters, 1), stall_tol=self.stall_tol,
                            use_pi=use_pi, pi_gamma=g, pi_halfwidth=self.pi_halfwidth,
-                           seed=self.seed, run_id=self.run_id)
+                           seed=self.seed, run_id=self.run_id, obstacle_kind=self.obstacle_kind)
 
 
 def batch_workload(seed: int = 0, n: int = 4096, T_range=(8, 64), O_range=(16, 1024),

@@ -485,7 +485,8 @@ class BatchPlanner:
             arr[i] = BatchScene(T=sp.T, G=sp.G, N=sp.N, O=sp.O, max_iters=sp.max_iters,
                                 alpha=sp.alpha, beta=sp.beta, seed=sp.seed, run_id=sp.run_id,
                                 stall_iters=sp.stall_iters, stall_tol=sp.stall_tol, n_pi=sp.n_pi,
-                                n_prior=sp.n_prior, pi_halfwidth=sp.pi_halfwidth, cycle=sp.cycle)
+                                n_prior=sp.n_prior, pi_halfwidth=sp.pi_halfwidth, cycle=sp.cycle,
+                                obstacle_kind=sp.obstacle_kind)
         self._arr = arr
         size = ctypes.c_size_t()
         check_batch(self.lib.sepso_batch_workspace_size(arr, self.n, ctypes.byref(size)))
