@@ -1034,7 +1034,52 @@ def run_poly(runs: int = 64, iters: int = 100):
         del pl
     out["workload"] = (f"400x400 map, 12 boxes + 4 U-shaped polygons (80 edges), T=8, G=8 x 170, "
                        f"{iters} iterations, Table hyper8path, alpha=30 beta=4, {runs} plans per graph")
+    out["batched_scenes"] = run_poly_batch()
     return out
+
+
+def run_poly_batch(n: int = 1024, iters: int = 100, seed: int = 0):
+    """Independent polygon scenes in the batched planner (one CUDA graph): each a
+    400 x 400 map with 4..16 axis-aligned boxes (centres U[60,340]^2, half-sizes
+    U[10,30]), T ~ U{8..32}, G = 8, N per group ~ U{32..170}, sampled hyper-parameters,
+    alpha 30, beta 4, ``iters`` iterations."""
+    import torch
+
+    from paper_2308_10169_gb300 import BatchPlanner
+    from paper_2308_10169_gb300.inputs import BatchSceneSpec, box, polygon_edges, sample_hyper
+    rng = np.random.default_rng(9000 + seed)
+    specs, hyper, obst = [], [], []
+    for i in range(n):
+        k = int(rng.integers(4, 17))
+        e = polygon_edges([box(*rng.uniform(60, 340, 2), *rng.uniform(10, 30, 2)) for _ in range(k)])
+        specs.append(BatchSceneSpec(T=int(rng.integers(8, 33)), G=8, N=int(rng.integers(32, 171)), O=len(e),
+                                    max_iters=iters, alpha=30.0, beta=4, seed=seed, run_id=i, obstacle_kind=1))
+        hyper.append(sample_hyper(int(rng.integers(1 << 30)), 8))
+        obst.append(e)
+    points = np.tile(np.array([[20, 20, 380, 380]], np.float32), (n, 1))
+    bp = BatchPlanner(specs)
+    bp.set_inputs(hyper, points, obst)
+    bp.autotune(trial_launches=3)
+    bp.run_async(True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    bp.run_async(True)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    res = bp.read()
+    pairs = sum(sp.G * sp.N * (sp.T + 1) * sp.O for sp in specs) * iters
+    achieved = pairs * 20 / (ms / 1e3) / 1e12
+    return {"workload": f"{n} scenes of 4..16 boxes, T~U{{8..32}}, G=8, N/group~U{{32..170}}, {iters} iterations, "
+                        "one CUDA graph (batched planner, obstacle_kind = polygons)",
+            "plans_per_s": n / (ms / 1e3), "ms": ms, "pair_tests_per_s": pairs / (ms / 1e3),
+            "median_cost": float(np.median([r["cost"] for r in res])),
+            "collision_free": float(np.mean([r["Q"] == 0 for r in res])),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak()[0], "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak()[0], "peak_source": fp32_peak()[1], "kernel": "batch_kernel",
+                         "flops_per_pair": 20},
+            "shape": bp.shape()}
 
 
 # Algorithmic work of a 3D path evaluation: per (segment, sphere) test 24 flops
