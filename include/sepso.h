@@ -462,6 +462,16 @@ int sepso_server_submit(sepso_server_handle h, int32_t agent, int32_t T, const f
 int sepso_server_submit_at(sepso_server_handle h, int32_t agent, int32_t T, const float* start,
                            const float* target, const float* circles, int32_t O, int64_t tag,
                            double arrival_s);
+/* As sepso_server_submit_at for a request among polygon obstacles (Sec. 3.3.1 map
+ * model): edges E x 4 (x0, y0, x1, y1; a closed polygon lists each side once), Q =
+ * the number of proper crossings of path segments and edges.  A slot holds at most
+ * min(Omax, 3 Omax / 4 rounded as the circle blocks are) edges -- the float4 records
+ * of its circle block.  Polygon requests are served without the learned prior (its
+ * raster reads circles): while a prior is attached they are refused, and a prior
+ * cannot be attached while polygon requests are queued or in flight.
+ * arrival_s < 0: now (as sepso_server_submit).  Errors: EINVAL. */
+int sepso_server_submit_polygons(sepso_server_handle h, int32_t agent, int32_t T, const float* start,
+                                 const float* target, const float* edges, int32_t E, int64_t tag, double arrival_s);
 /* The server clock (s since creation or the last restart); restart != 0 resets it. */
 double sepso_server_clock(sepso_server_handle h, int32_t restart);
 /* Tick natively until every submitted request (including future arrivals) has

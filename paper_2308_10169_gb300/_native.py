@@ -183,6 +183,8 @@ SIGNATURES = {
     "sepso_server_submit": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp, _fp, _i32, _i64]),
     "sepso_server_submit_at": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp, _fp, _i32, _i64,
                                               ctypes.c_double]),
+    "sepso_server_submit_polygons": (ctypes.c_int, [_vp, _i32, _i32, _fp, _fp, _fp, _i32, _i64,
+                                                    ctypes.c_double]),
     "sepso_server_clock": (ctypes.c_double, [_vp, _i32]),
     "sepso_server_run": (ctypes.c_int, [_vp, _i64]),
     "sepso_server_tick": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),

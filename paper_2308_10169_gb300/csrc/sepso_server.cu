@@ -167,7 +167,7 @@ __global__ void server_admit_kernel(BatchParams p, const Admit* admits, const fl
   }
   // the request's circle-pair block, staged by the host in the same layout
   float4* circ = const_cast<float4*>(p.circ) + S.co;
-  const int nf4 = S.O > 0 ? pair_block_f4(S.O) : 0;
+  const int nf4 = S.O > 0 ? (S.poly ? S.O : pair_block_f4(S.O)) : 0;
   for (int o = threadIdx.x; o < nf4; o += blockDim.x) circ[o] = admit_circ[A.c0 + o];
   for (int g = threadIdx.x; g < 2 * S.G; g += blockDim.x) {
     p.Gfit2[S.gso + g] = INFINITY;
@@ -239,8 +239,9 @@ __global__ void server_prior_kernel(BatchParams p, const Admit* admits, int n, c
 
 struct Request {
   int agent, T, O;
+  bool poly = false;        // O polygon edges instead of circles
   float pts[4];
-  std::vector<float> circ;  // O x 3
+  std::vector<float> circ;  // O x 3 (circles) or O x 4 (edges)
   long long tag;
   double arrival;           // server clock (s); admitted once the clock passes it
 };
@@ -248,6 +249,7 @@ struct Request {
 struct Slot {
   bool busy = false;
   int agent = -1, T = 0, O = 0;
+  bool poly = false;
   long long tag = 0;
   long long start_tick = 0;  // tick of the first iteration
   double arrival = 0.0;
@@ -470,7 +472,14 @@ int admit(sepso_server_ctx* h, int b) {
     std::memcpy(A.pts, r.pts, sizeof A.pts);
     A.slot = i;
     A.c0 = c0;
-    if (r.O > 0) {
+    d.poly = r.poly ? 1 : 0;
+    d.pad_poly = 0;
+    if (r.poly) {
+      d.n_pr = 0;  // no learned prior for a polygon request
+      for (int e = 0; e < r.O; ++e)
+        h->h_acirc[b][c0 + e] = make_float4(r.circ[4 * e], r.circ[4 * e + 1], r.circ[4 * e + 2], r.circ[4 * e + 3]);
+      c0 += r.O;
+    } else if (r.O > 0) {
       // circle-pair block (layout in sepso_device.cuh)
       const int K = circle_pairs(r.O), nf4 = pair_block_f4(r.O);
       float4* blk = h->h_acirc[b] + c0;
@@ -497,6 +506,7 @@ int admit(sepso_server_ctx* h, int b) {
     sl.agent = r.agent;
     sl.T = r.T;
     sl.O = r.O;
+    sl.poly = r.poly;
     sl.tag = r.tag;
     sl.start_tick = h->tick + 1 + defer;
     sl.arrival = r.arrival;
@@ -666,6 +676,10 @@ int sepso_server_set_prior(sepso_server_handle h, sepso_prior_handle prior, int3
     h->n_prior = 0;
     return SEPSO_OK;
   }
+  for (const Request& r : h->queue)
+    if (r.poly) return sfail(SEPSO_EINVAL, "polygon requests queued: the prior rasterises circles only");
+  for (const Slot& sl : h->slots)
+    if (sl.busy && sl.poly) return sfail(SEPSO_EINVAL, "polygon requests in flight: the prior rasterises circles only");
   int T = 0, mc = 0, cap = 0;
   float W = 0.0f, H = 0.0f;
   cudaStream_t st = nullptr;
@@ -715,6 +729,40 @@ int sepso_server_submit_at(sepso_server_handle h, int32_t agent, int32_t T, cons
         r.circ[3 * o + 2] < 0)
       return sfail(SEPSO_EINVAL, "circle %d invalid", o);
   r.tag = tag;
+  r.arrival = arrival_s;
+  if (!h->queue.empty() && arrival_s < h->queue.back().arrival)
+    return sfail(SEPSO_EINVAL, "requests must be submitted in arrival order");
+  h->queue.push_back(std::move(r));
+  return SEPSO_OK;
+}
+
+int sepso_server_submit_polygons(sepso_server_handle h, int32_t agent, int32_t T, const float* start,
+                                 const float* target, const float* edges, int32_t E, int64_t tag, double arrival_s) {
+  if (!h || !start || !target) return sfail(SEPSO_EINVAL, "NULL argument");
+  if (h->prior) return sfail(SEPSO_EINVAL, "polygon requests are served without the learned prior: detach it");
+  if (agent < 0 || agent >= h->cfg.n_agents) return sfail(SEPSO_EINVAL, "agent %d out of range", agent);
+  if (T < 1 || T > h->cfg.Tmax) return sfail(SEPSO_EINVAL, "T=%d outside [1, Tmax=%d]", T, h->cfg.Tmax);
+  const int cap = std::min(h->Om, pair_block_f4(h->Om));
+  if (E < 0 || E > cap || (E > 0 && !edges)) return sfail(SEPSO_EINVAL, "E=%d edges invalid (at most %d)", E, cap);
+  Request r;
+  r.agent = agent;
+  r.T = T;
+  r.O = E;
+  r.poly = true;
+  r.pts[0] = start[0];
+  r.pts[1] = start[1];
+  r.pts[2] = target[0];
+  r.pts[3] = target[1];
+  for (float v : r.pts)
+    if (!std::isfinite(v)) return sfail(SEPSO_EINVAL, "start/target not finite");
+  r.circ.assign(edges, edges + 4 * (size_t)E);
+  for (float v : r.circ)
+    if (!std::isfinite(v)) return sfail(SEPSO_EINVAL, "edge coordinate not finite");
+  r.tag = tag;
+  if (arrival_s < 0.0) {
+    const double now = now_s(h->t0);
+    arrival_s = h->queue.empty() ? now : std::max(now, h->queue.back().arrival);
+  }
   r.arrival = arrival_s;
   if (!h->queue.empty() && arrival_s < h->queue.back().arrival)
     return sfail(SEPSO_EINVAL, "requests must be submitted in arrival order");

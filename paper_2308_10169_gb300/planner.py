@@ -669,6 +669,13 @@ class Server:
                                                     fptr(_f32(target)), fptr(c) if c.size else None,
                                                     c.shape[0], tag, float(arrival_s)))
 
+    def submit_polygons(self, agent: int, T: int, start, target, edges, tag: int, arrival_s: float = -1.0):
+        """A request among polygon obstacles: edges (E, 4) as x0, y0, x1, y1."""
+        e = _f32(edges, (-1, 4))
+        self._check(self.lib.sepso_server_submit_polygons(self._h, agent, T, fptr(_f32(start)),
+                                                          fptr(_f32(target)), fptr(e) if e.size else None,
+                                                          e.shape[0], tag, float(arrival_s)))
+
     def clock(self, restart: bool = False) -> float:
         return float(self.lib.sepso_server_clock(self._h, int(restart)))
 
