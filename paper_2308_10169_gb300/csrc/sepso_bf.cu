@@ -324,6 +324,20 @@ __device__ __forceinline__ float sphere_row(const float* s, int T, const float* 
   return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
 }
 
+// Proper crossing of segment a -> a + u and edge d0 -> d1 (float4 x0, y0, x1, y1):
+// both pairs of orientations of opposite signs, strictly.  With v = d1 - d0 and w =
+// d0 - a: o1 = u x w, o3 = v x (-w), and o2 = o1 + u x v, o4 = o3 - u x v for the
+// other end points, each formed from differences of nearby points.
+__device__ __forceinline__ int edge_cross(float ax, float ay, float ux, float uy, const float4 d) {
+  const float vx = d.z - d.x, vy = d.w - d.y;
+  const float wx = d.x - ax, wy = d.y - ay;
+  const float o1 = ux * wy - uy * wx;
+  const float o3 = vy * wx - vx * wy;
+  const float c = ux * vy - uy * vx;
+  const float o2 = o1 + c, o4 = o3 - c;
+  return (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
+}
+
 // Objective 5 (Sec. 3.3.1 map model; Eqs. path_fit, lenth, penalty): length of the
 // path start -> waypoints -> target plus alpha * Q^beta, Q = the number of proper
 // crossings (strict orientation tests) between its T + 1 segments and the E obstacle
@@ -344,13 +358,7 @@ __device__ __forceinline__ float poly_row(const float* s, int T, const float* pt
     const float bx = k == T ? pts[2] : s[k], by = k == T ? pts[3] : s[T + k];
     const float ux = bx - ax, uy = by - ay;
     for (int e = lane; e < E; e += 32) {
-      const float4 d = edges[e];
-      const float vx = d.z - d.x, vy = d.w - d.y;
-      const float o1 = ux * (d.y - ay) - uy * (d.x - ax);
-      const float o2 = ux * (d.w - ay) - uy * (d.z - ax);
-      const float o3 = vx * (ay - d.y) - vy * (ax - d.x);
-      const float o4 = vx * (by - d.y) - vy * (bx - d.x);
-      q += (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
+      q += edge_cross(ax, ay, ux, uy, edges[e]);
     }
   }
   q = __reduce_add_sync(0xffffffffu, q);
@@ -819,13 +827,7 @@ __device__ __forceinline__ float poly_lane(const float* s, int T, const float* p
     const float ux = bx - ax, uy = by - ay;
     len += sqrtf(fmaf(ux, ux, uy * uy));
     for (int e = 0; e < E; ++e) {
-      const float4 d = edges[e];
-      const float vx = d.z - d.x, vy = d.w - d.y;
-      const float o1 = ux * (d.y - ay) - uy * (d.x - ax);
-      const float o2 = ux * (d.w - ay) - uy * (d.z - ax);
-      const float o3 = vx * (ay - d.y) - vy * (ax - d.x);
-      const float o4 = vx * (by - d.y) - vy * (bx - d.x);
-      q += (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
+      q += edge_cross(ax, ay, ux, uy, edges[e]);
     }
   }
   qout = q;

@@ -807,7 +807,7 @@ __device__ __forceinline__ void warp_fitness_pairs(float x, float y, int T, int 
   *q_out = hits;
 }
 
-// The same among polygon edges: lane s <= T stores segment s's end points, lane l
+// The same among polygon edges: lane s <= T stores segment s's start and direction, lane l
 // tests edges l, l + 32, ... against every segment (edge_crosses).
 __device__ __forceinline__ void warp_fitness_edges(float x, float y, int T, int lane, float sx, float sy, float tx,
                                                    float ty, const float4* __restrict__ edges, int E, float* fr,
@@ -820,7 +820,7 @@ __device__ __forceinline__ void warp_fitness_edges(float x, float y, int T, int 
     const float bx = lane == T ? tx : x, by = lane == T ? ty : y;
     const float dx = bx - ax, dy = by - ay;
     len = sqrtf(fmaf(dx, dx, dy * dy));
-    f4[2 * lane] = make_float4(ax, ay, bx, by);
+    f4[2 * lane] = make_float4(ax, ay, dx, dy);
   }
   __syncwarp();
   int hits = 0;
