@@ -324,20 +324,6 @@ __device__ __forceinline__ float sphere_row(const float* s, int T, const float* 
   return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
 }
 
-// Proper crossing of segment a -> a + u and edge d0 -> d1 (float4 x0, y0, x1, y1):
-// both pairs of orientations of opposite signs, strictly.  With v = d1 - d0 and w =
-// d0 - a: o1 = u x w, o3 = v x (-w), and o2 = o1 + u x v, o4 = o3 - u x v for the
-// other end points, each formed from differences of nearby points.
-__device__ __forceinline__ int edge_cross(float ax, float ay, float ux, float uy, const float4 d) {
-  const float vx = d.z - d.x, vy = d.w - d.y;
-  const float wx = d.x - ax, wy = d.y - ay;
-  const float o1 = ux * wy - uy * wx;
-  const float o3 = vy * wx - vx * wy;
-  const float c = ux * vy - uy * vx;
-  const float o2 = o1 + c, o4 = o3 - c;
-  return (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
-}
-
 // Objective 5 (Sec. 3.3.1 map model; Eqs. path_fit, lenth, penalty): length of the
 // path start -> waypoints -> target plus alpha * Q^beta, Q = the number of proper
 // crossings (strict orientation tests) between its T + 1 segments and the E obstacle
@@ -358,7 +344,7 @@ __device__ __forceinline__ float poly_row(const float* s, int T, const float* pt
     const float bx = k == T ? pts[2] : s[k], by = k == T ? pts[3] : s[T + k];
     const float ux = bx - ax, uy = by - ay;
     for (int e = lane; e < E; e += 32) {
-      q += edge_cross(ax, ay, ux, uy, edges[e]);
+      q += edge_crosses(ax, ay, ux, uy, edges[e]);
     }
   }
   q = __reduce_add_sync(0xffffffffu, q);
@@ -807,8 +793,8 @@ __global__ void __launch_bounds__(256) bf_small_kernel(const BfParams p) {
 // lanes.  Lane l of a warp owns one particle: it updates its row coordinate by
 // coordinate, keeps the new row in shared memory (stride D + 1: the lanes' rows fall
 // in different banks) and tests its T + 1 segments against every obstacle record
-// (an edge of objective 5, a sphere of objective 6), the record read by all lanes
-// at once (a broadcast).  Bests, keys and Pbest parities as in bf_iter_kernel.
+// (edge pairs of objective 5, sphere pairs of objective 6), each record read by all
+// lanes at once (a broadcast).  Bests, keys and Pbest parities as in bf_iter_kernel.
 // poly_lane_kernel runs objective 5, sphere_lane_kernel objective 6.
 // ---------------------------------------------------------------------------
 constexpr int kLaneMaxD = 64;
@@ -817,8 +803,25 @@ constexpr int kLaneThreads = 128;   // small CTAs: the single wave of lane CTAs 
 constexpr int kLaneMinPerSm = 256;   // particles per SM from which objective 5 uses a lane each
 constexpr long long kSmallMaxCoords = 8192;  // swarm size (G N D) up to which a run is one CTA
 
-__device__ __forceinline__ float poly_lane(const float* s, int T, const float* pts, const float4* edges, int E,
-                                           float alpha, int beta, int& qout) {
+// Packed FP32x2 arithmetic (two lanes of a 64-bit register pair).
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// Objective 5 in the lane kernel, on edge pairs: shared memory holds the edges two
+// by two as float4 (x0a, x0b, y0a, y0b) and float4 (vxa, vxb, -vya, -vyb), v = d1 -
+// d0 (an odd count padded with a zero edge, v = 0, whose o3 o4 vanishes: no hit), so
+// that packed FP32x2 instructions test a segment against two edges at once with the
+// orientations of edge_crosses: w = d0 - a, o1 = u x w, c = u x v, o2 = o1 + c, and
+// the negated pair m3 = -o3 = v x w, m4 = -o4 = m3 + c, whose product is o3 o4.
+__device__ __forceinline__ float poly_lane_pairs(const float* s, int T, const float* pts, const ulonglong2* ep, int K,
+                                                 float alpha, int beta, int& qout) {
   float len = 0.0f;
   int q = 0;
   for (int k = 0; k <= T; ++k) {
@@ -826,8 +829,20 @@ __device__ __forceinline__ float poly_lane(const float* s, int T, const float* p
     const float bx = k == T ? pts[2] : s[k], by = k == T ? pts[3] : s[T + k];
     const float ux = bx - ax, uy = by - ay;
     len += sqrtf(fmaf(ux, ux, uy * uy));
-    for (int e = 0; e < E; ++e) {
-      q += edge_cross(ax, ay, ux, uy, edges[e]);
+    const unsigned long long NAX = pack2(-ax, -ax), NAY = pack2(-ay, -ay), UX = pack2(ux, ux);
+    const unsigned long long NUX = pack2(-ux, -ux), NUY = pack2(-uy, -uy);
+#pragma unroll 2
+    for (int i = 0; i < K; ++i) {
+      const ulonglong2 d0 = ep[2 * i], v = ep[2 * i + 1];
+      const unsigned long long WX = fadd2(d0.x, NAX), WY = fadd2(d0.y, NAY);
+      const unsigned long long O1 = ffma2(UX, WY, fmul2(NUY, WX));
+      const unsigned long long C = ffma2(NUX, v.y, fmul2(NUY, v.x));
+      const unsigned long long M3 = ffma2(v.x, WY, fmul2(v.y, WX));
+      const unsigned long long P12 = fmul2(O1, fadd2(O1, C)), P34 = fmul2(M3, fadd2(M3, C));
+      float a12, b12, a34, b34;
+      unpack2(P12, a12, b12);
+      unpack2(P34, a34, b34);
+      q += (a12 < 0.0f && a34 < 0.0f) + (b12 < 0.0f && b34 < 0.0f);
     }
   }
   qout = q;
@@ -841,16 +856,6 @@ __device__ __forceinline__ float poly_lane(const float* s, int T, const float* p
 // -along = w.(-u), p = w + (-along) u, and S = max(|along| - h, 0)^2 + |p|^2 - r^2
 // per sphere, whose sign bit is the hit (S is never -0: the sum of -r^2 and
 // squares is +0 at the least when it vanishes).
-__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
 struct Seg3P {
   unsigned long long nmx, nmy, nmz, ux, uy, uz, nux, nuy, nuz;
   float h;
@@ -921,7 +926,7 @@ __device__ __forceinline__ float sphere_lane(const float* s, int T, const float*
 
 // Bytes of the obstacle records the lane kernel stages for n records.
 __host__ __device__ inline size_t lane_obstacle_bytes(int fn, int n) {
-  return fn == 6 ? (size_t)((n + 1) / 2) * 32 : (size_t)n * 16;
+  return fn == 5 || fn == 6 ? (size_t)((n + 1) / 2) * 32 : (size_t)n * 16;
 }
 
 template <int FN>
@@ -955,7 +960,13 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
       sedges[2 * i + 1] = make_float4(c0.z, c1.z, -(c0.w * c0.w), -(c1.w * c1.w));
     }
   } else {
-    for (int i = threadIdx.x; i < E; i += blockDim.x) sedges[i] = p.edges[i];
+    // edge pairs (x0a, x0b, y0a, y0b), (vxa, vxb, -vya, -vyb); the pad is a zero edge
+    for (int i = threadIdx.x; i < (E + 1) / 2; i += blockDim.x) {
+      const float4 e0 = p.edges[2 * i];
+      const float4 e1 = 2 * i + 1 < E ? p.edges[2 * i + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      sedges[2 * i] = make_float4(e0.x, e1.x, e0.y, e1.y);
+      sedges[2 * i + 1] = make_float4(e0.z - e0.x, e1.z - e1.x, -(e0.w - e0.y), -(e1.w - e1.y));
+    }
   }
   const uint32_t cyc = (uint32_t)p.warm[2];
   if (blockIdx.x == 0) {
@@ -1090,7 +1101,8 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
       float F = 0.0f;
       int qcount = 0;
       if (live)
-        F = FN == 5 ? poly_lane(srow, T, p.pts, sedges, E, p.alpha, p.beta, qcount)
+        F = FN == 5 ? poly_lane_pairs(srow, T, p.pts, reinterpret_cast<const ulonglong2*>(sedges), (E + 1) / 2,
+                                      p.alpha, p.beta, qcount)
                     : sphere_lane(srow, T, p.pts, reinterpret_cast<const ulonglong2*>(sedges), (E + 1) / 2, p.alpha,
                                   p.beta, qcount);
       const bool improved = live && F < pf;
