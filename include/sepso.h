@@ -465,8 +465,8 @@ int sepso_server_submit_at(sepso_server_handle h, int32_t agent, int32_t T, cons
 /* As sepso_server_submit_at for a request among polygon obstacles (Sec. 3.3.1 map
  * model): edges E x 4 (x0, y0, x1, y1; a closed polygon lists each side once), Q =
  * the number of proper crossings of path segments and edges.  A slot holds at most
- * min(Omax, 3 Omax / 4 rounded as the circle blocks are) edges -- the float4 records
- * of its circle block.  Polygon requests are served without the learned prior (its
+ * min(Omax, the float4 records of its circle block rounded down to even) edges (two
+ * edges take two float4s).  Polygon requests are served without the learned prior (its
  * raster reads circles): while a prior is attached they are refused, and a prior
  * cannot be attached while polygon requests are queued or in flight.
  * arrival_s < 0: now (as sepso_server_submit).  Errors: EINVAL. */

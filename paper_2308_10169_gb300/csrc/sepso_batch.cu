@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchParams p, int 
   if (tid == 0) mbar_init(&s_mbar, 1);
   __syncthreads();
   if (tid == 0 && fit_phase && S.O > 0) {
-    const uint32_t bytes = (uint32_t)(S.poly ? S.O : pair_block_f4(S.O)) * 16u;
+    const uint32_t bytes = (uint32_t)(S.poly ? edge_pair_f4(S.O) : pair_block_f4(S.O)) * 16u;
     mbar_expect_tx(&s_mbar, bytes);
     bulk_g2s(sC, p.circ + S.co, bytes, &s_mbar);
   }
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchParams p, int 
     const int ppw = 1;
     const int lsub = lane;
     const int K = circle_pairs(S.O);
-    const int split = warp_split(T, S.poly ? S.O : K);
+    const int split = warp_split(T, S.poly ? (S.O + 1) / 2 : K);
     const float2* sNr2 = reinterpret_cast<const float2*>(sC + K);
     const long long sj = S.so + (long long)(jl & 1) * M * (D + 4);
     for (int i0 = warp * ppw; i0 < nl; i0 += nwarps * ppw) {
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(512, 2) batch_kernel(const BatchParams p, int 
       float len;
       int qq;
       if (S.poly)
-        group_fitness_edges(sX + (live ? i : 0) * D, live, lp, T, split, S.O, sx, sy, tx, ty, sC, &len, &qq);
+        group_fitness_edge_pairs(sX + (live ? i : 0) * D, live, lp, T, split, S.O, sx, sy, tx, ty, sC, &len, &qq);
       else
         group_fitness_pairs(sX + (live ? i : 0) * D, live, lp, T, split, K, sx, sy, tx, ty, sC, sNr2, &len, &qq);
       if (S.nteam > 1)  // the team mates' paths as moving obstacles
@@ -430,13 +430,13 @@ __global__ void batch_gate_kernel(const BatchParams p) {
   }
   const float sx = p.pts[4 * s], sy = p.pts[4 * s + 1], tx = p.pts[4 * s + 2], ty = p.pts[4 * s + 3];
   const int K = circle_pairs(S.O);
-  const int split = warp_split(S.T, S.poly ? S.O : K);
+  const int split = warp_split(S.T, S.poly ? (S.O + 1) / 2 : K);
   const float4* cxy = p.circ + S.co;
   const float2* nr2 = reinterpret_cast<const float2*>(cxy + K);
   float len;
   int q;
   if (S.poly)
-    group_fitness_edges(p.prior_path + (long long)s * p.Dmax, true, 32, S.T, split, S.O, sx, sy, tx, ty, cxy, &len,
+    group_fitness_edge_pairs(p.prior_path + (long long)s * p.Dmax, true, 32, S.T, split, S.O, sx, sy, tx, ty, cxy, &len,
                         &q);
   else
     group_fitness_pairs(p.prior_path + (long long)s * p.Dmax, true, 32, S.T, split, K, sx, sy, tx, ty, cxy, nr2,
@@ -445,7 +445,7 @@ __global__ void batch_gate_kernel(const BatchParams p) {
   int ok = 1;
   if (S.has_prev && S.n_pi > 0) {
     if (S.poly)
-      group_fitness_edges(p.agent_prevT + (long long)s * p.Dmax, true, 32, S.T, split, S.O, sx, sy, tx, ty, cxy,
+      group_fitness_edge_pairs(p.agent_prevT + (long long)s * p.Dmax, true, 32, S.T, split, S.O, sx, sy, tx, ty, cxy,
                           &len, &q);
     else
       group_fitness_pairs(p.agent_prevT + (long long)s * p.Dmax, true, 32, S.T, split, K, sx, sy, tx, ty, cxy, nr2,
@@ -552,7 +552,7 @@ BatchLayout batch_layout(const sepso_batch_scene* sc, int32_t n) {
     L.nS += 2 * M * (D + 4);
     L.nG += (long long)sc[s].G * D;
     L.nT += D;
-    L.nC += sc[s].O > 0 ? (sc[s].obstacle_kind ? sc[s].O : pair_block_f4(sc[s].O)) : 0;
+    L.nC += sc[s].O > 0 ? (sc[s].obstacle_kind ? edge_pair_f4(sc[s].O) : pair_block_f4(sc[s].O)) : 0;
     L.nH += 6LL * sc[s].G;
     L.nW += 3LL * sc[s].G;
     L.nGS += 2LL * sc[s].G;
@@ -803,7 +803,7 @@ int sepso_batch_create(const sepso_batch_scene* scenes, int32_t n, float map_w, 
     d.so = so; so += 2LL * d.M * (d.D + 4);
     d.go = go; go += (long long)d.G * d.D;
     d.to = to; to += d.D;
-    d.co = co; co += d.O > 0 ? (c.obstacle_kind ? d.O : pair_block_f4(d.O)) : 0;
+    d.co = co; co += d.O > 0 ? (c.obstacle_kind ? edge_pair_f4(d.O) : pair_block_f4(d.O)) : 0;
     d.ho = ho; ho += 6LL * d.G;
     d.wo = wo; wo += 3LL * d.G;
     d.gso = gso; gso += 2LL * d.G;
@@ -823,7 +823,7 @@ int sepso_batch_create(const sepso_batch_scene* scenes, int32_t n, float map_w, 
     d.poly = c.obstacle_kind;
     d.pad_poly = 0;
     // the shared-memory obstacle area holds pair_block_f4(Omax) float4s: E edges
-    // need E, which pair_block_f4(2 E) covers
+    // need edge_pair_f4(E), which pair_block_f4(2 E) covers
     h->Omax = std::max(h->Omax, c.obstacle_kind ? 2 * c.O : c.O);
     h->Dmax = std::max(h->Dmax, 2 * c.T);
     h->Gmax = std::max(h->Gmax, c.G);
@@ -862,7 +862,7 @@ int sepso_batch_set_inputs(sepso_batch_handle h, const float* hyper, const float
   for (int i = 0; i < 4 * h->n; ++i)
     if (!std::isfinite(points[i])) return bfail(SEPSO_EINVAL, "points[%d] not finite", i);
   if (L.nC > 0 && !circles) return bfail(SEPSO_EINVAL, "circles is NULL");
-  // circle-pair blocks (layout in sepso_device.cuh), or a polygon scene's edges
+  // circle-pair blocks, or a polygon scene's edge pairs (layouts in sepso_device.cuh)
   std::vector<float4> c4((size_t)std::max(L.nC, 1LL), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
   long long src = 0;  // float offset into circles
   for (int s = 0; s < h->n; ++s) {
@@ -870,12 +870,10 @@ int sepso_batch_set_inputs(sepso_batch_handle h, const float* hyper, const float
     if (O == 0) continue;
     float4* blk = c4.data() + h->desc[s].co;
     if (h->scenes[s].obstacle_kind) {
-      for (int e = 0; e < O; ++e, src += 4) {
-        const float4 v = make_float4(circles[src], circles[src + 1], circles[src + 2], circles[src + 3]);
-        if (!std::isfinite(v.x) || !std::isfinite(v.y) || !std::isfinite(v.z) || !std::isfinite(v.w))
-          return bfail(SEPSO_EINVAL, "scene %d: edge %d not finite", s, e);
-        blk[e] = v;
-      }
+      for (int i = 0; i < 4 * O; ++i)
+        if (!std::isfinite(circles[src + i])) return bfail(SEPSO_EINVAL, "scene %d: edge %d not finite", s, i / 4);
+      pack_edge_pairs(circles + src, O, blk);
+      src += 4 * (long long)O;
       continue;
     }
     const int K = circle_pairs(O);

@@ -803,23 +803,8 @@ constexpr int kLaneThreads = 128;   // small CTAs: the single wave of lane CTAs 
 constexpr int kLaneMinPerSm = 256;   // particles per SM from which objective 5 uses a lane each
 constexpr long long kSmallMaxCoords = 8192;  // swarm size (G N D) up to which a run is one CTA
 
-// Packed FP32x2 arithmetic (two lanes of a 64-bit register pair).
-__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-// Objective 5 in the lane kernel, on edge pairs: shared memory holds the edges two
-// by two as float4 (x0a, x0b, y0a, y0b) and float4 (vxa, vxb, -vya, -vyb), v = d1 -
-// d0 (an odd count padded with a zero edge, v = 0, whose o3 o4 vanishes: no hit), so
-// that packed FP32x2 instructions test a segment against two edges at once with the
-// orientations of edge_crosses: w = d0 - a, o1 = u x w, c = u x v, o2 = o1 + c, and
-// the negated pair m3 = -o3 = v x w, m4 = -o4 = m3 + c, whose product is o3 o4.
+// Objective 5 in the lane kernel, on edge pairs (edge_pair_hits): shared memory
+// holds the edges two by two (layout at edge_pair_f4).
 __device__ __forceinline__ float poly_lane_pairs(const float* s, int T, const float* pts, const ulonglong2* ep, int K,
                                                  float alpha, int beta, int& qout) {
   float len = 0.0f;
@@ -829,21 +814,7 @@ __device__ __forceinline__ float poly_lane_pairs(const float* s, int T, const fl
     const float bx = k == T ? pts[2] : s[k], by = k == T ? pts[3] : s[T + k];
     const float ux = bx - ax, uy = by - ay;
     len += sqrtf(fmaf(ux, ux, uy * uy));
-    const unsigned long long NAX = pack2(-ax, -ax), NAY = pack2(-ay, -ay), UX = pack2(ux, ux);
-    const unsigned long long NUX = pack2(-ux, -ux), NUY = pack2(-uy, -uy);
-#pragma unroll 2
-    for (int i = 0; i < K; ++i) {
-      const ulonglong2 d0 = ep[2 * i], v = ep[2 * i + 1];
-      const unsigned long long WX = fadd2(d0.x, NAX), WY = fadd2(d0.y, NAY);
-      const unsigned long long O1 = ffma2(UX, WY, fmul2(NUY, WX));
-      const unsigned long long C = ffma2(NUX, v.y, fmul2(NUY, v.x));
-      const unsigned long long M3 = ffma2(v.x, WY, fmul2(v.y, WX));
-      const unsigned long long P12 = fmul2(O1, fadd2(O1, C)), P34 = fmul2(M3, fadd2(M3, C));
-      float a12, b12, a34, b34;
-      unpack2(P12, a12, b12);
-      unpack2(P34, a34, b34);
-      q += (a12 < 0.0f && a34 < 0.0f) + (b12 < 0.0f && b34 < 0.0f);
-    }
+    q += edge_pair_hits(ax, ay, ux, uy, ep, 0, K);
   }
   qout = q;
   return q > 0 ? len + alpha * pow_int((float)q, beta) : len;
@@ -961,12 +932,9 @@ __device__ __forceinline__ void path_lane_iter(const BfParams& p, int j, int mod
     }
   } else {
     // edge pairs (x0a, x0b, y0a, y0b), (vxa, vxb, -vya, -vyb); the pad is a zero edge
-    for (int i = threadIdx.x; i < (E + 1) / 2; i += blockDim.x) {
-      const float4 e0 = p.edges[2 * i];
-      const float4 e1 = 2 * i + 1 < E ? p.edges[2 * i + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      sedges[2 * i] = make_float4(e0.x, e1.x, e0.y, e1.y);
-      sedges[2 * i + 1] = make_float4(e0.z - e0.x, e1.z - e1.x, -(e0.w - e0.y), -(e1.w - e1.y));
-    }
+    for (int i = threadIdx.x; i < (E + 1) / 2; i += blockDim.x)
+      edge_pair(p.edges[2 * i], 2 * i + 1 < E ? p.edges[2 * i + 1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f),
+                sedges + 2 * i);
   }
   const uint32_t cyc = (uint32_t)p.warm[2];
   if (blockIdx.x == 0) {

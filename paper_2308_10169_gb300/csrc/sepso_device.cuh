@@ -424,6 +424,16 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fmul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 
 // The frame of segment [a, b] as scalars: unit direction, normal n = (-u_y, u_x),
 // the negated projections of the midpoint on both, and the half-length.
@@ -557,6 +567,48 @@ __device__ __forceinline__ int edge_crosses(float ax, float ay, float ux, float 
   return (o1 * o2 < 0.0f) && (o3 * o4 < 0.0f);
 }
 
+// Edge pairs: the edges two by two as float4 (x0a, x0b, y0a, y0b) and float4 (vxa,
+// vxb, -vya, -vyb), v = d1 - d0, an odd count padded with a zero edge (v = 0: o3 o4
+// vanishes, no hit); edge_pair_f4(E) float4s.  Packed FP32x2 instructions then test
+// a segment against two edges at once with edge_crosses' orientations: w = d0 - a,
+// o1 = u x w, c = u x v, o2 = o1 + c, and the negated pair m3 = -o3 = v x w, m4 =
+// -o4 = m3 + c, whose product is o3 o4.
+__host__ __device__ inline int edge_pair_f4(int E) { return 2 * ((E + 1) / 2); }
+__host__ __device__ inline void edge_pair(const float4 a, const float4 b, float4* out) {
+  out[0] = make_float4(a.x, b.x, a.y, b.y);
+  out[1] = make_float4(a.z - a.x, b.z - b.x, -(a.w - a.y), -(b.w - b.y));
+}
+// E edges (x0, y0, x1, y1 each) from host memory into edge_pair_f4(E) float4s.
+inline void pack_edge_pairs(const float* e, int E, float4* out) {
+  for (int k = 0; 2 * k < E; ++k) {
+    const float* a = e + 8 * k;
+    const float4 fa = make_float4(a[0], a[1], a[2], a[3]);
+    const float4 fb = 2 * k + 1 < E ? make_float4(a[4], a[5], a[6], a[7]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    edge_pair(fa, fb, out + 2 * k);
+  }
+}
+// Crossings of segment a -> a + u with edge pairs k0 .. k1 - 1.
+__device__ __forceinline__ int edge_pair_hits(float ax, float ay, float ux, float uy,
+                                              const ulonglong2* __restrict__ ep, int k0, int k1) {
+  const unsigned long long NAX = pack2(-ax, -ax), NAY = pack2(-ay, -ay), UX = pack2(ux, ux);
+  const unsigned long long NUX = pack2(-ux, -ux), NUY = pack2(-uy, -uy);
+  int hits = 0;
+#pragma unroll 2
+  for (int k = k0; k < k1; ++k) {
+    const ulonglong2 d0 = ep[2 * k], v = ep[2 * k + 1];
+    const unsigned long long WX = fadd2(d0.x, NAX), WY = fadd2(d0.y, NAY);
+    const unsigned long long O1 = ffma2(UX, WY, fmul2(NUY, WX));
+    const unsigned long long C = ffma2(NUX, v.y, fmul2(NUY, v.x));
+    const unsigned long long M3 = ffma2(v.x, WY, fmul2(v.y, WX));
+    const unsigned long long P12 = fmul2(O1, fadd2(O1, C)), P34 = fmul2(M3, fadd2(M3, C));
+    float a12, b12, a34, b34;
+    unpack2(P12, a12, b12);
+    unpack2(P34, a34, b34);
+    hits += (a12 < 0.0f && a34 < 0.0f) + (b12 < 0.0f && b34 < 0.0f);
+  }
+  return hits;
+}
+
 __device__ __forceinline__ int edge_hits(float ax, float ay, float bx, float by, const float4* __restrict__ edges,
                                          int e0, int e1) {
   const float ux = bx - ax, uy = by - ay;
@@ -590,6 +642,39 @@ __device__ __forceinline__ void group_fitness_edges(const float* x, bool live, i
         len += sqrtf(fmaf(dx, dx, dy * dy));
       }
       hits += edge_hits(ax, ay, bx, by, edges, c * chunk, min(E, c * chunk + chunk));
+    }
+  }
+  for (int off = lp >> 1; off > 0; off >>= 1) {
+    len += __shfl_xor_sync(0xffffffffu, len, off);
+    hits += __shfl_xor_sync(0xffffffffu, hits, off);
+  }
+  *len_out = len;
+  *q_out = hits;
+}
+
+// The same with the edges as edge pairs (edge_pair_f4(E) float4s): lanes take
+// (segment, edge-pair chunk) items.
+__device__ __forceinline__ void group_fitness_edge_pairs(const float* x, bool live, int lp, int T, int split, int E,
+                                                         float sx, float sy, float tx, float ty, const float4* edges,
+                                                         float* len_out, int* q_out) {
+  const int lsub = (threadIdx.x & 31) & (lp - 1);
+  const int items = (T + 1) * split;
+  const int K = (E + 1) / 2;
+  const int chunk = (K + split - 1) / split;
+  const ulonglong2* ep = reinterpret_cast<const ulonglong2*>(edges);
+  float len = 0.0f;
+  int hits = 0;
+  if (live) {
+    for (int it = lsub; it < items; it += lp) {
+      const int sg = it % (T + 1);
+      const int c = it / (T + 1);
+      const float ax = (sg == 0) ? sx : x[sg - 1];
+      const float ay = (sg == 0) ? sy : x[T + sg - 1];
+      const float bx = (sg == T) ? tx : x[sg];
+      const float by = (sg == T) ? ty : x[T + sg];
+      const float ux = bx - ax, uy = by - ay;
+      if (c == 0) len += sqrtf(fmaf(ux, ux, uy * uy));
+      hits += edge_pair_hits(ax, ay, ux, uy, ep, c * chunk, min(K, c * chunk + chunk));
     }
   }
   for (int off = lp >> 1; off > 0; off >>= 1) {

@@ -167,7 +167,7 @@ __global__ void server_admit_kernel(BatchParams p, const Admit* admits, const fl
   }
   // the request's circle-pair block, staged by the host in the same layout
   float4* circ = const_cast<float4*>(p.circ) + S.co;
-  const int nf4 = S.O > 0 ? (S.poly ? S.O : pair_block_f4(S.O)) : 0;
+  const int nf4 = S.O > 0 ? (S.poly ? edge_pair_f4(S.O) : pair_block_f4(S.O)) : 0;
   for (int o = threadIdx.x; o < nf4; o += blockDim.x) circ[o] = admit_circ[A.c0 + o];
   for (int g = threadIdx.x; g < 2 * S.G; g += blockDim.x) {
     p.Gfit2[S.gso + g] = INFINITY;
@@ -476,9 +476,8 @@ int admit(sepso_server_ctx* h, int b) {
     d.pad_poly = 0;
     if (r.poly) {
       d.n_pr = 0;  // no learned prior for a polygon request
-      for (int e = 0; e < r.O; ++e)
-        h->h_acirc[b][c0 + e] = make_float4(r.circ[4 * e], r.circ[4 * e + 1], r.circ[4 * e + 2], r.circ[4 * e + 3]);
-      c0 += r.O;
+      pack_edge_pairs(r.circ.data(), r.O, h->h_acirc[b] + c0);
+      c0 += edge_pair_f4(r.O);
     } else if (r.O > 0) {
       // circle-pair block (layout in sepso_device.cuh)
       const int K = circle_pairs(r.O), nf4 = pair_block_f4(r.O);
@@ -742,7 +741,7 @@ int sepso_server_submit_polygons(sepso_server_handle h, int32_t agent, int32_t T
   if (h->prior) return sfail(SEPSO_EINVAL, "polygon requests are served without the learned prior: detach it");
   if (agent < 0 || agent >= h->cfg.n_agents) return sfail(SEPSO_EINVAL, "agent %d out of range", agent);
   if (T < 1 || T > h->cfg.Tmax) return sfail(SEPSO_EINVAL, "T=%d outside [1, Tmax=%d]", T, h->cfg.Tmax);
-  const int cap = std::min(h->Om, pair_block_f4(h->Om));
+  const int cap = std::min(h->Om, pair_block_f4(h->Om) & ~1);  // the edge pairs fill the circle block
   if (E < 0 || E > cap || (E > 0 && !edges)) return sfail(SEPSO_EINVAL, "E=%d edges invalid (at most %d)", E, cap);
   Request r;
   r.agent = agent;
