@@ -807,13 +807,30 @@ constexpr long long kSmallMaxCoords = 8192;  // swarm size (G N D) up to which a
 // holds the edges two by two (layout at edge_pair_f4).
 __device__ __forceinline__ float poly_lane_pairs(const float* s, int T, const float* pts, const ulonglong2* ep, int K,
                                                  float alpha, int beta, int& qout) {
+  // segment k: start (ax, ay), direction (ux, uy)
+  auto seg = [&](int k, float& ax, float& ay, float& ux, float& uy) {
+    ax = k == 0 ? pts[0] : s[k - 1];
+    ay = k == 0 ? pts[1] : s[T + k - 1];
+    ux = (k == T ? pts[2] : s[k]) - ax;
+    uy = (k == T ? pts[3] : s[T + k]) - ay;
+  };
   float len = 0.0f;
-  int q = 0;
   for (int k = 0; k <= T; ++k) {
-    const float ax = k == 0 ? pts[0] : s[k - 1], ay = k == 0 ? pts[1] : s[T + k - 1];
-    const float bx = k == T ? pts[2] : s[k], by = k == T ? pts[3] : s[T + k];
-    const float ux = bx - ax, uy = by - ay;
+    float ax, ay, ux, uy;
+    seg(k, ax, ay, ux, uy);
     len += sqrtf(fmaf(ux, ux, uy * uy));
+  }
+  // the crossings two segments per edge-pair read
+  int q = 0, k = 0;
+  for (; k + 1 <= T; k += 2) {
+    float ax, ay, ux, uy, ax2, ay2, ux2, uy2;
+    seg(k, ax, ay, ux, uy);
+    seg(k + 1, ax2, ay2, ux2, uy2);
+    q += edge_pair_hits2(ax, ay, ux, uy, ax2, ay2, ux2, uy2, ep, K);
+  }
+  if (k <= T) {
+    float ax, ay, ux, uy;
+    seg(k, ax, ay, ux, uy);
     q += edge_pair_hits(ax, ay, ux, uy, ep, 0, K);
   }
   qout = q;

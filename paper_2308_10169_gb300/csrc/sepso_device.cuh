@@ -609,6 +609,38 @@ __device__ __forceinline__ int edge_pair_hits(float ax, float ay, float ux, floa
   return hits;
 }
 
+// The same for two segments (a -> a + u, a' -> a' + u') per edge pair read: two
+// independent chains per loaded record.
+__device__ __forceinline__ int edge_pair_hits2(float ax, float ay, float ux, float uy, float ax2, float ay2, float ux2,
+                                               float uy2, const ulonglong2* __restrict__ ep, int K) {
+  const unsigned long long NAX = pack2(-ax, -ax), NAY = pack2(-ay, -ay), UX = pack2(ux, ux);
+  const unsigned long long NUX = pack2(-ux, -ux), NUY = pack2(-uy, -uy);
+  const unsigned long long NAX2 = pack2(-ax2, -ax2), NAY2 = pack2(-ay2, -ay2), UX2 = pack2(ux2, ux2);
+  const unsigned long long NUX2 = pack2(-ux2, -ux2), NUY2 = pack2(-uy2, -uy2);
+  int hits = 0;
+  for (int k = 0; k < K; ++k) {
+    const ulonglong2 d0 = ep[2 * k], v = ep[2 * k + 1];
+    const unsigned long long WX = fadd2(d0.x, NAX), WY = fadd2(d0.y, NAY);
+    const unsigned long long WX2 = fadd2(d0.x, NAX2), WY2 = fadd2(d0.y, NAY2);
+    const unsigned long long O1 = ffma2(UX, WY, fmul2(NUY, WX));
+    const unsigned long long O1b = ffma2(UX2, WY2, fmul2(NUY2, WX2));
+    const unsigned long long C = ffma2(NUX, v.y, fmul2(NUY, v.x));
+    const unsigned long long Cb = ffma2(NUX2, v.y, fmul2(NUY2, v.x));
+    const unsigned long long M3 = ffma2(v.x, WY, fmul2(v.y, WX));
+    const unsigned long long M3b = ffma2(v.x, WY2, fmul2(v.y, WX2));
+    const unsigned long long P12 = fmul2(O1, fadd2(O1, C)), P34 = fmul2(M3, fadd2(M3, C));
+    const unsigned long long P12b = fmul2(O1b, fadd2(O1b, Cb)), P34b = fmul2(M3b, fadd2(M3b, Cb));
+    float a12, b12, a34, b34, c12, d12, c34, d34;
+    unpack2(P12, a12, b12);
+    unpack2(P34, a34, b34);
+    unpack2(P12b, c12, d12);
+    unpack2(P34b, c34, d34);
+    hits += (a12 < 0.0f && a34 < 0.0f) + (b12 < 0.0f && b34 < 0.0f) + (c12 < 0.0f && c34 < 0.0f) +
+            (d12 < 0.0f && d34 < 0.0f);
+  }
+  return hits;
+}
+
 __device__ __forceinline__ int edge_hits(float ax, float ay, float bx, float by, const float4* __restrict__ edges,
                                          int e0, int e1) {
   const float ux = bx - ax, uy = by - ay;
